@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Benchmark: InFo-ESRF analyses per second on one GB300 (or N replicas).
+
+One step = one full analysis (mean update + perturbation update: anomalies,
+localized-covariance bands, quadrature, Ritz pairs, the persistent batched
+shifted PCG over all 1280 + 1 systems, quadrature accumulation and the
+state update) of the 1-D Gaussian-forecast workload n=8192, N=40, d=1024,
+Q=32, in FP32 bulk arithmetic with FP64 scalars, through the C ABI.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "perturbation-update analyses/sec at <=1e-4 rel err vs FP64; matvec HBM GB/s"
+UNIT = "analyses/s"
+WORKLOAD = "gauss1d_n8192_N40_d1024_Q32_R0.25_gc256 (1280 shifted systems + mean)"
+TOL_MIXED = 1e-6
+RITZ = 10
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _clock_sampler(path):
+    cmd = ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+           "--format=csv,noheader,nounits", "-lms", "200"]
+    try:
+        return subprocess.Popen(cmd, stdout=open(path, "w"), stderr=subprocess.DEVNULL)
+    except OSError:
+        return None
+
+
+def _clock_summary(path, gpu_index):
+    sm, mx, reasons = [], 0.0, set()
+    try:
+        for line in open(path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9 or f[0] != str(gpu_index):
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+    except OSError:
+        pass
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _oracle_analysis(pr):
+    from oracle import filter as F
+    mu = F.mean_update(pr.X, pr.obs_idx, pr.y, pr.R, pr.grid)
+    A = F.perturbation_update(pr.X, pr.obs_idx, pr.R, pr.grid, pr.Q)
+    return mu, A
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle, as it stands, on the host cores."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    from paper_2503_00253_gb300 import workloads
+    pr = workloads.config2()
+    for _ in range(args.warmup):
+        _oracle_analysis(pr)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _oracle_analysis(pr)
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "precision": "fp64 dense oracle"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "one full analysis (mean + perturbation update, dense FP64) per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2503_00253_gb300 import binding as B
+    from paper_2503_00253_gb300 import workloads
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    B.library()
+    pr = workloads.config2()
+    X = torch.tensor(pr.X, device=dev)
+    obs = torch.tensor(pr.obs_idx, device=dev)
+    y = torch.tensor(pr.y, device=dev)
+    R = torch.tensor(pr.R, device=dev)
+    N, n = pr.X.shape
+    d = pr.d
+    max_oo, max_xo = B.neighbor_counts(pr.grid, obs)
+    cap = max(max_oo, max_xo)
+    prec = B.PRECISION_FP32 if args.precision == "fp32" else B.PRECISION_FP64
+    tol = TOL_MIXED if prec == B.PRECISION_FP32 else args.fp64_tol
+    opts = B.make_options(precision=prec, ritz_rank=RITZ, max_neighbors=cap)
+    g = B.make_grid(pr.grid)
+    import ctypes
+    need = B.library().info_esrf_workspace_size(ctypes.byref(g), N, d, pr.Q, ctypes.byref(opts))
+    wsp = B.workspace(need, dev)
+    mu_a = torch.empty(n, dtype=torch.float64, device=dev)
+    A_a = torch.empty((N, n), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(stats=False):
+        return B.info_esrf_analysis(pr.grid, X, obs, y, R, pr.Q, tol, opts, ws=wsp, mu_a=mu_a, A_a=A_a,
+                                    stats=stats, stream=stream)[2]
+
+    # one run with stats: iteration counts for the flop count, and parity vs the oracle
+    st = step(stats=True)
+    torch.cuda.synchronize()
+    result = {}
+    if rank == 0 and not args.no_parity:
+        from oracle import filter as F
+        mu_ref, A_ref = _oracle_analysis(pr)
+        Af = pr.X - pr.X.mean(0)
+        result["rel_err"] = F.relative_increment_error(A_a.cpu().numpy(), A_ref, Af)
+        mu0 = pr.X.mean(0)
+        result["rel_err_mean"] = float(np.linalg.norm(mu_a.cpu().numpy() - mu_ref) / np.linalg.norm(mu_ref - mu0))
+
+    # exact band size for the algorithmic flop count
+    prep = B.Prepared(pr.grid, X, obs, R, pr.Q, opts)
+    nnz_C = int(prep.export("oo_nnz").sum())
+    nnz_xo = int(prep.export("xo_nnz").sum())
+    del prep
+
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    events = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    for e in events:
+        e.record(stream)
+    B.set_phase_events(opts, events)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clock_path = os.path.join(tempfile.gettempdir(), f"clocks_{os.getpid()}.csv")
+    sampler = _clock_sampler(clock_path) if rank == 0 else None
+    time.sleep(0.3 if sampler else 0.0)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = B.launch_count()
+    step_ms, pcg_ms, phase_ms = [], [], [[0.0] * 4 for _ in range(args.steps)]
+    for s in range(args.steps):
+        flush.fill_(float(s))                       # evicts L2 between timed steps
+        step()
+        events[4].synchronize()
+        step_ms.append(events[0].elapsed_time(events[4]))
+        for i in range(4):
+            phase_ms[s][i] = events[i].elapsed_time(events[i + 1])
+        pcg_ms.append(phase_ms[s][2])
+    torch.cuda.synchronize()
+    launches = B.launch_count() - launches0
+    total_ms = sum(step_ms)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    B.set_phase_events(opts, None)
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    Xh = torch.tensor(pr.X).pin_memory()
+    obsh = torch.tensor(pr.obs_idx).pin_memory()
+    yh = torch.tensor(pr.y).pin_memory()
+    Rh = torch.tensor(pr.R).pin_memory()
+    mu_h = torch.empty(n, dtype=torch.float64).pin_memory()
+    A_h = torch.empty((N, n), dtype=torch.float64).pin_memory()
+    Xd, obsd, yd, Rd = (torch.empty_like(t, device=dev) for t in (Xh, obsh, yh, Rh))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_ms = []
+    for s in range(args.warmup + args.steps):
+        flush.fill_(float(s))
+        e0.record(stream)
+        for dst, src in ((Xd, Xh), (obsd, obsh), (yd, yh), (Rd, Rh)):
+            dst.copy_(src, non_blocking=True)
+        B.info_esrf_analysis(pr.grid, Xd, obsd, yd, Rd, pr.Q, tol, opts, ws=wsp, mu_a=mu_a, A_a=A_a,
+                             stats=False, stream=stream)
+        mu_h.copy_(mu_a, non_blocking=True)
+        A_h.copy_(A_a, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if s >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    if sampler:
+        sampler.terminate()
+        sampler.wait()
+    clocks = _clock_summary(clock_path, local) if rank == 0 else {}
+    h2d = sum(t.numel() * t.element_size() for t in (Xh, obsh, yh, Rh))
+    d2h = mu_h.numel() * 8 + A_h.numel() * 8
+    e2e_total = sum(e2e_ms)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+
+    # FP64 comparator on the same GPU (plain FP64 batched PCG with the paper's preconditioner)
+    fp64 = None
+    if rank == 0 and prec == B.PRECISION_FP32 and args.fp64_steps > 0:
+        o64 = B.make_options(precision=B.PRECISION_FP64, ritz_rank=RITZ, max_neighbors=cap)
+        need64 = B.library().info_esrf_workspace_size(ctypes.byref(g), N, d, pr.Q, ctypes.byref(o64))
+        w64 = B.workspace(need64, dev)
+        mu64 = torch.empty_like(mu_a)
+        A64 = torch.empty_like(A_a)
+        st64 = B.info_esrf_analysis(pr.grid, X, obs, y, R, pr.Q, TOL_MIXED, o64, ws=w64, mu_a=mu64, A_a=A64,
+                                    stats=True, stream=stream)[2]
+        ts = []
+        for s in range(args.fp64_steps):
+            flush.fill_(float(s))
+            e0.record(stream)
+            B.info_esrf_analysis(pr.grid, X, obs, y, R, pr.Q, TOL_MIXED, o64, ws=w64, mu_a=mu64, A_a=A64,
+                                 stats=False, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        fp64 = {"value": 1e3 / statistics.mean(ts), "unit": UNIT, "tol": TOL_MIXED, "steps": args.fp64_steps,
+                "iters_mean": st64["iters_mean"], "ms_per_step": statistics.mean(ts)}
+        if "rel_err" in result:
+            from oracle import filter as F
+            mu_ref, A_ref = _oracle_analysis(pr)
+            fp64["rel_err"] = F.relative_increment_error(A64.cpu().numpy(), A_ref, pr.X - pr.X.mean(0))
+        del w64
+
+    # FMA probe: measured FP32 ALU rate of this GPU (context for the ALU roofline)
+    probe32, _ = B.fma_probe(1, 1 << 16)
+
+    if rank != 0:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    ms_step = total_ms / args.steps
+    value = ws * args.steps / (total_ms * 1e-3)
+    # algorithmic work of the PCG launch: per system-iteration
+    #   2 nnz(C) (matvec) + 2 d (shift) + 8 k d (LMP projections and apply) + 10 d (dots, axpys)
+    sys_iters = st["iters_mean"] * st["n_systems"]
+    flops_iter = 2 * nnz_C / d + 2 + 8 * RITZ + 10            # per row of one system-iteration
+    pcg_flops = sys_iters * d * flops_iter
+    pcg_ms_mean = statistics.mean(pcg_ms)
+    achieved = pcg_flops / (pcg_ms_mean * 1e-3) / 1e12
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    max_mhz = clocks.get("sm_max_mhz") or 2070.0
+    peak = sms * 128 * 2 * max_mhz * 1e6 / 1e12
+    # matvec bytes: the band of C (values + columns) read once per system-group iteration, plus p and y
+    esz = 4 if prec == B.PRECISION_FP32 else 8
+    jt = 8 if prec == B.PRECISION_FP32 else 4
+    group_iters = sys_iters / jt
+    matvec_bytes = group_iters * (nnz_C * (esz + 4) + 2 * d * jt * esz)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec == B.PRECISION_FP32 else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "N": N, "d": d, "Q": pr.Q, "systems": st["n_systems"],
+                   "precision": "fp32 bulk, fp64 scalars and quadrature sum" if prec else "fp64",
+                   "tol": tol, "ritz_rank": RITZ, "band_nnz": nnz_C, "l2": "flushed between steps (512 MB write)",
+                   "replicas": ws},
+        "clocks": clocks,
+        "e2e": {"value": ws * args.steps / (e2e_total * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "kernel": "k_pcg (persistent batched shifted PCG)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None, "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
+                     "fma_probe_tflops": probe32 / 1e12, "pcg_ms": pcg_ms_mean},
+        "matvec_gbs": matvec_bytes / (pcg_ms_mean * 1e-3) / 1e9,
+        "phases_ms": {k: statistics.mean(p[i] for p in phase_ms)
+                      for i, k in enumerate(["setup_a1_a3", "ritz_a4", "pcg_a5_a8", "finish_a9_a11"])},
+        "iters_mean": st["iters_mean"], "iters_max": st["iters_max"], "ell": st["ell_used"],
+    }
+    line.update(result)
+    if fp64:
+        line["fp64_pcg"] = fp64
+    if not args.no_cpu_baseline:
+        from oracle import filter as F  # noqa: F401
+        t0 = time.perf_counter()
+        runs = 0
+        while runs < 3 and (time.perf_counter() - t0) < 20.0:
+            _oracle_analysis(pr)
+            runs += 1
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": runs / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"{runs} full analyses of the same workload (dense FP64 NumPy/LAPACK)"}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--fp64-tol", type=float, default=1e-12)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-parity", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,192 @@
+/*
+ * info_esrf.h -- C ABI of a single-GPU (sm_103a) library for the InFo-ESRF
+ * mean update and perturbation update (Armstrong & Grooms, "Data
+ * Assimilation With An Integral-Form Ensemble Square-Root Filter").
+ *
+ * Operations
+ *   Mean update (Sec. 3.2, Eq. info_esrf_mean_solve):
+ *       mu_a = mu + Sxh (R + Shh)^-1 (y - H mu).
+ *   Perturbation update (Sec. 3.2, Eq. info_esrf_perturbation_solve, App. D-E):
+ *       z_a^(i) = z^(i) - Sxh sum_q p_q v_q^(i),  ((s_q + 1) R + Shh) v_q^(i) = w^(i),
+ *   with (s_q, p_q) the elliptic (App. D, Eq. elliptic_quadrature_rule) or
+ *   Gauss-Legendre (Eq. gaussian_quadrature_rule) rule, every system solved
+ *   in the normalized form of Eq. normalized_linear_solve by PCG with the
+ *   limited-memory preconditioner of App. E.
+ *   Localized covariances (Sec. 2.3, Eq. localized_state_covar):
+ *       Sxx = L o (Z Z^T),  Sxh = Sxx H^T,  Shh = H Sxx H^T,
+ *   Z the normalized perturbations (Eq. normalized_perturbations), H the
+ *   observation subsampling operator given by obs_idx, R diagonal, and L the
+ *   Gaspari-Cohn localization of the grid distance.
+ *
+ * Conventions
+ *   - Every array argument named *_dev is a DEVICE pointer; the caller owns it.
+ *   - Ensembles are member-major: X[k * n + x] is member k at grid point x.
+ *   - Outputs: mu_a [n] the analysis mean; A_a [N][n] the analysis anomalies
+ *     sqrt(N - 1) z_a^(i), so the analysis ensemble is mu_a + A_a.
+ *   - obs_idx [d]: strictly increasing flat grid indices in [0, n).
+ *   - R_diag [d]: observation-error variances, > 0.
+ *   - workspace: caller-allocated device memory of info_esrf_workspace_size()
+ *     bytes, 256-byte aligned.  The library keeps no pointer after return
+ *     and allocates nothing.
+ *   - stream: a cudaStream_t passed as void*; NULL is the legacy stream.  All
+ *     work is stream-ordered.  If stats is NULL the call returns as soon as
+ *     the work is queued; otherwise it waits for the stream and fills stats,
+ *     and device-detected input errors become the return code.
+ *
+ * Return codes: 0 success; > 0 warning (outputs written); < 0 error
+ * (outputs unspecified, nothing freed or leaked).
+ */
+#ifndef INFO_ESRF_H
+#define INFO_ESRF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define INFO_ESRF_OK 0
+#define INFO_ESRF_NOT_CONVERGED 1          /* some system hit max_iter */
+#define INFO_ESRF_ERR_INVALID_ARG (-1)     /* bad size, pointer or option */
+#define INFO_ESRF_ERR_BAD_OBS_INDEX (-2)   /* obs_idx out of range or not increasing */
+#define INFO_ESRF_ERR_NONPOSITIVE_R (-3)   /* R_diag <= 0 or not finite */
+#define INFO_ESRF_ERR_WORKSPACE (-4)       /* workspace too small or misaligned */
+#define INFO_ESRF_ERR_CUDA (-5)            /* a CUDA runtime call failed */
+#define INFO_ESRF_ERR_NONFINITE (-6)       /* NaN or Inf in the ensemble */
+#define INFO_ESRF_ERR_BAND_OVERFLOW (-7)   /* more neighbours than max_neighbors */
+#define INFO_ESRF_ERR_BREAKDOWN (-8)       /* PCG breakdown (p^T C_q p <= 0) */
+#define INFO_ESRF_ERR_UNSUPPORTED (-9)     /* size beyond a documented limit */
+
+#define INFO_ESRF_PRECISION_FP64 0         /* every vector and matrix in FP64 */
+#define INFO_ESRF_PRECISION_FP32 1         /* FP32 bulk, FP64 scalars and quadrature sum */
+
+#define INFO_ESRF_RULE_ELLIPTIC 0          /* App. D, Eq. elliptic_quadrature_rule */
+#define INFO_ESRF_RULE_GAUSS_LEGENDRE 1    /* App. D, Eq. gaussian_quadrature_rule */
+
+/* Regular grid.  Flat index = (z * shape[1] + y) * shape[0] + x.  Axes of
+ * extent 1 are ignored.  The Gaspari-Cohn argument is
+ * r = sqrt(sum_axes (dist_axis / half_width[axis])^2), L = GC(r), zero for
+ * r >= 2 (support 2 * half_width).  On periodic axes dist is the chordal
+ * distance (n / pi) sin(pi |i - j| / n) if chordal != 0 (Sec. 4.1, Sec. 5.2),
+ * otherwise the minimum-image distance; on other axes |i - j|. */
+typedef struct {
+  int64_t shape[3];
+  int32_t periodic[3];
+  int32_t chordal;
+  double half_width[3];
+} info_esrf_grid;
+
+typedef struct {
+  int32_t precision;      /* INFO_ESRF_PRECISION_*; default FP64 */
+  int32_t ritz_rank;      /* k_R Ritz vectors in the preconditioner (App. E); 0 = none; <= 24; default 10 */
+  int32_t oversample;     /* extra test vectors of the randomized eigensolver; default 10; k_R + oversample <= 32 */
+  int32_t power_iters;    /* power iterations of the range finder; default 1 */
+  int32_t max_iter;       /* PCG iteration cap; default 1000 */
+  int32_t fixed_iters;    /* > 0: run exactly this many PCG iterations (paper's experiments) */
+  int32_t rule;           /* INFO_ESRF_RULE_*; default elliptic */
+  int32_t learn_rank;     /* rank of the learned correction (<= 6 with k_R <= 12, else <= 8) */
+  double ell;             /* spectrum bound of App. D; <= 0: power of ten above a Gershgorin bound of C */
+  uint64_t seed;          /* Philox key of the randomized eigensolver's test matrix */
+  int64_t max_neighbors;  /* band capacity per row; <= 0: bound from the geometry */
+  /* Learned diagonal-plus-low-rank correction, device arrays in FP32, or NULL:
+   * learn_diag [Q + 1][d] >= 0 and learn_U [Q + 1][d][learn_rank]; slot Q is
+   * the mean system.  The preconditioner becomes P_q^-1 + D_q + U_q U_q^T. */
+  const float* learn_diag;
+  const float* learn_U;
+  /* NULL, or 5 cudaEvent_t handles (as void*) recorded on the call's stream
+   * at the phase boundaries: start; after the setup of a1-a3 (anomalies, W,
+   * bands, quadrature); after the Ritz pairs (a4); after the persistent PCG
+   * (a5-a8); after the accumulation and state update (a9-a11). */
+  void* const* phase_events;
+} info_esrf_options;
+
+typedef struct {
+  int32_t status;         /* return code of the call */
+  int32_t device_flags;   /* raw device status bits */
+  int32_t iters_max;      /* max PCG iterations over systems */
+  int32_t n_systems;      /* systems solved (Q * N perturbation + mean) */
+  double iters_mean;
+  int32_t n_unconverged;
+  int32_t pad_;
+  double max_rel_resid;   /* max recurrence ||r|| / ||b|| at exit */
+  double ell_used;
+  double gershgorin;      /* max_a sum_b |C(a, b)| */
+} info_esrf_stats;
+
+/* One problem of a batched call: inputs and outputs are device pointers.
+ * mu_a or A_a may be NULL to skip that update (y may then be NULL too). */
+typedef struct {
+  info_esrf_grid grid;
+  int64_t N;              /* members, >= 2 */
+  int64_t d;              /* observations, >= 1 */
+  int32_t Q;              /* quadrature nodes, >= 1 */
+  int32_t pad_;
+  double tol;             /* PCG relative residual tolerance */
+  const double* X;        /* [N][n] */
+  const int64_t* obs_idx; /* [d] */
+  const double* y;        /* [d] */
+  const double* R_diag;   /* [d] */
+  double* mu_a;           /* [n] or NULL */
+  double* A_a;            /* [N][n] or NULL */
+  int64_t max_oo;         /* band capacities; <= 0: from the options / geometry */
+  int64_t max_xo;
+} info_esrf_problem;
+
+/* Fills *opt with the defaults listed above. */
+void info_esrf_default_options(info_esrf_options* opt);
+
+/* Human-readable text of a return code (static storage). */
+const char* info_esrf_error_string(int code);
+
+int info_esrf_version(void);
+
+/* Exact band capacities for one observation pattern: the largest number of
+ * observations inside the Gaspari-Cohn support of any observation (*max_oo)
+ * and of any grid point (*max_xo).  counts_dev is a caller-owned device
+ * buffer of two int64 values used as the kernel's output.  Runs on the
+ * device and synchronizes the stream.  Use the results as problem.max_oo /
+ * max_xo (or options.max_neighbors) to shrink the workspace below the
+ * geometric bound, which assumes every grid point in the support box is
+ * observed. */
+int info_esrf_neighbor_counts(const info_esrf_grid* grid, int64_t d, const int64_t* obs_idx_dev,
+                              int64_t* counts_dev, void* stream, int64_t* max_oo, int64_t* max_xo);
+
+/* Workspace bytes for one problem (both updates) and for a batch. */
+size_t info_esrf_workspace_size(const info_esrf_grid* grid, int64_t N, int64_t d, int32_t Q,
+                                const info_esrf_options* opt);
+size_t info_esrf_batched_workspace_size(const info_esrf_problem* probs, int32_t count,
+                                        const info_esrf_options* opt);
+
+/* Mean update alone (Sec. 3.2, Eq. info_esrf_mean_solve).  Writes mu_a_dev [n]. */
+int info_esrf_mean_update(const info_esrf_grid* grid, int64_t N, const double* X_dev, int64_t d,
+                          const int64_t* obs_idx_dev, const double* y_dev, const double* R_diag_dev,
+                          double tol, const info_esrf_options* opt, void* workspace, size_t ws_bytes,
+                          void* stream, double* mu_a_dev, info_esrf_stats* stats);
+
+/* Perturbation update alone (Sec. 3.2, App. D-E).  Writes A_a_dev [N][n]. */
+int info_esrf_perturbation_update(const info_esrf_grid* grid, int64_t N, const double* X_dev, int64_t d,
+                                  const int64_t* obs_idx_dev, const double* R_diag_dev, int32_t Q,
+                                  double tol, const info_esrf_options* opt, void* workspace,
+                                  size_t ws_bytes, void* stream, double* A_a_dev, info_esrf_stats* stats);
+
+/* Both updates of one analysis sharing one setup (the mean system rides in
+ * the same persistent PCG launch).  Writes mu_a_dev [n] and A_a_dev [N][n]. */
+int info_esrf_analysis(const info_esrf_grid* grid, int64_t N, const double* X_dev, int64_t d,
+                       const int64_t* obs_idx_dev, const double* y_dev, const double* R_diag_dev,
+                       int32_t Q, double tol, const info_esrf_options* opt, void* workspace,
+                       size_t ws_bytes, void* stream, double* mu_a_dev, double* A_a_dev,
+                       info_esrf_stats* stats);
+
+/* Many independent problems of uneven n, N, d and Q in one pass: every stage
+ * is one launch over all problems and the PCG is one persistent launch over
+ * all of their systems.  count <= 64.  stats, if not NULL, has count entries. */
+int info_esrf_analysis_batched(const info_esrf_problem* probs, int32_t count,
+                               const info_esrf_options* opt, void* workspace, size_t ws_bytes,
+                               void* stream, info_esrf_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* INFO_ESRF_H */

@@ -1,0 +1,96 @@
+/*
+ * info_esrf_stages.h -- stage-level entry points of the InFo-ESRF library,
+ * for testing each step of the analysis on its own and for callers that
+ * reuse one prepared operator.  Same conventions as info_esrf.h: *_dev are
+ * device pointers owned by the caller; stream is a cudaStream_t as void*.
+ *
+ * A "prepared" workspace is one on which info_esrf_prepare() ran with the
+ * same (grid, N, d, Q, options); the other calls below recompute its layout
+ * from those arguments and read it.
+ */
+#ifndef INFO_ESRF_STAGES_H
+#define INFO_ESRF_STAGES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include "info_esrf.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Items readable with info_esrf_prepared_export (host destination). */
+#define INFO_ESRF_ITEM_SCALARS 0   /* double[8]: Gershgorin bound, min_a C(a,a), ell, 0... */
+#define INFO_ESRF_ITEM_STATUS 1    /* int32[4]: device status bits */
+#define INFO_ESRF_ITEM_QUAD_S 2    /* double[Q] nodes s_q */
+#define INFO_ESRF_ITEM_QUAD_P 3    /* double[Q] weights p_q */
+#define INFO_ESRF_ITEM_THETA 4     /* double[k_R] Ritz values of C */
+#define INFO_ESRF_ITEM_PHI 5       /* T[d][k_R] Ritz vectors (T = FP64 or FP32 by precision) */
+#define INFO_ESRF_ITEM_CPHI 6      /* T[d][k_R] C Phi */
+#define INFO_ESRF_ITEM_OO_VAL 7    /* T[max_oo][d] band of C, entry e of row a at e*d + a */
+#define INFO_ESRF_ITEM_OO_COL 8    /* int32[max_oo][d] column (obs index) of each entry */
+#define INFO_ESRF_ITEM_OO_NNZ 9    /* int32[d] entries per row */
+#define INFO_ESRF_ITEM_XO_VAL 10   /* T[max_xo][n] band of Sxh, entry e of row x at e*n + x */
+#define INFO_ESRF_ITEM_XO_COL 11   /* int32[max_xo][n] */
+#define INFO_ESRF_ITEM_XO_NNZ 12   /* int32[n] */
+#define INFO_ESRF_ITEM_W 13        /* T[d][N] observed normalized anomalies W = H Z (Eq. normalized_perturbations) */
+#define INFO_ESRF_ITEM_MU 14       /* double[n] ensemble mean */
+
+/* Standard normals from Philox4x32-10 (Salmon et al., SC'11) with Box-Muller:
+ * element e uses counter (e/2, 0, 0, 0) and key (seed lo, seed hi); the test
+ * matrix of the randomized eigensolver (App. E) is element (a, j) = e = j*d + a. */
+int info_esrf_philox_normals(uint64_t seed, int64_t count, double* out_dev, void* stream);
+
+/* Quadrature nodes s_q and weights p_q, q = 1..Q (App. D): the elliptic rule
+ * (Eq. elliptic_quadrature_rule) for spectrum bound ell > 0, or Gauss-Legendre
+ * (Eq. gaussian_quadrature_rule, ell ignored). */
+int info_esrf_quadrature_nodes(int32_t Q, double ell, int32_t rule, double* s_dev, double* p_dev,
+                               void* stream);
+
+/* Runs the setup of one analysis into the workspace: anomalies and W = H Z
+ * (Eq. normalized_perturbations), the bands of C = R^-1/2 Shh R^-1/2 and of
+ * Sxh (Sec. 2.3), the quadrature (App. D) and the Ritz pairs (App. E). */
+int info_esrf_prepare(const info_esrf_grid* grid, int64_t N, const double* X_dev, int64_t d,
+                      const int64_t* obs_idx_dev, const double* R_diag_dev, int32_t Q,
+                      const info_esrf_options* opt, void* workspace, size_t ws_bytes, void* stream);
+
+/* Y_v = sigma_v P_v + C P_v for nvec vectors P [nvec][d] (FP64 in and out; the
+ * product runs in the workspace's precision).  The localized-covariance
+ * matvec of every PCG iteration (App. E, Eq. normalized_linear_solve). */
+int info_esrf_prepared_obs_matvec(const info_esrf_grid* grid, int64_t N, int64_t d, int32_t Q,
+                                  const info_esrf_options* opt, void* workspace, size_t ws_bytes,
+                                  int32_t nvec, const double* P_dev, const double* sigma_dev,
+                                  double* Y_dev, void* stream);
+
+/* Z_v = P^-1 R_v with the limited-memory preconditioner of App. E for the
+ * shifted matrix sigma_v I + C (theta = Ritz values + sigma_v,
+ * beta = sigma_v + min_a C(a, a)), R and Z [nvec][d] in FP64. */
+int info_esrf_prepared_lmp_apply(const info_esrf_grid* grid, int64_t N, int64_t d, int32_t Q,
+                                 const info_esrf_options* opt, void* workspace, size_t ws_bytes,
+                                 int32_t nvec, const double* R_dev, const double* sigma_dev,
+                                 double* Z_dev, void* stream);
+
+/* Copies one prepared array (INFO_ESRF_ITEM_*) to host memory; synchronizes. */
+int info_esrf_prepared_export(const info_esrf_grid* grid, int64_t N, int64_t d, int32_t Q,
+                              const info_esrf_options* opt, void* workspace, size_t ws_bytes,
+                              int32_t item, void* dst_host, size_t dst_bytes, void* stream);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (host-side counter; used to report launches per analysis). */
+int64_t info_esrf_launch_count(void);
+
+/* Sustained FMA throughput of this GPU: every SM runs independent FMA chains
+ * for about iters steps per thread in FP32 (precision 1) or FP64 (precision 0).
+ * Writes the achieved FLOP/s (2 per FMA) and the kernel time in ms; synchronizes. */
+int info_esrf_fma_probe(int32_t precision, int64_t iters, double* flops_per_s, double* ms, void* stream);
+
+/* Band capacities the workspace layout uses for these arguments. */
+int info_esrf_prepared_band_capacity(const info_esrf_grid* grid, int64_t N, int64_t d, int32_t Q,
+                                     const info_esrf_options* opt, int64_t* max_oo, int64_t* max_xo);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* INFO_ESRF_STAGES_H */

@@ -1,0 +1,428 @@
+"""Thin Python binding of the C ABI (include/info_esrf.h, include/info_esrf_stages.h).
+
+Argument marshalling only: ctypes structures that mirror the C structs, and
+functions with the C names that take torch tensors, pass their device
+pointers and the current CUDA stream, and return the outputs.  Every step of
+the analysis runs inside ``libinfo_esrf.so``; if the library is missing the
+import fails, there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import torch
+
+from . import build as _build
+
+c_int32, c_int64, c_double, c_uint64, c_void_p = (ctypes.c_int32, ctypes.c_int64, ctypes.c_double,
+                                                  ctypes.c_uint64, ctypes.c_void_p)
+
+OK = 0
+NOT_CONVERGED = 1
+ERR_INVALID_ARG = -1
+ERR_BAD_OBS_INDEX = -2
+ERR_NONPOSITIVE_R = -3
+ERR_WORKSPACE = -4
+ERR_CUDA = -5
+ERR_NONFINITE = -6
+ERR_BAND_OVERFLOW = -7
+ERR_BREAKDOWN = -8
+ERR_UNSUPPORTED = -9
+
+PRECISION_FP64 = 0
+PRECISION_FP32 = 1
+RULE_ELLIPTIC = 0
+RULE_GAUSS_LEGENDRE = 1
+
+ITEM = dict(scalars=0, status=1, quad_s=2, quad_p=3, theta=4, phi=5, cphi=6, oo_val=7, oo_col=8,
+            oo_nnz=9, xo_val=10, xo_col=11, xo_nnz=12, W=13, mu=14)
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("shape", c_int64 * 3), ("periodic", c_int32 * 3), ("chordal", c_int32),
+                ("half_width", c_double * 3)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", c_int32), ("ritz_rank", c_int32), ("oversample", c_int32),
+                ("power_iters", c_int32), ("max_iter", c_int32), ("fixed_iters", c_int32),
+                ("rule", c_int32), ("learn_rank", c_int32), ("ell", c_double), ("seed", c_uint64),
+                ("max_neighbors", c_int64), ("learn_diag", c_void_p), ("learn_U", c_void_p),
+                ("phase_events", ctypes.POINTER(c_void_p))]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("status", c_int32), ("device_flags", c_int32), ("iters_max", c_int32),
+                ("n_systems", c_int32), ("iters_mean", c_double), ("n_unconverged", c_int32),
+                ("pad_", c_int32), ("max_rel_resid", c_double), ("ell_used", c_double),
+                ("gershgorin", c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+
+
+class ProblemC(ctypes.Structure):
+    _fields_ = [("grid", Grid), ("N", c_int64), ("d", c_int64), ("Q", c_int32), ("pad_", c_int32),
+                ("tol", c_double), ("X", c_void_p), ("obs_idx", c_void_p), ("y", c_void_p),
+                ("R_diag", c_void_p), ("mu_a", c_void_p), ("A_a", c_void_p), ("max_oo", c_int64),
+                ("max_xo", c_int64)]
+
+
+_LIB = None
+
+
+def library() -> ctypes.CDLL:
+    """Loads libinfo_esrf.so (building it first if sources are newer)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.library_path()
+    if not _build.up_to_date():
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing; run build() first")
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    sig = {
+        "info_esrf_default_options": (None, [P(Options)]),
+        "info_esrf_error_string": (ctypes.c_char_p, [c_int32]),
+        "info_esrf_version": (c_int32, []),
+        "info_esrf_neighbor_counts": (c_int32, [P(Grid), c_int64, c_void_p, c_void_p, c_void_p,
+                                                P(c_int64), P(c_int64)]),
+        "info_esrf_workspace_size": (ctypes.c_size_t, [P(Grid), c_int64, c_int64, c_int32, P(Options)]),
+        "info_esrf_batched_workspace_size": (ctypes.c_size_t, [P(ProblemC), c_int32, P(Options)]),
+        "info_esrf_mean_update": (c_int32, [P(Grid), c_int64, c_void_p, c_int64, c_void_p, c_void_p,
+                                            c_void_p, c_double, P(Options), c_void_p, ctypes.c_size_t,
+                                            c_void_p, c_void_p, P(Stats)]),
+        "info_esrf_perturbation_update": (c_int32, [P(Grid), c_int64, c_void_p, c_int64, c_void_p,
+                                                    c_void_p, c_int32, c_double, P(Options), c_void_p,
+                                                    ctypes.c_size_t, c_void_p, c_void_p, P(Stats)]),
+        "info_esrf_analysis": (c_int32, [P(Grid), c_int64, c_void_p, c_int64, c_void_p, c_void_p,
+                                         c_void_p, c_int32, c_double, P(Options), c_void_p,
+                                         ctypes.c_size_t, c_void_p, c_void_p, c_void_p, P(Stats)]),
+        "info_esrf_analysis_batched": (c_int32, [P(ProblemC), c_int32, P(Options), c_void_p,
+                                                 ctypes.c_size_t, c_void_p, P(Stats)]),
+        "info_esrf_philox_normals": (c_int32, [c_uint64, c_int64, c_void_p, c_void_p]),
+        "info_esrf_quadrature_nodes": (c_int32, [c_int32, c_double, c_int32, c_void_p, c_void_p,
+                                                 c_void_p]),
+        "info_esrf_prepare": (c_int32, [P(Grid), c_int64, c_void_p, c_int64, c_void_p, c_void_p,
+                                        c_int32, P(Options), c_void_p, ctypes.c_size_t, c_void_p]),
+        "info_esrf_prepared_obs_matvec": (c_int32, [P(Grid), c_int64, c_int64, c_int32, P(Options),
+                                                    c_void_p, ctypes.c_size_t, c_int32, c_void_p,
+                                                    c_void_p, c_void_p, c_void_p]),
+        "info_esrf_prepared_lmp_apply": (c_int32, [P(Grid), c_int64, c_int64, c_int32, P(Options),
+                                                   c_void_p, ctypes.c_size_t, c_int32, c_void_p,
+                                                   c_void_p, c_void_p, c_void_p]),
+        "info_esrf_prepared_export": (c_int32, [P(Grid), c_int64, c_int64, c_int32, P(Options),
+                                                c_void_p, ctypes.c_size_t, c_int32, c_void_p,
+                                                ctypes.c_size_t, c_void_p]),
+        "info_esrf_launch_count": (c_int64, []),
+        "info_esrf_fma_probe": (c_int32, [c_int32, c_int64, P(c_double), P(c_double), c_void_p]),
+        "info_esrf_prepared_band_capacity": (c_int32, [P(Grid), c_int64, c_int64, c_int32, P(Options),
+                                                       P(c_int64), P(c_int64)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+class InfoEsrfError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = library().info_esrf_error_string(code).decode()
+        super().__init__(f"{where}: {msg} (code {code})")
+        self.code = code
+
+
+def _check(code: int, where: str, allow_warning: bool = True) -> int:
+    if code < 0 or (code > 0 and not allow_warning):
+        raise InfoEsrfError(code, where)
+    return code
+
+
+# ---------------------------------------------------------------------------
+# Marshalling helpers
+# ---------------------------------------------------------------------------
+
+def make_grid(grid) -> Grid:
+    """Converts any object with shape / periodic / half_width / chordal attributes."""
+    g = Grid()
+    shape = list(grid.shape) + [1] * (3 - len(grid.shape))
+    per = list(grid.periodic) + [False] * (3 - len(grid.periodic))
+    hw = list(grid.half_width) + [1.0] * (3 - len(grid.half_width))
+    for i in range(3):
+        g.shape[i] = int(shape[i])
+        g.periodic[i] = 1 if per[i] else 0
+        g.half_width[i] = float(hw[i])
+    g.chordal = 1 if getattr(grid, "chordal", True) else 0
+    return g
+
+
+def make_options(precision: int = PRECISION_FP64, ritz_rank: int = 10, oversample: int = 10,
+                 power_iters: int = 1, max_iter: int = 1000, fixed_iters: int = 0,
+                 rule: int = RULE_ELLIPTIC, ell: float = 0.0, seed: int = 0x1234ABCD,
+                 max_neighbors: int = 0, learn_diag: Optional[torch.Tensor] = None,
+                 learn_U: Optional[torch.Tensor] = None, learn_rank: int = 0) -> Options:
+    o = Options()
+    library().info_esrf_default_options(ctypes.byref(o))
+    o.precision, o.ritz_rank, o.oversample, o.power_iters = precision, ritz_rank, oversample, power_iters
+    o.max_iter, o.fixed_iters, o.rule, o.ell, o.seed = max_iter, fixed_iters, rule, ell, seed
+    o.max_neighbors = max_neighbors
+    if learn_diag is not None:
+        _need(learn_diag, torch.float32, "learn_diag")
+        o.learn_diag = learn_diag.data_ptr()
+        o.learn_rank = learn_rank
+        if learn_rank > 0:
+            _need(learn_U, torch.float32, "learn_U")
+            o.learn_U = learn_U.data_ptr()
+    return o
+
+
+def _need(t: torch.Tensor, dtype, name: str):
+    if not isinstance(t, torch.Tensor) or t.dtype != dtype or not t.is_cuda or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous CUDA tensor of {dtype}")
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def set_phase_events(options: Options, events) -> None:
+    """Records the 5 torch.cuda.Event objects at the library's phase boundaries (None: off)."""
+    if events is None:
+        options.phase_events = None
+        return
+    arr = (c_void_p * 5)(*[e.cuda_event for e in events])
+    options._phase_keep = arr
+    options.phase_events = ctypes.cast(arr, ctypes.POINTER(c_void_p))
+
+
+def launch_count() -> int:
+    return int(library().info_esrf_launch_count())
+
+
+def fma_probe(precision: int, iters: int, stream=None):
+    f, ms = c_double(), c_double()
+    _check(library().info_esrf_fma_probe(precision, iters, ctypes.byref(f), ctypes.byref(ms), _stream(stream)),
+           "info_esrf_fma_probe")
+    return f.value, ms.value
+
+
+def workspace(nbytes: int, device=None) -> torch.Tensor:
+    """Device workspace (256-byte aligned; torch allocations are)."""
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device or "cuda")
+
+
+def neighbor_counts(grid, obs_idx: torch.Tensor, stream=None):
+    _need(obs_idx, torch.int64, "obs_idx")
+    g = make_grid(grid)
+    buf = torch.zeros(2, dtype=torch.int64, device=obs_idx.device)
+    a, b = c_int64(), c_int64()
+    _check(library().info_esrf_neighbor_counts(ctypes.byref(g), obs_idx.numel(), obs_idx.data_ptr(),
+                                               buf.data_ptr(), _stream(stream), ctypes.byref(a),
+                                               ctypes.byref(b)), "info_esrf_neighbor_counts")
+    return int(a.value), int(b.value)
+
+
+def workspace_size(grid, N: int, d: int, Q: int, options: Options) -> int:
+    g = make_grid(grid)
+    return int(library().info_esrf_workspace_size(ctypes.byref(g), N, d, Q, ctypes.byref(options)))
+
+
+# ---------------------------------------------------------------------------
+# Entry points with the C names
+# ---------------------------------------------------------------------------
+
+def info_esrf_analysis(grid, X: torch.Tensor, obs_idx: torch.Tensor, y: torch.Tensor, R: torch.Tensor,
+                       Q: int, tol: float, options: Optional[Options] = None, ws: Optional[torch.Tensor] = None,
+                       mu_a: Optional[torch.Tensor] = None, A_a: Optional[torch.Tensor] = None,
+                       stats: bool = True, stream=None, allow_warning: bool = True):
+    """Mean and perturbation update of one analysis.  Returns (mu_a, A_a, stats or None)."""
+    for t, name, dt in ((X, "X", torch.float64), (obs_idx, "obs_idx", torch.int64),
+                        (y, "y", torch.float64), (R, "R", torch.float64)):
+        _need(t, dt, name)
+    N, n = X.shape
+    d = obs_idx.numel()
+    o = options if options is not None else make_options()
+    g = make_grid(grid)
+    need = library().info_esrf_workspace_size(ctypes.byref(g), N, d, Q, ctypes.byref(o))
+    if ws is None:
+        ws = workspace(need, X.device)
+    if mu_a is None:
+        mu_a = torch.empty(n, dtype=torch.float64, device=X.device)
+    if A_a is None:
+        A_a = torch.empty((N, n), dtype=torch.float64, device=X.device)
+    st = Stats()
+    code = library().info_esrf_analysis(ctypes.byref(g), N, X.data_ptr(), d, obs_idx.data_ptr(), y.data_ptr(),
+                                        R.data_ptr(), Q, tol, ctypes.byref(o), ws.data_ptr(), ws.numel(),
+                                        _stream(stream), mu_a.data_ptr(), A_a.data_ptr(),
+                                        ctypes.byref(st) if stats else None)
+    _check(code, "info_esrf_analysis", allow_warning)
+    return mu_a, A_a, (st.as_dict() if stats else None)
+
+
+def info_esrf_mean_update(grid, X, obs_idx, y, R, tol, options=None, ws=None, mu_a=None, stats=True,
+                          stream=None):
+    for t, name, dt in ((X, "X", torch.float64), (obs_idx, "obs_idx", torch.int64),
+                        (y, "y", torch.float64), (R, "R", torch.float64)):
+        _need(t, dt, name)
+    N, n = X.shape
+    d = obs_idx.numel()
+    o = options if options is not None else make_options()
+    g = make_grid(grid)
+    if ws is None:
+        ws = workspace(library().info_esrf_workspace_size(ctypes.byref(g), N, d, 1, ctypes.byref(o)), X.device)
+    if mu_a is None:
+        mu_a = torch.empty(n, dtype=torch.float64, device=X.device)
+    st = Stats()
+    code = library().info_esrf_mean_update(ctypes.byref(g), N, X.data_ptr(), d, obs_idx.data_ptr(), y.data_ptr(),
+                                           R.data_ptr(), tol, ctypes.byref(o), ws.data_ptr(), ws.numel(),
+                                           _stream(stream), mu_a.data_ptr(), ctypes.byref(st) if stats else None)
+    _check(code, "info_esrf_mean_update")
+    return mu_a, (st.as_dict() if stats else None)
+
+
+def info_esrf_perturbation_update(grid, X, obs_idx, R, Q, tol, options=None, ws=None, A_a=None, stats=True,
+                                  stream=None):
+    for t, name, dt in ((X, "X", torch.float64), (obs_idx, "obs_idx", torch.int64), (R, "R", torch.float64)):
+        _need(t, dt, name)
+    N, n = X.shape
+    d = obs_idx.numel()
+    o = options if options is not None else make_options()
+    g = make_grid(grid)
+    if ws is None:
+        ws = workspace(library().info_esrf_workspace_size(ctypes.byref(g), N, d, Q, ctypes.byref(o)), X.device)
+    if A_a is None:
+        A_a = torch.empty((N, n), dtype=torch.float64, device=X.device)
+    st = Stats()
+    code = library().info_esrf_perturbation_update(ctypes.byref(g), N, X.data_ptr(), d, obs_idx.data_ptr(),
+                                                   R.data_ptr(), Q, tol, ctypes.byref(o), ws.data_ptr(),
+                                                   ws.numel(), _stream(stream), A_a.data_ptr(),
+                                                   ctypes.byref(st) if stats else None)
+    _check(code, "info_esrf_perturbation_update")
+    return A_a, (st.as_dict() if stats else None)
+
+
+def info_esrf_analysis_batched(problems: Sequence[dict], options: Optional[Options] = None,
+                               ws: Optional[torch.Tensor] = None, stats: bool = True, stream=None):
+    """problems: dicts with grid, X, obs_idx, y, R, Q, tol and optional mu_a, A_a, max_oo, max_xo."""
+    arr = (ProblemC * len(problems))()
+    keep = []
+    for i, p in enumerate(problems):
+        X = p["X"]
+        _need(X, torch.float64, "X")
+        N, n = X.shape
+        mu_a = p.get("mu_a")
+        A_a = p.get("A_a")
+        if mu_a is None:
+            mu_a = torch.empty(n, dtype=torch.float64, device=X.device)
+        if A_a is None:
+            A_a = torch.empty((N, n), dtype=torch.float64, device=X.device)
+        keep.append((mu_a, A_a))
+        c = arr[i]
+        c.grid = make_grid(p["grid"])
+        c.N, c.d, c.Q, c.tol = N, p["obs_idx"].numel(), int(p["Q"]), float(p["tol"])
+        c.X, c.obs_idx, c.y, c.R_diag = X.data_ptr(), p["obs_idx"].data_ptr(), p["y"].data_ptr(), p["R"].data_ptr()
+        c.mu_a, c.A_a = mu_a.data_ptr(), A_a.data_ptr()
+        c.max_oo, c.max_xo = int(p.get("max_oo", 0)), int(p.get("max_xo", 0))
+    o = options if options is not None else make_options()
+    need = library().info_esrf_batched_workspace_size(arr, len(problems), ctypes.byref(o))
+    if need == 0:
+        raise InfoEsrfError(ERR_INVALID_ARG, "info_esrf_batched_workspace_size")
+    if ws is None or ws.numel() < need:
+        ws = workspace(need)
+    st = (Stats * len(problems))()
+    code = library().info_esrf_analysis_batched(arr, len(problems), ctypes.byref(o), ws.data_ptr(), ws.numel(),
+                                                _stream(stream), st if stats else None)
+    _check(code, "info_esrf_analysis_batched")
+    return keep, ([s.as_dict() for s in st] if stats else None)
+
+
+def info_esrf_philox_normals(seed: int, count: int, device="cuda", stream=None) -> torch.Tensor:
+    out = torch.empty(max(count, 1), dtype=torch.float64, device=device)
+    _check(library().info_esrf_philox_normals(seed, count, out.data_ptr(), _stream(stream)),
+           "info_esrf_philox_normals")
+    return out[:count]
+
+
+def info_esrf_quadrature_nodes(Q: int, ell: float, rule: int = RULE_ELLIPTIC, device="cuda", stream=None):
+    s = torch.empty(Q, dtype=torch.float64, device=device)
+    p = torch.empty(Q, dtype=torch.float64, device=device)
+    _check(library().info_esrf_quadrature_nodes(Q, ell, rule, s.data_ptr(), p.data_ptr(), _stream(stream)),
+           "info_esrf_quadrature_nodes")
+    return s, p
+
+
+class Prepared:
+    """A workspace on which info_esrf_prepare ran, with its stage-level calls."""
+
+    def __init__(self, grid, X, obs_idx, R, Q, options: Optional[Options] = None, stream=None):
+        _need(X, torch.float64, "X")
+        _need(obs_idx, torch.int64, "obs_idx")
+        _need(R, torch.float64, "R")
+        self.g = make_grid(grid)
+        self.N, self.n = X.shape
+        self.d = obs_idx.numel()
+        self.Q = Q
+        self.o = options if options is not None else make_options()
+        self.precision = self.o.precision
+        lib = library()
+        need = lib.info_esrf_workspace_size(ctypes.byref(self.g), self.N, self.d, Q, ctypes.byref(self.o))
+        self.ws = workspace(need, X.device)
+        self.stream = stream
+        _check(lib.info_esrf_prepare(ctypes.byref(self.g), self.N, X.data_ptr(), self.d, obs_idx.data_ptr(),
+                                     R.data_ptr(), Q, ctypes.byref(self.o), self.ws.data_ptr(), self.ws.numel(),
+                                     _stream(stream)), "info_esrf_prepare")
+
+    def _args(self):
+        return (ctypes.byref(self.g), self.N, self.d, self.Q, ctypes.byref(self.o), self.ws.data_ptr(),
+                self.ws.numel())
+
+    def obs_matvec(self, P: torch.Tensor, sigma: torch.Tensor) -> torch.Tensor:
+        _need(P, torch.float64, "P")
+        _need(sigma, torch.float64, "sigma")
+        Y = torch.empty_like(P)
+        _check(library().info_esrf_prepared_obs_matvec(*self._args(), P.shape[0], P.data_ptr(), sigma.data_ptr(),
+                                                       Y.data_ptr(), _stream(self.stream)),
+               "info_esrf_prepared_obs_matvec")
+        return Y
+
+    def lmp_apply(self, Rv: torch.Tensor, sigma: torch.Tensor) -> torch.Tensor:
+        _need(Rv, torch.float64, "R")
+        _need(sigma, torch.float64, "sigma")
+        Z = torch.empty_like(Rv)
+        _check(library().info_esrf_prepared_lmp_apply(*self._args(), Rv.shape[0], Rv.data_ptr(), sigma.data_ptr(),
+                                                      Z.data_ptr(), _stream(self.stream)),
+               "info_esrf_prepared_lmp_apply")
+        return Z
+
+    def capacity(self):
+        a, b = c_int64(), c_int64()
+        _check(library().info_esrf_prepared_band_capacity(ctypes.byref(self.g), self.N, self.d, self.Q,
+                                                          ctypes.byref(self.o), ctypes.byref(a), ctypes.byref(b)),
+               "info_esrf_prepared_band_capacity")
+        return int(a.value), int(b.value)
+
+    def export(self, item: str):
+        """Copies one prepared array to a host torch tensor."""
+        import numpy as np
+        esz = 8 if self.precision == 0 else 4
+        fdt = np.float64 if esz == 8 else np.float32
+        mo, mx = self.capacity()
+        kR = min(self.o.ritz_rank, self.d)
+        shapes = dict(scalars=(8, np.float64), status=(4, np.int32), quad_s=(self.Q, np.float64),
+                      quad_p=(self.Q, np.float64), theta=(kR, np.float64), phi=(self.d * kR, fdt),
+                      cphi=(self.d * kR, fdt), oo_val=(mo * self.d, fdt), oo_col=(mo * self.d, np.int32),
+                      oo_nnz=(self.d, np.int32), xo_val=(mx * self.n, fdt), xo_col=(mx * self.n, np.int32),
+                      xo_nnz=(self.n, np.int32), W=(self.d * self.N, fdt), mu=(self.n, np.float64))
+        count, dt = shapes[item]
+        out = np.zeros(max(count, 1), dtype=dt)
+        _check(library().info_esrf_prepared_export(*self._args(), ITEM[item], out.ctypes.data, out.nbytes,
+                                                   _stream(self.stream)), "info_esrf_prepared_export")
+        return out[:count]

@@ -1,0 +1,589 @@
+// Host side of the C ABI: argument checks, workspace layout, the launch
+// sequence of one analysis and the optional stats read-back.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <vector>
+
+#include "info_esrf.h"
+#include "info_esrf_stages.h"
+#include "internal.h"
+
+using namespace infoesrf;
+
+namespace infoesrf {
+static std::atomic<long long> g_launches{0};
+void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace infoesrf
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct Carver {
+  char* base;        // may be null while sizing
+  size_t off = 0;
+  template <typename P>
+  P* take(size_t bytes) {
+    P* p = base ? reinterpret_cast<P*>(base + off) : nullptr;
+    off = align_up(off + (bytes ? bytes : 1));
+    return p;
+  }
+};
+
+int num_sms_current() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 160;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+    cudaGetLastError();
+    return 160;
+  }
+  return sms;
+}
+
+// Geometry -> device grid descriptor; candidate reach per axis.
+int make_grid(const info_esrf_grid* g, GridDev* out) {
+  if (!g) return INFO_ESRF_ERR_INVALID_ARG;
+  memset(out, 0, sizeof(*out));
+  out->chordal = g->chordal ? 1 : 0;
+  for (int ax = 0; ax < 3; ++ax) {
+    const int64_t e = g->shape[ax];
+    if (e < 1) return INFO_ESRF_ERR_INVALID_ARG;
+    out->ext[ax] = e;
+    out->periodic[ax] = g->periodic[ax] ? 1 : 0;
+    if (e == 1) {
+      out->reach[ax] = 0;
+      out->whole[ax] = 1;
+      out->inv_c[ax] = 0.0;
+      continue;
+    }
+    const double c = g->half_width[ax];
+    if (!(c > 0.0) || !isfinite(c)) return INFO_ESRF_ERR_INVALID_ARG;
+    out->inv_c[ax] = 1.0 / c;
+    // candidates: every offset whose axis distance alone can be below 2c
+    double lim = 2.0 * c;
+    int64_t reach;
+    if (out->periodic[ax] && out->chordal) {
+      const double top = (double)e / M_PI;        // largest chordal distance
+      if (lim >= top) reach = e;                  // whole axis
+      else reach = (int64_t)floor((double)e / M_PI * asin(lim * M_PI / (double)e)) + 1;
+    } else {
+      reach = (int64_t)ceil(lim);
+    }
+    if (out->periodic[ax]) {
+      if (2 * reach + 1 >= e) { out->whole[ax] = 1; reach = e; }
+    } else if (reach >= e) {
+      reach = e - 1;
+    }
+    out->reach[ax] = reach;
+  }
+  return 0;
+}
+
+int64_t geometric_bound(const GridDev& g, int64_t d) {
+  double count = 1.0;
+  for (int ax = 0; ax < 3; ++ax) {
+    if (g.ext[ax] <= 1) continue;
+    count *= g.whole[ax] ? (double)g.ext[ax] : (double)(2 * g.reach[ax] + 1);
+  }
+  return (int64_t)std::min<double>(count, (double)d);
+}
+
+int check_options(const info_esrf_options* in, info_esrf_options* out) {
+  info_esrf_default_options(out);
+  if (in) *out = *in;
+  if (out->precision != 0 && out->precision != 1) return INFO_ESRF_ERR_INVALID_ARG;
+  if (out->ritz_rank < 0 || out->ritz_rank > kMaxK) return INFO_ESRF_ERR_UNSUPPORTED;
+  if (out->oversample < 0) return INFO_ESRF_ERR_INVALID_ARG;
+  if (out->power_iters < 0 || out->power_iters > 8) return INFO_ESRF_ERR_INVALID_ARG;
+  if (out->max_iter < 1 && out->fixed_iters <= 0) return INFO_ESRF_ERR_INVALID_ARG;
+  if (out->rule != 0 && out->rule != 1) return INFO_ESRF_ERR_INVALID_ARG;
+  if (out->learn_rank < 0 || out->learn_rank > kMaxLearnRank) return INFO_ESRF_ERR_UNSUPPORTED;
+  if (out->learn_diag && out->learn_rank > 0 && !out->learn_U) return INFO_ESRF_ERR_INVALID_ARG;
+  if (out->learn_diag && out->ritz_rank <= 12 && out->learn_rank > 6) return INFO_ESRF_ERR_UNSUPPORTED;
+  return 0;
+}
+
+// Fills pr (sizes, options) and carves its workspace slice.
+void carve_problem(Carver& cv, ProblemDev& pr, const info_esrf_options& o) {
+  const size_t esz = o.precision == 0 ? 8 : 4;
+  const int64_t n = pr.n, N = pr.N, d = pr.d;
+  const int l = pr.l, k = pr.kR;
+  pr.mu = cv.take<double>(n * 8);
+  pr.Zt = cv.take<void>(n * N * esz);
+  pr.W = cv.take<void>(d * N * esz);
+  pr.rinv = cv.take<double>(d * 8);
+  pr.bmean = cv.take<double>(d * 8);
+  pr.scal = cv.take<double>(8 * 8);
+  pr.status = cv.take<int32_t>(4 * 4);
+  pr.s = cv.take<double>((size_t)std::max(pr.Q, 1) * 8);
+  pr.p = cv.take<double>((size_t)std::max(pr.Q, 1) * 8);
+  pr.oo_val = cv.take<void>((size_t)pr.max_oo * d * esz);
+  pr.oo_col = cv.take<int32_t>((size_t)pr.max_oo * d * 4);
+  pr.oo_nnz = cv.take<int32_t>(d * 4);
+  pr.xo_val = cv.take<void>((size_t)pr.max_xo * n * esz);
+  pr.xo_col = cv.take<int32_t>((size_t)pr.max_xo * n * 4);
+  pr.xo_nnz = cv.take<int32_t>(n * 4);
+  pr.Om = cv.take<double>((size_t)d * l * 8);
+  pr.Yb = cv.take<double>((size_t)d * l * 8);
+  pr.Gm = cv.take<double>((size_t)l * l * 8);
+  pr.Rm = cv.take<double>((size_t)l * l * 8);
+  pr.ev = cv.take<double>((size_t)l * 8);
+  pr.Phi = cv.take<void>((size_t)d * k * esz);
+  pr.CPhi = cv.take<void>((size_t)d * k * esz);
+  pr.theta = cv.take<double>((size_t)k * 8);
+  pr.gram = cv.take<double>((size_t)3 * k * k * 8);
+  pr.U = cv.take<void>((size_t)pr.num_groups * d * pr.JT * esz);
+  pr.iters = cv.take<int32_t>((size_t)pr.num_groups * pr.JT * 4);
+  pr.relres = cv.take<double>((size_t)pr.num_groups * pr.JT * 8);
+  pr.Vbar = cv.take<double>((size_t)d * (N + 1) * 8);
+  pr.VbarT = cv.take<void>((size_t)d * (N + 1) * esz);
+}
+
+// Builds the host table for a batch; with ws == nullptr only sizes it.
+int build_table(const info_esrf_problem* probs, int32_t count, const info_esrf_options& o, void* ws,
+                ProblemTable& tab, size_t* bytes_out, ProblemDev** dtab_out, int32_t** counter_out,
+                void** scratch_out, size_t* scratch_bytes_out, int num_sms) {
+  if (count < 1) return INFO_ESRF_ERR_INVALID_ARG;
+  if (count > kMaxProblems) return INFO_ESRF_ERR_UNSUPPORTED;
+  memset(&tab, 0, sizeof(tab));
+  tab.count = count;
+  Carver cv{reinterpret_cast<char*>(ws)};
+  ProblemDev* dtab = cv.take<ProblemDev>(sizeof(ProblemDev) * count);
+  int32_t* counter = cv.take<int32_t>(64);
+  int group_base = 0;
+  const int JT = pcg_jt(o.precision);
+  for (int i = 0; i < count; ++i) {
+    const info_esrf_problem& P = probs[i];
+    ProblemDev& pr = tab.p[i];
+    int rc = make_grid(&P.grid, &pr.grid);
+    if (rc) return rc;
+    pr.n = P.grid.shape[0] * P.grid.shape[1] * P.grid.shape[2];
+    pr.N = P.N;
+    pr.d = P.d;
+    pr.do_mean = P.mu_a != nullptr;
+    pr.do_pert = P.A_a != nullptr;
+    if (!pr.do_mean && !pr.do_pert) return INFO_ESRF_ERR_INVALID_ARG;
+    if (pr.N < 2 || pr.d < 1 || pr.n < 1 || pr.d > pr.n) return INFO_ESRF_ERR_INVALID_ARG;
+    if (pr.n > INT32_MAX || pr.d > INT32_MAX) return INFO_ESRF_ERR_UNSUPPORTED;
+    pr.Q = pr.do_pert ? P.Q : 0;
+    if (pr.do_pert && P.Q < 1) return INFO_ESRF_ERR_INVALID_ARG;
+    if (o.fixed_iters <= 0 && !(P.tol > 0.0)) return INFO_ESRF_ERR_INVALID_ARG;
+    if (!P.X || !P.obs_idx || !P.R_diag || (pr.do_mean && !P.y)) return INFO_ESRF_ERR_INVALID_ARG;
+    pr.tol = P.tol;
+    pr.kR = (int32_t)std::min<int64_t>(o.ritz_rank, pr.d);
+    pr.l = pr.kR > 0 ? (int32_t)std::min<int64_t>(std::min<int64_t>(pr.kR + o.oversample, kMaxRitz), pr.d) : 0;
+    pr.rule = o.rule;
+    pr.precision = o.precision;
+    pr.fixed_iters = o.fixed_iters;
+    pr.max_iter = o.max_iter;
+    pr.power_iters = o.power_iters;
+    pr.learn_rank = o.learn_diag ? o.learn_rank : 0;
+    pr.learn_diag = o.learn_diag;
+    pr.learn_U = o.learn_U;
+    pr.ell_fixed = o.ell;
+    pr.seed = o.seed;
+    pr.sqrt_nm1 = sqrt((double)(pr.N - 1));
+    const int64_t gb = geometric_bound(pr.grid, pr.d);
+    int64_t cap_oo = P.max_oo > 0 ? P.max_oo : (o.max_neighbors > 0 ? o.max_neighbors : gb);
+    int64_t cap_xo = P.max_xo > 0 ? P.max_xo : (o.max_neighbors > 0 ? o.max_neighbors : gb);
+    pr.max_oo = std::min(cap_oo, pr.d);
+    pr.max_xo = std::min(cap_xo, pr.d);
+    pr.X = P.X;
+    pr.obs = P.obs_idx;
+    pr.y = P.y;
+    pr.R = P.R_diag;
+    pr.mu_a = P.mu_a;
+    pr.A_a = P.A_a;
+    pr.JT = JT;
+    pr.groups_per_q = (int32_t)((pr.N + JT - 1) / JT);
+    pr.num_groups = (pr.do_pert ? pr.Q * pr.groups_per_q : 0) + (pr.do_mean ? 1 : 0);
+    pr.group_base = group_base;
+    group_base += pr.num_groups;
+    carve_problem(cv, pr, o);
+  }
+  tab.total_groups = group_base;
+  const size_t sb = pcg_scratch_bytes(tab, num_sms);
+  void* scratch = cv.take<void>(sb);
+  *bytes_out = cv.off;
+  if (dtab_out) *dtab_out = dtab;
+  if (counter_out) *counter_out = counter;
+  if (scratch_out) *scratch_out = scratch;
+  if (scratch_bytes_out) *scratch_bytes_out = sb;
+  return 0;
+}
+
+int status_to_code(int32_t bits) {
+  if (bits & kStatBadObs) return INFO_ESRF_ERR_BAD_OBS_INDEX;
+  if (bits & kStatBadR) return INFO_ESRF_ERR_NONPOSITIVE_R;
+  if (bits & kStatNonFinite) return INFO_ESRF_ERR_NONFINITE;
+  if (bits & kStatBandOverflow) return INFO_ESRF_ERR_BAND_OVERFLOW;
+  if (bits & kStatBreakdown) return INFO_ESRF_ERR_BREAKDOWN;
+  if (bits & kStatNotConverged) return INFO_ESRF_NOT_CONVERGED;
+  return INFO_ESRF_OK;
+}
+
+int run_batch(const info_esrf_problem* probs, int32_t count, const info_esrf_options* opt_in, void* ws,
+              size_t ws_bytes, void* stream, info_esrf_stats* stats) {
+  info_esrf_options o;
+  int rc = check_options(opt_in, &o);
+  if (rc) return rc;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0) return INFO_ESRF_ERR_WORKSPACE;
+  const int sms = num_sms_current();
+  static thread_local ProblemTable tab;   // large; keep it off the stack
+  size_t need = 0;
+  ProblemDev* dtab = nullptr;
+  int32_t* counter = nullptr;
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  rc = build_table(probs, count, o, ws, tab, &need, &dtab, &counter, &scratch, &scratch_bytes, sms);
+  if (rc) return rc;
+  if (need > ws_bytes) return INFO_ESRF_ERR_WORKSPACE;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaGetLastError();
+  auto mark = [&](int i) {
+    if (o.phase_events && o.phase_events[i]) cudaEventRecord(reinterpret_cast<cudaEvent_t>(o.phase_events[i]), st);
+  };
+  mark(0);
+  launch_prepare(tab, dtab, st);
+  launch_anomalies(tab, dtab, st);
+  launch_bands(tab, dtab, st);
+  launch_quadrature(tab, dtab, st);
+  mark(1);
+  launch_ritz(tab, dtab, st);
+  mark(2);
+  if (launch_pcg(tab, dtab, counter, scratch, scratch_bytes, sms, st) != 0) return INFO_ESRF_ERR_WORKSPACE;
+  mark(3);
+  launch_finish(tab, dtab, st);
+  mark(4);
+  if (cudaGetLastError() != cudaSuccess) return INFO_ESRF_ERR_CUDA;
+  if (!stats) return INFO_ESRF_OK;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return INFO_ESRF_ERR_CUDA;
+  int worst = INFO_ESRF_OK;
+  for (int i = 0; i < count; ++i) {
+    const ProblemDev& pr = tab.p[i];
+    info_esrf_stats& s = stats[i];
+    memset(&s, 0, sizeof(s));
+    int32_t status[4];
+    double scal[8];
+    const size_t nsys = (size_t)pr.num_groups * pr.JT;
+    std::vector<int32_t> it(nsys);
+    std::vector<double> rr(nsys);
+    if (cudaMemcpy(status, pr.status, sizeof(status), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(scal, pr.scal, sizeof(scal), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(it.data(), pr.iters, nsys * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(rr.data(), pr.relres, nsys * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return INFO_ESRF_ERR_CUDA;
+    // count live systems: perturbation lanes < N per group and the mean lane
+    int64_t live = 0, sum_it = 0;
+    int32_t it_max = 0, unconv = 0;
+    double rmax = 0.0;
+    for (int g = 0; g < pr.num_groups; ++g) {
+      const bool mean_group = pr.do_mean && g == pr.num_groups - 1;
+      const int lanes = mean_group ? 1 : (int)std::min<int64_t>(pr.JT, pr.N - (g % pr.groups_per_q) * pr.JT);
+      for (int j = 0; j < lanes; ++j) {
+        const size_t sidx = (size_t)g * pr.JT + j;
+        ++live;
+        sum_it += it[sidx];
+        it_max = std::max(it_max, it[sidx]);
+        rmax = std::max(rmax, rr[sidx]);
+        if (o.fixed_iters <= 0 && !(rr[sidx] <= pr.tol)) ++unconv;
+      }
+    }
+    s.device_flags = status[0];
+    s.iters_max = it_max;
+    s.n_systems = (int32_t)live;
+    s.iters_mean = live ? (double)sum_it / (double)live : 0.0;
+    s.n_unconverged = unconv;
+    s.max_rel_resid = rmax;
+    s.ell_used = scal[2];
+    s.gershgorin = scal[0];
+    s.status = status_to_code(status[0]);
+    if (s.status < 0 && (worst >= 0 || s.status < worst)) worst = s.status;
+    else if (worst == INFO_ESRF_OK && s.status > 0) worst = s.status;
+  }
+  return worst;
+}
+
+info_esrf_problem one_problem(const info_esrf_grid* grid, int64_t N, const double* X, int64_t d,
+                              const int64_t* obs, const double* y, const double* R, int32_t Q, double tol,
+                              double* mu_a, double* A_a) {
+  info_esrf_problem P;
+  memset(&P, 0, sizeof(P));
+  if (grid) P.grid = *grid;
+  P.N = N;
+  P.d = d;
+  P.Q = Q;
+  P.tol = tol;
+  P.X = X;
+  P.obs_idx = obs;
+  P.y = y;
+  P.R_diag = R;
+  P.mu_a = mu_a;
+  P.A_a = A_a;
+  return P;
+}
+
+}  // namespace
+
+extern "C" {
+
+void info_esrf_default_options(info_esrf_options* opt) {
+  if (!opt) return;
+  memset(opt, 0, sizeof(*opt));
+  opt->precision = INFO_ESRF_PRECISION_FP64;
+  opt->ritz_rank = 10;
+  opt->oversample = 10;
+  opt->power_iters = 1;
+  opt->max_iter = 1000;
+  opt->fixed_iters = 0;
+  opt->rule = INFO_ESRF_RULE_ELLIPTIC;
+  opt->learn_rank = 0;
+  opt->ell = 0.0;
+  opt->seed = 0x1234abcdULL;
+  opt->max_neighbors = 0;
+  opt->learn_diag = nullptr;
+  opt->learn_U = nullptr;
+  opt->phase_events = nullptr;
+}
+
+const char* info_esrf_error_string(int code) {
+  switch (code) {
+    case INFO_ESRF_OK: return "ok";
+    case INFO_ESRF_NOT_CONVERGED: return "some PCG system reached the iteration cap";
+    case INFO_ESRF_ERR_INVALID_ARG: return "invalid argument";
+    case INFO_ESRF_ERR_BAD_OBS_INDEX: return "observation index out of range or not strictly increasing";
+    case INFO_ESRF_ERR_NONPOSITIVE_R: return "observation-error variance not positive and finite";
+    case INFO_ESRF_ERR_WORKSPACE: return "workspace too small or not 256-byte aligned";
+    case INFO_ESRF_ERR_CUDA: return "CUDA runtime error";
+    case INFO_ESRF_ERR_NONFINITE: return "non-finite value in the ensemble";
+    case INFO_ESRF_ERR_BAND_OVERFLOW: return "more neighbours than the band capacity";
+    case INFO_ESRF_ERR_BREAKDOWN: return "PCG breakdown";
+    case INFO_ESRF_ERR_UNSUPPORTED: return "size beyond a documented limit";
+    default: return "unknown status";
+  }
+}
+
+int info_esrf_version(void) { return 10000; }
+
+int64_t info_esrf_launch_count(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
+
+int info_esrf_neighbor_counts(const info_esrf_grid* grid, int64_t d, const int64_t* obs_idx_dev,
+                              int64_t* counts_dev, void* stream, int64_t* max_oo, int64_t* max_xo) {
+  GridDev g;
+  int rc = make_grid(grid, &g);
+  if (rc) return rc;
+  if (d < 1 || !obs_idx_dev || !counts_dev || !max_oo || !max_xo) return INFO_ESRF_ERR_INVALID_ARG;
+  const int64_t n = g.ext[0] * g.ext[1] * g.ext[2];
+  if (d > n) return INFO_ESRF_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaGetLastError();
+  launch_count_neighbours(g, obs_idx_dev, d, n, counts_dev, st);
+  int64_t host[2] = {0, 0};
+  if (cudaMemcpyAsync(host, counts_dev, sizeof(host), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return INFO_ESRF_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return INFO_ESRF_ERR_CUDA;
+  *max_oo = host[0];
+  *max_xo = host[1];
+  return 0;
+}
+
+size_t info_esrf_batched_workspace_size(const info_esrf_problem* probs, int32_t count,
+                                        const info_esrf_options* opt) {
+  info_esrf_options o;
+  if (check_options(opt, &o)) return 0;
+  static thread_local ProblemTable tab;
+  size_t need = 0;
+  if (build_table(probs, count, o, nullptr, tab, &need, nullptr, nullptr, nullptr, nullptr, num_sms_current()))
+    return 0;
+  return need;
+}
+
+size_t info_esrf_workspace_size(const info_esrf_grid* grid, int64_t N, int64_t d, int32_t Q,
+                                const info_esrf_options* opt) {
+  // both updates: dummy non-null pointers mark mu_a and A_a as requested
+  static double dummy;
+  static int64_t idummy;
+  info_esrf_problem P = one_problem(grid, N, &dummy, d, &idummy, &dummy, &dummy, Q, 1.0, &dummy, &dummy);
+  return info_esrf_batched_workspace_size(&P, 1, opt);
+}
+
+int info_esrf_mean_update(const info_esrf_grid* grid, int64_t N, const double* X_dev, int64_t d,
+                          const int64_t* obs_idx_dev, const double* y_dev, const double* R_diag_dev, double tol,
+                          const info_esrf_options* opt, void* workspace, size_t ws_bytes, void* stream,
+                          double* mu_a_dev, info_esrf_stats* stats) {
+  if (!mu_a_dev) return INFO_ESRF_ERR_INVALID_ARG;
+  info_esrf_problem P = one_problem(grid, N, X_dev, d, obs_idx_dev, y_dev, R_diag_dev, 0, tol, mu_a_dev, nullptr);
+  return run_batch(&P, 1, opt, workspace, ws_bytes, stream, stats);
+}
+
+int info_esrf_perturbation_update(const info_esrf_grid* grid, int64_t N, const double* X_dev, int64_t d,
+                                  const int64_t* obs_idx_dev, const double* R_diag_dev, int32_t Q, double tol,
+                                  const info_esrf_options* opt, void* workspace, size_t ws_bytes, void* stream,
+                                  double* A_a_dev, info_esrf_stats* stats) {
+  if (!A_a_dev) return INFO_ESRF_ERR_INVALID_ARG;
+  info_esrf_problem P = one_problem(grid, N, X_dev, d, obs_idx_dev, nullptr, R_diag_dev, Q, tol, nullptr, A_a_dev);
+  return run_batch(&P, 1, opt, workspace, ws_bytes, stream, stats);
+}
+
+int info_esrf_analysis(const info_esrf_grid* grid, int64_t N, const double* X_dev, int64_t d,
+                       const int64_t* obs_idx_dev, const double* y_dev, const double* R_diag_dev, int32_t Q,
+                       double tol, const info_esrf_options* opt, void* workspace, size_t ws_bytes, void* stream,
+                       double* mu_a_dev, double* A_a_dev, info_esrf_stats* stats) {
+  if (!mu_a_dev || !A_a_dev) return INFO_ESRF_ERR_INVALID_ARG;
+  info_esrf_problem P = one_problem(grid, N, X_dev, d, obs_idx_dev, y_dev, R_diag_dev, Q, tol, mu_a_dev, A_a_dev);
+  return run_batch(&P, 1, opt, workspace, ws_bytes, stream, stats);
+}
+
+int info_esrf_analysis_batched(const info_esrf_problem* probs, int32_t count, const info_esrf_options* opt,
+                               void* workspace, size_t ws_bytes, void* stream, info_esrf_stats* stats) {
+  if (!probs) return INFO_ESRF_ERR_INVALID_ARG;
+  return run_batch(probs, count, opt, workspace, ws_bytes, stream, stats);
+}
+
+// ---------------------------------------------------------------------------
+// Stage entry points (info_esrf_stages.h)
+// ---------------------------------------------------------------------------
+
+int info_esrf_philox_normals(uint64_t seed, int64_t count, double* out_dev, void* stream) {
+  if (count < 0 || (count > 0 && !out_dev)) return INFO_ESRF_ERR_INVALID_ARG;
+  cudaGetLastError();
+  launch_philox(seed, count, out_dev, reinterpret_cast<cudaStream_t>(stream));
+  return cudaGetLastError() == cudaSuccess ? 0 : INFO_ESRF_ERR_CUDA;
+}
+
+int info_esrf_quadrature_nodes(int32_t Q, double ell, int32_t rule, double* s_dev, double* p_dev, void* stream) {
+  if (Q < 1 || !s_dev || !p_dev || (rule != 0 && rule != 1) || (rule == 0 && !(ell > 0.0)))
+    return INFO_ESRF_ERR_INVALID_ARG;
+  cudaGetLastError();
+  launch_quadrature_nodes(Q, ell, rule, s_dev, p_dev, reinterpret_cast<cudaStream_t>(stream));
+  return cudaGetLastError() == cudaSuccess ? 0 : INFO_ESRF_ERR_CUDA;
+}
+
+static int prepare_one(const info_esrf_grid* grid, int64_t N, const double* X_dev, int64_t d,
+                       const int64_t* obs_idx_dev, const double* R_diag_dev, int32_t Q,
+                       const info_esrf_options* opt_in, void* ws, size_t ws_bytes, void* stream, bool run,
+                       ProblemDev** dpr, ProblemDev* hpr) {
+  info_esrf_options o;
+  int rc = check_options(opt_in, &o);
+  if (rc) return rc;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0) return INFO_ESRF_ERR_WORKSPACE;
+  static double dummy;
+  info_esrf_problem P = one_problem(grid, N, X_dev, d, obs_idx_dev, nullptr, R_diag_dev, Q, 1.0, nullptr, &dummy);
+  static thread_local ProblemTable tab;
+  size_t need = 0;
+  ProblemDev* dtab = nullptr;
+  rc = build_table(&P, 1, o, ws, tab, &need, &dtab, nullptr, nullptr, nullptr, num_sms_current());
+  if (rc) return rc;
+  if (need > ws_bytes) return INFO_ESRF_ERR_WORKSPACE;
+  *dpr = dtab;
+  *hpr = tab.p[0];
+  if (!run) return 0;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaGetLastError();
+  launch_prepare(tab, dtab, st);
+  launch_anomalies(tab, dtab, st);
+  launch_bands(tab, dtab, st);
+  launch_quadrature(tab, dtab, st);
+  launch_ritz(tab, dtab, st);
+  return cudaGetLastError() == cudaSuccess ? 0 : INFO_ESRF_ERR_CUDA;
+}
+
+int info_esrf_prepare(const info_esrf_grid* grid, int64_t N, const double* X_dev, int64_t d,
+                      const int64_t* obs_idx_dev, const double* R_diag_dev, int32_t Q,
+                      const info_esrf_options* opt, void* workspace, size_t ws_bytes, void* stream) {
+  ProblemDev* dpr;
+  ProblemDev hpr;
+  return prepare_one(grid, N, X_dev, d, obs_idx_dev, R_diag_dev, Q, opt, workspace, ws_bytes, stream, true, &dpr,
+                     &hpr);
+}
+
+int info_esrf_prepared_obs_matvec(const info_esrf_grid* grid, int64_t N, int64_t d, int32_t Q,
+                                  const info_esrf_options* opt, void* workspace, size_t ws_bytes, int32_t nvec,
+                                  const double* P_dev, const double* sigma_dev, double* Y_dev, void* stream) {
+  ProblemDev* dpr;
+  ProblemDev hpr;
+  static double dx;
+  static int64_t di;
+  int rc = prepare_one(grid, N, &dx, d, &di, &dx, Q, opt, workspace, ws_bytes, stream, false, &dpr, &hpr);
+  if (rc) return rc;
+  if (nvec < 0 || (nvec > 0 && (!P_dev || !sigma_dev || !Y_dev))) return INFO_ESRF_ERR_INVALID_ARG;
+  cudaGetLastError();
+  launch_obs_matvec(hpr, dpr, nvec, P_dev, sigma_dev, Y_dev, reinterpret_cast<cudaStream_t>(stream));
+  return cudaGetLastError() == cudaSuccess ? 0 : INFO_ESRF_ERR_CUDA;
+}
+
+int info_esrf_prepared_lmp_apply(const info_esrf_grid* grid, int64_t N, int64_t d, int32_t Q,
+                                 const info_esrf_options* opt, void* workspace, size_t ws_bytes, int32_t nvec,
+                                 const double* R_dev, const double* sigma_dev, double* Z_dev, void* stream) {
+  ProblemDev* dpr;
+  ProblemDev hpr;
+  static double dx;
+  static int64_t di;
+  int rc = prepare_one(grid, N, &dx, d, &di, &dx, Q, opt, workspace, ws_bytes, stream, false, &dpr, &hpr);
+  if (rc) return rc;
+  if (nvec < 0 || (nvec > 0 && (!R_dev || !sigma_dev || !Z_dev))) return INFO_ESRF_ERR_INVALID_ARG;
+  cudaGetLastError();
+  launch_lmp_apply(hpr, dpr, nvec, R_dev, sigma_dev, Z_dev, reinterpret_cast<cudaStream_t>(stream));
+  return cudaGetLastError() == cudaSuccess ? 0 : INFO_ESRF_ERR_CUDA;
+}
+
+int info_esrf_prepared_export(const info_esrf_grid* grid, int64_t N, int64_t d, int32_t Q,
+                              const info_esrf_options* opt, void* workspace, size_t ws_bytes, int32_t item,
+                              void* dst_host, size_t dst_bytes, void* stream) {
+  ProblemDev* dpr;
+  ProblemDev hpr;
+  static double dx;
+  static int64_t di;
+  int rc = prepare_one(grid, N, &dx, d, &di, &dx, Q, opt, workspace, ws_bytes, stream, false, &dpr, &hpr);
+  if (rc) return rc;
+  const size_t esz = hpr.precision == 0 ? 8 : 4;
+  const void* src = nullptr;
+  size_t bytes = 0;
+  switch (item) {
+    case INFO_ESRF_ITEM_SCALARS: src = hpr.scal; bytes = 8 * 8; break;
+    case INFO_ESRF_ITEM_STATUS: src = hpr.status; bytes = 4 * 4; break;
+    case INFO_ESRF_ITEM_QUAD_S: src = hpr.s; bytes = (size_t)hpr.Q * 8; break;
+    case INFO_ESRF_ITEM_QUAD_P: src = hpr.p; bytes = (size_t)hpr.Q * 8; break;
+    case INFO_ESRF_ITEM_THETA: src = hpr.theta; bytes = (size_t)hpr.kR * 8; break;
+    case INFO_ESRF_ITEM_PHI: src = hpr.Phi; bytes = (size_t)hpr.d * hpr.kR * esz; break;
+    case INFO_ESRF_ITEM_CPHI: src = hpr.CPhi; bytes = (size_t)hpr.d * hpr.kR * esz; break;
+    case INFO_ESRF_ITEM_OO_VAL: src = hpr.oo_val; bytes = (size_t)hpr.max_oo * hpr.d * esz; break;
+    case INFO_ESRF_ITEM_OO_COL: src = hpr.oo_col; bytes = (size_t)hpr.max_oo * hpr.d * 4; break;
+    case INFO_ESRF_ITEM_OO_NNZ: src = hpr.oo_nnz; bytes = (size_t)hpr.d * 4; break;
+    case INFO_ESRF_ITEM_XO_VAL: src = hpr.xo_val; bytes = (size_t)hpr.max_xo * hpr.n * esz; break;
+    case INFO_ESRF_ITEM_XO_COL: src = hpr.xo_col; bytes = (size_t)hpr.max_xo * hpr.n * 4; break;
+    case INFO_ESRF_ITEM_XO_NNZ: src = hpr.xo_nnz; bytes = (size_t)hpr.n * 4; break;
+    case INFO_ESRF_ITEM_W: src = hpr.W; bytes = (size_t)hpr.d * hpr.N * esz; break;
+    case INFO_ESRF_ITEM_MU: src = hpr.mu; bytes = (size_t)hpr.n * 8; break;
+    default: return INFO_ESRF_ERR_INVALID_ARG;
+  }
+  if (!dst_host || dst_bytes < bytes) return INFO_ESRF_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (bytes && cudaMemcpyAsync(dst_host, src, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return INFO_ESRF_ERR_CUDA;
+  return cudaStreamSynchronize(st) == cudaSuccess ? 0 : INFO_ESRF_ERR_CUDA;
+}
+
+int info_esrf_prepared_band_capacity(const info_esrf_grid* grid, int64_t N, int64_t d, int32_t Q,
+                                     const info_esrf_options* opt, int64_t* max_oo, int64_t* max_xo) {
+  info_esrf_options o;
+  int rc = check_options(opt, &o);
+  if (rc) return rc;
+  static double dx;
+  static int64_t di;
+  info_esrf_problem P = one_problem(grid, N, &dx, d, &di, nullptr, &dx, Q, 1.0, nullptr, &dx);
+  static thread_local ProblemTable tab;
+  size_t need = 0;
+  rc = build_table(&P, 1, o, nullptr, tab, &need, nullptr, nullptr, nullptr, nullptr, 160);
+  if (rc) return rc;
+  if (max_oo) *max_oo = tab.p[0].max_oo;
+  if (max_xo) *max_xo = tab.p[0].max_xo;
+  return 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,97 @@
+// a9-a11: quadrature-weighted accumulation and the state-space update.
+//
+//   vbar^(i) = R^-1/2 sum_q p_q u_q^(i)                       (Sec. 3.2, App. E)
+//   z_a^(i)  = z^(i) - Sxh vbar^(i),  A_a = sqrt(N-1) Z_a       (Sec. 3.2)
+//   mu_a     = mu + Sxh R^-1/2 u_mean                           (Eq. info_esrf_mean_solve)
+//
+// The quadrature sum is FP64.  Sxh is the state-obs band formed in setup, so
+// the state update is one banded product with N + 1 right-hand sides.
+#include "common.cuh"
+#include "internal.h"
+
+namespace infoesrf {
+
+template <typename T>
+__global__ void k_accumulate(const ProblemDev* tab) {
+  const ProblemDev& pr = tab[blockIdx.y];
+  const int64_t N1 = pr.N + 1;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= pr.d * N1) return;
+  const int64_t a = i / N1, m = i % N1;
+  const int JT = pr.JT;
+  const int64_t d = pr.d;
+  const T* U = reinterpret_cast<const T*>(pr.U);
+  double acc = 0.0;
+  if (m < pr.N) {
+    if (pr.do_pert) {
+      const int64_t g0 = m / JT, lane = m % JT;
+      for (int q = 0; q < pr.Q; ++q) {
+        const int64_t g = (int64_t)q * pr.groups_per_q + g0;
+        acc += pr.p[q] * (double)U[(g * d + a) * JT + lane];
+      }
+    }
+  } else if (pr.do_mean) {
+    const int64_t g = pr.do_pert ? (int64_t)pr.Q * pr.groups_per_q : 0;
+    acc = (double)U[(g * d + a) * JT];
+  }
+  const double v = pr.rinv[a] * acc;
+  pr.Vbar[a * N1 + m] = v;
+  reinterpret_cast<T*>(pr.VbarT)[a * N1 + m] = to_t<T>(v);
+}
+
+// One thread per state point, members in chunks of 32 accumulators.
+template <typename T>
+__global__ void k_state_apply(const ProblemDev* tab) {
+  const ProblemDev& pr = tab[blockIdx.y];
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= pr.n) return;
+  const int64_t n = pr.n, N = pr.N, N1 = N + 1;
+  const T* val = reinterpret_cast<const T*>(pr.xo_val);
+  const T* Vb = reinterpret_cast<const T*>(pr.VbarT);
+  const int nnz = pr.xo_nnz[x];
+  const double mu = pr.mu[x];
+  for (int64_t c0 = 0; c0 < N1; c0 += 32) {
+    const bool need = (c0 < N && pr.do_pert) || (c0 + 32 > N && pr.do_mean);
+    if (!need) continue;
+    T acc[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) acc[i] = T(0);
+    for (int e = 0; e < nnz; ++e) {
+      const T v = val[(int64_t)e * n + x];
+      const int64_t b = pr.xo_col[(int64_t)e * n + x];
+      const T* row = Vb + b * N1 + c0;
+#pragma unroll
+      for (int i = 0; i < 32; ++i)
+        if (c0 + i < N1) acc[i] += v * row[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      const int64_t m = c0 + i;
+      if (m < N) {
+        if (pr.do_pert) pr.A_a[m * n + x] = (pr.X[m * n + x] - mu) - pr.sqrt_nm1 * (double)acc[i];
+      } else if (m == N) {
+        if (pr.do_mean) pr.mu_a[x] = mu + (double)acc[i];
+      }
+    }
+  }
+}
+
+void launch_finish(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st) {
+  int64_t dn1 = 0, nmax = 0;
+  for (int i = 0; i < tab.count; ++i) {
+    const ProblemDev& p = tab.p[i];
+    dn1 = p.d * (p.N + 1) > dn1 ? p.d * (p.N + 1) : dn1;
+    nmax = p.n > nmax ? p.n : nmax;
+  }
+  const dim3 ga((unsigned)((dn1 + 255) / 256), tab.count);
+  const dim3 gs((unsigned)((nmax + 127) / 128), tab.count);
+  if (tab.p[0].precision == 0) {
+    k_accumulate<double><<<ga, 256, 0, st>>>(dtab); note_launches(1);
+    k_state_apply<double><<<gs, 128, 0, st>>>(dtab); note_launches(1);
+  } else {
+    k_accumulate<float><<<ga, 256, 0, st>>>(dtab); note_launches(1);
+    k_state_apply<float><<<gs, 128, 0, st>>>(dtab); note_launches(1);
+  }
+}
+
+}  // namespace infoesrf

@@ -1,0 +1,125 @@
+// Internal layout shared by the host API and the kernels (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace infoesrf {
+
+constexpr int kMaxProblems = 64;      // problems per batched call
+constexpr int kMaxRitz = 32;          // k_R + oversampling
+constexpr int kMaxK = 24;             // Ritz vectors used by the preconditioner
+constexpr int kMaxLearnRank = 8;      // rank of the learned correction
+constexpr int kThreads = 256;         // CTA size of the persistent PCG kernel
+
+// Status bits written by kernels (ws status word 0).
+enum : int32_t {
+  kStatBadObs = 1 << 0,        // obs index out of range or not strictly increasing
+  kStatBadR = 1 << 1,          // R <= 0 or not finite
+  kStatNonFinite = 1 << 2,     // non-finite ensemble value
+  kStatBandOverflow = 1 << 3,  // more neighbours than the band capacity
+  kStatBreakdown = 1 << 4,     // PCG breakdown (p^T A p <= 0 or NaN)
+  kStatNotConverged = 1 << 5,  // iteration cap reached
+  kStatEigFail = 1 << 6,       // randomized eigensolver lost rank
+};
+
+struct GridDev {
+  int64_t ext[3];
+  int64_t reach[3];      // candidate half-window per axis (grid units)
+  int32_t whole[3];      // 1: scan the whole axis
+  int32_t periodic[3];
+  int32_t chordal;
+  int32_t pad_;
+  double inv_c[3];       // 1 / half-width
+};
+
+// Everything one problem needs on the device.  Pointers into the caller's
+// buffers and into the workspace; sizes; offsets into the global group space.
+struct ProblemDev {
+  GridDev grid;
+  int64_t n, N, d;
+  int32_t Q, kR, l, do_mean, do_pert, rule, precision, fixed_iters;
+  int32_t max_iter, power_iters, learn_rank, pad_;
+  double tol, ell_fixed, sqrt_nm1;
+  uint64_t seed;
+  int64_t max_oo, max_xo;      // ELL capacities (obs-obs, state-obs)
+  // inputs (caller-owned, device)
+  const double* X;      // [N][n]
+  const int64_t* obs;   // [d]
+  const double* y;      // [d] (mean update only)
+  const double* R;      // [d]
+  // outputs (caller-owned, device)
+  double* mu_a;         // [n]
+  double* A_a;          // [N][n]
+  // workspace
+  double* mu;           // [n]
+  void* Zt;             // [n][N] T normalized anomalies, state-major
+  void* W;              // [d][N] T observed anomalies W = H Z
+  double* rinv;         // [d] R^-1/2
+  double* bmean;        // [d] R^-1/2 (y - H mu)
+  double* scal;         // [8] 0 gershgorin bound, 1 min diag C, 2 ell, 3 sum p
+  int32_t* status;      // [4]
+  double* s;            // [Q] quadrature nodes
+  double* p;            // [Q] quadrature weights
+  void* oo_val;         // [max_oo][d] T: C(a, b) (ELL, transposed)
+  int32_t* oo_col;      // [max_oo][d]
+  int32_t* oo_nnz;      // [d]
+  void* xo_val;         // [max_xo][n] T: Sxh(x, b) (ELL, transposed)
+  int32_t* xo_col;      // [max_xo][n]
+  int32_t* xo_nnz;      // [n]
+  // randomized eigensolver
+  double* Om;           // [d][l] test matrix / range basis (in place)
+  double* Yb;           // [d][l]
+  double* Gm;           // [l][l] Gram / projected matrix
+  double* Rm;           // [l][l] Cholesky factor / eigenvectors
+  double* ev;           // [l] eigenvalues (descending)
+  void* Phi;            // [d][kR] T Ritz vectors
+  void* CPhi;           // [d][kR] T C Phi
+  double* theta;        // [kR] Ritz values of C
+  double* gram;         // [3][kR][kR]: Phi^T Phi, A^T Phi, A^T A with A = C Phi
+  // learned diagonal-plus-low-rank correction (optional)
+  const float* learn_diag;   // [Q + 1][d] >= 0, NULL: none
+  const float* learn_U;      // [Q + 1][d][learn_rank]
+  // batched PCG
+  int32_t JT, groups_per_q, num_groups, group_base;
+  void* U;              // [num_groups][d][JT] T solutions u of C_q u = b
+  int32_t* iters;       // [num_groups * JT]
+  double* relres;       // [num_groups * JT] final ||r|| / ||b|| (recurrence)
+  double* Vbar;         // [d][N + 1] FP64 R^-1/2 sum_q p_q u_q (last column: mean)
+  void* VbarT;          // [d][N + 1] T copy for the state apply
+};
+
+struct ProblemTable {
+  int32_t count;
+  int32_t total_groups;
+  int32_t pad_[2];
+  ProblemDev p[kMaxProblems];
+};
+
+// Launchers (one per stage).  All are stream-ordered and never synchronize.
+void launch_prepare(const ProblemTable& tab, ProblemDev* dtab, cudaStream_t st);
+void launch_anomalies(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st);
+void launch_bands(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st);
+void launch_quadrature(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st);
+void launch_ritz(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st);
+int launch_pcg(const ProblemTable& tab, const ProblemDev* dtab, int32_t* counter, void* scratch,
+               size_t scratch_bytes, int num_sms, cudaStream_t st);
+void launch_finish(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st);
+void launch_count_neighbours(const GridDev& g, const int64_t* obs, int64_t d, int64_t n,
+                             int64_t* out2, cudaStream_t st);
+void launch_philox(uint64_t seed, int64_t count, double* out, cudaStream_t st);
+void launch_quadrature_nodes(int32_t Q, double ell, int32_t rule, double* s, double* p, cudaStream_t st);
+void launch_obs_matvec(const ProblemDev& pr, const ProblemDev* dpr, int32_t nvec, const double* P,
+                       const double* sigma, double* Y, cudaStream_t st);
+void launch_lmp_apply(const ProblemDev& pr, const ProblemDev* dpr, int32_t nvec, const double* Rv,
+                      const double* sigma, double* Z, cudaStream_t st);
+
+// Host-side count of kernel launches issued by this library.
+void note_launches(int n);
+
+// PCG vector scratch per CTA when vectors do not fit in shared memory.
+size_t pcg_scratch_bytes(const ProblemTable& tab, int num_sms);
+int pcg_jt(int precision);
+
+}  // namespace infoesrf

@@ -1,0 +1,330 @@
+"""GPU parity: every stage of the CUDA path against the FP64 oracle, through the C ABI.
+
+Tolerances: FP64 path <= 1e-10 relative error of the analysis increment
+(PCG tolerance 1e-12); FP32 bulk path <= 1e-4 (PCG tolerance 1e-6).  The
+relative increment error is ||A_gpu - A_ref||_F / ||A_ref - A_f||_F.
+"""
+import math
+import types
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import filter as F
+from oracle import localization, pcg, philox, quadrature
+from paper_2503_00253_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2503_00253_gb300 import binding
+    binding.library()
+    return binding
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def run_analysis(B, pr, precision=0, tol=None, **kw):
+    opts = B.make_options(precision=precision, **kw)
+    tol = pr.tol if tol is None else tol
+    mu_a, A_a, st = B.info_esrf_analysis(pr.grid, dev(pr.X), dev(pr.obs_idx), dev(pr.y), dev(pr.R),
+                                         pr.Q, tol, opts)
+    torch.cuda.synchronize()
+    return mu_a.cpu().numpy(), A_a.cpu().numpy(), st
+
+
+def errors(pr, mu_a, A_a, ell=None, rule="elliptic"):
+    A_ref = F.perturbation_update(pr.X, pr.obs_idx, pr.R, pr.grid, pr.Q, ell=ell, rule=rule)
+    mu_ref = F.mean_update(pr.X, pr.obs_idx, pr.y, pr.R, pr.grid)
+    Af = pr.X - pr.X.mean(0)
+    mu0 = pr.X.mean(0)
+    ea = F.relative_increment_error(A_a, A_ref, Af)
+    em = float(np.linalg.norm(mu_a - mu_ref) / np.linalg.norm(mu_ref - mu0))
+    return ea, em
+
+
+# ---------------------------------------------------------------------------
+# a2 quadrature, Philox
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("Q,ell", [(1, 10.0), (7, 100.0), (16, 100.0), (32, 1000.0), (48, 1e4)])
+def test_quadrature_nodes_match_oracle(B, Q, ell):
+    s, p = B.info_esrf_quadrature_nodes(Q, ell)
+    s_ref, p_ref = quadrature.elliptic_rule(Q, ell)
+    assert np.max(np.abs(s.cpu().numpy() / s_ref - 1)) < 1e-11
+    assert np.max(np.abs(p.cpu().numpy() / p_ref - 1)) < 1e-11
+
+
+@pytest.mark.parametrize("Q", [1, 2, 5, 16, 33])
+def test_gauss_legendre_nodes_match_oracle(B, Q):
+    s, p = B.info_esrf_quadrature_nodes(Q, 1.0, B.RULE_GAUSS_LEGENDRE)
+    s_ref, p_ref = quadrature.gauss_legendre_rule(Q)
+    order = np.argsort(s.cpu().numpy())
+    assert np.max(np.abs(s.cpu().numpy()[order] / s_ref - 1)) < 1e-10
+    assert np.max(np.abs(p.cpu().numpy()[order] / p_ref - 1)) < 1e-10
+
+
+def test_philox_normals_match_oracle(B):
+    for seed, count in ((0, 5), (123456789, 1001), (2**40 + 7, 4096)):
+        g = B.info_esrf_philox_normals(seed, count).cpu().numpy()
+        ref = philox.normals(count, seed)
+        assert np.max(np.abs(g - ref)) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# a1/a5: anomalies, bands of C and Sxh, matvec
+# ---------------------------------------------------------------------------
+
+def _dense_from_ell(val, col, nnz, rows, cols, cap):
+    M = np.zeros((rows, cols))
+    for a in range(rows):
+        for e in range(nnz[a]):
+            M[a, col[e * rows + a]] += val[e * rows + a]
+    return M
+
+
+SMALL_GRIDS = [
+    ("1d", lambda: workloads.gaussian_problem_1d("s", n=300, N=11, length_scale=6.0, obs_stride=3, r2=0.4,
+                                                 half_width=9.0, Q=5, tol=1e-12, seed=1, obs_offset=1)),
+    ("1d_minimage", lambda: workloads.gaussian_problem_1d("s", n=256, N=9, length_scale=6.0, obs_stride=2,
+                                                          r2=0.4, half_width=7.5, Q=4, tol=1e-12, seed=2,
+                                                          chordal=False)),
+    ("layered", lambda: workloads.random_obs_problem(workloads.Grid((40, 1, 6), (True, False, False),
+                                                                    (5.0, 1.0, 1.5)), N=10, d=70, r2=0.8,
+                                                     Q=6, tol=1e-12, seed=3)),
+    ("2d", lambda: workloads.random_obs_problem(workloads.Grid((24, 20, 1), (True, True, False),
+                                                               (3.0, 2.5, 1.0)), N=7, d=90, r2=0.5, Q=5,
+                                                tol=1e-12, seed=4)),
+]
+
+
+@pytest.mark.parametrize("name,make", SMALL_GRIDS)
+@pytest.mark.parametrize("precision", [0, 1])
+def test_prepared_bands_match_oracle(B, name, make, precision):
+    pr = make()
+    opts = B.make_options(precision=precision, ritz_rank=4, oversample=4)
+    P = B.Prepared(pr.grid, dev(pr.X), dev(pr.obs_idx), dev(pr.R), pr.Q, opts)
+    torch.cuda.synchronize()
+    mo, mx = P.capacity()
+    mu, Z = F.anomalies(pr.X)
+    W, Sxh, Shh = F.localized_covariances(Z, pr.obs_idx, pr.grid)
+    C = F.normalized_obs_covariance(Shh, pr.R)
+    tol = 1e-13 if precision == 0 else 2e-6
+    assert np.max(np.abs(P.export("mu") - mu)) < 1e-13 * np.max(np.abs(mu) + 1)
+    assert np.max(np.abs(P.export("W").reshape(pr.d, pr.N) - W)) < tol * np.max(np.abs(W))
+    Cg = _dense_from_ell(P.export("oo_val"), P.export("oo_col"), P.export("oo_nnz"), pr.d, pr.d, mo)
+    assert np.max(np.abs(Cg - C)) < tol * np.max(np.abs(C))
+    # the band holds exactly the pairs inside the GC support
+    L_oo = localization.localization_matrix(pr.grid, pr.obs_idx, pr.obs_idx)
+    assert np.array_equal(P.export("oo_nnz"), (L_oo > 0).sum(1))
+    Sg = _dense_from_ell(P.export("xo_val"), P.export("xo_col"), P.export("xo_nnz"), pr.n, pr.d, mx)
+    assert np.max(np.abs(Sg - Sxh)) < tol * np.max(np.abs(Sxh))
+    sc = P.export("scalars")
+    assert abs(sc[0] / quadrature.gershgorin_bound(C) - 1) < (1e-12 if precision == 0 else 1e-5)
+    assert abs(sc[1] / np.min(np.diag(C)) - 1) < (1e-12 if precision == 0 else 1e-5)
+    assert int(P.export("status")[0]) == 0
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_obs_matvec_matches_oracle(B, precision):
+    pr = workloads.gaussian_problem_1d("m", n=2000, N=13, length_scale=8.0, obs_stride=3, r2=0.3,
+                                       half_width=20.0, Q=3, tol=1e-12, seed=5)
+    opts = B.make_options(precision=precision, ritz_rank=0)
+    P = B.Prepared(pr.grid, dev(pr.X), dev(pr.obs_idx), dev(pr.R), pr.Q, opts)
+    mu, Z = F.anomalies(pr.X)
+    W, Sxh, Shh = F.localized_covariances(Z, pr.obs_idx, pr.grid)
+    C = F.normalized_obs_covariance(Shh, pr.R)
+    rng = np.random.default_rng(0)
+    V = rng.standard_normal((5, pr.d))
+    sig = np.array([1.0, 2.5, 1e3, 1.0 + 1e-9, 17.0])
+    Y = P.obs_matvec(dev(V), dev(sig)).cpu().numpy()
+    ref = sig[:, None] * V + V @ C.T
+    tol = 1e-13 if precision == 0 else 3e-6
+    assert np.max(np.abs(Y - ref)) < tol * np.max(np.abs(ref))
+
+
+# ---------------------------------------------------------------------------
+# a4/a7: Ritz pairs and the limited-memory preconditioner
+# ---------------------------------------------------------------------------
+
+def test_ritz_pairs_and_lmp_match_oracle(B):
+    pr = workloads.gaussian_problem_1d("r", n=1200, N=15, length_scale=6.0, obs_stride=2, r2=0.3,
+                                       half_width=12.0, Q=4, tol=1e-12, seed=6)
+    k, os_, seed = 8, 8, 987654321
+    opts = B.make_options(precision=0, ritz_rank=k, oversample=os_, seed=seed)
+    P = B.Prepared(pr.grid, dev(pr.X), dev(pr.obs_idx), dev(pr.R), pr.Q, opts)
+    mu, Z = F.anomalies(pr.X)
+    W, Sxh, Shh = F.localized_covariances(Z, pr.obs_idx, pr.grid)
+    C = F.normalized_obs_covariance(Shh, pr.R)
+    Om = philox.test_matrix(pr.d, k + os_, seed)
+    Phi_ref, th_ref = pcg.randomized_ritz(C, k, Om, power_iters=1)
+    th = P.export("theta")
+    assert np.max(np.abs(th - th_ref) / th_ref[0]) < 1e-10
+    Phi = P.export("phi").reshape(pr.d, k)
+    overlap = np.abs(Phi.T @ Phi_ref)
+    assert np.max(np.abs(overlap - np.eye(k))) < 1e-7
+    # LMP applied to random vectors for three shifts, against the oracle's own Ritz pairs
+    rng = np.random.default_rng(1)
+    Rv = rng.standard_normal((3, pr.d))
+    sig = np.array([1.0, 3.7, 250.0])
+    Zg = P.lmp_apply(dev(Rv), dev(sig)).cpu().numpy()
+    cmin = np.min(np.diag(C))
+    for v in range(3):
+        Chat_Phi = C @ Phi_ref + sig[v] * Phi_ref
+        z = pcg.lmp_apply(Rv[v], Chat_Phi, Phi_ref, th_ref + sig[v], sig[v] + cmin)
+        assert np.max(np.abs(Zg[v] - z)) < 1e-8 * np.max(np.abs(z))
+
+
+# ---------------------------------------------------------------------------
+# end to end
+# ---------------------------------------------------------------------------
+
+def test_config1_fp64_parity(B):
+    pr = workloads.config1()
+    mu_a, A_a, st = run_analysis(B, pr, precision=0)
+    ea, em = errors(pr, mu_a, A_a)
+    assert st["status"] == 0 and st["n_unconverged"] == 0
+    assert st["n_systems"] == pr.Q * pr.N + 1
+    assert ea <= 1e-10 and em <= 1e-10, (ea, em)
+    # zero-mean analysis perturbations (Theorem 3)
+    assert np.max(np.abs(A_a.sum(0))) < 1e-10 * np.max(np.abs(A_a))
+
+
+@pytest.mark.parametrize("name,make", SMALL_GRIDS)
+@pytest.mark.parametrize("precision,tol,bound", [(0, 1e-12, 1e-10), (1, 1e-6, 1e-4)])
+def test_small_problems_parity(B, name, make, precision, tol, bound):
+    pr = make()
+    mu_a, A_a, st = run_analysis(B, pr, precision=precision, tol=tol, ritz_rank=5, oversample=5)
+    ea, em = errors(pr, mu_a, A_a)
+    assert st["status"] == 0, st
+    assert ea <= bound and em <= bound, (ea, em)
+
+
+@pytest.mark.parametrize("kw", [dict(ritz_rank=0), dict(ritz_rank=24, oversample=8), dict(rule=1),
+                                dict(ell=1e5), dict(power_iters=0)])
+def test_option_variants_parity(B, kw):
+    pr = workloads.gaussian_problem_1d("v", n=900, N=10, length_scale=5.0, obs_stride=3, r2=0.5,
+                                       half_width=10.0, Q=9, tol=1e-12, seed=8)
+    mu_a, A_a, st = run_analysis(B, pr, precision=0, **kw)
+    rule = "gauss_legendre" if kw.get("rule") == 1 else "elliptic"
+    ea, em = errors(pr, mu_a, A_a, ell=kw.get("ell"), rule=rule)
+    assert st["status"] == 0, st
+    assert ea <= 1e-10 and em <= 1e-10, (ea, em)
+
+
+@pytest.mark.parametrize("N,Q,stride", [(2, 1, 5), (3, 2, 7), (9, 3, 1), (17, 5, 4)])
+def test_ragged_and_degenerate_sizes(B, N, Q, stride):
+    pr = workloads.gaussian_problem_1d("g", n=331, N=N, length_scale=5.0, obs_stride=stride, r2=0.7,
+                                       half_width=6.0, Q=Q, tol=1e-12, seed=N * 10 + Q)
+    for precision, bound, tol in ((0, 1e-10, 1e-12), (1, 1e-4, 1e-6)):
+        mu_a, A_a, st = run_analysis(B, pr, precision=precision, tol=tol, ritz_rank=3, oversample=3)
+        ea, em = errors(pr, mu_a, A_a)
+        assert st["status"] == 0, st
+        assert ea <= bound and em <= bound, (precision, ea, em)
+
+
+def test_single_observation(B):
+    pr = workloads.gaussian_problem_1d("one", n=50, N=6, length_scale=4.0, obs_stride=50, r2=0.2,
+                                       half_width=5.0, Q=4, tol=1e-12, seed=9)
+    assert pr.d == 1
+    mu_a, A_a, st = run_analysis(B, pr, precision=0, ritz_rank=2)
+    ea, em = errors(pr, mu_a, A_a)
+    assert ea <= 1e-10 and em <= 1e-10
+
+
+def test_mean_and_perturbation_calls_alone(B):
+    pr = workloads.gaussian_problem_1d("sep", n=500, N=12, length_scale=5.0, obs_stride=4, r2=0.5,
+                                       half_width=8.0, Q=6, tol=1e-12, seed=10)
+    X, obs, y, R = dev(pr.X), dev(pr.obs_idx), dev(pr.y), dev(pr.R)
+    mu_a, st = B.info_esrf_mean_update(pr.grid, X, obs, y, R, 1e-12)
+    A_a, st2 = B.info_esrf_perturbation_update(pr.grid, X, obs, R, pr.Q, 1e-12)
+    torch.cuda.synchronize()
+    ea, em = errors(pr, mu_a.cpu().numpy(), A_a.cpu().numpy())
+    assert st["n_systems"] == 1 and st2["n_systems"] == pr.Q * pr.N
+    assert ea <= 1e-10 and em <= 1e-10
+
+
+def test_fixed_iterations_match_oracle_pcg(B):
+    """Paper-style fixed iteration counts (2 and 10): same iterates as the oracle's PCG + LMP."""
+    pr = workloads.gaussian_problem_1d("fix", n=600, N=8, length_scale=6.0, obs_stride=2, r2=0.4,
+                                       half_width=10.0, Q=5, tol=1e-12, seed=11)
+    k, os_, seed = 6, 6, 4242
+    mu, Z = F.anomalies(pr.X)
+    W, Sxh, Shh = F.localized_covariances(Z, pr.obs_idx, pr.grid)
+    C = F.normalized_obs_covariance(Shh, pr.R)
+    s, p = quadrature.elliptic_rule(pr.Q, F.choose_ell(Shh, pr.R))
+    Om = philox.test_matrix(pr.d, k + os_, seed)
+    for iters in (2, 10):
+        vbar, _ = pcg.solve_normalized(C, s, p, W, pr.R, k=k, Omega=Om, fixed_iters=iters)
+        A_ref = math.sqrt(pr.N - 1) * (Z - Sxh @ vbar).T
+        opts = B.make_options(precision=0, ritz_rank=k, oversample=os_, seed=seed, fixed_iters=iters)
+        A_a, st = B.info_esrf_perturbation_update(pr.grid, dev(pr.X), dev(pr.obs_idx), dev(pr.R), pr.Q, 1e-12,
+                                                  opts)
+        Af = pr.X - pr.X.mean(0)
+        err = F.relative_increment_error(A_a.cpu().numpy(), A_ref, Af)
+        assert err < 1e-9, (iters, err)
+        assert st["iters_max"] == iters
+
+
+def test_config2_parity_fp64_and_fp32(B):
+    pr = workloads.config2()
+    A_ref = F.perturbation_update(pr.X, pr.obs_idx, pr.R, pr.grid, pr.Q)
+    mu_ref = F.mean_update(pr.X, pr.obs_idx, pr.y, pr.R, pr.grid)
+    Af = pr.X - pr.X.mean(0)
+    mu0 = pr.X.mean(0)
+    for precision, tol, bound in ((0, 1e-12, 1e-10), (1, 1e-6, 1e-4)):
+        mu_a, A_a, st = run_analysis(B, pr, precision=precision, tol=tol)
+        ea = F.relative_increment_error(A_a, A_ref, Af)
+        em = float(np.linalg.norm(mu_a - mu_ref) / np.linalg.norm(mu_ref - mu0))
+        assert st["status"] == 0, st
+        assert st["n_systems"] == 1281
+        assert ea <= bound and em <= bound, (precision, ea, em)
+
+
+def test_batched_uneven_parity(B):
+    probs = workloads.uneven_batch(count=5, seed=12, tol=1e-12, n_min=200, n_max=1500)
+    dicts = [dict(grid=p.grid, X=dev(p.X), obs_idx=dev(p.obs_idx), y=dev(p.y), R=dev(p.R), Q=p.Q, tol=1e-12)
+             for p in probs]
+    outs, stats = B.info_esrf_analysis_batched(dicts, B.make_options(precision=0))
+    torch.cuda.synchronize()
+    for p, (mu_a, A_a), st in zip(probs, outs, stats):
+        ea, em = errors(p, mu_a.cpu().numpy(), A_a.cpu().numpy())
+        assert st["status"] == 0 and st["n_systems"] == p.Q * p.N + 1
+        assert ea <= 1e-10 and em <= 1e-10, (p.name, ea, em)
+
+
+# ---------------------------------------------------------------------------
+# failure handling (host-visible status; nothing faults)
+# ---------------------------------------------------------------------------
+
+def test_invalid_inputs_return_codes(B):
+    pr = workloads.gaussian_problem_1d("bad", n=200, N=6, length_scale=4.0, obs_stride=4, r2=0.5,
+                                       half_width=5.0, Q=3, tol=1e-10, seed=13)
+    def call(obs=None, R=None, X=None):
+        with pytest.raises(B.InfoEsrfError) as ei:
+            B.info_esrf_analysis(pr.grid, dev(pr.X if X is None else X), dev(pr.obs_idx if obs is None else obs),
+                                 dev(pr.y), dev(pr.R if R is None else R), pr.Q, pr.tol)
+        return ei.value.code
+    bad_obs = pr.obs_idx.copy(); bad_obs[3] = 10**6
+    assert call(obs=bad_obs) == B.ERR_BAD_OBS_INDEX
+    unsorted = pr.obs_idx.copy(); unsorted[[1, 2]] = unsorted[[2, 1]]
+    assert call(obs=unsorted) == B.ERR_BAD_OBS_INDEX
+    badR = pr.R.copy(); badR[0] = 0.0
+    assert call(R=badR) == B.ERR_NONPOSITIVE_R
+    badX = pr.X.copy(); badX[1, 5] = np.nan
+    assert call(X=badX) == B.ERR_NONFINITE
+
+
+def test_iteration_cap_reports_not_converged(B):
+    pr = workloads.gaussian_problem_1d("cap", n=400, N=5, length_scale=6.0, obs_stride=2, r2=0.1,
+                                       half_width=10.0, Q=4, tol=1e-14, seed=14)
+    opts = B.make_options(precision=0, ritz_rank=0, max_iter=2)
+    mu_a, A_a, st = B.info_esrf_analysis(pr.grid, dev(pr.X), dev(pr.obs_idx), dev(pr.y), dev(pr.R), pr.Q,
+                                         1e-14, opts)
+    assert st["status"] == B.NOT_CONVERGED and st["n_unconverged"] > 0 and st["iters_max"] == 2
+    assert np.all(np.isfinite(A_a.cpu().numpy()))
