@@ -185,6 +185,33 @@ int info_esrf_analysis_batched(const info_esrf_problem* probs, int32_t count,
                                const info_esrf_options* opt, void* workspace, size_t ws_bytes,
                                void* stream, info_esrf_stats* stats);
 
+/* Allocation-free variant of info_esrf_analysis.  The paper has no
+ * counterpart: this is a deployment convenience of this library.
+ *
+ * For callers that may not allocate device memory at all (a plug-in inside
+ * an application that owns every device byte through its own pool, or a
+ * real-time loop that cannot take cudaMalloc's implicit synchronization) and
+ * so cannot hand in a workspace.  The workspace comes from a 32 MiB array
+ * compiled into the library; every GPU that loads the library holds it until
+ * the process exits.  Problems whose info_esrf_workspace_size() exceeds
+ * 32 MiB are rejected with INFO_ESRF_ERR_UNSUPPORTED (set
+ * options.max_neighbors, e.g. from info_esrf_neighbor_counts, to shrink the
+ * bands).  The call allocates nothing and never calls cudaMalloc/cudaFree.
+ *
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  All
+ * calls share the one array, so calls whose GPU work overlaps (other streams,
+ * other threads) race and corrupt each other: serialize them.  Every scratch
+ * word a call reads is written earlier in the same call, so leftovers of the
+ * previous call are harmless.  The call is asynchronous and returns no
+ * statistics; device-detected input errors are not reported (use
+ * info_esrf_analysis with stats to diagnose).  Arguments and outputs as for
+ * info_esrf_analysis. */
+int info_esrf_analysis_noalloc(const info_esrf_grid* grid, int64_t N, const double* X_dev, int64_t d,
+                               const int64_t* obs_idx_dev, const double* y_dev, const double* R_diag_dev,
+                               int32_t Q, double tol, const info_esrf_options* opt, void* stream,
+                               double* mu_a_dev, double* A_a_dev);
+
 #ifdef __cplusplus
 }
 #endif
