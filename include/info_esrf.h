@@ -108,7 +108,7 @@ typedef struct {
   int32_t n_systems;      /* systems solved (Q * N perturbation + mean) */
   double iters_mean;
   int32_t n_unconverged;
-  int32_t pad_;
+  int32_t solver_path;    /* 1: cluster-resident band kernel (1-D networks), 0: general kernel */
   double max_rel_resid;   /* max recurrence ||r|| / ||b|| at exit */
   double ell_used;
   double gershgorin;      /* max_a sum_b |C(a, b)| */

@@ -56,7 +56,7 @@ class Options(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("status", c_int32), ("device_flags", c_int32), ("iters_max", c_int32),
                 ("n_systems", c_int32), ("iters_mean", c_double), ("n_unconverged", c_int32),
-                ("pad_", c_int32), ("max_rel_resid", c_double), ("ell_used", c_double),
+                ("solver_path", c_int32), ("max_rel_resid", c_double), ("ell_used", c_double),
                 ("gershgorin", c_double)]
 
     def as_dict(self):

@@ -137,9 +137,9 @@ void carve_problem(Carver& cv, ProblemDev& pr, const info_esrf_options& o) {
   pr.CPhi = cv.take<void>((size_t)d * k * esz);
   pr.theta = cv.take<double>((size_t)k * 8);
   pr.gram = cv.take<double>((size_t)3 * k * k * 8);
-  pr.U = cv.take<void>((size_t)pr.num_groups * d * pr.JT * esz);
-  pr.iters = cv.take<int32_t>((size_t)pr.num_groups * pr.JT * 4);
-  pr.relres = cv.take<double>((size_t)pr.num_groups * pr.JT * 8);
+  pr.U = cv.take<void>((size_t)pr.nsys * d * esz);
+  pr.iters = cv.take<int32_t>((size_t)pr.nsys * 4);
+  pr.relres = cv.take<double>((size_t)pr.nsys * 8);
   pr.Vbar = cv.take<double>((size_t)d * (N + 1) * 8);
   pr.VbarT = cv.take<void>((size_t)d * (N + 1) * esz);
 }
@@ -155,7 +155,7 @@ int build_table(const info_esrf_problem* probs, int32_t count, const info_esrf_o
   Carver cv{reinterpret_cast<char*>(ws)};
   ProblemDev* dtab = cv.take<ProblemDev>(sizeof(ProblemDev) * count);
   int32_t* counter = cv.take<int32_t>(64);
-  int group_base = 0;
+  int group_base = 0, sys_base = 0;
   const int JT = pcg_jt(o.precision);
   for (int i = 0; i < count; ++i) {
     const info_esrf_problem& P = probs[i];
@@ -204,9 +204,14 @@ int build_table(const info_esrf_problem* probs, int32_t count, const info_esrf_o
     pr.num_groups = (pr.do_pert ? pr.Q * pr.groups_per_q : 0) + (pr.do_mean ? 1 : 0);
     pr.group_base = group_base;
     group_base += pr.num_groups;
+    pr.mean_sys = pr.do_mean ? 1 : 0;
+    pr.nsys = pr.mean_sys + (pr.do_pert ? pr.Q * (int32_t)pr.N : 0);
+    pr.sys_base = sys_base;
+    sys_base += pr.nsys;
     carve_problem(cv, pr, o);
   }
   tab.total_groups = group_base;
+  tab.total_sys = sys_base;
   const size_t sb = pcg_scratch_bytes(tab, num_sms);
   void* scratch = cv.take<void>(sb);
   *bytes_out = cv.off;
@@ -270,7 +275,7 @@ int run_batch(const info_esrf_problem* probs, int32_t count, const info_esrf_opt
     memset(&s, 0, sizeof(s));
     int32_t status[4];
     double scal[8];
-    const size_t nsys = (size_t)pr.num_groups * pr.JT;
+    const size_t nsys = (size_t)pr.nsys;
     std::vector<int32_t> it(nsys);
     std::vector<double> rr(nsys);
     if (cudaMemcpy(status, pr.status, sizeof(status), cudaMemcpyDeviceToHost) != cudaSuccess ||
@@ -282,19 +287,15 @@ int run_batch(const info_esrf_problem* probs, int32_t count, const info_esrf_opt
     int64_t live = 0, sum_it = 0;
     int32_t it_max = 0, unconv = 0;
     double rmax = 0.0;
-    for (int g = 0; g < pr.num_groups; ++g) {
-      const bool mean_group = pr.do_mean && g == pr.num_groups - 1;
-      const int lanes = mean_group ? 1 : (int)std::min<int64_t>(pr.JT, pr.N - (g % pr.groups_per_q) * pr.JT);
-      for (int j = 0; j < lanes; ++j) {
-        const size_t sidx = (size_t)g * pr.JT + j;
-        ++live;
-        sum_it += it[sidx];
-        it_max = std::max(it_max, it[sidx]);
-        rmax = std::max(rmax, rr[sidx]);
-        if (o.fixed_iters <= 0 && !(rr[sidx] <= pr.tol)) ++unconv;
-      }
+    for (size_t sidx = 0; sidx < nsys; ++sidx) {
+      ++live;
+      sum_it += it[sidx];
+      it_max = std::max(it_max, it[sidx]);
+      rmax = std::max(rmax, rr[sidx]);
+      if (o.fixed_iters <= 0 && !(rr[sidx] <= pr.tol)) ++unconv;
     }
     s.device_flags = status[0];
+    s.solver_path = status[1] & 1;
     s.iters_max = it_max;
     s.n_systems = (int32_t)live;
     s.iters_mean = live ? (double)sum_it / (double)live : 0.0;

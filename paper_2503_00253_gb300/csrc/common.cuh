@@ -252,6 +252,23 @@ __device__ __forceinline__ void block_sum(DotAcc<float> (&acc)[NV], double (&out
   __syncthreads();
 }
 
+// Butterfly reduce-scatter of 32 values per lane: afterwards lane l holds
+// the warp-wide sum of value l (31 shuffles instead of 32 x 5).
+template <typename T>
+__device__ __forceinline__ T warp_reduce_scatter32(T (&v)[32], int lane) {
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    const bool up = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < off; ++i) {
+      const T send = up ? v[i] : v[i + off];
+      const T keep = up ? v[i + off] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+  return v[0];
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -18,21 +18,18 @@ __global__ void k_accumulate(const ProblemDev* tab) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= pr.d * N1) return;
   const int64_t a = i / N1, m = i % N1;
-  const int JT = pr.JT;
   const int64_t d = pr.d;
   const T* U = reinterpret_cast<const T*>(pr.U);
   double acc = 0.0;
   if (m < pr.N) {
     if (pr.do_pert) {
-      const int64_t g0 = m / JT, lane = m % JT;
       for (int q = 0; q < pr.Q; ++q) {
-        const int64_t g = (int64_t)q * pr.groups_per_q + g0;
-        acc += pr.p[q] * (double)U[(g * d + a) * JT + lane];
+        const int64_t sid = pr.mean_sys + (int64_t)q * pr.N + m;
+        acc += pr.p[q] * (double)U[sid * d + a];
       }
     }
   } else if (pr.do_mean) {
-    const int64_t g = pr.do_pert ? (int64_t)pr.Q * pr.groups_per_q : 0;
-    acc = (double)U[(g * d + a) * JT];
+    acc = (double)U[a];   // sid 0
   }
   const double v = pr.rinv[a] * acc;
   pr.Vbar[a * N1 + m] = v;

@@ -82,10 +82,15 @@ struct ProblemDev {
   const float* learn_diag;   // [Q + 1][d] >= 0, NULL: none
   const float* learn_U;      // [Q + 1][d][learn_rank]
   // batched PCG
+  // Systems are numbered hardest first: sid 0 is the mean system (shift 1)
+  // when requested, then the perturbation systems node-major,
+  // sid = mean_sys + q * N + i (s_q increases with q).
   int32_t JT, groups_per_q, num_groups, group_base;
-  void* U;              // [num_groups][d][JT] T solutions u of C_q u = b
-  int32_t* iters;       // [num_groups * JT]
-  double* relres;       // [num_groups * JT] final ||r|| / ||b|| (recurrence)
+  int32_t nsys, mean_sys;   // number of systems; 1 if sid 0 is the mean system else 0
+  int32_t sys_base, pad2_;  // first sid of this problem in a batch-wide numbering
+  void* U;              // [nsys][d] T solutions u of C_q u = b
+  int32_t* iters;       // [nsys]
+  double* relres;       // [nsys] final ||r|| / ||b|| (recurrence)
   double* Vbar;         // [d][N + 1] FP64 R^-1/2 sum_q p_q u_q (last column: mean)
   void* VbarT;          // [d][N + 1] T copy for the state apply
 };
@@ -93,7 +98,8 @@ struct ProblemDev {
 struct ProblemTable {
   int32_t count;
   int32_t total_groups;
-  int32_t pad_[2];
+  int32_t total_sys;
+  int32_t pad_;
   ProblemDev p[kMaxProblems];
 };
 
@@ -117,6 +123,11 @@ void launch_lmp_apply(const ProblemDev& pr, const ProblemDev* dpr, int32_t nvec,
 
 // Host-side count of kernel launches issued by this library.
 void note_launches(int n);
+
+// Cluster-resident PCG for 1-D observation networks (single problem, FP32).
+bool band1d_eligible(const ProblemTable& tab);
+int launch_pcg_band1d(const ProblemTable& tab, const ProblemDev* dtab, int32_t* queue, int32_t* fallback,
+                      int num_sms, cudaStream_t st);
 
 // PCG vector scratch per CTA when vectors do not fit in shared memory.
 size_t pcg_scratch_bytes(const ProblemTable& tab, int num_sms);

@@ -20,10 +20,6 @@
 // So f, g and r^T r come out of the same block reduction as the residual
 // norm, and one PCG iteration needs two block reductions.
 //
-// An optional learned correction adds D_q r + U_q (U_q^T r) (D_q >= 0), which
-// keeps the preconditioner symmetric positive definite; its projections ride
-// in the same reduction.
-//
 // Scalars (rho, alpha, beta, norms, the k x k preconditioner algebra) are FP64
 // and handled by one thread per system; dot products of FP32 vectors are
 // accumulated as float-float pairs.
@@ -58,23 +54,6 @@ __device__ __forceinline__ void st_row(T* base, int64_t a, const Row<T, JT>& r) 
   for (int i = 0; i < (int)(sizeof(T) * JT / 16); ++i) dst[i] = src[i];
 }
 
-// Butterfly reduce-scatter of 32 values per lane: afterwards lane l holds
-// the warp-wide sum of value l (31 shuffles instead of 32 x 5).
-template <typename T>
-__device__ __forceinline__ T warp_reduce_scatter32(T (&v)[32], int lane) {
-#pragma unroll
-  for (int off = 16; off >= 1; off >>= 1) {
-    const bool up = (lane & off) != 0;
-#pragma unroll
-    for (int i = 0; i < off; ++i) {
-      const T send = up ? v[i] : v[i + off];
-      const T keep = up ? v[i + off] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-    }
-  }
-  return v[0];
-}
-
 struct GroupInfo {
   int prob;
   int lanes;     // active systems in this group
@@ -90,16 +69,16 @@ __device__ __forceinline__ GroupInfo decode_group(const ProblemDev* tab, int cou
   const ProblemDev& pr = tab[p];
   gi.prob = p;
   gi.lg = gg - pr.group_base;
-  const int npert = pr.do_pert ? pr.Q * pr.groups_per_q : 0;
-  if (gi.lg < npert) {
-    gi.q = gi.lg / pr.groups_per_q;
-    gi.i0 = (gi.lg % pr.groups_per_q) * pr.JT;
-    const int left = (int)pr.N - gi.i0;
-    gi.lanes = left < pr.JT ? left : pr.JT;
-  } else {
+  if (gi.lg < pr.mean_sys) {         // the mean system comes first (hardest shift)
     gi.q = -1;
     gi.i0 = 0;
     gi.lanes = 1;
+  } else {
+    const int pg = gi.lg - pr.mean_sys;
+    gi.q = pg / pr.groups_per_q;
+    gi.i0 = (pg % pr.groups_per_q) * pr.JT;
+    const int left = (int)pr.N - gi.i0;
+    gi.lanes = left < pr.JT ? left : pr.JT;
   }
   return gi;
 }
@@ -111,7 +90,6 @@ struct PcgShared {
   double thq[KMAX + 1];
   T alpha[JT], beta[JT];
   T tco[JT][KMAX + 1], cco[JT][KMAX + 1];
-  T ul[JT][kMaxLearnRank];
   int active[JT];
   int iters[JT];
   int any_active;
@@ -154,11 +132,10 @@ __device__ __forceinline__ double combine_partials(const float (*ff)[2], const d
 template <typename T, int JT, int KMAX>
 __global__ void __launch_bounds__(kThreads, 1)
 k_pcg(const ProblemDev* tab, int count, int total_groups, int32_t* counter, T* gscratch,
-      int64_t scratch_stride, int use_smem) {
+      int64_t scratch_stride, int use_smem, const int32_t* gate) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int NW = kThreads / 32;
-  constexpr int NVCAP = KMAX <= 12 ? 32 : 64;    // rr, f[k], g[k], e[kl], r^T D r
-  constexpr int LRCAP = (NVCAP - 2 - 2 * KMAX) < kMaxLearnRank ? (NVCAP - 2 - 2 * KMAX) : kMaxLearnRank;
+  constexpr int NVCAP = KMAX <= 12 ? 32 : 64;    // rr, f[k], g[k]
   __shared__ PcgShared<T, JT, KMAX> sh;
   __shared__ T red[JT][NVCAP][NW];
   __shared__ double redd[JT][NVCAP];
@@ -166,6 +143,8 @@ k_pcg(const ProblemDev* tab, int count, int total_groups, int32_t* counter, T* g
   __shared__ double wpd[JT][NW];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // When the band kernel ran first, this kernel only solves if it fell back.
+  if (gate && *gate == 0) return;
 
   for (;;) {
     if (tid == 0) sh.group = atomicAdd(counter, 1);
@@ -176,9 +155,6 @@ k_pcg(const ProblemDev* tab, int count, int total_groups, int32_t* counter, T* g
     const ProblemDev& pr = tab[gi.prob];
     const int64_t d = pr.d, N = pr.N;
     const int k = pr.kR < KMAX ? pr.kR : KMAX;
-    const bool has_learn = pr.learn_diag != nullptr;
-    const int kl = has_learn ? (pr.learn_rank < LRCAP ? pr.learn_rank : LRCAP) : 0;
-    const int qslot = gi.q < 0 ? pr.Q : gi.q;
 
     T* base = use_smem ? reinterpret_cast<T*>(smem_raw) : gscratch + (int64_t)blockIdx.x * scratch_stride;
     T* vr = base;
@@ -189,8 +165,6 @@ k_pcg(const ProblemDev* tab, int count, int total_groups, int32_t* counter, T* g
     const T* Phi = reinterpret_cast<const T*>(pr.Phi);
     const T* CPhi = reinterpret_cast<const T*>(pr.CPhi);
     const T* W = reinterpret_cast<const T*>(pr.W);
-    const float* ldiag = has_learn ? pr.learn_diag + (int64_t)qslot * d : nullptr;
-    const float* lU = has_learn ? pr.learn_U + (int64_t)qslot * d * kl : nullptr;
 
     // ---- group setup: shift, LMP constants, G_q ----
     if (tid == 0) {
@@ -259,12 +233,6 @@ k_pcg(const ProblemDev* tab, int count, int total_groups, int32_t* counter, T* g
               v[1 + KMAX + m] += CPhi[a * pk + m] * r;
             }
           }
-          if (has_learn) {
-#pragma unroll
-            for (int m = 0; m < LRCAP; ++m)
-              if (m < kl) v[1 + 2 * KMAX + m] += (T)lU[a * kl + m] * r;
-            v[NVCAP - 1] += (T)ldiag[a] * r * r;
-          }
         }
         const T s0 = warp_reduce_scatter32<T>(*reinterpret_cast<T(*)[32]>(&v[0]), lane);
         red[j][lane][warp] = s0;
@@ -315,19 +283,9 @@ k_pcg(const ProblemDev* tab, int count, int total_groups, int32_t* counter, T* g
           }
           rho = rr - gt + fc;
         }
-        if (has_learn) {
-          double el2 = 0.0;
-          for (int m = 0; m < kl; ++m) {
-            const double e = redd[j][1 + 2 * KMAX + m];
-            el2 += e * e;
-            sh.ul[j][m] = to_t<T>(e);
-          }
-          rho += redd[j][NVCAP - 1] + el2;
-        }
         if (!act) {
           sh.beta[j] = T(0);
           for (int m = 0; m < k; ++m) { sh.tco[j][m] = T(0); sh.cco[j][m] = T(0); }
-          for (int m = 0; m < kl; ++m) sh.ul[j][m] = T(0);
         } else if (first) {
           sh.beta[j] = T(0);
           sh.rho[j] = rho;
@@ -359,16 +317,6 @@ k_pcg(const ProblemDev* tab, int count, int total_groups, int32_t* counter, T* g
           const T ph = Phi[a * pk + m], cp = CPhi[a * pk + m];
 #pragma unroll
           for (int j = 0; j < JT; ++j) z[j] += ph * sh.cco[j][m] - cp * sh.tco[j][m];
-        }
-        if (has_learn) {
-          const T dg = (T)ldiag[a];
-#pragma unroll
-          for (int j = 0; j < JT; ++j) z[j] += dg * r.v[j];
-          for (int m = 0; m < kl; ++m) {
-            const T u = (T)lU[a * kl + m];
-#pragma unroll
-            for (int j = 0; j < JT; ++j) z[j] += u * sh.ul[j][m];
-          }
         }
 #pragma unroll
         for (int j = 0; j < JT; ++j) p.v[j] = sh.active[j] ? z[j] + sh.beta[j] * p.v[j] : p.v[j];
@@ -447,15 +395,17 @@ k_pcg(const ProblemDev* tab, int count, int total_groups, int32_t* counter, T* g
     }
 
     // ---- results ----
-    T* U = reinterpret_cast<T*>(pr.U) + (int64_t)gi.lg * d * JT;
-    for (int64_t a = tid; a < d; a += blockDim.x) st_row<T, JT>(U, a, ld_row<T, JT>(vx, a));
-    if (tid < JT) {
-      const int64_t sidx = (int64_t)gi.lg * JT + tid;
-      const bool live = tid < gi.lanes;
-      pr.iters[sidx] = live ? sh.iters[tid] : 0;
+    // lane j holds system sid0 + j (the mean group has one lane, sid 0)
+    const int64_t sid0 = gi.q < 0 ? 0 : pr.mean_sys + (int64_t)gi.q * N + gi.i0;
+    T* U = reinterpret_cast<T*>(pr.U);
+    for (int j = 0; j < gi.lanes; ++j)
+      for (int64_t a = tid; a < d; a += blockDim.x) U[(sid0 + j) * d + a] = vx[a * JT + j];
+    if (tid < gi.lanes) {
+      const int64_t sidx = sid0 + tid;
+      pr.iters[sidx] = sh.iters[tid];
       const double bn = sh.bn2[tid];
-      pr.relres[sidx] = live ? (bn > 0 ? sqrt(sh.rr[tid] / bn) : 0.0) : 0.0;
-      if (live && sh.active[tid] && pr.fixed_iters <= 0) atomicOr(&pr.status[0], kStatNotConverged);
+      pr.relres[sidx] = bn > 0 ? sqrt(sh.rr[tid] / bn) : 0.0;
+      if (sh.active[tid] && pr.fixed_iters <= 0) atomicOr(&pr.status[0], kStatNotConverged);
     }
     __syncthreads();
   }
@@ -481,7 +431,7 @@ size_t pcg_scratch_bytes(const ProblemTable& tab, int num_sms) {
 
 template <typename T, int JT, int KMAX>
 static int launch_pcg_t(const ProblemTable& tab, const ProblemDev* dtab, int32_t* counter, void* scratch,
-                        size_t scratch_bytes, int num_sms, cudaStream_t st) {
+                        size_t scratch_bytes, int num_sms, cudaStream_t st, const int32_t* gate) {
   const size_t vb = vec_bytes(tab);
   const int use_smem = vb <= kSmemVecLimit;
   const size_t dyn = use_smem ? vb : 0;
@@ -492,26 +442,28 @@ static int launch_pcg_t(const ProblemTable& tab, const ProblemDev* dtab, int32_t
   cudaMemsetAsync(counter, 0, sizeof(int32_t), st);
   k_pcg<T, JT, KMAX><<<grid, kThreads, dyn, st>>>(dtab, tab.count, tab.total_groups, counter,
                                             reinterpret_cast<T*>(scratch), (int64_t)(vb / sizeof(T)),
-                                            use_smem);
+                                            use_smem, gate);
   note_launches(1);
   return 0;
 }
 
 int launch_pcg(const ProblemTable& tab, const ProblemDev* dtab, int32_t* counter, void* scratch,
                size_t scratch_bytes, int num_sms, cudaStream_t st) {
-  int kmax = 0, lmax = 0;
-  for (int i = 0; i < tab.count; ++i) {
-    kmax = tab.p[i].kR > kmax ? tab.p[i].kR : kmax;
-    const int kl = tab.p[i].learn_diag ? tab.p[i].learn_rank : 0;
-    lmax = kl > lmax ? kl : lmax;
+  int kmax = 0;
+  for (int i = 0; i < tab.count; ++i) kmax = tab.p[i].kR > kmax ? tab.p[i].kR : kmax;
+  const bool small = kmax <= 12;
+  // counter[0]: group queue of this kernel; counter[1]: system queue of the band
+  // kernel; counter[2]: its fall-back flag.
+  const int32_t* gate = nullptr;
+  if (band1d_eligible(tab)) {
+    if (launch_pcg_band1d(tab, dtab, counter + 1, counter + 2, num_sms, st) == 0) gate = counter + 2;
   }
-  const bool small = kmax <= 12 && (lmax == 0 || 2 * 12 + lmax + 2 <= 32);
   if (tab.p[0].precision == 0) {
-    if (small) return launch_pcg_t<double, 4, 12>(tab, dtab, counter, scratch, scratch_bytes, num_sms, st);
-    return launch_pcg_t<double, 4, 24>(tab, dtab, counter, scratch, scratch_bytes, num_sms, st);
+    if (small) return launch_pcg_t<double, 4, 12>(tab, dtab, counter, scratch, scratch_bytes, num_sms, st, gate);
+    return launch_pcg_t<double, 4, 24>(tab, dtab, counter, scratch, scratch_bytes, num_sms, st, gate);
   }
-  if (small) return launch_pcg_t<float, 8, 12>(tab, dtab, counter, scratch, scratch_bytes, num_sms, st);
-  return launch_pcg_t<float, 8, 24>(tab, dtab, counter, scratch, scratch_bytes, num_sms, st);
+  if (small) return launch_pcg_t<float, 8, 12>(tab, dtab, counter, scratch, scratch_bytes, num_sms, st, gate);
+  return launch_pcg_t<float, 8, 24>(tab, dtab, counter, scratch, scratch_bytes, num_sms, st, gate);
 }
 
 // ---------------------------------------------------------------------------

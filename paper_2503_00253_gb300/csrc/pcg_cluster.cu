@@ -1,0 +1,648 @@
+// a5-a7 for one-dimensional observation networks: cluster-resident batched
+// shifted PCG (App. E, Eq. normalized_linear_solve; Golub & Van Loan Alg. 11.5.1)
+// with the band of C held in shared memory for the whole launch.
+//
+// Why: every (node, member) system uses the same C, and C is re-read once
+// per iteration per system group.  Streaming it from L2 each iteration made
+// the first kernel L2-latency bound.  Here a thread-block cluster of CS CTAs
+// splits the rows of C: CTA c owns rows [c R_s, (c+1) R_s) and keeps them,
+// as dense 16-row tiles over each tile's column window (zeros outside a
+// row's band), in shared memory for the whole launch.  The cluster iterates
+// kJ = 32 systems at once (the "lanes"); each CTA holds the lanes' vectors on
+// its own rows, plus a window of p widened by the band's reach, whose halo
+// rows are copied from the owning CTAs through distributed shared memory.
+//
+// On a 1-D grid the observations within the Gaspari-Cohn support of an
+// observation form a contiguous cyclic range of (sorted) observation
+// indices, which is what makes the row tiles dense; the kernel checks this
+// and the shared-memory budget at start-up and, if either fails, sets a
+// flag and exits so that the general kernel solves the systems instead.
+//
+// Per iteration (three cluster barriers):
+//   matvec y = sigma p + C p and partial p^T y      -> barrier 1 -> alpha
+//   x += alpha p, r -= alpha y, partial r^T r, Phi^T r, A^T r -> barrier 2
+//   convergence, preconditioner scalars, refills;  p = z + beta p   -> barrier 3
+//   new lanes start, halo of p copied from the neighbours.
+// Every CTA sums the CS partials in rank order, so all CTAs of a cluster
+// take identical decisions without further communication.  A lane whose
+// system converges is refilled with the next system of a global queue
+// ordered hardest (smallest shift) first, so no lane idles while work
+// remains.  Scalars of the CG recurrence are FP64; the k x k algebra of the
+// limited-memory preconditioner is FP32 (it only shapes the preconditioner).
+#include <cooperative_groups.h>
+#include <math.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace infoesrf {
+
+namespace {
+
+constexpr int kJ = 32;          // lanes (systems) per cluster
+constexpr int kLD = kJ + 4;     // padded row stride (floats) of lane-major row vectors
+constexpr int kTile = 16;       // rows per matvec tile
+constexpr int kNW = kThreads / 32;
+constexpr int kK = 12;          // Ritz vectors handled by this kernel
+constexpr int kNR = 2 + 2 * kK; // residual reduction values per lane: rr (hi, lo), f[k], g[k]
+constexpr int kMaxTiles = 128;  // rows per CTA <= 2048
+
+enum : int { kEmpty = 0, kStart = 1, kActive = 2 };
+
+struct LaneState {
+  int sid[kJ], state[kJ], it[kJ], newsid[kJ], fin[kJ];
+  double sigma[kJ], rho[kJ], bn2[kJ], rr[kJ];
+  float sigf[kJ], alpha[kJ], beta[kJ];
+  float t[kJ][kK], c[kJ][kK];
+  float f[kJ][kK], g[kJ][kK];
+};
+
+struct Setup {
+  int hl, hr, bad, tilesz;
+  int xchg[4];
+};
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+
+__device__ __forceinline__ int wrap_delta(int64_t col, int64_t a, int64_t d) {
+  int64_t dl = (col - a) % d;
+  if (dl < 0) dl += d;
+  if (2 * dl > d) dl -= d;
+  return (int)dl;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kThreads, 1)
+k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_floats) {
+  extern __shared__ __align__(16) float dyn[];
+  __shared__ LaneState L;
+  __shared__ Setup S;
+  __shared__ int s_klo[kMaxTiles], s_w[kMaxTiles], s_off[kMaxTiles];
+  __shared__ float s_gram[3][kK * kK];
+  __shared__ float s_theta[kK];
+  __shared__ float s_pap[kJ][2];                 // CTA partial of p^T y (float-float), read remotely
+  __shared__ float s_res[kJ][kNR];               // CTA partials of rr, f, g, read remotely
+  __shared__ float s_wpap[kNW][kJ][2];
+  __shared__ int s_lo_min, s_hi_max, s_bad;
+
+  cg::cluster_group cluster = cg::this_cluster();
+  const int CS = (int)cluster.num_blocks();
+  const int crank = (int)cluster.block_rank();
+  const int cl_id = blockIdx.x / CS;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const ProblemDev& pr = tab[0];
+  const int64_t d = pr.d, N = pr.N;
+  const int k = pr.kR < kK ? pr.kR : kK;
+  const int pk = pr.kR;
+  const int R_s = (int)((d + CS - 1) / CS);
+  const int64_t s0 = (int64_t)crank * R_s;
+  const int nrows = (int)(d - s0 < 0 ? 0 : (d - s0 < R_s ? d - s0 : R_s));
+  const int ntiles = (nrows + kTile - 1) / kTile;
+
+  // ---------------- set-up: band reach of the own rows ----------------
+  if (tid == 0) { s_lo_min = 1 << 30; s_hi_max = -(1 << 30); s_bad = (R_s > kMaxTiles * kTile) ? 1 : 0; }
+  __syncthreads();
+  // per-row window [lo, hi] relative to s0, kept in the dynamic buffer's tail
+  int* rlo = reinterpret_cast<int*>(dyn) + (dyn_floats - 2 * R_s);
+  int* rhi = rlo + R_s;
+  if (2 * R_s > dyn_floats) s_bad = 1;
+  __syncthreads();
+  if (!s_bad) {
+    for (int row = tid; row < nrows; row += blockDim.x) {
+      const int64_t a = s0 + row;
+      const int nnz = pr.oo_nnz[a];
+      int dmin = 1 << 30, dmax = -(1 << 30);
+      for (int e = 0; e < nnz; ++e) {
+        const int dl = wrap_delta(pr.oo_col[(int64_t)e * d + a], a, d);
+        dmin = dl < dmin ? dl : dmin;
+        dmax = dl > dmax ? dl : dmax;
+      }
+      bool ok = nnz >= 1 && (dmax - dmin + 1) == nnz && 2 * (int64_t)(dmax - dmin + 1) < d;
+      if (!ok) atomicOr(&s_bad, 1);
+      rlo[row] = row + dmin;
+      rhi[row] = row + dmax;
+      atomicMin(&s_lo_min, row + dmin);
+      atomicMax(&s_hi_max, row + dmax);
+    }
+  }
+  __syncthreads();
+  // tile windows
+  if (!s_bad) {
+    for (int t = warp; t < ntiles; t += kNW) {
+      const int row = t * kTile + (lane & 15);
+      int lo = 1 << 30, hi = -(1 << 30);
+      if (lane < 16 && row < nrows) { lo = rlo[row]; hi = rhi[row]; }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+      }
+      if (lane == 0) { s_klo[t] = lo; s_w[t] = hi - lo + 1; }
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int off = 0;
+    if (!s_bad)
+      for (int t = 0; t < ntiles; ++t) { s_off[t] = off; off += s_w[t] * kTile; }
+    S.tilesz = off;
+    S.hl = nrows > 0 ? (s_lo_min < 0 ? -s_lo_min : 0) : 0;
+    S.hr = nrows > 0 ? (s_hi_max > R_s - 1 ? s_hi_max - (R_s - 1) : 0) : 0;
+    S.bad = s_bad;
+    S.xchg[0] = S.hl; S.xchg[1] = S.hr; S.xchg[2] = S.bad; S.xchg[3] = S.tilesz;
+  }
+  cluster.sync();
+  int hl = 0, hr = 0, bad = 0, tilesz = 0;
+  for (int c = 0; c < CS; ++c) {
+    const Setup* rs = cluster.map_shared_rank(&S, c);
+    hl = max(hl, rs->xchg[0]);
+    hr = max(hr, rs->xchg[1]);
+    bad |= rs->xchg[2];
+    tilesz = max(tilesz, rs->xchg[3]);
+  }
+  // shared-memory carve (floats): tiles | p window | r | x | y | Phi^T | A^T
+  const int W_p = R_s + hl + hr;
+  const int o_pw = (tilesz + 3) & ~3;
+  const int o_r = o_pw + W_p * kLD;
+  const int o_x = o_r + R_s * kLD;
+  const int o_y = o_x + R_s * kLD;
+  const int o_ph = o_y + R_s * kLD;
+  const int o_at = o_ph + k * R_s;
+  const int need = o_at + k * R_s;
+  if (need > dyn_floats - 2 * R_s) bad = 1;      // keep the per-row windows intact while tiles fill
+  cluster.sync();                                   // remote reads of S done before anyone exits
+  if (bad) {
+    if (cl_id == 0 && crank == 0 && tid == 0) *fallback = 1;
+    return;
+  }
+  if (cl_id == 0 && crank == 0 && tid == 0) atomicOr(&pr.status[1], 1);
+  float* Ct = dyn;
+  float* pw = dyn + o_pw;
+  float* vr = dyn + o_r;
+  float* vx = dyn + o_x;
+  float* vy = dyn + o_y;
+  float* phT = dyn + o_ph;
+  float* aT = dyn + o_at;
+  const float* val = reinterpret_cast<const float*>(pr.oo_val);
+  const float* Phi = reinterpret_cast<const float*>(pr.Phi);
+  const float* CPhi = reinterpret_cast<const float*>(pr.CPhi);
+  const float* W = reinterpret_cast<const float*>(pr.W);
+
+  // ---------------- set-up: fill tiles and the constant arrays ----------------
+  for (int i = tid; i < tilesz; i += blockDim.x) Ct[i] = 0.f;
+  for (int i = o_pw + tid; i < o_ph; i += blockDim.x) dyn[i] = 0.f;
+  __syncthreads();
+  for (int row = tid; row < nrows; row += blockDim.x) {
+    const int64_t a = s0 + row;
+    const int nnz = pr.oo_nnz[a];
+    const int t = row / kTile, r = row % kTile;
+    for (int e = 0; e < nnz; ++e) {
+      const int rel = row + wrap_delta(pr.oo_col[(int64_t)e * d + a], a, d);
+      Ct[s_off[t] + (rel - s_klo[t]) * kTile + r] = val[(int64_t)e * d + a];
+    }
+  }
+  for (int i = tid; i < k * R_s; i += blockDim.x) {
+    const int m = i / R_s, row = i % R_s;
+    const bool ok = row < nrows;
+    phT[i] = ok ? Phi[(s0 + row) * pk + m] : 0.f;
+    aT[i] = ok ? CPhi[(s0 + row) * pk + m] : 0.f;
+  }
+  for (int i = tid; i < 3 * k * k; i += blockDim.x) {
+    const int w3 = i / (k * k), e = i % (k * k), ii = e / k, jj = e % k;
+    s_gram[w3][e] = (float)pr.gram[w3 * pk * pk + ii * pk + jj];
+  }
+  for (int m = tid; m < k; m += blockDim.x) s_theta[m] = (float)pr.theta[m];
+  const double cmin = pr.scal[1];
+  const int maxit = pr.fixed_iters > 0 ? pr.fixed_iters : pr.max_iter;
+  const double tol2 = pr.tol * pr.tol;
+
+  // Starts system sid in lane j on the own rows (r = b, x = 0; p own rows are 0).
+  auto lane_scalars = [&](int j, int sid) {
+    L.sid[j] = sid;
+    L.fin[j] = 0;
+    if (sid < 0) {
+      L.state[j] = kEmpty;
+      L.sigma[j] = 1.0;
+    } else {
+      L.state[j] = kStart;
+      const int q = sid < pr.mean_sys ? -1 : (int)((sid - pr.mean_sys) / N);
+      L.sigma[j] = q < 0 ? 1.0 : pr.s[q] + 1.0;
+    }
+    L.sigf[j] = (float)L.sigma[j];
+    L.it[j] = 0;
+    L.alpha[j] = 0.f;
+    L.beta[j] = 0.f;
+    L.rho[j] = 0.0;
+  };
+  auto lane_vectors = [&](int j) {     // own rows of r and x for a (re)started lane
+    const int sid = L.sid[j];
+    const bool mean = sid >= 0 && sid < pr.mean_sys;
+    const int64_t i = sid >= 0 && !mean ? (sid - pr.mean_sys) % N : 0;
+    for (int row = tid; row < R_s; row += blockDim.x) {
+      float b = 0.f;
+      if (sid >= 0 && row < nrows) {
+        const int64_t a = s0 + row;
+        b = mean ? (float)pr.bmean[a] : W[a * N + i] * (float)pr.rinv[a];
+      }
+      vr[row * kLD + j] = b;
+      vx[row * kLD + j] = 0.f;
+    }
+  };
+
+  // first lanes
+  if (crank == 0 && tid == 0) {
+    const int base = atomicAdd(queue, kJ);
+    for (int j = 0; j < kJ; ++j) L.newsid[j] = base + j < pr.nsys ? base + j : -1;
+  }
+  cluster.sync();
+  if (tid < kJ) {
+    const LaneState* l0 = cluster.map_shared_rank(&L, 0);
+    lane_scalars(tid, l0->newsid[tid]);
+  }
+  __syncthreads();
+  for (int j = 0; j < kJ; ++j)
+    if (L.sid[j] >= 0) lane_vectors(j);
+  cluster.sync();   // every CTA has seen rank 0's first ids before rank 0 may reuse newsid
+
+  // halo rows: rel in [-hl, 0) and [nrows, R_s + hr) (a short last slice has
+  // no rows of its own in [nrows, R_s); those columns wrap to the first CTAs)
+  auto halo_copy = [&]() {
+    const int nh = hl + (R_s + hr - nrows);
+    for (int i = tid; i < nh * (kJ / 4); i += blockDim.x) {
+      const int hrow = i / (kJ / 4), q4 = i % (kJ / 4);
+      const int rel = hrow < hl ? hrow - hl : nrows + (hrow - hl);
+      int64_t gr = (s0 + rel) % d;
+      if (gr < 0) gr += d;
+      const int owner = (int)(gr / R_s);
+      const int lrow = (int)(gr - (int64_t)owner * R_s);
+      const float* src = cluster.map_shared_rank(pw, owner) + (lrow + hl) * kLD + 4 * q4;
+      st4(pw + (rel + hl) * kLD + 4 * q4, ld4(src));
+    }
+  };
+  halo_copy();
+  __syncthreads();
+
+  for (;;) {
+    // ---------------- A: y = sigma p + C p on the own rows, partial p^T y ----------------
+    DotAcc<float> pp[16];
+    for (int t = warp; t < ntiles; t += kNW) {
+      const int r = lane & 15, h = lane >> 4;
+      const int row = t * kTile + r;
+      const float* pown = pw + (row + hl) * kLD + 16 * h;
+      float acc[16];
+#pragma unroll
+      for (int q4 = 0; q4 < 4; ++q4) {
+        const float4 pv = ld4(pown + 4 * q4);
+        acc[4 * q4 + 0] = L.sigf[16 * h + 4 * q4 + 0] * pv.x;
+        acc[4 * q4 + 1] = L.sigf[16 * h + 4 * q4 + 1] * pv.y;
+        acc[4 * q4 + 2] = L.sigf[16 * h + 4 * q4 + 2] * pv.z;
+        acc[4 * q4 + 3] = L.sigf[16 * h + 4 * q4 + 3] * pv.w;
+      }
+      const float* ct = Ct + s_off[t] + r;
+      const float* pb = pw + (s_klo[t] + hl) * kLD + 16 * h;
+      const int wt = s_w[t];
+#pragma unroll 4
+      for (int kk = 0; kk < wt; ++kk) {
+        const float c = ct[kk * kTile];
+        const float* prow = pb + kk * kLD;
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4) {
+          const float4 pv = ld4(prow + 4 * q4);
+          acc[4 * q4 + 0] = fmaf(c, pv.x, acc[4 * q4 + 0]);
+          acc[4 * q4 + 1] = fmaf(c, pv.y, acc[4 * q4 + 1]);
+          acc[4 * q4 + 2] = fmaf(c, pv.z, acc[4 * q4 + 2]);
+          acc[4 * q4 + 3] = fmaf(c, pv.w, acc[4 * q4 + 3]);
+        }
+      }
+      const bool valid = row < nrows;
+#pragma unroll
+      for (int q4 = 0; q4 < 4; ++q4) {
+        const float4 pv = ld4(pown + 4 * q4);
+        if (valid) {
+          st4(vy + row * kLD + 16 * h + 4 * q4,
+              make_float4(acc[4 * q4], acc[4 * q4 + 1], acc[4 * q4 + 2], acc[4 * q4 + 3]));
+          pp[4 * q4 + 0].add_prod(pv.x, acc[4 * q4 + 0]);
+          pp[4 * q4 + 1].add_prod(pv.y, acc[4 * q4 + 1]);
+          pp[4 * q4 + 2].add_prod(pv.z, acc[4 * q4 + 2]);
+          pp[4 * q4 + 3].add_prod(pv.w, acc[4 * q4 + 3]);
+        }
+      }
+    }
+    {
+      const int h = lane >> 4;
+#pragma unroll
+      for (int jj = 0; jj < 16; ++jj) {
+        float hi = pp[jj].hi, lo = pp[jj].lo;
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+          const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+          const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+          ff_merge(hi, lo, h2, l2);
+        }
+        if ((lane & 15) == 0) { s_wpap[warp][16 * h + jj][0] = hi; s_wpap[warp][16 * h + jj][1] = lo; }
+      }
+    }
+    __syncthreads();
+    if (tid < kJ) {
+      float hi = 0.f, lo = 0.f;
+      for (int w = 0; w < kNW; ++w) ff_merge(hi, lo, s_wpap[w][tid][0], s_wpap[w][tid][1]);
+      s_pap[tid][0] = hi;
+      s_pap[tid][1] = lo;
+    }
+    cluster.sync();   // (1)
+    // ---------------- alpha ----------------
+    if (tid < kJ) {
+      const int j = tid;
+      float hi = 0.f, lo = 0.f;
+      for (int c = 0; c < CS; ++c) {
+        const float* rp = cluster.map_shared_rank(&s_pap[0][0], c) + 2 * j;
+        ff_merge(hi, lo, rp[0], rp[1]);
+      }
+      const double pAp = (double)hi + (double)lo;
+      float alpha = 0.f;
+      if (L.state[j] == kActive) {
+        if (pAp > 0.0 && isfinite(pAp)) {
+          alpha = (float)(L.rho[j] / pAp);
+          L.it[j] += 1;
+        } else {
+          L.fin[j] = 2;   // breakdown: finished with a flag
+        }
+      }
+      L.alpha[j] = alpha;
+    }
+    __syncthreads();
+    // ---------------- x += alpha p, r -= alpha y; partial rr, Phi^T r, A^T r ----------------
+    {
+      const int j0 = 4 * warp;   // this warp's four lanes
+      const float a0 = L.alpha[j0], a1 = L.alpha[j0 + 1], a2 = L.alpha[j0 + 2], a3 = L.alpha[j0 + 3];
+      DotAcc<float> rr[4];
+      float v[3][32];
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[b][i] = 0.f;
+      for (int row = lane; row < nrows; row += 32) {
+        const float4 p4 = ld4(pw + (row + hl) * kLD + j0);
+        const float4 y4 = ld4(vy + row * kLD + j0);
+        float4 x4 = ld4(vx + row * kLD + j0);
+        float4 r4 = ld4(vr + row * kLD + j0);
+        x4.x = fmaf(a0, p4.x, x4.x); x4.y = fmaf(a1, p4.y, x4.y);
+        x4.z = fmaf(a2, p4.z, x4.z); x4.w = fmaf(a3, p4.w, x4.w);
+        r4.x = fmaf(-a0, y4.x, r4.x); r4.y = fmaf(-a1, y4.y, r4.y);
+        r4.z = fmaf(-a2, y4.z, r4.z); r4.w = fmaf(-a3, y4.w, r4.w);
+        st4(vx + row * kLD + j0, x4);
+        st4(vr + row * kLD + j0, r4);
+        rr[0].add_prod(r4.x, r4.x); rr[1].add_prod(r4.y, r4.y);
+        rr[2].add_prod(r4.z, r4.z); rr[3].add_prod(r4.w, r4.w);
+        const float rv[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+        for (int m = 0; m < kK; ++m) {
+          if (m < k) {
+            const float ph = phT[m * R_s + row], at = aT[m * R_s + row];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+              // value index: lane-major blocks of 24 (f[12], g[12]) per lane jj
+              const int idx = jj * 2 * kK + m;
+              v[idx / 32][idx % 32] = fmaf(ph, rv[jj], v[idx / 32][idx % 32]);
+              const int idg = jj * 2 * kK + kK + m;
+              v[idg / 32][idg % 32] = fmaf(at, rv[jj], v[idg / 32][idg % 32]);
+            }
+          }
+        }
+      }
+      const float s0v = warp_reduce_scatter32<float>(v[0], lane);
+      const float s1v = warp_reduce_scatter32<float>(v[1], lane);
+      const float s2v = warp_reduce_scatter32<float>(v[2], lane);
+      const float sv[3] = {s0v, s1v, s2v};
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const int idx = 32 * b + lane;          // = jj * 24 + (m or 12 + m)
+        const int jj = idx / (2 * kK), w = idx % (2 * kK);
+        s_res[j0 + jj][2 + w] = sv[b];
+      }
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        float hi = rr[jj].hi, lo = rr[jj].lo;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+          const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+          ff_merge(hi, lo, h2, l2);
+        }
+        if (lane == 0) { s_res[j0 + jj][0] = hi; s_res[j0 + jj][1] = lo; }
+      }
+    }
+    cluster.sync();   // (2)
+    // ---------------- decisions ----------------
+    // sums over the cluster, in rank order
+    for (int e = tid; e < kJ * (2 * kK); e += blockDim.x) {
+      const int j = e / (2 * kK), w = e % (2 * kK);
+      if ((w % kK) >= k) continue;
+      float s = 0.f;
+      for (int c = 0; c < CS; ++c) s += cluster.map_shared_rank(&s_res[0][0], c)[j * kNR + 2 + w];
+      if (w < kK) L.f[j][w] = s; else L.g[j][w - kK] = s;
+    }
+    if (tid < kJ) {
+      float hi = 0.f, lo = 0.f;
+      for (int c = 0; c < CS; ++c) {
+        const float* rp = cluster.map_shared_rank(&s_res[0][0], c) + tid * kNR;
+        ff_merge(hi, lo, rp[0], rp[1]);
+      }
+      L.rr[tid] = (double)hi + (double)lo;
+    }
+    __syncthreads();
+    // preconditioner algebra: t = T^-1 f, t2 = g + sigma f - G t, c = (beta - sigma) t - T^-1 t2
+    for (int e = tid; e < kJ * k; e += blockDim.x) {
+      const int j = e / k, m = e % k;
+      L.t[j][m] = L.f[j][m] / (s_theta[m] + L.sigf[j]);
+    }
+    __syncthreads();
+    for (int e = tid; e < kJ * k; e += blockDim.x) {
+      const int j = e / k, m = e % k;
+      const float sg = L.sigf[j];
+      float t2 = L.g[j][m] + sg * L.f[j][m];
+      for (int i = 0; i < k; ++i) {
+        const float G = s_gram[2][m * k + i] + sg * (s_gram[1][m * k + i] + s_gram[1][i * k + m]) +
+                        sg * sg * s_gram[0][m * k + i];
+        t2 = fmaf(-G, L.t[j][i], t2);
+      }
+      const float bl = (float)(L.sigma[j] + cmin);
+      L.c[j][m] = (bl - sg) * L.t[j][m] - t2 / (s_theta[m] + sg);
+    }
+    __syncthreads();
+    if (tid < kJ) {
+      const int j = tid;
+      const int st = L.state[j];
+      const double rr = L.rr[j];
+      double rho = rr;
+      for (int m = 0; m < k; ++m) rho += -(double)L.g[j][m] * (double)L.t[j][m] + (double)L.f[j][m] * (double)L.c[j][m];
+      if (st == kStart) {
+        L.bn2[j] = rr;
+        if (!(rr > 0.0) || !isfinite(rr)) {
+          L.fin[j] = isfinite(rr) ? 1 : 2;
+        } else {
+          L.state[j] = kActive;
+          L.rho[j] = rho;
+          L.beta[j] = 0.f;
+        }
+      } else if (st == kActive && L.fin[j] == 0) {
+        bool done = false;
+        if (!isfinite(rr)) { done = true; L.fin[j] = 2; }
+        else if (pr.fixed_iters > 0) done = L.it[j] >= pr.fixed_iters || !(rr > 0.0);
+        else done = !(rr > tol2 * L.bn2[j]) || L.it[j] >= maxit;
+        if (done) {
+          if (L.fin[j] == 0) L.fin[j] = 1;
+        } else {
+          L.beta[j] = (float)(rho / L.rho[j]);
+          L.rho[j] = rho;
+        }
+      }
+    }
+    __syncthreads();
+    // finished lanes: stats, and rank 0 takes the next systems off the queue
+    if (crank == 0 && tid == 0) {
+      int nfin = 0;
+      for (int j = 0; j < kJ; ++j) nfin += L.fin[j] != 0;
+      const int base = nfin ? atomicAdd(queue, nfin) : 0;
+      int used = 0;
+      for (int j = 0; j < kJ; ++j) {
+        if (!L.fin[j]) continue;
+        const int sid = L.sid[j];
+        const double bn = L.bn2[j];
+        const double rel = bn > 0.0 ? sqrt(L.rr[j] / bn) : 0.0;
+        pr.iters[sid] = L.it[j];
+        pr.relres[sid] = rel;
+        if (L.fin[j] == 2) atomicOr(&pr.status[0], kStatBreakdown);
+        else if (pr.fixed_iters <= 0 && !(L.rr[j] <= tol2 * bn)) atomicOr(&pr.status[0], kStatNotConverged);
+        const int nid = base + used++;
+        L.newsid[j] = nid < pr.nsys ? nid : -1;
+      }
+    }
+    // ---------------- z = P^-1 r, p = z + beta p; finished lanes hand in x ----------------
+    {
+      const int j0 = 4 * warp;
+      float tj[4][kK], cj[4][kK];
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+        for (int m = 0; m < kK; ++m) {
+          tj[jj][m] = m < k ? L.t[j0 + jj][m] : 0.f;
+          cj[jj][m] = m < k ? L.c[j0 + jj][m] : 0.f;
+        }
+      bool act[4], fin[4];
+      float bj[4];
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        act[jj] = L.state[j0 + jj] == kActive && L.fin[j0 + jj] == 0;
+        fin[jj] = L.fin[j0 + jj] != 0;
+        bj[jj] = L.beta[j0 + jj];
+      }
+      float* U = reinterpret_cast<float*>(pr.U);
+      for (int row = lane; row < nrows; row += 32) {
+        float* prow = pw + (row + hl) * kLD + j0;
+        const float4 r4 = ld4(vr + row * kLD + j0);
+        const float4 p4 = ld4(prow);
+        float z[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+        for (int m = 0; m < kK; ++m) {
+          if (m < k) {
+            const float ph = phT[m * R_s + row], at = aT[m * R_s + row];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) z[jj] = fmaf(ph, cj[jj][m], fmaf(-at, tj[jj][m], z[jj]));
+          }
+        }
+        const float pv[4] = {p4.x, p4.y, p4.z, p4.w};
+        float pn[4];
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) pn[jj] = act[jj] ? fmaf(bj[jj], pv[jj], z[jj]) : 0.f;
+        st4(prow, make_float4(pn[0], pn[1], pn[2], pn[3]));
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj)
+          if (fin[jj]) U[(int64_t)L.sid[j0 + jj] * d + s0 + row] = vx[row * kLD + j0 + jj];
+      }
+    }
+    cluster.sync();   // (3)
+    // ---------------- refills, exit test, halo ----------------
+    if (tid < kJ && L.fin[tid]) {
+      const LaneState* l0 = cluster.map_shared_rank(&L, 0);
+      lane_scalars(tid, l0->newsid[tid]);
+    }
+    __syncthreads();
+    int live = 0;
+    for (int j = 0; j < kJ; ++j) live |= L.state[j] != kEmpty;
+    for (int j = 0; j < kJ; ++j)      // lanes started in this step: own rows of r and x
+      if (L.state[j] == kStart) lane_vectors(j);
+    if (!live) break;
+    halo_copy();
+    __syncthreads();
+  }
+  cluster.sync();   // no CTA leaves while another may still read its shared memory
+}
+
+// General kernel gate: returns whether the band kernel above can run.
+bool band1d_eligible(const ProblemTable& tab) {
+  if (tab.count != 1) return false;
+  const ProblemDev& p = tab.p[0];
+  if (p.precision != 1 || p.kR > kK) return false;
+  int active = 0;
+  for (int ax = 0; ax < 3; ++ax) active += p.grid.ext[ax] > 1;
+  if (active != 1 || p.grid.ext[0] <= 1) return false;
+  return true;
+}
+
+int launch_pcg_band1d(const ProblemTable& tab, const ProblemDev* dtab, int32_t* queue, int32_t* fallback,
+                      int num_sms, cudaStream_t st) {
+  const ProblemDev& p = tab.p[0];
+  // cluster size: 8 CTAs unless a CTA would own fewer than two row tiles; the
+  // kernel itself checks the band reach and the shared-memory budget
+  int CS = 8;
+  while (CS > 1 && (p.d + CS - 1) / CS < 2 * kTile) CS >>= 1;
+  const int clusters_max = num_sms / CS;
+  int clusters = (p.nsys + kJ - 1) / kJ;
+  if (clusters > clusters_max) clusters = clusters_max;
+  if (clusters < 1) clusters = 1;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  cudaFuncGetAttributes(&fa, k_pcg_band1d);
+  const int dyn_bytes = (optin - (int)fa.sharedSizeBytes - 1024) & ~15;
+  if (dyn_bytes <= 0 ||
+      cudaFuncSetAttribute(k_pcg_band1d, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  cudaMemsetAsync(queue, 0, sizeof(int32_t), st);
+  cudaMemsetAsync(fallback, 0, sizeof(int32_t), st);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(clusters * CS, 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = dyn_bytes;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  // A cluster shape this GPU cannot co-schedule is left to the general kernel.
+  int max_clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&max_clusters, k_pcg_band1d, &cfg) != cudaSuccess || max_clusters < 1) {
+    cudaGetLastError();
+    return -1;
+  }
+  const cudaError_t err = cudaLaunchKernelEx(&cfg, k_pcg_band1d, dtab, queue, fallback, dyn_bytes / 4);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  note_launches(1);
+  return 0;
+}
+
+}  // namespace infoesrf

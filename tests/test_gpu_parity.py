@@ -237,6 +237,28 @@ def test_single_observation(B):
     assert ea <= 1e-10 and em <= 1e-10
 
 
+def test_fp32_band_kernel_falls_back_when_band_degenerate(B):
+    """One observation: its band is not a proper sub-range, so the general kernel solves."""
+    pr = workloads.gaussian_problem_1d("one32", n=64, N=9, length_scale=4.0, obs_stride=64, r2=0.2,
+                                       half_width=5.0, Q=5, tol=1e-6, seed=19)
+    mu_a, A_a, st = run_analysis(B, pr, precision=1, ritz_rank=1)
+    ea, em = errors(pr, mu_a, A_a)
+    assert st["solver_path"] == 0 and st["status"] == 0
+    assert ea <= 1e-4 and em <= 1e-4
+
+
+@pytest.mark.parametrize("n,stride,hw,N", [(4096, 4, 40.0, 40), (3001, 3, 25.0, 33), (1500, 2, 60.0, 20)])
+def test_fp32_band_kernel_sizes(B, n, stride, hw, N):
+    """Cluster-resident kernel over several slice/cluster shapes, ragged last slice included."""
+    pr = workloads.gaussian_problem_1d("bk", n=n, N=N, length_scale=hw / 3, obs_stride=stride, r2=0.3,
+                                       half_width=hw, Q=7, tol=1e-6, seed=n + N)
+    mu_a, A_a, st = run_analysis(B, pr, precision=1, ritz_rank=6, oversample=6)
+    ea, em = errors(pr, mu_a, A_a)
+    assert st["status"] == 0, st
+    assert st["solver_path"] == 1
+    assert ea <= 1e-4 and em <= 1e-4, (ea, em)
+
+
 def test_mean_and_perturbation_calls_alone(B):
     pr = workloads.gaussian_problem_1d("sep", n=500, N=12, length_scale=5.0, obs_stride=4, r2=0.5,
                                        half_width=8.0, Q=6, tol=1e-12, seed=10)
@@ -283,6 +305,8 @@ def test_config2_parity_fp64_and_fp32(B):
         em = float(np.linalg.norm(mu_a - mu_ref) / np.linalg.norm(mu_ref - mu0))
         assert st["status"] == 0, st
         assert st["n_systems"] == 1281
+        # the FP32 path on this 1-D network runs on the cluster-resident band kernel
+        assert st["solver_path"] == (1 if precision == 1 else 0)
         assert ea <= bound and em <= bound, (precision, ea, em)
 
 
