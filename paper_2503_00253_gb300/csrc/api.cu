@@ -128,8 +128,8 @@ void carve_problem(Carver& cv, ProblemDev& pr, const info_esrf_options& o) {
   pr.xo_val = cv.take<void>((size_t)pr.max_xo * n * esz);
   pr.xo_col = cv.take<int32_t>((size_t)pr.max_xo * n * 4);
   pr.xo_nnz = cv.take<int32_t>(n * 4);
-  pr.Om = cv.take<double>((size_t)d * l * 8);
-  pr.Yb = cv.take<double>((size_t)d * l * 8);
+  pr.Om = cv.take<void>((size_t)d * l * esz);
+  pr.Yb = cv.take<void>((size_t)d * l * esz);
   pr.Gm = cv.take<double>((size_t)l * l * 8);
   pr.Rm = cv.take<double>((size_t)l * l * 8);
   pr.ev = cv.take<double>((size_t)l * 8);

@@ -36,52 +36,45 @@ __global__ void k_accumulate(const ProblemDev* tab) {
   reinterpret_cast<T*>(pr.VbarT)[a * N1 + m] = to_t<T>(v);
 }
 
-// One thread per state point, members in chunks of 32 accumulators.
+// One thread per (member or mean column, state point), state points fastest
+// so that band loads and output stores are coalesced.
 template <typename T>
 __global__ void k_state_apply(const ProblemDev* tab) {
-  const ProblemDev& pr = tab[blockIdx.y];
+  const ProblemDev& pr = tab[blockIdx.z];
   const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= pr.n) return;
+  const int64_t m = blockIdx.y;                 // column: member m < N, or the mean (m == N)
   const int64_t n = pr.n, N = pr.N, N1 = N + 1;
-  const T* val = reinterpret_cast<const T*>(pr.xo_val);
-  const T* Vb = reinterpret_cast<const T*>(pr.VbarT);
+  if (x >= n || m > N) return;
+  if (m < N && !pr.do_pert) return;
+  if (m == N && !pr.do_mean) return;
+  const T* __restrict__ val = reinterpret_cast<const T*>(pr.xo_val);
+  const int32_t* __restrict__ col = pr.xo_col;
+  const T* __restrict__ Vb = reinterpret_cast<const T*>(pr.VbarT);
   const int nnz = pr.xo_nnz[x];
-  const double mu = pr.mu[x];
-  for (int64_t c0 = 0; c0 < N1; c0 += 32) {
-    const bool need = (c0 < N && pr.do_pert) || (c0 + 32 > N && pr.do_mean);
-    if (!need) continue;
-    T acc[32];
-#pragma unroll
-    for (int i = 0; i < 32; ++i) acc[i] = T(0);
-    for (int e = 0; e < nnz; ++e) {
-      const T v = val[(int64_t)e * n + x];
-      const int64_t b = pr.xo_col[(int64_t)e * n + x];
-      const T* row = Vb + b * N1 + c0;
-#pragma unroll
-      for (int i = 0; i < 32; ++i)
-        if (c0 + i < N1) acc[i] += v * row[i];
-    }
-#pragma unroll
-    for (int i = 0; i < 32; ++i) {
-      const int64_t m = c0 + i;
-      if (m < N) {
-        if (pr.do_pert) pr.A_a[m * n + x] = (pr.X[m * n + x] - mu) - pr.sqrt_nm1 * (double)acc[i];
-      } else if (m == N) {
-        if (pr.do_mean) pr.mu_a[x] = mu + (double)acc[i];
-      }
-    }
+  T acc0 = T(0), acc1 = T(0);
+  int e = 0;
+#pragma unroll 4
+  for (; e + 1 < nnz; e += 2) {
+    acc0 += val[(int64_t)e * n + x] * Vb[(int64_t)col[(int64_t)e * n + x] * N1 + m];
+    acc1 += val[(int64_t)(e + 1) * n + x] * Vb[(int64_t)col[(int64_t)(e + 1) * n + x] * N1 + m];
   }
+  if (e < nnz) acc0 += val[(int64_t)e * n + x] * Vb[(int64_t)col[(int64_t)e * n + x] * N1 + m];
+  const double inc = (double)(acc0 + acc1);
+  const double mu = pr.mu[x];
+  if (m < N) pr.A_a[m * n + x] = (pr.X[m * n + x] - mu) - pr.sqrt_nm1 * inc;
+  else pr.mu_a[x] = mu + inc;
 }
 
 void launch_finish(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st) {
-  int64_t dn1 = 0, nmax = 0;
+  int64_t dn1 = 0, nmax = 0, Nmax = 0;
   for (int i = 0; i < tab.count; ++i) {
     const ProblemDev& p = tab.p[i];
     dn1 = p.d * (p.N + 1) > dn1 ? p.d * (p.N + 1) : dn1;
     nmax = p.n > nmax ? p.n : nmax;
+    Nmax = p.N > Nmax ? p.N : Nmax;
   }
   const dim3 ga((unsigned)((dn1 + 255) / 256), tab.count);
-  const dim3 gs((unsigned)((nmax + 127) / 128), tab.count);
+  const dim3 gs((unsigned)((nmax + 127) / 128), (unsigned)(Nmax + 1), tab.count);
   if (tab.p[0].precision == 0) {
     k_accumulate<double><<<ga, 256, 0, st>>>(dtab); note_launches(1);
     k_state_apply<double><<<gs, 128, 0, st>>>(dtab); note_launches(1);

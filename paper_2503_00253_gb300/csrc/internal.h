@@ -69,8 +69,8 @@ struct ProblemDev {
   int32_t* xo_col;      // [max_xo][n]
   int32_t* xo_nnz;      // [n]
   // randomized eigensolver
-  double* Om;           // [d][l] test matrix / range basis (in place)
-  double* Yb;           // [d][l]
+  void* Om;             // [d][l] T test matrix / range basis
+  void* Yb;             // [d][l] T image of the basis under C
   double* Gm;           // [l][l] Gram / projected matrix
   double* Rm;           // [l][l] Cholesky factor / eigenvectors
   double* ev;           // [l] eigenvalues (descending)

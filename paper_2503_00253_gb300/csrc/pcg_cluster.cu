@@ -48,6 +48,7 @@ constexpr int kNW = kThreads / 32;
 constexpr int kK = 12;          // Ritz vectors handled by this kernel
 constexpr int kNR = 2 + 2 * kK; // residual reduction values per lane: rr (hi, lo), f[k], g[k]
 constexpr int kMaxTiles = 128;  // rows per CTA <= 2048
+constexpr int kMaxCS = 8;       // CTAs per cluster
 
 enum : int { kEmpty = 0, kStart = 1, kActive = 2 };
 
@@ -62,6 +63,7 @@ struct LaneState {
 struct Setup {
   int hl, hr, bad, tilesz;
   int xchg[4];
+  int npush;       // halo rows this CTA pushes to the cluster
 };
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
@@ -84,8 +86,9 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
   __shared__ int s_klo[kMaxTiles], s_w[kMaxTiles], s_off[kMaxTiles];
   __shared__ float s_gram[3][kK * kK];
   __shared__ float s_theta[kK];
-  __shared__ float s_pap[kJ][2];                 // CTA partial of p^T y (float-float), read remotely
-  __shared__ float s_res[kJ][kNR];               // CTA partials of rr, f, g, read remotely
+  // partial sums pushed by every CTA of the cluster into every CTA (slot = source rank)
+  __shared__ float s_pap_in[kMaxCS][kJ][2];      // p^T y (float-float)
+  __shared__ float s_res_in[kMaxCS][kJ][kNR];    // rr (float-float), Phi^T r, A^T r
   __shared__ float s_wpap[kNW][kJ][2];
   __shared__ int s_lo_min, s_hi_max, s_bad;
 
@@ -164,7 +167,36 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
     bad |= rs->xchg[2];
     tilesz = max(tilesz, rs->xchg[3]);
   }
-  // shared-memory carve (floats): tiles | p window | r | x | y | Phi^T | A^T
+  // halo rows of every CTA that this CTA owns: (own row, destination, window row)
+  auto nrows_of = [&](int c2) {
+    const int64_t s02 = (int64_t)c2 * R_s;
+    return (int)(d - s02 < 0 ? 0 : (d - s02 < R_s ? d - s02 : R_s));
+  };
+  auto for_each_push = [&](auto&& f) {     // enumerates targets, thread-strided
+    const int per = hl + R_s + hr;           // window rows per CTA (own rows skipped)
+    for (int e = tid; e < CS * per; e += blockDim.x) {
+      const int c2 = e / per, wrow = e % per;  // wrow = rel2 + hl
+      const int rel2 = wrow - hl;
+      const int nr2 = nrows_of(c2);
+      if (rel2 >= 0 && rel2 < nr2) continue;   // own row of c2, not a halo row
+      int64_t g = ((int64_t)c2 * R_s + rel2) % d;
+      if (g < 0) g += d;
+      const int owner = (int)(g / R_s);
+      if (owner != crank) continue;
+      f((int)(g - s0), c2, wrow);
+    }
+  };
+  if (tid == 0) S.npush = 0;
+  __syncthreads();
+  {
+    int cnt = 0;
+    for_each_push([&](int, int, int) { ++cnt; });
+    if (cnt) atomicAdd(&S.npush, cnt);
+  }
+  cluster.sync();
+  int npush_max = 0;
+  for (int c = 0; c < CS; ++c) npush_max = max(npush_max, cluster.map_shared_rank(&S, c)->npush);
+  // shared-memory carve (floats): tiles | p window | r | x | y | Phi^T | A^T | push table
   const int W_p = R_s + hl + hr;
   const int o_pw = (tilesz + 3) & ~3;
   const int o_r = o_pw + W_p * kLD;
@@ -172,7 +204,8 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
   const int o_y = o_x + R_s * kLD;
   const int o_ph = o_y + R_s * kLD;
   const int o_at = o_ph + k * R_s;
-  const int need = o_at + k * R_s;
+  const int o_push = (o_at + k * R_s + 1) & ~1;
+  const int need = o_push + 2 * npush_max;
   if (need > dyn_floats - 2 * R_s) bad = 1;      // keep the per-row windows intact while tiles fill
   cluster.sync();                                   // remote reads of S done before anyone exits
   if (bad) {
@@ -187,6 +220,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
   float* vy = dyn + o_y;
   float* phT = dyn + o_ph;
   float* aT = dyn + o_at;
+  int2* push = reinterpret_cast<int2*>(dyn + o_push);
   const float* val = reinterpret_cast<const float*>(pr.oo_val);
   const float* Phi = reinterpret_cast<const float*>(pr.Phi);
   const float* CPhi = reinterpret_cast<const float*>(pr.CPhi);
@@ -216,6 +250,13 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
     s_gram[w3][e] = (float)pr.gram[w3 * pk * pk + ii * pk + jj];
   }
   for (int m = tid; m < k; m += blockDim.x) s_theta[m] = (float)pr.theta[m];
+  __shared__ int s_npush;
+  if (tid == 0) s_npush = 0;
+  __syncthreads();
+  for_each_push([&](int row, int c2, int wrow) {
+    const int slot = atomicAdd(&s_npush, 1);
+    push[slot] = make_int2(row | (c2 << 16), wrow);
+  });
   const double cmin = pr.scal[1];
   const int maxit = pr.fixed_iters > 0 ? pr.fixed_iters : pr.max_iter;
   const double tol2 = pr.tol * pr.tol;
@@ -238,53 +279,34 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
     L.beta[j] = 0.f;
     L.rho[j] = 0.0;
   };
-  auto lane_vectors = [&](int j) {     // own rows of r and x for a (re)started lane
-    const int sid = L.sid[j];
-    const bool mean = sid >= 0 && sid < pr.mean_sys;
-    const int64_t i = sid >= 0 && !mean ? (sid - pr.mean_sys) % N : 0;
-    for (int row = tid; row < R_s; row += blockDim.x) {
+  auto lane_vectors_all = [&]() {      // own rows of r and x for every lane in state kStart
+    for (int e = tid; e < R_s * kJ; e += blockDim.x) {
+      const int row = e / kJ, j = e % kJ;
+      if (L.state[j] != kStart) continue;
+      const int sid = L.sid[j];
+      const bool mean = sid < pr.mean_sys;
       float b = 0.f;
-      if (sid >= 0 && row < nrows) {
+      if (row < nrows) {
         const int64_t a = s0 + row;
-        b = mean ? (float)pr.bmean[a] : W[a * N + i] * (float)pr.rinv[a];
+        b = mean ? (float)pr.bmean[a] : W[a * N + (sid - pr.mean_sys) % N] * (float)pr.rinv[a];
       }
       vr[row * kLD + j] = b;
       vx[row * kLD + j] = 0.f;
     }
   };
-
-  // first lanes
-  if (crank == 0 && tid == 0) {
-    const int base = atomicAdd(queue, kJ);
-    for (int j = 0; j < kJ; ++j) L.newsid[j] = base + j < pr.nsys ? base + j : -1;
+  // first lanes: rank 0 takes kJ systems and pushes their ids to every CTA
+  if (crank == 0 && warp == 0) {
+    int base = 0;
+    if (lane == 0) base = atomicAdd(queue, kJ);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    const int v = base + lane < pr.nsys ? base + lane : -1;
+    for (int dst = 0; dst < CS; ++dst) cluster.map_shared_rank(&L.newsid[0], dst)[lane] = v;
   }
   cluster.sync();
-  if (tid < kJ) {
-    const LaneState* l0 = cluster.map_shared_rank(&L, 0);
-    lane_scalars(tid, l0->newsid[tid]);
-  }
+  if (tid < kJ) lane_scalars(tid, L.newsid[tid]);
   __syncthreads();
-  for (int j = 0; j < kJ; ++j)
-    if (L.sid[j] >= 0) lane_vectors(j);
-  cluster.sync();   // every CTA has seen rank 0's first ids before rank 0 may reuse newsid
-
-  // halo rows: rel in [-hl, 0) and [nrows, R_s + hr) (a short last slice has
-  // no rows of its own in [nrows, R_s); those columns wrap to the first CTAs)
-  auto halo_copy = [&]() {
-    const int nh = hl + (R_s + hr - nrows);
-    for (int i = tid; i < nh * (kJ / 4); i += blockDim.x) {
-      const int hrow = i / (kJ / 4), q4 = i % (kJ / 4);
-      const int rel = hrow < hl ? hrow - hl : nrows + (hrow - hl);
-      int64_t gr = (s0 + rel) % d;
-      if (gr < 0) gr += d;
-      const int owner = (int)(gr / R_s);
-      const int lrow = (int)(gr - (int64_t)owner * R_s);
-      const float* src = cluster.map_shared_rank(pw, owner) + (lrow + hl) * kLD + 4 * q4;
-      st4(pw + (rel + hl) * kLD + 4 * q4, ld4(src));
-    }
-  };
-  halo_copy();
-  __syncthreads();
+  lane_vectors_all();
+  cluster.sync();   // all CTAs initialized before anyone pushes into their windows
 
   for (;;) {
     // ---------------- A: y = sigma p + C p on the own rows, partial p^T y ----------------
@@ -347,21 +369,20 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       }
     }
     __syncthreads();
-    if (tid < kJ) {
+    if (tid < kJ * CS) {
+      const int j = tid % kJ, dst = tid / kJ;
       float hi = 0.f, lo = 0.f;
-      for (int w = 0; w < kNW; ++w) ff_merge(hi, lo, s_wpap[w][tid][0], s_wpap[w][tid][1]);
-      s_pap[tid][0] = hi;
-      s_pap[tid][1] = lo;
+      for (int w = 0; w < kNW; ++w) ff_merge(hi, lo, s_wpap[w][j][0], s_wpap[w][j][1]);
+      float* rp = cluster.map_shared_rank(&s_pap_in[crank][j][0], dst);
+      rp[0] = hi;
+      rp[1] = lo;
     }
     cluster.sync();   // (1)
     // ---------------- alpha ----------------
     if (tid < kJ) {
       const int j = tid;
       float hi = 0.f, lo = 0.f;
-      for (int c = 0; c < CS; ++c) {
-        const float* rp = cluster.map_shared_rank(&s_pap[0][0], c) + 2 * j;
-        ff_merge(hi, lo, rp[0], rp[1]);
-      }
+      for (int c = 0; c < CS; ++c) ff_merge(hi, lo, s_pap_in[c][j][0], s_pap_in[c][j][1]);
       const double pAp = (double)hi + (double)lo;
       float alpha = 0.f;
       if (L.state[j] == kActive) {
@@ -418,12 +439,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       const float s1v = warp_reduce_scatter32<float>(v[1], lane);
       const float s2v = warp_reduce_scatter32<float>(v[2], lane);
       const float sv[3] = {s0v, s1v, s2v};
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        const int idx = 32 * b + lane;          // = jj * 24 + (m or 12 + m)
-        const int jj = idx / (2 * kK), w = idx % (2 * kK);
-        s_res[j0 + jj][2 + w] = sv[b];
-      }
+      float rhi[4], rlo[4];
 #pragma unroll
       for (int jj = 0; jj < 4; ++jj) {
         float hi = rr[jj].hi, lo = rr[jj].lo;
@@ -433,25 +449,37 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
           const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
           ff_merge(hi, lo, h2, l2);
         }
-        if (lane == 0) { s_res[j0 + jj][0] = hi; s_res[j0 + jj][1] = lo; }
+        rhi[jj] = hi;
+        rlo[jj] = lo;
+      }
+      // push this warp's four lanes to every CTA of the cluster
+      for (int dst = 0; dst < CS; ++dst) {
+        float* base = cluster.map_shared_rank(&s_res_in[crank][0][0], dst);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          const int idx = 32 * b + lane;          // = jj * 24 + (m or 12 + m)
+          const int jj = idx / (2 * kK), w = idx % (2 * kK);
+          base[(j0 + jj) * kNR + 2 + w] = sv[b];
+        }
+        if (lane < 4) {
+          base[(j0 + lane) * kNR] = lane == 0 ? rhi[0] : lane == 1 ? rhi[1] : lane == 2 ? rhi[2] : rhi[3];
+          base[(j0 + lane) * kNR + 1] = lane == 0 ? rlo[0] : lane == 1 ? rlo[1] : lane == 2 ? rlo[2] : rlo[3];
+        }
       }
     }
     cluster.sync();   // (2)
     // ---------------- decisions ----------------
-    // sums over the cluster, in rank order
+    // sums over the cluster, in rank order, from the local receive buffers
     for (int e = tid; e < kJ * (2 * kK); e += blockDim.x) {
       const int j = e / (2 * kK), w = e % (2 * kK);
       if ((w % kK) >= k) continue;
-      float s = 0.f;
-      for (int c = 0; c < CS; ++c) s += cluster.map_shared_rank(&s_res[0][0], c)[j * kNR + 2 + w];
-      if (w < kK) L.f[j][w] = s; else L.g[j][w - kK] = s;
+      float sacc = 0.f;
+      for (int c = 0; c < CS; ++c) sacc += s_res_in[c][j][2 + w];
+      if (w < kK) L.f[j][w] = sacc; else L.g[j][w - kK] = sacc;
     }
     if (tid < kJ) {
       float hi = 0.f, lo = 0.f;
-      for (int c = 0; c < CS; ++c) {
-        const float* rp = cluster.map_shared_rank(&s_res[0][0], c) + tid * kNR;
-        ff_merge(hi, lo, rp[0], rp[1]);
-      }
+      for (int c = 0; c < CS; ++c) ff_merge(hi, lo, s_res_in[c][tid][0], s_res_in[c][tid][1]);
       L.rr[tid] = (double)hi + (double)lo;
     }
     __syncthreads();
@@ -504,22 +532,23 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
     }
     __syncthreads();
     // finished lanes: stats, and rank 0 takes the next systems off the queue
-    if (crank == 0 && tid == 0) {
-      int nfin = 0;
-      for (int j = 0; j < kJ; ++j) nfin += L.fin[j] != 0;
-      const int base = nfin ? atomicAdd(queue, nfin) : 0;
-      int used = 0;
-      for (int j = 0; j < kJ; ++j) {
-        if (!L.fin[j]) continue;
+    if (crank == 0 && warp == 0) {
+      const int j = lane;
+      const bool f = L.fin[j] != 0;
+      const unsigned fm = __ballot_sync(0xffffffffu, f);
+      int base = 0;
+      if (lane == 0 && fm) base = atomicAdd(queue, __popc(fm));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (f) {
         const int sid = L.sid[j];
         const double bn = L.bn2[j];
-        const double rel = bn > 0.0 ? sqrt(L.rr[j] / bn) : 0.0;
         pr.iters[sid] = L.it[j];
-        pr.relres[sid] = rel;
+        pr.relres[sid] = bn > 0.0 ? sqrt(L.rr[j] / bn) : 0.0;
         if (L.fin[j] == 2) atomicOr(&pr.status[0], kStatBreakdown);
         else if (pr.fixed_iters <= 0 && !(L.rr[j] <= tol2 * bn)) atomicOr(&pr.status[0], kStatNotConverged);
-        const int nid = base + used++;
-        L.newsid[j] = nid < pr.nsys ? nid : -1;
+        const int nid = base + __popc(fm & ((1u << j) - 1u));
+        const int v = nid < pr.nsys ? nid : -1;
+        for (int dst = 0; dst < CS; ++dst) cluster.map_shared_rank(&L.newsid[0], dst)[j] = v;
       }
     }
     // ---------------- z = P^-1 r, p = z + beta p; finished lanes hand in x ----------------
@@ -565,19 +594,25 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
           if (fin[jj]) U[(int64_t)L.sid[j0 + jj] * d + s0 + row] = vx[row * kLD + j0 + jj];
       }
     }
+    __syncthreads();
+    // push the own rows that other windows hold as halo rows
+    {
+      const int np = s_npush;
+      for (int e = tid; e < np * (kJ / 4); e += blockDim.x) {
+        const int2 t = push[e / (kJ / 4)];
+        const int q4 = e % (kJ / 4);
+        const int row = t.x & 0xffff, c2 = t.x >> 16;
+        st4(cluster.map_shared_rank(pw, c2) + t.y * kLD + 4 * q4, ld4(pw + (row + hl) * kLD + 4 * q4));
+      }
+    }
     cluster.sync();   // (3)
     // ---------------- refills, exit test, halo ----------------
-    if (tid < kJ && L.fin[tid]) {
-      const LaneState* l0 = cluster.map_shared_rank(&L, 0);
-      lane_scalars(tid, l0->newsid[tid]);
-    }
+    if (tid < kJ && L.fin[tid]) lane_scalars(tid, L.newsid[tid]);
     __syncthreads();
     int live = 0;
     for (int j = 0; j < kJ; ++j) live |= L.state[j] != kEmpty;
-    for (int j = 0; j < kJ; ++j)      // lanes started in this step: own rows of r and x
-      if (L.state[j] == kStart) lane_vectors(j);
     if (!live) break;
-    halo_copy();
+    lane_vectors_all();   // lanes started in this step: own rows of r and x
     __syncthreads();
   }
   cluster.sync();   // no CTA leaves while another may still read its shared memory
@@ -601,9 +636,8 @@ int launch_pcg_band1d(const ProblemTable& tab, const ProblemDev* dtab, int32_t* 
   // kernel itself checks the band reach and the shared-memory budget
   int CS = 8;
   while (CS > 1 && (p.d + CS - 1) / CS < 2 * kTile) CS >>= 1;
-  const int clusters_max = num_sms / CS;
   int clusters = (p.nsys + kJ - 1) / kJ;
-  if (clusters > clusters_max) clusters = clusters_max;
+  if (clusters > num_sms / CS) clusters = num_sms / CS;
   if (clusters < 1) clusters = 1;
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
@@ -630,11 +664,17 @@ int launch_pcg_band1d(const ProblemTable& tab, const ProblemDev* dtab, int32_t* 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  // A cluster shape this GPU cannot co-schedule is left to the general kernel.
+  // A cluster shape this GPU cannot co-schedule is left to the general kernel;
+  // launch no more clusters than can run at once (later ones would only find
+  // the queue drained).
   int max_clusters = 0;
   if (cudaOccupancyMaxActiveClusters(&max_clusters, k_pcg_band1d, &cfg) != cudaSuccess || max_clusters < 1) {
     cudaGetLastError();
     return -1;
+  }
+  if (clusters > max_clusters) {
+    clusters = max_clusters;
+    cfg.gridDim = dim3(clusters * CS, 1, 1);
   }
   const cudaError_t err = cudaLaunchKernelEx(&cfg, k_pcg_band1d, dtab, queue, fallback, dyn_bytes / 4);
   if (err != cudaSuccess) {

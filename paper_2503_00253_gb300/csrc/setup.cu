@@ -382,271 +382,281 @@ void launch_philox(uint64_t seed, int64_t count, double* out, cudaStream_t st) {
 
 // ---------------------------------------------------------------------------
 // a4: randomized Ritz pairs of C (App. E; Halko, Martinsson, Tropp Alg. 5.3
-// on a range basis from Alg. 4.3 with power_iters power iterations).
-// Vectors here are FP64 [d][l]; the band is read in its stored type.
+// on a range basis from their Alg. 4.3 with power_iters power iterations).
+//
+// Two [d][l] buffers of the bulk type T (Om and Yb) hold the basis and its
+// image under C; `src` selects which one a kernel reads.  Gram matrices are
+// summed with DotAcc<T> and kept in FP64.  Orthonormalization is CholeskyQR2
+// (each pass: G = X^T X, G = R^T R, X <- X R^-1, the Cholesky factor formed
+// redundantly by every row block).  The l x l eigenproblem uses cyclic
+// Jacobi with one thread per matrix entry and l/2 disjoint rotations per
+// round (round-robin ordering), in the bulk precision.
 // ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T* ritz_buf(const ProblemDev& pr, int which) {
+  return reinterpret_cast<T*>(which == 0 ? pr.Om : pr.Yb);
+}
+
+template <typename T>
 __global__ void k_ritz_omega(const ProblemDev* tab) {
   const ProblemDev& pr = tab[blockIdx.y];
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (pr.l <= 0 || i >= pr.d * pr.l) return;
   const int64_t a = i / pr.l, j = i % pr.l;
-  pr.Om[i] = philox_normal(pr.seed, (uint64_t)(j * pr.d + a));
+  ritz_buf<T>(pr, 0)[i] = to_t<T>(philox_normal(pr.seed, (uint64_t)(j * pr.d + a)));
 }
 
-// Y[a][j] = sum_b C(a, b) V[b][j], one thread per (a, j).
+// dst = C src, one thread per (row, column); the band loop is unrolled so that
+// several entries are in flight.
 template <typename T>
-__global__ void k_ritz_matvec(const ProblemDev* tab, int from_om) {
+__global__ void k_ritz_matvec(const ProblemDev* tab, int src) {
   const ProblemDev& pr = tab[blockIdx.y];
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (pr.l <= 0 || i >= pr.d * pr.l) return;
-  const int64_t a = i / pr.l, j = i % pr.l, d = pr.d, l = pr.l;
-  const double* V = from_om ? pr.Om : pr.Yb;
-  double* Y = from_om ? pr.Yb : pr.Om;
-  const T* val = tp<const T>(pr.oo_val);
-  double acc = 0.0;
+  const int l = pr.l;
+  if (l <= 0 || i >= pr.d * l) return;
+  const int64_t d = pr.d, a = i / l, j = i % l;
+  const T* __restrict__ V = ritz_buf<T>(pr, src);
+  T* Y = ritz_buf<T>(pr, 1 - src);
+  const T* __restrict__ val = tp<const T>(pr.oo_val);
+  const int32_t* __restrict__ col = pr.oo_col;
+  T acc0 = T(0), acc1 = T(0);
   const int nnz = pr.oo_nnz[a];
-  for (int e = 0; e < nnz; ++e) acc += (double)val[e * d + a] * V[(int64_t)pr.oo_col[e * d + a] * l + j];
-  Y[a * l + j] = acc;
+  int e = 0;
+#pragma unroll 4
+  for (; e + 1 < nnz; e += 2) {
+    acc0 += val[(int64_t)e * d + a] * V[(int64_t)col[(int64_t)e * d + a] * l + j];
+    acc1 += val[(int64_t)(e + 1) * d + a] * V[(int64_t)col[(int64_t)(e + 1) * d + a] * l + j];
+  }
+  if (e < nnz) acc0 += val[(int64_t)e * d + a] * V[(int64_t)col[(int64_t)e * d + a] * l + j];
+  Y[a * l + j] = acc0 + acc1;
 }
 
-// G = A^T B for [d][l] FP64 matrices, one block per (i, j) with j >= i.
-__global__ void k_ritz_gram(const ProblemDev* tab, int which) {
+// G[i][j] = sum_a A[a][i] B[a][j] (FP64 result), one block per entry.
+// sym: A = B = buf(src) and only j >= i is computed (mirrored).
+template <typename T>
+__global__ void k_ritz_gram(const ProblemDev* tab, int srcA, int srcB, int sym) {
   const ProblemDev& pr = tab[blockIdx.y];
   const int l = pr.l;
   const int pair = blockIdx.x;
   if (l <= 0 || pair >= l * l) return;
   const int i = pair / l, j = pair % l;
-  if (j < i) return;
-  // which: 0 -> G = Y^T Y (Y = Yb); 1 -> G = Om^T Yb
-  const double* A = which == 0 ? pr.Yb : pr.Om;
-  const double* B = pr.Yb;
-  double acc = 0.0;
-  for (int64_t a = threadIdx.x; a < pr.d; a += blockDim.x) acc += A[a * l + i] * B[a * l + j];
-  __shared__ double red[32];
-  acc = warp_sum(acc);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-  __syncthreads();
+  if (sym && j < i) return;
+  const T* A = ritz_buf<T>(pr, srcA);
+  const T* Bm = ritz_buf<T>(pr, srcB);
+  DotAcc<T> acc;
+  for (int64_t a = threadIdx.x; a < pr.d; a += blockDim.x) acc.add_prod(A[a * l + i], Bm[a * l + j]);
+  DotAcc<T> accs[1] = {acc};
+  double out[1];
+  __shared__ double scratch[2 * kThreads / 32];
+  block_sum<1>(accs, out, scratch);
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    if (which == 1) {
-      // symmetric part of Om^T C Om: (i,j) and (j,i) accumulate separately below
-      pr.Gm[i * l + j] = s;
-    } else {
-      pr.Gm[i * l + j] = s;
-      pr.Gm[j * l + i] = s;
-    }
+    pr.Gm[i * l + j] = out[0];
+    if (sym) pr.Gm[j * l + i] = out[0];
   }
 }
 
-// Lower-triangular entries (i > j) of Om^T Yb for symmetrization.
-__global__ void k_ritz_gram_lower(const ProblemDev* tab) {
+// X_dst = X_src R^-1 with G = R^T R the Cholesky factorization of the Gram
+// matrix in Gm (formed redundantly per block by warp 0, lanes over columns).
+// A non-positive pivot zeroes that column (rank loss) and flags kStatEigFail.
+template <typename T>
+__global__ void k_ritz_orth(const ProblemDev* tab, int src) {
   const ProblemDev& pr = tab[blockIdx.y];
   const int l = pr.l;
-  const int pair = blockIdx.x;
-  if (l <= 0 || pair >= l * l) return;
-  const int i = pair / l, j = pair % l;
-  if (j >= i) return;
-  double acc = 0.0;
-  for (int64_t a = threadIdx.x; a < pr.d; a += blockDim.x) acc += pr.Om[a * l + i] * pr.Yb[a * l + j];
-  __shared__ double red[32];
-  acc = warp_sum(acc);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  if (l <= 0) return;
+  __shared__ double Rs[kMaxRitz][kMaxRitz + 1];
+  __shared__ double Gs[kMaxRitz][kMaxRitz + 1];
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+    Gs[e / l][e % l] = pr.Gm[e];
+    Rs[e / l][e % l] = 0.0;
+  }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    pr.Rm[i * l + j] = s;   // stash; combined in the eigensolver
-  }
-}
-
-// Cholesky G = R^T R (upper R) in one thread; a non-positive pivot zeroes the
-// column (rank loss) and flags kStatEigFail.
-__global__ void k_ritz_cholesky(const ProblemDev* tab) {
-  const ProblemDev& pr = tab[blockIdx.x];
-  const int l = pr.l;
-  if (threadIdx.x != 0 || l <= 0) return;
-  double* G = pr.Gm;
-  double* Rr = pr.Rm;
-  for (int i = 0; i < l * l; ++i) Rr[i] = 0.0;
-  double tr = 0.0;
-  for (int i = 0; i < l; ++i) tr += G[i * l + i];
-  const double tiny = 1e-28 * (tr > 0 ? tr : 1.0);
-  for (int j = 0; j < l; ++j) {
-    double s = G[j * l + j];
-    for (int k = 0; k < j; ++k) s -= Rr[k * l + j] * Rr[k * l + j];
-    if (!(s > tiny)) {
-      for (int c = j; c < l; ++c) Rr[j * l + c] = 0.0;
-      atomicOr(&pr.status[0], kStatEigFail);
-      continue;
-    }
-    const double rjj = sqrt(s);
-    Rr[j * l + j] = rjj;
-    for (int c = j + 1; c < l; ++c) {
-      double t = G[j * l + c];
-      for (int k = 0; k < j; ++k) t -= Rr[k * l + j] * Rr[k * l + c];
-      Rr[j * l + c] = t / rjj;
+  if (threadIdx.x < 32) {
+    const int c = threadIdx.x;
+    double tr = 0.0;
+    for (int i = 0; i < l; ++i) tr += Gs[i][i];
+    const double tiny = 1e-28 * (tr > 0 ? tr : 1.0);
+    for (int j = 0; j < l; ++j) {
+      // pivot (all lanes compute it redundantly from shared values)
+      double sjj = Gs[j][j];
+      for (int k = 0; k < j; ++k) sjj -= Rs[k][j] * Rs[k][j];
+      const bool ok = sjj > tiny;
+      const double rjj = ok ? sqrt(sjj) : 0.0;
+      if (c > j && c < l) {
+        double t = Gs[j][c];
+        for (int k = 0; k < j; ++k) t -= Rs[k][j] * Rs[k][c];
+        Rs[j][c] = ok ? t / rjj : 0.0;
+      }
+      if (c == j) Rs[j][j] = rjj;
+      if (!ok && c == 0 && blockIdx.x == 0) atomicOr(&pr.status[0], kStatEigFail);
+      __syncwarp();
     }
   }
-}
-
-// Om[a][:] = Yb[a][:] R^-1 (row-wise forward substitution); zero pivots give zero columns.
-__global__ void k_ritz_trsm(const ProblemDev* tab) {
-  const ProblemDev& pr = tab[blockIdx.y];
+  __syncthreads();
   const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int l = pr.l;
-  if (l <= 0 || a >= pr.d) return;
-  double row[kMaxRitz];
-  for (int j = 0; j < l; ++j) {
-    double t = pr.Yb[a * l + j];
-    for (int k = 0; k < j; ++k) t -= row[k] * pr.Rm[k * l + j];
-    const double rjj = pr.Rm[j * l + j];
-    row[j] = rjj > 0.0 ? t / rjj : 0.0;
+  if (a >= pr.d) return;
+  const T* X = ritz_buf<T>(pr, src);
+  T* Y = ritz_buf<T>(pr, 1 - src);
+  T row[kMaxRitz];
+#pragma unroll
+  for (int j = 0; j < kMaxRitz; ++j) {
+    if (j < l) {
+      T t = X[a * l + j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) t -= row[k] * to_t<T>(Rs[k][j]);
+      row[j] = Rs[j][j] > 0.0 ? t / to_t<T>(Rs[j][j]) : T(0);
+    } else {
+      row[j] = T(0);
+    }
   }
-  for (int j = 0; j < l; ++j) pr.Om[a * l + j] = row[j];
+#pragma unroll
+  for (int j = 0; j < kMaxRitz; ++j)
+    if (j < l) Y[a * l + j] = row[j];
 }
 
-// Copies Om -> Yb (so that the next orthonormalization reads Yb).
-__global__ void k_ritz_copy(const ProblemDev* tab) {
-  const ProblemDev& pr = tab[blockIdx.y];
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (pr.l <= 0 || i >= pr.d * pr.l) return;
-  pr.Yb[i] = pr.Om[i];
-}
-
-// Symmetric Jacobi eigensolver for B = (Om^T C Om + its transpose) / 2 (l x l),
-// one block per problem, cyclic sweeps with l/2 disjoint rotations per round
-// (round-robin ordering).  Output: ev (descending), Rm = eigenvectors (columns).
+// Element-parallel cyclic Jacobi on B = sym(Om^T C Om) (Gm holds Om^T (C Om)),
+// one thread per entry.  Output: ev (descending) and Rm (eigenvectors).
+template <typename T>
 __global__ void k_ritz_jacobi(const ProblemDev* tab) {
   const ProblemDev& pr = tab[blockIdx.x];
   const int l = pr.l;
   if (l <= 0) return;
-  __shared__ double A[kMaxRitz][kMaxRitz + 1];
-  __shared__ double V[kMaxRitz][kMaxRitz + 1];
-  __shared__ double cs[kMaxRitz / 2 + 1][2];
-  __shared__ int pq[kMaxRitz / 2 + 1][2];
-  __shared__ int perm[kMaxRitz + 1];
-  __shared__ double off_s;
+  __shared__ T A[2][kMaxRitz][kMaxRitz + 1];
+  __shared__ T V[2][kMaxRitz][kMaxRitz + 1];
+  __shared__ T cs[kMaxRitz][2];        // (c, s) of the pair containing index i, per index
+  __shared__ int partner[kMaxRitz];
+  __shared__ int first[kMaxRitz];      // 1 if i is the lower index of its pair
+  __shared__ double off_s, tot_s;
   const int tid = threadIdx.x;
-  for (int i = tid; i < l * l; i += blockDim.x) {
-    const int r = i / l, c = i % l;
-    double v;
-    if (r == c) v = pr.Gm[r * l + c];
-    else if (r < c) v = 0.5 * (pr.Gm[r * l + c] + pr.Rm[c * l + r]);
-    else v = 0.5 * (pr.Gm[c * l + r] + pr.Rm[r * l + c]);
-    A[r][c] = v;
-    V[r][c] = (r == c) ? 1.0 : 0.0;
+  const int i = tid / kMaxRitz, j = tid % kMaxRitz;
+  const bool mine = i < l && j < l;
+  if (mine) {
+    const double b = 0.5 * (pr.Gm[i * l + j] + pr.Gm[j * l + i]);
+    A[0][i][j] = to_t<T>(b);
+    V[0][i][j] = i == j ? T(1) : T(0);
   }
-  const int m = (l + 1) & ~1;   // even count for round-robin, index l is a dummy
-  if (tid < m) perm[tid] = tid;
+  const int m = (l + 1) & ~1;   // even count; index l is a dummy when l is odd
+  int cur = 0;
   __syncthreads();
-  for (int sweep = 0; sweep < 30; ++sweep) {
-    if (tid == 0) {
-      double off = 0.0, tot = 0.0;
-      for (int r = 0; r < l; ++r)
-        for (int c = 0; c < l; ++c) {
-          const double v = A[r][c] * A[r][c];
-          tot += v;
-          if (r != c) off += v;
-        }
-      off_s = (off <= 1e-30 * tot) ? -1.0 : off;
+  __shared__ T red_off[kMaxRitz], red_tot[kMaxRitz];
+  const int max_sweeps = sizeof(T) == 4 ? 12 : 30;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    {
+      // off-diagonal and total squared norms: warp i holds row i
+      T v = mine ? A[cur][i][j] * A[cur][i][j] : T(0);
+      T o = (mine && i != j) ? v : T(0);
+#pragma unroll
+      for (int sh = 16; sh > 0; sh >>= 1) {
+        v += __shfl_xor_sync(0xffffffffu, v, sh);
+        o += __shfl_xor_sync(0xffffffffu, o, sh);
+      }
+      if ((tid & 31) == 0) { red_tot[i] = v; red_off[i] = o; }
+      __syncthreads();
+      if (tid == 0) {
+        double to = 0.0, of = 0.0;
+        for (int u = 0; u < l; ++u) { to += (double)red_tot[u]; of += (double)red_off[u]; }
+        off_s = of;
+        tot_s = to;
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    if (off_s < 0.0) break;
+    const double eps = sizeof(T) == 4 ? 1e-11 : 1e-30;
+    if (!(off_s > eps * tot_s)) break;
     for (int round = 0; round < m - 1; ++round) {
-      const int npairs = m / 2;
-      if (tid < npairs) {
-        int p = perm[tid], q = perm[m - 1 - tid];
-        if (p > q) { const int t = p; p = q; q = t; }
-        double c = 1.0, s = 0.0;
-        if (q < l && A[p][q] != 0.0) {
-          const double theta = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
-          const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-          c = 1.0 / sqrt(t * t + 1.0);
-          s = t * c;
+      // circle method: position 0 fixed, others rotate by `round`
+      if (tid < m) {
+        const int x = tid;
+        const int pos = x == 0 ? 0 : ((x - 1 - round) % (m - 1) + (m - 1)) % (m - 1) + 1;
+        const int ppos = m - 1 - pos;
+        const int y = ppos == 0 ? 0 : ((ppos - 1 + round) % (m - 1)) + 1;
+        if (x < l) {
+          partner[x] = y;
+          first[x] = x < y;
         }
-        pq[tid][0] = p;
-        pq[tid][1] = q;
-        cs[tid][0] = c;
-        cs[tid][1] = s;
       }
       __syncthreads();
-      // rows: A <- J^T A
-      for (int i = tid; i < npairs * l; i += blockDim.x) {
-        const int k = i / l, col = i % l;
-        const int p = pq[k][0], q = pq[k][1];
-        if (q >= l) continue;
-        const double c = cs[k][0], s = cs[k][1];
-        const double ap = A[p][col], aq = A[q][col];
-        A[p][col] = c * ap - s * aq;
-        A[q][col] = s * ap + c * aq;
+      if (tid < l) {
+        const int x = tid, y = partner[x];
+        if (x < y && y < l) {
+          T c = T(1), s = T(0);
+          const T apq = A[cur][x][y];
+          if (apq != T(0)) {
+            const T theta = (A[cur][y][y] - A[cur][x][x]) / (T(2) * apq);
+            const T t = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
+            c = T(1) / sqrt(t * t + T(1));
+            s = t * c;
+          }
+          cs[x][0] = c; cs[x][1] = s;
+          cs[y][0] = c; cs[y][1] = s;
+        } else if (y >= l) {
+          cs[x][0] = T(1); cs[x][1] = T(0);
+        }
       }
       __syncthreads();
-      // columns: A <- A J, V <- V J
-      for (int i = tid; i < npairs * l; i += blockDim.x) {
-        const int k = i / l, row = i % l;
-        const int p = pq[k][0], q = pq[k][1];
-        if (q >= l) continue;
-        const double c = cs[k][0], s = cs[k][1];
-        const double ap = A[row][p], aq = A[row][q];
-        A[row][p] = c * ap - s * aq;
-        A[row][q] = s * ap + c * aq;
-        const double vp = V[row][p], vq = V[row][q];
-        V[row][p] = c * vp - s * vq;
-        V[row][q] = s * vp + c * vq;
+      if (mine) {
+        // coefficients of row/column index u: new_u = al * X_p + be * X_q for its pair (p < q)
+        auto coef = [&](int u, int& p, int& q, T& al, T& be) {
+          const int v2 = partner[u];
+          if (v2 >= l) { p = u; q = u; al = T(1); be = T(0); return; }
+          const T c = cs[u][0], s = cs[u][1];
+          if (first[u]) { p = u; q = v2; al = c; be = -s; }
+          else { p = v2; q = u; al = s; be = c; }
+        };
+        int pi, qi, pj, qj;
+        T ai, bi, aj, bj;
+        coef(i, pi, qi, ai, bi);
+        coef(j, pj, qj, aj, bj);
+        const T(*Ac)[kMaxRitz + 1] = A[cur];
+        T nv;
+        if (pi == qi && pj == qj) nv = Ac[i][j];
+        else if (pi == qi) nv = aj * Ac[i][pj] + bj * Ac[i][qj];
+        else if (pj == qj) nv = ai * Ac[pi][j] + bi * Ac[qi][j];
+        else nv = ai * (aj * Ac[pi][pj] + bj * Ac[pi][qj]) + bi * (aj * Ac[qi][pj] + bj * Ac[qi][qj]);
+        A[1 - cur][i][j] = nv;
+        V[1 - cur][i][j] = pj == qj ? V[cur][i][j] : aj * V[cur][i][pj] + bj * V[cur][i][qj];
       }
       __syncthreads();
-      if (tid == 0) {   // round-robin rotation keeping perm[0] fixed
-        const int last = perm[m - 1];
-        for (int i = m - 1; i > 1; --i) perm[i] = perm[i - 1];
-        perm[1] = last;
-      }
-      __syncthreads();
+      cur = 1 - cur;
     }
   }
-  // sort eigenvalues descending (selection by one thread; l <= 32)
-  if (tid == 0) {
-    int order[kMaxRitz];
-    bool used[kMaxRitz];
-    for (int i = 0; i < l; ++i) used[i] = false;
-    for (int r = 0; r < l; ++r) {
-      int best = -1;
-      for (int i = 0; i < l; ++i)
-        if (!used[i] && (best < 0 || A[i][i] > A[best][best])) best = i;
-      used[best] = true;
-      order[r] = best;
+  // descending order: rank of each diagonal entry
+  if (tid < l) {
+    const T di = A[cur][tid][tid];
+    int rank = 0;
+    for (int u = 0; u < l; ++u) {
+      const T du = A[cur][u][u];
+      rank += (du > di) || (du == di && u < tid);
     }
-    for (int r = 0; r < l; ++r) {
-      pr.ev[r] = A[order[r]][order[r]];
-      for (int i = 0; i < l; ++i) pr.Rm[i * l + r] = V[i][order[r]];
-    }
+    pr.ev[rank] = (double)di;
+    for (int u = 0; u < l; ++u) pr.Rm[u * l + rank] = (double)V[cur][u][tid];
   }
 }
 
-// Phi = Om V_k, C Phi = Yb V_k (stored in T), theta = top k eigenvalues.
+// Phi = basis V_k, C Phi = image V_k (stored in T), theta = top k eigenvalues.
 template <typename T>
-__global__ void k_ritz_vectors(const ProblemDev* tab) {
+__global__ void k_ritz_vectors(const ProblemDev* tab, int basis) {
   const ProblemDev& pr = tab[blockIdx.y];
   const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int l = pr.l, k = pr.kR;
   if (k <= 0 || a >= pr.d) return;
+  const T* Qb = ritz_buf<T>(pr, basis);
+  const T* Pb = ritz_buf<T>(pr, 1 - basis);
   T* Phi = tp<T>(pr.Phi);
   T* CPhi = tp<T>(pr.CPhi);
   for (int j = 0; j < k; ++j) {
-    double ph = 0.0, cp = 0.0;
+    T ph = T(0), cp = T(0);
     for (int i = 0; i < l; ++i) {
-      const double v = pr.Rm[i * l + j];
-      ph += pr.Om[a * l + i] * v;
-      cp += pr.Yb[a * l + i] * v;
+      const T v = to_t<T>(pr.Rm[i * l + j]);
+      ph += Qb[a * l + i] * v;
+      cp += Pb[a * l + i] * v;
     }
-    Phi[a * k + j] = to_t<T>(ph);
-    CPhi[a * k + j] = to_t<T>(cp);
+    Phi[a * k + j] = ph;
+    CPhi[a * k + j] = cp;
   }
   if (a == 0)
     for (int j = 0; j < k; ++j) pr.theta[j] = pr.ev[j];
 }
 
-// Gram matrices of the stored (rounded) Phi and A = C Phi in FP64:
+// Gram matrices of the stored Phi and A = C Phi in FP64:
 // gram[0] = Phi^T Phi, gram[1] = A^T Phi, gram[2] = A^T A.  One block per entry.
 template <typename T>
 __global__ void k_ritz_grams(const ProblemDev* tab) {
@@ -659,20 +669,17 @@ __global__ void k_ritz_grams(const ProblemDev* tab) {
   const T* A = tp<const T>(pr.CPhi);
   const T* L = which == 0 ? Phi : A;
   const T* Rr = which == 2 ? A : Phi;
-  double acc = 0.0;
-  for (int64_t a = threadIdx.x; a < pr.d; a += blockDim.x) acc += (double)L[a * k + i] * (double)Rr[a * k + j];
-  __shared__ double red[32];
-  acc = warp_sum(acc);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    pr.gram[e] = s;
-  }
+  DotAcc<T> acc;
+  for (int64_t a = threadIdx.x; a < pr.d; a += blockDim.x) acc.add_prod(L[a * k + i], Rr[a * k + j]);
+  DotAcc<T> accs[1] = {acc};
+  double out[1];
+  __shared__ double scratch[2 * kThreads / 32];
+  block_sum<1>(accs, out, scratch);
+  if (threadIdx.x == 0) pr.gram[e] = out[0];
 }
 
-void launch_ritz(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st) {
+template <typename T>
+static void launch_ritz_t(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st) {
   int64_t dl = 0, dmax = 0;
   int lmax = 0, kmax = 0;
   for (int i = 0; i < tab.count; ++i) {
@@ -683,46 +690,42 @@ void launch_ritz(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t s
     kmax = p.kR > kmax ? p.kR : kmax;
   }
   if (lmax <= 0 || kmax <= 0) return;
-  const bool f64 = tab.p[0].precision == 0;
   const dim3 gdl((unsigned)((dl + 255) / 256), tab.count);
   const dim3 gd((unsigned)((dmax + 255) / 256), tab.count);
   const dim3 gll((unsigned)(lmax * lmax), tab.count);
-  auto matvec = [&](int from_om) {
-    if (f64) k_ritz_matvec<double><<<gdl, 256, 0, st>>>(dtab, from_om);
-    else k_ritz_matvec<float><<<gdl, 256, 0, st>>>(dtab, from_om);
+  int cur = 0;   // buffer holding the current basis candidate
+  auto matvec = [&]() {   // buf[1 - cur] = C buf[cur]
+    k_ritz_matvec<T><<<gdl, 256, 0, st>>>(dtab, cur);
     note_launches(1);
   };
-  auto orthonormalize = [&]() {   // Yb -> Om with CholeskyQR2
-    for (int pass = 0; pass < 2; ++pass) {
-      k_ritz_gram<<<gll, 256, 0, st>>>(dtab, 0); note_launches(1);
-      k_ritz_cholesky<<<tab.count, 32, 0, st>>>(dtab); note_launches(1);
-      k_ritz_trsm<<<gd, 256, 0, st>>>(dtab); note_launches(1);
-      if (pass == 0) {
-        k_ritz_copy<<<gdl, 256, 0, st>>>(dtab);
-        note_launches(1);
-      }
-    }
+  auto orth2 = [&](int x) {   // orthonormalize buf[x] in place (scratch: the other buffer)
+    k_ritz_gram<T><<<gll, 256, 0, st>>>(dtab, x, x, 1);
+    k_ritz_orth<T><<<gd, 256, 0, st>>>(dtab, x);          // buf[1-x] = buf[x] R^-1
+    k_ritz_gram<T><<<gll, 256, 0, st>>>(dtab, 1 - x, 1 - x, 1);
+    k_ritz_orth<T><<<gd, 256, 0, st>>>(dtab, 1 - x);      // buf[x] = buf[1-x] R^-1
+    note_launches(4);
   };
-  k_ritz_omega<<<gdl, 256, 0, st>>>(dtab); note_launches(1);
-  matvec(1);                                   // Yb = C Om
-  int power = tab.p[0].power_iters;
-  for (int it = 0; it < power; ++it) {
-    orthonormalize();                          // Om = orth(Yb)
-    matvec(1);                                 // Yb = C Om
-  }
-  orthonormalize();                            // Om = orth(Yb): range basis
-  matvec(1);                                   // Yb = C Om
-  k_ritz_gram<<<gll, 256, 0, st>>>(dtab, 1);   // Gm (upper) = Om^T Yb
+  k_ritz_omega<T><<<gdl, 256, 0, st>>>(dtab);               // buf0 = Omega
   note_launches(1);
-  k_ritz_gram_lower<<<gll, 256, 0, st>>>(dtab); note_launches(1);
-  k_ritz_jacobi<<<tab.count, 128, 0, st>>>(dtab); note_launches(1);
-  if (f64) {
-    k_ritz_vectors<double><<<gd, 256, 0, st>>>(dtab); note_launches(1);
-    k_ritz_grams<double><<<dim3(3 * kmax * kmax, tab.count), 256, 0, st>>>(dtab); note_launches(1);
-  } else {
-    k_ritz_vectors<float><<<gd, 256, 0, st>>>(dtab); note_launches(1);
-    k_ritz_grams<float><<<dim3(3 * kmax * kmax, tab.count), 256, 0, st>>>(dtab); note_launches(1);
+  matvec();                                                 // buf1 = C buf0
+  cur = 1;
+  for (int it = 0; it < tab.p[0].power_iters; ++it) {
+    orth2(cur);                                             // buf[cur] orthonormal
+    matvec();                                               // buf[1-cur] = C buf[cur]
+    cur = 1 - cur;
   }
+  orth2(cur);                                               // basis in buf[cur]
+  matvec();                                                 // image in buf[1-cur]
+  k_ritz_gram<T><<<gll, 256, 0, st>>>(dtab, cur, 1 - cur, 0);   // Gm = Q^T (C Q)
+  k_ritz_jacobi<T><<<tab.count, kMaxRitz * kMaxRitz, 0, st>>>(dtab);
+  k_ritz_vectors<T><<<gd, 256, 0, st>>>(dtab, cur);
+  k_ritz_grams<T><<<dim3(3 * kmax * kmax, tab.count), 256, 0, st>>>(dtab);
+  note_launches(4);
+}
+
+void launch_ritz(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st) {
+  if (tab.p[0].precision == 0) launch_ritz_t<double>(tab, dtab, st);
+  else launch_ritz_t<float>(tab, dtab, st);
 }
 
 }  // namespace infoesrf
