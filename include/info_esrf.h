@@ -85,15 +85,25 @@ typedef struct {
   int32_t max_iter;       /* PCG iteration cap; default 1000 */
   int32_t fixed_iters;    /* > 0: run exactly this many PCG iterations (paper's experiments) */
   int32_t rule;           /* INFO_ESRF_RULE_*; default elliptic */
-  int32_t learn_rank;     /* rank of the learned correction (<= 6 with k_R <= 12, else <= 8) */
+  int32_t reserved;       /* set to 0 */
   double ell;             /* spectrum bound of App. D; <= 0: power of ten above a Gershgorin bound of C */
   uint64_t seed;          /* Philox key of the randomized eigensolver's test matrix */
   int64_t max_neighbors;  /* band capacity per row; <= 0: bound from the geometry */
-  /* Learned diagonal-plus-low-rank correction, device arrays in FP32, or NULL:
-   * learn_diag [Q + 1][d] >= 0 and learn_U [Q + 1][d][learn_rank]; slot Q is
-   * the mean system.  The preconditioner becomes P_q^-1 + D_q + U_q U_q^T. */
-  const float* learn_diag;
-  const float* learn_U;
+  /* Learned preconditioner correction (not in the paper), or NULL: device
+   * array of info_esrf_learn_nparams() floats, the parameters of the network
+   * described in info_esrf_stages.h.  Each shifted system is then
+   * preconditioned by M_q = a_q P_q^-1 + S_q^T S_q (symmetric positive
+   * definite), a_q and the stencil S_q produced by the network from the
+   * shift and the spectrum statistics of C.  Used by the cluster-resident
+   * FP32 solver for 1-D networks; a system that breaks down or reaches
+   * max_iter with it is solved again with P_q^-1 alone.  Convergence is
+   * always tested on the unpreconditioned residual ||b - C_q u||. */
+  const float* learned_model;
+  double learned_max_shift;  /* > 0: the learned term is used only for shifts sigma = s_q + 1 <= this */
+  /* NULL, or a device int32 array receiving each system's PCG iteration
+   * count (single-problem calls): with the mean update, entry 0 is the mean
+   * system and 1 + q * N + i the perturbation systems; without it, q * N + i. */
+  int32_t* system_iters;
   /* NULL, or 5 cudaEvent_t handles (as void*) recorded on the call's stream
    * at the phase boundaries: start; after the setup of a1-a3 (anomalies, W,
    * bands, quadrature); after the Ritz pairs (a4); after the persistent PCG

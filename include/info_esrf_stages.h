@@ -89,6 +89,70 @@ int info_esrf_fma_probe(int32_t precision, int64_t iters, double* flops_per_s, d
 int info_esrf_prepared_band_capacity(const info_esrf_grid* grid, int64_t N, int64_t d, int32_t Q,
                                      const info_esrf_options* opt, int64_t* max_oo, int64_t* max_xo);
 
+/* ------------------------------------------------------------------------
+ * Learned preconditioner correction.  Not in the paper: the paper's
+ * preconditioner is the limited-memory one of App. E.  Each shifted system
+ * may instead use M_q = a_q P_q^-1 + S_q^T S_q (a_q > 0; S_q a circulant
+ * stencil over the observation index, (S r)_a = sum_{t=-h..h} w[t+h]
+ * r_{(a+t) mod d}, h = info_esrf_learn_halfwidth()), symmetric positive
+ * definite by construction.  a_q = exp(out_0) / sigma and w_q = out_1.. /
+ * sqrt(sigma) (relative to C_q^-1 ~ I / sigma), out from a network applied to
+ *   phi = (log(sigma)/5, (log(sigma)/5)^2, log(mean_a C(a,a))/5, log(b)/10),
+ * sigma = s_q + 1, b the Gershgorin bound of C:
+ *   h1 = tanh(W1 phi + b1), h2 = tanh(W2 h1 + b2), out = W3 h2 + b3,
+ * parameters packed as one float vector W1[32][4], b1[32], W2[32][32],
+ * b2[32], W3[18][32], b3[18] (info_esrf_learn_nparams() values).
+ * Training minimizes L = mean_s ||a_s z_s + S_s^T S_s y_s - v_s||^2 / ||v_s||^2
+ * over Krylov samples (v, y = C_q v, z = P_q^-1 y, phi) from
+ * info_esrf_krylov_capture.  Sample arrays are [S][d] float, phi [S][4].
+ * ------------------------------------------------------------------------ */
+int32_t info_esrf_learn_nparams(void);
+int32_t info_esrf_learn_halfwidth(void);
+
+/* coef[s] = (a_s, w_s[2h+1]) for nshift feature rows (inference). */
+int info_esrf_learn_coefficients(const float* theta_dev, int32_t nshift, const float* feat_dev, float* coef_dev,
+                                 void* stream);
+
+/* Scratch bytes for info_esrf_learn_loss_grad / _train with nsamp samples. */
+size_t info_esrf_learn_scratch_size(int32_t nsamp);
+
+/* grad = dL/dtheta and *loss_dev = L (device double, may be NULL), by the
+ * hand-written forward and backward kernels; d <= 8192. */
+int info_esrf_learn_loss_grad(const float* theta_dev, int32_t nsamp, int64_t d, const float* feat_dev,
+                              const float* V_dev, const float* Y_dev, const float* Z_dev, float* grad_dev,
+                              double* loss_dev, void* scratch_dev, size_t scratch_bytes, void* stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) at step number `step` >= 1;
+ * m_dev and v_dev are the moment buffers (zero before the first step). */
+int info_esrf_learn_adam_step(float* theta_dev, float* m_dev, float* v_dev, const float* grad_dev, int32_t step,
+                              float lr, void* stream);
+
+/* `steps` Adam steps starting at step number first_step, stream-ordered;
+ * loss_hist_dev (device, `steps` doubles) receives L before each step. */
+int info_esrf_learn_train(float* theta_dev, float* m_dev, float* v_dev, int32_t first_step, int32_t steps, float lr,
+                          int32_t nsamp, int64_t d, const float* feat_dev, const float* V_dev, const float* Y_dev,
+                          const float* Z_dev, float* grad_dev, double* loss_hist_dev, void* scratch_dev,
+                          size_t scratch_bytes, void* stream);
+
+/* Krylov samples of the method's own PCG (paper preconditioner, FP32 vectors):
+ * prepares one analysis into the workspace (as info_esrf_prepare) and, for
+ * each of the nsel systems sel_dev[] (number q * N + i: shift sigma = s_q + 1),
+ * runs K iterations of that PCG from a random right-hand side (Philox keyed by
+ * options.seed and the system, drawn again whenever ||r|| <= 1e-6 ||b||),
+ * recording v = p/||p||, y = C_q v, z = P_q^-1 y and phi.
+ * Outputs [nsel * K][d] and [nsel * K][4], float; d <= 10240. */
+int info_esrf_krylov_capture(const info_esrf_grid* grid, int64_t N, const double* X_dev, int64_t d,
+                             const int64_t* obs_idx_dev, const double* R_diag_dev, int32_t Q,
+                             const info_esrf_options* opt, void* workspace, size_t ws_bytes, int32_t nsel,
+                             const int32_t* sel_dev, int32_t K, float* V_dev, float* Y_dev, float* Z_dev,
+                             float* feat_dev, void* stream);
+
+/* Versioned binary model file: 8-byte tag "IESRFNN1", int32 parameter count,
+ * parameters (float), then the shift cut-off (double, see
+ * options.learned_max_shift); little-endian.  Host arrays. */
+int info_esrf_model_save(const char* path, const float* theta_host, double max_shift);
+int info_esrf_model_load(const char* path, float* theta_host, double* max_shift);
+
 #ifdef __cplusplus
 }
 #endif

@@ -48,9 +48,9 @@ class Grid(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("ritz_rank", c_int32), ("oversample", c_int32),
                 ("power_iters", c_int32), ("max_iter", c_int32), ("fixed_iters", c_int32),
-                ("rule", c_int32), ("learn_rank", c_int32), ("ell", c_double), ("seed", c_uint64),
-                ("max_neighbors", c_int64), ("learn_diag", c_void_p), ("learn_U", c_void_p),
-                ("phase_events", ctypes.POINTER(c_void_p))]
+                ("rule", c_int32), ("reserved", c_int32), ("ell", c_double), ("seed", c_uint64),
+                ("max_neighbors", c_int64), ("learned_model", c_void_p), ("learned_max_shift", c_double),
+                ("system_iters", c_void_p), ("phase_events", ctypes.POINTER(c_void_p))]
 
 
 class Stats(ctypes.Structure):
@@ -119,6 +119,24 @@ def library() -> ctypes.CDLL:
                                                 c_void_p, ctypes.c_size_t, c_int32, c_void_p,
                                                 ctypes.c_size_t, c_void_p]),
         "info_esrf_launch_count": (c_int64, []),
+        "info_esrf_learn_nparams": (c_int32, []),
+        "info_esrf_learn_halfwidth": (c_int32, []),
+        "info_esrf_learn_coefficients": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
+        "info_esrf_learn_scratch_size": (ctypes.c_size_t, [c_int32]),
+        "info_esrf_learn_loss_grad": (c_int32, [c_void_p, c_int32, c_int64, c_void_p, c_void_p, c_void_p,
+                                                c_void_p, c_void_p, c_void_p, c_void_p, ctypes.c_size_t,
+                                                c_void_p]),
+        "info_esrf_learn_adam_step": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
+                                                ctypes.c_float, c_void_p]),
+        "info_esrf_learn_train": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, ctypes.c_float,
+                                            c_int32, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                            c_void_p, c_void_p, ctypes.c_size_t, c_void_p]),
+        "info_esrf_krylov_capture": (c_int32, [P(Grid), c_int64, c_void_p, c_int64, c_void_p, c_void_p,
+                                               c_int32, P(Options), c_void_p, ctypes.c_size_t, c_int32,
+                                               c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
+                                               c_void_p]),
+        "info_esrf_model_save": (c_int32, [ctypes.c_char_p, c_void_p, c_double]),
+        "info_esrf_model_load": (c_int32, [ctypes.c_char_p, c_void_p, P(c_double)]),
         "info_esrf_fma_probe": (c_int32, [c_int32, c_int64, P(c_double), P(c_double), c_void_p]),
         "info_esrf_prepared_band_capacity": (c_int32, [P(Grid), c_int64, c_int64, c_int32, P(Options),
                                                        P(c_int64), P(c_int64)]),
@@ -165,20 +183,22 @@ def make_grid(grid) -> Grid:
 def make_options(precision: int = PRECISION_FP64, ritz_rank: int = 10, oversample: int = 10,
                  power_iters: int = 1, max_iter: int = 1000, fixed_iters: int = 0,
                  rule: int = RULE_ELLIPTIC, ell: float = 0.0, seed: int = 0x1234ABCD,
-                 max_neighbors: int = 0, learn_diag: Optional[torch.Tensor] = None,
-                 learn_U: Optional[torch.Tensor] = None, learn_rank: int = 0) -> Options:
+                 max_neighbors: int = 0, learned_model: Optional[torch.Tensor] = None,
+                 learned_max_shift: float = 0.0, system_iters: Optional[torch.Tensor] = None) -> Options:
     o = Options()
     library().info_esrf_default_options(ctypes.byref(o))
     o.precision, o.ritz_rank, o.oversample, o.power_iters = precision, ritz_rank, oversample, power_iters
     o.max_iter, o.fixed_iters, o.rule, o.ell, o.seed = max_iter, fixed_iters, rule, ell, seed
     o.max_neighbors = max_neighbors
-    if learn_diag is not None:
-        _need(learn_diag, torch.float32, "learn_diag")
-        o.learn_diag = learn_diag.data_ptr()
-        o.learn_rank = learn_rank
-        if learn_rank > 0:
-            _need(learn_U, torch.float32, "learn_U")
-            o.learn_U = learn_U.data_ptr()
+    if system_iters is not None:
+        _need(system_iters, torch.int32, "system_iters")
+        o.system_iters = system_iters.data_ptr()
+        o._iters_keep = system_iters
+    if learned_model is not None:
+        _need(learned_model, torch.float32, "learned_model")
+        o.learned_model = learned_model.data_ptr()
+        o.learned_max_shift = float(learned_max_shift)
+        o._model_keep = learned_model
     return o
 
 
@@ -357,6 +377,88 @@ def info_esrf_quadrature_nodes(Q: int, ell: float, rule: int = RULE_ELLIPTIC, de
     _check(library().info_esrf_quadrature_nodes(Q, ell, rule, s.data_ptr(), p.data_ptr(), _stream(stream)),
            "info_esrf_quadrature_nodes")
     return s, p
+
+
+# ---------------------------------------------------------------------------
+# Learned preconditioner correction
+# ---------------------------------------------------------------------------
+
+def learn_nparams() -> int:
+    return int(library().info_esrf_learn_nparams())
+
+
+def krylov_capture(grid, X, obs_idx, R, Q, sel, K, options: Optional[Options] = None, stream=None):
+    """Krylov samples (V, Y, Z, feat) of the method's own PCG for systems `sel`."""
+    o = options if options is not None else make_options(precision=PRECISION_FP32)
+    g = make_grid(grid)
+    N, n = X.shape
+    d = obs_idx.numel()
+    need = library().info_esrf_workspace_size(ctypes.byref(g), N, d, Q, ctypes.byref(o))
+    ws = workspace(need, X.device)
+    sel_t = torch.as_tensor(sel, dtype=torch.int32, device=X.device)
+    S = sel_t.numel() * K
+    V = torch.empty((S, d), dtype=torch.float32, device=X.device)
+    Y = torch.empty_like(V)
+    Z = torch.empty_like(V)
+    feat = torch.empty((S, 4), dtype=torch.float32, device=X.device)
+    _check(library().info_esrf_krylov_capture(ctypes.byref(g), N, X.data_ptr(), d, obs_idx.data_ptr(), R.data_ptr(),
+                                              Q, ctypes.byref(o), ws.data_ptr(), ws.numel(), sel_t.numel(),
+                                              sel_t.data_ptr(), K, V.data_ptr(), Y.data_ptr(), Z.data_ptr(),
+                                              feat.data_ptr(), _stream(stream)), "info_esrf_krylov_capture")
+    return V, Y, Z, feat
+
+
+def learn_loss_grad(theta, feat, V, Y, Z, stream=None):
+    S, d = V.shape
+    scratch = workspace(library().info_esrf_learn_scratch_size(S), V.device)
+    grad = torch.empty_like(theta)
+    loss = torch.zeros(1, dtype=torch.float64, device=V.device)
+    _check(library().info_esrf_learn_loss_grad(theta.data_ptr(), S, d, feat.data_ptr(), V.data_ptr(), Y.data_ptr(),
+                                               Z.data_ptr(), grad.data_ptr(), loss.data_ptr(), scratch.data_ptr(),
+                                               scratch.numel(), _stream(stream)), "info_esrf_learn_loss_grad")
+    return float(loss.item()), grad
+
+
+def learn_train(theta, feat, V, Y, Z, steps, lr=1e-2, state=None, stream=None):
+    """Adam training in place on theta (device float).  Returns (loss history, state)."""
+    S, d = V.shape
+    if state is None:
+        state = dict(m=torch.zeros_like(theta), v=torch.zeros_like(theta), step=1)
+    scratch = workspace(library().info_esrf_learn_scratch_size(S), V.device)
+    grad = torch.empty_like(theta)
+    hist = torch.zeros(steps, dtype=torch.float64, device=V.device)
+    _check(library().info_esrf_learn_train(theta.data_ptr(), state["m"].data_ptr(), state["v"].data_ptr(),
+                                           state["step"], steps, lr, S, d, feat.data_ptr(), V.data_ptr(),
+                                           Y.data_ptr(), Z.data_ptr(), grad.data_ptr(), hist.data_ptr(),
+                                           scratch.data_ptr(), scratch.numel(), _stream(stream)),
+           "info_esrf_learn_train")
+    state["step"] += steps
+    return hist, state
+
+
+def learn_coefficients(theta, feat, stream=None):
+    nshift = feat.shape[0]
+    coef = torch.empty((nshift, 2 * int(library().info_esrf_learn_halfwidth()) + 2), dtype=torch.float32,
+                       device=feat.device)
+    _check(library().info_esrf_learn_coefficients(theta.data_ptr(), nshift, feat.data_ptr(), coef.data_ptr(),
+                                                  _stream(stream)), "info_esrf_learn_coefficients")
+    return coef
+
+
+def model_save(path: str, theta_host, max_shift: float = 0.0) -> None:
+    import numpy as np
+    arr = np.ascontiguousarray(np.asarray(theta_host, dtype=np.float32))
+    _check(library().info_esrf_model_save(path.encode(), arr.ctypes.data, float(max_shift)),
+           "info_esrf_model_save")
+
+
+def model_load(path: str):
+    """Returns (parameters as a float32 NumPy array, shift cut-off)."""
+    import numpy as np
+    arr = np.zeros(learn_nparams(), dtype=np.float32)
+    ms = c_double()
+    _check(library().info_esrf_model_load(path.encode(), arr.ctypes.data, ctypes.byref(ms)), "info_esrf_model_load")
+    return arr, float(ms.value)
 
 
 class Prepared:

@@ -1,6 +1,7 @@
 // Host side of the C ABI: argument checks, workspace layout, the launch
 // sequence of one analysis and the optional stats read-back.
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -102,9 +103,7 @@ int check_options(const info_esrf_options* in, info_esrf_options* out) {
   if (out->power_iters < 0 || out->power_iters > 8) return INFO_ESRF_ERR_INVALID_ARG;
   if (out->max_iter < 1 && out->fixed_iters <= 0) return INFO_ESRF_ERR_INVALID_ARG;
   if (out->rule != 0 && out->rule != 1) return INFO_ESRF_ERR_INVALID_ARG;
-  if (out->learn_rank < 0 || out->learn_rank > kMaxLearnRank) return INFO_ESRF_ERR_UNSUPPORTED;
-  if (out->learn_diag && out->learn_rank > 0 && !out->learn_U) return INFO_ESRF_ERR_INVALID_ARG;
-  if (out->learn_diag && out->ritz_rank <= 12 && out->learn_rank > 6) return INFO_ESRF_ERR_UNSUPPORTED;
+  if (out->reserved != 0) return INFO_ESRF_ERR_INVALID_ARG;
   return 0;
 }
 
@@ -142,6 +141,7 @@ void carve_problem(Carver& cv, ProblemDev& pr, const info_esrf_options& o) {
   pr.relres = cv.take<double>((size_t)pr.nsys * 8);
   pr.Vbar = cv.take<double>((size_t)d * (N + 1) * 8);
   pr.VbarT = cv.take<void>((size_t)d * (N + 1) * esz);
+  pr.learn_coef = cv.take<float>((size_t)(pr.Q + 1) * kLearnOut * 4);
 }
 
 // Builds the host table for a batch; with ws == nullptr only sizes it.
@@ -182,9 +182,8 @@ int build_table(const info_esrf_problem* probs, int32_t count, const info_esrf_o
     pr.fixed_iters = o.fixed_iters;
     pr.max_iter = o.max_iter;
     pr.power_iters = o.power_iters;
-    pr.learn_rank = o.learn_diag ? o.learn_rank : 0;
-    pr.learn_diag = o.learn_diag;
-    pr.learn_U = o.learn_U;
+    pr.learned_model = o.learned_model;
+    pr.learned_max_shift = o.learned_max_shift;
     pr.ell_fixed = o.ell;
     pr.seed = o.seed;
     pr.sqrt_nm1 = sqrt((double)(pr.N - 1));
@@ -260,10 +259,14 @@ int run_batch(const info_esrf_problem* probs, int32_t count, const info_esrf_opt
   launch_quadrature(tab, dtab, st);
   mark(1);
   launch_ritz(tab, dtab, st);
+  launch_learn_coef(tab, dtab, st);
   mark(2);
   if (launch_pcg(tab, dtab, counter, scratch, scratch_bytes, sms, st) != 0) return INFO_ESRF_ERR_WORKSPACE;
   mark(3);
   launch_finish(tab, dtab, st);
+  if (o.system_iters && count == 1)
+    cudaMemcpyAsync(o.system_iters, tab.p[0].iters, (size_t)tab.p[0].nsys * sizeof(int32_t),
+                    cudaMemcpyDeviceToDevice, st);
   mark(4);
   if (cudaGetLastError() != cudaSuccess) return INFO_ESRF_ERR_CUDA;
   if (!stats) return INFO_ESRF_OK;
@@ -343,12 +346,13 @@ void info_esrf_default_options(info_esrf_options* opt) {
   opt->max_iter = 1000;
   opt->fixed_iters = 0;
   opt->rule = INFO_ESRF_RULE_ELLIPTIC;
-  opt->learn_rank = 0;
+  opt->reserved = 0;
   opt->ell = 0.0;
   opt->seed = 0x1234abcdULL;
   opt->max_neighbors = 0;
-  opt->learn_diag = nullptr;
-  opt->learn_U = nullptr;
+  opt->learned_model = nullptr;
+  opt->learned_max_shift = 0.0;
+  opt->system_iters = nullptr;
   opt->phase_events = nullptr;
 }
 
@@ -491,6 +495,7 @@ static int prepare_one(const info_esrf_grid* grid, int64_t N, const double* X_de
   launch_bands(tab, dtab, st);
   launch_quadrature(tab, dtab, st);
   launch_ritz(tab, dtab, st);
+  launch_learn_coef(tab, dtab, st);
   return cudaGetLastError() == cudaSuccess ? 0 : INFO_ESRF_ERR_CUDA;
 }
 
@@ -568,6 +573,55 @@ int info_esrf_prepared_export(const info_esrf_grid* grid, int64_t N, int64_t d, 
   if (bytes && cudaMemcpyAsync(dst_host, src, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return INFO_ESRF_ERR_CUDA;
   return cudaStreamSynchronize(st) == cudaSuccess ? 0 : INFO_ESRF_ERR_CUDA;
+}
+
+int info_esrf_krylov_capture(const info_esrf_grid* grid, int64_t N, const double* X_dev, int64_t d,
+                             const int64_t* obs_idx_dev, const double* R_diag_dev, int32_t Q,
+                             const info_esrf_options* opt, void* workspace, size_t ws_bytes, int32_t nsel,
+                             const int32_t* sel_dev, int32_t K, float* V_dev, float* Y_dev, float* Z_dev,
+                             float* feat_dev, void* stream) {
+  if (nsel < 1 || K < 1 || !sel_dev || !V_dev || !Y_dev || !Z_dev || !feat_dev) return INFO_ESRF_ERR_INVALID_ARG;
+  info_esrf_options o;
+  int rc = check_options(opt, &o);
+  if (rc) return rc;
+  if (o.precision != INFO_ESRF_PRECISION_FP32) return INFO_ESRF_ERR_UNSUPPORTED;
+  ProblemDev* dpr;
+  ProblemDev hpr;
+  rc = prepare_one(grid, N, X_dev, d, obs_idx_dev, R_diag_dev, Q, opt, workspace, ws_bytes, stream, true, &dpr,
+                   &hpr);
+  if (rc) return rc;
+  static thread_local ProblemTable tab;
+  tab.count = 1;
+  tab.p[0] = hpr;
+  cudaGetLastError();
+  rc = launch_krylov_capture(tab, dpr, nsel, sel_dev, K, V_dev, Y_dev, Z_dev, feat_dev,
+                             reinterpret_cast<cudaStream_t>(stream));
+  if (rc) return rc;
+  return cudaGetLastError() == cudaSuccess ? 0 : INFO_ESRF_ERR_CUDA;
+}
+
+int info_esrf_model_save(const char* path, const float* theta_host, double max_shift) {
+  if (!path || !theta_host) return INFO_ESRF_ERR_INVALID_ARG;
+  FILE* f = fopen(path, "wb");
+  if (!f) return INFO_ESRF_ERR_INVALID_ARG;
+  const char tag[8] = {'I', 'E', 'S', 'R', 'F', 'N', 'N', '1'};
+  const int32_t np = kLearnParams;
+  const bool ok = fwrite(tag, 1, 8, f) == 8 && fwrite(&np, 4, 1, f) == 1 &&
+                  fwrite(theta_host, sizeof(float), np, f) == (size_t)np && fwrite(&max_shift, 8, 1, f) == 1;
+  return (fclose(f) == 0 && ok) ? 0 : INFO_ESRF_ERR_INVALID_ARG;
+}
+
+int info_esrf_model_load(const char* path, float* theta_host, double* max_shift) {
+  if (!path || !theta_host || !max_shift) return INFO_ESRF_ERR_INVALID_ARG;
+  FILE* f = fopen(path, "rb");
+  if (!f) return INFO_ESRF_ERR_INVALID_ARG;
+  char tag[8];
+  int32_t np = 0;
+  bool ok = fread(tag, 1, 8, f) == 8 && memcmp(tag, "IESRFNN1", 8) == 0 && fread(&np, 4, 1, f) == 1 &&
+            np == kLearnParams && fread(theta_host, sizeof(float), np, f) == (size_t)np &&
+            fread(max_shift, 8, 1, f) == 1;
+  fclose(f);
+  return ok ? 0 : INFO_ESRF_ERR_INVALID_ARG;
 }
 
 int info_esrf_prepared_band_capacity(const info_esrf_grid* grid, int64_t N, int64_t d, int32_t Q,

@@ -10,7 +10,10 @@ namespace infoesrf {
 constexpr int kMaxProblems = 64;      // problems per batched call
 constexpr int kMaxRitz = 32;          // k_R + oversampling
 constexpr int kMaxK = 24;             // Ritz vectors used by the preconditioner
-constexpr int kMaxLearnRank = 8;      // rank of the learned correction
+constexpr int kLearnH = 8;            // half-width of the learned stencil
+constexpr int kLearnTaps = 2 * kLearnH + 1;
+constexpr int kLearnOut = 1 + kLearnTaps;  // log a and the taps
+constexpr int kLearnParams = 1810;    // network parameters (see learn.cu)
 constexpr int kThreads = 256;         // CTA size of the persistent PCG kernel
 
 // Status bits written by kernels (ws status word 0).
@@ -40,7 +43,7 @@ struct ProblemDev {
   GridDev grid;
   int64_t n, N, d;
   int32_t Q, kR, l, do_mean, do_pert, rule, precision, fixed_iters;
-  int32_t max_iter, power_iters, learn_rank, pad_;
+  int32_t max_iter, power_iters, pad0_, pad_;
   double tol, ell_fixed, sqrt_nm1;
   uint64_t seed;
   int64_t max_oo, max_xo;      // ELL capacities (obs-obs, state-obs)
@@ -58,7 +61,7 @@ struct ProblemDev {
   void* W;              // [d][N] T observed anomalies W = H Z
   double* rinv;         // [d] R^-1/2
   double* bmean;        // [d] R^-1/2 (y - H mu)
-  double* scal;         // [8] 0 gershgorin bound, 1 min diag C, 2 ell, 3 sum p
+  double* scal;         // [8] 0 gershgorin bound, 1 min diag C, 2 ell, 3 unused, 4 sum of diag C
   int32_t* status;      // [4]
   double* s;            // [Q] quadrature nodes
   double* p;            // [Q] quadrature weights
@@ -78,9 +81,10 @@ struct ProblemDev {
   void* CPhi;           // [d][kR] T C Phi
   double* theta;        // [kR] Ritz values of C
   double* gram;         // [3][kR][kR]: Phi^T Phi, A^T Phi, A^T A with A = C Phi
-  // learned diagonal-plus-low-rank correction (optional)
-  const float* learn_diag;   // [Q + 1][d] >= 0, NULL: none
-  const float* learn_U;      // [Q + 1][d][learn_rank]
+  // learned correction a_q P_q^-1 + S_q^T S_q (optional)
+  const float* learned_model;   // network parameters, NULL: none
+  double learned_max_shift;     // > 0: learned term only for sigma <= this
+  float* learn_coef;            // [Q + 1][kLearnOut]: a_q, taps (slot Q: mean system)
   // batched PCG
   // Systems are numbered hardest first: sid 0 is the mean system (shift 1)
   // when requested, then the perturbation systems node-major,
@@ -123,6 +127,11 @@ void launch_lmp_apply(const ProblemDev& pr, const ProblemDev* dpr, int32_t nvec,
 
 // Host-side count of kernel launches issued by this library.
 void note_launches(int n);
+
+// Learned correction: per-shift coefficients, Krylov capture.
+void launch_learn_coef(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st);
+int launch_krylov_capture(const ProblemTable& tab, const ProblemDev* dtab, int nsel, const int32_t* sel, int K,
+                          float* V, float* Y, float* Z, float* feat, cudaStream_t st);
 
 // Cluster-resident PCG for 1-D observation networks (single problem, FP32).
 bool band1d_eligible(const ProblemTable& tab);

@@ -45,8 +45,12 @@ constexpr int kJ = 32;          // lanes (systems) per cluster
 constexpr int kLD = kJ + 4;     // padded row stride (floats) of lane-major row vectors
 constexpr int kTile = 16;       // rows per matvec tile
 constexpr int kNW = kThreads / 32;
-constexpr int kK = 12;          // Ritz vectors handled by this kernel
-constexpr int kNR = 2 + 2 * kK; // residual reduction values per lane: rr (hi, lo), f[k], g[k]
+constexpr int kK = 10;          // Ritz vectors handled by this kernel
+constexpr int kNR = 4 + 2 * kK; // residual reduction values per lane: rr (hi, lo), uu (hi, lo), f[k], g[k]
+constexpr int kRetry = 1 << 30; // queue id flag: solve this system again without the learned term
+constexpr int kTH = 2 * kLearnH;          // half-width of T = S^T S (autocorrelation of the taps)
+constexpr int kTT = 2 * kTH + 1;          // taps of T
+constexpr int kTrRows = 4;                // rows per thread for which T r is kept in registers
 constexpr int kMaxTiles = 128;  // rows per CTA <= 2048
 constexpr int kMaxCS = 8;       // CTAs per cluster
 
@@ -58,12 +62,16 @@ struct LaneState {
   float sigf[kJ], alpha[kJ], beta[kJ];
   float t[kJ][kK], c[kJ][kK];
   float f[kJ][kK], g[kJ][kK];
+  double rtr[kJ];                     // r^T T r of the learned term
+  float la[kJ], lt[kJ][kTT];          // learned correction: a and the taps of T = S^T S per lane
+  int learn[kJ];
 };
 
 struct Setup {
   int hl, hr, bad, tilesz;
   int xchg[4];
-  int npush;       // halo rows this CTA pushes to the cluster
+  int npush;       // halo rows of p this CTA pushes to the cluster
+  int nrpush;      // halo rows of r (learned term)
 };
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
@@ -110,7 +118,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
   if (tid == 0) { s_lo_min = 1 << 30; s_hi_max = -(1 << 30); s_bad = (R_s > kMaxTiles * kTile) ? 1 : 0; }
   __syncthreads();
   // per-row window [lo, hi] relative to s0, kept in the dynamic buffer's tail
-  int* rlo = reinterpret_cast<int*>(dyn) + (dyn_floats - 2 * R_s);
+  int* rlo = reinterpret_cast<int*>(dyn);
   int* rhi = rlo + R_s;
   if (2 * R_s > dyn_floats) s_bad = 1;
   __syncthreads();
@@ -172,11 +180,11 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
     const int64_t s02 = (int64_t)c2 * R_s;
     return (int)(d - s02 < 0 ? 0 : (d - s02 < R_s ? d - s02 : R_s));
   };
-  auto for_each_push = [&](auto&& f) {     // enumerates targets, thread-strided
-    const int per = hl + R_s + hr;           // window rows per CTA (own rows skipped)
+  auto for_each_push_w = [&](int wl, int wr, auto&& f) {   // window [-wl, R_s + wr), thread-strided
+    const int per = wl + R_s + wr;           // window rows per CTA (own rows skipped)
     for (int e = tid; e < CS * per; e += blockDim.x) {
-      const int c2 = e / per, wrow = e % per;  // wrow = rel2 + hl
-      const int rel2 = wrow - hl;
+      const int c2 = e / per, wrow = e % per;  // wrow = rel2 + wl
+      const int rel2 = wrow - wl;
       const int nr2 = nrows_of(c2);
       if (rel2 >= 0 && rel2 < nr2) continue;   // own row of c2, not a halo row
       int64_t g = ((int64_t)c2 * R_s + rel2) % d;
@@ -186,27 +194,36 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       f((int)(g - s0), c2, wrow);
     }
   };
-  if (tid == 0) S.npush = 0;
+  auto for_each_push = [&](auto&& f) { for_each_push_w(hl, hr, f); };
+  // learned term: T r needs r on a window of +-kTH rows around the own rows
+  const bool learn_ok = pr.learned_model != nullptr && R_s <= 32 * kTrRows;
+  if (tid == 0) { S.npush = 0; S.nrpush = 0; }
   __syncthreads();
   {
-    int cnt = 0;
+    int cnt = 0, cnt2 = 0;
     for_each_push([&](int, int, int) { ++cnt; });
+    if (learn_ok) for_each_push_w(kTH, kTH, [&](int, int, int) { ++cnt2; });
     if (cnt) atomicAdd(&S.npush, cnt);
+    if (cnt2) atomicAdd(&S.nrpush, cnt2);
   }
   cluster.sync();
-  int npush_max = 0;
-  for (int c = 0; c < CS; ++c) npush_max = max(npush_max, cluster.map_shared_rank(&S, c)->npush);
+  int npush_max = 0, nrpush_max = 0;
+  for (int c = 0; c < CS; ++c) {
+    npush_max = max(npush_max, cluster.map_shared_rank(&S, c)->npush);
+    nrpush_max = max(nrpush_max, cluster.map_shared_rank(&S, c)->nrpush);
+  }
   // shared-memory carve (floats): tiles | p window | r | x | y | Phi^T | A^T | push table
   const int W_p = R_s + hl + hr;
   const int o_pw = (tilesz + 3) & ~3;
   const int o_r = o_pw + W_p * kLD;
   const int o_x = o_r + R_s * kLD;
-  const int o_y = o_x + R_s * kLD;
-  const int o_ph = o_y + R_s * kLD;
+  const int o_y = o_x + R_s * kLD;                 // y, then the r window, own rows at +kTH
+  const int o_ph = o_y + (R_s + 2 * kTH) * kLD;
   const int o_at = o_ph + k * R_s;
   const int o_push = (o_at + k * R_s + 1) & ~1;
-  const int need = o_push + 2 * npush_max;
-  if (need > dyn_floats - 2 * R_s) bad = 1;      // keep the per-row windows intact while tiles fill
+  const int o_rpush = o_push + 2 * npush_max;
+  const int need = o_rpush + 2 * nrpush_max;
+  if (need > dyn_floats) bad = 1;
   cluster.sync();                                   // remote reads of S done before anyone exits
   if (bad) {
     if (cl_id == 0 && crank == 0 && tid == 0) *fallback = 1;
@@ -221,6 +238,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
   float* phT = dyn + o_ph;
   float* aT = dyn + o_at;
   int2* push = reinterpret_cast<int2*>(dyn + o_push);
+  int2* rpush = reinterpret_cast<int2*>(dyn + o_rpush);
   const float* val = reinterpret_cast<const float*>(pr.oo_val);
   const float* Phi = reinterpret_cast<const float*>(pr.Phi);
   const float* CPhi = reinterpret_cast<const float*>(pr.CPhi);
@@ -250,21 +268,31 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
     s_gram[w3][e] = (float)pr.gram[w3 * pk * pk + ii * pk + jj];
   }
   for (int m = tid; m < k; m += blockDim.x) s_theta[m] = (float)pr.theta[m];
-  __shared__ int s_npush;
-  if (tid == 0) s_npush = 0;
+  __shared__ int s_npush, s_nrpush;
+  if (tid == 0) { s_npush = 0; s_nrpush = 0; }
   __syncthreads();
   for_each_push([&](int row, int c2, int wrow) {
     const int slot = atomicAdd(&s_npush, 1);
     push[slot] = make_int2(row | (c2 << 16), wrow);
   });
+  if (learn_ok)
+    for_each_push_w(kTH, kTH, [&](int row, int c2, int wrow) {
+      const int slot = atomicAdd(&s_nrpush, 1);
+      rpush[slot] = make_int2(row | (c2 << 16), wrow);
+    });
   const double cmin = pr.scal[1];
   const int maxit = pr.fixed_iters > 0 ? pr.fixed_iters : pr.max_iter;
   const double tol2 = pr.tol * pr.tol;
 
   // Starts system sid in lane j on the own rows (r = b, x = 0; p own rows are 0).
-  auto lane_scalars = [&](int j, int sid) {
+  auto lane_scalars = [&](int j, int code) {
+    const bool retry = code >= kRetry;
+    const int sid = retry ? code - kRetry : code;
     L.sid[j] = sid;
     L.fin[j] = 0;
+    L.learn[j] = 0;
+    L.la[j] = 1.f;
+    for (int u = 0; u < kTT; ++u) L.lt[j][u] = 0.f;
     if (sid < 0) {
       L.state[j] = kEmpty;
       L.sigma[j] = 1.0;
@@ -272,6 +300,20 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       L.state[j] = kStart;
       const int q = sid < pr.mean_sys ? -1 : (int)((sid - pr.mean_sys) / N);
       L.sigma[j] = q < 0 ? 1.0 : pr.s[q] + 1.0;
+      const float* cf = pr.learn_coef + (int64_t)(q < 0 ? pr.Q : q) * kLearnOut;
+      if (learn_ok && !retry && cf[0] > 0.f) {
+        L.learn[j] = 1;
+        L.la[j] = cf[0];
+        // T = S^T S: t[D] = sum_u w[u] w[u - D], D = -kTH..kTH
+        for (int D = -kTH; D <= kTH; ++D) {
+          float acc = 0.f;
+          for (int u = 0; u < kLearnTaps; ++u) {
+            const int v2 = u - D;
+            if (v2 >= 0 && v2 < kLearnTaps) acc = fmaf(cf[1 + u], cf[1 + v2], acc);
+          }
+          L.lt[j][D + kTH] = acc;
+        }
+      }
     }
     L.sigf[j] = (float)L.sigma[j];
     L.it[j] = 0;
@@ -345,7 +387,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       for (int q4 = 0; q4 < 4; ++q4) {
         const float4 pv = ld4(pown + 4 * q4);
         if (valid) {
-          st4(vy + row * kLD + 16 * h + 4 * q4,
+          st4(vy + (row + kTH) * kLD + 16 * h + 4 * q4,
               make_float4(acc[4 * q4], acc[4 * q4 + 1], acc[4 * q4 + 2], acc[4 * q4 + 3]));
           pp[4 * q4 + 0].add_prod(pv.x, acc[4 * q4 + 0]);
           pp[4 * q4 + 1].add_prod(pv.y, acc[4 * q4 + 1]);
@@ -397,18 +439,21 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
     }
     __syncthreads();
     // ---------------- x += alpha p, r -= alpha y; partial rr, Phi^T r, A^T r ----------------
+    float4 trr[kTrRows];   // (T r) of this thread's rows and its warp's four lanes (learned term)
     {
       const int j0 = 4 * warp;   // this warp's four lanes
       const float a0 = L.alpha[j0], a1 = L.alpha[j0 + 1], a2 = L.alpha[j0 + 2], a3 = L.alpha[j0 + 3];
       DotAcc<float> rr[4];
-      float v[3][32];
+      // partial Phi^T r and A^T r of the four lanes: value jj * 2kK + (m | kK + m),
+      // 80 values held as two blocks of 32 and one of 16
+      float v0[32], v1[32], v2[16];
 #pragma unroll
-      for (int b = 0; b < 3; ++b)
+      for (int i = 0; i < 32; ++i) { v0[i] = 0.f; v1[i] = 0.f; }
 #pragma unroll
-        for (int i = 0; i < 32; ++i) v[b][i] = 0.f;
+      for (int i = 0; i < 16; ++i) v2[i] = 0.f;
       for (int row = lane; row < nrows; row += 32) {
         const float4 p4 = ld4(pw + (row + hl) * kLD + j0);
-        const float4 y4 = ld4(vy + row * kLD + j0);
+        const float4 y4 = ld4(vy + (row + kTH) * kLD + j0);
         float4 x4 = ld4(vx + row * kLD + j0);
         float4 r4 = ld4(vr + row * kLD + j0);
         x4.x = fmaf(a0, p4.x, x4.x); x4.y = fmaf(a1, p4.y, x4.y);
@@ -417,6 +462,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
         r4.z = fmaf(-a2, y4.z, r4.z); r4.w = fmaf(-a3, y4.w, r4.w);
         st4(vx + row * kLD + j0, x4);
         st4(vr + row * kLD + j0, r4);
+        st4(vy + (row + kTH) * kLD + j0, r4);     // r window (y is no longer needed)
         rr[0].add_prod(r4.x, r4.x); rr[1].add_prod(r4.y, r4.y);
         rr[2].add_prod(r4.z, r4.z); rr[3].add_prod(r4.w, r4.w);
         const float rv[4] = {r4.x, r4.y, r4.z, r4.w};
@@ -426,44 +472,103 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
             const float ph = phT[m * R_s + row], at = aT[m * R_s + row];
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj) {
-              // value index: lane-major blocks of 24 (f[12], g[12]) per lane jj
-              const int idx = jj * 2 * kK + m;
-              v[idx / 32][idx % 32] = fmaf(ph, rv[jj], v[idx / 32][idx % 32]);
-              const int idg = jj * 2 * kK + kK + m;
-              v[idg / 32][idg % 32] = fmaf(at, rv[jj], v[idg / 32][idg % 32]);
+              const int idx = jj * 2 * kK + m, idg = idx + kK;
+              float& vf = idx < 32 ? v0[idx] : idx < 64 ? v1[idx - 32] : v2[idx - 64];
+              vf = fmaf(ph, rv[jj], vf);
+              float& vg = idg < 32 ? v0[idg] : idg < 64 ? v1[idg - 32] : v2[idg - 64];
+              vg = fmaf(at, rv[jj], vg);
             }
           }
         }
       }
-      const float s0v = warp_reduce_scatter32<float>(v[0], lane);
-      const float s1v = warp_reduce_scatter32<float>(v[1], lane);
-      const float s2v = warp_reduce_scatter32<float>(v[2], lane);
-      const float sv[3] = {s0v, s1v, s2v};
-      float rhi[4], rlo[4];
+      // learned term, applied periodically across the slices: the halo rows
+      // of the r window come from their owners, then T r = S^T S r on the own
+      // rows stays in registers until the direction update
+      DotAcc<float> uu[4];
+      bool any_learn = false;
+      if (learn_ok) {
+        __syncthreads();
+        const int nrp = s_nrpush;
+        for (int e = tid; e < nrp * (kJ / 4); e += blockDim.x) {
+          const int2 t = rpush[e / (kJ / 4)];
+          const int q4 = e % (kJ / 4);
+          const int row = t.x & 0xffff, c2 = t.x >> 16;
+          st4(cluster.map_shared_rank(vy, c2) + t.y * kLD + 4 * q4, ld4(vy + (row + kTH) * kLD + 4 * q4));
+        }
+        cluster.sync();   // (2a) r windows complete
+        any_learn = L.learn[j0] | L.learn[j0 + 1] | L.learn[j0 + 2] | L.learn[j0 + 3];
+        if (any_learn) {
+          int i = 0;
+          for (int row = lane; row < nrows; row += 32, ++i) {
+            float4 t4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int tp = 0; tp < kTT; ++tp) {
+              const float4 r4 = ld4(vy + (row + tp) * kLD + j0);   // r[row + tp - kTH]
+              t4.x = fmaf(L.lt[j0][tp], r4.x, t4.x);
+              t4.y = fmaf(L.lt[j0 + 1][tp], r4.y, t4.y);
+              t4.z = fmaf(L.lt[j0 + 2][tp], r4.z, t4.z);
+              t4.w = fmaf(L.lt[j0 + 3][tp], r4.w, t4.w);
+            }
+            const float4 r4 = ld4(vy + (row + kTH) * kLD + j0);
+            uu[0].add_prod(r4.x, t4.x); uu[1].add_prod(r4.y, t4.y);
+            uu[2].add_prod(r4.z, t4.z); uu[3].add_prod(r4.w, t4.w);
+#pragma unroll
+            for (int ii = 0; ii < kTrRows; ++ii)
+              if (ii == i) trr[ii] = t4;
+          }
+        }
+      }
+      const float s0v = warp_reduce_scatter32<float>(v0, lane);
+      const float s1v = warp_reduce_scatter32<float>(v1, lane);
+      // 16-value block: fold the warp halves, then reduce-scatter over 16 lanes
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v2[i] += __shfl_xor_sync(0xffffffffu, v2[i], 16);
+#pragma unroll
+      for (int off = 8; off >= 1; off >>= 1) {
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < off; ++i) {
+          const float send = up ? v2[i] : v2[i + off];
+          const float keep = up ? v2[i + off] : v2[i];
+          v2[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+      }
+      const float sv[3] = {s0v, s1v, v2[0]};
+      float rhi[4], rlo[4], uhi[4], ulo[4];
 #pragma unroll
       for (int jj = 0; jj < 4; ++jj) {
-        float hi = rr[jj].hi, lo = rr[jj].lo;
+        float hi = rr[jj].hi, lo = rr[jj].lo, hu = uu[jj].hi, lu = uu[jj].lo;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
           const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
           ff_merge(hi, lo, h2, l2);
+          if (any_learn) {
+            const float h3 = __shfl_xor_sync(0xffffffffu, hu, o);
+            const float l3 = __shfl_xor_sync(0xffffffffu, lu, o);
+            ff_merge(hu, lu, h3, l3);
+          }
         }
         rhi[jj] = hi;
         rlo[jj] = lo;
+        uhi[jj] = hu;
+        ulo[jj] = lu;
       }
       // push this warp's four lanes to every CTA of the cluster
       for (int dst = 0; dst < CS; ++dst) {
         float* base = cluster.map_shared_rank(&s_res_in[crank][0][0], dst);
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
-          const int idx = 32 * b + lane;          // = jj * 24 + (m or 12 + m)
+          const int idx = 32 * b + lane;          // = jj * 2kK + (m or kK + m)
+          if (idx >= 4 * 2 * kK) continue;
           const int jj = idx / (2 * kK), w = idx % (2 * kK);
-          base[(j0 + jj) * kNR + 2 + w] = sv[b];
+          base[(j0 + jj) * kNR + 4 + w] = sv[b];
         }
         if (lane < 4) {
           base[(j0 + lane) * kNR] = lane == 0 ? rhi[0] : lane == 1 ? rhi[1] : lane == 2 ? rhi[2] : rhi[3];
           base[(j0 + lane) * kNR + 1] = lane == 0 ? rlo[0] : lane == 1 ? rlo[1] : lane == 2 ? rlo[2] : rlo[3];
+          base[(j0 + lane) * kNR + 2] = lane == 0 ? uhi[0] : lane == 1 ? uhi[1] : lane == 2 ? uhi[2] : uhi[3];
+          base[(j0 + lane) * kNR + 3] = lane == 0 ? ulo[0] : lane == 1 ? ulo[1] : lane == 2 ? ulo[2] : ulo[3];
         }
       }
     }
@@ -474,13 +579,18 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       const int j = e / (2 * kK), w = e % (2 * kK);
       if ((w % kK) >= k) continue;
       float sacc = 0.f;
-      for (int c = 0; c < CS; ++c) sacc += s_res_in[c][j][2 + w];
+      for (int c = 0; c < CS; ++c) sacc += s_res_in[c][j][4 + w];
       if (w < kK) L.f[j][w] = sacc; else L.g[j][w - kK] = sacc;
     }
     if (tid < kJ) {
       float hi = 0.f, lo = 0.f;
-      for (int c = 0; c < CS; ++c) ff_merge(hi, lo, s_res_in[c][tid][0], s_res_in[c][tid][1]);
+      float hu = 0.f, lu = 0.f;
+      for (int c = 0; c < CS; ++c) {
+        ff_merge(hi, lo, s_res_in[c][tid][0], s_res_in[c][tid][1]);
+        ff_merge(hu, lu, s_res_in[c][tid][2], s_res_in[c][tid][3]);
+      }
       L.rr[tid] = (double)hi + (double)lo;
+      L.rtr[tid] = L.learn[tid] ? (double)hu + (double)lu : 0.0;
     }
     __syncthreads();
     // preconditioner algebra: t = T^-1 f, t2 = g + sigma f - G t, c = (beta - sigma) t - T^-1 t2
@@ -506,8 +616,10 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       const int j = tid;
       const int st = L.state[j];
       const double rr = L.rr[j];
-      double rho = rr;
-      for (int m = 0; m < k; ++m) rho += -(double)L.g[j][m] * (double)L.t[j][m] + (double)L.f[j][m] * (double)L.c[j][m];
+      // rho = r^T M r = a r^T P^-1 r + r^T S^T S r
+      double rpr = rr;
+      for (int m = 0; m < k; ++m) rpr += -(double)L.g[j][m] * (double)L.t[j][m] + (double)L.f[j][m] * (double)L.c[j][m];
+      const double rho = (double)L.la[j] * rpr + L.rtr[j];
       if (st == kStart) {
         L.bn2[j] = rr;
         if (!(rr > 0.0) || !isfinite(rr)) {
@@ -535,19 +647,27 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
     if (crank == 0 && warp == 0) {
       const int j = lane;
       const bool f = L.fin[j] != 0;
-      const unsigned fm = __ballot_sync(0xffffffffu, f);
+      const double bn = L.bn2[j];
+      const bool failed = f && (L.fin[j] == 2 || (pr.fixed_iters <= 0 && !(L.rr[j] <= tol2 * bn)));
+      const bool retry = failed && L.learn[j];          // plain PCG solves it again
+      const bool take = f && !retry;
+      const unsigned fm = __ballot_sync(0xffffffffu, take);
       int base = 0;
       if (lane == 0 && fm) base = atomicAdd(queue, __popc(fm));
       base = __shfl_sync(0xffffffffu, base, 0);
       if (f) {
         const int sid = L.sid[j];
-        const double bn = L.bn2[j];
-        pr.iters[sid] = L.it[j];
-        pr.relres[sid] = bn > 0.0 ? sqrt(L.rr[j] / bn) : 0.0;
-        if (L.fin[j] == 2) atomicOr(&pr.status[0], kStatBreakdown);
-        else if (pr.fixed_iters <= 0 && !(L.rr[j] <= tol2 * bn)) atomicOr(&pr.status[0], kStatNotConverged);
-        const int nid = base + __popc(fm & ((1u << j) - 1u));
-        const int v = nid < pr.nsys ? nid : -1;
+        int v;
+        if (retry) {
+          v = sid + kRetry;
+        } else {
+          pr.iters[sid] = L.it[j];
+          pr.relres[sid] = bn > 0.0 ? sqrt(L.rr[j] / bn) : 0.0;
+          if (L.fin[j] == 2) atomicOr(&pr.status[0], kStatBreakdown);
+          else if (failed) atomicOr(&pr.status[0], kStatNotConverged);
+          const int nid = base + __popc(fm & ((1u << j) - 1u));
+          v = nid < pr.nsys ? nid : -1;
+        }
         for (int dst = 0; dst < CS; ++dst) cluster.map_shared_rank(&L.newsid[0], dst)[j] = v;
       }
     }
@@ -563,13 +683,16 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
           cj[jj][m] = m < k ? L.c[j0 + jj][m] : 0.f;
         }
       bool act[4], fin[4];
-      float bj[4];
+      float bj[4], aj[4];
 #pragma unroll
       for (int jj = 0; jj < 4; ++jj) {
         act[jj] = L.state[j0 + jj] == kActive && L.fin[j0 + jj] == 0;
         fin[jj] = L.fin[j0 + jj] != 0;
         bj[jj] = L.beta[j0 + jj];
+        aj[jj] = L.la[j0 + jj];
       }
+      const bool any_learn2 = L.learn[j0] | L.learn[j0 + 1] | L.learn[j0 + 2] | L.learn[j0 + 3];
+      int ir = 0;
       float* U = reinterpret_cast<float*>(pr.U);
       for (int row = lane; row < nrows; row += 32) {
         float* prow = pw + (row + hl) * kLD + j0;
@@ -584,6 +707,17 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
             for (int jj = 0; jj < 4; ++jj) z[jj] = fmaf(ph, cj[jj][m], fmaf(-at, tj[jj][m], z[jj]));
           }
         }
+        if (any_learn2) {
+          float4 w4 = make_float4(0.f, 0.f, 0.f, 0.f);     // (T r)_row from the residual step
+#pragma unroll
+          for (int ii = 0; ii < kTrRows; ++ii)
+            if (ii == ir) w4 = trr[ii];
+          z[0] = fmaf(aj[0], z[0], w4.x);
+          z[1] = fmaf(aj[1], z[1], w4.y);
+          z[2] = fmaf(aj[2], z[2], w4.z);
+          z[3] = fmaf(aj[3], z[3], w4.w);
+        }
+        ++ir;
         const float pv[4] = {p4.x, p4.y, p4.z, p4.w};
         float pn[4];
 #pragma unroll

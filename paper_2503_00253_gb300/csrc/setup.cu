@@ -40,8 +40,7 @@ __global__ void k_clear_scalars(ProblemDev* tab) {
   if (threadIdx.x == 0) {
     pr.scal[0] = 0.0;
     pr.scal[1] = __longlong_as_double(0x7ff0000000000000LL);  // +inf, atomically lowered
-    pr.scal[2] = 0.0;
-    pr.scal[3] = 0.0;
+    for (int i = 2; i < 8; ++i) pr.scal[i] = 0.0;
     for (int i = 0; i < 4; ++i) pr.status[i] = 0;
   }
 }
@@ -176,7 +175,10 @@ __global__ void k_band(const ProblemDev* tab) {
           col[e * rows + row] = (int32_t)b;
         }
         rowsum += fabs(v);
-        if (OBS_ROWS && b == row) atomic_min_nonneg(&pr.scal[1], v);
+        if (OBS_ROWS && b == row) {
+          atomic_min_nonneg(&pr.scal[1], v);
+          atomicAdd(&pr.scal[4], v);
+        }
       }
       count += __popc(mask);
     }
