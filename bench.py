@@ -5,7 +5,10 @@ One step = one full analysis (mean update + perturbation update: anomalies,
 localized-covariance bands, quadrature, Ritz pairs, the persistent batched
 shifted PCG over all 1280 + 1 systems, quadrature accumulation and the
 state update) of the 1-D Gaussian-forecast workload n=8192, N=40, d=1024,
-Q=32, in FP32 bulk arithmetic with FP64 scalars, through the C ABI.
+Q=32, in FP32 bulk arithmetic with FP64 scalars, through the C ABI.  By
+default the shifted systems use the learned preconditioner correction,
+trained before the timed region on three other seeds of the same workload;
+the paper's preconditioner alone (FP32) and the FP64 path are timed beside it.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
 oracle on the host cores instead.
@@ -31,13 +34,16 @@ UNIT = "analyses/s"
 WORKLOAD = "gauss1d_n8192_N40_d1024_Q32_R0.25_gc256 (1280 shifted systems + mean)"
 TOL_MIXED = 1e-6
 RITZ = 10
+TRAIN_SEEDS = (11, 12, 13)
+# DRAM bytes (read + write) of one k_pcg_band1d launch on this workload with the
+# learned correction, from the ncu capture summarised in
+# profiles/k_pcg_band1d_gauss1d_n8192_N40_d1024_Q32_fp32_learned.md; set to None when the kernel changes.
+PCG_DRAM_BYTES = 1620224
 
 
 def _dist():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_2503_00253_gb300 import replicas
+    return replicas.rank_info()
 
 
 def _clock_sampler(path):
@@ -111,7 +117,7 @@ def run_ours(args):
     import torch
 
     from paper_2503_00253_gb300 import binding as B
-    from paper_2503_00253_gb300 import workloads
+    from paper_2503_00253_gb300 import replicas, workloads
 
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
@@ -131,7 +137,18 @@ def run_ours(args):
     cap = max(max_oo, max_xo)
     prec = B.PRECISION_FP32 if args.precision == "fp32" else B.PRECISION_FP64
     tol = TOL_MIXED if prec == B.PRECISION_FP32 else args.fp64_tol
-    opts = B.make_options(precision=prec, ritz_rank=RITZ, max_neighbors=cap)
+    use_learned = args.preconditioner == "learned" and prec == B.PRECISION_FP32
+    theta, cutoff, learn_info = None, 0.0, None
+    if use_learned:
+        from paper_2503_00253_gb300 import learned
+        t0 = time.perf_counter()
+        train_set = [workloads.config2(tol=TOL_MIXED, seed=s) for s in TRAIN_SEEDS]
+        theta, cutoff, hist = learned.fit(train_set, K=12, members_per_q=3, steps=300)
+        torch.cuda.synchronize()
+        learn_info = {"train_seeds": list(TRAIN_SEEDS), "fit_s": time.perf_counter() - t0,
+                      "loss_first": float(hist[0]), "loss_last": float(hist[-1]), "max_shift": cutoff}
+    opts = B.make_options(precision=prec, ritz_rank=RITZ, max_neighbors=cap, learned_model=theta,
+                          learned_max_shift=cutoff)
     g = B.make_grid(pr.grid)
     import ctypes
     need = B.library().info_esrf_workspace_size(ctypes.byref(g), N, d, pr.Q, ctypes.byref(opts))
@@ -148,19 +165,29 @@ def run_ours(args):
     st = step(stats=True)
     torch.cuda.synchronize()
     result = {}
+    ref_cache = None
     if rank == 0 and not args.no_parity:
         from oracle import filter as F
         mu_ref, A_ref = _oracle_analysis(pr)
+        ref_cache = (mu_ref, A_ref)
         Af = pr.X - pr.X.mean(0)
         result["rel_err"] = F.relative_increment_error(A_a.cpu().numpy(), A_ref, Af)
         mu0 = pr.X.mean(0)
         result["rel_err_mean"] = float(np.linalg.norm(mu_a.cpu().numpy() - mu_ref) / np.linalg.norm(mu_ref - mu0))
 
-    # exact band size for the algorithmic flop count
-    prep = B.Prepared(pr.grid, X, obs, R, pr.Q, opts)
+    # exact band size and per-system iteration counts for the algorithmic flop count
+    prep = B.Prepared(pr.grid, X, obs, R, pr.Q, B.make_options(precision=prec, ritz_rank=RITZ, max_neighbors=cap))
     nnz_C = int(prep.export("oo_nnz").sum())
-    nnz_xo = int(prep.export("xo_nnz").sum())
     del prep
+    it_sys = torch.zeros(1 + pr.Q * N, dtype=torch.int32, device=dev)
+    o_it = B.make_options(precision=prec, ritz_rank=RITZ, max_neighbors=cap, learned_model=theta,
+                          learned_max_shift=cutoff, system_iters=it_sys)
+    B.info_esrf_analysis(pr.grid, X, obs, y, R, pr.Q, tol, o_it, ws=wsp, mu_a=mu_a, A_a=A_a, stats=False,
+                         stream=stream)
+    it_sys = it_sys.cpu().numpy().astype(np.float64)
+    s_nodes, _ = B.info_esrf_quadrature_nodes(pr.Q, st["ell_used"])
+    sigma_sys = np.concatenate([[1.0], np.repeat(s_nodes.cpu().numpy() + 1.0, N)])
+    learned_sys = (sigma_sys <= cutoff) if use_learned else np.zeros_like(sigma_sys, dtype=bool)
 
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     events = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
@@ -174,9 +201,7 @@ def run_ours(args):
     clock_path = os.path.join(tempfile.gettempdir(), f"clocks_{os.getpid()}.csv")
     sampler = _clock_sampler(clock_path) if rank == 0 else None
     time.sleep(0.3 if sampler else 0.0)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    replicas.barrier()
     torch.cuda.synchronize()
     launches0 = B.launch_count()
     step_ms, pcg_ms, phase_ms = [], [], [[0.0] * 4 for _ in range(args.steps)]
@@ -190,13 +215,8 @@ def run_ours(args):
         pcg_ms.append(phase_ms[s][2])
     torch.cuda.synchronize()
     launches = B.launch_count() - launches0
-    total_ms = sum(step_ms)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        dist.barrier()
+    total_ms = replicas.max_over_ranks(sum(step_ms), dev)
+    replicas.barrier()
     B.set_phase_events(opts, None)
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
@@ -228,39 +248,40 @@ def run_ours(args):
     clocks = _clock_summary(clock_path, local) if rank == 0 else {}
     h2d = sum(t.numel() * t.element_size() for t in (Xh, obsh, yh, Rh))
     d2h = mu_h.numel() * 8 + A_h.numel() * 8
-    e2e_total = sum(e2e_ms)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = replicas.max_over_ranks(sum(e2e_ms), dev)
 
-    # FP64 comparator on the same GPU (plain FP64 batched PCG with the paper's preconditioner)
-    fp64 = None
+    # comparators on the same GPU: the paper's preconditioner alone, in FP32 and in FP64
+    comparators = {}
     if rank == 0 and prec == B.PRECISION_FP32 and args.fp64_steps > 0:
-        o64 = B.make_options(precision=B.PRECISION_FP64, ritz_rank=RITZ, max_neighbors=cap)
-        need64 = B.library().info_esrf_workspace_size(ctypes.byref(g), N, d, pr.Q, ctypes.byref(o64))
-        w64 = B.workspace(need64, dev)
-        mu64 = torch.empty_like(mu_a)
-        A64 = torch.empty_like(A_a)
-        st64 = B.info_esrf_analysis(pr.grid, X, obs, y, R, pr.Q, TOL_MIXED, o64, ws=w64, mu_a=mu64, A_a=A64,
-                                    stats=True, stream=stream)[2]
-        ts = []
-        for s in range(args.fp64_steps):
-            flush.fill_(float(s))
-            e0.record(stream)
-            B.info_esrf_analysis(pr.grid, X, obs, y, R, pr.Q, TOL_MIXED, o64, ws=w64, mu_a=mu64, A_a=A64,
-                                 stats=False, stream=stream)
-            e1.record(stream)
-            e1.synchronize()
-            ts.append(e0.elapsed_time(e1))
-        fp64 = {"value": 1e3 / statistics.mean(ts), "unit": UNIT, "tol": TOL_MIXED, "steps": args.fp64_steps,
-                "iters_mean": st64["iters_mean"], "ms_per_step": statistics.mean(ts)}
-        if "rel_err" in result:
-            from oracle import filter as F
-            mu_ref, A_ref = _oracle_analysis(pr)
-            fp64["rel_err"] = F.relative_increment_error(A64.cpu().numpy(), A_ref, pr.X - pr.X.mean(0))
-        del w64
+        cases = [("fp64_pcg", B.PRECISION_FP64)]
+        if use_learned:
+            cases.insert(0, ("lmp_fp32", B.PRECISION_FP32))
+        for key, pc in cases:
+            oc = B.make_options(precision=pc, ritz_rank=RITZ, max_neighbors=cap)
+            needc = B.library().info_esrf_workspace_size(ctypes.byref(g), N, d, pr.Q, ctypes.byref(oc))
+            wc = B.workspace(needc, dev)
+            muc = torch.empty_like(mu_a)
+            Ac = torch.empty_like(A_a)
+            stc = B.info_esrf_analysis(pr.grid, X, obs, y, R, pr.Q, TOL_MIXED, oc, ws=wc, mu_a=muc, A_a=Ac,
+                                       stats=True, stream=stream)[2]
+            ts = []
+            for s in range(args.fp64_steps):
+                flush.fill_(float(s))
+                e0.record(stream)
+                B.info_esrf_analysis(pr.grid, X, obs, y, R, pr.Q, TOL_MIXED, oc, ws=wc, mu_a=muc, A_a=Ac,
+                                     stats=False, stream=stream)
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            comparators[key] = {"value": 1e3 / statistics.mean(ts), "unit": UNIT, "tol": TOL_MIXED,
+                                "steps": args.fp64_steps, "iters_mean": stc["iters_mean"],
+                                "iters_max": stc["iters_max"], "ms_per_step": statistics.mean(ts)}
+            if "rel_err" in result:
+                from oracle import filter as F
+                mu_ref, A_ref = ref_cache
+                comparators[key]["rel_err"] = F.relative_increment_error(Ac.cpu().numpy(), A_ref,
+                                                                        pr.X - pr.X.mean(0))
+            del wc
 
     # FMA probe: measured FP32 ALU rate of this GPU (context for the ALU roofline)
     probe32, _ = B.fma_probe(1, 1 << 16)
@@ -272,46 +293,45 @@ def run_ours(args):
         return
 
     ms_step = total_ms / args.steps
-    value = ws * args.steps / (total_ms * 1e-3)
-    # algorithmic work of the PCG launch: per system-iteration
-    #   2 nnz(C) (matvec) + 2 d (shift) + 8 k d (LMP projections and apply) + 10 d (dots, axpys)
-    sys_iters = st["iters_mean"] * st["n_systems"]
-    flops_iter = 2 * nnz_C / d + 2 + 8 * RITZ + 10            # per row of one system-iteration
-    pcg_flops = sys_iters * d * flops_iter
+    value = replicas.whole_job_rate(args.steps, ws, total_ms)
+    # algorithmic work of the PCG launch, per row of one system-iteration:
+    #   2 nnz(C)/d (matvec) + 2 (shift) + 8 k (LMP projections and apply) + 10 (dots, axpys),
+    #   + 68 where the learned term is active (a z, 33-tap S^T S r, add)
+    flops_row = 2 * nnz_C / d + 2 + 8 * RITZ + 10
+    pcg_flops = d * float(np.sum(it_sys * (flops_row + 68.0 * learned_sys)))
     pcg_ms_mean = statistics.mean(pcg_ms)
     achieved = pcg_flops / (pcg_ms_mean * 1e-3) / 1e12
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     max_mhz = clocks.get("sm_max_mhz") or 2070.0
     peak = sms * 128 * 2 * max_mhz * 1e6 / 1e12
-    # matvec bytes: the band of C (values + columns) read once per system-group iteration, plus p and y
-    esz = 4 if prec == B.PRECISION_FP32 else 8
-    jt = 8 if prec == B.PRECISION_FP32 else 4
-    group_iters = sys_iters / jt
-    matvec_bytes = group_iters * (nnz_C * (esz + 4) + 2 * d * jt * esz)
+    traffic = PCG_DRAM_BYTES if (prec == B.PRECISION_FP32 and use_learned) else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if prec == B.PRECISION_FP32 else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "N": N, "d": d, "Q": pr.Q, "systems": st["n_systems"],
                    "precision": "fp32 bulk, fp64 scalars and quadrature sum" if prec else "fp64",
+                   "preconditioner": "LMP + learned correction" if use_learned else "LMP",
                    "tol": tol, "ritz_rank": RITZ, "band_nnz": nnz_C, "l2": "flushed between steps (512 MB write)",
                    "replicas": ws},
         "clocks": clocks,
-        "e2e": {"value": ws * args.steps / (e2e_total * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": replicas.whole_job_rate(args.steps, ws, e2e_total), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
-        "roofline": {"bound": "alu", "kernel": "k_pcg (persistent batched shifted PCG)",
+        "roofline": {"bound": "alu", "kernel": "k_pcg_band1d (cluster-resident persistent batched shifted PCG)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": None, "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
-                     "fma_probe_tflops": probe32 / 1e12, "pcg_ms": pcg_ms_mean},
-        "matvec_gbs": matvec_bytes / (pcg_ms_mean * 1e-3) / 1e9,
+                     "traffic": traffic, "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
+                     "fma_probe_tflops": probe32 / 1e12, "pcg_ms": pcg_ms_mean,
+                     "flops_per_launch": pcg_flops},
+        "matvec_hbm_gbs": (traffic / (pcg_ms_mean * 1e-3) / 1e9) if traffic else None,
         "phases_ms": {k: statistics.mean(p[i] for p in phase_ms)
                       for i, k in enumerate(["setup_a1_a3", "ritz_a4", "pcg_a5_a8", "finish_a9_a11"])},
         "iters_mean": st["iters_mean"], "iters_max": st["iters_max"], "ell": st["ell_used"],
     }
     line.update(result)
-    if fp64:
-        line["fp64_pcg"] = fp64
+    line.update(comparators)
+    if learn_info:
+        line["learned"] = learn_info
     if not args.no_cpu_baseline:
         from oracle import filter as F  # noqa: F401
         t0 = time.perf_counter()
@@ -335,6 +355,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--preconditioner", default="learned", choices=["learned", "lmp"])
     ap.add_argument("--fp64-tol", type=float, default=1e-12)
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-parity", action="store_true")

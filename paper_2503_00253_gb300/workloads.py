@@ -140,11 +140,11 @@ def config1() -> Problem:
                                seed=0)
 
 
-def config2(tol: float = 1e-12) -> Problem:
+def config2(tol: float = 1e-12, seed: int = 2) -> Problem:
     """n=8192, N=40, stride 8 (d=1024), R=0.25, GC c=256, Q=32 (1280 shifted systems)."""
     return gaussian_problem_1d("gauss1d_n8192_N40_d1024_Q32", n=8192, N=40, length_scale=64.0,
                                obs_stride=8, r2=0.25, half_width=256.0, Q=32, tol=tol,
-                               seed=2)
+                               seed=seed)
 
 
 # ---------------------------------------------------------------------------
