@@ -197,6 +197,36 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    # CUDA graph of one analysis call (the library's launch sequence, replayed
+    # without host launch overhead); the direct call is the fallback
+    graph, graph_err, graph_launches = None, None, 0
+    if args.graph:
+        B.set_phase_events(opts, None)           # timing events cannot be recorded inside a graph
+        try:
+            cap = torch.cuda.Stream(dev)
+            cap.wait_stream(stream)
+            g_ = torch.cuda.CUDAGraph()
+            n_cap0 = B.launch_count()
+            with torch.cuda.graph(g_, stream=cap):
+                B.info_esrf_analysis(pr.grid, X, obs, y, R, pr.Q, tol, opts, ws=wsp, mu_a=mu_a, A_a=A_a,
+                                     stats=False, stream=cap)
+            stream.wait_stream(cap)
+            graph_launches = B.launch_count() - n_cap0
+            graph = g_
+            for _ in range(args.warmup):
+                with torch.cuda.stream(stream):
+                    graph.replay()
+            torch.cuda.synchronize()
+        except Exception as exc:                  # capture refused: time the direct call
+            graph, graph_err = None, f"{type(exc).__name__}: {exc}"
+            torch.cuda.synchronize()
+
+    def timed_step():
+        if graph is not None:
+            with torch.cuda.stream(stream):
+                graph.replay()
+        else:
+            step()
 
     clock_path = os.path.join(tempfile.gettempdir(), f"clocks_{os.getpid()}.csv")
     sampler = _clock_sampler(clock_path) if rank == 0 else None
@@ -204,19 +234,31 @@ def run_ours(args):
     replicas.barrier()
     torch.cuda.synchronize()
     launches0 = B.launch_count()
-    step_ms, pcg_ms, phase_ms = [], [], [[0.0] * 4 for _ in range(args.steps)]
+    step_ms = []
+    t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for s in range(args.steps):
         flush.fill_(float(s))                       # evicts L2 between timed steps
-        step()
-        events[4].synchronize()
-        step_ms.append(events[0].elapsed_time(events[4]))
-        for i in range(4):
-            phase_ms[s][i] = events[i].elapsed_time(events[i + 1])
-        pcg_ms.append(phase_ms[s][2])
+        t0e.record(stream)
+        timed_step()
+        t1e.record(stream)
+        t1e.synchronize()
+        step_ms.append(t0e.elapsed_time(t1e))
     torch.cuda.synchronize()
     launches = B.launch_count() - launches0
+    if graph is not None:
+        launches = graph_launches * args.steps      # kernels in the graph, replayed once per step
     total_ms = replicas.max_over_ranks(sum(step_ms), dev)
     replicas.barrier()
+    # phase times (and the PCG launch time of the roofline) from direct calls
+    # with events recorded at the phase boundaries
+    B.set_phase_events(opts, events)
+    pcg_ms, phase_ms = [], []
+    for s in range(max(3, min(args.steps, 10))):
+        flush.fill_(float(s))
+        step()
+        events[4].synchronize()
+        phase_ms.append([events[i].elapsed_time(events[i + 1]) for i in range(4)])
+        pcg_ms.append(phase_ms[-1][2])
     B.set_phase_events(opts, None)
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
@@ -313,7 +355,8 @@ def run_ours(args):
                    "precision": "fp32 bulk, fp64 scalars and quadrature sum" if prec else "fp64",
                    "preconditioner": "LMP + learned correction" if use_learned else "LMP",
                    "tol": tol, "ritz_rank": RITZ, "band_nnz": nnz_C, "l2": "flushed between steps (512 MB write)",
-                   "replicas": ws},
+                   "replicas": ws, "launch": "cuda graph of the analysis call" if graph is not None else
+                   "direct call", **({"graph_error": graph_err} if graph_err else {})},
         "clocks": clocks,
         "e2e": {"value": replicas.whole_job_rate(args.steps, ws, e2e_total), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
@@ -324,6 +367,7 @@ def run_ours(args):
                      "fma_probe_tflops": probe32 / 1e12, "pcg_ms": pcg_ms_mean,
                      "flops_per_launch": pcg_flops},
         "matvec_hbm_gbs": (traffic / (pcg_ms_mean * 1e-3) / 1e9) if traffic else None,
+        "direct_call_ms": statistics.mean(sum(p) for p in phase_ms),
         "phases_ms": {k: statistics.mean(p[i] for p in phase_ms)
                       for i, k in enumerate(["setup_a1_a3", "ritz_a4", "pcg_a5_a8", "finish_a9_a11"])},
         "iters_mean": st["iters_mean"], "iters_max": st["iters_max"], "ell": st["ell_used"],
@@ -356,6 +400,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--preconditioner", default="learned", choices=["learned", "lmp"])
+    ap.add_argument("--graph", type=int, default=1, help="replay the analysis as a CUDA graph (0: direct calls)")
     ap.add_argument("--fp64-tol", type=float, default=1e-12)
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-parity", action="store_true")

@@ -113,6 +113,7 @@ void carve_problem(Carver& cv, ProblemDev& pr, const info_esrf_options& o) {
   const int64_t n = pr.n, N = pr.N, d = pr.d;
   const int l = pr.l, k = pr.kR;
   pr.mu = cv.take<double>(n * 8);
+  pr.d2tab = cv.take<double>((size_t)(pr.grid.ext[0] + pr.grid.ext[1] + pr.grid.ext[2]) * 8);
   pr.Zt = cv.take<void>(n * N * esz);
   pr.W = cv.take<void>(d * N * esz);
   pr.rinv = cv.take<double>(d * 8);
@@ -142,6 +143,7 @@ void carve_problem(Carver& cv, ProblemDev& pr, const info_esrf_options& o) {
   pr.Vbar = cv.take<double>((size_t)d * (N + 1) * 8);
   pr.VbarT = cv.take<void>((size_t)d * (N + 1) * esz);
   pr.learn_coef = cv.take<float>((size_t)(pr.Q + 1) * kLearnOut * 4);
+  pr.learn_T = cv.take<float>((size_t)(pr.Q + 1) * kLearnT * 4);
 }
 
 // Builds the host table for a batch; with ws == nullptr only sizes it.
@@ -231,6 +233,44 @@ int status_to_code(int32_t bits) {
   return INFO_ESRF_OK;
 }
 
+// Side stream and events, per host thread and device, for the work that
+// overlaps the main sequence: the quadrature and the state-obs band run while
+// the Ritz pairs are computed.  Created on first use and kept for the life of
+// the thread (like a library handle).
+struct AuxStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t mid = nullptr, jq = nullptr, jb = nullptr;
+};
+
+AuxStream* aux_stream() {
+  constexpr int kMaxDev = 64;
+  static thread_local AuxStream aux[kMaxDev];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  AuxStream& a = aux[dev];
+  if (!a.s) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t e[3] = {nullptr, nullptr, nullptr};
+    bool ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
+    for (int i = 0; i < 3 && ok; ++i) ok = cudaEventCreateWithFlags(&e[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      for (int i = 0; i < 3; ++i)
+        if (e[i]) cudaEventDestroy(e[i]);
+      if (s) cudaStreamDestroy(s);
+      return nullptr;
+    }
+    a.s = s;
+    a.mid = e[0];
+    a.jq = e[1];
+    a.jb = e[2];
+  }
+  return &a;
+}
+
 int run_batch(const info_esrf_problem* probs, int32_t count, const info_esrf_options* opt_in, void* ws,
               size_t ws_bytes, void* stream, info_esrf_stats* stats) {
   info_esrf_options o;
@@ -255,14 +295,32 @@ int run_batch(const info_esrf_problem* probs, int32_t count, const info_esrf_opt
   mark(0);
   launch_prepare(tab, dtab, st);
   launch_anomalies(tab, dtab, st);
-  launch_bands(tab, dtab, st);
-  launch_quadrature(tab, dtab, st);
+  launch_band_obs(tab, dtab, st);
+  // the quadrature and the state-obs band overlap the Ritz stage on a side
+  // stream, which rejoins before the first use of each
+  AuxStream* aux = aux_stream();
+  if (aux) {
+    cudaEventRecord(aux->mid, st);
+    cudaStreamWaitEvent(aux->s, aux->mid, 0);
+    launch_quadrature(tab, dtab, aux->s);
+    cudaEventRecord(aux->jq, aux->s);
+    launch_band_state(tab, dtab, aux->s);
+    cudaEventRecord(aux->jb, aux->s);
+  } else {
+    launch_quadrature(tab, dtab, st);
+    launch_band_state(tab, dtab, st);
+  }
   mark(1);
   launch_ritz(tab, dtab, st);
+  if (aux) cudaStreamWaitEvent(st, aux->jq, 0);
   launch_learn_coef(tab, dtab, st);
   mark(2);
-  if (launch_pcg(tab, dtab, counter, scratch, scratch_bytes, sms, st) != 0) return INFO_ESRF_ERR_WORKSPACE;
+  if (launch_pcg(tab, dtab, counter, scratch, scratch_bytes, sms, st) != 0) {
+    if (aux) cudaStreamWaitEvent(st, aux->jb, 0);
+    return INFO_ESRF_ERR_WORKSPACE;
+  }
   mark(3);
+  if (aux) cudaStreamWaitEvent(st, aux->jb, 0);
   launch_finish(tab, dtab, st);
   if (o.system_iters && count == 1)
     cudaMemcpyAsync(o.system_iters, tab.p[0].iters, (size_t)tab.p[0].nsys * sizeof(int32_t),

@@ -68,6 +68,33 @@ __device__ __forceinline__ double gaspari_cohn(double z) {
   return 0.0;
 }
 
+// r^2 from the per-axis table tab[off_ax + |a_ax - b_ax|] = (dist_ax / c_ax)^2,
+// off = (0, ext0, ext0 + ext1); filled by k_dist_table with axis_distance.
+__device__ __forceinline__ double scaled_r2_tab(const GridDev& g, const double* tab, const Coord3& a,
+                                                const Coord3& b) {
+  double r2 = 0.0;
+  const int64_t ca[3] = {a.x, a.y, a.z};
+  const int64_t cb[3] = {b.x, b.y, b.z};
+  int64_t off = 0;
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    if (g.ext[ax] > 1) {
+      const int64_t delta = ca[ax] > cb[ax] ? ca[ax] - cb[ax] : cb[ax] - ca[ax];
+      r2 += tab[off + delta];
+    }
+    off += g.ext[ax];
+  }
+  return r2;
+}
+
+// Gaspari-Cohn in single precision (the FP32 path's band values).
+__device__ __forceinline__ float gaspari_cohn_f(float z) {
+  z = fabsf(z);
+  if (z <= 1.f) return (((-0.25f * z + 0.5f) * z + 0.625f) * z - 5.f / 3.f) * z * z + 1.f;
+  if (z < 2.f) return ((((z / 12.f - 0.5f) * z + 0.625f) * z + 5.f / 3.f) * z - 5.f) * z + 4.f - (2.f / 3.f) / z;
+  return 0.f;
+}
+
 // First index i in sorted a[lo, hi) with a[i] >= key.
 __device__ __forceinline__ int64_t lower_bound_i64(const int64_t* a, int64_t lo, int64_t hi, int64_t key) {
   while (lo < hi) {

@@ -13,6 +13,7 @@ constexpr int kMaxK = 24;             // Ritz vectors used by the preconditioner
 constexpr int kLearnH = 8;            // half-width of the learned stencil
 constexpr int kLearnTaps = 2 * kLearnH + 1;
 constexpr int kLearnOut = 1 + kLearnTaps;  // log a and the taps
+constexpr int kLearnT = 4 * kLearnH + 1;   // taps of S^T S
 constexpr int kLearnParams = 1810;    // network parameters (see learn.cu)
 constexpr int kThreads = 256;         // CTA size of the persistent PCG kernel
 
@@ -57,6 +58,7 @@ struct ProblemDev {
   double* A_a;          // [N][n]
   // workspace
   double* mu;           // [n]
+  double* d2tab;        // [ext0 + ext1 + ext2] (axis distance / half-width)^2 by index offset
   void* Zt;             // [n][N] T normalized anomalies, state-major
   void* W;              // [d][N] T observed anomalies W = H Z
   double* rinv;         // [d] R^-1/2
@@ -85,6 +87,7 @@ struct ProblemDev {
   const float* learned_model;   // network parameters, NULL: none
   double learned_max_shift;     // > 0: learned term only for sigma <= this
   float* learn_coef;            // [Q + 1][kLearnOut]: a_q, taps (slot Q: mean system)
+  float* learn_T;               // [Q + 1][kLearnT]: taps of T_q = S_q^T S_q, offsets -2h..2h
   // batched PCG
   // Systems are numbered hardest first: sid 0 is the mean system (shift 1)
   // when requested, then the perturbation systems node-major,
@@ -111,6 +114,8 @@ struct ProblemTable {
 void launch_prepare(const ProblemTable& tab, ProblemDev* dtab, cudaStream_t st);
 void launch_anomalies(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st);
 void launch_bands(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st);
+void launch_band_obs(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st);
+void launch_band_state(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st);
 void launch_quadrature(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st);
 void launch_ritz(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st);
 int launch_pcg(const ProblemTable& tab, const ProblemDev* dtab, int32_t* counter, void* scratch,

@@ -36,11 +36,12 @@ static_assert(kOB3 + kLearnOut == kLearnParams, "parameter layout");
 }  // namespace
 
 __device__ __forceinline__ void learn_features(double sigma, double mean_diag, double gersh, float* phi) {
-  const float ls = (float)(log(sigma) / 5.0);
+  // single-precision logarithms (features of a small network; FP64 is slow here)
+  const float ls = logf((float)sigma) * 0.2f;
   phi[0] = ls;
   phi[1] = ls * ls;
-  phi[2] = (float)(log(mean_diag > 1e-30 ? mean_diag : 1e-30) / 5.0);
-  phi[3] = (float)(log(gersh > 1e-30 ? gersh : 1e-30) / 10.0);
+  phi[2] = logf(fmaxf((float)mean_diag, 1e-30f)) * 0.2f;
+  phi[3] = logf(fmaxf((float)gersh, 1e-30f)) * 0.1f;
 }
 
 // Forward pass by one thread (inference: a handful of shifts).
@@ -63,26 +64,66 @@ __device__ void learn_forward_thread(const float* th, const float* phi, float* o
   }
 }
 
+// Forward pass by one warp (lane i computes hidden unit i; kHid = 32); the
+// same sums in the same order as learn_forward_thread.  Lane o < kLearnOut
+// returns out[o].
+__device__ __forceinline__ float learn_forward_warp(const float* th, const float* phi, int lane) {
+  static_assert(kHid == 32, "one hidden unit per lane");
+  float a = th[kOB1 + lane];
+  for (int c = 0; c < kIn; ++c) a = fmaf(th[kOW1 + lane * kIn + c], phi[c], a);
+  const float h1 = tanhf(a);
+  float b = th[kOB2 + lane];
+#pragma unroll 8
+  for (int j = 0; j < kHid; ++j) b = fmaf(th[kOW2 + lane * kHid + j], __shfl_sync(0xffffffffu, h1, j), b);
+  const float h2 = tanhf(b);
+  const int o = lane < kLearnOut ? lane : 0;
+  float r = th[kOB3 + o];
+#pragma unroll 8
+  for (int j = 0; j < kHid; ++j) r = fmaf(th[kOW3 + o * kHid + j], __shfl_sync(0xffffffffu, h2, j), r);
+  return r;
+}
+
 // Per-shift coefficients of one problem: coef[q] = (a_q, w_q[17]) for q < Q,
-// slot Q for the mean system (sigma = 1).
+// slot Q for the mean system (sigma = 1).  One warp per shift.
 __global__ void k_learn_coef_problem(const ProblemDev* tab) {
   const ProblemDev& pr = tab[blockIdx.y];
   if (!pr.learned_model) return;
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (q > pr.Q) return;
   const double sigma = q < pr.Q ? pr.s[q] + 1.0 : 1.0;
   float* cq = pr.learn_coef + (int64_t)q * kLearnOut;
+  float* tq = pr.learn_T + (int64_t)q * kLearnT;
   if (pr.learned_max_shift > 0.0 && sigma > pr.learned_max_shift) {
-    for (int j = 0; j < kLearnOut; ++j) cq[j] = 0.f;   // a = 0: this shift uses P_q^-1 alone
+    if (lane < kLearnOut) cq[lane] = 0.f;   // a = 0: this shift uses P_q^-1 alone
+    tq[lane] = 0.f;
+    if (lane == 0) tq[kLearnT - 1] = 0.f;
     return;
   }
-  float phi[kIn], out[kLearnOut];
-  learn_features(sigma, pr.scal[4] / (double)pr.d, pr.scal[0], phi);
-  learn_forward_thread(pr.learned_model, phi, out);
-  float* c = pr.learn_coef + (int64_t)q * kLearnOut;
-  const float rs = (float)(1.0 / sqrt(sigma));
-  c[0] = expf(out[0]) * rs * rs;
-  for (int j = 1; j < kLearnOut; ++j) c[j] = out[j] * rs;
+  float phi[kIn];
+  if (lane == 0) learn_features(sigma, pr.scal[4] / (double)pr.d, pr.scal[0], phi);
+#pragma unroll
+  for (int c = 0; c < kIn; ++c) phi[c] = __shfl_sync(0xffffffffu, phi[c], 0);
+  const float out = learn_forward_warp(pr.learned_model, phi, lane);
+  const float rs = rsqrtf((float)sigma);
+  if (lane == 0) cq[0] = expf(out) * rs * rs;
+  else if (lane < kLearnOut) cq[lane] = out * rs;
+  // T = S^T S: t[D] = sum_u w[u] w[u - D], D = -2h..2h; pass 0 gives D = lane - 2h,
+  // pass 1 gives D = lane + 32 - 2h (only D = 2h, on lane 0, is in range)
+  const float w = lane >= 1 && lane < kLearnOut ? out * rs : 0.f;   // lane 1 + u holds w[u]
+#pragma unroll
+  for (int pass = 0; pass < 2; ++pass) {
+    const int Dl = lane + 32 * pass - 2 * kLearnH;
+    float acc = 0.f;
+    for (int u = 0; u < kLearnTaps; ++u) {
+      const float wu = __shfl_sync(0xffffffffu, w, 1 + u);
+      const int v2 = u - Dl;
+      const bool in = v2 >= 0 && v2 < kLearnTaps;
+      const float wv = __shfl_sync(0xffffffffu, w, 1 + (in ? v2 : 0));
+      if (in) acc = fmaf(wu, wv, acc);
+    }
+    if (Dl <= 2 * kLearnH) tq[Dl + 2 * kLearnH] = acc;
+  }
 }
 
 void launch_learn_coef(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st) {
@@ -93,7 +134,8 @@ void launch_learn_coef(const ProblemTable& tab, const ProblemDev* dtab, cudaStre
     any |= tab.p[i].learned_model != nullptr;
   }
   if (!any) return;
-  k_learn_coef_problem<<<dim3((qmax + 1 + 63) / 64, tab.count), 64, 0, st>>>(dtab);
+  constexpr int kWarps = 8;
+  k_learn_coef_problem<<<dim3((qmax + 1 + kWarps - 1) / kWarps, tab.count), 32 * kWarps, 0, st>>>(dtab);
   note_launches(1);
 }
 

@@ -304,15 +304,8 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       if (learn_ok && !retry && cf[0] > 0.f) {
         L.learn[j] = 1;
         L.la[j] = cf[0];
-        // T = S^T S: t[D] = sum_u w[u] w[u - D], D = -kTH..kTH
-        for (int D = -kTH; D <= kTH; ++D) {
-          float acc = 0.f;
-          for (int u = 0; u < kLearnTaps; ++u) {
-            const int v2 = u - D;
-            if (v2 >= 0 && v2 < kLearnTaps) acc = fmaf(cf[1 + u], cf[1 + v2], acc);
-          }
-          L.lt[j][D + kTH] = acc;
-        }
+        const float* tT = pr.learn_T + (int64_t)(q < 0 ? pr.Q : q) * kLearnT;   // taps of S^T S
+        for (int u = 0; u < kTT; ++u) L.lt[j][u] = tT[u];
       }
     }
     L.sigf[j] = (float)L.sigma[j];
@@ -397,18 +390,25 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       }
     }
     {
-      const int h = lane >> 4;
+      // reduce-scatter over the 16 rows of each half-warp: lane 16 h + r ends
+      // with the float-float sum of lane j = 16 h + r (15 exchanges, not 64)
+      float vh[16], vl[16];
 #pragma unroll
-      for (int jj = 0; jj < 16; ++jj) {
-        float hi = pp[jj].hi, lo = pp[jj].lo;
+      for (int jj = 0; jj < 16; ++jj) { vh[jj] = pp[jj].hi; vl[jj] = pp[jj].lo; }
 #pragma unroll
-        for (int o = 8; o > 0; o >>= 1) {
-          const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
-          const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-          ff_merge(hi, lo, h2, l2);
+      for (int off = 8; off >= 1; off >>= 1) {
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < off; ++i) {
+          const float sh = up ? vh[i] : vh[i + off], sl = up ? vl[i] : vl[i + off];
+          float kh = up ? vh[i + off] : vh[i], kl = up ? vl[i + off] : vl[i];
+          ff_merge(kh, kl, __shfl_xor_sync(0xffffffffu, sh, off), __shfl_xor_sync(0xffffffffu, sl, off));
+          vh[i] = kh;
+          vl[i] = kl;
         }
-        if ((lane & 15) == 0) { s_wpap[warp][16 * h + jj][0] = hi; s_wpap[warp][16 * h + jj][1] = lo; }
       }
+      s_wpap[warp][lane][0] = vh[0];
+      s_wpap[warp][lane][1] = vl[0];
     }
     __syncthreads();
     if (tid < kJ * CS) {
@@ -425,11 +425,11 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       const int j = tid;
       float hi = 0.f, lo = 0.f;
       for (int c = 0; c < CS; ++c) ff_merge(hi, lo, s_pap_in[c][j][0], s_pap_in[c][j][1]);
-      const double pAp = (double)hi + (double)lo;
+      const float pAp = hi + lo;          // alpha is FP32: no FP64 division here
       float alpha = 0.f;
       if (L.state[j] == kActive) {
-        if (pAp > 0.0 && isfinite(pAp)) {
-          alpha = (float)(L.rho[j] / pAp);
+        if (pAp > 0.f && isfinite(pAp)) {
+          alpha = (float)L.rho[j] / pAp;
           L.it[j] += 1;
         } else {
           L.fin[j] = 2;   // breakdown: finished with a flag
@@ -616,10 +616,11 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       const int j = tid;
       const int st = L.state[j];
       const double rr = L.rr[j];
-      // rho = r^T M r = a r^T P^-1 r + r^T S^T S r
-      double rpr = rr;
-      for (int m = 0; m < k; ++m) rpr += -(double)L.g[j][m] * (double)L.t[j][m] + (double)L.f[j][m] * (double)L.c[j][m];
-      const double rho = (double)L.la[j] * rpr + L.rtr[j];
+      // rho = r^T M r = a r^T P^-1 r + r^T S^T S r; the k-term LMP correction
+      // to r^T r is summed in FP32 (it shapes the preconditioner only)
+      float corr = 0.f;
+      for (int m = 0; m < k; ++m) corr = fmaf(L.f[j][m], L.c[j][m], fmaf(-L.g[j][m], L.t[j][m], corr));
+      const double rho = (double)L.la[j] * (rr + (double)corr) + L.rtr[j];
       if (st == kStart) {
         L.bn2[j] = rr;
         if (!(rr > 0.0) || !isfinite(rr)) {
@@ -637,7 +638,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
         if (done) {
           if (L.fin[j] == 0) L.fin[j] = 1;
         } else {
-          L.beta[j] = (float)(rho / L.rho[j]);
+          L.beta[j] = (float)rho / (float)L.rho[j];
           L.rho[j] = rho;
         }
       }

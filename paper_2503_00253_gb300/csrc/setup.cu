@@ -10,6 +10,8 @@
 // path).  Sums that feed scalars use DotAcc<T> (float-float for float).
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -128,6 +130,20 @@ void launch_anomalies(const ProblemTable& tab, const ProblemDev* dtab, cudaStrea
 // in increasing candidate order to the ELL row (column-major: entry e of row
 // a at e * rows + a).
 // ---------------------------------------------------------------------------
+// Per-axis table of (axis distance / half-width)^2 for every index offset, so
+// that the band kernels need no transcendental per candidate pair.
+__global__ void k_dist_table(const ProblemDev* tab) {
+  const ProblemDev& pr = tab[blockIdx.y];
+  const GridDev& g = pr.grid;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t total = g.ext[0] + g.ext[1] + g.ext[2];
+  if (i >= total) return;
+  const int ax = i < g.ext[0] ? 0 : (i < g.ext[0] + g.ext[1] ? 1 : 2);
+  const int64_t delta = i - (ax == 0 ? 0 : ax == 1 ? g.ext[0] : g.ext[0] + g.ext[1]);
+  const double dd = axis_distance(g, ax, 0, delta) * g.inv_c[ax];
+  pr.d2tab[i] = dd * dd;
+}
+
 template <typename T, bool OBS_ROWS>
 __global__ void k_band(const ProblemDev* tab) {
   const ProblemDev& pr = tab[blockIdx.y];
@@ -156,13 +172,14 @@ __global__ void k_band(const ProblemDev* tab) {
       bool keep = false;
       if (b < b1) {
         const Coord3 bc = flat_to_coord(g, pr.obs[b]);
-        const double r = scaled_distance(g, pc, bc);
-        if (r < 2.0) {
+        const double r2 = scaled_r2_tab(g, pr.d2tab, pc, bc);
+        if (r2 < 4.0) {
           keep = true;
           DotAcc<T> acc;
           const T* wb = W + b * N;
           for (int64_t k = 0; k < N; ++k) acc.add_prod(src[k], wb[k]);
-          v = gaspari_cohn(r) * acc.value();
+          const double gc = sizeof(T) == 8 ? gaspari_cohn(sqrt(r2)) : (double)gaspari_cohn_f(sqrtf((float)r2));
+          v = gc * acc.value();
           if (OBS_ROWS) v *= ra * pr.rinv[b];
         }
       }
@@ -192,21 +209,35 @@ __global__ void k_band(const ProblemDev* tab) {
   }
 }
 
-void launch_bands(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st) {
-  int64_t nmax = 0, dmax = 0;
+// Band of C (obs rows), with the distance table it needs; the table must be
+// complete before launch_band_state runs too.
+void launch_band_obs(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st) {
+  int64_t dmax = 0, emax = 0;
   for (int i = 0; i < tab.count; ++i) {
-    nmax = tab.p[i].n > nmax ? tab.p[i].n : nmax;
+    const GridDev& g = tab.p[i].grid;
     dmax = tab.p[i].d > dmax ? tab.p[i].d : dmax;
+    emax = std::max<int64_t>(emax, g.ext[0] + g.ext[1] + g.ext[2]);
   }
+  k_dist_table<<<dim3((unsigned)((emax + 255) / 256), tab.count), 256, 0, st>>>(dtab); note_launches(1);
   dim3 go((unsigned)((dmax * 32 + 255) / 256), tab.count);
+  if (tab.p[0].precision == 0) k_band<double, true><<<go, 256, 0, st>>>(dtab);
+  else k_band<float, true><<<go, 256, 0, st>>>(dtab);
+  note_launches(1);
+}
+
+// Band of Sxh (state rows); needed only by the state update.
+void launch_band_state(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st) {
+  int64_t nmax = 0;
+  for (int i = 0; i < tab.count; ++i) nmax = tab.p[i].n > nmax ? tab.p[i].n : nmax;
   dim3 gx((unsigned)((nmax * 32 + 255) / 256), tab.count);
-  if (tab.p[0].precision == 0) {
-    k_band<double, true><<<go, 256, 0, st>>>(dtab); note_launches(1);
-    k_band<double, false><<<gx, 256, 0, st>>>(dtab); note_launches(1);
-  } else {
-    k_band<float, true><<<go, 256, 0, st>>>(dtab); note_launches(1);
-    k_band<float, false><<<gx, 256, 0, st>>>(dtab); note_launches(1);
-  }
+  if (tab.p[0].precision == 0) k_band<double, false><<<gx, 256, 0, st>>>(dtab);
+  else k_band<float, false><<<gx, 256, 0, st>>>(dtab);
+  note_launches(1);
+}
+
+void launch_bands(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st) {
+  launch_band_obs(tab, dtab, st);
+  launch_band_state(tab, dtab, st);
 }
 
 // Counts neighbours to size the bands: out2[0] = max obs per obs row,
@@ -408,29 +439,48 @@ __global__ void k_ritz_omega(const ProblemDev* tab) {
   ritz_buf<T>(pr, 0)[i] = to_t<T>(philox_normal(pr.seed, (uint64_t)(j * pr.d + a)));
 }
 
-// dst = C src, one thread per (row, column); the band loop is unrolled so that
-// several entries are in flight.
+// dst = C src: one warp per row, lanes over the row's band entries; each lane
+// accumulates all l columns of its entries, then a butterfly reduce-scatter
+// leaves column j's sum in lane j.
 template <typename T>
 __global__ void k_ritz_matvec(const ProblemDev* tab, int src) {
   const ProblemDev& pr = tab[blockIdx.y];
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int l = pr.l;
-  if (l <= 0 || i >= pr.d * l) return;
-  const int64_t d = pr.d, a = i / l, j = i % l;
+  const int lane = threadIdx.x & 31;
+  const int64_t a = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (l <= 0 || a >= pr.d) return;
+  const int64_t d = pr.d;
   const T* __restrict__ V = ritz_buf<T>(pr, src);
   T* Y = ritz_buf<T>(pr, 1 - src);
   const T* __restrict__ val = tp<const T>(pr.oo_val);
   const int32_t* __restrict__ col = pr.oo_col;
-  T acc0 = T(0), acc1 = T(0);
   const int nnz = pr.oo_nnz[a];
-  int e = 0;
-#pragma unroll 4
-  for (; e + 1 < nnz; e += 2) {
-    acc0 += val[(int64_t)e * d + a] * V[(int64_t)col[(int64_t)e * d + a] * l + j];
-    acc1 += val[(int64_t)(e + 1) * d + a] * V[(int64_t)col[(int64_t)(e + 1) * d + a] * l + j];
+  T acc[32];
+#pragma unroll
+  for (int m = 0; m < 32; ++m) acc[m] = T(0);
+  const bool vec4 = sizeof(T) == 4 && (l & 3) == 0;
+  for (int e = lane; e < nnz; e += 32) {
+    const T c = val[(int64_t)e * d + a];
+    const T* vr = V + (int64_t)col[(int64_t)e * d + a] * l;
+    if (vec4) {
+#pragma unroll
+      for (int m4 = 0; m4 < 8; ++m4) {
+        if (4 * m4 < l) {
+          const float4 v = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(vr) + 4 * m4);
+          acc[4 * m4 + 0] += c * (T)v.x;
+          acc[4 * m4 + 1] += c * (T)v.y;
+          acc[4 * m4 + 2] += c * (T)v.z;
+          acc[4 * m4 + 3] += c * (T)v.w;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < 32; ++m)
+        if (m < l) acc[m] += c * vr[m];
+    }
   }
-  if (e < nnz) acc0 += val[(int64_t)e * d + a] * V[(int64_t)col[(int64_t)e * d + a] * l + j];
-  Y[a * l + j] = acc0 + acc1;
+  const T sum = warp_reduce_scatter32<T>(acc, lane);
+  if (lane < l) Y[a * l + lane] = sum;
 }
 
 // G[i][j] = sum_a A[a][i] B[a][j] (FP64 result), one block per entry.
@@ -458,39 +508,68 @@ __global__ void k_ritz_gram(const ProblemDev* tab, int srcA, int srcB, int sym) 
 }
 
 // X_dst = X_src R^-1 with G = R^T R the Cholesky factorization of the Gram
-// matrix in Gm (formed redundantly per block by warp 0, lanes over columns).
-// A non-positive pivot zeroes that column (rank loss) and flags kStatEigFail.
+// matrix in Gm.  Right-looking factorization by warp 0 (lane c owns column c):
+// each step takes the pivot's reciprocal square root (FP32 seed, two Newton
+// steps in FP64), scales row j and updates the trailing upper triangle, so the
+// dependent FP64 chain is a few operations per column.  A non-positive pivot
+// zeroes that column (rank loss) and flags kStatEigFail.  R goes to shared
+// memory in the bulk type for the triangular solve, one thread per row.
 template <typename T>
 __global__ void k_ritz_orth(const ProblemDev* tab, int src) {
   const ProblemDev& pr = tab[blockIdx.y];
   const int l = pr.l;
   if (l <= 0) return;
-  __shared__ double Rs[kMaxRitz][kMaxRitz + 1];
-  __shared__ double Gs[kMaxRitz][kMaxRitz + 1];
-  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
-    Gs[e / l][e % l] = pr.Gm[e];
-    Rs[e / l][e % l] = 0.0;
-  }
+  __shared__ double G[kMaxRitz][kMaxRitz + 1];
+  __shared__ double Rrow[kMaxRitz];
+  __shared__ double s_inv;
+  __shared__ T Rt[kMaxRitz][kMaxRitz + 1];
+  __shared__ T rinv[kMaxRitz];
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) G[e / l][e % l] = pr.Gm[e];
   __syncthreads();
-  if (threadIdx.x < 32) {
-    const int c = threadIdx.x;
-    double tr = 0.0;
-    for (int i = 0; i < l; ++i) tr += Gs[i][i];
-    const double tiny = 1e-28 * (tr > 0 ? tr : 1.0);
+  // FP64 work is spread over four warps (one per SM sub-partition): the pivot by
+  // warp 0, the row scaling and the trailing update of the upper triangle by all.
+  constexpr int kCT = 128;
+  const int t = threadIdx.x;
+  if (t < kCT) {
+    double tiny = 0.0;
+    if (t < 32) {
+      double tr = t < l ? G[t][t] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+      tiny = 1e-28 * (tr > 0 ? tr : 1.0);
+    }
     for (int j = 0; j < l; ++j) {
-      // pivot (all lanes compute it redundantly from shared values)
-      double sjj = Gs[j][j];
-      for (int k = 0; k < j; ++k) sjj -= Rs[k][j] * Rs[k][j];
-      const bool ok = sjj > tiny;
-      const double rjj = ok ? sqrt(sjj) : 0.0;
-      if (c > j && c < l) {
-        double t = Gs[j][c];
-        for (int k = 0; k < j; ++k) t -= Rs[k][j] * Rs[k][c];
-        Rs[j][c] = ok ? t / rjj : 0.0;
+      if (t < 32) {
+        // 1 / sqrt(G_jj): FP32 seed, one Newton step in FP64 (relative error ~1e-14)
+        const double gjj = G[j][j];
+        const bool ok = gjj > tiny;
+        double inv = 0.0;
+        if (ok) {
+          const double y = (double)rsqrtf((float)gjj);
+          inv = y * fma(-0.5 * gjj * y, y, 1.5);
+        }
+        if (t == 0) {
+          s_inv = inv;
+          Rt[j][j] = to_t<T>(gjj * inv);
+          rinv[j] = to_t<T>(inv);
+          if (!ok && blockIdx.x == 0) atomicOr(&pr.status[0], kStatEigFail);
+        }
       }
-      if (c == j) Rs[j][j] = rjj;
-      if (!ok && c == 0 && blockIdx.x == 0) atomicOr(&pr.status[0], kStatEigFail);
-      __syncwarp();
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      const double inv = s_inv;
+      for (int c = j + 1 + t; c < l; c += kCT) {
+        const double r = G[j][c] * inv;
+        Rrow[c] = r;
+        Rt[j][c] = to_t<T>(r);
+      }
+      if (t < j) Rt[j][t] = T(0);
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      const int mrem = l - 1 - j;
+      for (int e = t; e < mrem * mrem; e += kCT) {
+        const int c2 = j + 1 + e / mrem, c = j + 1 + e % mrem;
+        if (c2 <= c) G[c2][c] -= Rrow[c2] * Rrow[c];
+      }
+      asm volatile("bar.sync 1, 128;" ::: "memory");
     }
   }
   __syncthreads();
@@ -504,8 +583,8 @@ __global__ void k_ritz_orth(const ProblemDev* tab, int src) {
     if (j < l) {
       T t = X[a * l + j];
 #pragma unroll
-      for (int k = 0; k < j; ++k) t -= row[k] * to_t<T>(Rs[k][j]);
-      row[j] = Rs[j][j] > 0.0 ? t / to_t<T>(Rs[j][j]) : T(0);
+      for (int k = 0; k < j; ++k) t -= row[k] * Rt[k][j];
+      row[j] = t * rinv[j];
     } else {
       row[j] = T(0);
     }
@@ -516,7 +595,32 @@ __global__ void k_ritz_orth(const ProblemDev* tab, int src) {
 }
 
 // Element-parallel cyclic Jacobi on B = sym(Om^T C Om) (Gm holds Om^T (C Om)),
-// one thread per entry.  Output: ev (descending) and Rm (eigenvectors).
+// one thread per entry.  The round-robin pairing of every round is tabulated
+// once; a round is then two barriers (rotations, then the two-sided update).
+// Output: ev (descending) and Rm (eigenvectors).
+template <typename T>
+__device__ __forceinline__ void jacobi_rotation(T app, T aqq, T apq, T& c, T& s) {
+  c = T(1);
+  s = T(0);
+  if (apq != T(0)) {
+    const T theta = (aqq - app) / (T(2) * apq);
+    const T t = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
+    c = T(1) / sqrt(t * t + T(1));
+    s = t * c;
+  }
+}
+template <>
+__device__ __forceinline__ void jacobi_rotation<float>(float app, float aqq, float apq, float& c, float& s) {
+  c = 1.f;
+  s = 0.f;
+  if (apq != 0.f) {
+    const float theta = __fdividef(aqq - app, 2.f * apq);
+    const float t = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.f)));
+    c = rsqrtf(fmaf(t, t, 1.f));
+    s = t * c;
+  }
+}
+
 template <typename T>
 __global__ void k_ritz_jacobi(const ProblemDev* tab) {
   const ProblemDev& pr = tab[blockIdx.x];
@@ -524,23 +628,30 @@ __global__ void k_ritz_jacobi(const ProblemDev* tab) {
   if (l <= 0) return;
   __shared__ T A[2][kMaxRitz][kMaxRitz + 1];
   __shared__ T V[2][kMaxRitz][kMaxRitz + 1];
-  __shared__ T cs[kMaxRitz][2];        // (c, s) of the pair containing index i, per index
-  __shared__ int partner[kMaxRitz];
-  __shared__ int first[kMaxRitz];      // 1 if i is the lower index of its pair
-  __shared__ double off_s, tot_s;
+  __shared__ T cs[kMaxRitz][2];                 // (c, s) of the pair containing index x
+  __shared__ int8_t partner[kMaxRitz][kMaxRitz];  // [round][x]
+  __shared__ T red_off[kMaxRitz], red_tot[kMaxRitz];
+  __shared__ int go_on;
   const int tid = threadIdx.x;
   const int i = tid / kMaxRitz, j = tid % kMaxRitz;
   const bool mine = i < l && j < l;
+  const int m = (l + 1) & ~1;   // even count; index l is a dummy when l is odd
   if (mine) {
     const double b = 0.5 * (pr.Gm[i * l + j] + pr.Gm[j * l + i]);
     A[0][i][j] = to_t<T>(b);
     V[0][i][j] = i == j ? T(1) : T(0);
   }
-  const int m = (l + 1) & ~1;   // even count; index l is a dummy when l is odd
+  // circle method: position 0 fixed, the others rotate by one per round
+  if (i < m - 1 && j < m) {
+    const int round = i, x = j;
+    const int pos = x == 0 ? 0 : ((x - 1 - round) % (m - 1) + (m - 1)) % (m - 1) + 1;
+    const int ppos = m - 1 - pos;
+    partner[round][x] = (int8_t)(ppos == 0 ? 0 : ((ppos - 1 + round) % (m - 1)) + 1);
+  }
   int cur = 0;
   __syncthreads();
-  __shared__ T red_off[kMaxRitz], red_tot[kMaxRitz];
   const int max_sweeps = sizeof(T) == 4 ? 12 : 30;
+  const T eps = sizeof(T) == 4 ? T(1e-11) : T(1e-30);
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     {
       // off-diagonal and total squared norms: warp i holds row i
@@ -551,42 +662,26 @@ __global__ void k_ritz_jacobi(const ProblemDev* tab) {
         v += __shfl_xor_sync(0xffffffffu, v, sh);
         o += __shfl_xor_sync(0xffffffffu, o, sh);
       }
-      if ((tid & 31) == 0) { red_tot[i] = v; red_off[i] = o; }
+      if (j == 0) { red_tot[i] = v; red_off[i] = o; }
       __syncthreads();
-      if (tid == 0) {
-        double to = 0.0, of = 0.0;
-        for (int u = 0; u < l; ++u) { to += (double)red_tot[u]; of += (double)red_off[u]; }
-        off_s = of;
-        tot_s = to;
+      if (tid < 32) {
+        T to = red_tot[tid], of = red_off[tid];
+#pragma unroll
+        for (int sh = 16; sh > 0; sh >>= 1) {
+          to += __shfl_xor_sync(0xffffffffu, to, sh);
+          of += __shfl_xor_sync(0xffffffffu, of, sh);
+        }
+        if (tid == 0) go_on = of > eps * to;
       }
       __syncthreads();
     }
-    const double eps = sizeof(T) == 4 ? 1e-11 : 1e-30;
-    if (!(off_s > eps * tot_s)) break;
+    if (!go_on) break;
     for (int round = 0; round < m - 1; ++round) {
-      // circle method: position 0 fixed, others rotate by `round`
-      if (tid < m) {
-        const int x = tid;
-        const int pos = x == 0 ? 0 : ((x - 1 - round) % (m - 1) + (m - 1)) % (m - 1) + 1;
-        const int ppos = m - 1 - pos;
-        const int y = ppos == 0 ? 0 : ((ppos - 1 + round) % (m - 1)) + 1;
-        if (x < l) {
-          partner[x] = y;
-          first[x] = x < y;
-        }
-      }
-      __syncthreads();
       if (tid < l) {
-        const int x = tid, y = partner[x];
+        const int x = tid, y = partner[round][x];
         if (x < y && y < l) {
-          T c = T(1), s = T(0);
-          const T apq = A[cur][x][y];
-          if (apq != T(0)) {
-            const T theta = (A[cur][y][y] - A[cur][x][x]) / (T(2) * apq);
-            const T t = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
-            c = T(1) / sqrt(t * t + T(1));
-            s = t * c;
-          }
+          T c, s;
+          jacobi_rotation<T>(A[cur][x][x], A[cur][y][y], A[cur][x][y], c, s);
           cs[x][0] = c; cs[x][1] = s;
           cs[y][0] = c; cs[y][1] = s;
         } else if (y >= l) {
@@ -597,10 +692,10 @@ __global__ void k_ritz_jacobi(const ProblemDev* tab) {
       if (mine) {
         // coefficients of row/column index u: new_u = al * X_p + be * X_q for its pair (p < q)
         auto coef = [&](int u, int& p, int& q, T& al, T& be) {
-          const int v2 = partner[u];
+          const int v2 = partner[round][u];
           if (v2 >= l) { p = u; q = u; al = T(1); be = T(0); return; }
           const T c = cs[u][0], s = cs[u][1];
-          if (first[u]) { p = u; q = v2; al = c; be = -s; }
+          if (u < v2) { p = u; q = v2; al = c; be = -s; }
           else { p = v2; q = u; al = s; be = c; }
         };
         int pi, qi, pj, qj;
@@ -633,23 +728,128 @@ __global__ void k_ritz_jacobi(const ProblemDev* tab) {
   }
 }
 
+// One-sided (Hestenes) Jacobi by one warp in FP32, for the mixed path: lane c
+// holds column c of U (starting as B) and of V (starting as I) in registers;
+// each round rotates the column pairs of the round-robin schedule so that they
+// become orthogonal, partners exchanging columns by shuffles (no barriers).
+// At convergence B V = U with orthogonal columns, so the columns of V are
+// eigenvectors and lambda_c = v_c . (B v_c) = v_c . u_c (sign kept).
+template <int LM>
+__global__ void k_ritz_jacobi_warp(const ProblemDev* tab) {
+  const ProblemDev& pr = tab[blockIdx.x];
+  const int l = pr.l;
+  const int c = threadIdx.x;
+  if (l <= 0) return;
+  float u[LM], v[LM];
+#pragma unroll
+  for (int i = 0; i < LM; ++i) {
+    u[i] = (i < l && c < l) ? (float)(0.5 * (pr.Gm[i * l + c] + pr.Gm[c * l + i])) : 0.f;
+    v[i] = (i == c && c < l) ? 1.f : 0.f;
+  }
+  const int m = (l + 1) & ~1;
+  // A pair counts as unconverged while the cosine of its columns exceeds 1e-5
+  // and |u_p . u_q| exceeds 2e-6 of the largest squared column norm: the FP32
+  // rounding noise of a small column (~eps |B|) keeps u_p . u_q near
+  // eps |B|^2 however long the sweeps go on.
+  float nrm = 0.f;   // |u_c|^2, kept up to date through the rotations
+#pragma unroll
+  for (int i = 0; i < LM; ++i) nrm = fmaf(u[i], u[i], nrm);
+  float scale = nrm;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) scale = fmaxf(scale, __shfl_xor_sync(0xffffffffu, scale, o));
+  const float gabs = 2e-6f * scale;
+  for (int sweep = 0; sweep < 16; ++sweep) {
+    int busy = 0;
+    for (int round = 0; round < m - 1; ++round) {
+      int p = c;   // partner of column c in this round (c itself: idle)
+      if (c < m) {
+        const int pos = c == 0 ? 0 : ((c - 1 - round) % (m - 1) + (m - 1)) % (m - 1) + 1;
+        const int ppos = m - 1 - pos;
+        p = ppos == 0 ? 0 : ((ppos - 1 + round) % (m - 1)) + 1;
+      }
+      const bool act = c < l && p < l && p != c;
+      if (!act) p = c;
+      float up[LM];
+      float g = 0.f;
+#pragma unroll
+      for (int i = 0; i < LM; ++i) {
+        up[i] = __shfl_sync(0xffffffffu, u[i], p);
+        g = fmaf(u[i], up[i], g);
+      }
+      const float nrm_p = __shfl_sync(0xffffffffu, nrm, p);
+      // same rotation on both lanes: al, be are the squared norms of the lower and upper column
+      const bool lower = c < p;
+      const float al = lower ? nrm : nrm_p, be = lower ? nrm_p : nrm;
+      float cs = 1.f, sn = 0.f, tt = 0.f;
+      if (act && g != 0.f) {
+        busy |= fabsf(g) > gabs && fabsf(g) > 1e-5f * sqrtf(al * be);
+        const float zeta = __fdividef(be - al, 2.f * g);
+        tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+        cs = rsqrtf(fmaf(tt, tt, 1.f));
+        sn = cs * tt;
+      }
+      // [x_lo, x_hi] <- [cs x_lo - sn x_hi, sn x_lo + cs x_hi]
+      const float f_own = cs, f_oth = lower ? -sn : sn;
+#pragma unroll
+      for (int i = 0; i < LM; ++i) {
+        u[i] = f_own * u[i] + f_oth * up[i];
+        const float vp = __shfl_sync(0xffffffffu, v[i], p);
+        v[i] = f_own * v[i] + f_oth * vp;
+      }
+      nrm = fmaxf(lower ? al - tt * g : be + tt * g, 0.f);
+    }
+    // refresh the norms from the columns once per sweep
+    nrm = 0.f;
+#pragma unroll
+    for (int i = 0; i < LM; ++i) nrm = fmaf(u[i], u[i], nrm);
+    if (!__any_sync(0xffffffffu, busy)) break;
+  }
+  float lam = 0.f;
+#pragma unroll
+  for (int i = 0; i < LM; ++i) lam = fmaf(v[i], u[i], lam);
+  // descending order
+  int rank = 0;
+  for (int o = 0; o < l; ++o) {
+    const float lo = __shfl_sync(0xffffffffu, lam, o);
+    rank += (lo > lam) || (lo == lam && o < c);
+  }
+  if (c < l) {
+    pr.ev[rank] = (double)lam;
+#pragma unroll
+    for (int i = 0; i < LM; ++i)
+      if (i < l) pr.Rm[i * l + rank] = (double)v[i];
+  }
+}
+
 // Phi = basis V_k, C Phi = image V_k (stored in T), theta = top k eigenvalues.
 template <typename T>
 __global__ void k_ritz_vectors(const ProblemDev* tab, int basis) {
   const ProblemDev& pr = tab[blockIdx.y];
-  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int l = pr.l, k = pr.kR;
-  if (k <= 0 || a >= pr.d) return;
+  if (k <= 0) return;
+  __shared__ T Vk[kMaxRitz][kMaxK];
+  for (int e = threadIdx.x; e < l * k; e += blockDim.x) Vk[e / k][e % k] = to_t<T>(pr.Rm[(e / k) * l + e % k]);
+  __syncthreads();
+  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= pr.d) return;
   const T* Qb = ritz_buf<T>(pr, basis);
   const T* Pb = ritz_buf<T>(pr, 1 - basis);
   T* Phi = tp<T>(pr.Phi);
   T* CPhi = tp<T>(pr.CPhi);
+  T q[kMaxRitz], c[kMaxRitz];
+#pragma unroll
+  for (int i = 0; i < kMaxRitz; ++i) {
+    q[i] = i < l ? Qb[a * l + i] : T(0);
+    c[i] = i < l ? Pb[a * l + i] : T(0);
+  }
   for (int j = 0; j < k; ++j) {
     T ph = T(0), cp = T(0);
-    for (int i = 0; i < l; ++i) {
-      const T v = to_t<T>(pr.Rm[i * l + j]);
-      ph += Qb[a * l + i] * v;
-      cp += Pb[a * l + i] * v;
+#pragma unroll
+    for (int i = 0; i < kMaxRitz; ++i) {
+      if (i < l) {
+        ph += q[i] * Vk[i][j];
+        cp += c[i] * Vk[i][j];
+      }
     }
     Phi[a * k + j] = ph;
     CPhi[a * k + j] = cp;
@@ -694,10 +894,11 @@ static void launch_ritz_t(const ProblemTable& tab, const ProblemDev* dtab, cudaS
   if (lmax <= 0 || kmax <= 0) return;
   const dim3 gdl((unsigned)((dl + 255) / 256), tab.count);
   const dim3 gd((unsigned)((dmax + 255) / 256), tab.count);
+  const dim3 gdw((unsigned)((dmax * 32 + 255) / 256), tab.count);   // one warp per row
   const dim3 gll((unsigned)(lmax * lmax), tab.count);
   int cur = 0;   // buffer holding the current basis candidate
   auto matvec = [&]() {   // buf[1 - cur] = C buf[cur]
-    k_ritz_matvec<T><<<gdl, 256, 0, st>>>(dtab, cur);
+    k_ritz_matvec<T><<<gdw, 256, 0, st>>>(dtab, cur);
     note_launches(1);
   };
   auto orth2 = [&](int x) {   // orthonormalize buf[x] in place (scratch: the other buffer)
@@ -719,7 +920,12 @@ static void launch_ritz_t(const ProblemTable& tab, const ProblemDev* dtab, cudaS
   orth2(cur);                                               // basis in buf[cur]
   matvec();                                                 // image in buf[1-cur]
   k_ritz_gram<T><<<gll, 256, 0, st>>>(dtab, cur, 1 - cur, 0);   // Gm = Q^T (C Q)
-  k_ritz_jacobi<T><<<tab.count, kMaxRitz * kMaxRitz, 0, st>>>(dtab);
+  if (sizeof(T) == 4) {
+    if (lmax <= 16) k_ritz_jacobi_warp<16><<<tab.count, 32, 0, st>>>(dtab);
+    else if (lmax <= 24) k_ritz_jacobi_warp<24><<<tab.count, 32, 0, st>>>(dtab);
+    else k_ritz_jacobi_warp<32><<<tab.count, 32, 0, st>>>(dtab);
+  }
+  else k_ritz_jacobi<T><<<tab.count, kMaxRitz * kMaxRitz, 0, st>>>(dtab);
   k_ritz_vectors<T><<<gd, 256, 0, st>>>(dtab, cur);
   k_ritz_grams<T><<<dim3(3 * kmax * kmax, tab.count), 256, 0, st>>>(dtab);
   note_launches(4);

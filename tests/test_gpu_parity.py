@@ -180,6 +180,35 @@ def test_ritz_pairs_and_lmp_match_oracle(B):
         assert np.max(np.abs(Zg[v] - z)) < 1e-8 * np.max(np.abs(z))
 
 
+def test_ritz_pairs_fp32_match_oracle(B):
+    """Mixed path: FP32 basis with FP64 Cholesky, one-warp FP32 Jacobi."""
+    pr = workloads.gaussian_problem_1d("r32", n=1600, N=20, length_scale=8.0, obs_stride=2, r2=0.3,
+                                       half_width=16.0, Q=4, tol=1e-6, seed=7)
+    k, os_, seed = 10, 10, 12345
+    opts = B.make_options(precision=1, ritz_rank=k, oversample=os_, seed=seed)
+    P = B.Prepared(pr.grid, dev(pr.X), dev(pr.obs_idx), dev(pr.R), pr.Q, opts)
+    mu, Z = F.anomalies(pr.X)
+    W, Sxh, Shh = F.localized_covariances(Z, pr.obs_idx, pr.grid)
+    C = F.normalized_obs_covariance(Shh, pr.R)
+    Om = philox.test_matrix(pr.d, k + os_, seed)
+    Phi_ref, th_ref = pcg.randomized_ritz(C, k, Om, power_iters=1)
+    th = P.export("theta")
+    assert np.all(np.diff(th) <= 0)
+    assert np.max(np.abs(th - th_ref) / th_ref[0]) < 1e-4
+    Phi = P.export("phi").reshape(pr.d, k).astype(np.float64)
+    CPhi = P.export("cphi").reshape(pr.d, k).astype(np.float64)
+    assert np.max(np.abs(Phi.T @ Phi - np.eye(k))) < 1e-4
+    assert np.max(np.abs(CPhi - C @ Phi)) < 1e-5 * np.max(np.abs(CPhi))
+    # Rayleigh quotients of the returned vectors are the returned values
+    rq = np.einsum("ai,ai->i", Phi, C @ Phi)
+    assert np.max(np.abs(rq - th) / th[0]) < 1e-4
+    # leading Ritz vectors agree with the oracle's where the gap is large
+    gap = np.abs(np.diff(th_ref)) / th_ref[0]
+    for i in range(k - 1):
+        if gap[i] > 1e-2 and (i == 0 or gap[i - 1] > 1e-2):
+            assert abs(Phi[:, i] @ Phi_ref[:, i]) > 1 - 1e-3
+
+
 # ---------------------------------------------------------------------------
 # end to end
 # ---------------------------------------------------------------------------
@@ -352,3 +381,34 @@ def test_iteration_cap_reports_not_converged(B):
                                          1e-14, opts)
     assert st["status"] == B.NOT_CONVERGED and st["n_unconverged"] > 0 and st["iters_max"] == 2
     assert np.all(np.isfinite(A_a.cpu().numpy()))
+
+
+def test_analysis_replays_as_cuda_graph(B):
+    """The analysis call captures into a CUDA graph (side stream included) and
+    its replay reproduces the direct call bit for bit."""
+    pr = workloads.gaussian_problem_1d("g", n=2048, N=16, length_scale=16.0, obs_stride=4, r2=0.5,
+                                       half_width=40.0, Q=8, tol=1e-6, seed=43)
+    X, obs, y, R = dev(pr.X), dev(pr.obs_idx), dev(pr.y), dev(pr.R)
+    opts = B.make_options(precision=B.PRECISION_FP32)
+    import ctypes
+    g = B.make_grid(pr.grid)
+    need = B.library().info_esrf_workspace_size(ctypes.byref(g), pr.N, pr.d, pr.Q, ctypes.byref(opts))
+    ws = B.workspace(need, X.device)
+    mu1 = torch.empty(pr.n, dtype=torch.float64, device="cuda")
+    A1 = torch.empty((pr.N, pr.n), dtype=torch.float64, device="cuda")
+    B.info_esrf_analysis(pr.grid, X, obs, y, R, pr.Q, 1e-6, opts, ws=ws, mu_a=mu1, A_a=A1, stats=False)
+    torch.cuda.synchronize()
+    ref_mu, ref_A = mu1.clone(), A1.clone()
+    mu1.zero_()
+    A1.zero_()
+    cap = torch.cuda.Stream()
+    cap.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=cap):
+        B.info_esrf_analysis(pr.grid, X, obs, y, R, pr.Q, 1e-6, opts, ws=ws, mu_a=mu1, A_a=A1, stats=False,
+                             stream=cap)
+    torch.cuda.current_stream().wait_stream(cap)
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(mu1, ref_mu) and torch.equal(A1, ref_A)
