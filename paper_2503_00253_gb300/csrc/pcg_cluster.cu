@@ -58,12 +58,14 @@ enum : int { kEmpty = 0, kStart = 1, kActive = 2 };
 
 struct LaneState {
   int sid[kJ], state[kJ], it[kJ], newsid[kJ], fin[kJ];
-  double sigma[kJ], rho[kJ], bn2[kJ], rr[kJ];
+  double sigma[kJ];
+  float rho[kJ];                      // r^T M r of the current iterate
+  float rrh[kJ], rrl[kJ];             // r^T r as a float-float pair (FP64-accurate)
+  float bn2[kJ];                      // b^T b
   float sigf[kJ], alpha[kJ], beta[kJ];
   float t[kJ][kK], c[kJ][kK];
-  float f[kJ][kK], g[kJ][kK];
-  double rtr[kJ];                     // r^T T r of the learned term
-  float la[kJ], lt[kJ][kTT];          // learned correction: a and the taps of T = S^T S per lane
+  float la[kJ], ltT[kTT][kJ];         // learned correction: a and the taps of T = S^T S (tap-major)
+  float bmf[kJ];                      // beta_q - sigma_q of the preconditioner (App. E)
   int learn[kJ];
 };
 
@@ -77,11 +79,12 @@ struct Setup {
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 
-__device__ __forceinline__ int wrap_delta(int64_t col, int64_t a, int64_t d) {
-  int64_t dl = (col - a) % d;
+// Cyclic offset col - a folded into (-d/2, d/2] (0 <= col, a < d < 2^31).
+__device__ __forceinline__ int wrap_delta(int col, int a, int d) {
+  int dl = col - a;
   if (dl < 0) dl += d;
   if (2 * dl > d) dl -= d;
-  return (int)dl;
+  return dl;
 }
 
 }  // namespace
@@ -128,7 +131,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       const int nnz = pr.oo_nnz[a];
       int dmin = 1 << 30, dmax = -(1 << 30);
       for (int e = 0; e < nnz; ++e) {
-        const int dl = wrap_delta(pr.oo_col[(int64_t)e * d + a], a, d);
+        const int dl = wrap_delta(pr.oo_col[(int64_t)e * d + a], (int)a, (int)d);
         dmin = dl < dmin ? dl : dmin;
         dmax = dl > dmax ? dl : dmax;
       }
@@ -187,9 +190,10 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       const int rel2 = wrow - wl;
       const int nr2 = nrows_of(c2);
       if (rel2 >= 0 && rel2 < nr2) continue;   // own row of c2, not a halo row
-      int64_t g = ((int64_t)c2 * R_s + rel2) % d;
-      if (g < 0) g += d;
-      const int owner = (int)(g / R_s);
+      int g = c2 * R_s + rel2;          // |rel2| < d, so one fold is enough
+      if (g < 0) g += (int)d;
+      if (g >= d) g -= (int)d;
+      const int owner = g / R_s;
       if (owner != crank) continue;
       f((int)(g - s0), c2, wrow);
     }
@@ -253,7 +257,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
     const int nnz = pr.oo_nnz[a];
     const int t = row / kTile, r = row % kTile;
     for (int e = 0; e < nnz; ++e) {
-      const int rel = row + wrap_delta(pr.oo_col[(int64_t)e * d + a], a, d);
+      const int rel = row + wrap_delta(pr.oo_col[(int64_t)e * d + a], (int)a, (int)d);
       Ct[s_off[t] + (rel - s_klo[t]) * kTile + r] = val[(int64_t)e * d + a];
     }
   }
@@ -282,7 +286,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
     });
   const double cmin = pr.scal[1];
   const int maxit = pr.fixed_iters > 0 ? pr.fixed_iters : pr.max_iter;
-  const double tol2 = pr.tol * pr.tol;
+  const float tol2f = (float)(pr.tol * pr.tol);
 
   // Starts system sid in lane j on the own rows (r = b, x = 0; p own rows are 0).
   auto lane_scalars = [&](int j, int code) {
@@ -292,7 +296,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
     L.fin[j] = 0;
     L.learn[j] = 0;
     L.la[j] = 1.f;
-    for (int u = 0; u < kTT; ++u) L.lt[j][u] = 0.f;
+    for (int u = 0; u < kTT; ++u) L.ltT[u][j] = 0.f;
     if (sid < 0) {
       L.state[j] = kEmpty;
       L.sigma[j] = 1.0;
@@ -305,14 +309,15 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
         L.learn[j] = 1;
         L.la[j] = cf[0];
         const float* tT = pr.learn_T + (int64_t)(q < 0 ? pr.Q : q) * kLearnT;   // taps of S^T S
-        for (int u = 0; u < kTT; ++u) L.lt[j][u] = tT[u];
+        for (int u = 0; u < kTT; ++u) L.ltT[u][j] = tT[u];
       }
     }
     L.sigf[j] = (float)L.sigma[j];
+    L.bmf[j] = (float)(L.sigma[j] + cmin) - L.sigf[j];
     L.it[j] = 0;
     L.alpha[j] = 0.f;
     L.beta[j] = 0.f;
-    L.rho[j] = 0.0;
+    L.rho[j] = 0.f;
   };
   auto lane_vectors_all = [&]() {      // own rows of r and x for every lane in state kStart
     for (int e = tid; e < R_s * kJ; e += blockDim.x) {
@@ -345,70 +350,62 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
 
   for (;;) {
     // ---------------- A: y = sigma p + C p on the own rows, partial p^T y ----------------
-    DotAcc<float> pp[16];
-    for (int t = warp; t < ntiles; t += kNW) {
-      const int r = lane & 15, h = lane >> 4;
-      const int row = t * kTile + r;
-      const float* pown = pw + (row + hl) * kLD + 16 * h;
-      float acc[16];
-#pragma unroll
-      for (int q4 = 0; q4 < 4; ++q4) {
-        const float4 pv = ld4(pown + 4 * q4);
-        acc[4 * q4 + 0] = L.sigf[16 * h + 4 * q4 + 0] * pv.x;
-        acc[4 * q4 + 1] = L.sigf[16 * h + 4 * q4 + 1] * pv.y;
-        acc[4 * q4 + 2] = L.sigf[16 * h + 4 * q4 + 2] * pv.z;
-        acc[4 * q4 + 3] = L.sigf[16 * h + 4 * q4 + 3] * pv.w;
-      }
-      const float* ct = Ct + s_off[t] + r;
-      const float* pb = pw + (s_klo[t] + hl) * kLD + 16 * h;
-      const int wt = s_w[t];
-#pragma unroll 4
-      for (int kk = 0; kk < wt; ++kk) {
-        const float c = ct[kk * kTile];
-        const float* prow = pb + kk * kLD;
-#pragma unroll
-        for (int q4 = 0; q4 < 4; ++q4) {
-          const float4 pv = ld4(prow + 4 * q4);
-          acc[4 * q4 + 0] = fmaf(c, pv.x, acc[4 * q4 + 0]);
-          acc[4 * q4 + 1] = fmaf(c, pv.y, acc[4 * q4 + 1]);
-          acc[4 * q4 + 2] = fmaf(c, pv.z, acc[4 * q4 + 2]);
-          acc[4 * q4 + 3] = fmaf(c, pv.w, acc[4 * q4 + 3]);
-        }
-      }
-      const bool valid = row < nrows;
-#pragma unroll
-      for (int q4 = 0; q4 < 4; ++q4) {
-        const float4 pv = ld4(pown + 4 * q4);
-        if (valid) {
-          st4(vy + (row + kTH) * kLD + 16 * h + 4 * q4,
-              make_float4(acc[4 * q4], acc[4 * q4 + 1], acc[4 * q4 + 2], acc[4 * q4 + 3]));
-          pp[4 * q4 + 0].add_prod(pv.x, acc[4 * q4 + 0]);
-          pp[4 * q4 + 1].add_prod(pv.y, acc[4 * q4 + 1]);
-          pp[4 * q4 + 2].add_prod(pv.z, acc[4 * q4 + 2]);
-          pp[4 * q4 + 3].add_prod(pv.w, acc[4 * q4 + 3]);
-        }
-      }
-    }
+    // A warp takes one 16-row tile; thread (rg, lg) = (lane / 8, lane % 8) owns
+    // rows 4 rg .. 4 rg + 3 of it for lanes 4 lg .. 4 lg + 3, so each column of
+    // the tile costs two 16-byte shared loads for 16 FMAs.
     {
-      // reduce-scatter over the 16 rows of each half-warp: lane 16 h + r ends
-      // with the float-float sum of lane j = 16 h + r (15 exchanges, not 64)
-      float vh[16], vl[16];
+      const int rg = lane >> 3, lg = lane & 7;
+      const float s0g = L.sigf[4 * lg], s1g = L.sigf[4 * lg + 1], s2g = L.sigf[4 * lg + 2], s3g = L.sigf[4 * lg + 3];
+      DotAcc<float> pp[4];
+      for (int t = warp; t < ntiles; t += kNW) {
+        const int row0 = t * kTile + 4 * rg;
+        float4 acc[4];
 #pragma unroll
-      for (int jj = 0; jj < 16; ++jj) { vh[jj] = pp[jj].hi; vl[jj] = pp[jj].lo; }
+        for (int r = 0; r < 4; ++r) {
+          const float4 pv = ld4(pw + (row0 + r + hl) * kLD + 4 * lg);
+          acc[r] = make_float4(s0g * pv.x, s1g * pv.y, s2g * pv.z, s3g * pv.w);
+        }
+        const float* ct = Ct + s_off[t] + 4 * rg;
+        const float* pb = pw + (s_klo[t] + hl) * kLD + 4 * lg;
+        const int wt = s_w[t];
+#pragma unroll 4
+        for (int kk = 0; kk < wt; ++kk) {
+          const float4 c4 = ld4(ct + kk * kTile);
+          const float4 p4 = ld4(pb + kk * kLD);
+          acc[0].x = fmaf(c4.x, p4.x, acc[0].x); acc[0].y = fmaf(c4.x, p4.y, acc[0].y);
+          acc[0].z = fmaf(c4.x, p4.z, acc[0].z); acc[0].w = fmaf(c4.x, p4.w, acc[0].w);
+          acc[1].x = fmaf(c4.y, p4.x, acc[1].x); acc[1].y = fmaf(c4.y, p4.y, acc[1].y);
+          acc[1].z = fmaf(c4.y, p4.z, acc[1].z); acc[1].w = fmaf(c4.y, p4.w, acc[1].w);
+          acc[2].x = fmaf(c4.z, p4.x, acc[2].x); acc[2].y = fmaf(c4.z, p4.y, acc[2].y);
+          acc[2].z = fmaf(c4.z, p4.z, acc[2].z); acc[2].w = fmaf(c4.z, p4.w, acc[2].w);
+          acc[3].x = fmaf(c4.w, p4.x, acc[3].x); acc[3].y = fmaf(c4.w, p4.y, acc[3].y);
+          acc[3].z = fmaf(c4.w, p4.z, acc[3].z); acc[3].w = fmaf(c4.w, p4.w, acc[3].w);
+        }
 #pragma unroll
-      for (int off = 8; off >= 1; off >>= 1) {
-        const bool up = (lane & off) != 0;
-#pragma unroll
-        for (int i = 0; i < off; ++i) {
-          const float sh = up ? vh[i] : vh[i + off], sl = up ? vl[i] : vl[i + off];
-          float kh = up ? vh[i + off] : vh[i], kl = up ? vl[i + off] : vl[i];
-          ff_merge(kh, kl, __shfl_xor_sync(0xffffffffu, sh, off), __shfl_xor_sync(0xffffffffu, sl, off));
-          vh[i] = kh;
-          vl[i] = kl;
+        for (int r = 0; r < 4; ++r) {
+          const int row = row0 + r;
+          if (row < nrows) {
+            const float4 pv = ld4(pw + (row + hl) * kLD + 4 * lg);
+            st4(vy + (row + kTH) * kLD + 4 * lg, acc[r]);
+            pp[0].add_prod(pv.x, acc[r].x);
+            pp[1].add_prod(pv.y, acc[r].y);
+            pp[2].add_prod(pv.z, acc[r].z);
+            pp[3].add_prod(pv.w, acc[r].w);
+          }
         }
       }
-      s_wpap[warp][lane][0] = vh[0];
-      s_wpap[warp][lane][1] = vl[0];
+      // sum over the four row groups (lane bits 3, 4): lane lg then holds lanes 4 lg .. 4 lg + 3
+#pragma unroll
+      for (int l4 = 0; l4 < 4; ++l4) {
+        float hi = pp[l4].hi, lo = pp[l4].lo;
+#pragma unroll
+        for (int o = 8; o <= 16; o <<= 1) {
+          const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+          const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+          ff_merge(hi, lo, h2, l2);
+        }
+        if (rg == 0) { s_wpap[warp][4 * lg + l4][0] = hi; s_wpap[warp][4 * lg + l4][1] = lo; }
+      }
     }
     __syncthreads();
     if (tid < kJ * CS) {
@@ -429,7 +426,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       float alpha = 0.f;
       if (L.state[j] == kActive) {
         if (pAp > 0.f && isfinite(pAp)) {
-          alpha = (float)L.rho[j] / pAp;
+          alpha = L.rho[j] / pAp;
           L.it[j] += 1;
         } else {
           L.fin[j] = 2;   // breakdown: finished with a flag
@@ -498,23 +495,28 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
         cluster.sync();   // (2a) r windows complete
         any_learn = L.learn[j0] | L.learn[j0 + 1] | L.learn[j0 + 2] | L.learn[j0 + 3];
         if (any_learn) {
-          int i = 0;
-          for (int row = lane; row < nrows; row += 32, ++i) {
-            float4 t4 = make_float4(0.f, 0.f, 0.f, 0.f);
+          // rows lane + 32 ii (all inside the r window, which spans R_s + 2 kTH rows)
 #pragma unroll
-            for (int tp = 0; tp < kTT; ++tp) {
-              const float4 r4 = ld4(vy + (row + tp) * kLD + j0);   // r[row + tp - kTH]
-              t4.x = fmaf(L.lt[j0][tp], r4.x, t4.x);
-              t4.y = fmaf(L.lt[j0 + 1][tp], r4.y, t4.y);
-              t4.z = fmaf(L.lt[j0 + 2][tp], r4.z, t4.z);
-              t4.w = fmaf(L.lt[j0 + 3][tp], r4.w, t4.w);
+          for (int ii = 0; ii < kTrRows; ++ii) trr[ii] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 3
+          for (int tp = 0; tp < kTT; ++tp) {
+            const float4 w4 = ld4(&L.ltT[tp][j0]);
+#pragma unroll
+            for (int ii = 0; ii < kTrRows; ++ii) {
+              const float4 r4 = ld4(vy + (lane + 32 * ii + tp) * kLD + j0);   // r[row + tp - kTH]
+              trr[ii].x = fmaf(w4.x, r4.x, trr[ii].x);
+              trr[ii].y = fmaf(w4.y, r4.y, trr[ii].y);
+              trr[ii].z = fmaf(w4.z, r4.z, trr[ii].z);
+              trr[ii].w = fmaf(w4.w, r4.w, trr[ii].w);
             }
-            const float4 r4 = ld4(vy + (row + kTH) * kLD + j0);
-            uu[0].add_prod(r4.x, t4.x); uu[1].add_prod(r4.y, t4.y);
-            uu[2].add_prod(r4.z, t4.z); uu[3].add_prod(r4.w, t4.w);
+          }
 #pragma unroll
-            for (int ii = 0; ii < kTrRows; ++ii)
-              if (ii == i) trr[ii] = t4;
+          for (int ii = 0; ii < kTrRows; ++ii) {
+            if (lane + 32 * ii < nrows) {
+              const float4 r4 = ld4(vy + (lane + 32 * ii + kTH) * kLD + j0);
+              uu[0].add_prod(r4.x, trr[ii].x); uu[1].add_prod(r4.y, trr[ii].y);
+              uu[2].add_prod(r4.z, trr[ii].z); uu[3].add_prod(r4.w, trr[ii].w);
+            }
           }
         }
       }
@@ -534,26 +536,38 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
         }
       }
       const float sv[3] = {s0v, s1v, v2[0]};
-      float rhi[4], rlo[4], uhi[4], ulo[4];
+      // r^T r and r^T T r of the four lanes: eight float-float values,
+      // reduce-scattered over the lane bits 4, 3, 2 and summed over bits 1, 0;
+      // lane L ends with value v = 4 b4 + 2 b3 + b2 (v < 4: r^T r of lane j0 + v,
+      // v >= 4: r^T T r of lane j0 + v - 4)
+      float vh[8], vl[8];
 #pragma unroll
       for (int jj = 0; jj < 4; ++jj) {
-        float hi = rr[jj].hi, lo = rr[jj].lo, hu = uu[jj].hi, lu = uu[jj].lo;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
-          const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-          ff_merge(hi, lo, h2, l2);
-          if (any_learn) {
-            const float h3 = __shfl_xor_sync(0xffffffffu, hu, o);
-            const float l3 = __shfl_xor_sync(0xffffffffu, lu, o);
-            ff_merge(hu, lu, h3, l3);
-          }
-        }
-        rhi[jj] = hi;
-        rlo[jj] = lo;
-        uhi[jj] = hu;
-        ulo[jj] = lu;
+        vh[jj] = rr[jj].hi; vl[jj] = rr[jj].lo;
+        vh[4 + jj] = uu[jj].hi; vl[4 + jj] = uu[jj].lo;
       }
+#pragma unroll
+      for (int lev = 0; lev < 3; ++lev) {
+        const int off = 16 >> lev, half = 4 >> lev;
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+          const float sh = up ? vh[i] : vh[i + half], sl = up ? vl[i] : vl[i + half];
+          float kh = up ? vh[i + half] : vh[i], kl = up ? vl[i + half] : vl[i];
+          ff_merge(kh, kl, __shfl_xor_sync(0xffffffffu, sh, off), __shfl_xor_sync(0xffffffffu, sl, off));
+          vh[i] = kh;
+          vl[i] = kl;
+        }
+      }
+      float qh = vh[0], ql = vl[0];
+#pragma unroll
+      for (int o = 2; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, qh, o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, ql, o);
+        ff_merge(qh, ql, h2, l2);
+      }
+      const int qv = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+      const int qdst = (j0 + (qv & 3)) * kNR + (qv < 4 ? 0 : 2);
       // push this warp's four lanes to every CTA of the cluster
       for (int dst = 0; dst < CS; ++dst) {
         float* base = cluster.map_shared_rank(&s_res_in[crank][0][0], dst);
@@ -564,124 +578,94 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
           const int jj = idx / (2 * kK), w = idx % (2 * kK);
           base[(j0 + jj) * kNR + 4 + w] = sv[b];
         }
-        if (lane < 4) {
-          base[(j0 + lane) * kNR] = lane == 0 ? rhi[0] : lane == 1 ? rhi[1] : lane == 2 ? rhi[2] : rhi[3];
-          base[(j0 + lane) * kNR + 1] = lane == 0 ? rlo[0] : lane == 1 ? rlo[1] : lane == 2 ? rlo[2] : rlo[3];
-          base[(j0 + lane) * kNR + 2] = lane == 0 ? uhi[0] : lane == 1 ? uhi[1] : lane == 2 ? uhi[2] : uhi[3];
-          base[(j0 + lane) * kNR + 3] = lane == 0 ? ulo[0] : lane == 1 ? ulo[1] : lane == 2 ? ulo[2] : ulo[3];
+        if ((lane & 3) == 0) {
+          base[qdst] = qh;
+          base[qdst + 1] = ql;
         }
       }
     }
     cluster.sync();   // (2)
-    // ---------------- decisions ----------------
-    // sums over the cluster, in rank order, from the local receive buffers
-    for (int e = tid; e < kJ * (2 * kK); e += blockDim.x) {
-      const int j = e / (2 * kK), w = e % (2 * kK);
-      if ((w % kK) >= k) continue;
-      float sacc = 0.f;
-      for (int c = 0; c < CS; ++c) sacc += s_res_in[c][j][4 + w];
-      if (w < kK) L.f[j][w] = sacc; else L.g[j][w - kK] = sacc;
-    }
-    if (tid < kJ) {
-      float hi = 0.f, lo = 0.f;
-      float hu = 0.f, lu = 0.f;
-      for (int c = 0; c < CS; ++c) {
-        ff_merge(hi, lo, s_res_in[c][tid][0], s_res_in[c][tid][1]);
-        ff_merge(hu, lu, s_res_in[c][tid][2], s_res_in[c][tid][3]);
-      }
-      L.rr[tid] = (double)hi + (double)lo;
-      L.rtr[tid] = L.learn[tid] ? (double)hu + (double)lu : 0.0;
-    }
-    __syncthreads();
-    // preconditioner algebra: t = T^-1 f, t2 = g + sigma f - G t, c = (beta - sigma) t - T^-1 t2
-    for (int e = tid; e < kJ * k; e += blockDim.x) {
-      const int j = e / k, m = e % k;
-      L.t[j][m] = L.f[j][m] / (s_theta[m] + L.sigf[j]);
-    }
-    __syncthreads();
-    for (int e = tid; e < kJ * k; e += blockDim.x) {
-      const int j = e / k, m = e % k;
-      const float sg = L.sigf[j];
-      float t2 = L.g[j][m] + sg * L.f[j][m];
-      for (int i = 0; i < k; ++i) {
-        const float G = s_gram[2][m * k + i] + sg * (s_gram[1][m * k + i] + s_gram[1][i * k + m]) +
-                        sg * sg * s_gram[0][m * k + i];
-        t2 = fmaf(-G, L.t[j][i], t2);
-      }
-      const float bl = (float)(L.sigma[j] + cmin);
-      L.c[j][m] = (bl - sg) * L.t[j][m] - t2 / (s_theta[m] + sg);
-    }
-    __syncthreads();
-    if (tid < kJ) {
-      const int j = tid;
-      const int st = L.state[j];
-      const double rr = L.rr[j];
-      // rho = r^T M r = a r^T P^-1 r + r^T S^T S r; the k-term LMP correction
-      // to r^T r is summed in FP32 (it shapes the preconditioner only)
-      float corr = 0.f;
-      for (int m = 0; m < k; ++m) corr = fmaf(L.f[j][m], L.c[j][m], fmaf(-L.g[j][m], L.t[j][m], corr));
-      const double rho = (double)L.la[j] * (rr + (double)corr) + L.rtr[j];
-      if (st == kStart) {
-        L.bn2[j] = rr;
-        if (!(rr > 0.0) || !isfinite(rr)) {
-          L.fin[j] = isfinite(rr) ? 1 : 2;
-        } else {
-          L.state[j] = kActive;
-          L.rho[j] = rho;
-          L.beta[j] = 0.f;
-        }
-      } else if (st == kActive && L.fin[j] == 0) {
-        bool done = false;
-        if (!isfinite(rr)) { done = true; L.fin[j] = 2; }
-        else if (pr.fixed_iters > 0) done = L.it[j] >= pr.fixed_iters || !(rr > 0.0);
-        else done = !(rr > tol2 * L.bn2[j]) || L.it[j] >= maxit;
-        if (done) {
-          if (L.fin[j] == 0) L.fin[j] = 1;
-        } else {
-          L.beta[j] = (float)rho / (float)L.rho[j];
-          L.rho[j] = rho;
-        }
-      }
-    }
-    __syncthreads();
-    // finished lanes: stats, and rank 0 takes the next systems off the queue
-    if (crank == 0 && warp == 0) {
-      const int j = lane;
-      const bool f = L.fin[j] != 0;
-      const double bn = L.bn2[j];
-      const bool failed = f && (L.fin[j] == 2 || (pr.fixed_iters <= 0 && !(L.rr[j] <= tol2 * bn)));
-      const bool retry = failed && L.learn[j];          // plain PCG solves it again
-      const bool take = f && !retry;
-      const unsigned fm = __ballot_sync(0xffffffffu, take);
-      int base = 0;
-      if (lane == 0 && fm) base = atomicAdd(queue, __popc(fm));
-      base = __shfl_sync(0xffffffffu, base, 0);
-      if (f) {
-        const int sid = L.sid[j];
-        int v;
-        if (retry) {
-          v = sid + kRetry;
-        } else {
-          pr.iters[sid] = L.it[j];
-          pr.relres[sid] = bn > 0.0 ? sqrt(L.rr[j] / bn) : 0.0;
-          if (L.fin[j] == 2) atomicOr(&pr.status[0], kStatBreakdown);
-          else if (failed) atomicOr(&pr.status[0], kStatNotConverged);
-          const int nid = base + __popc(fm & ((1u << j) - 1u));
-          v = nid < pr.nsys ? nid : -1;
-        }
-        for (int dst = 0; dst < CS; ++dst) cluster.map_shared_rank(&L.newsid[0], dst)[j] = v;
-      }
-    }
-    // ---------------- z = P^-1 r, p = z + beta p; finished lanes hand in x ----------------
+    // ---------------- decisions, then z = P^-1 r and p = z + beta p ----------------
+    // Each warp handles its four lanes (the lanes of the residual step), so no
+    // block barrier is needed until the queue.  Sums over the cluster are taken
+    // in rank order from the local receive buffers, identically in every CTA.
+    // Preconditioner algebra: t = T^-1 f, t2 = g + sigma f - G_q t,
+    // c = (beta - sigma) t - T^-1 t2, with G_q = (C_q Phi)^T (C_q Phi).
     {
       const int j0 = 4 * warp;
+      const int m = lane & 15;
+      const bool mv = m < k;
+#pragma unroll
+      for (int pass = 0; pass < 2; ++pass) {
+        const int j = j0 + 2 * pass + (lane >> 4);
+        float f = 0.f, g = 0.f;
+        if (mv)
+          for (int c = 0; c < CS; ++c) {
+            f += s_res_in[c][j][4 + m];
+            g += s_res_in[c][j][4 + kK + m];
+          }
+        const float sg = L.sigf[j];
+        const float rth = mv ? __frcp_rn(s_theta[m] + sg) : 0.f;   // (T_q)^-1 entry
+        const float t = f * rth;
+        float t2 = g + sg * f;
+        for (int i = 0; i < k; ++i) {
+          const float ti = __shfl_sync(0xffffffffu, t, (lane & 16) + i);
+          if (mv) {
+            const float G = s_gram[2][m * k + i] + sg * (s_gram[1][m * k + i] + s_gram[1][i * k + m]) +
+                            sg * sg * s_gram[0][m * k + i];
+            t2 = fmaf(-G, ti, t2);
+          }
+        }
+        const float cc = mv ? fmaf(L.bmf[j], t, -t2 * rth) : 0.f;
+        if (mv) { L.t[j][m] = t; L.c[j][m] = cc; }
+        // rho = r^T M r = a r^T P^-1 r + r^T S^T S r.  The dot products are
+        // float-float (FP64-accurate); rho, alpha and beta multiply FP32
+        // vectors and are formed in FP32, and so is the k-term LMP correction.
+        float corr = mv ? fmaf(f, cc, -g * t) : 0.f;
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) corr += __shfl_xor_sync(0xffffffffu, corr, o);
+        if (m == 0) {
+          float hi = 0.f, lo = 0.f, hu = 0.f, lu = 0.f;
+          for (int c = 0; c < CS; ++c) {
+            ff_merge(hi, lo, s_res_in[c][j][0], s_res_in[c][j][1]);
+            ff_merge(hu, lu, s_res_in[c][j][2], s_res_in[c][j][3]);
+          }
+          L.rrh[j] = hi;
+          L.rrl[j] = lo;
+          const float rr = hi + lo;
+          const float rho = L.la[j] * (rr + corr) + (L.learn[j] ? hu + lu : 0.f);
+          const int st = L.state[j];
+          if (st == kStart) {
+            L.bn2[j] = rr;
+            if (!(rr > 0.f) || !isfinite(rr)) {
+              L.fin[j] = isfinite(rr) ? 1 : 2;
+            } else {
+              L.state[j] = kActive;
+              L.rho[j] = rho;
+              L.beta[j] = 0.f;
+            }
+          } else if (st == kActive && L.fin[j] == 0) {
+            bool done = false;
+            if (!isfinite(rr)) { done = true; L.fin[j] = 2; }
+            else if (pr.fixed_iters > 0) done = L.it[j] >= pr.fixed_iters || !(rr > 0.f);
+            else done = !(rr > tol2f * L.bn2[j]) || L.it[j] >= maxit;
+            if (done) {
+              if (L.fin[j] == 0) L.fin[j] = 1;
+            } else {
+              L.beta[j] = rho / L.rho[j];
+              L.rho[j] = rho;
+            }
+          }
+        }
+      }
+      __syncwarp();
       float tj[4][kK], cj[4][kK];
 #pragma unroll
       for (int jj = 0; jj < 4; ++jj)
 #pragma unroll
-        for (int m = 0; m < kK; ++m) {
-          tj[jj][m] = m < k ? L.t[j0 + jj][m] : 0.f;
-          cj[jj][m] = m < k ? L.c[j0 + jj][m] : 0.f;
+        for (int mm = 0; mm < kK; ++mm) {
+          tj[jj][mm] = mm < k ? L.t[j0 + jj][mm] : 0.f;
+          cj[jj][mm] = mm < k ? L.c[j0 + jj][mm] : 0.f;
         }
       bool act[4], fin[4];
       float bj[4], aj[4];
@@ -701,11 +685,11 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
         const float4 p4 = ld4(prow);
         float z[4] = {r4.x, r4.y, r4.z, r4.w};
 #pragma unroll
-        for (int m = 0; m < kK; ++m) {
-          if (m < k) {
-            const float ph = phT[m * R_s + row], at = aT[m * R_s + row];
+        for (int mm = 0; mm < kK; ++mm) {
+          if (mm < k) {
+            const float ph = phT[mm * R_s + row], at = aT[mm * R_s + row];
 #pragma unroll
-            for (int jj = 0; jj < 4; ++jj) z[jj] = fmaf(ph, cj[jj][m], fmaf(-at, tj[jj][m], z[jj]));
+            for (int jj = 0; jj < 4; ++jj) z[jj] = fmaf(ph, cj[jj][mm], fmaf(-at, tj[jj][mm], z[jj]));
           }
         }
         if (any_learn2) {
@@ -730,6 +714,35 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       }
     }
     __syncthreads();
+    // finished lanes: stats, and rank 0 takes the next systems off the queue
+    if (crank == 0 && warp == 0) {
+      const int j = lane;
+      const bool f = L.fin[j] != 0;
+      const float bn = L.bn2[j];
+      const float rrj = L.rrh[j] + L.rrl[j];
+      const bool failed = f && (L.fin[j] == 2 || (pr.fixed_iters <= 0 && !(rrj <= tol2f * bn)));
+      const bool retry = failed && L.learn[j];          // plain PCG solves it again
+      const bool take = f && !retry;
+      const unsigned fm = __ballot_sync(0xffffffffu, take);
+      int base = 0;
+      if (lane == 0 && fm) base = atomicAdd(queue, __popc(fm));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (f) {
+        const int sid = L.sid[j];
+        int v;
+        if (retry) {
+          v = sid + kRetry;
+        } else {
+          pr.iters[sid] = L.it[j];
+          pr.relres[sid] = bn > 0.f ? sqrt(((double)L.rrh[j] + (double)L.rrl[j]) / (double)bn) : 0.0;
+          if (L.fin[j] == 2) atomicOr(&pr.status[0], kStatBreakdown);
+          else if (failed) atomicOr(&pr.status[0], kStatNotConverged);
+          const int nid = base + __popc(fm & ((1u << j) - 1u));
+          v = nid < pr.nsys ? nid : -1;
+        }
+        for (int dst = 0; dst < CS; ++dst) cluster.map_shared_rank(&L.newsid[0], dst)[j] = v;
+      }
+    }
     // push the own rows that other windows hold as halo rows
     {
       const int np = s_npush;

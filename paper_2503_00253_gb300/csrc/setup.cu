@@ -758,7 +758,9 @@ __global__ void k_ritz_jacobi_warp(const ProblemDev* tab) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) scale = fmaxf(scale, __shfl_xor_sync(0xffffffffu, scale, o));
   const float gabs = 2e-6f * scale;
-  for (int sweep = 0; sweep < 16; ++sweep) {
+  // cyclic Jacobi converges quadratically: six sweeps reach FP32 rounding on
+  // these sizes (l <= 32), and the Ritz pairs only shape the preconditioner
+  for (int sweep = 0; sweep < 6; ++sweep) {
     int busy = 0;
     for (int round = 0; round < m - 1; ++round) {
       int p = c;   // partner of column c in this round (c itself: idle)
@@ -770,12 +772,13 @@ __global__ void k_ritz_jacobi_warp(const ProblemDev* tab) {
       const bool act = c < l && p < l && p != c;
       if (!act) p = c;
       float up[LM];
-      float g = 0.f;
+      float g4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int i = 0; i < LM; ++i) {
         up[i] = __shfl_sync(0xffffffffu, u[i], p);
-        g = fmaf(u[i], up[i], g);
+        g4[i & 3] = fmaf(u[i], up[i], g4[i & 3]);
       }
+      const float g = (g4[0] + g4[1]) + (g4[2] + g4[3]);
       const float nrm_p = __shfl_sync(0xffffffffu, nrm, p);
       // same rotation on both lanes: al, be are the squared norms of the lower and upper column
       const bool lower = c < p;
