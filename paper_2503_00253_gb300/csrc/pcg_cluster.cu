@@ -67,6 +67,7 @@ struct LaneState {
   float la[kJ], ltT[kTT][kJ];         // learned correction: a and the taps of T = S^T S (tap-major)
   float bmf[kJ];                      // beta_q - sigma_q of the preconditioner (App. E)
   int learn[kJ];
+  int mem[kJ];                        // ensemble member of the lane's system, -1 for the mean system
 };
 
 struct Setup {
@@ -77,6 +78,15 @@ struct Setup {
 };
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+
+// 4-byte asynchronous copy global -> shared (completion: cp_async_wait_all + a barrier).
+__device__ __forceinline__ void cp_async4(float* dst_smem, const float* src_global) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst_smem);
+  const size_t g = __cvta_generic_to_global(src_global);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 
 // Cyclic offset col - a folded into (-d/2, d/2] (0 <= col, a < d < 2^31).
@@ -126,21 +136,30 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
   if (2 * R_s > dyn_floats) s_bad = 1;
   __syncthreads();
   if (!s_bad) {
-    for (int row = tid; row < nrows; row += blockDim.x) {
-      const int64_t a = s0 + row;
-      const int nnz = pr.oo_nnz[a];
-      int dmin = 1 << 30, dmax = -(1 << 30);
-      for (int e = 0; e < nnz; ++e) {
-        const int dl = wrap_delta(pr.oo_col[(int64_t)e * d + a], (int)a, (int)d);
-        dmin = dl < dmin ? dl : dmin;
-        dmax = dl > dmax ? dl : dmax;
+    // two threads per row (alternate entries), combined by a shuffle
+    for (int base = 0; base < nrows; base += (int)blockDim.x / 2) {
+      const int row = base + (tid >> 1), part = tid & 1;
+      int dmin = 1 << 30, dmax = -(1 << 30), nnz = 0;
+      if (row < nrows) {
+        const int64_t a = s0 + row;
+        nnz = pr.oo_nnz[a];
+#pragma unroll 4
+        for (int e = part; e < nnz; e += 2) {
+          const int dl = wrap_delta(pr.oo_col[(int64_t)e * d + a], (int)a, (int)d);
+          dmin = dl < dmin ? dl : dmin;
+          dmax = dl > dmax ? dl : dmax;
+        }
       }
-      bool ok = nnz >= 1 && (dmax - dmin + 1) == nnz && 2 * (int64_t)(dmax - dmin + 1) < d;
-      if (!ok) atomicOr(&s_bad, 1);
-      rlo[row] = row + dmin;
-      rhi[row] = row + dmax;
-      atomicMin(&s_lo_min, row + dmin);
-      atomicMax(&s_hi_max, row + dmax);
+      dmin = min(dmin, __shfl_xor_sync(0xffffffffu, dmin, 1));
+      dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, 1));
+      if (row < nrows && part == 0) {
+        bool ok = nnz >= 1 && (dmax - dmin + 1) == nnz && 2 * (int64_t)(dmax - dmin + 1) < d;
+        if (!ok) atomicOr(&s_bad, 1);
+        rlo[row] = row + dmin;
+        rhi[row] = row + dmax;
+        atomicMin(&s_lo_min, row + dmin);
+        atomicMax(&s_hi_max, row + dmax);
+      }
     }
   }
   __syncthreads();
@@ -226,7 +245,8 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
   const int o_at = o_ph + k * R_s;
   const int o_push = (o_at + k * R_s + 1) & ~1;
   const int o_rpush = o_push + 2 * npush_max;
-  const int need = o_rpush + 2 * nrpush_max;
+  const int o_rinv = o_rpush + 2 * nrpush_max;     // R^-1/2 of the own rows
+  const int need = o_rinv + R_s;
   if (need > dyn_floats) bad = 1;
   cluster.sync();                                   // remote reads of S done before anyone exits
   if (bad) {
@@ -243,6 +263,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
   float* aT = dyn + o_at;
   int2* push = reinterpret_cast<int2*>(dyn + o_push);
   int2* rpush = reinterpret_cast<int2*>(dyn + o_rpush);
+  float* s_rinv = dyn + o_rinv;
   const float* val = reinterpret_cast<const float*>(pr.oo_val);
   const float* Phi = reinterpret_cast<const float*>(pr.Phi);
   const float* CPhi = reinterpret_cast<const float*>(pr.CPhi);
@@ -252,15 +273,19 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
   for (int i = tid; i < tilesz; i += blockDim.x) Ct[i] = 0.f;
   for (int i = o_pw + tid; i < o_ph; i += blockDim.x) dyn[i] = 0.f;
   __syncthreads();
-  for (int row = tid; row < nrows; row += blockDim.x) {
+  for (int base = 0; base < nrows; base += (int)blockDim.x / 2) {
+    const int row = base + (tid >> 1), part = tid & 1;
+    if (row >= nrows) continue;
     const int64_t a = s0 + row;
     const int nnz = pr.oo_nnz[a];
     const int t = row / kTile, r = row % kTile;
-    for (int e = 0; e < nnz; ++e) {
+#pragma unroll 4
+    for (int e = part; e < nnz; e += 2) {
       const int rel = row + wrap_delta(pr.oo_col[(int64_t)e * d + a], (int)a, (int)d);
       Ct[s_off[t] + (rel - s_klo[t]) * kTile + r] = val[(int64_t)e * d + a];
     }
   }
+  for (int row = tid; row < R_s; row += blockDim.x) s_rinv[row] = row < nrows ? (float)pr.rinv[s0 + row] : 0.f;
   for (int i = tid; i < k * R_s; i += blockDim.x) {
     const int m = i / R_s, row = i % R_s;
     const bool ok = row < nrows;
@@ -297,12 +322,14 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
     L.learn[j] = 0;
     L.la[j] = 1.f;
     for (int u = 0; u < kTT; ++u) L.ltT[u][j] = 0.f;
+    L.mem[j] = -1;
     if (sid < 0) {
       L.state[j] = kEmpty;
       L.sigma[j] = 1.0;
     } else {
       L.state[j] = kStart;
       const int q = sid < pr.mean_sys ? -1 : (int)((sid - pr.mean_sys) / N);
+      if (q >= 0) L.mem[j] = (int)((sid - pr.mean_sys) % N);
       L.sigma[j] = q < 0 ? 1.0 : pr.s[q] + 1.0;
       const float* cf = pr.learn_coef + (int64_t)(q < 0 ? pr.Q : q) * kLearnOut;
       if (learn_ok && !retry && cf[0] > 0.f) {
@@ -319,20 +346,32 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
     L.beta[j] = 0.f;
     L.rho[j] = 0.f;
   };
-  auto lane_vectors_all = [&]() {      // own rows of r and x for every lane in state kStart
-    for (int e = tid; e < R_s * kJ; e += blockDim.x) {
-      const int row = e / kJ, j = e % kJ;
-      if (L.state[j] != kStart) continue;
-      const int sid = L.sid[j];
-      const bool mean = sid < pr.mean_sys;
-      float b = 0.f;
-      if (row < nrows) {
-        const int64_t a = s0 + row;
-        b = mean ? (float)pr.bmean[a] : W[a * N + (sid - pr.mean_sys) % N] * (float)pr.rinv[a];
-      }
-      vr[row * kLD + j] = b;
-      vx[row * kLD + j] = 0.f;
+  // Own rows of r and x for every lane in state kStart: x = 0, and r receives the
+  // member's observed anomalies by asynchronous copies that complete during the
+  // matvec; the residual step scales them by R^-1/2 (the mean system's
+  // right-hand side, already scaled, is stored directly).
+  __shared__ int s_start[kJ], s_nstart, s_live;
+  auto lane_masks = [&]() {           // warp 0: which lanes are live / just started
+    if (tid < kJ) {
+      const unsigned lm = __ballot_sync(0xffffffffu, L.state[tid] != kEmpty);
+      const unsigned sm = __ballot_sync(0xffffffffu, L.state[tid] == kStart);
+      if (sm & (1u << tid)) s_start[__popc(sm & ((1u << tid) - 1u))] = tid;
+      if (tid == 0) { s_live = lm != 0u; s_nstart = __popc(sm); }
     }
+  };
+  auto lane_vectors_all = [&]() {
+    const int ns = s_nstart;
+    for (int e = tid; e < R_s * ns; e += blockDim.x) {
+      const int row = e / ns, j = s_start[e % ns];
+      float* dst = vr + row * kLD + j;
+      vx[row * kLD + j] = 0.f;
+      if (row >= nrows) { *dst = 0.f; continue; }
+      const int64_t a = s0 + row;
+      const int i = L.mem[j];
+      if (i < 0) *dst = (float)pr.bmean[a];
+      else cp_async4(dst, W + a * N + i);
+    }
+    cp_async_commit();
   };
   // first lanes: rank 0 takes kJ systems and pushes their ids to every CTA
   if (crank == 0 && warp == 0) {
@@ -344,6 +383,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
   }
   cluster.sync();
   if (tid < kJ) lane_scalars(tid, L.newsid[tid]);
+  lane_masks();
   __syncthreads();
   lane_vectors_all();
   cluster.sync();   // all CTAs initialized before anyone pushes into their windows
@@ -434,6 +474,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       }
       L.alpha[j] = alpha;
     }
+    cp_async_wait_all();   // right-hand sides of lanes started in the previous step
     __syncthreads();
     // ---------------- x += alpha p, r -= alpha y; partial rr, Phi^T r, A^T r ----------------
     float4 trr[kTrRows];   // (T r) of this thread's rows and its warp's four lanes (learned term)
@@ -448,11 +489,22 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       for (int i = 0; i < 32; ++i) { v0[i] = 0.f; v1[i] = 0.f; }
 #pragma unroll
       for (int i = 0; i < 16; ++i) v2[i] = 0.f;
+      bool sc[4];
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) sc[jj] = L.state[j0 + jj] == kStart && L.mem[j0 + jj] >= 0;
+      const bool any_sc = sc[0] | sc[1] | sc[2] | sc[3];
       for (int row = lane; row < nrows; row += 32) {
         const float4 p4 = ld4(pw + (row + hl) * kLD + j0);
         const float4 y4 = ld4(vy + (row + kTH) * kLD + j0);
         float4 x4 = ld4(vx + row * kLD + j0);
         float4 r4 = ld4(vr + row * kLD + j0);
+        if (any_sc) {                                   // b = R^-1/2 w of a lane started last step
+          const float ri = s_rinv[row];
+          if (sc[0]) r4.x *= ri;
+          if (sc[1]) r4.y *= ri;
+          if (sc[2]) r4.z *= ri;
+          if (sc[3]) r4.w *= ri;
+        }
         x4.x = fmaf(a0, p4.x, x4.x); x4.y = fmaf(a1, p4.y, x4.y);
         x4.z = fmaf(a2, p4.z, x4.z); x4.w = fmaf(a3, p4.w, x4.w);
         r4.x = fmaf(-a0, y4.x, r4.x); r4.y = fmaf(-a1, y4.y, r4.y);
@@ -598,19 +650,26 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
 #pragma unroll
       for (int pass = 0; pass < 2; ++pass) {
         const int j = j0 + 2 * pass + (lane >> 4);
-        float f = 0.f, g = 0.f;
-        if (mv)
-          for (int c = 0; c < CS; ++c) {
-            f += s_res_in[c][j][4 + m];
-            g += s_res_in[c][j][4 + kK + m];
-          }
+        // pairwise (tree) sums over the cluster's partials, the same order in every CTA
+        float fc[kMaxCS], gc[kMaxCS];
+#pragma unroll
+        for (int c = 0; c < kMaxCS; ++c) {
+          fc[c] = (mv && c < CS) ? s_res_in[c][j][4 + m] : 0.f;
+          gc[c] = (mv && c < CS) ? s_res_in[c][j][4 + kK + m] : 0.f;
+        }
+#pragma unroll
+        for (int w2 = 1; w2 < kMaxCS; w2 <<= 1)
+#pragma unroll
+          for (int c = 0; c + w2 < kMaxCS; c += 2 * w2) { fc[c] += fc[c + w2]; gc[c] += gc[c + w2]; }
+        const float f = fc[0], g = gc[0];
         const float sg = L.sigf[j];
         const float rth = mv ? __frcp_rn(s_theta[m] + sg) : 0.f;   // (T_q)^-1 entry
         const float t = f * rth;
         float t2 = g + sg * f;
-        for (int i = 0; i < k; ++i) {
+#pragma unroll
+        for (int i = 0; i < kK; ++i) {
           const float ti = __shfl_sync(0xffffffffu, t, (lane & 16) + i);
-          if (mv) {
+          if (mv && i < k) {
             const float G = s_gram[2][m * k + i] + sg * (s_gram[1][m * k + i] + s_gram[1][i * k + m]) +
                             sg * sg * s_gram[0][m * k + i];
             t2 = fmaf(-G, ti, t2);
@@ -625,11 +684,23 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
 #pragma unroll
         for (int o = 8; o > 0; o >>= 1) corr += __shfl_xor_sync(0xffffffffu, corr, o);
         if (m == 0) {
-          float hi = 0.f, lo = 0.f, hu = 0.f, lu = 0.f;
-          for (int c = 0; c < CS; ++c) {
-            ff_merge(hi, lo, s_res_in[c][j][0], s_res_in[c][j][1]);
-            ff_merge(hu, lu, s_res_in[c][j][2], s_res_in[c][j][3]);
+          float rh[kMaxCS], rl[kMaxCS], uh[kMaxCS], ul[kMaxCS];
+#pragma unroll
+          for (int c = 0; c < kMaxCS; ++c) {
+            const bool in = c < CS;
+            rh[c] = in ? s_res_in[c][j][0] : 0.f;
+            rl[c] = in ? s_res_in[c][j][1] : 0.f;
+            uh[c] = in ? s_res_in[c][j][2] : 0.f;
+            ul[c] = in ? s_res_in[c][j][3] : 0.f;
           }
+#pragma unroll
+          for (int w2 = 1; w2 < kMaxCS; w2 <<= 1)
+#pragma unroll
+            for (int c = 0; c + w2 < kMaxCS; c += 2 * w2) {
+              ff_merge(rh[c], rl[c], rh[c + w2], rl[c + w2]);
+              ff_merge(uh[c], ul[c], uh[c + w2], ul[c + w2]);
+            }
+          const float hi = rh[0], lo = rl[0], hu = uh[0], lu = ul[0];
           L.rrh[j] = hi;
           L.rrl[j] = lo;
           const float rr = hi + lo;
@@ -756,10 +827,9 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
     cluster.sync();   // (3)
     // ---------------- refills, exit test, halo ----------------
     if (tid < kJ && L.fin[tid]) lane_scalars(tid, L.newsid[tid]);
+    lane_masks();
     __syncthreads();
-    int live = 0;
-    for (int j = 0; j < kJ; ++j) live |= L.state[j] != kEmpty;
-    if (!live) break;
+    if (!s_live) break;
     lane_vectors_all();   // lanes started in this step: own rows of r and x
     __syncthreads();
   }
