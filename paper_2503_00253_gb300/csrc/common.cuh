@@ -183,6 +183,55 @@ __device__ __forceinline__ double philox_normal(uint64_t seed, uint64_t e) {
   return (e & 1) ? rad * sin(2.0 * kPi * u2) : rad * cos(2.0 * kPi * u2);
 }
 
+// Standard normals in FP32 arithmetic from the same counter scheme (the
+// mixed-precision path stores the test matrix in FP32 anyway).
+__device__ __forceinline__ float philox_normal_f(uint64_t seed, uint64_t e) {
+  const uint64_t t = e >> 1;
+  const uint4 o = philox4x32_10(make_uint4((uint32_t)t, (uint32_t)(t >> 32), 0u, 0u),
+                                make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+  const float u1 = fmaf((float)o.x, 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+  const float u2 = fmaf((float)o.y, 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+  const float rad = sqrtf(-2.f * logf(u1));
+  float sv, cv;
+  sincospif(2.f * u2, &sv, &cv);
+  return (e & 1) ? rad * sv : rad * cv;
+}
+
+// Float-float arithmetic (a value is hi + lo, |lo| <= ulp(hi) / 2): about 48
+// significant bits from FP32 operations (Dekker's TwoProd through fma,
+// Knuth's TwoSum), used where FP64 instruction latency would dominate.
+struct FF {
+  float h, l;
+};
+__device__ __forceinline__ FF ff_norm(float s, float e) {
+  const float h = s + e;
+  return FF{h, e - (h - s)};
+}
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+  const float p = a.h * b.h;
+  const float e = fmaf(a.h, b.h, -p) + fmaf(a.h, b.l, a.l * b.h);
+  return ff_norm(p, e);
+}
+__device__ __forceinline__ FF ff_sub(FF a, FF b) {
+  const float s = a.h - b.h;
+  const float v = s - a.h;
+  const float e = ((a.h - (s - v)) - (b.h + v)) + (a.l - b.l);
+  return ff_norm(s, e);
+}
+__device__ __forceinline__ FF ff_from(double x) {
+  const float h = (float)x;
+  return FF{h, (float)(x - (double)h)};
+}
+// 1 / sqrt(g) for g > 0: FP32 seed, one Newton step with the residual
+// 1 - g y0^2 formed exactly enough in float-float arithmetic.
+__device__ __forceinline__ FF ff_rsqrt(FF g) {
+  const float y0 = rsqrtf(g.h);
+  const float p = y0 * y0, pe = fmaf(y0, y0, -p);      // y0^2 = p + pe exactly
+  const float t = g.h * p, te = fmaf(g.h, p, -t);      // g.h p = t + te exactly
+  const float r = (1.f - t) - (te + fmaf(g.h, pe, g.l * p));
+  return ff_norm(y0, 0.5f * y0 * r);
+}
+
 // ---------------------------------------------------------------------------
 // Accumulators.  For FP64 vectors a plain double sum.  For FP32 vectors a
 // float-float (hi, lo) pair: products are split exactly with an FMA and

@@ -118,6 +118,8 @@ void launch_band_obs(const ProblemTable& tab, const ProblemDev* dtab, cudaStream
 void launch_band_state(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st);
 void launch_quadrature(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st);
 void launch_ritz(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st);
+int launch_ritz_cluster(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st);
+bool ritz_cluster_fits(int64_t d, int l);
 int launch_pcg(const ProblemTable& tab, const ProblemDev* dtab, int32_t* counter, void* scratch,
                size_t scratch_bytes, int num_sms, cudaStream_t st);
 void launch_finish(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st);

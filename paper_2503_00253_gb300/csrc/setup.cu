@@ -508,66 +508,61 @@ __global__ void k_ritz_gram(const ProblemDev* tab, int srcA, int srcB, int sym) 
 }
 
 // X_dst = X_src R^-1 with G = R^T R the Cholesky factorization of the Gram
-// matrix in Gm.  Right-looking factorization by warp 0 (lane c owns column c):
-// each step takes the pivot's reciprocal square root (FP32 seed, two Newton
-// steps in FP64), scales row j and updates the trailing upper triangle, so the
-// dependent FP64 chain is a few operations per column.  A non-positive pivot
-// zeroes that column (rank loss) and flags kStatEigFail.  R goes to shared
-// memory in the bulk type for the triangular solve, one thread per row.
+// matrix in Gm.  Right-looking factorization in float-float arithmetic by four
+// warps: warp 0 takes the pivot's reciprocal square root, all threads scale
+// row j and update the trailing upper triangle.  A non-positive pivot zeroes
+// that column (rank loss) and flags kStatEigFail.  R goes to shared memory in
+// the bulk type for the triangular solve, one thread per row.
 template <typename T>
 __global__ void k_ritz_orth(const ProblemDev* tab, int src) {
   const ProblemDev& pr = tab[blockIdx.y];
   const int l = pr.l;
   if (l <= 0) return;
-  __shared__ double G[kMaxRitz][kMaxRitz + 1];
-  __shared__ double Rrow[kMaxRitz];
-  __shared__ double s_inv;
+  __shared__ FF G[kMaxRitz][kMaxRitz + 1];
+  __shared__ FF Rrow[kMaxRitz];
+  __shared__ FF s_inv;
+  __shared__ float s_tiny;
   __shared__ T Rt[kMaxRitz][kMaxRitz + 1];
   __shared__ T rinv[kMaxRitz];
-  for (int e = threadIdx.x; e < l * l; e += blockDim.x) G[e / l][e % l] = pr.Gm[e];
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+    const int i = e / l, c = e % l;
+    if (i <= c) G[i][c] = ff_from(pr.Gm[e]);
+  }
+  if (threadIdx.x < 32) {
+    float tr = threadIdx.x < l ? (float)pr.Gm[threadIdx.x * (l + 1)] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    if (threadIdx.x == 0) s_tiny = 1e-28f * (tr > 0.f ? tr : 1.f);
+  }
   __syncthreads();
-  // FP64 work is spread over four warps (one per SM sub-partition): the pivot by
-  // warp 0, the row scaling and the trailing update of the upper triangle by all.
   constexpr int kCT = 128;
   const int t = threadIdx.x;
   if (t < kCT) {
-    double tiny = 0.0;
-    if (t < 32) {
-      double tr = t < l ? G[t][t] : 0.0;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
-      tiny = 1e-28 * (tr > 0 ? tr : 1.0);
-    }
+    const float tiny = s_tiny;
     for (int j = 0; j < l; ++j) {
-      if (t < 32) {
-        // 1 / sqrt(G_jj): FP32 seed, one Newton step in FP64 (relative error ~1e-14)
-        const double gjj = G[j][j];
-        const bool ok = gjj > tiny;
-        double inv = 0.0;
-        if (ok) {
-          const double y = (double)rsqrtf((float)gjj);
-          inv = y * fma(-0.5 * gjj * y, y, 1.5);
-        }
-        if (t == 0) {
-          s_inv = inv;
-          Rt[j][j] = to_t<T>(gjj * inv);
-          rinv[j] = to_t<T>(inv);
-          if (!ok && blockIdx.x == 0) atomicOr(&pr.status[0], kStatEigFail);
-        }
+      if (t == 0) {
+        const FF gjj = G[j][j];
+        const bool ok = gjj.h > tiny;
+        const FF inv = ok ? ff_rsqrt(gjj) : FF{0.f, 0.f};
+        s_inv = inv;
+        const FF rjj = ff_mul(gjj, inv);
+        Rt[j][j] = (T)rjj.h + (T)rjj.l;
+        rinv[j] = (T)inv.h + (T)inv.l;
+        if (!ok && blockIdx.x == 0) atomicOr(&pr.status[0], kStatEigFail);
       }
       asm volatile("bar.sync 1, 128;" ::: "memory");
-      const double inv = s_inv;
+      const FF inv = s_inv;
       for (int c = j + 1 + t; c < l; c += kCT) {
-        const double r = G[j][c] * inv;
+        const FF r = ff_mul(G[j][c], inv);
         Rrow[c] = r;
-        Rt[j][c] = to_t<T>(r);
+        Rt[j][c] = (T)r.h + (T)r.l;
       }
       if (t < j) Rt[j][t] = T(0);
       asm volatile("bar.sync 1, 128;" ::: "memory");
       const int mrem = l - 1 - j;
       for (int e = t; e < mrem * mrem; e += kCT) {
         const int c2 = j + 1 + e / mrem, c = j + 1 + e % mrem;
-        if (c2 <= c) G[c2][c] -= Rrow[c2] * Rrow[c];
+        if (c2 <= c) G[c2][c] = ff_sub(G[c2][c], ff_mul(Rrow[c2], Rrow[c]));
       }
       asm volatile("bar.sync 1, 128;" ::: "memory");
     }
@@ -650,7 +645,9 @@ __global__ void k_ritz_jacobi(const ProblemDev* tab) {
   }
   int cur = 0;
   __syncthreads();
-  const int max_sweeps = sizeof(T) == 4 ? 12 : 30;
+  // cyclic Jacobi converges quadratically; six sweeps reach FP32 rounding for
+  // l <= 32 (the Ritz pairs only shape the preconditioner)
+  const int max_sweeps = sizeof(T) == 4 ? 6 : 30;
   const T eps = sizeof(T) == 4 ? T(1e-11) : T(1e-30);
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     {
@@ -728,99 +725,115 @@ __global__ void k_ritz_jacobi(const ProblemDev* tab) {
   }
 }
 
-// One-sided (Hestenes) Jacobi by one warp in FP32, for the mixed path: lane c
-// holds column c of U (starting as B) and of V (starting as I) in registers;
-// each round rotates the column pairs of the round-robin schedule so that they
-// become orthogonal, partners exchanging columns by shuffles (no barriers).
-// At convergence B V = U with orthogonal columns, so the columns of V are
-// eigenvectors and lambda_c = v_c . (B v_c) = v_c . u_c (sign kept).
-template <int LM>
-__global__ void k_ritz_jacobi_warp(const ProblemDev* tab) {
+// One-sided (Hestenes) cyclic Jacobi for the FP32 path: one warp per column
+// pair of a round (lane i holds row i), U = B, V = I initially; each round
+// rotates its pairs so that their columns of U become orthogonal.  At
+// convergence B V = U with orthogonal columns, so the columns of V are
+// eigenvectors and lambda_c = v_c . u_c (sign kept).  Squared column norms are
+// carried through the rotations (alpha' = alpha - t g, beta' = beta + t g) and
+// recomputed once per sweep.
+__global__ void k_ritz_jacobi_pairs(const ProblemDev* tab) {
   const ProblemDev& pr = tab[blockIdx.x];
   const int l = pr.l;
-  const int c = threadIdx.x;
   if (l <= 0) return;
-  float u[LM], v[LM];
-#pragma unroll
-  for (int i = 0; i < LM; ++i) {
-    u[i] = (i < l && c < l) ? (float)(0.5 * (pr.Gm[i * l + c] + pr.Gm[c * l + i])) : 0.f;
-    v[i] = (i == c && c < l) ? 1.f : 0.f;
+  __shared__ float U[kMaxRitz][kMaxRitz + 1], V[kMaxRitz][kMaxRitz + 1];
+  __shared__ float nrm[kMaxRitz];
+  __shared__ float s_scale;
+  __shared__ int8_t pair_p[kMaxRitz][kMaxRitz / 2], pair_q[kMaxRitz][kMaxRitz / 2];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int e = tid; e < l * l; e += blockDim.x) {
+    const int i = e / l, c = e % l;
+    U[i][c] = (float)(0.5 * (pr.Gm[i * l + c] + pr.Gm[c * l + i]));
+    V[i][c] = i == c ? 1.f : 0.f;
   }
-  const int m = (l + 1) & ~1;
-  // A pair counts as unconverged while the cosine of its columns exceeds 1e-5
-  // and |u_p . u_q| exceeds 2e-6 of the largest squared column norm: the FP32
-  // rounding noise of a small column (~eps |B|) keeps u_p . u_q near
-  // eps |B|^2 however long the sweeps go on.
-  float nrm = 0.f;   // |u_c|^2, kept up to date through the rotations
+  const int m = (l + 1) & ~1, npairs = m / 2;
+  // round-robin schedule (circle method): slot 0 fixed, slot s > 0 holds
+  // ((s - 1 + round) mod (m - 1)) + 1; pair w of a round joins slots w and m - 1 - w
+  for (int e = tid; e < (m - 1) * npairs; e += blockDim.x) {
+    const int round = e / npairs, w = e % npairs;
+    const int s1 = w, s2 = m - 1 - w;
+    int p = s1 == 0 ? 0 : ((s1 - 1 + round) % (m - 1)) + 1;
+    int q = ((s2 - 1 + round) % (m - 1)) + 1;
+    if (p > q) { const int x = p; p = q; q = x; }
+    pair_p[round][w] = (int8_t)p;
+    pair_q[round][w] = (int8_t)q;
+  }
+  __syncthreads();
+  auto refresh_norms = [&]() {
+    for (int c = warp; c < l; c += nw) {
+      const float u = lane < l ? U[lane][c] : 0.f;
+      float a = u * u;
 #pragma unroll
-  for (int i = 0; i < LM; ++i) nrm = fmaf(u[i], u[i], nrm);
-  float scale = nrm;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) scale = fmaxf(scale, __shfl_xor_sync(0xffffffffu, scale, o));
-  const float gabs = 2e-6f * scale;
-  // cyclic Jacobi converges quadratically: six sweeps reach FP32 rounding on
-  // these sizes (l <= 32), and the Ritz pairs only shape the preconditioner
-  for (int sweep = 0; sweep < 6; ++sweep) {
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (lane == 0) nrm[c] = a;
+    }
+  };
+  refresh_norms();
+  __syncthreads();
+  if (tid == 0) {
+    float mx = 0.f;
+    for (int c = 0; c < l; ++c) mx = fmaxf(mx, nrm[c]);
+    s_scale = mx;
+  }
+  __syncthreads();
+  // a pair stays unconverged while the cosine of its columns exceeds 1e-5 and
+  // |u_p . u_q| exceeds 2e-6 of the largest squared column norm (below that it
+  // is FP32 rounding noise of the small columns)
+  const float gabs = 2e-6f * s_scale;
+  // four sweeps: cyclic Jacobi is quadratically convergent, and the Ritz pairs
+  // only shape the preconditioner (a round costs a few hundred cycles of
+  // dependent latency, so the sweep count is the cost)
+  for (int sweep = 0; sweep < 4; ++sweep) {
     int busy = 0;
     for (int round = 0; round < m - 1; ++round) {
-      int p = c;   // partner of column c in this round (c itself: idle)
-      if (c < m) {
-        const int pos = c == 0 ? 0 : ((c - 1 - round) % (m - 1) + (m - 1)) % (m - 1) + 1;
-        const int ppos = m - 1 - pos;
-        p = ppos == 0 ? 0 : ((ppos - 1 + round) % (m - 1)) + 1;
-      }
-      const bool act = c < l && p < l && p != c;
-      if (!act) p = c;
-      float up[LM];
-      float g4[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int w = warp; w < npairs; w += nw) {
+        const int p = pair_p[round][w], q = pair_q[round][w];
+        if (q >= l) continue;
+        const float up = lane < l ? U[lane][p] : 0.f, uq = lane < l ? U[lane][q] : 0.f;
+        float g = up * uq;
 #pragma unroll
-      for (int i = 0; i < LM; ++i) {
-        up[i] = __shfl_sync(0xffffffffu, u[i], p);
-        g4[i & 3] = fmaf(u[i], up[i], g4[i & 3]);
-      }
-      const float g = (g4[0] + g4[1]) + (g4[2] + g4[3]);
-      const float nrm_p = __shfl_sync(0xffffffffu, nrm, p);
-      // same rotation on both lanes: al, be are the squared norms of the lower and upper column
-      const bool lower = c < p;
-      const float al = lower ? nrm : nrm_p, be = lower ? nrm_p : nrm;
-      float cs = 1.f, sn = 0.f, tt = 0.f;
-      if (act && g != 0.f) {
+        for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+        const float al = nrm[p], be = nrm[q];
+        if (g == 0.f) continue;
         busy |= fabsf(g) > gabs && fabsf(g) > 1e-5f * sqrtf(al * be);
+        // rotation from approximate reciprocals and roots: any orthogonal rotation
+        // keeps B V = U exact; these only change how fast the pair converges
         const float zeta = __fdividef(be - al, 2.f * g);
-        tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
-        cs = rsqrtf(fmaf(tt, tt, 1.f));
-        sn = cs * tt;
+        const float z2 = fmaf(zeta, zeta, 1.f);
+        const float tt = copysignf(1.f, zeta) * __fdividef(1.f, fabsf(zeta) + z2 * rsqrtf(z2));
+        const float cs = rsqrtf(fmaf(tt, tt, 1.f)), sn = cs * tt;
+        if (lane < l) {
+          U[lane][p] = cs * up - sn * uq;
+          U[lane][q] = sn * up + cs * uq;
+          const float vp = V[lane][p], vq = V[lane][q];
+          V[lane][p] = cs * vp - sn * vq;
+          V[lane][q] = sn * vp + cs * vq;
+        }
+        if (lane == 0) {
+          nrm[p] = fmaxf(al - tt * g, 0.f);
+          nrm[q] = fmaxf(be + tt * g, 0.f);
+        }
       }
-      // [x_lo, x_hi] <- [cs x_lo - sn x_hi, sn x_lo + cs x_hi]
-      const float f_own = cs, f_oth = lower ? -sn : sn;
-#pragma unroll
-      for (int i = 0; i < LM; ++i) {
-        u[i] = f_own * u[i] + f_oth * up[i];
-        const float vp = __shfl_sync(0xffffffffu, v[i], p);
-        v[i] = f_own * v[i] + f_oth * vp;
-      }
-      nrm = fmaxf(lower ? al - tt * g : be + tt * g, 0.f);
+      __syncthreads();
     }
-    // refresh the norms from the columns once per sweep
-    nrm = 0.f;
-#pragma unroll
-    for (int i = 0; i < LM; ++i) nrm = fmaf(u[i], u[i], nrm);
-    if (!__any_sync(0xffffffffu, busy)) break;
+    refresh_norms();
+    if (!__syncthreads_or(busy)) break;
   }
-  float lam = 0.f;
+  // eigenvalues (Rayleigh quotients) and the descending order
+  __shared__ float lam[kMaxRitz];
+  for (int c = warp; c < l; c += nw) {
+    float a = lane < l ? V[lane][c] * U[lane][c] : 0.f;
 #pragma unroll
-  for (int i = 0; i < LM; ++i) lam = fmaf(v[i], u[i], lam);
-  // descending order
-  int rank = 0;
-  for (int o = 0; o < l; ++o) {
-    const float lo = __shfl_sync(0xffffffffu, lam, o);
-    rank += (lo > lam) || (lo == lam && o < c);
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) lam[c] = a;
   }
-  if (c < l) {
-    pr.ev[rank] = (double)lam;
-#pragma unroll
-    for (int i = 0; i < LM; ++i)
-      if (i < l) pr.Rm[i * l + rank] = (double)v[i];
+  __syncthreads();
+  if (tid < l) {
+    const float di = lam[tid];
+    int rank = 0;
+    for (int u = 0; u < l; ++u) rank += (lam[u] > di) || (lam[u] == di && u < tid);
+    pr.ev[rank] = (double)di;
+    for (int u = 0; u < l; ++u) pr.Rm[u * l + rank] = (double)V[u][tid];
   }
 }
 
@@ -923,11 +936,7 @@ static void launch_ritz_t(const ProblemTable& tab, const ProblemDev* dtab, cudaS
   orth2(cur);                                               // basis in buf[cur]
   matvec();                                                 // image in buf[1-cur]
   k_ritz_gram<T><<<gll, 256, 0, st>>>(dtab, cur, 1 - cur, 0);   // Gm = Q^T (C Q)
-  if (sizeof(T) == 4) {
-    if (lmax <= 16) k_ritz_jacobi_warp<16><<<tab.count, 32, 0, st>>>(dtab);
-    else if (lmax <= 24) k_ritz_jacobi_warp<24><<<tab.count, 32, 0, st>>>(dtab);
-    else k_ritz_jacobi_warp<32><<<tab.count, 32, 0, st>>>(dtab);
-  }
+  if (sizeof(T) == 4) k_ritz_jacobi_pairs<<<tab.count, 32 * ((lmax + 1) / 2), 0, st>>>(dtab);
   else k_ritz_jacobi<T><<<tab.count, kMaxRitz * kMaxRitz, 0, st>>>(dtab);
   k_ritz_vectors<T><<<gd, 256, 0, st>>>(dtab, cur);
   k_ritz_grams<T><<<dim3(3 * kmax * kmax, tab.count), 256, 0, st>>>(dtab);
@@ -935,8 +944,18 @@ static void launch_ritz_t(const ProblemTable& tab, const ProblemDev* dtab, cudaS
 }
 
 void launch_ritz(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st) {
-  if (tab.p[0].precision == 0) launch_ritz_t<double>(tab, dtab, st);
-  else launch_ritz_t<float>(tab, dtab, st);
+  if (tab.p[0].precision == 0) {
+    launch_ritz_t<double>(tab, dtab, st);
+    return;
+  }
+  // FP32: one cluster launch for the whole stage when every problem fits it
+  bool fused = true;
+  for (int i = 0; i < tab.count; ++i) {
+    const ProblemDev& p = tab.p[i];
+    fused &= p.l > 0 && p.kR > 0 && p.l <= kMaxRitz && p.kR <= kMaxK && ritz_cluster_fits(p.d, p.l);
+  }
+  if (fused && launch_ritz_cluster(tab, dtab, st) == 0) return;
+  launch_ritz_t<float>(tab, dtab, st);
 }
 
 }  // namespace infoesrf
