@@ -38,7 +38,7 @@ TRAIN_SEEDS = (11, 12, 13)
 # DRAM bytes (read + write) of one k_pcg_band1d launch on this workload with the
 # learned correction, from the ncu capture summarised in
 # profiles/k_pcg_band1d_gauss1d_n8192_N40_d1024_Q32_fp32_learned.md; set to None when the kernel changes.
-PCG_DRAM_BYTES = 1620224
+PCG_DRAM_BYTES = 1448960
 
 
 def _dist():
@@ -203,14 +203,14 @@ def run_ours(args):
     if args.graph:
         B.set_phase_events(opts, None)           # timing events cannot be recorded inside a graph
         try:
-            cap = torch.cuda.Stream(dev)
-            cap.wait_stream(stream)
+            cap_stream = torch.cuda.Stream(dev)
+            cap_stream.wait_stream(stream)
             g_ = torch.cuda.CUDAGraph()
             n_cap0 = B.launch_count()
-            with torch.cuda.graph(g_, stream=cap):
+            with torch.cuda.graph(g_, stream=cap_stream):
                 B.info_esrf_analysis(pr.grid, X, obs, y, R, pr.Q, tol, opts, ws=wsp, mu_a=mu_a, A_a=A_a,
-                                     stats=False, stream=cap)
-            stream.wait_stream(cap)
+                                     stats=False, stream=cap_stream)
+            stream.wait_stream(cap_stream)
             graph_launches = B.launch_count() - n_cap0
             graph = g_
             for _ in range(args.warmup):
