@@ -153,9 +153,8 @@ def config2(tol: float = 1e-12, seed: int = 2) -> Problem:
 
 def ll96_tendency(X: np.ndarray, F: float, gamma: float) -> np.ndarray:
     """dX/dt for states X[..., nz, nx] (layer-major, longitude periodic)."""
-    xm1 = np.roll(X, 1, axis=-1)
-    xp1 = np.roll(X, -1, axis=-1)
-    xm2 = np.roll(X, 2, axis=-1)
+    P = np.concatenate([X[..., -2:], X, X[..., :1]], axis=-1)   # periodic halo: 2 left, 1 right
+    xm2, xm1, xp1 = P[..., :-3], P[..., 1:-2], P[..., 3:]
     dX = xm1 * (xp1 - xm2) - X + F
     coup = np.zeros_like(X)
     coup[..., 1:, :] += gamma * (X[..., :-1, :] - X[..., 1:, :])
