@@ -149,6 +149,16 @@ def run_ours(args):
                       "loss_first": float(hist[0]), "loss_last": float(hist[-1]), "max_shift": cutoff}
     opts = B.make_options(precision=prec, ritz_rank=RITZ, max_neighbors=cap, learned_model=theta,
                           learned_max_shift=cutoff)
+    # native autotuner (untimed): cluster size, power iterations and oversampling of the eigensolver,
+    # the settings that do not change the converged answer
+    tune_info = None
+    if args.autotune:
+        t0 = time.perf_counter()
+        best = B.autotune([dict(grid=pr.grid, X=X, obs_idx=obs, y=y, R=R, Q=pr.Q, tol=tol, max_oo=max_oo,
+                                max_xo=max_xo)], opts)
+        torch.cuda.synchronize()
+        tune_info = {"cluster_size": int(opts.cluster_size), "power_iters": int(opts.power_iters),
+                     "oversample": int(opts.oversample), "best_ms": best, "tune_s": time.perf_counter() - t0}
     g = B.make_grid(pr.grid)
     import ctypes
     need = B.library().info_esrf_workspace_size(ctypes.byref(g), N, d, pr.Q, ctypes.byref(opts))
@@ -176,12 +186,16 @@ def run_ours(args):
         result["rel_err_mean"] = float(np.linalg.norm(mu_a.cpu().numpy() - mu_ref) / np.linalg.norm(mu_ref - mu0))
 
     # exact band size and per-system iteration counts for the algorithmic flop count
-    prep = B.Prepared(pr.grid, X, obs, R, pr.Q, B.make_options(precision=prec, ritz_rank=RITZ, max_neighbors=cap))
+    prep = B.Prepared(pr.grid, X, obs, R, pr.Q, B.make_options(precision=prec, ritz_rank=RITZ, max_neighbors=cap,
+                                                              oversample=int(opts.oversample),
+                                                              power_iters=int(opts.power_iters)))
     nnz_C = int(prep.export("oo_nnz").sum())
     del prep
     it_sys = torch.zeros(1 + pr.Q * N, dtype=torch.int32, device=dev)
     o_it = B.make_options(precision=prec, ritz_rank=RITZ, max_neighbors=cap, learned_model=theta,
-                          learned_max_shift=cutoff, system_iters=it_sys)
+                          learned_max_shift=cutoff, system_iters=it_sys, oversample=int(opts.oversample),
+                          power_iters=int(opts.power_iters))
+    o_it.cluster_size = opts.cluster_size
     B.info_esrf_analysis(pr.grid, X, obs, y, R, pr.Q, tol, o_it, ws=wsp, mu_a=mu_a, A_a=A_a, stats=False,
                          stream=stream)
     it_sys = it_sys.cpu().numpy().astype(np.float64)
@@ -376,6 +390,8 @@ def run_ours(args):
     line.update(comparators)
     if learn_info:
         line["learned"] = learn_info
+    if tune_info:
+        line["autotune"] = tune_info
     if not args.no_cpu_baseline:
         from oracle import filter as F  # noqa: F401
         t0 = time.perf_counter()
@@ -401,6 +417,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--preconditioner", default="learned", choices=["learned", "lmp"])
     ap.add_argument("--graph", type=int, default=1, help="replay the analysis as a CUDA graph (0: direct calls)")
+    ap.add_argument("--autotune", type=int, default=1, help="run the native autotuner before the timed region")
     ap.add_argument("--fp64-tol", type=float, default=1e-12)
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-parity", action="store_true")

@@ -85,7 +85,7 @@ typedef struct {
   int32_t max_iter;       /* PCG iteration cap; default 1000 */
   int32_t fixed_iters;    /* > 0: run exactly this many PCG iterations (paper's experiments) */
   int32_t rule;           /* INFO_ESRF_RULE_*; default elliptic */
-  int32_t reserved;       /* set to 0 */
+  int32_t cluster_size;   /* CTAs per cluster of the FP32 cluster-resident PCG kernel: 0 = chosen from d, or 2, 4, 8 */
   double ell;             /* spectrum bound of App. D; <= 0: power of ten above a Gershgorin bound of C */
   uint64_t seed;          /* Philox key of the randomized eigensolver's test matrix */
   int64_t max_neighbors;  /* band capacity per row; <= 0: bound from the geometry */
@@ -194,6 +194,19 @@ int info_esrf_analysis(const info_esrf_grid* grid, int64_t N, const double* X_de
 int info_esrf_analysis_batched(const info_esrf_problem* probs, int32_t count,
                                const info_esrf_options* opt, void* workspace, size_t ws_bytes,
                                void* stream, info_esrf_stats* stats);
+
+/* Autotuner (not in the paper): times the analysis of probs[0..count) with
+ * each candidate setting of the launch and eigensolver parameters that do not
+ * change the converged answer -- cluster_size (0 or 4), power_iters (0 or 1)
+ * and oversample (6 or 10) -- starting from *opt, and writes the fastest into
+ * *opt (other fields untouched).  A candidate whose warm-up run leaves a
+ * system unconverged, fails, or needs more workspace than ws_bytes is skipped.
+ * Each candidate runs once untimed and three times timed (CUDA events on
+ * stream); the problems' outputs are overwritten and the stream is
+ * synchronized.  best_ms (host, may be NULL) receives the fastest mean time
+ * per call.  Returns 0, or the first error of the base setting. */
+int info_esrf_autotune(const info_esrf_problem* probs, int32_t count, info_esrf_options* opt, void* workspace,
+                       size_t ws_bytes, void* stream, double* best_ms);
 
 /* Allocation-free variant of info_esrf_analysis.  The paper has no
  * counterpart: this is a deployment convenience of this library.

@@ -48,7 +48,7 @@ class Grid(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("ritz_rank", c_int32), ("oversample", c_int32),
                 ("power_iters", c_int32), ("max_iter", c_int32), ("fixed_iters", c_int32),
-                ("rule", c_int32), ("reserved", c_int32), ("ell", c_double), ("seed", c_uint64),
+                ("rule", c_int32), ("cluster_size", c_int32), ("ell", c_double), ("seed", c_uint64),
                 ("max_neighbors", c_int64), ("learned_model", c_void_p), ("learned_max_shift", c_double),
                 ("system_iters", c_void_p), ("phase_events", ctypes.POINTER(c_void_p))]
 
@@ -135,6 +135,8 @@ def library() -> ctypes.CDLL:
                                                c_int32, P(Options), c_void_p, ctypes.c_size_t, c_int32,
                                                c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
                                                c_void_p]),
+        "info_esrf_autotune": (c_int32, [P(ProblemC), c_int32, P(Options), c_void_p, ctypes.c_size_t, c_void_p,
+                                          P(c_double)]),
         "info_esrf_model_save": (c_int32, [ctypes.c_char_p, c_void_p, c_double]),
         "info_esrf_model_load": (c_int32, [ctypes.c_char_p, c_void_p, P(c_double)]),
         "info_esrf_fma_probe": (c_int32, [c_int32, c_int64, P(c_double), P(c_double), c_void_p]),
@@ -362,6 +364,37 @@ def info_esrf_analysis_batched(problems: Sequence[dict], options: Optional[Optio
                                                 _stream(stream), st if stats else None)
     _check(code, "info_esrf_analysis_batched")
     return keep, ([s.as_dict() for s in st] if stats else None)
+
+
+def autotune(problems: Sequence[dict], options: Options, ws: Optional[torch.Tensor] = None, stream=None):
+    """Times the candidate settings on these problems (overwriting their outputs) and writes the fastest
+    cluster_size, power_iters and oversample into `options`.  Returns the best time per call (ms)."""
+    arr = (ProblemC * len(problems))()
+    keep = []
+    for i, p in enumerate(problems):
+        X = p["X"]
+        _need(X, torch.float64, "X")
+        N, n = X.shape
+        mu_a = p.get("mu_a")
+        A_a = p.get("A_a")
+        if mu_a is None:
+            mu_a = torch.empty(n, dtype=torch.float64, device=X.device)
+        if A_a is None:
+            A_a = torch.empty((N, n), dtype=torch.float64, device=X.device)
+        keep.append((mu_a, A_a))
+        c = arr[i]
+        c.grid = make_grid(p["grid"])
+        c.N, c.d, c.Q, c.tol = N, p["obs_idx"].numel(), int(p["Q"]), float(p["tol"])
+        c.X, c.obs_idx, c.y, c.R_diag = X.data_ptr(), p["obs_idx"].data_ptr(), p["y"].data_ptr(), p["R"].data_ptr()
+        c.mu_a, c.A_a = mu_a.data_ptr(), A_a.data_ptr()
+        c.max_oo, c.max_xo = int(p.get("max_oo", 0)), int(p.get("max_xo", 0))
+    need = library().info_esrf_batched_workspace_size(arr, len(problems), ctypes.byref(options))
+    if ws is None or ws.numel() < need:
+        ws = workspace(need)
+    best = c_double(0.0)
+    _check(library().info_esrf_autotune(arr, len(problems), ctypes.byref(options), ws.data_ptr(), ws.numel(),
+                                        _stream(stream), ctypes.byref(best)), "info_esrf_autotune")
+    return best.value
 
 
 def info_esrf_philox_normals(seed: int, count: int, device="cuda", stream=None) -> torch.Tensor:

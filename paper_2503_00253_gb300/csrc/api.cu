@@ -103,7 +103,8 @@ int check_options(const info_esrf_options* in, info_esrf_options* out) {
   if (out->power_iters < 0 || out->power_iters > 8) return INFO_ESRF_ERR_INVALID_ARG;
   if (out->max_iter < 1 && out->fixed_iters <= 0) return INFO_ESRF_ERR_INVALID_ARG;
   if (out->rule != 0 && out->rule != 1) return INFO_ESRF_ERR_INVALID_ARG;
-  if (out->reserved != 0) return INFO_ESRF_ERR_INVALID_ARG;
+  if (out->cluster_size != 0 && out->cluster_size != 2 && out->cluster_size != 4 && out->cluster_size != 8)
+    return INFO_ESRF_ERR_INVALID_ARG;
   return 0;
 }
 
@@ -154,6 +155,7 @@ int build_table(const info_esrf_problem* probs, int32_t count, const info_esrf_o
   if (count > kMaxProblems) return INFO_ESRF_ERR_UNSUPPORTED;
   memset(&tab, 0, sizeof(tab));
   tab.count = count;
+  tab.cluster_size = o.cluster_size;
   Carver cv{reinterpret_cast<char*>(ws)};
   ProblemDev* dtab = cv.take<ProblemDev>(sizeof(ProblemDev) * count);
   int32_t* counter = cv.take<int32_t>(64);
@@ -299,21 +301,23 @@ int run_batch(const info_esrf_problem* probs, int32_t count, const info_esrf_opt
   // the quadrature and the state-obs band overlap the Ritz stage on a side
   // stream, which rejoins before the first use of each
   AuxStream* aux = aux_stream();
+  // the learned coefficients need only the quadrature and the band's scalars
   if (aux) {
     cudaEventRecord(aux->mid, st);
     cudaStreamWaitEvent(aux->s, aux->mid, 0);
     launch_quadrature(tab, dtab, aux->s);
+    launch_learn_coef(tab, dtab, aux->s);
     cudaEventRecord(aux->jq, aux->s);
     launch_band_state(tab, dtab, aux->s);
     cudaEventRecord(aux->jb, aux->s);
   } else {
     launch_quadrature(tab, dtab, st);
+    launch_learn_coef(tab, dtab, st);
     launch_band_state(tab, dtab, st);
   }
   mark(1);
   launch_ritz(tab, dtab, st);
   if (aux) cudaStreamWaitEvent(st, aux->jq, 0);
-  launch_learn_coef(tab, dtab, st);
   mark(2);
   if (launch_pcg(tab, dtab, counter, scratch, scratch_bytes, sms, st) != 0) {
     if (aux) cudaStreamWaitEvent(st, aux->jb, 0);
@@ -404,7 +408,7 @@ void info_esrf_default_options(info_esrf_options* opt) {
   opt->max_iter = 1000;
   opt->fixed_iters = 0;
   opt->rule = INFO_ESRF_RULE_ELLIPTIC;
-  opt->reserved = 0;
+  opt->cluster_size = 0;
   opt->ell = 0.0;
   opt->seed = 0x1234abcdULL;
   opt->max_neighbors = 0;
@@ -500,6 +504,69 @@ int info_esrf_analysis(const info_esrf_grid* grid, int64_t N, const double* X_de
   if (!mu_a_dev || !A_a_dev) return INFO_ESRF_ERR_INVALID_ARG;
   info_esrf_problem P = one_problem(grid, N, X_dev, d, obs_idx_dev, y_dev, R_diag_dev, Q, tol, mu_a_dev, A_a_dev);
   return run_batch(&P, 1, opt, workspace, ws_bytes, stream, stats);
+}
+
+int info_esrf_autotune(const info_esrf_problem* probs, int32_t count, info_esrf_options* opt, void* workspace,
+                       size_t ws_bytes, void* stream, double* best_ms) {
+  if (!probs || !opt || count < 1) return INFO_ESRF_ERR_INVALID_ARG;
+  info_esrf_options base;
+  int rc = check_options(opt, &base);
+  if (rc) return rc;
+  base.phase_events = nullptr;
+  base.system_iters = nullptr;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    return INFO_ESRF_ERR_CUDA;
+  }
+  std::vector<info_esrf_stats> stats((size_t)count);
+  double best = -1.0;
+  info_esrf_options best_o = base;
+  int first_rc = 0;
+  const int cs_list[2] = {0, 4}, pi_list[2] = {0, 1}, os_list[2] = {6, 10};
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b)
+      for (int c = 0; c < 2; ++c) {
+        info_esrf_options o = base;
+        o.cluster_size = cs_list[a];
+        o.power_iters = pi_list[b];
+        o.oversample = os_list[c];
+        if (o.ritz_rank + o.oversample > kMaxRitz) continue;
+        if (info_esrf_batched_workspace_size(probs, count, &o) > ws_bytes) continue;
+        int r = run_batch(probs, count, &o, workspace, ws_bytes, stream, stats.data());
+        if (r < 0) {
+          if (!first_rc) first_rc = r;
+          continue;
+        }
+        bool ok = true;
+        for (int i = 0; i < count; ++i) ok &= stats[i].n_unconverged == 0 && stats[i].status == 0;
+        if (!ok) continue;
+        cudaEventRecord(e0, st);
+        for (int rep = 0; rep < 3; ++rep) run_batch(probs, count, &o, workspace, ws_bytes, stream, nullptr);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          return INFO_ESRF_ERR_CUDA;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per = ms / 3.0;
+        if (best < 0.0 || per < best) {
+          best = per;
+          best_o = o;
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best < 0.0) return first_rc ? first_rc : INFO_ESRF_ERR_UNSUPPORTED;
+  opt->cluster_size = best_o.cluster_size;
+  opt->power_iters = best_o.power_iters;
+  opt->oversample = best_o.oversample;
+  if (best_ms) *best_ms = best;
+  return INFO_ESRF_OK;
 }
 
 int info_esrf_analysis_batched(const info_esrf_problem* probs, int32_t count, const info_esrf_options* opt,

@@ -106,7 +106,7 @@ struct ProblemTable {
   int32_t count;
   int32_t total_groups;
   int32_t total_sys;
-  int32_t pad_;
+  int32_t cluster_size;         // options.cluster_size (0: chosen from d)
   ProblemDev p[kMaxProblems];
 };
 

@@ -852,7 +852,7 @@ int launch_pcg_band1d(const ProblemTable& tab, const ProblemDev* dtab, int32_t* 
   const ProblemDev& p = tab.p[0];
   // cluster size: 8 CTAs unless a CTA would own fewer than two row tiles; the
   // kernel itself checks the band reach and the shared-memory budget
-  int CS = 8;
+  int CS = tab.cluster_size > 0 ? tab.cluster_size : 8;
   while (CS > 1 && (p.d + CS - 1) / CS < 2 * kTile) CS >>= 1;
   int clusters = (p.nsys + kJ - 1) / kJ;
   if (clusters > num_sms / CS) clusters = num_sms / CS;

@@ -492,3 +492,21 @@ def test_layered_l96_cycling_tracks_truth(B):
     assert np.mean(rmse_a[30:]) < 0.45 * clim, (rmse_a, clim)
     assert np.mean(rmse_a[30:]) < 0.6 * np.mean(rmse_a[:5])
     assert np.mean(rmse_a) < np.mean(rmse_f)
+
+
+def test_autotune_picks_a_converging_setting_and_keeps_parity(B):
+    """The native autotuner times cluster size, power iterations and oversampling on the caller's
+    problem and returns one of its candidates; the tuned analysis still matches the oracle."""
+    pr = workloads.gaussian_problem_1d("tune", n=4096, N=16, length_scale=32.0, obs_stride=4, r2=0.25,
+                                       half_width=128.0, Q=12, tol=1e-6, seed=51)
+    probs = [dict(grid=pr.grid, X=dev(pr.X), obs_idx=dev(pr.obs_idx), y=dev(pr.y), R=dev(pr.R), Q=pr.Q, tol=1e-6)]
+    opts = B.make_options(precision=1)
+    best = B.autotune(probs, opts)
+    assert best > 0.0
+    assert opts.cluster_size in (0, 4) and opts.power_iters in (0, 1) and opts.oversample in (6, 10)
+    mu_a, A_a, st = B.info_esrf_analysis(pr.grid, probs[0]["X"], probs[0]["obs_idx"], probs[0]["y"], probs[0]["R"],
+                                         pr.Q, 1e-6, opts)
+    torch.cuda.synchronize()
+    assert st["status"] == 0 and st["n_unconverged"] == 0
+    ea, em = errors(pr, mu_a.cpu().numpy(), A_a.cpu().numpy())
+    assert ea <= 1e-4 and em <= 1e-4
