@@ -85,7 +85,10 @@ typedef struct {
   int32_t max_iter;       /* PCG iteration cap; default 1000 */
   int32_t fixed_iters;    /* > 0: run exactly this many PCG iterations (paper's experiments) */
   int32_t rule;           /* INFO_ESRF_RULE_*; default elliptic */
-  int32_t cluster_size;   /* CTAs per cluster of the FP32 cluster-resident PCG kernel: 0 = chosen from d, or 2, 4, 8 */
+  int32_t cluster_size;   /* CTAs per cluster of the FP32 cluster-resident PCG kernel (one-dimensional grids):
+                             2, 4 or 8 (halved while a CTA would own fewer than 32 rows), one launch per
+                             eligible problem; 0 = 8 for a single problem, and that kernel off in a batch
+                             of several; -1 = off (the general PCG kernel solves every system) */
   double ell;             /* spectrum bound of App. D; <= 0: power of ten above a Gershgorin bound of C */
   uint64_t seed;          /* Philox key of the randomized eigensolver's test matrix */
   int64_t max_neighbors;  /* band capacity per row; <= 0: bound from the geometry */
@@ -197,7 +200,7 @@ int info_esrf_analysis_batched(const info_esrf_problem* probs, int32_t count,
 
 /* Autotuner (not in the paper): times the analysis of probs[0..count) with
  * each candidate setting of the launch and eigensolver parameters that do not
- * change the converged answer -- cluster_size (0 or 4), power_iters (0 or 1)
+ * change the converged answer -- cluster_size (0, 4 or -1), power_iters (0 or 1)
  * and oversample (6 or 10) -- starting from *opt, and writes the fastest into
  * *opt (other fields untouched).  A candidate whose warm-up run leaves a
  * system unconverged, fails, or needs more workspace than ws_bytes is skipped.

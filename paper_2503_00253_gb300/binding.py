@@ -186,12 +186,14 @@ def make_options(precision: int = PRECISION_FP64, ritz_rank: int = 10, oversampl
                  power_iters: int = 1, max_iter: int = 1000, fixed_iters: int = 0,
                  rule: int = RULE_ELLIPTIC, ell: float = 0.0, seed: int = 0x1234ABCD,
                  max_neighbors: int = 0, learned_model: Optional[torch.Tensor] = None,
-                 learned_max_shift: float = 0.0, system_iters: Optional[torch.Tensor] = None) -> Options:
+                 learned_max_shift: float = 0.0, system_iters: Optional[torch.Tensor] = None,
+                 cluster_size: int = 0) -> Options:
     o = Options()
     library().info_esrf_default_options(ctypes.byref(o))
     o.precision, o.ritz_rank, o.oversample, o.power_iters = precision, ritz_rank, oversample, power_iters
     o.max_iter, o.fixed_iters, o.rule, o.ell, o.seed = max_iter, fixed_iters, rule, ell, seed
     o.max_neighbors = max_neighbors
+    o.cluster_size = cluster_size
     if system_iters is not None:
         _need(system_iters, torch.int32, "system_iters")
         o.system_iters = system_iters.data_ptr()

@@ -103,7 +103,8 @@ int check_options(const info_esrf_options* in, info_esrf_options* out) {
   if (out->power_iters < 0 || out->power_iters > 8) return INFO_ESRF_ERR_INVALID_ARG;
   if (out->max_iter < 1 && out->fixed_iters <= 0) return INFO_ESRF_ERR_INVALID_ARG;
   if (out->rule != 0 && out->rule != 1) return INFO_ESRF_ERR_INVALID_ARG;
-  if (out->cluster_size != 0 && out->cluster_size != 2 && out->cluster_size != 4 && out->cluster_size != 8)
+  if (out->cluster_size != 0 && out->cluster_size != -1 && out->cluster_size != 2 && out->cluster_size != 4 &&
+      out->cluster_size != 8)
     return INFO_ESRF_ERR_INVALID_ARG;
   return 0;
 }
@@ -158,7 +159,7 @@ int build_table(const info_esrf_problem* probs, int32_t count, const info_esrf_o
   tab.cluster_size = o.cluster_size;
   Carver cv{reinterpret_cast<char*>(ws)};
   ProblemDev* dtab = cv.take<ProblemDev>(sizeof(ProblemDev) * count);
-  int32_t* counter = cv.take<int32_t>(64);
+  int32_t* counter = cv.take<int32_t>(kCounterInts * sizeof(int32_t));
   int group_base = 0, sys_base = 0;
   const int JT = pcg_jt(o.precision);
   for (int i = 0; i < count; ++i) {
@@ -525,8 +526,8 @@ int info_esrf_autotune(const info_esrf_problem* probs, int32_t count, info_esrf_
   double best = -1.0;
   info_esrf_options best_o = base;
   int first_rc = 0;
-  const int cs_list[2] = {0, 4}, pi_list[2] = {0, 1}, os_list[2] = {6, 10};
-  for (int a = 0; a < 2; ++a)
+  const int cs_list[3] = {0, 4, -1}, pi_list[2] = {0, 1}, os_list[2] = {6, 10};
+  for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 2; ++b)
       for (int c = 0; c < 2; ++c) {
         info_esrf_options o = base;

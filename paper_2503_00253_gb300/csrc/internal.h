@@ -140,10 +140,18 @@ void launch_learn_coef(const ProblemTable& tab, const ProblemDev* dtab, cudaStre
 int launch_krylov_capture(const ProblemTable& tab, const ProblemDev* dtab, int nsel, const int32_t* sel, int K,
                           float* V, float* Y, float* Z, float* feat, cudaStream_t st);
 
-// Cluster-resident PCG for 1-D observation networks (single problem, FP32).
-bool band1d_eligible(const ProblemTable& tab);
-int launch_pcg_band1d(const ProblemTable& tab, const ProblemDev* dtab, int32_t* queue, int32_t* fallback,
+// Cluster-resident PCG for 1-D observation networks (FP32), one launch per
+// problem: p is the host copy, dp the device copy of the same problem.
+bool band1d_eligible(const ProblemDev& p);
+int band1d_cluster_size(const ProblemDev& p, int requested);
+int launch_pcg_band1d(const ProblemDev& p, const ProblemDev* dp, int CS, int32_t* queue, int32_t* fallback,
                       int num_sms, cudaStream_t st);
+
+// Work counters of the PCG stage: [0] group queue of the general kernel,
+// [1 + i] system queue of the band kernel for problem i, [1 + kMaxProblems + i]
+// its fall-back flag.
+constexpr int kCounterInts = 256;
+static_assert(1 + 2 * kMaxProblems <= kCounterInts, "PCG counter area");
 
 // PCG vector scratch per CTA when vectors do not fit in shared memory.
 size_t pcg_scratch_bytes(const ProblemTable& tab, int num_sms);

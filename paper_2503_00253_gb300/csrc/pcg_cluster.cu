@@ -836,24 +836,26 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
   cluster.sync();   // no CTA leaves while another may still read its shared memory
 }
 
-// General kernel gate: returns whether the band kernel above can run.
-bool band1d_eligible(const ProblemTable& tab) {
-  if (tab.count != 1) return false;
-  const ProblemDev& p = tab.p[0];
-  if (p.precision != 1 || p.kR > kK) return false;
+// Whether the band kernel above can take problem p (FP32, at most kK Ritz
+// vectors, a one-dimensional grid); the kernel itself checks the band reach
+// and the shared-memory budget and otherwise sets the fall-back flag.
+bool band1d_eligible(const ProblemDev& p) {
+  if (p.precision != 1 || p.kR > kK || p.nsys < 1) return false;
   int active = 0;
   for (int ax = 0; ax < 3; ++ax) active += p.grid.ext[ax] > 1;
-  if (active != 1 || p.grid.ext[0] <= 1) return false;
-  return true;
+  return active == 1 && p.grid.ext[0] > 1;
 }
 
-int launch_pcg_band1d(const ProblemTable& tab, const ProblemDev* dtab, int32_t* queue, int32_t* fallback,
-                      int num_sms, cudaStream_t st) {
-  const ProblemDev& p = tab.p[0];
-  // cluster size: 8 CTAs unless a CTA would own fewer than two row tiles; the
-  // kernel itself checks the band reach and the shared-memory budget
-  int CS = tab.cluster_size > 0 ? tab.cluster_size : 8;
+// Cluster size for problem p: the requested one (0: 8), halved while a CTA
+// would own fewer than two row tiles.
+int band1d_cluster_size(const ProblemDev& p, int requested) {
+  int CS = requested > 0 ? requested : kMaxCS;
   while (CS > 1 && (p.d + CS - 1) / CS < 2 * kTile) CS >>= 1;
+  return CS;
+}
+
+int launch_pcg_band1d(const ProblemDev& p, const ProblemDev* dp, int CS, int32_t* queue, int32_t* fallback,
+                      int num_sms, cudaStream_t st) {
   int clusters = (p.nsys + kJ - 1) / kJ;
   if (clusters > num_sms / CS) clusters = num_sms / CS;
   if (clusters < 1) clusters = 1;
@@ -894,7 +896,7 @@ int launch_pcg_band1d(const ProblemTable& tab, const ProblemDev* dtab, int32_t* 
     clusters = max_clusters;
     cfg.gridDim = dim3(clusters * CS, 1, 1);
   }
-  const cudaError_t err = cudaLaunchKernelEx(&cfg, k_pcg_band1d, dtab, queue, fallback, dyn_bytes / 4);
+  const cudaError_t err = cudaLaunchKernelEx(&cfg, k_pcg_band1d, dp, queue, fallback, dyn_bytes / 4);
   if (err != cudaSuccess) {
     cudaGetLastError();
     return -1;

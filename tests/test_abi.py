@@ -86,6 +86,10 @@ def test_host_side_validation_without_gpu(lib):
     assert L.info_esrf_workspace_size(ctypes.byref(g), 10, 200, 4, ctypes.byref(o)) == 0
     o2 = binding.make_options(ritz_rank=40)
     assert L.info_esrf_workspace_size(ctypes.byref(g), 10, 20, 4, ctypes.byref(o2)) == 0
+    # cluster sizes: 0 (chosen), -1 (band kernel off), 2, 4, 8; anything else is rejected
+    for cs, ok in ((0, True), (-1, True), (2, True), (4, True), (8, True), (3, False), (16, False), (-2, False)):
+        oc = binding.make_options(cluster_size=cs)
+        assert (L.info_esrf_workspace_size(ctypes.byref(g), 10, 20, 4, ctypes.byref(oc)) > 0) == ok, cs
     g.half_width[0] = 0.0
     assert L.info_esrf_workspace_size(ctypes.byref(g), 10, 20, 4, ctypes.byref(o)) == 0
     # null workspace is rejected before any launch

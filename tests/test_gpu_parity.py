@@ -431,6 +431,44 @@ def test_batched_equals_single_calls_bit_for_bit(B):
         assert st["iters_max"] == st_s["iters_max"]
 
 
+def test_batched_fp32_mixes_band_and_general_kernels(B):
+    """FP32 batch with cluster_size 8: three 1-D problems go to the cluster-resident
+    band kernel (one launch each), one 1-D problem with a single observation falls back on
+    the device, and a 2-D problem is solved by the general kernel.  Every problem
+    meets the mixed-precision bound against the oracle, reports the path that
+    solved it, and equals its single call bit for bit."""
+    probs = workloads.uneven_batch(count=3, seed=31, tol=1e-6, n_min=1000, n_max=3000)
+    probs.append(workloads.gaussian_problem_1d("one32", n=64, N=9, length_scale=4.0, obs_stride=64, r2=0.2,
+                                               half_width=5.0, Q=5, tol=1e-6, seed=19))
+    probs.append(workloads.random_obs_problem(workloads.Grid((24, 20, 1), (True, True, False), (3.0, 2.5, 1.0)),
+                                              N=7, d=90, r2=0.5, Q=5, tol=1e-6, seed=4))
+    expect_path = [1, 1, 1, 0, 0]
+    dicts = [dict(grid=p.grid, X=dev(p.X), obs_idx=dev(p.obs_idx), y=dev(p.y), R=dev(p.R), Q=p.Q, tol=1e-6)
+             for p in probs]
+    opts = B.make_options(precision=B.PRECISION_FP32, ritz_rank=8, cluster_size=8)
+    outs, stats = B.info_esrf_analysis_batched(dicts, opts)
+    torch.cuda.synchronize()
+    for p, dct, (mu_b, A_b), st, path in zip(probs, dicts, outs, stats, expect_path):
+        assert st["status"] == 0 and st["solver_path"] == path, (p.name, st)
+        ea, em = errors(p, mu_b.cpu().numpy(), A_b.cpu().numpy())
+        assert ea <= 1e-4 and em <= 1e-4, (p.name, ea, em)
+        mu_s, A_s, st_s = B.info_esrf_analysis(p.grid, dct["X"], dct["obs_idx"], dct["y"], dct["R"], p.Q, 1e-6,
+                                               opts)
+        torch.cuda.synchronize()
+        assert st_s["solver_path"] == path
+        assert torch.equal(mu_b, mu_s) and torch.equal(A_b, A_s), p.name
+    # cluster_size -1 turns the band kernel off, and 0 leaves it off in a batch:
+    # the general kernel solves every problem
+    for cs in (-1, 0):
+        outs, stats = B.info_esrf_analysis_batched(dicts, B.make_options(precision=B.PRECISION_FP32, ritz_rank=8,
+                                                                         cluster_size=cs))
+        torch.cuda.synchronize()
+        for p, (mu_b, A_b), st in zip(probs, outs, stats):
+            assert st["status"] == 0 and st["solver_path"] == 0, (cs, p.name, st)
+            ea, em = errors(p, mu_b.cpu().numpy(), A_b.cpu().numpy())
+            assert ea <= 1e-4 and em <= 1e-4, (cs, p.name, ea, em)
+
+
 def _l96(nx, nz, N, spinup, seed, c_x, c_z):
     return workloads.layered_l96_problem(nx=nx, nz=nz, N=N, spinup=spinup, seed=seed, Q=24, c_x=c_x, c_z=c_z)
 
@@ -503,7 +541,7 @@ def test_autotune_picks_a_converging_setting_and_keeps_parity(B):
     opts = B.make_options(precision=1)
     best = B.autotune(probs, opts)
     assert best > 0.0
-    assert opts.cluster_size in (0, 4) and opts.power_iters in (0, 1) and opts.oversample in (6, 10)
+    assert opts.cluster_size in (0, 4, -1) and opts.power_iters in (0, 1) and opts.oversample in (6, 10)
     mu_a, A_a, st = B.info_esrf_analysis(pr.grid, probs[0]["X"], probs[0]["obs_idx"], probs[0]["y"], probs[0]["R"],
                                          pr.Q, 1e-6, opts)
     torch.cuda.synchronize()
