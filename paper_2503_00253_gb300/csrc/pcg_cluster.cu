@@ -89,6 +89,25 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 
+// x = hi + lo with hi = x rounded to TF32 (nearest, ties away) and lo the
+// remainder rounded to TF32; x - hi is exact in FP32.
+__device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(x));
+  const float r = x - __uint_as_float(hi);
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(r));
+}
+
+// D += A B for one 16 x 8 x 8 TF32 tile, FP32 accumulation.  Fragments (g =
+// lane / 4, q = lane % 4): a = A[g][q], A[g+8][q], A[g][q+4], A[g+8][q+4];
+// b = B[q][g], B[q+4][g]; d = D[g][2q], D[g][2q+1], D[g+8][2q], D[g+8][2q+1].
+__device__ __forceinline__ void mma_tf32(float& d0, float& d1, float& d2, float& d3, const uint32_t (&a)[4],
+                                         uint32_t b0, uint32_t b1) {
+  asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d0), "+f"(d1), "+f"(d2), "+f"(d3)
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
 // Cyclic offset col - a folded into (-d/2, d/2] (0 <= col, a < d < 2^31).
 __device__ __forceinline__ int wrap_delta(int col, int a, int d) {
   int dl = col - a;
@@ -102,7 +121,7 @@ __device__ __forceinline__ int wrap_delta(int col, int a, int d) {
 __global__ void __launch_bounds__(kThreads, 1)
 k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_floats) {
   extern __shared__ __align__(16) float dyn[];
-  __shared__ LaneState L;
+  __shared__ __align__(16) LaneState L;
   __shared__ Setup S;
   __shared__ int s_klo[kMaxTiles], s_w[kMaxTiles], s_off[kMaxTiles];
   __shared__ float s_gram[3][kK * kK];
@@ -174,7 +193,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
         lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
         hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
       }
-      if (lane == 0) { s_klo[t] = lo; s_w[t] = hi - lo + 1; }
+      if (lane == 0) { s_klo[t] = lo; s_w[t] = (hi - lo + 1 + 7) & ~7; }   // whole 8-column chunks
     }
   }
   __syncthreads();
@@ -238,7 +257,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
   // shared-memory carve (floats): tiles | p window | r | x | y | Phi^T | A^T | push table
   const int W_p = R_s + hl + hr;
   const int o_pw = (tilesz + 3) & ~3;
-  const int o_r = o_pw + W_p * kLD;
+  const int o_r = o_pw + (W_p + 8) * kLD;          // p window + 8 zero rows read by padded chunks
   const int o_x = o_r + R_s * kLD;
   const int o_y = o_x + R_s * kLD;                 // y, then the r window, own rows at +kTH
   const int o_ph = o_y + (R_s + 2 * kTH) * kLD;
@@ -282,7 +301,11 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
 #pragma unroll 4
     for (int e = part; e < nnz; e += 2) {
       const int rel = row + wrap_delta(pr.oo_col[(int64_t)e * d + a], (int)a, (int)d);
-      Ct[s_off[t] + (rel - s_klo[t]) * kTile + r] = val[(int64_t)e * d + a];
+      // fragment order: chunk of 8 columns, then lane (r % 8) * 4 + kc % 4, then
+      // the element r / 8 + 2 (kc / 4) of that lane's A operand
+      const int kk = rel - s_klo[t], kc = kk & 7;
+      Ct[s_off[t] + (kk >> 3) * 128 + ((r & 7) * 4 + (kc & 3)) * 4 + (r >> 3) + 2 * (kc >> 2)] =
+          val[(int64_t)e * d + a];
     }
   }
   for (int row = tid; row < R_s; row += blockDim.x) s_rinv[row] = row < nrows ? (float)pr.rinv[s0 + row] : 0.f;
@@ -390,62 +413,97 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
 
   for (;;) {
     // ---------------- A: y = sigma p + C p on the own rows, partial p^T y ----------------
-    // A warp takes one 16-row tile; thread (rg, lg) = (lane / 8, lane % 8) owns
-    // rows 4 rg .. 4 rg + 3 of it for lanes 4 lg .. 4 lg + 3, so each column of
-    // the tile costs two 16-byte shared loads for 16 FMAs.
+    // On the tensor cores: mma.sync m16n8k8 with TF32 operands and FP32
+    // accumulation, each product split in three, a b = a_h b_h + (a_h b_l +
+    // a_l b_h), with a_l, b_l the TF32 remainders, which keeps it near FP32
+    // accuracy.  A warp takes one 16-row tile (its A operand) and runs over
+    // the tile's 8-column chunks (the k steps) for all kJ lanes.  Column n of
+    // n-block nb is lane 4 n + nb: a thread's B operands for the four n-blocks
+    // are then one 16-byte load per k row, and its results are lanes
+    // 8 q .. 8 q + 7 of rows g and g + 8 (g = lane / 4, q = lane % 4).
     {
-      const int rg = lane >> 3, lg = lane & 7;
-      const float s0g = L.sigf[4 * lg], s1g = L.sigf[4 * lg + 1], s2g = L.sigf[4 * lg + 2], s3g = L.sigf[4 * lg + 3];
-      DotAcc<float> pp[4];
+      const int g = lane >> 2, q = lane & 3;
+      DotAcc<float> pp[8];   // p^T y of lanes 8 q + i over this warp's rows
       for (int t = warp; t < ntiles; t += kNW) {
-        const int row0 = t * kTile + 4 * rg;
-        float4 acc[4];
+        const int rA = t * kTile + g, rB = rA + 8;
+        float dA[8], dB[8], eA[8], eB[8];   // a_h b_h and the correction terms, lanes 8 q + i
+        {
+          const float4 s0 = ld4(&L.sigf[8 * q]), s1 = ld4(&L.sigf[8 * q + 4]);
+          const float sg[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+          const float4 a0 = ld4(pw + (rA + hl) * kLD + 8 * q), a1 = ld4(pw + (rA + hl) * kLD + 8 * q + 4);
+          const float4 b0 = ld4(pw + (rB + hl) * kLD + 8 * q), b1 = ld4(pw + (rB + hl) * kLD + 8 * q + 4);
+          const float pa[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+          const float pbv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const float4 pv = ld4(pw + (row0 + r + hl) * kLD + 4 * lg);
-          acc[r] = make_float4(s0g * pv.x, s1g * pv.y, s2g * pv.z, s3g * pv.w);
+          for (int i = 0; i < 8; ++i) {
+            dA[i] = sg[i] * pa[i];
+            dB[i] = sg[i] * pbv[i];
+            eA[i] = 0.f;
+            eB[i] = 0.f;
+          }
         }
-        const float* ct = Ct + s_off[t] + 4 * rg;
-        const float* pb = pw + (s_klo[t] + hl) * kLD + 4 * lg;
-        const int wt = s_w[t];
-#pragma unroll 4
-        for (int kk = 0; kk < wt; ++kk) {
-          const float4 c4 = ld4(ct + kk * kTile);
-          const float4 p4 = ld4(pb + kk * kLD);
-          acc[0].x = fmaf(c4.x, p4.x, acc[0].x); acc[0].y = fmaf(c4.x, p4.y, acc[0].y);
-          acc[0].z = fmaf(c4.x, p4.z, acc[0].z); acc[0].w = fmaf(c4.x, p4.w, acc[0].w);
-          acc[1].x = fmaf(c4.y, p4.x, acc[1].x); acc[1].y = fmaf(c4.y, p4.y, acc[1].y);
-          acc[1].z = fmaf(c4.y, p4.z, acc[1].z); acc[1].w = fmaf(c4.y, p4.w, acc[1].w);
-          acc[2].x = fmaf(c4.z, p4.x, acc[2].x); acc[2].y = fmaf(c4.z, p4.y, acc[2].y);
-          acc[2].z = fmaf(c4.z, p4.z, acc[2].z); acc[2].w = fmaf(c4.z, p4.w, acc[2].w);
-          acc[3].x = fmaf(c4.w, p4.x, acc[3].x); acc[3].y = fmaf(c4.w, p4.y, acc[3].y);
-          acc[3].z = fmaf(c4.w, p4.z, acc[3].z); acc[3].w = fmaf(c4.w, p4.w, acc[3].w);
-        }
+        const float* ct = Ct + s_off[t] + 4 * lane;
+        const float* pb = pw + (s_klo[t] + hl + q) * kLD + 4 * g;
+        const int nch = s_w[t] >> 3;
+#pragma unroll 2
+        for (int c = 0; c < nch; ++c) {
+          const float4 a4 = ld4(ct + c * 128);
+          const float4 u4 = ld4(pb + (8 * c) * kLD);       // B[q][n] of n-blocks 0..3
+          const float4 v4 = ld4(pb + (8 * c + 4) * kLD);   // B[q + 4][n]
+          uint32_t ah[4], al[4];
+          tf32_split(a4.x, ah[0], al[0]);
+          tf32_split(a4.y, ah[1], al[1]);
+          tf32_split(a4.z, ah[2], al[2]);
+          tf32_split(a4.w, ah[3], al[3]);
+          const float uu[4] = {u4.x, u4.y, u4.z, u4.w}, vv[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const int row = row0 + r;
+          for (int nb = 0; nb < 4; ++nb) {
+            uint32_t uh, ul, vh, vl;
+            tf32_split(uu[nb], uh, ul);
+            tf32_split(vv[nb], vh, vl);
+            mma_tf32(dA[nb], dA[4 + nb], dB[nb], dB[4 + nb], ah, uh, vh);
+            mma_tf32(eA[nb], eA[4 + nb], eB[nb], eB[4 + nb], ah, ul, vl);
+            mma_tf32(eA[nb], eA[4 + nb], eB[nb], eB[4 + nb], al, uh, vh);
+          }
+        }
+        // D element i of a row is lane 8 q + i after the permutation above
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int row = h ? rB : rA;
           if (row < nrows) {
-            const float4 pv = ld4(pw + (row + hl) * kLD + 4 * lg);
-            st4(vy + (row + kTH) * kLD + 4 * lg, acc[r]);
-            pp[0].add_prod(pv.x, acc[r].x);
-            pp[1].add_prod(pv.y, acc[r].y);
-            pp[2].add_prod(pv.z, acc[r].z);
-            pp[3].add_prod(pv.w, acc[r].w);
+            float y[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) y[i] = h ? dB[i] + eB[i] : dA[i] + eA[i];
+            const float4 p0 = ld4(pw + (row + hl) * kLD + 8 * q), p1 = ld4(pw + (row + hl) * kLD + 8 * q + 4);
+            st4(vy + (row + kTH) * kLD + 8 * q, make_float4(y[0], y[1], y[2], y[3]));
+            st4(vy + (row + kTH) * kLD + 8 * q + 4, make_float4(y[4], y[5], y[6], y[7]));
+            pp[0].add_prod(p0.x, y[0]); pp[1].add_prod(p0.y, y[1]);
+            pp[2].add_prod(p0.z, y[2]); pp[3].add_prod(p0.w, y[3]);
+            pp[4].add_prod(p1.x, y[4]); pp[5].add_prod(p1.y, y[5]);
+            pp[6].add_prod(p1.z, y[6]); pp[7].add_prod(p1.w, y[7]);
           }
         }
       }
-      // sum over the four row groups (lane bits 3, 4): lane lg then holds lanes 4 lg .. 4 lg + 3
+      // reduce-scatter the eight float-float sums over g (lane bits 4, 3, 2):
+      // lane (g, q) ends with the sum of lane 8 q + g
+      float vh[8], vl[8];
 #pragma unroll
-      for (int l4 = 0; l4 < 4; ++l4) {
-        float hi = pp[l4].hi, lo = pp[l4].lo;
+      for (int i = 0; i < 8; ++i) { vh[i] = pp[i].hi; vl[i] = pp[i].lo; }
 #pragma unroll
-        for (int o = 8; o <= 16; o <<= 1) {
-          const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
-          const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-          ff_merge(hi, lo, h2, l2);
+      for (int lev = 0; lev < 3; ++lev) {
+        const int off = 16 >> lev, half = 4 >> lev;
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+          const float sh = up ? vh[i] : vh[i + half], sl = up ? vl[i] : vl[i + half];
+          float kh = up ? vh[i + half] : vh[i], kl = up ? vl[i + half] : vl[i];
+          ff_merge(kh, kl, __shfl_xor_sync(0xffffffffu, sh, off), __shfl_xor_sync(0xffffffffu, sl, off));
+          vh[i] = kh;
+          vl[i] = kl;
         }
-        if (rg == 0) { s_wpap[warp][4 * lg + l4][0] = hi; s_wpap[warp][4 * lg + l4][1] = lo; }
       }
+      s_wpap[warp][8 * q + g][0] = vh[0];
+      s_wpap[warp][8 * q + g][1] = vl[0];
     }
     __syncthreads();
     if (tid < kJ * CS) {
