@@ -30,6 +30,7 @@
 // remains.  Scalars of the CG recurrence are FP64; the k x k algebra of the
 // limited-memory preconditioner is FP32 (it only shapes the preconditioner).
 #include <cooperative_groups.h>
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include "common.cuh"
@@ -89,23 +90,28 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 
-// x = hi + lo with hi = x rounded to TF32 (nearest, ties away) and lo the
-// remainder rounded to TF32; x - hi is exact in FP32.
-__device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(x));
-  const float r = x - __uint_as_float(hi);
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(r));
+// Two FP32 values (already scaled into FP16 range) as hi + lo pairs of
+// packed FP16: hi = the values rounded to FP16, lo = the remainders rounded to
+// FP16 (the remainder itself is exact in FP32).  The lower half holds x0.
+__device__ __forceinline__ void f16_split2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+  const __half2 h = __floats2half2_rn(x0, x1);
+  const float2 hf = __half22float2(h);
+  const __half2 l = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
-// D += A B for one 16 x 8 x 8 TF32 tile, FP32 accumulation.  Fragments (g =
-// lane / 4, q = lane % 4): a = A[g][q], A[g+8][q], A[g][q+4], A[g+8][q+4];
-// b = B[q][g], B[q+4][g]; d = D[g][2q], D[g][2q+1], D[g+8][2q], D[g+8][2q+1].
-__device__ __forceinline__ void mma_tf32(float& d0, float& d1, float& d2, float& d3, const uint32_t (&a)[4],
-                                         uint32_t b0, uint32_t b1) {
-  asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+// D += A B for one 16 x 8 x 16 FP16 tile, FP32 accumulation.  Fragments
+// (g = lane / 4, q = lane % 4; a register holds two consecutive k, the lower
+// k in its lower half): a = A[g][2q..], A[g+8][2q..], A[g][2q+8..],
+// A[g+8][2q+8..]; b = B[2q..][g], B[2q+8..][g]; d = D[g][2q], D[g][2q+1],
+// D[g+8][2q], D[g+8][2q+1].
+__device__ __forceinline__ void mma_f16(float& d0, float& d1, float& d2, float& d3, const uint4& a, uint32_t b0,
+                                        uint32_t b1) {
+  asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
       "{%0,%1,%2,%3};\n"
       : "+f"(d0), "+f"(d1), "+f"(d2), "+f"(d3)
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+      : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
 }
 
 // Cyclic offset col - a folded into (-d/2, d/2] (0 <= col, a < d < 2^31).
@@ -116,6 +122,20 @@ __device__ __forceinline__ int wrap_delta(int col, int a, int d) {
   return dl;
 }
 
+// Power-of-two scale that brings |m| into [0.5, 1) (1 when m is 0 or not finite).
+__device__ __forceinline__ void pow2_scale(float m, float& scale, float& inv) {
+  if (m > 0.f && isfinite(m)) {
+    int e = 0;
+    frexpf(m, &e);
+    e = e < -100 ? -100 : (e > 100 ? 100 : e);
+    scale = ldexpf(1.f, -e);
+    inv = ldexpf(1.f, e);
+  } else {
+    scale = 1.f;
+    inv = 1.f;
+  }
+}
+
 }  // namespace
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -124,6 +144,9 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
   __shared__ __align__(16) LaneState L;
   __shared__ Setup S;
   __shared__ int s_klo[kMaxTiles], s_w[kMaxTiles], s_off[kMaxTiles];
+  __shared__ float s_ascale[kMaxTiles], s_ainv[kMaxTiles];   // power-of-two scale of C per tile (FP16 operands)
+  __shared__ __align__(16) float s_pmax_in[kMaxCS][kJ];     // max |p| per lane over each CTA's own rows
+  __shared__ __align__(16) float s_pscale[kJ], s_pinv[kJ];  // power-of-two scale of p per lane
   __shared__ float s_gram[3][kK * kK];
   __shared__ float s_theta[kK];
   // partial sums pushed by every CTA of the cluster into every CTA (slot = source rank)
@@ -193,7 +216,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
         lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
         hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
       }
-      if (lane == 0) { s_klo[t] = lo; s_w[t] = (hi - lo + 1 + 7) & ~7; }   // whole 8-column chunks
+      if (lane == 0) { s_klo[t] = lo; s_w[t] = (hi - lo + 1 + 15) & ~15; }   // whole 16-column chunks
     }
   }
   __syncthreads();
@@ -257,7 +280,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
   // shared-memory carve (floats): tiles | p window | r | x | y | Phi^T | A^T | push table
   const int W_p = R_s + hl + hr;
   const int o_pw = (tilesz + 3) & ~3;
-  const int o_r = o_pw + (W_p + 8) * kLD;          // p window + 8 zero rows read by padded chunks
+  const int o_r = o_pw + (W_p + 16) * kLD;         // p window + 16 zero rows read by padded chunks
   const int o_x = o_r + R_s * kLD;
   const int o_y = o_x + R_s * kLD;                 // y, then the r window, own rows at +kTH
   const int o_ph = o_y + (R_s + 2 * kTH) * kLD;
@@ -292,20 +315,43 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
   for (int i = tid; i < tilesz; i += blockDim.x) Ct[i] = 0.f;
   for (int i = o_pw + tid; i < o_ph; i += blockDim.x) dyn[i] = 0.f;
   __syncthreads();
+  // C is stored per tile as FP16 hi + lo pairs of C scaled by a power of two
+  // (max |C| of the tile into [0.5, 1)), in MMA fragment order: per 16-column
+  // chunk, the hi halves of the 32 lanes (8 each), then the lo halves.
+  for (int t = tid; t < ntiles; t += blockDim.x) reinterpret_cast<int*>(s_ascale)[t] = 0;
+  __syncthreads();
   for (int base = 0; base < nrows; base += (int)blockDim.x / 2) {
     const int row = base + (tid >> 1), part = tid & 1;
     if (row >= nrows) continue;
     const int64_t a = s0 + row;
     const int nnz = pr.oo_nnz[a];
-    const int t = row / kTile, r = row % kTile;
-#pragma unroll 4
-    for (int e = part; e < nnz; e += 2) {
-      const int rel = row + wrap_delta(pr.oo_col[(int64_t)e * d + a], (int)a, (int)d);
-      // fragment order: chunk of 8 columns, then lane (r % 8) * 4 + kc % 4, then
-      // the element r / 8 + 2 (kc / 4) of that lane's A operand
-      const int kk = rel - s_klo[t], kc = kk & 7;
-      Ct[s_off[t] + (kk >> 3) * 128 + ((r & 7) * 4 + (kc & 3)) * 4 + (r >> 3) + 2 * (kc >> 2)] =
-          val[(int64_t)e * d + a];
+    float m = 0.f;
+    for (int e = part; e < nnz; e += 2) m = fmaxf(m, fabsf(val[(int64_t)e * d + a]));
+    atomicMax(reinterpret_cast<int*>(s_ascale) + row / kTile, __float_as_int(m));   // m >= 0: int order
+  }
+  __syncthreads();
+  for (int t = tid; t < ntiles; t += blockDim.x) pow2_scale(s_ascale[t], s_ascale[t], s_ainv[t]);
+  __syncthreads();
+  {
+    __half* Ch = reinterpret_cast<__half*>(Ct);
+    for (int base = 0; base < nrows; base += (int)blockDim.x / 2) {
+      const int row = base + (tid >> 1), part = tid & 1;
+      if (row >= nrows) continue;
+      const int64_t a = s0 + row;
+      const int nnz = pr.oo_nnz[a];
+      const int t = row / kTile, r = row % kTile;
+      const float sc = s_ascale[t];
+      for (int e = part; e < nnz; e += 2) {
+        const int rel = row + wrap_delta(pr.oo_col[(int64_t)e * d + a], (int)a, (int)d);
+        const int kk = rel - s_klo[t], kc = kk & 15;
+        const int ln = (r & 7) * 4 + ((kc & 7) >> 1);         // lane holding this element
+        const int h = (r >> 3) * 2 + (kc >> 3) * 4 + (kc & 1);  // half within the lane's 8
+        const float v = val[(int64_t)e * d + a] * sc;
+        const __half hv = __float2half_rn(v);
+        const int64_t at = 2 * (int64_t)s_off[t] + (kk >> 4) * 512 + ln * 8 + h;
+        Ch[at] = hv;
+        Ch[at + 256] = __float2half_rn(v - __half2float(hv));
+      }
     }
   }
   for (int row = tid; row < R_s; row += blockDim.x) s_rinv[row] = row < nrows ? (float)pr.rinv[s0 + row] : 0.f;
@@ -406,6 +452,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
   }
   cluster.sync();
   if (tid < kJ) lane_scalars(tid, L.newsid[tid]);
+  if (tid < kJ) { s_pscale[tid] = 1.f; s_pinv[tid] = 1.f; }
   lane_masks();
   __syncthreads();
   lane_vectors_all();
@@ -413,74 +460,68 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
 
   for (;;) {
     // ---------------- A: y = sigma p + C p on the own rows, partial p^T y ----------------
-    // On the tensor cores: mma.sync m16n8k8 with TF32 operands and FP32
-    // accumulation, each product split in three, a b = a_h b_h + (a_h b_l +
-    // a_l b_h), with a_l, b_l the TF32 remainders, which keeps it near FP32
-    // accuracy.  A warp takes one 16-row tile (its A operand) and runs over
-    // the tile's 8-column chunks (the k steps) for all kJ lanes.  Column n of
-    // n-block nb is lane 4 n + nb: a thread's B operands for the four n-blocks
-    // are then one 16-byte load per k row, and its results are lanes
-    // 8 q .. 8 q + 7 of rows g and g + 8 (g = lane / 4, q = lane % 4).
+    // On the tensor cores: mma.sync m16n8k16 with FP16 operands and FP32
+    // accumulation.  C (per tile) and p (per lane, over the whole cluster) are
+    // scaled by powers of two into [0.5, 1) and split into FP16 hi + lo, and
+    // each product is taken in three terms, a b = a_h b_h + (a_h b_l + a_l b_h),
+    // which keeps it near FP32 accuracy; the scales are undone exactly.  A warp
+    // takes one 16-row tile (its A operand) and runs over the tile's 16-column
+    // chunks (the k steps) for all kJ lanes.  Column n of n-block nb is lane
+    // 4 n + nb: a thread's B operands for the four n-blocks then come from one
+    // 16-byte load per k row, and its results are lanes 8 q .. 8 q + 7 of rows
+    // g and g + 8 (g = lane / 4, q = lane % 4).
     {
       const int g = lane >> 2, q = lane & 3;
+      const float4 ps4 = ld4(&s_pscale[4 * g]);   // scales of this thread's B columns (lanes 4 g + nb)
+      const float psc[4] = {ps4.x, ps4.y, ps4.z, ps4.w};
       DotAcc<float> pp[8];   // p^T y of lanes 8 q + i over this warp's rows
       for (int t = warp; t < ntiles; t += kNW) {
         const int rA = t * kTile + g, rB = rA + 8;
         float dA[8], dB[8], eA[8], eB[8];   // a_h b_h and the correction terms, lanes 8 q + i
-        {
-          const float4 s0 = ld4(&L.sigf[8 * q]), s1 = ld4(&L.sigf[8 * q + 4]);
-          const float sg[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
-          const float4 a0 = ld4(pw + (rA + hl) * kLD + 8 * q), a1 = ld4(pw + (rA + hl) * kLD + 8 * q + 4);
-          const float4 b0 = ld4(pw + (rB + hl) * kLD + 8 * q), b1 = ld4(pw + (rB + hl) * kLD + 8 * q + 4);
-          const float pa[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-          const float pbv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            dA[i] = sg[i] * pa[i];
-            dB[i] = sg[i] * pbv[i];
-            eA[i] = 0.f;
-            eB[i] = 0.f;
-          }
-        }
+        for (int i = 0; i < 8; ++i) { dA[i] = 0.f; dB[i] = 0.f; eA[i] = 0.f; eB[i] = 0.f; }
         const float* ct = Ct + s_off[t] + 4 * lane;
-        const float* pb = pw + (s_klo[t] + hl + q) * kLD + 4 * g;
-        const int nch = s_w[t] >> 3;
+        const float* pb = pw + (s_klo[t] + hl + 2 * q) * kLD + 4 * g;
+        const int nch = s_w[t] >> 4;
 #pragma unroll 2
         for (int c = 0; c < nch; ++c) {
-          const float4 a4 = ld4(ct + c * 128);
-          const float4 u4 = ld4(pb + (8 * c) * kLD);       // B[q][n] of n-blocks 0..3
-          const float4 v4 = ld4(pb + (8 * c + 4) * kLD);   // B[q + 4][n]
-          uint32_t ah[4], al[4];
-          tf32_split(a4.x, ah[0], al[0]);
-          tf32_split(a4.y, ah[1], al[1]);
-          tf32_split(a4.z, ah[2], al[2]);
-          tf32_split(a4.w, ah[3], al[3]);
-          const float uu[4] = {u4.x, u4.y, u4.z, u4.w}, vv[4] = {v4.x, v4.y, v4.z, v4.w};
+          const uint4 ah = *reinterpret_cast<const uint4*>(ct + c * 256);
+          const uint4 al = *reinterpret_cast<const uint4*>(ct + c * 256 + 128);
+          const float* pc = pb + (16 * c) * kLD;
+          const float4 k0 = ld4(pc), k1 = ld4(pc + kLD);                // B rows 2q, 2q + 1
+          const float4 k8 = ld4(pc + 8 * kLD), k9 = ld4(pc + 9 * kLD);  // B rows 2q + 8, 2q + 9
+          const float b0[4] = {k0.x, k0.y, k0.z, k0.w}, b1[4] = {k1.x, k1.y, k1.z, k1.w};
+          const float b8[4] = {k8.x, k8.y, k8.z, k8.w}, b9[4] = {k9.x, k9.y, k9.z, k9.w};
 #pragma unroll
           for (int nb = 0; nb < 4; ++nb) {
-            uint32_t uh, ul, vh, vl;
-            tf32_split(uu[nb], uh, ul);
-            tf32_split(vv[nb], vh, vl);
-            mma_tf32(dA[nb], dA[4 + nb], dB[nb], dB[4 + nb], ah, uh, vh);
-            mma_tf32(eA[nb], eA[4 + nb], eB[nb], eB[4 + nb], ah, ul, vl);
-            mma_tf32(eA[nb], eA[4 + nb], eB[nb], eB[4 + nb], al, uh, vh);
+            uint32_t h0, l0, h1, l1;
+            f16_split2(b0[nb] * psc[nb], b1[nb] * psc[nb], h0, l0);
+            f16_split2(b8[nb] * psc[nb], b9[nb] * psc[nb], h1, l1);
+            mma_f16(dA[nb], dA[4 + nb], dB[nb], dB[4 + nb], ah, h0, h1);
+            mma_f16(eA[nb], eA[4 + nb], eB[nb], eB[4 + nb], ah, l0, l1);
+            mma_f16(eA[nb], eA[4 + nb], eB[nb], eB[4 + nb], al, h0, h1);
           }
         }
         // D element i of a row is lane 8 q + i after the permutation above
+        const float ia = s_ainv[t];
+        const float4 si0 = ld4(&s_pinv[8 * q]), si1 = ld4(&s_pinv[8 * q + 4]);
+        const float4 sg0 = ld4(&L.sigf[8 * q]), sg1 = ld4(&L.sigf[8 * q + 4]);
+        const float un[8] = {ia * si0.x, ia * si0.y, ia * si0.z, ia * si0.w,
+                             ia * si1.x, ia * si1.y, ia * si1.z, ia * si1.w};
+        const float sg[8] = {sg0.x, sg0.y, sg0.z, sg0.w, sg1.x, sg1.y, sg1.z, sg1.w};
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int row = h ? rB : rA;
           if (row < nrows) {
+            const float4 p0 = ld4(pw + (row + hl) * kLD + 8 * q), p1 = ld4(pw + (row + hl) * kLD + 8 * q + 4);
+            const float pv[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
             float y[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) y[i] = h ? dB[i] + eB[i] : dA[i] + eA[i];
-            const float4 p0 = ld4(pw + (row + hl) * kLD + 8 * q), p1 = ld4(pw + (row + hl) * kLD + 8 * q + 4);
+            for (int i = 0; i < 8; ++i) y[i] = fmaf(sg[i], pv[i], ((h ? dB[i] : dA[i]) + (h ? eB[i] : eA[i])) * un[i]);
             st4(vy + (row + kTH) * kLD + 8 * q, make_float4(y[0], y[1], y[2], y[3]));
             st4(vy + (row + kTH) * kLD + 8 * q + 4, make_float4(y[4], y[5], y[6], y[7]));
-            pp[0].add_prod(p0.x, y[0]); pp[1].add_prod(p0.y, y[1]);
-            pp[2].add_prod(p0.z, y[2]); pp[3].add_prod(p0.w, y[3]);
-            pp[4].add_prod(p1.x, y[4]); pp[5].add_prod(p1.y, y[5]);
-            pp[6].add_prod(p1.z, y[6]); pp[7].add_prod(p1.w, y[7]);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) pp[i].add_prod(pv[i], y[i]);
           }
         }
       }
@@ -807,6 +848,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       }
       const bool any_learn2 = L.learn[j0] | L.learn[j0 + 1] | L.learn[j0 + 2] | L.learn[j0 + 3];
       int ir = 0;
+      float pmx[4] = {0.f, 0.f, 0.f, 0.f};   // max |p| of the four lanes over this thread's rows
       float* U = reinterpret_cast<float*>(pr.U);
       for (int row = lane; row < nrows; row += 32) {
         float* prow = pw + (row + hl) * kLD + j0;
@@ -835,12 +877,21 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
         const float pv[4] = {p4.x, p4.y, p4.z, p4.w};
         float pn[4];
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) pn[jj] = act[jj] ? fmaf(bj[jj], pv[jj], z[jj]) : 0.f;
+        for (int jj = 0; jj < 4; ++jj) {
+          pn[jj] = act[jj] ? fmaf(bj[jj], pv[jj], z[jj]) : 0.f;
+          pmx[jj] = fmaxf(pmx[jj], fabsf(pn[jj]));
+        }
         st4(prow, make_float4(pn[0], pn[1], pn[2], pn[3]));
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj)
           if (fin[jj]) U[(int64_t)L.sid[j0 + jj] * d + s0 + row] = vx[row * kLD + j0 + jj];
       }
+      // the lanes' max |p| over the own rows, to every CTA (the scale of p in the next matvec)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) pmx[jj] = fmaxf(pmx[jj], __shfl_xor_sync(0xffffffffu, pmx[jj], o));
+      if (lane < CS) st4(cluster.map_shared_rank(&s_pmax_in[crank][j0], lane), make_float4(pmx[0], pmx[1], pmx[2], pmx[3]));
     }
     __syncthreads();
     // finished lanes: stats, and rank 0 takes the next systems off the queue
@@ -885,6 +936,11 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
     cluster.sync();   // (3)
     // ---------------- refills, exit test, halo ----------------
     if (tid < kJ && L.fin[tid]) lane_scalars(tid, L.newsid[tid]);
+    if (tid < kJ) {
+      float m = 0.f;
+      for (int c = 0; c < CS; ++c) m = fmaxf(m, s_pmax_in[c][tid]);
+      pow2_scale(m, s_pscale[tid], s_pinv[tid]);
+    }
     lane_masks();
     __syncthreads();
     if (!s_live) break;

@@ -61,58 +61,97 @@ void launch_prepare(const ProblemTable& tab, ProblemDev* dtab, cudaStream_t st) 
 // ---------------------------------------------------------------------------
 // a1: ensemble mean and normalized anomalies Z (Eq. normalized_perturbations)
 // ---------------------------------------------------------------------------
+// One CTA per 32 consecutive state points (kAnomPts); warp w of the 8 takes
+// the members w, w + 8, ...  Reads of X are coalesced over the points, the
+// member sum is FP64 in a fixed order (per warp, then over the warps), and
+// Z^T [n][N] is written through a shared-memory transpose, 32 members at a
+// time, so that each point's member run is contiguous.
+constexpr int kAnomPts = 32;
 template <typename T>
-__global__ void k_anomalies(const ProblemDev* tab) {
+__global__ void __launch_bounds__(256) k_anomalies(const ProblemDev* tab) {
   const ProblemDev& pr = tab[blockIdx.y];
-  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= pr.n) return;
+  const int64_t x0 = (int64_t)blockIdx.x * kAnomPts;
+  if (x0 >= pr.n) return;
   const int64_t N = pr.N, n = pr.n;
+  const int lx = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t x = x0 + lx;
+  const bool in = x < n;
+  __shared__ double s_part[8][kAnomPts];
+  __shared__ double s_mu[kAnomPts];
+  __shared__ T s_tile[kAnomPts][33];
+  __shared__ int s_bad;
+  if (threadIdx.x == 0) s_bad = 0;
   double sum = 0.0;
   bool bad = false;
-  for (int64_t k = 0; k < N; ++k) {
-    const double v = pr.X[k * n + x];
-    bad |= !isfinite(v);
-    sum += v;
+  if (in)
+    for (int64_t k = w; k < N; k += 8) {
+      const double v = pr.X[k * n + x];
+      bad |= !isfinite(v);
+      sum += v;
+    }
+  s_part[w][lx] = sum;
+  __syncthreads();
+  if (bad) s_bad = 1;
+  if (w == 0) {
+    double t = 0.0;
+    for (int u = 0; u < 8; ++u) t += s_part[u][lx];
+    const double mu = t / (double)N;
+    s_mu[lx] = mu;
+    if (in) pr.mu[x] = mu;
   }
-  const double mu = sum / (double)N;
-  pr.mu[x] = mu;
+  __syncthreads();
+  const double mu = s_mu[lx];
   const double scale = 1.0 / pr.sqrt_nm1;
   T* Zt = tp<T>(pr.Zt);
-  for (int64_t k = 0; k < N; ++k) Zt[x * N + k] = to_t<T>((pr.X[k * n + x] - mu) * scale);
-  if (bad) atomicOr(&pr.status[0], kStatNonFinite);
+  const int np = (int)(n - x0 < kAnomPts ? n - x0 : kAnomPts);
+  for (int64_t c0 = 0; c0 < N; c0 += 32) {
+    const int nk = (int)(N - c0 < 32 ? N - c0 : 32);
+    for (int kk = w; kk < nk; kk += 8)
+      s_tile[lx][kk] = in ? to_t<T>((pr.X[(c0 + kk) * n + x] - mu) * scale) : to_t<T>(0.0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < np * 32; e += blockDim.x) {
+      const int xi = e >> 5, kk = e & 31;
+      if (kk < nk) Zt[(x0 + xi) * N + c0 + kk] = s_tile[xi][kk];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && s_bad) atomicOr(&pr.status[0], kStatNonFinite);
 }
 
-// W = H Z (rows of Z at the observed points), R^-1/2 and the mean right-hand side.
+// W = H Z (rows of Z at the observed points), one thread per (observation,
+// member) element so that the copy is coalesced; the member-0 thread of each
+// observation also checks its index, forms R^-1/2 and the mean right-hand side.
 template <typename T>
 __global__ void k_observe(const ProblemDev* tab) {
   const ProblemDev& pr = tab[blockIdx.y];
-  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (a >= pr.d) return;
+  const int64_t N = pr.N;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= pr.d * N) return;
+  const int64_t a = i / N, k = i - a * N;
   int64_t o = pr.obs[a];
-  bool bad_obs = o < 0 || o >= pr.n || (a > 0 && pr.obs[a - 1] >= o);
+  const bool bad_obs = o < 0 || o >= pr.n || (a > 0 && pr.obs[a - 1] >= o);
   if (o < 0) o = 0;
   if (o >= pr.n) o = pr.n - 1;
+  tp<T>(pr.W)[i] = tp<const T>(pr.Zt)[o * N + k];
+  if (k != 0) return;
   const double r = pr.R[a];
   const bool bad_r = !(r > 0.0) || !isfinite(r);
   const double ri = bad_r ? 0.0 : 1.0 / sqrt(r);
   pr.rinv[a] = ri;
-  const T* Zt = tp<const T>(pr.Zt);
-  T* W = tp<T>(pr.W);
-  for (int64_t k = 0; k < pr.N; ++k) W[a * pr.N + k] = Zt[o * pr.N + k];
   if (pr.do_mean) pr.bmean[a] = ri * (pr.y[a] - pr.mu[o]);
   if (bad_obs) atomicOr(&pr.status[0], kStatBadObs);
   if (bad_r) atomicOr(&pr.status[0], kStatBadR);
 }
 
 void launch_anomalies(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st) {
-  int64_t nmax = 0, dmax = 0;
+  int64_t nmax = 0, dnmax = 0;
   for (int i = 0; i < tab.count; ++i) {
     nmax = tab.p[i].n > nmax ? tab.p[i].n : nmax;
-    dmax = tab.p[i].d > dmax ? tab.p[i].d : dmax;
+    dnmax = tab.p[i].d * tab.p[i].N > dnmax ? tab.p[i].d * tab.p[i].N : dnmax;
   }
   const bool f64 = tab.p[0].precision == 0;
-  dim3 g1((unsigned)((nmax + 255) / 256), tab.count);
-  dim3 g2((unsigned)((dmax + 255) / 256), tab.count);
+  dim3 g1((unsigned)((nmax + kAnomPts - 1) / kAnomPts), tab.count);
+  dim3 g2((unsigned)((dnmax + 255) / 256), tab.count);
   if (f64) {
     k_anomalies<double><<<g1, 256, 0, st>>>(dtab); note_launches(1);
     k_observe<double><<<g2, 256, 0, st>>>(dtab); note_launches(1);
@@ -177,7 +216,28 @@ __global__ void k_band(const ProblemDev* tab) {
           keep = true;
           DotAcc<T> acc;
           const T* wb = W + b * N;
-          for (int64_t k = 0; k < N; ++k) acc.add_prod(src[k], wb[k]);
+          // 16-byte loads when the member rows allow them (same order of terms)
+          if (sizeof(T) == 4 && (N & 3) == 0) {
+            const float4* s4 = reinterpret_cast<const float4*>(src);
+            const float4* w4 = reinterpret_cast<const float4*>(wb);
+            for (int64_t k = 0; k < N / 4; ++k) {
+              const float4 u = s4[k], v4 = w4[k];
+              acc.add_prod((T)u.x, (T)v4.x);
+              acc.add_prod((T)u.y, (T)v4.y);
+              acc.add_prod((T)u.z, (T)v4.z);
+              acc.add_prod((T)u.w, (T)v4.w);
+            }
+          } else if (sizeof(T) == 8 && (N & 1) == 0) {
+            const double2* s2 = reinterpret_cast<const double2*>(src);
+            const double2* w2 = reinterpret_cast<const double2*>(wb);
+            for (int64_t k = 0; k < N / 2; ++k) {
+              const double2 u = s2[k], v2 = w2[k];
+              acc.add_prod((T)u.x, (T)v2.x);
+              acc.add_prod((T)u.y, (T)v2.y);
+            }
+          } else {
+            for (int64_t k = 0; k < N; ++k) acc.add_prod(src[k], wb[k]);
+          }
           const double gc = sizeof(T) == 8 ? gaspari_cohn(sqrt(r2)) : (double)gaspari_cohn_f(sqrtf((float)r2));
           v = gc * acc.value();
           if (OBS_ROWS) v *= ra * pr.rinv[b];
