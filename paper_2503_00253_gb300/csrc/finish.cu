@@ -36,33 +36,47 @@ __global__ void k_accumulate(const ProblemDev* tab) {
   reinterpret_cast<T*>(pr.VbarT)[a * N1 + m] = to_t<T>(v);
 }
 
-// One thread per (member or mean column, state point), state points fastest
-// so that band loads and output stores are coalesced.
+// One thread per (state point, pair of columns: member m < N, or the mean
+// m == N), state points fastest so that band loads and output stores are
+// coalesced; each band entry is read once for both columns of the pair (one
+// column per thread left the band reads doubled, four left too few warps to
+// hide the gathers).
+constexpr int kStateCols = 2;
 template <typename T>
 __global__ void k_state_apply(const ProblemDev* tab) {
   const ProblemDev& pr = tab[blockIdx.z];
   const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t m = blockIdx.y;                 // column: member m < N, or the mean (m == N)
   const int64_t n = pr.n, N = pr.N, N1 = N + 1;
-  if (x >= n || m > N) return;
-  if (m < N && !pr.do_pert) return;
-  if (m == N && !pr.do_mean) return;
+  const int64_t m0 = (int64_t)blockIdx.y * kStateCols;
+  if (x >= n || m0 > N) return;
   const T* __restrict__ val = reinterpret_cast<const T*>(pr.xo_val);
   const int32_t* __restrict__ col = pr.xo_col;
   const T* __restrict__ Vb = reinterpret_cast<const T*>(pr.VbarT);
   const int nnz = pr.xo_nnz[x];
-  T acc0 = T(0), acc1 = T(0);
-  int e = 0;
+  const int nc = (int)(N1 - m0 < kStateCols ? N1 - m0 : kStateCols);
+  T acc[kStateCols];
+#pragma unroll
+  for (int j = 0; j < kStateCols; ++j) acc[j] = T(0);
 #pragma unroll 4
-  for (; e + 1 < nnz; e += 2) {
-    acc0 += val[(int64_t)e * n + x] * Vb[(int64_t)col[(int64_t)e * n + x] * N1 + m];
-    acc1 += val[(int64_t)(e + 1) * n + x] * Vb[(int64_t)col[(int64_t)(e + 1) * n + x] * N1 + m];
+  for (int e = 0; e < nnz; ++e) {
+    const T v = val[(int64_t)e * n + x];
+    const T* vb = Vb + (int64_t)col[(int64_t)e * n + x] * N1 + m0;
+#pragma unroll
+    for (int j = 0; j < kStateCols; ++j)
+      if (j < nc) acc[j] += v * vb[j];
   }
-  if (e < nnz) acc0 += val[(int64_t)e * n + x] * Vb[(int64_t)col[(int64_t)e * n + x] * N1 + m];
-  const double inc = (double)(acc0 + acc1);
   const double mu = pr.mu[x];
-  if (m < N) pr.A_a[m * n + x] = (pr.X[m * n + x] - mu) - pr.sqrt_nm1 * inc;
-  else pr.mu_a[x] = mu + inc;
+#pragma unroll
+  for (int j = 0; j < kStateCols; ++j) {
+    if (j >= nc) break;
+    const int64_t m = m0 + j;
+    const double inc = (double)acc[j];
+    if (m < N) {
+      if (pr.do_pert) pr.A_a[m * n + x] = (pr.X[m * n + x] - mu) - pr.sqrt_nm1 * inc;
+    } else if (pr.do_mean) {
+      pr.mu_a[x] = mu + inc;
+    }
+  }
 }
 
 void launch_finish(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st) {
@@ -74,7 +88,7 @@ void launch_finish(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t
     Nmax = p.N > Nmax ? p.N : Nmax;
   }
   const dim3 ga((unsigned)((dn1 + 255) / 256), tab.count);
-  const dim3 gs((unsigned)((nmax + 127) / 128), (unsigned)(Nmax + 1), tab.count);
+  const dim3 gs((unsigned)((nmax + 127) / 128), (unsigned)((Nmax + kStateCols) / kStateCols), tab.count);
   if (tab.p[0].precision == 0) {
     k_accumulate<double><<<ga, 256, 0, st>>>(dtab); note_launches(1);
     k_state_apply<double><<<gs, 128, 0, st>>>(dtab); note_launches(1);

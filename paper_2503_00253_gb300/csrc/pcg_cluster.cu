@@ -171,6 +171,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
 
   // ---------------- set-up: band reach of the own rows ----------------
   if (tid == 0) { s_lo_min = 1 << 30; s_hi_max = -(1 << 30); s_bad = (R_s > kMaxTiles * kTile) ? 1 : 0; }
+  for (int t = tid; t < kMaxTiles; t += blockDim.x) reinterpret_cast<int*>(s_ascale)[t] = 0;
   __syncthreads();
   // per-row window [lo, hi] relative to s0, kept in the dynamic buffer's tail
   int* rlo = reinterpret_cast<int*>(dyn);
@@ -178,10 +179,13 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
   if (2 * R_s > dyn_floats) s_bad = 1;
   __syncthreads();
   if (!s_bad) {
-    // two threads per row (alternate entries), combined by a shuffle
+    // two threads per row (alternate entries), combined by a shuffle; the same
+    // pass takes each 16-row tile's max |C| (the FP16 scale of its tile)
+    const float* cval = reinterpret_cast<const float*>(pr.oo_val);
     for (int base = 0; base < nrows; base += (int)blockDim.x / 2) {
       const int row = base + (tid >> 1), part = tid & 1;
       int dmin = 1 << 30, dmax = -(1 << 30), nnz = 0;
+      float amax = 0.f;
       if (row < nrows) {
         const int64_t a = s0 + row;
         nnz = pr.oo_nnz[a];
@@ -190,7 +194,9 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
           const int dl = wrap_delta(pr.oo_col[(int64_t)e * d + a], (int)a, (int)d);
           dmin = dl < dmin ? dl : dmin;
           dmax = dl > dmax ? dl : dmax;
+          amax = fmaxf(amax, fabsf(cval[(int64_t)e * d + a]));
         }
+        atomicMax(reinterpret_cast<int*>(s_ascale) + row / kTile, __float_as_int(amax));   // amax >= 0: int order
       }
       dmin = min(dmin, __shfl_xor_sync(0xffffffffu, dmin, 1));
       dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, 1));
@@ -318,18 +324,6 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
   // C is stored per tile as FP16 hi + lo pairs of C scaled by a power of two
   // (max |C| of the tile into [0.5, 1)), in MMA fragment order: per 16-column
   // chunk, the hi halves of the 32 lanes (8 each), then the lo halves.
-  for (int t = tid; t < ntiles; t += blockDim.x) reinterpret_cast<int*>(s_ascale)[t] = 0;
-  __syncthreads();
-  for (int base = 0; base < nrows; base += (int)blockDim.x / 2) {
-    const int row = base + (tid >> 1), part = tid & 1;
-    if (row >= nrows) continue;
-    const int64_t a = s0 + row;
-    const int nnz = pr.oo_nnz[a];
-    float m = 0.f;
-    for (int e = part; e < nnz; e += 2) m = fmaxf(m, fabsf(val[(int64_t)e * d + a]));
-    atomicMax(reinterpret_cast<int*>(s_ascale) + row / kTile, __float_as_int(m));   // m >= 0: int order
-  }
-  __syncthreads();
   for (int t = tid; t < ntiles; t += blockDim.x) pow2_scale(s_ascale[t], s_ascale[t], s_ainv[t]);
   __syncthreads();
   {

@@ -32,19 +32,30 @@ struct TableChunk {
   ProblemDev p[kChunk];
 };
 
-__global__ void k_write_table(const TableChunk c, ProblemDev* dst) {
-  const int i = threadIdx.x;
-  if (i < c.count) dst[c.first + i] = c.p[i];
-}
-
-__global__ void k_clear_scalars(ProblemDev* tab) {
-  const ProblemDev& pr = tab[blockIdx.x];
-  if (threadIdx.x == 0) {
-    pr.scal[0] = 0.0;
-    pr.scal[1] = __longlong_as_double(0x7ff0000000000000LL);  // +inf, atomically lowered
-    for (int i = 2; i < 8; ++i) pr.scal[i] = 0.0;
-    for (int i = 0; i < 4; ++i) pr.status[i] = 0;
+// One launch per chunk of problems: block (0, i) writes problem i's table entry
+// and clears its scalars and status; every block fills part of its per-axis
+// table of (axis distance / half-width)^2 for every index offset, which the
+// band kernels use instead of a transcendental per candidate pair.  Only the
+// parameter copy of the table is read, so no block waits for the upload.
+__global__ void k_prepare(const TableChunk c, ProblemDev* dst) {
+  const int i = blockIdx.y;
+  if (i >= c.count) return;
+  const ProblemDev& pc = c.p[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    dst[c.first + i] = pc;
+    pc.scal[0] = 0.0;
+    pc.scal[1] = __longlong_as_double(0x7ff0000000000000LL);  // +inf, atomically lowered
+    for (int u = 2; u < 8; ++u) pc.scal[u] = 0.0;
+    for (int u = 0; u < 4; ++u) pc.status[u] = 0;
   }
+  const GridDev& g = pc.grid;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t total = g.ext[0] + g.ext[1] + g.ext[2];
+  if (e >= total) return;
+  const int ax = e < g.ext[0] ? 0 : (e < g.ext[0] + g.ext[1] ? 1 : 2);
+  const int64_t delta = e - (ax == 0 ? 0 : ax == 1 ? g.ext[0] : g.ext[0] + g.ext[1]);
+  const double dd = axis_distance(g, ax, 0, delta) * g.inv_c[ax];
+  pc.d2tab[e] = dd * dd;
 }
 
 void launch_prepare(const ProblemTable& tab, ProblemDev* dtab, cudaStream_t st) {
@@ -52,10 +63,15 @@ void launch_prepare(const ProblemTable& tab, ProblemDev* dtab, cudaStream_t st) 
     TableChunk c;
     c.first = first;
     c.count = tab.count - first < kChunk ? tab.count - first : kChunk;
-    for (int i = 0; i < c.count; ++i) c.p[i] = tab.p[first + i];
-    k_write_table<<<1, 32, 0, st>>>(c, dtab); note_launches(1);
+    int64_t emax = 1;
+    for (int i = 0; i < c.count; ++i) {
+      c.p[i] = tab.p[first + i];
+      const GridDev& g = tab.p[first + i].grid;
+      emax = std::max<int64_t>(emax, g.ext[0] + g.ext[1] + g.ext[2]);
+    }
+    k_prepare<<<dim3((unsigned)((emax + 255) / 256), (unsigned)c.count), 256, 0, st>>>(c, dtab);
+    note_launches(1);
   }
-  k_clear_scalars<<<tab.count, 32, 0, st>>>(dtab); note_launches(1);
 }
 
 // ---------------------------------------------------------------------------
@@ -169,20 +185,6 @@ void launch_anomalies(const ProblemTable& tab, const ProblemDev* dtab, cudaStrea
 // in increasing candidate order to the ELL row (column-major: entry e of row
 // a at e * rows + a).
 // ---------------------------------------------------------------------------
-// Per-axis table of (axis distance / half-width)^2 for every index offset, so
-// that the band kernels need no transcendental per candidate pair.
-__global__ void k_dist_table(const ProblemDev* tab) {
-  const ProblemDev& pr = tab[blockIdx.y];
-  const GridDev& g = pr.grid;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t total = g.ext[0] + g.ext[1] + g.ext[2];
-  if (i >= total) return;
-  const int ax = i < g.ext[0] ? 0 : (i < g.ext[0] + g.ext[1] ? 1 : 2);
-  const int64_t delta = i - (ax == 0 ? 0 : ax == 1 ? g.ext[0] : g.ext[0] + g.ext[1]);
-  const double dd = axis_distance(g, ax, 0, delta) * g.inv_c[ax];
-  pr.d2tab[i] = dd * dd;
-}
-
 template <typename T, bool OBS_ROWS>
 __global__ void k_band(const ProblemDev* tab) {
   const ProblemDev& pr = tab[blockIdx.y];
@@ -269,16 +271,10 @@ __global__ void k_band(const ProblemDev* tab) {
   }
 }
 
-// Band of C (obs rows), with the distance table it needs; the table must be
-// complete before launch_band_state runs too.
+// Band of C (obs rows); the distance table comes from launch_prepare.
 void launch_band_obs(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st) {
-  int64_t dmax = 0, emax = 0;
-  for (int i = 0; i < tab.count; ++i) {
-    const GridDev& g = tab.p[i].grid;
-    dmax = tab.p[i].d > dmax ? tab.p[i].d : dmax;
-    emax = std::max<int64_t>(emax, g.ext[0] + g.ext[1] + g.ext[2]);
-  }
-  k_dist_table<<<dim3((unsigned)((emax + 255) / 256), tab.count), 256, 0, st>>>(dtab); note_launches(1);
+  int64_t dmax = 0;
+  for (int i = 0; i < tab.count; ++i) dmax = tab.p[i].d > dmax ? tab.p[i].d : dmax;
   dim3 go((unsigned)((dmax * 32 + 255) / 256), tab.count);
   if (tab.p[0].precision == 0) k_band<double, true><<<go, 256, 0, st>>>(dtab);
   else k_band<float, true><<<go, 256, 0, st>>>(dtab);
