@@ -201,7 +201,7 @@ int info_esrf_analysis_batched(const info_esrf_problem* probs, int32_t count,
 /* Autotuner (not in the paper): times the analysis of probs[0..count) with
  * each candidate setting of the launch and eigensolver parameters that do not
  * change the converged answer -- cluster_size (0, 4 or -1), power_iters (0 or 1)
- * and oversample (6 or 10) -- starting from *opt, and writes the fastest into
+ * and oversample (2, 6 or 10) -- starting from *opt, and writes the fastest into
  * *opt (other fields untouched).  A candidate whose warm-up run leaves a
  * system unconverged, fails, or needs more workspace than ws_bytes is skipped.
  * Each candidate runs once untimed and three times timed (CUDA events on

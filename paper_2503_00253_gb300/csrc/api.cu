@@ -526,10 +526,10 @@ int info_esrf_autotune(const info_esrf_problem* probs, int32_t count, info_esrf_
   double best = -1.0;
   info_esrf_options best_o = base;
   int first_rc = 0;
-  const int cs_list[3] = {0, 4, -1}, pi_list[2] = {0, 1}, os_list[2] = {6, 10};
+  const int cs_list[3] = {0, 4, -1}, pi_list[2] = {0, 1}, os_list[3] = {2, 6, 10};
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 2; ++b)
-      for (int c = 0; c < 2; ++c) {
+      for (int c = 0; c < 3; ++c) {
         info_esrf_options o = base;
         o.cluster_size = cs_list[a];
         o.power_iters = pi_list[b];

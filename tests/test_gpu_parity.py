@@ -541,7 +541,7 @@ def test_autotune_picks_a_converging_setting_and_keeps_parity(B):
     opts = B.make_options(precision=1)
     best = B.autotune(probs, opts)
     assert best > 0.0
-    assert opts.cluster_size in (0, 4, -1) and opts.power_iters in (0, 1) and opts.oversample in (6, 10)
+    assert opts.cluster_size in (0, 4, -1) and opts.power_iters in (0, 1) and opts.oversample in (2, 6, 10)
     mu_a, A_a, st = B.info_esrf_analysis(pr.grid, probs[0]["X"], probs[0]["obs_idx"], probs[0]["y"], probs[0]["R"],
                                          pr.Q, 1e-6, opts)
     torch.cuda.synchronize()
