@@ -129,8 +129,16 @@ __device__ __forceinline__ double combine_partials(const float (*ff)[2], const d
   }
 }
 
+// CTAs per SM the kernel is compiled for: kPcgFp32CtasPerSm for the FP32 path
+// with a small Ritz rank (the register budget a thread then gets lets that
+// many 256-thread CTAs share an SM), one otherwise.  The grid is sized by the
+// measured occupancy at launch, and the vector scratch by this count.
+constexpr int kPcgFp32CtasPerSm = 2;
+template <typename T, int KMAX>
+constexpr int pcg_ctas_per_sm() { return (sizeof(T) == 4 && KMAX <= 12) ? kPcgFp32CtasPerSm : 1; }
+
 template <typename T, int JT, int KMAX>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, pcg_ctas_per_sm<T, KMAX>())
 k_pcg(const ProblemDev* tab, int count, int total_groups, int32_t* counter, T* gscratch,
       int64_t scratch_stride, int use_smem, uint64_t band_mask, const int32_t* band_fb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -438,7 +446,10 @@ static constexpr size_t kSmemVecLimit = 160 * 1024;
 size_t pcg_scratch_bytes(const ProblemTable& tab, int num_sms) {
   const size_t vb = vec_bytes(tab);
   if (vb <= kSmemVecLimit) return 0;
-  return vb * (size_t)num_sms;
+  int kmax = 0;
+  for (int i = 0; i < tab.count; ++i) kmax = tab.p[i].kR > kmax ? tab.p[i].kR : kmax;
+  const int per_sm = (tab.p[0].precision == 1 && kmax <= 12) ? kPcgFp32CtasPerSm : 1;
+  return vb * (size_t)num_sms * (size_t)per_sm;   // one slice per resident CTA
 }
 
 template <typename T, int JT, int KMAX>
@@ -449,8 +460,16 @@ static int launch_pcg_t(const ProblemTable& tab, const ProblemDev* dtab, int32_t
   const int use_smem = vb <= kSmemVecLimit;
   const size_t dyn = use_smem ? vb : 0;
   cudaFuncSetAttribute(k_pcg<T, JT, KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemVecLimit);
-  int grid = tab.total_groups < num_sms ? tab.total_groups : num_sms;
-  if (!use_smem && scratch_bytes < vb * (size_t)grid) return -1;
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<T, JT, KMAX>, kThreads, dyn) != cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  int64_t want = (int64_t)per_sm * num_sms;
+  if (!use_smem && vb > 0) want = std::min<int64_t>(want, (int64_t)(scratch_bytes / vb));   // scratch slices
+  int grid = (int)std::min<int64_t>(tab.total_groups, want);
+  if (!use_smem && grid < 1 && tab.total_groups > 0) return -1;
   if (grid <= 0) return 0;
   cudaMemsetAsync(counter, 0, sizeof(int32_t), st);
   k_pcg<T, JT, KMAX><<<grid, kThreads, dyn, st>>>(dtab, tab.count, tab.total_groups, counter,
