@@ -204,10 +204,10 @@ int info_esrf_analysis_batched(const info_esrf_problem* probs, int32_t count,
  * and oversample (2, 6 or 10) -- starting from *opt, and writes the fastest into
  * *opt (other fields untouched).  A candidate whose warm-up run leaves a
  * system unconverged, fails, or needs more workspace than ws_bytes is skipped.
- * Each candidate runs once untimed and three times timed (CUDA events on
- * stream); the problems' outputs are overwritten and the stream is
- * synchronized.  best_ms (host, may be NULL) receives the fastest mean time
- * per call.  Returns 0, or the first error of the base setting. */
+ * Each candidate runs once untimed and then five times, each call timed on
+ * its own (CUDA events on stream), and is ranked by its fastest call; the
+ * problems' outputs are overwritten and the stream is synchronized.  best_ms
+ * (host, may be NULL) receives the winner's fastest time per call.  Returns 0, or the first error of the base setting. */
 int info_esrf_autotune(const info_esrf_problem* probs, int32_t count, info_esrf_options* opt, void* workspace,
                        size_t ws_bytes, void* stream, double* best_ms);
 
