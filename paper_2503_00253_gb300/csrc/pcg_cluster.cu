@@ -144,7 +144,6 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
   __shared__ __align__(16) LaneState L;
   __shared__ Setup S;
   __shared__ int s_klo[kMaxTiles], s_w[kMaxTiles], s_off[kMaxTiles];
-  __shared__ float s_ascale[kMaxTiles], s_ainv[kMaxTiles];   // power-of-two scale of C per tile (FP16 operands)
   __shared__ __align__(16) float s_pmax_in[kMaxCS][kJ];     // max |p| per lane over each CTA's own rows
   __shared__ __align__(16) float s_pscale[kJ], s_pinv[kJ];  // power-of-two scale of p per lane
   __shared__ float s_gram[3][kK * kK];
@@ -171,16 +170,16 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
 
   // ---------------- set-up: band reach of the own rows ----------------
   if (tid == 0) { s_lo_min = 1 << 30; s_hi_max = -(1 << 30); s_bad = (R_s > kMaxTiles * kTile) ? 1 : 0; }
-  for (int t = tid; t < kMaxTiles; t += blockDim.x) reinterpret_cast<int*>(s_ascale)[t] = 0;
   __syncthreads();
   // per-row window [lo, hi] relative to s0, kept in the dynamic buffer's tail
   int* rlo = reinterpret_cast<int*>(dyn);
   int* rhi = rlo + R_s;
-  if (2 * R_s > dyn_floats) s_bad = 1;
+  float* ramax = dyn + 2 * R_s;   // max |C| of each own row (its FP16 scale)
+  if (3 * R_s > dyn_floats) s_bad = 1;
   __syncthreads();
   if (!s_bad) {
     // two threads per row (alternate entries), combined by a shuffle; the same
-    // pass takes each 16-row tile's max |C| (the FP16 scale of its tile)
+    // pass takes each row's max |C| (the FP16 scale of its row)
     const float* cval = reinterpret_cast<const float*>(pr.oo_val);
     for (int base = 0; base < nrows; base += (int)blockDim.x / 2) {
       const int row = base + (tid >> 1), part = tid & 1;
@@ -196,8 +195,9 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
           dmax = dl > dmax ? dl : dmax;
           amax = fmaxf(amax, fabsf(cval[(int64_t)e * d + a]));
         }
-        atomicMax(reinterpret_cast<int*>(s_ascale) + row / kTile, __float_as_int(amax));   // amax >= 0: int order
       }
+      amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, 1));
+      if (row < nrows && part == 0) ramax[row] = amax;
       dmin = min(dmin, __shfl_xor_sync(0xffffffffu, dmin, 1));
       dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, 1));
       if (row < nrows && part == 0) {
@@ -294,8 +294,9 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
   const int o_push = (o_at + k * R_s + 1) & ~1;
   const int o_rpush = o_push + 2 * npush_max;
   const int o_rinv = o_rpush + 2 * nrpush_max;     // R^-1/2 of the own rows
-  const int need = o_rinv + R_s;
-  if (need > dyn_floats) bad = 1;
+  const int o_rsc = o_rinv + R_s;                  // power-of-two scale of each row of C, and its inverse
+  const int need = o_rsc + 2 * R_s;
+  if (need > dyn_floats || o_rsc < 3 * R_s) bad = 1;   // the scales are copied out of the head region
   cluster.sync();                                   // remote reads of S done before anyone exits
   if (bad) {
     if (cl_id == 0 && crank == 0 && tid == 0) *fallback = 1;
@@ -312,20 +313,26 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
   int2* push = reinterpret_cast<int2*>(dyn + o_push);
   int2* rpush = reinterpret_cast<int2*>(dyn + o_rpush);
   float* s_rinv = dyn + o_rinv;
+  float* rsc = dyn + o_rsc;
+  float* rsi = rsc + R_s;
   const float* val = reinterpret_cast<const float*>(pr.oo_val);
   const float* Phi = reinterpret_cast<const float*>(pr.Phi);
   const float* CPhi = reinterpret_cast<const float*>(pr.CPhi);
   const float* W = reinterpret_cast<const float*>(pr.W);
 
   // ---------------- set-up: fill tiles and the constant arrays ----------------
+  // the row scales leave the head of the buffer before the tiles overwrite it
+  for (int row = tid; row < R_s; row += blockDim.x) pow2_scale(row < nrows ? ramax[row] : 0.f, rsc[row], rsi[row]);
+  __syncthreads();
   for (int i = tid; i < tilesz; i += blockDim.x) Ct[i] = 0.f;
   for (int i = o_pw + tid; i < o_ph; i += blockDim.x) dyn[i] = 0.f;
   __syncthreads();
-  // C is stored per tile as FP16 hi + lo pairs of C scaled by a power of two
-  // (max |C| of the tile into [0.5, 1)), in MMA fragment order: per 16-column
-  // chunk, the hi halves of the 32 lanes (8 each), then the lo halves.
-  for (int t = tid; t < ntiles; t += blockDim.x) pow2_scale(s_ascale[t], s_ascale[t], s_ainv[t]);
-  __syncthreads();
+  // C is stored per tile as FP16 hi + lo pairs of C with each row scaled by a
+  // power of two (the row's max |C| into [0.5, 1)), in MMA fragment order: per
+  // 16-column chunk, the hi halves of the 32 lanes (8 each), then the lo halves.
+  // Scaling row i of A scales row i of A B, so the matvec undoes it per output
+  // row; rows of very different size (observation errors of very different
+  // size) each keep FP16's relative precision.
   {
     __half* Ch = reinterpret_cast<__half*>(Ct);
     for (int base = 0; base < nrows; base += (int)blockDim.x / 2) {
@@ -334,7 +341,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       const int64_t a = s0 + row;
       const int nnz = pr.oo_nnz[a];
       const int t = row / kTile, r = row % kTile;
-      const float sc = s_ascale[t];
+      const float sc = rsc[row];
       for (int e = part; e < nnz; e += 2) {
         const int rel = row + wrap_delta(pr.oo_col[(int64_t)e * d + a], (int)a, (int)d);
         const int kk = rel - s_klo[t], kc = kk & 15;
@@ -497,21 +504,21 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
           }
         }
         // D element i of a row is lane 8 q + i after the permutation above
-        const float ia = s_ainv[t];
         const float4 si0 = ld4(&s_pinv[8 * q]), si1 = ld4(&s_pinv[8 * q + 4]);
         const float4 sg0 = ld4(&L.sigf[8 * q]), sg1 = ld4(&L.sigf[8 * q + 4]);
-        const float un[8] = {ia * si0.x, ia * si0.y, ia * si0.z, ia * si0.w,
-                             ia * si1.x, ia * si1.y, ia * si1.z, ia * si1.w};
+        const float un[8] = {si0.x, si0.y, si0.z, si0.w, si1.x, si1.y, si1.z, si1.w};
         const float sg[8] = {sg0.x, sg0.y, sg0.z, sg0.w, sg1.x, sg1.y, sg1.z, sg1.w};
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int row = h ? rB : rA;
           if (row < nrows) {
+            const float ir = rsi[row];   // inverse scale of this row of C
             const float4 p0 = ld4(pw + (row + hl) * kLD + 8 * q), p1 = ld4(pw + (row + hl) * kLD + 8 * q + 4);
             const float pv[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
             float y[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) y[i] = fmaf(sg[i], pv[i], ((h ? dB[i] : dA[i]) + (h ? eB[i] : eA[i])) * un[i]);
+            for (int i = 0; i < 8; ++i)
+              y[i] = fmaf(sg[i], pv[i], ((h ? dB[i] : dA[i]) + (h ? eB[i] : eA[i])) * (ir * un[i]));
             st4(vy + (row + kTH) * kLD + 8 * q, make_float4(y[0], y[1], y[2], y[3]));
             st4(vy + (row + kTH) * kLD + 8 * q + 4, make_float4(y[4], y[5], y[6], y[7]));
 #pragma unroll

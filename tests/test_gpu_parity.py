@@ -288,6 +288,24 @@ def test_fp32_band_kernel_sizes(B, n, stride, hw, N):
     assert ea <= 1e-4 and em <= 1e-4, (ea, em)
 
 
+def test_fp32_band_kernel_with_widely_varying_R(B):
+    """Observation-error variances spread over four orders of magnitude, so that
+    neighbouring rows of C differ in size by up to 10^4: the cluster kernel's
+    FP16 tensor-core matvec (C split into scaled FP16 pairs) must still meet the
+    mixed-precision bound."""
+    import dataclasses
+    pr = workloads.gaussian_problem_1d("rvar", n=4096, N=24, length_scale=24.0, obs_stride=4, r2=0.5,
+                                       half_width=60.0, Q=12, tol=1e-6, seed=77)
+    rng = np.random.default_rng(78)
+    R = 0.5 * 10.0 ** rng.uniform(-2.0, 2.0, pr.d)
+    y = pr.truth[pr.obs_idx] + np.sqrt(R) * rng.standard_normal(pr.d)
+    pr = dataclasses.replace(pr, R=R, y=y)
+    mu_a, A_a, st = run_analysis(B, pr, precision=1, ritz_rank=8)
+    ea, em = errors(pr, mu_a, A_a)
+    assert st["status"] == 0 and st["solver_path"] == 1, st
+    assert ea <= 1e-4 and em <= 1e-4, (ea, em)
+
+
 def test_mean_and_perturbation_calls_alone(B):
     pr = workloads.gaussian_problem_1d("sep", n=500, N=12, length_scale=5.0, obs_stride=4, r2=0.5,
                                        half_width=8.0, Q=6, tol=1e-12, seed=10)
