@@ -18,17 +18,24 @@
 // and the shared-memory budget at start-up and, if either fails, sets a
 // flag and exits so that the general kernel solves the systems instead.
 //
-// Per iteration (three cluster barriers):
+// The band matvec runs on the tensor cores (mma.sync, FP16 operands split
+// into hi + lo pairs after power-of-two scaling, FP32 accumulation; see the
+// matvec step below for why this keeps FP32 accuracy).
+//
+// Per iteration (three cluster barriers, a fourth for the learned term's r
+// halo):
 //   matvec y = sigma p + C p and partial p^T y      -> barrier 1 -> alpha
 //   x += alpha p, r -= alpha y, partial r^T r, Phi^T r, A^T r -> barrier 2
-//   convergence, preconditioner scalars, refills;  p = z + beta p   -> barrier 3
+//   convergence, preconditioner scalars, refills;  p = z + beta p, the lanes'
+//   max |p| (the next matvec's scale)               -> barrier 3
 //   new lanes start, halo of p copied from the neighbours.
 // Every CTA sums the CS partials in rank order, so all CTAs of a cluster
 // take identical decisions without further communication.  A lane whose
 // system converges is refilled with the next system of a global queue
 // ordered hardest (smallest shift) first, so no lane idles while work
-// remains.  Scalars of the CG recurrence are FP64; the k x k algebra of the
-// limited-memory preconditioner is FP32 (it only shapes the preconditioner).
+// remains.  Dot products of the FP32 vectors are float-float sums (FP64
+// accuracy without the FP64 pipe); the CG scalars formed from them and the
+// k x k algebra of the limited-memory preconditioner are FP32.
 #include <cooperative_groups.h>
 #include <cuda_fp16.h>
 #include <math.h>
