@@ -459,12 +459,32 @@ static int launch_pcg_t(const ProblemTable& tab, const ProblemDev* dtab, int32_t
   const size_t vb = vec_bytes(tab);
   const int use_smem = vb <= kSmemVecLimit;
   const size_t dyn = use_smem ? vb : 0;
-  cudaFuncSetAttribute(k_pcg<T, JT, KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemVecLimit);
-  int per_sm = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<T, JT, KMAX>, kThreads, dyn) != cudaSuccess ||
-      per_sm < 1) {
+  // the attribute once per thread and device, the occupancy per dynamic size
+  constexpr int kMaxDev = 64;
+  static thread_local bool attr_set[kMaxDev] = {};
+  static thread_local size_t occ_dyn[kMaxDev] = {};
+  static thread_local int occ_per_sm[kMaxDev] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
     cudaGetLastError();
-    per_sm = 1;
+    dev = -1;
+  }
+  if (dev < 0 || !attr_set[dev]) {
+    cudaFuncSetAttribute(k_pcg<T, JT, KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemVecLimit);
+    if (dev >= 0) attr_set[dev] = true;
+  }
+  int per_sm = 0;
+  if (dev >= 0 && occ_per_sm[dev] > 0 && occ_dyn[dev] == dyn) per_sm = occ_per_sm[dev];
+  if (per_sm < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<T, JT, KMAX>, kThreads, dyn) != cudaSuccess ||
+        per_sm < 1) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+    if (dev >= 0) {
+      occ_dyn[dev] = dyn;
+      occ_per_sm[dev] = per_sm;
+    }
   }
   int64_t want = (int64_t)per_sm * num_sms;
   if (!use_smem && vb > 0) want = std::min<int64_t>(want, (int64_t)(scratch_bytes / vb));   // scratch slices

@@ -976,22 +976,44 @@ int band1d_cluster_size(const ProblemDev& p, int requested) {
   return CS;
 }
 
+// Launch facts that depend only on the device (the dynamic shared-memory
+// size and its function attribute) or on the device and the cluster size (the
+// co-resident cluster count), looked up once per thread and device.
+struct BandLaunchInfo {
+  bool ready = false;
+  int dyn_bytes = 0;                  // <= 0: the kernel cannot be configured on this device
+  int max_clusters[kMaxCS + 1] = {};  // 0: not looked up yet, -1: this cluster shape cannot run
+};
+
 int launch_pcg_band1d(const ProblemDev& p, const ProblemDev* dp, int CS, int32_t* queue, int32_t* fallback,
                       int num_sms, cudaStream_t st) {
   int clusters = (p.nsys + kJ - 1) / kJ;
   if (clusters > num_sms / CS) clusters = num_sms / CS;
   if (clusters < 1) clusters = 1;
-  int dev = 0, optin = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  cudaFuncAttributes fa;
-  cudaFuncGetAttributes(&fa, k_pcg_band1d);
-  const int dyn_bytes = (optin - (int)fa.sharedSizeBytes - 1024) & ~15;
-  if (dyn_bytes <= 0 ||
-      cudaFuncSetAttribute(k_pcg_band1d, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_bytes) != cudaSuccess) {
+  constexpr int kMaxDev = 64;
+  static thread_local BandLaunchInfo info_by_dev[kMaxDev];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev || CS < 1 || CS > kMaxCS) {
     cudaGetLastError();
     return -1;
   }
+  BandLaunchInfo& info = info_by_dev[dev];
+  if (!info.ready) {
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    cudaFuncGetAttributes(&fa, k_pcg_band1d);
+    info.dyn_bytes = (optin - (int)fa.sharedSizeBytes - 1024) & ~15;
+    if (info.dyn_bytes <= 0 ||
+        cudaFuncSetAttribute(k_pcg_band1d, cudaFuncAttributeMaxDynamicSharedMemorySize, info.dyn_bytes) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      info.dyn_bytes = 0;
+    }
+    info.ready = true;
+  }
+  const int dyn_bytes = info.dyn_bytes;
+  if (dyn_bytes <= 0) return -1;
   cudaMemsetAsync(queue, 0, sizeof(int32_t), st);
   cudaMemsetAsync(fallback, 0, sizeof(int32_t), st);
   cudaLaunchConfig_t cfg = {};
@@ -1009,11 +1031,16 @@ int launch_pcg_band1d(const ProblemDev& p, const ProblemDev* dp, int CS, int32_t
   // A cluster shape this GPU cannot co-schedule is left to the general kernel;
   // launch no more clusters than can run at once (later ones would only find
   // the queue drained).
-  int max_clusters = 0;
-  if (cudaOccupancyMaxActiveClusters(&max_clusters, k_pcg_band1d, &cfg) != cudaSuccess || max_clusters < 1) {
-    cudaGetLastError();
-    return -1;
+  if (info.max_clusters[CS] == 0) {
+    int mc = 0;
+    if (cudaOccupancyMaxActiveClusters(&mc, k_pcg_band1d, &cfg) != cudaSuccess || mc < 1) {
+      cudaGetLastError();
+      mc = -1;
+    }
+    info.max_clusters[CS] = mc;
   }
+  const int max_clusters = info.max_clusters[CS];
+  if (max_clusters < 1) return -1;
   if (clusters > max_clusters) {
     clusters = max_clusters;
     cfg.gridDim = dim3(clusters * CS, 1, 1);

@@ -402,9 +402,21 @@ int launch_ritz_cluster(const ProblemTable& tab, const ProblemDev* dtab, cudaStr
   size_t dyn = 0;
   for (int i = 0; i < tab.count; ++i) dyn = std::max(dyn, (size_t)tab.p[i].d * (size_t)tab.p[i].l * 4);
   dyn = std::max(dyn, (size_t)2 * kRMaxRows * (kRL + 1) * 4);   // Phi / C Phi own rows reuse the area
-  if (cudaFuncSetAttribute(k_ritz_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess) {
+  // the attribute allows the largest staging area once per thread and device
+  constexpr int kMaxDev = 64;
+  static thread_local bool attr_set[kMaxDev] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
     cudaGetLastError();
     return -1;
+  }
+  if (!attr_set[dev]) {
+    const size_t most = std::max(kRStageBytes, (size_t)2 * kRMaxRows * (kRL + 1) * 4);
+    if (cudaFuncSetAttribute(k_ritz_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most) != cudaSuccess) {
+      cudaGetLastError();
+      return -1;
+    }
+    attr_set[dev] = true;
   }
   cfg.dynamicSmemBytes = dyn;
   cfg.stream = st;
