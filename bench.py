@@ -38,7 +38,7 @@ TRAIN_SEEDS = (11, 12, 13)
 # DRAM bytes (read + write) of one k_pcg_band1d launch on this workload with the
 # learned correction, from the ncu capture summarised in
 # profiles/k_pcg_band1d_gauss1d_n8192_N40_d1024_Q32_fp32_learned.md; set to None when the kernel changes.
-PCG_DRAM_BYTES = None
+PCG_DRAM_BYTES = 1458176
 
 
 def _dist():
