@@ -69,7 +69,7 @@ __device__ __forceinline__ double gaspari_cohn(double z) {
 }
 
 // r^2 from the per-axis table tab[off_ax + |a_ax - b_ax|] = (dist_ax / c_ax)^2,
-// off = (0, ext0, ext0 + ext1); filled by k_dist_table with axis_distance.
+// off = (0, ext0, ext0 + ext1); filled by k_prepare with axis_distance.
 __device__ __forceinline__ double scaled_r2_tab(const GridDev& g, const double* tab, const Coord3& a,
                                                 const Coord3& b) {
   double r2 = 0.0;

@@ -334,7 +334,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
   for (int i = tid; i < tilesz; i += blockDim.x) Ct[i] = 0.f;
   for (int i = o_pw + tid; i < o_ph; i += blockDim.x) dyn[i] = 0.f;
   __syncthreads();
-  // C is stored per tile as FP16 hi + lo pairs of C with each row scaled by a
+  // C is stored tile by tile as FP16 hi + lo pairs of C with each row scaled by a
   // power of two (the row's max |C| into [0.5, 1)), in MMA fragment order: per
   // 16-column chunk, the hi halves of the 32 lanes (8 each), then the lo halves.
   // Scaling row i of A scales row i of A B, so the matvec undoes it per output
@@ -469,7 +469,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
   for (;;) {
     // ---------------- A: y = sigma p + C p on the own rows, partial p^T y ----------------
     // On the tensor cores: mma.sync m16n8k16 with FP16 operands and FP32
-    // accumulation.  C (per tile) and p (per lane, over the whole cluster) are
+    // accumulation.  C (per row) and p (per lane, over the whole cluster) are
     // scaled by powers of two into [0.5, 1) and split into FP16 hi + lo, and
     // each product is taken in three terms, a b = a_h b_h + (a_h b_l + a_l b_h),
     // which keeps it near FP32 accuracy; the scales are undone exactly.  A warp
