@@ -156,8 +156,8 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
   __shared__ float s_gram[3][kK * kK];
   __shared__ float s_theta[kK];
   // partial sums pushed by every CTA of the cluster into every CTA (slot = source rank)
-  __shared__ float s_pap_in[kMaxCS][kJ][2];      // p^T y (float-float)
-  __shared__ float s_res_in[kMaxCS][kJ][kNR];    // rr (float-float), Phi^T r, A^T r
+  __shared__ __align__(16) float s_pap_in[kMaxCS][kJ][2];      // p^T y (float-float)
+  __shared__ __align__(16) float s_res_in[kMaxCS][kJ][kNR];    // rr (float-float), Phi^T r, A^T r
   __shared__ float s_wpap[kNW][kJ][2];
   __shared__ int s_lo_min, s_hi_max, s_bad;
 
@@ -559,9 +559,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       const int j = tid % kJ, dst = tid / kJ;
       float hi = 0.f, lo = 0.f;
       for (int w = 0; w < kNW; ++w) ff_merge(hi, lo, s_wpap[w][j][0], s_wpap[w][j][1]);
-      float* rp = cluster.map_shared_rank(&s_pap_in[crank][j][0], dst);
-      rp[0] = hi;
-      rp[1] = lo;
+      *reinterpret_cast<float2*>(cluster.map_shared_rank(&s_pap_in[crank][j][0], dst)) = make_float2(hi, lo);
     }
     cluster.sync();   // (1)
     // ---------------- alpha ----------------
@@ -727,19 +725,27 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       }
       const int qv = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
       const int qdst = (j0 + (qv & 3)) * kNR + (qv < 4 ? 0 : 2);
-      // push this warp's four lanes to every CTA of the cluster
-      for (int dst = 0; dst < CS; ++dst) {
-        float* base = cluster.map_shared_rank(&s_res_in[crank][0][0], dst);
+      // push this warp's four lanes to every CTA of the cluster.  Distributed
+      // shared-memory stores are separate transactions, so lanes 4 k gather
+      // values 4 k .. 4 k + 3 of each block and store them as one 16-byte word
+      // (2 kK is a multiple of 4, so a group never straddles two lanes' rows).
+      float4 sv4[3];
 #pragma unroll
-        for (int b = 0; b < 3; ++b) {
-          const int idx = 32 * b + lane;          // = jj * 2kK + (m or kK + m)
-          if (idx >= 4 * 2 * kK) continue;
-          const int jj = idx / (2 * kK), w = idx % (2 * kK);
-          base[(j0 + jj) * kNR + 4 + w] = sv[b];
-        }
-        if ((lane & 3) == 0) {
-          base[qdst] = qh;
-          base[qdst + 1] = ql;
+      for (int b = 0; b < 3; ++b)
+        sv4[b] = make_float4(sv[b], __shfl_down_sync(0xffffffffu, sv[b], 1),
+                             __shfl_down_sync(0xffffffffu, sv[b], 2), __shfl_down_sync(0xffffffffu, sv[b], 3));
+      static_assert((2 * kK) % 4 == 0 && kNR % 4 == 0, "16-byte groups of the residual partials");
+      if ((lane & 3) == 0) {
+        for (int dst = 0; dst < CS; ++dst) {
+          float* base = cluster.map_shared_rank(&s_res_in[crank][0][0], dst);
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+            const int idx = 32 * b + lane;          // = jj * 2kK + (m or kK + m)
+            if (idx >= 4 * 2 * kK) continue;
+            const int jj = idx / (2 * kK), w = idx % (2 * kK);
+            st4(base + (j0 + jj) * kNR + 4 + w, sv4[b]);
+          }
+          *reinterpret_cast<float2*>(base + qdst) = make_float2(qh, ql);
         }
       }
     }
