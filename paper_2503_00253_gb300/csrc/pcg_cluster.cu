@@ -555,11 +555,14 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       s_wpap[warp][8 * q + g][1] = vl[0];
     }
     __syncthreads();
-    if (tid < kJ * CS) {
-      const int j = tid % kJ, dst = tid / kJ;
-      float hi = 0.f, lo = 0.f;
-      for (int w = 0; w < kNW; ++w) ff_merge(hi, lo, s_wpap[w][j][0], s_wpap[w][j][1]);
-      *reinterpret_cast<float2*>(cluster.map_shared_rank(&s_pap_in[crank][j][0], dst)) = make_float2(hi, lo);
+    if (tid < (kJ / 2) * CS) {   // two lanes per thread: one 16-byte store per destination
+      const int j = 2 * (tid % (kJ / 2)), dst = tid / (kJ / 2);
+      float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+      for (int w = 0; w < kNW; ++w) {
+        ff_merge(h0, l0, s_wpap[w][j][0], s_wpap[w][j][1]);
+        ff_merge(h1, l1, s_wpap[w][j + 1][0], s_wpap[w][j + 1][1]);
+      }
+      st4(cluster.map_shared_rank(&s_pap_in[crank][j][0], dst), make_float4(h0, l0, h1, l1));
     }
     cluster.sync();   // (1)
     // ---------------- alpha ----------------
