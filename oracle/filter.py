@@ -3,7 +3,9 @@
 Follows the paper's formulas literally, with dense matrices and direct solves:
 
 * Eq. normalized_perturbations: z^(i) = (x^(i) - mu) / sqrt(N - 1); W = H Z with
-  H the observation subsampling operator (rows of the identity at obs_idx).
+  H the observation subsampling operator (rows of the identity at obs_idx), or,
+  in the *_H functions, a general linear operator H [d][n] (the paper's
+  experiments observe weighted sums, Sec. 4.1 and Sec. 5.1).
 * Eq. localized_state_covar and Sec. 2.3: Sxx = L o (Z Z^T), Sxh = Sxx H^T,
   Shh = H Sxx H^T.
 * Eq. info_esrf_mean_solve: mu_a = mu + Sxh (R + Shh)^-1 (y - H mu).
@@ -81,6 +83,44 @@ def perturbation_solves(Shh, W, R, s, p):
     for sq, pq in zip(s, p):
         vbar += pq * np.linalg.solve((sq + 1.0) * Rm + Shh, W)
     return vbar
+
+
+def localized_covariances_H(Z, H, grid, L=None):
+    """The same covariances for a general linear observation operator H [d][n]
+    (Sec. 2.3: h linearized, model-space localization): W = H Z,
+    Sxh = (L o Z Z^T) H^T [n][d], Shh = H Sxh [d][d]."""
+    n = Z.shape[0]
+    H = np.asarray(H, dtype=np.float64)
+    if L is None:
+        Lxx = localization.localization_matrix(grid, np.arange(n), np.arange(n))
+    else:
+        Lxx = np.asarray(L, dtype=np.float64)
+    Sxh = (Lxx * (Z @ Z.T)) @ H.T
+    return H @ Z, Sxh, H @ Sxh
+
+
+def mean_update_H(X, H, y, R, grid, L=None):
+    """Eq. info_esrf_mean_solve with a general H: mu_a = mu + Sxh (R + Shh)^-1 (y - H mu)."""
+    mu, Z = anomalies(X)
+    W, Sxh, Shh = localized_covariances_H(Z, H, grid, L)
+    innov = np.asarray(y, dtype=np.float64) - np.asarray(H, dtype=np.float64) @ mu
+    return mu + Sxh @ np.linalg.solve(np.diag(R) + Shh, innov)
+
+
+def _perturbation_from(Z, W, Sxh, Shh, R, Q, ell, rule):
+    """z_a^(i) = z^(i) - Sxh sum_q p_q ((s_q + 1) R + Shh)^-1 w^(i) (Sec. 3.2), exact solves."""
+    ell_used = choose_ell(Shh, R, ell)
+    s, p = quadrature.quadrature(Q, ell_used, rule)
+    vbar = perturbation_solves(Shh, W, R, s, p)
+    N = Z.shape[1]
+    return math.sqrt(N - 1) * (Z - Sxh @ vbar).T
+
+
+def perturbation_update_H(X, H, R, grid, Q, ell=None, rule="elliptic", L=None):
+    """Analysis anomalies A_a [N][n] of Sec. 3.2 for a general linear H [d][n]."""
+    mu, Z = anomalies(X)
+    W, Sxh, Shh = localized_covariances_H(Z, H, grid, L)
+    return _perturbation_from(Z, W, Sxh, Shh, R, Q, ell, rule)
 
 
 def perturbation_update(X, obs_idx, R, grid, Q, ell=None, rule="elliptic", L=None,

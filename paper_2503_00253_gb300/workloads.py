@@ -242,3 +242,60 @@ def random_obs_problem(grid: Grid, N: int, d: int, r2: float, Q: int, tol: float
     R = r2 * (0.5 + rng.random(d))
     y = truth[obs_idx] + np.sqrt(R) * rng.standard_normal(d)
     return Problem(f"random_{n}_{d}", grid, X, truth, obs_idx, y, R, Q, tol)
+
+
+def gaussian_channel_operator(n: int, d: int, bandwidth: float, cutoff: float = 1e-10):
+    """Weighted-sum observations in the form of the single-cycle experiment
+    (Sec. 4.1): row i weights state j by exp(-c(j, centre_i)^2 / (2 b^2)), with
+    c the chordal distance on the circle of circumference n and centres evenly
+    spaced (n / d apart).  Weights below ``cutoff`` are dropped.  Returns the
+    dense matrix [d][n] and its CSR arrays (rowptr, col, val)."""
+    j = np.arange(n)
+    centres = (np.arange(d) * n) // d
+    delta = np.abs(j[None, :] - centres[:, None])
+    c = _chordal(delta, n)
+    H = np.exp(-(c ** 2) / (2.0 * bandwidth ** 2))
+    H[H < cutoff] = 0.0
+    return H, _csr(H)
+
+
+def column_sum_operator(grid_shape, columns, channels: int, spacing: float, bandwidth: float):
+    """Vertical weighted sums in the form of the layered experiment (Sec. 5.1):
+    for each observed column x and channel r, sum_z X[z][x] f_r(z) with
+    f_r(z) proportional to exp(-(z - spacing r)^2 / (2 b^2)) and sum_z f_r(z)^2 = 1
+    (z and r counted from 1).  ``grid_shape`` is (nx, 1, nz); flat index z nx + x.
+    Returns the dense matrix [len(columns) channels][n] and its CSR arrays."""
+    nx, _, nz = (int(v) for v in grid_shape)
+    n = nx * nz
+    z = np.arange(1, nz + 1)
+    rows = []
+    for x in columns:
+        for r in range(1, channels + 1):
+            f = np.exp(-((z - spacing * r) ** 2) / (2.0 * bandwidth ** 2))
+            f /= math.sqrt(float((f ** 2).sum()))
+            row = np.zeros(n)
+            row[(z - 1) * nx + int(x)] = f
+            rows.append(row)
+    H = np.array(rows)
+    return H, _csr(H)
+
+
+def _csr(H: np.ndarray):
+    rowptr = np.zeros(H.shape[0] + 1, dtype=np.int64)
+    cols, vals = [], []
+    for i in range(H.shape[0]):
+        nz = np.nonzero(H[i])[0]
+        cols.append(nz)
+        vals.append(H[i, nz])
+        rowptr[i + 1] = rowptr[i] + nz.size
+    return rowptr, np.concatenate(cols).astype(np.int64), np.concatenate(vals).astype(np.float64)
+
+
+def general_obs_problem(name: str, grid: Grid, X: np.ndarray, truth: np.ndarray, H: np.ndarray, r2: float,
+                        Q: int, tol: float, seed: int):
+    """Observations y = H truth + noise with variance r2 for a dense H [d][n]."""
+    rng = np.random.default_rng(seed)
+    d = H.shape[0]
+    R = np.full(d, float(r2))
+    y = H @ truth + math.sqrt(r2) * rng.standard_normal(d)
+    return dict(name=name, grid=grid, X=X, truth=truth, H=H, y=y, R=R, Q=Q, tol=tol)

@@ -176,3 +176,66 @@ def test_getkf_gain_matches_eigen_f2():
     f2 = 1.0 / (1.0 + lam + np.sqrt(1.0 + lam))
     G2 = Sxh @ (rih[:, None] * (V @ np.diag(f2) @ V.T) * rih[None, :])
     assert np.max(np.abs(G - G2)) < 1e-12 * np.max(np.abs(G))
+
+
+# ---------------------------------------------------------------------------
+# General linear observation operators (Sec. 2.3 with h linearized; the
+# paper's experiments observe weighted sums, Sec. 4.1 and Sec. 5.1)
+# ---------------------------------------------------------------------------
+
+def test_general_H_selection_matches_subsampling():
+    """H = rows of the identity at obs_idx gives the subsampling path's results."""
+    pr = _small(n=60, N=8, stride=3, hw=6.0, seed=5)
+    H = np.eye(pr.n)[pr.obs_idx]
+    A = F.perturbation_update_H(pr.X, H, pr.R, pr.grid, Q=12)
+    A_ref = F.perturbation_update(pr.X, pr.obs_idx, pr.R, pr.grid, Q=12)
+    Af = pr.X - pr.X.mean(0)
+    assert F.relative_increment_error(A, A_ref, Af) < 1e-12
+    mu = F.mean_update_H(pr.X, H, pr.y, pr.R, pr.grid)
+    mu_ref = F.mean_update(pr.X, pr.obs_idx, pr.y, pr.R, pr.grid)
+    assert np.max(np.abs(mu - mu_ref)) < 1e-12 * np.max(np.abs(mu_ref))
+
+
+def test_general_H_unlocalized_analysis_covariance_is_kalman():
+    """Weighted-sum observations, no localization, many nodes: Z_a Z_a^T is the
+    Kalman analysis covariance S - S H^T (R + H S H^T)^-1 H S with S = Z Z^T."""
+    pr = _small(n=60, N=7, seed=6)
+    H, _ = workloads.gaussian_channel_operator(pr.n, 12, 3.0)
+    R = 0.3 * (1.0 + np.linspace(0, 1, 12))
+    A = F.perturbation_update_H(pr.X, H, R, pr.grid, Q=48, ell=1e4, L=np.ones((pr.n, pr.n)))
+    Za = A.T / math.sqrt(pr.N - 1)
+    mu, Z = F.anomalies(pr.X)
+    S = Z @ Z.T
+    Sa = S - S @ H.T @ np.linalg.solve(np.diag(R) + H @ S @ H.T, H @ S)
+    assert np.max(np.abs(Za @ Za.T - Sa)) < 1e-10 * np.max(np.abs(S))
+
+
+def test_general_H_mean_update_information_form():
+    """mu_a with a weighted-sum H equals (Sxx^-1 + H^T R^-1 H)^-1 applied as in the
+    information form (N > n so that the localized Sxx is invertible)."""
+    pr = _small(n=10, N=25, stride=2, hw=4.0, seed=7)
+    H, _ = workloads.gaussian_channel_operator(pr.n, 4, 1.5)
+    rng = np.random.default_rng(8)
+    y = rng.standard_normal(4)
+    R = np.full(4, 0.4)
+    mu, Z = F.anomalies(pr.X)
+    L = localization.localization_matrix(pr.grid, np.arange(pr.n), np.arange(pr.n))
+    Sxx = L * (Z @ Z.T)
+    Rinv = np.diag(1.0 / R)
+    Sa = np.linalg.inv(np.linalg.inv(Sxx) + H.T @ Rinv @ H)
+    mu_info = mu + Sa @ H.T @ Rinv @ (y - H @ mu)
+    mu_a = F.mean_update_H(pr.X, H, y, R, pr.grid)
+    assert np.max(np.abs(mu_a - mu_info)) < 1e-9 * np.max(np.abs(mu_info - mu))
+
+
+def test_weighted_sum_operators_follow_the_paper_forms():
+    """Channel weights peak at 1 on their centre and decay as the Gaussian of the
+    chordal distance; column-sum weights have unit 2-norm per channel."""
+    H, (rp, col, val) = workloads.gaussian_channel_operator(200, 10, 4.0)
+    assert np.allclose(H[np.arange(10), (np.arange(10) * 200) // 10], 1.0)
+    c = (200 / math.pi) * math.sin(math.pi * 3 / 200)
+    assert abs(H[0, 3] - math.exp(-c * c / 32.0)) < 1e-15
+    assert np.array_equal(np.diff(rp), (H != 0).sum(1))
+    H2, _ = workloads.column_sum_operator((8, 1, 12), [1, 5], 3, 4.0, 2.0)
+    assert np.allclose((H2 ** 2).sum(1), 1.0)
+    assert np.all(H2.reshape(6, 12, 8)[:, :, [0, 2, 3, 4, 6, 7]] == 0.0)
