@@ -144,6 +144,22 @@ typedef struct {
   double* A_a;            /* [N][n] or NULL */
   int64_t max_oo;         /* band capacities; <= 0: from the options / geometry */
   int64_t max_xo;
+  /* General linear observation operator, or NULL (subsampling at obs_idx).
+   * The paper's experiments observe weighted sums of the state (Sec. 4.1,
+   * Sec. 5.1); with h linearized and model-space localization (Sec. 2.3) the
+   * covariances are Sxh = (L o Z Z^T) H^T [n][d] and Shh = H Sxh [d][d].  H is
+   * given in CSR form as device arrays, one row per observation: H_rowptr [d + 1]
+   * (H_rowptr[0] = 0, non-decreasing, H_rowptr[d] = H_nnz), H_col [H_nnz] state
+   * indices in [0, n), H_val [H_nnz] weights.  obs_idx is then not read, and y
+   * (if given) is an observation of H x.  Both covariances are formed densely,
+   * so n d <= 2^28 (INFO_ESRF_ERR_UNSUPPORTED above); the PCG runs in the
+   * general kernel.  A malformed H (row pointers or columns out of range)
+   * makes the call return INFO_ESRF_ERR_BAD_OBS_INDEX; no entry outside the
+   * arrays is read. */
+  const int64_t* H_rowptr;
+  const int64_t* H_col;
+  const double* H_val;
+  int64_t H_nnz;
 } info_esrf_problem;
 
 /* Fills *opt with the defaults listed above. */

@@ -67,7 +67,8 @@ class ProblemC(ctypes.Structure):
     _fields_ = [("grid", Grid), ("N", c_int64), ("d", c_int64), ("Q", c_int32), ("pad_", c_int32),
                 ("tol", c_double), ("X", c_void_p), ("obs_idx", c_void_p), ("y", c_void_p),
                 ("R_diag", c_void_p), ("mu_a", c_void_p), ("A_a", c_void_p), ("max_oo", c_int64),
-                ("max_xo", c_int64)]
+                ("max_xo", c_int64), ("H_rowptr", c_void_p), ("H_col", c_void_p), ("H_val", c_void_p),
+                ("H_nnz", c_int64)]
 
 
 _LIB = None
@@ -333,9 +334,35 @@ def info_esrf_perturbation_update(grid, X, obs_idx, R, Q, tol, options=None, ws=
     return A_a, (st.as_dict() if stats else None)
 
 
+def _fill_problem(c: "ProblemC", p: dict, X: torch.Tensor, mu_a: torch.Tensor, A_a: torch.Tensor) -> None:
+    """One problem of a batched call.  Observations are either indices (``obs_idx``)
+    or a general linear operator ``H`` = (rowptr int64 [d + 1], col int64 [nnz],
+    val float64 [nnz]), device tensors in CSR form."""
+    N = X.shape[0]
+    c.grid = make_grid(p["grid"])
+    H = p.get("H")
+    if H is not None:
+        rowptr, col, val = H
+        _need(rowptr, torch.int64, "H rowptr")
+        _need(col, torch.int64, "H col")
+        _need(val, torch.float64, "H val")
+        d = rowptr.numel() - 1
+        c.H_rowptr, c.H_col, c.H_val, c.H_nnz = rowptr.data_ptr(), col.data_ptr(), val.data_ptr(), col.numel()
+        c.obs_idx = None
+    else:
+        d = p["obs_idx"].numel()
+        c.obs_idx = p["obs_idx"].data_ptr()
+        c.H_rowptr, c.H_col, c.H_val, c.H_nnz = None, None, None, 0
+    c.N, c.d, c.Q, c.tol = N, d, int(p["Q"]), float(p["tol"])
+    c.X, c.y, c.R_diag = X.data_ptr(), p["y"].data_ptr(), p["R"].data_ptr()
+    c.mu_a, c.A_a = mu_a.data_ptr(), A_a.data_ptr()
+    c.max_oo, c.max_xo = int(p.get("max_oo", 0)), int(p.get("max_xo", 0))
+
+
 def info_esrf_analysis_batched(problems: Sequence[dict], options: Optional[Options] = None,
                                ws: Optional[torch.Tensor] = None, stats: bool = True, stream=None):
-    """problems: dicts with grid, X, obs_idx, y, R, Q, tol and optional mu_a, A_a, max_oo, max_xo."""
+    """problems: dicts with grid, X, obs_idx (or H, see _fill_problem), y, R, Q, tol and optional
+    mu_a, A_a, max_oo, max_xo."""
     arr = (ProblemC * len(problems))()
     keep = []
     for i, p in enumerate(problems):
@@ -349,12 +376,7 @@ def info_esrf_analysis_batched(problems: Sequence[dict], options: Optional[Optio
         if A_a is None:
             A_a = torch.empty((N, n), dtype=torch.float64, device=X.device)
         keep.append((mu_a, A_a))
-        c = arr[i]
-        c.grid = make_grid(p["grid"])
-        c.N, c.d, c.Q, c.tol = N, p["obs_idx"].numel(), int(p["Q"]), float(p["tol"])
-        c.X, c.obs_idx, c.y, c.R_diag = X.data_ptr(), p["obs_idx"].data_ptr(), p["y"].data_ptr(), p["R"].data_ptr()
-        c.mu_a, c.A_a = mu_a.data_ptr(), A_a.data_ptr()
-        c.max_oo, c.max_xo = int(p.get("max_oo", 0)), int(p.get("max_xo", 0))
+        _fill_problem(arr[i], p, X, mu_a, A_a)
     o = options if options is not None else make_options()
     need = library().info_esrf_batched_workspace_size(arr, len(problems), ctypes.byref(o))
     if need == 0:
@@ -384,12 +406,7 @@ def autotune(problems: Sequence[dict], options: Options, ws: Optional[torch.Tens
         if A_a is None:
             A_a = torch.empty((N, n), dtype=torch.float64, device=X.device)
         keep.append((mu_a, A_a))
-        c = arr[i]
-        c.grid = make_grid(p["grid"])
-        c.N, c.d, c.Q, c.tol = N, p["obs_idx"].numel(), int(p["Q"]), float(p["tol"])
-        c.X, c.obs_idx, c.y, c.R_diag = X.data_ptr(), p["obs_idx"].data_ptr(), p["y"].data_ptr(), p["R"].data_ptr()
-        c.mu_a, c.A_a = mu_a.data_ptr(), A_a.data_ptr()
-        c.max_oo, c.max_xo = int(p.get("max_oo", 0)), int(p.get("max_xo", 0))
+        _fill_problem(arr[i], p, X, mu_a, A_a)
     need = library().info_esrf_batched_workspace_size(arr, len(problems), ctypes.byref(options))
     if ws is None or ws.numel() < need:
         ws = workspace(need)

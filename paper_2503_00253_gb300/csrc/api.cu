@@ -178,7 +178,9 @@ int build_table(const info_esrf_problem* probs, int32_t count, const info_esrf_o
     pr.Q = pr.do_pert ? P.Q : 0;
     if (pr.do_pert && P.Q < 1) return INFO_ESRF_ERR_INVALID_ARG;
     if (o.fixed_iters <= 0 && !(P.tol > 0.0)) return INFO_ESRF_ERR_INVALID_ARG;
-    if (!P.X || !P.obs_idx || !P.R_diag || (pr.do_mean && !P.y)) return INFO_ESRF_ERR_INVALID_ARG;
+    const bool general_h = P.H_rowptr != nullptr;
+    if (!P.X || (!P.obs_idx && !general_h) || !P.R_diag || (pr.do_mean && !P.y)) return INFO_ESRF_ERR_INVALID_ARG;
+    if (general_h && (!P.H_col || !P.H_val || P.H_nnz < 0)) return INFO_ESRF_ERR_INVALID_ARG;
     pr.tol = P.tol;
     pr.kR = (int32_t)std::min<int64_t>(o.ritz_rank, pr.d);
     pr.l = pr.kR > 0 ? (int32_t)std::min<int64_t>(std::min<int64_t>(pr.kR + o.oversample, kMaxRitz), pr.d) : 0;
@@ -192,13 +194,24 @@ int build_table(const info_esrf_problem* probs, int32_t count, const info_esrf_o
     pr.ell_fixed = o.ell;
     pr.seed = o.seed;
     pr.sqrt_nm1 = sqrt((double)(pr.N - 1));
-    const int64_t gb = geometric_bound(pr.grid, pr.d);
-    int64_t cap_oo = P.max_oo > 0 ? P.max_oo : (o.max_neighbors > 0 ? o.max_neighbors : gb);
-    int64_t cap_xo = P.max_xo > 0 ? P.max_xo : (o.max_neighbors > 0 ? o.max_neighbors : gb);
-    pr.max_oo = std::min(cap_oo, pr.d);
-    pr.max_xo = std::min(cap_xo, pr.d);
+    if (general_h) {
+      // dense covariances: every row of C and of Sxh holds all d columns
+      if (pr.n * pr.d > (int64_t(1) << 28)) return INFO_ESRF_ERR_UNSUPPORTED;
+      pr.max_oo = pr.d;
+      pr.max_xo = pr.d;
+    } else {
+      const int64_t gb = geometric_bound(pr.grid, pr.d);
+      int64_t cap_oo = P.max_oo > 0 ? P.max_oo : (o.max_neighbors > 0 ? o.max_neighbors : gb);
+      int64_t cap_xo = P.max_xo > 0 ? P.max_xo : (o.max_neighbors > 0 ? o.max_neighbors : gb);
+      pr.max_oo = std::min(cap_oo, pr.d);
+      pr.max_xo = std::min(cap_xo, pr.d);
+    }
     pr.X = P.X;
-    pr.obs = P.obs_idx;
+    pr.obs = general_h ? nullptr : P.obs_idx;
+    pr.H_rowptr = P.H_rowptr;
+    pr.H_col = general_h ? P.H_col : nullptr;
+    pr.H_val = general_h ? P.H_val : nullptr;
+    pr.H_nnz = general_h ? P.H_nnz : 0;
     pr.y = P.y;
     pr.R = P.R_diag;
     pr.mu_a = P.mu_a;

@@ -50,7 +50,11 @@ struct ProblemDev {
   int64_t max_oo, max_xo;      // ELL capacities (obs-obs, state-obs)
   // inputs (caller-owned, device)
   const double* X;      // [N][n]
-  const int64_t* obs;   // [d]
+  const int64_t* obs;   // [d] (subsampling; NULL with a general H)
+  const int64_t* H_rowptr;   // general observation operator (CSR, [d + 1]), or NULL
+  const int64_t* H_col;      // [H_nnz]
+  const double* H_val;       // [H_nnz]
+  int64_t H_nnz;
   const double* y;      // [d] (mean update only)
   const double* R;      // [d]
   // outputs (caller-owned, device)

@@ -971,7 +971,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
 // vectors, a one-dimensional grid); the kernel itself checks the band reach
 // and the shared-memory budget and otherwise sets the fall-back flag.
 bool band1d_eligible(const ProblemDev& p) {
-  if (p.precision != 1 || p.kR > kK || p.nsys < 1) return false;
+  if (p.precision != 1 || p.kR > kK || p.nsys < 1 || p.H_rowptr) return false;   // dense C: the general kernel
   int active = 0;
   for (int ax = 0; ax < 3; ++ax) active += p.grid.ext[ax] > 1;
   return active == 1 && p.grid.ext[0] > 1;

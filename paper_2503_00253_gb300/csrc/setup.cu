@@ -140,6 +140,7 @@ __global__ void __launch_bounds__(256) k_anomalies(const ProblemDev* tab) {
 template <typename T>
 __global__ void k_observe(const ProblemDev* tab) {
   const ProblemDev& pr = tab[blockIdx.y];
+  if (pr.H_rowptr) return;   // general observation operator: k_observe_H
   const int64_t N = pr.N;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= pr.d * N) return;
@@ -159,6 +160,139 @@ __global__ void k_observe(const ProblemDev* tab) {
   if (bad_r) atomicOr(&pr.status[0], kStatBadR);
 }
 
+// ---------------------------------------------------------------------------
+// General linear observation operator H (CSR, one row per observation; the
+// paper's weighted sums, Sec. 4.1 and Sec. 5.1).  With h linearized and
+// model-space localization (Sec. 2.3): W = H Z, Sxh = (L o Z Z^T) H^T,
+// Shh = H Sxh, so C = R^-1/2 H Sxh R^-1/2.  Both are dense ([n][d], [d][d])
+// and stored in the ELL layouts of the subsampling path with every column
+// present, so the later stages run unchanged.  Row pointers and columns are
+// checked before any entry is read.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool h_row(const ProblemDev& pr, int64_t a, int64_t& e0, int64_t& e1) {
+  e0 = pr.H_rowptr[a];
+  e1 = pr.H_rowptr[a + 1];
+  if (e0 < 0 || e1 < e0 || e1 > pr.H_nnz || (a == 0 && e0 != 0)) {
+    e0 = 0;
+    e1 = 0;
+    return false;
+  }
+  return true;
+}
+
+// W = H Z, one thread per (observation, member); the member-0 thread of each
+// observation also forms R^-1/2 and the mean right-hand side R^-1/2 (y - H mu).
+template <typename T>
+__global__ void k_observe_H(const ProblemDev* tab) {
+  const ProblemDev& pr = tab[blockIdx.y];
+  if (!pr.H_rowptr) return;
+  const int64_t N = pr.N;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= pr.d * N) return;
+  const int64_t a = i / N, k = i - a * N;
+  int64_t e0, e1;
+  bool bad = !h_row(pr, a, e0, e1);
+  const T* Zt = tp<const T>(pr.Zt);
+  double w = 0.0, hmu = 0.0;
+  for (int64_t e = e0; e < e1; ++e) {
+    const int64_t c = pr.H_col[e];
+    if (c < 0 || c >= pr.n) {
+      bad = true;
+      continue;
+    }
+    const double h = pr.H_val[e];
+    w += h * (double)Zt[c * N + k];
+    if (k == 0) hmu += h * pr.mu[c];
+  }
+  tp<T>(pr.W)[i] = to_t<T>(w);
+  if (k != 0) return;
+  const double r = pr.R[a];
+  const bool bad_r = !(r > 0.0) || !isfinite(r);
+  const double ri = bad_r ? 0.0 : 1.0 / sqrt(r);
+  pr.rinv[a] = ri;
+  if (pr.do_mean) pr.bmean[a] = ri * (pr.y[a] - hmu);
+  if (bad) atomicOr(&pr.status[0], kStatBadObs);
+  if (bad_r) atomicOr(&pr.status[0], kStatBadR);
+}
+
+// Sxh(x, b) = sum_j H(b, j) L(x, j) z_x . z_j, thread x (consecutive, so that
+// the ELL writes are coalesced) of observation column b = blockIdx.y.
+template <typename T>
+__global__ void k_sxh_H(const ProblemDev* tab) {
+  const ProblemDev& pr = tab[blockIdx.z];
+  if (!pr.H_rowptr) return;
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t b = blockIdx.y;
+  const int64_t n = pr.n, N = pr.N;
+  if (x >= n || b >= pr.d) return;
+  const GridDev& g = pr.grid;
+  const Coord3 px = flat_to_coord(g, x);
+  const T* Zt = tp<const T>(pr.Zt);
+  const T* zx = Zt + x * N;
+  int64_t e0, e1;
+  h_row(pr, b, e0, e1);
+  double acc = 0.0;
+  for (int64_t e = e0; e < e1; ++e) {
+    const int64_t c = pr.H_col[e];
+    if (c < 0 || c >= n) continue;
+    const double r2 = scaled_r2_tab(g, pr.d2tab, px, flat_to_coord(g, c));
+    if (!(r2 < 4.0)) continue;
+    DotAcc<T> dot;
+    const T* zc = Zt + c * N;
+    for (int64_t k = 0; k < N; ++k) dot.add_prod(zx[k], zc[k]);
+    const double gc = sizeof(T) == 8 ? gaspari_cohn(sqrt(r2)) : (double)gaspari_cohn_f(sqrtf((float)r2));
+    acc += pr.H_val[e] * gc * dot.value();
+  }
+  tp<T>(pr.xo_val)[b * n + x] = to_t<T>(acc);
+  pr.xo_col[b * n + x] = (int32_t)b;
+  if (b == 0) pr.xo_nnz[x] = (int32_t)pr.d;
+}
+
+// C(a, b) = R_a^-1/2 R_b^-1/2 sum_x H(a, x) Sxh(x, b), one warp per row a with
+// the lanes over b; the Gershgorin bound, the minimum and the sum of the
+// diagonal as in k_band.
+template <typename T>
+__global__ void k_c_H(const ProblemDev* tab) {
+  const ProblemDev& pr = tab[blockIdx.y];
+  if (!pr.H_rowptr) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t a = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t n = pr.n, d = pr.d;
+  if (a >= d) return;
+  int64_t e0, e1;
+  h_row(pr, a, e0, e1);
+  const T* S = tp<const T>(pr.xo_val);
+  const double ra = pr.rinv[a];
+  double rowsum = 0.0;
+  for (int64_t b = lane; b < d; b += 32) {
+    double acc = 0.0;
+    for (int64_t e = e0; e < e1; ++e) {
+      const int64_t c = pr.H_col[e];
+      if (c < 0 || c >= n) continue;
+      acc += pr.H_val[e] * (double)S[b * n + c];
+    }
+    const double v = ra * pr.rinv[b] * acc;
+    tp<T>(pr.oo_val)[b * d + a] = to_t<T>(v);
+    pr.oo_col[b * d + a] = (int32_t)b;
+    rowsum += fabs(v);
+    if (b == a) {
+      atomic_min_nonneg(&pr.scal[1], fmax(v, 0.0));
+      atomicAdd(&pr.scal[4], v);
+    }
+  }
+  rowsum = warp_sum(rowsum);
+  if (lane == 0) {
+    pr.oo_nnz[a] = (int32_t)d;
+    atomic_max_nonneg(&pr.scal[0], rowsum);
+  }
+}
+
+static bool any_general_h(const ProblemTable& tab) {
+  for (int i = 0; i < tab.count; ++i)
+    if (tab.p[i].H_rowptr) return true;
+  return false;
+}
+
 void launch_anomalies(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st) {
   int64_t nmax = 0, dnmax = 0;
   for (int i = 0; i < tab.count; ++i) {
@@ -171,9 +305,11 @@ void launch_anomalies(const ProblemTable& tab, const ProblemDev* dtab, cudaStrea
   if (f64) {
     k_anomalies<double><<<g1, 256, 0, st>>>(dtab); note_launches(1);
     k_observe<double><<<g2, 256, 0, st>>>(dtab); note_launches(1);
+    if (any_general_h(tab)) { k_observe_H<double><<<g2, 256, 0, st>>>(dtab); note_launches(1); }
   } else {
     k_anomalies<float><<<g1, 256, 0, st>>>(dtab); note_launches(1);
     k_observe<float><<<g2, 256, 0, st>>>(dtab); note_launches(1);
+    if (any_general_h(tab)) { k_observe_H<float><<<g2, 256, 0, st>>>(dtab); note_launches(1); }
   }
 }
 
@@ -188,6 +324,7 @@ void launch_anomalies(const ProblemTable& tab, const ProblemDev* dtab, cudaStrea
 template <typename T, bool OBS_ROWS>
 __global__ void k_band(const ProblemDev* tab) {
   const ProblemDev& pr = tab[blockIdx.y];
+  if (pr.H_rowptr) return;   // general observation operator: k_sxh_H and k_c_H
   const int lane = threadIdx.x & 31;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t rows = OBS_ROWS ? pr.d : pr.n;
@@ -279,6 +416,25 @@ void launch_band_obs(const ProblemTable& tab, const ProblemDev* dtab, cudaStream
   if (tab.p[0].precision == 0) k_band<double, true><<<go, 256, 0, st>>>(dtab);
   else k_band<float, true><<<go, 256, 0, st>>>(dtab);
   note_launches(1);
+  if (any_general_h(tab)) {
+    // dense Sxh first (C is formed from it), then C
+    int64_t nmax = 0, dh = 0;
+    for (int i = 0; i < tab.count; ++i)
+      if (tab.p[i].H_rowptr) {
+        nmax = std::max<int64_t>(nmax, tab.p[i].n);
+        dh = std::max<int64_t>(dh, tab.p[i].d);
+      }
+    const dim3 gs((unsigned)((nmax + 127) / 128), (unsigned)dh, tab.count);
+    const dim3 gc((unsigned)((dh * 32 + 255) / 256), tab.count);
+    if (tab.p[0].precision == 0) {
+      k_sxh_H<double><<<gs, 128, 0, st>>>(dtab);
+      k_c_H<double><<<gc, 256, 0, st>>>(dtab);
+    } else {
+      k_sxh_H<float><<<gs, 128, 0, st>>>(dtab);
+      k_c_H<float><<<gc, 256, 0, st>>>(dtab);
+    }
+    note_launches(2);
+  }
 }
 
 // Band of Sxh (state rows); needed only by the state update.

@@ -566,3 +566,100 @@ def test_autotune_picks_a_converging_setting_and_keeps_parity(B):
     assert st["status"] == 0 and st["n_unconverged"] == 0
     ea, em = errors(pr, mu_a.cpu().numpy(), A_a.cpu().numpy())
     assert ea <= 1e-4 and em <= 1e-4
+
+
+# ---------------------------------------------------------------------------
+# General linear observation operators (the paper's weighted sums)
+# ---------------------------------------------------------------------------
+
+def _h_dict(pr, H, y, R, tol):
+    _, (rowptr, col, val) = H
+    return dict(grid=pr.grid, X=dev(pr.X), H=(dev(rowptr), dev(col), dev(val)), y=dev(y), R=dev(R), Q=pr.Q,
+                tol=tol)
+
+
+def _h_errors(pr, Hd, y, R, mu_a, A_a):
+    A_ref = F.perturbation_update_H(pr.X, Hd, R, pr.grid, pr.Q)
+    mu_ref = F.mean_update_H(pr.X, Hd, y, R, pr.grid)
+    Af = pr.X - pr.X.mean(0)
+    ea = F.relative_increment_error(A_a, A_ref, Af)
+    em = float(np.linalg.norm(mu_a - mu_ref) / np.linalg.norm(mu_ref - pr.X.mean(0)))
+    return ea, em
+
+
+@pytest.mark.parametrize("precision,tol,bound", [(0, 1e-12, 1e-10), (1, 1e-6, 1e-4)])
+def test_general_H_gaussian_channels_parity(B, precision, tol, bound):
+    """The single-cycle experiment's operator shape (Sec. 4.1): n = 2000 on a circle,
+    d = 100 Gaussian-weighted channel sums of bandwidth 10, N = 20."""
+    pr = workloads.gaussian_problem_1d("chan", n=2000, N=20, length_scale=10.0, obs_stride=20, r2=0.5,
+                                       half_width=20.0, Q=16, tol=tol, seed=91)
+    H = workloads.gaussian_channel_operator(pr.n, 100, 10.0)
+    rng = np.random.default_rng(92)
+    R = np.full(100, 0.5)
+    y = H[0] @ pr.truth + np.sqrt(R) * rng.standard_normal(100)
+    outs, stats = B.info_esrf_analysis_batched([_h_dict(pr, H, y, R, tol)], B.make_options(precision=precision))
+    torch.cuda.synchronize()
+    (mu_a, A_a), st = outs[0], stats[0]
+    assert st["status"] == 0 and st["solver_path"] == 0, st
+    ea, em = _h_errors(pr, H[0], y, R, mu_a.cpu().numpy(), A_a.cpu().numpy())
+    assert ea <= bound and em <= bound, (ea, em)
+
+
+@pytest.mark.parametrize("precision,tol,bound", [(0, 1e-12, 1e-10), (1, 1e-6, 1e-4)])
+def test_general_H_column_sums_layered_parity(B, precision, tol, bound):
+    """The layered experiment's operator shape (Sec. 5.1): 8 observed columns of a
+    40 x 32 grid, 5 weighted vertical sums each, isotropic localization length 3."""
+    grid = workloads.Grid((40, 1, 32), (True, False, False), (3.0, 1.0, 3.0))
+    base = workloads.random_obs_problem(grid, N=24, d=10, r2=0.25, Q=8, tol=tol, seed=93)
+    H = workloads.column_sum_operator((40, 1, 32), list(range(0, 40, 5)), 5, 6.0, 8.0)
+    rng = np.random.default_rng(94)
+    R = np.full(40, 0.25)
+    y = H[0] @ base.truth + np.sqrt(R) * rng.standard_normal(40)
+    outs, stats = B.info_esrf_analysis_batched([_h_dict(base, H, y, R, tol)], B.make_options(precision=precision))
+    torch.cuda.synchronize()
+    (mu_a, A_a), st = outs[0], stats[0]
+    assert st["status"] == 0, st
+    ea, em = _h_errors(base, H[0], y, R, mu_a.cpu().numpy(), A_a.cpu().numpy())
+    assert ea <= bound and em <= bound, (ea, em)
+
+
+def test_batch_mixes_index_and_general_H_problems(B):
+    """An index-observed problem and a weighted-sum problem in one batched call:
+    each meets the FP64 bound and equals its own single-problem call bit for bit."""
+    p1 = workloads.gaussian_problem_1d("idx", n=600, N=12, length_scale=6.0, obs_stride=4, r2=0.4,
+                                       half_width=10.0, Q=6, tol=1e-12, seed=95)
+    p2 = workloads.gaussian_problem_1d("chan2", n=800, N=10, length_scale=8.0, obs_stride=16, r2=0.5,
+                                       half_width=16.0, Q=8, tol=1e-12, seed=96)
+    H = workloads.gaussian_channel_operator(p2.n, 40, 6.0)
+    y2 = H[0] @ p2.truth + 0.3 * np.random.default_rng(97).standard_normal(40)
+    R2 = np.full(40, 0.4)
+    d1 = dict(grid=p1.grid, X=dev(p1.X), obs_idx=dev(p1.obs_idx), y=dev(p1.y), R=dev(p1.R), Q=p1.Q, tol=1e-12)
+    d2 = _h_dict(p2, H, y2, R2, 1e-12)
+    opts = B.make_options(precision=0)
+    outs, stats = B.info_esrf_analysis_batched([d1, d2], opts)
+    torch.cuda.synchronize()
+    assert all(s["status"] == 0 for s in stats), stats
+    ea, em = errors(p1, outs[0][0].cpu().numpy(), outs[0][1].cpu().numpy())
+    assert ea <= 1e-10 and em <= 1e-10, (ea, em)
+    ea, em = _h_errors(p2, H[0], y2, R2, outs[1][0].cpu().numpy(), outs[1][1].cpu().numpy())
+    assert ea <= 1e-10 and em <= 1e-10, (ea, em)
+    for dd, (mu_b, A_b) in ((d1, outs[0]), (d2, outs[1])):
+        single, _ = B.info_esrf_analysis_batched([dd], opts)
+        torch.cuda.synchronize()
+        assert torch.equal(single[0][0], mu_b) and torch.equal(single[0][1], A_b)
+
+
+def test_general_H_malformed_is_rejected(B):
+    """A column index outside the state makes the call fail with the bad-observation
+    code; nothing outside the arrays is read."""
+    pr = workloads.gaussian_problem_1d("badH", n=300, N=8, length_scale=5.0, obs_stride=10, r2=0.5,
+                                       half_width=8.0, Q=4, tol=1e-10, seed=98)
+    Hd, (rowptr, col, val) = workloads.gaussian_channel_operator(pr.n, 12, 4.0)
+    col = col.copy()
+    col[5] = pr.n + 7
+    y = Hd @ pr.truth
+    R = np.full(12, 0.5)
+    d = dict(grid=pr.grid, X=dev(pr.X), H=(dev(rowptr), dev(col), dev(val)), y=dev(y), R=dev(R), Q=pr.Q, tol=1e-10)
+    with pytest.raises(B.InfoEsrfError) as ei:
+        B.info_esrf_analysis_batched([d], B.make_options(precision=0))
+    assert ei.value.code == B.ERR_BAD_OBS_INDEX
