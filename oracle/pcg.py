@@ -12,6 +12,16 @@ eigendecomposition (Halko, Martinsson, Tropp Alg. 5.3) of C, computed once
 and shifted to every q: Phi_q = Phi, theta_q = theta(C) + s_q + 1.
 beta_q = min_a C_q(a, a) = s_q + 1 + min_a C(a, a).
 
+Multi-shift CG (Sec. 3.3, first alternative to per-system PCG; shift
+invariance of Krylov subspaces): in normalized form every C_q is the same C
+shifted by sigma_q = s_q + 1, so K_k(C + sigma I, b) does not depend on sigma.
+One CG run on the base system (C + sigma_0 I) u = b, sigma_0 = min_q sigma_q,
+yields every shifted iterate: the shifted residuals stay collinear with the
+base residual, r_k^(q) = zeta_k^(q) r_k, and zeta, alpha^(q), beta^(q) follow
+from matching the three-term residual recurrences of CG for the two systems
+(Frommer & Glassner 1998; Jegerlehner 1996).  It runs without a
+preconditioner, as the paper notes.
+
 Readings (the paper does not fix them): Gaussian test matrix with
 ``oversample`` = 10 extra columns and ``power_iters`` = 1 power iteration
 on the range finder; x0 = 0; stop when ||r||_2 <= tol ||b||_2 or after
@@ -113,4 +123,85 @@ def solve_normalized(C, s, p, W, R, k=10, Omega=None, tol=1e-12, max_iter=1000,
             u, it = pcg(A_mv, B[:, i], Minv, tol, max_iter, fixed_iters)
             ubar[:, i] += pq * u
             iters[qi, i] = it
+    return rih[:, None] * ubar, iters
+
+
+def multishift_cg(A_mv, b, shifts, tol=1e-12, max_iter=1000, fixed_iters=None):
+    """Solves (A + shifts[q] I) x_q = b for every q from one CG run (Sec. 3.3).
+
+    The base system is A + sigma_0 I with sigma_0 = min(shifts); shift q is
+    sigma_0 + delta_q.  With beta_{-1} = 0, alpha_{-1} = 1 and
+    zeta_{-1} = zeta_0 = 1, iteration k of base CG (alpha_k, beta_k) gives
+
+        zeta_{k+1} = zeta_k zeta_{k-1} alpha_{k-1} /
+                     (alpha_k beta_{k-1} (zeta_{k-1} - zeta_k) + zeta_{k-1} alpha_{k-1} (1 + delta alpha_k)),
+        alpha_k^(q) = alpha_k zeta_{k+1} / zeta_k,   beta_k^(q) = beta_k (zeta_{k+1} / zeta_k)^2,
+        x^(q) += alpha_k^(q) p^(q),   p^(q) <- zeta_{k+1} r_{k+1} + beta_k^(q) p^(q).
+
+    Shift q stops being updated once its residual |zeta^(q)| ||r|| is at most
+    tol ||b|| (with fixed_iters: 1e-30 ||b||, so that zeta never underflows);
+    the run ends when every shift has stopped, at max_iter, or after
+    fixed_iters iterations.  Returns (X [Q][d], iters [Q], relres [Q]).
+    """
+    shifts = np.asarray(shifts, dtype=np.float64)
+    nq = shifts.shape[0]
+    d = b.shape[0]
+    X = np.zeros((nq, d))
+    iters = np.zeros(nq, dtype=np.int64)
+    relres = np.zeros(nq)
+    bnorm = float(np.linalg.norm(b))
+    if bnorm == 0.0 or nq == 0:
+        return X, iters, relres
+    sigma0 = float(shifts.min())
+    delta = shifts - sigma0
+    stop = (1e-30 if fixed_iters is not None else tol) * bnorm
+    limit = fixed_iters if fixed_iters is not None else max_iter
+    r = b.copy()
+    p = b.copy()
+    rr = float(r @ r)
+    P = np.tile(b, (nq, 1))
+    zeta = np.ones(nq)
+    zeta_prev = np.ones(nq)
+    alpha_prev, beta_prev = 1.0, 0.0
+    active = np.full(nq, True)
+    relres[:] = 1.0
+    k = 0
+    while k < limit and active.any():
+        Ap = A_mv(p) + sigma0 * p
+        alpha = rr / float(p @ Ap)
+        r = r - alpha * Ap
+        rr_new = float(r @ r)
+        beta = rr_new / rr
+        for q in np.nonzero(active)[0]:
+            z0, zm = zeta[q], zeta_prev[q]
+            z1 = z0 * zm * alpha_prev / (alpha * beta_prev * (zm - z0) + zm * alpha_prev * (1.0 + delta[q] * alpha))
+            ratio = z1 / z0
+            X[q] += alpha * ratio * P[q]
+            P[q] = z1 * r + beta * ratio * ratio * P[q]
+            zeta_prev[q], zeta[q] = z0, z1
+            iters[q] = k + 1
+            relres[q] = abs(z1) * np.sqrt(rr_new) / bnorm
+            if abs(z1) * np.sqrt(rr_new) <= stop:
+                active[q] = False
+        p = r + beta * p
+        rr = rr_new
+        alpha_prev, beta_prev = alpha, beta
+        k += 1
+    return X, iters, relres
+
+
+def solve_normalized_multishift(C, s, p, W, R, tol=1e-12, max_iter=1000, fixed_iters=None):
+    """vbar^(i) = R^-1/2 sum_q p_q u_q^(i) with all Q shifts of member i solved
+    by one multi-shift CG run on C (no preconditioner).  Returns (vbar [d][N],
+    iterations [Q][N])."""
+    d, N = W.shape
+    rih = 1.0 / np.sqrt(np.asarray(R, dtype=np.float64))
+    B = rih[:, None] * W
+    shifts = np.asarray(s, dtype=np.float64) + 1.0
+    ubar = np.zeros_like(W)
+    iters = np.zeros((len(s), N), dtype=np.int64)
+    for i in range(N):
+        U, it, _ = multishift_cg(lambda v: C @ v, B[:, i], shifts, tol, max_iter, fixed_iters)
+        ubar[:, i] = np.asarray(p) @ U
+        iters[:, i] = it
     return rih[:, None] * ubar, iters

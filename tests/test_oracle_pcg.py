@@ -85,3 +85,86 @@ def test_pcg_lmp_same_answer_fewer_iterations():
     for v in (v0, v1):
         assert np.max(np.abs(v - ref)) < 1e-9 * np.max(np.abs(ref))
     assert it1.sum() < it0.sum()
+
+
+# ---------------------------------------------------------------------------
+# Multi-shift CG (Sec. 3.3, shift invariance of Krylov subspaces)
+# ---------------------------------------------------------------------------
+
+def _krylov_galerkin(A, b, sigma, k):
+    """Definition of the k-th CG iterate for A + sigma I: the Galerkin
+    projection onto K_k(A, b) = span{b, A b, ..., A^(k-1) b} (the space does
+    not depend on sigma), from an orthonormal basis built column by column."""
+    V = np.zeros((b.shape[0], k))
+    v = b / np.linalg.norm(b)
+    for j in range(k):
+        for _ in range(2):                       # Gram-Schmidt twice
+            v = v - V[:, :j] @ (V[:, :j].T @ v)
+        V[:, j] = v / np.linalg.norm(v)
+        v = A @ V[:, j]
+    M = V.T @ (A + sigma * np.eye(A.shape[0])) @ V
+    return V @ np.linalg.solve(M, V.T @ b)
+
+
+def test_multishift_iterates_are_galerkin_projections():
+    """After k iterations every shifted iterate is the CG (Galerkin) iterate of
+    its own system in K_k: this fixes zeta, alpha^(q) and beta^(q) at every step."""
+    rng = np.random.default_rng(3)
+    d = 14
+    Qm, _ = np.linalg.qr(rng.standard_normal((d, d)))
+    lam = np.geomspace(0.02, 30.0, d)
+    A = (Qm * lam) @ Qm.T
+    b = rng.standard_normal(d)
+    shifts = np.array([0.7, 0.9, 2.5, 40.0, 900.0])
+    for k in range(1, 9):
+        X, it, _ = pcg.multishift_cg(lambda v: A @ v, b, shifts, fixed_iters=k)
+        for q, sg in enumerate(shifts):
+            ref = _krylov_galerkin(A, b, sg, k)
+            assert np.linalg.norm(X[q] - ref) <= 1e-9 * np.linalg.norm(ref), (k, q)
+        assert np.all(it[:3] == k)
+
+
+def test_multishift_base_shift_is_plain_cg():
+    """With one shift, the run is textbook CG on A + sigma I (Golub & Van Loan
+    Alg. 11.5.1 without preconditioner), iterate for iterate."""
+    pr, W, C = _C(seed=4)
+    b = W[:, 1] / np.sqrt(pr.R)
+    for k in (1, 3, 7):
+        X, it, _ = pcg.multishift_cg(lambda v: C @ v, b, [1.7], fixed_iters=k)
+        x, kk = pcg.pcg(lambda v: 1.7 * v + C @ v, b, lambda r: r, fixed_iters=k)
+        assert kk == k and it[0] == k
+        assert np.linalg.norm(X[0] - x) <= 1e-13 * np.linalg.norm(x)
+
+
+def test_multishift_converges_to_dense_solves_for_every_shift():
+    """Each shifted solution meets its tolerance against a dense solve, including
+    the shifts that stopped early; larger shifts need fewer iterations."""
+    pr, W, C = _C(seed=5)
+    d = C.shape[0]
+    s, _ = quadrature.elliptic_rule(16, 100.0)
+    shifts = s + 1.0
+    b = W[:, 2] / np.sqrt(pr.R)
+    X, it, rel = pcg.multishift_cg(lambda v: C @ v, b, shifts, tol=1e-12)
+    for q, sg in enumerate(shifts):
+        A = C + sg * np.eye(d)
+        assert np.linalg.norm(b - A @ X[q]) <= 5e-12 * np.linalg.norm(b), q
+        assert rel[q] <= 1e-12
+    assert np.all(np.diff(it) <= 0) and it[-1] < it[0]
+
+
+def test_multishift_quadrature_sum_matches_exact_perturbation_solves():
+    """vbar from one multi-shift run per member equals the same-node result of
+    Sec. 3.2 (exact solves) to the CG tolerance."""
+    pr, W, C = _C(seed=6)
+    s, p = quadrature.elliptic_rule(12, quadrature.ell_rule(C))
+    mu, Z = F.anomalies(pr.X)
+    _, _, Shh = F.localized_covariances(Z, pr.obs_idx, pr.grid)
+    ref = F.perturbation_solves(Shh, W, pr.R, s, p)
+    vbar, iters = pcg.solve_normalized_multishift(C, s, p, W, pr.R, tol=1e-13)
+    assert np.linalg.norm(vbar - ref) <= 1e-10 * np.linalg.norm(ref)
+    assert iters.shape == (12, W.shape[1]) and iters.max() < C.shape[0]
+
+
+def test_multishift_zero_rhs():
+    X, it, rel = pcg.multishift_cg(lambda v: v, np.zeros(5), [1.0, 2.0], tol=1e-10)
+    assert not X.any() and not it.any() and not rel.any()
