@@ -309,18 +309,21 @@ def run_ours(args):
     # comparators on the same GPU: the paper's preconditioner alone, in FP32 and in FP64
     comparators = {}
     if rank == 0 and prec == B.PRECISION_FP32 and args.fp64_steps > 0:
-        cases = [("fp64_pcg", B.PRECISION_FP64)]
+        cases = [("fp64_pcg", B.PRECISION_FP64, B.SOLVER_PCG)]
         if use_learned:
-            cases.insert(0, ("lmp_fp32", B.PRECISION_FP32))
-        for key, pc in cases:
-            oc = B.make_options(precision=pc, ritz_rank=RITZ, max_neighbors=cap)
+            cases.insert(0, ("lmp_fp32", B.PRECISION_FP32, B.SOLVER_PCG))
+        # one unpreconditioned CG run per member for all shifts (Sec. 3.3)
+        cases.insert(0, ("multishift_fp32", B.PRECISION_FP32, B.SOLVER_MULTISHIFT))
+        for key, pc, sv in cases:
+            oc = B.make_options(precision=pc, ritz_rank=RITZ, max_neighbors=cap, solver=sv)
             needc = B.library().info_esrf_workspace_size(ctypes.byref(g), N, d, pr.Q, ctypes.byref(oc))
             wc = B.workspace(needc, dev)
             muc = torch.empty_like(mu_a)
             Ac = torch.empty_like(A_a)
             stc = B.info_esrf_analysis(pr.grid, X, obs, y, R, pr.Q, TOL_MIXED, oc, ws=wc, mu_a=muc, A_a=Ac,
                                        stats=True, stream=stream)[2]
-            ts = []
+            ts, phc = [], []
+            B.set_phase_events(oc, events)
             for s in range(args.fp64_steps):
                 flush.fill_(float(s))
                 e0.record(stream)
@@ -329,9 +332,13 @@ def run_ours(args):
                 e1.record(stream)
                 e1.synchronize()
                 ts.append(e0.elapsed_time(e1))
+                phc.append([events[i].elapsed_time(events[i + 1]) for i in range(4)])
+            B.set_phase_events(oc, None)
             comparators[key] = {"value": 1e3 / statistics.mean(ts), "unit": UNIT, "tol": TOL_MIXED,
                                 "steps": args.fp64_steps, "iters_mean": stc["iters_mean"],
-                                "iters_max": stc["iters_max"], "ms_per_step": statistics.mean(ts)}
+                                "iters_max": stc["iters_max"], "ms_per_step": statistics.mean(ts),
+                                "phases_ms": [statistics.mean(p[i] for p in phc) for i in range(4)],
+                                "launch": "direct call"}
             if "rel_err" in result:
                 from oracle import filter as F
                 mu_ref, A_ref = ref_cache

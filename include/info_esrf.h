@@ -64,6 +64,9 @@ extern "C" {
 #define INFO_ESRF_RULE_ELLIPTIC 0          /* App. D, Eq. elliptic_quadrature_rule */
 #define INFO_ESRF_RULE_GAUSS_LEGENDRE 1    /* App. D, Eq. gaussian_quadrature_rule */
 
+#define INFO_ESRF_SOLVER_PCG 0             /* one PCG run per (node, member) system (Sec. 3.3, App. E) */
+#define INFO_ESRF_SOLVER_MULTISHIFT 1      /* one CG run per member for all Q shifts (Sec. 3.3, item 1) */
+
 /* Regular grid.  Flat index = (z * shape[1] + y) * shape[0] + x.  Axes of
  * extent 1 are ignored.  The Gaspari-Cohn argument is
  * r = sqrt(sum_axes (dist_axis / half_width[axis])^2), L = GC(r), zero for
@@ -112,6 +115,21 @@ typedef struct {
    * bands, quadrature); after the Ritz pairs (a4); after the persistent PCG
    * (a5-a8); after the accumulation and state update (a9-a11). */
   void* const* phase_events;
+  /* INFO_ESRF_SOLVER_*; default PCG.  MULTISHIFT solves all Q shifted systems
+   * of a member with one unpreconditioned CG run on C + sigma_0 I, sigma_0 the
+   * smallest shift, using the shift invariance of Krylov subspaces (Sec. 3.3,
+   * first alternative; the systems are exact shifts of C in normalized form,
+   * App. E).  The mean system is a chain with the single shift 1.  Each shift
+   * stops at ||r_q|| <= tol ||b||; max_iter and fixed_iters count iterations
+   * of the run.  ritz_rank, oversample, power_iters and learned_model are then
+   * not used (no Ritz stage), and cluster_size 2, 4 or 8 sets the CTAs per
+   * cluster of the multi-shift kernel (0 or -1: chosen from d).  Every CTA
+   * keeps a full copy of each chain's direction next to its own rows, so one
+   * chain needs about 1.5 d elements of shared memory per CTA (8 CTAs per
+   * cluster): d above about 35,000 (FP32) or 18,000 (FP64) returns
+   * INFO_ESRF_ERR_UNSUPPORTED. */
+  int32_t solver;
+  int32_t reserved_;
 } info_esrf_options;
 
 typedef struct {
@@ -121,7 +139,8 @@ typedef struct {
   int32_t n_systems;      /* systems solved (Q * N perturbation + mean) */
   double iters_mean;
   int32_t n_unconverged;
-  int32_t solver_path;    /* 1: cluster-resident band kernel (1-D networks), 0: general kernel */
+  int32_t solver_path;    /* 1: cluster-resident band kernel (1-D networks), 0: general kernel,
+                             2: multi-shift CG */
   double max_rel_resid;   /* max recurrence ||r|| / ||b|| at exit */
   double ell_used;
   double gershgorin;      /* max_a sum_b |C(a, b)| */

@@ -35,6 +35,8 @@ PRECISION_FP64 = 0
 PRECISION_FP32 = 1
 RULE_ELLIPTIC = 0
 RULE_GAUSS_LEGENDRE = 1
+SOLVER_PCG = 0
+SOLVER_MULTISHIFT = 1
 
 ITEM = dict(scalars=0, status=1, quad_s=2, quad_p=3, theta=4, phi=5, cphi=6, oo_val=7, oo_col=8,
             oo_nnz=9, xo_val=10, xo_col=11, xo_nnz=12, W=13, mu=14)
@@ -50,7 +52,8 @@ class Options(ctypes.Structure):
                 ("power_iters", c_int32), ("max_iter", c_int32), ("fixed_iters", c_int32),
                 ("rule", c_int32), ("cluster_size", c_int32), ("ell", c_double), ("seed", c_uint64),
                 ("max_neighbors", c_int64), ("learned_model", c_void_p), ("learned_max_shift", c_double),
-                ("system_iters", c_void_p), ("phase_events", ctypes.POINTER(c_void_p))]
+                ("system_iters", c_void_p), ("phase_events", ctypes.POINTER(c_void_p)),
+                ("solver", c_int32), ("reserved_", c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -188,13 +191,14 @@ def make_options(precision: int = PRECISION_FP64, ritz_rank: int = 10, oversampl
                  rule: int = RULE_ELLIPTIC, ell: float = 0.0, seed: int = 0x1234ABCD,
                  max_neighbors: int = 0, learned_model: Optional[torch.Tensor] = None,
                  learned_max_shift: float = 0.0, system_iters: Optional[torch.Tensor] = None,
-                 cluster_size: int = 0) -> Options:
+                 cluster_size: int = 0, solver: int = SOLVER_PCG) -> Options:
     o = Options()
     library().info_esrf_default_options(ctypes.byref(o))
     o.precision, o.ritz_rank, o.oversample, o.power_iters = precision, ritz_rank, oversample, power_iters
     o.max_iter, o.fixed_iters, o.rule, o.ell, o.seed = max_iter, fixed_iters, rule, ell, seed
     o.max_neighbors = max_neighbors
     o.cluster_size = cluster_size
+    o.solver = solver
     if system_iters is not None:
         _need(system_iters, torch.int32, "system_iters")
         o.system_iters = system_iters.data_ptr()

@@ -106,6 +106,8 @@ int check_options(const info_esrf_options* in, info_esrf_options* out) {
   if (out->cluster_size != 0 && out->cluster_size != -1 && out->cluster_size != 2 && out->cluster_size != 4 &&
       out->cluster_size != 8)
     return INFO_ESRF_ERR_INVALID_ARG;
+  if (out->solver != INFO_ESRF_SOLVER_PCG && out->solver != INFO_ESRF_SOLVER_MULTISHIFT)
+    return INFO_ESRF_ERR_INVALID_ARG;
   return 0;
 }
 
@@ -229,8 +231,13 @@ int build_table(const info_esrf_problem* probs, int32_t count, const info_esrf_o
   }
   tab.total_groups = group_base;
   tab.total_sys = sys_base;
-  const size_t sb = pcg_scratch_bytes(tab, num_sms);
+  tab.solver = o.solver;
+  const size_t sb = o.solver == INFO_ESRF_SOLVER_PCG ? pcg_scratch_bytes(tab, num_sms) : 0;
   void* scratch = cv.take<void>(sb);
+  if (o.solver == INFO_ESRF_SOLVER_MULTISHIFT) {
+    if (mscg_plan(tab, num_sms, o.cluster_size, &tab.ms) != 0) return INFO_ESRF_ERR_UNSUPPORTED;
+    tab.ms_scratch = tab.ms.scratch_bytes ? cv.take<void>(tab.ms.scratch_bytes) : nullptr;
+  }
   *bytes_out = cv.off;
   if (dtab_out) *dtab_out = dtab;
   if (counter_out) *counter_out = counter;
@@ -312,34 +319,58 @@ int run_batch(const info_esrf_problem* probs, int32_t count, const info_esrf_opt
   launch_prepare(tab, dtab, st);
   launch_anomalies(tab, dtab, st);
   launch_band_obs(tab, dtab, st);
-  // the quadrature and the state-obs band overlap the Ritz stage on a side
-  // stream, which rejoins before the first use of each
-  AuxStream* aux = aux_stream();
-  // the learned coefficients need only the quadrature and the band's scalars
-  if (aux) {
-    cudaEventRecord(aux->mid, st);
-    cudaStreamWaitEvent(aux->s, aux->mid, 0);
-    launch_quadrature(tab, dtab, aux->s);
-    launch_learn_coef(tab, dtab, aux->s);
-    cudaEventRecord(aux->jq, aux->s);
-    launch_band_state(tab, dtab, aux->s);
-    cudaEventRecord(aux->jb, aux->s);
-  } else {
+  if (o.solver == INFO_ESRF_SOLVER_MULTISHIFT) {
+    // no Ritz stage and no learned coefficients: the quadrature and the
+    // state-obs band run on the side stream while nothing else waits
+    AuxStream* aux = aux_stream();
+    if (aux) {
+      cudaEventRecord(aux->mid, st);
+      cudaStreamWaitEvent(aux->s, aux->mid, 0);
+      launch_band_state(tab, dtab, aux->s);
+      cudaEventRecord(aux->jb, aux->s);
+    } else {
+      launch_band_state(tab, dtab, st);
+    }
     launch_quadrature(tab, dtab, st);
-    launch_learn_coef(tab, dtab, st);
-    launch_band_state(tab, dtab, st);
-  }
-  mark(1);
-  launch_ritz(tab, dtab, st);
-  if (aux) cudaStreamWaitEvent(st, aux->jq, 0);
-  mark(2);
-  if (launch_pcg(tab, dtab, counter, scratch, scratch_bytes, sms, st) != 0) {
+    mark(1);
+    mark(2);
+    if (launch_mscg(tab, dtab, tab.ms, sms, st) != 0) {
+      if (aux) cudaStreamWaitEvent(st, aux->jb, 0);
+      return INFO_ESRF_ERR_CUDA;
+    }
+    mark(3);
     if (aux) cudaStreamWaitEvent(st, aux->jb, 0);
-    return INFO_ESRF_ERR_WORKSPACE;
+    launch_finish(tab, dtab, st, false);
+  } else {
+    // the quadrature and the state-obs band overlap the Ritz stage on a side
+    // stream, which rejoins before the first use of each
+    AuxStream* aux = aux_stream();
+    // the learned coefficients need only the quadrature and the band's scalars
+    if (aux) {
+      cudaEventRecord(aux->mid, st);
+      cudaStreamWaitEvent(aux->s, aux->mid, 0);
+      launch_quadrature(tab, dtab, aux->s);
+      launch_learn_coef(tab, dtab, aux->s);
+      cudaEventRecord(aux->jq, aux->s);
+      launch_band_state(tab, dtab, aux->s);
+      cudaEventRecord(aux->jb, aux->s);
+    } else {
+      launch_quadrature(tab, dtab, st);
+      launch_learn_coef(tab, dtab, st);
+      launch_band_state(tab, dtab, st);
+    }
+    mark(1);
+    launch_ritz(tab, dtab, st);
+    if (aux) cudaStreamWaitEvent(st, aux->jq, 0);
+    mark(2);
+    if (launch_pcg(tab, dtab, counter, scratch, scratch_bytes, sms, st) != 0) {
+      if (aux) cudaStreamWaitEvent(st, aux->jb, 0);
+      return INFO_ESRF_ERR_WORKSPACE;
+    }
+    mark(3);
+    if (aux) cudaStreamWaitEvent(st, aux->jb, 0);
+    launch_finish(tab, dtab, st);
   }
-  mark(3);
-  if (aux) cudaStreamWaitEvent(st, aux->jb, 0);
-  launch_finish(tab, dtab, st);
   if (o.system_iters && count == 1)
     cudaMemcpyAsync(o.system_iters, tab.p[0].iters, (size_t)tab.p[0].nsys * sizeof(int32_t),
                     cudaMemcpyDeviceToDevice, st);
@@ -374,7 +405,7 @@ int run_batch(const info_esrf_problem* probs, int32_t count, const info_esrf_opt
       if (o.fixed_iters <= 0 && !(rr[sidx] <= pr.tol)) ++unconv;
     }
     s.device_flags = status[0];
-    s.solver_path = status[1] & 1;
+    s.solver_path = (status[1] & 2) ? 2 : (status[1] & 1);
     s.iters_max = it_max;
     s.n_systems = (int32_t)live;
     s.iters_mean = live ? (double)sum_it / (double)live : 0.0;

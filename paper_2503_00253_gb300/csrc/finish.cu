@@ -79,7 +79,7 @@ __global__ void k_state_apply(const ProblemDev* tab) {
   }
 }
 
-void launch_finish(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st) {
+void launch_finish(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st, bool accumulate) {
   int64_t dn1 = 0, nmax = 0, Nmax = 0;
   for (int i = 0; i < tab.count; ++i) {
     const ProblemDev& p = tab.p[i];
@@ -90,10 +90,10 @@ void launch_finish(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t
   const dim3 ga((unsigned)((dn1 + 255) / 256), tab.count);
   const dim3 gs((unsigned)((nmax + 127) / 128), (unsigned)((Nmax + kStateCols) / kStateCols), tab.count);
   if (tab.p[0].precision == 0) {
-    k_accumulate<double><<<ga, 256, 0, st>>>(dtab); note_launches(1);
+    if (accumulate) { k_accumulate<double><<<ga, 256, 0, st>>>(dtab); note_launches(1); }
     k_state_apply<double><<<gs, 128, 0, st>>>(dtab); note_launches(1);
   } else {
-    k_accumulate<float><<<ga, 256, 0, st>>>(dtab); note_launches(1);
+    if (accumulate) { k_accumulate<float><<<ga, 256, 0, st>>>(dtab); note_launches(1); }
     k_state_apply<float><<<gs, 128, 0, st>>>(dtab); note_launches(1);
   }
 }

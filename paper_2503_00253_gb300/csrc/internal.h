@@ -106,12 +106,30 @@ struct ProblemDev {
   void* VbarT;          // [d][N + 1] T copy for the state apply
 };
 
+// Launch plan of the multi-shift CG kernel (host side): CTAs per cluster,
+// observation rows per CTA (a multiple of 4), length of each full copy of p,
+// shift slots per chain (a multiple of 4), band slots of C per row, element
+// size, and for every chain-group size LC = 1..4 whether the CTA's slice of C
+// and the shifted directions fit in shared memory (else they are read from
+// the band in L2, or kept in the CTA's scratch slice) with the resulting
+// dynamic size; LCmax is the largest LC that fits at all.
+struct MsPlan {
+  int CS, Rc, dall, Qs, cap, esz, LCmax;
+  int c_smem[5], ps_smem[5];
+  size_t dyn[5];
+  size_t scratch_bytes;
+};
+
 struct ProblemTable {
   int32_t count;
   int32_t total_groups;
   int32_t total_sys;
   int32_t cluster_size;         // options.cluster_size (0: chosen from d)
   ProblemDev p[kMaxProblems];
+  // host-only (never uploaded): the solver and the multi-shift plan
+  int32_t solver;
+  MsPlan ms;
+  void* ms_scratch;
 };
 
 // Launchers (one per stage).  All are stream-ordered and never synchronize.
@@ -126,7 +144,8 @@ int launch_ritz_cluster(const ProblemTable& tab, const ProblemDev* dtab, cudaStr
 bool ritz_cluster_fits(int64_t d, int l);
 int launch_pcg(const ProblemTable& tab, const ProblemDev* dtab, int32_t* counter, void* scratch,
                size_t scratch_bytes, int num_sms, cudaStream_t st);
-void launch_finish(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st);
+// accumulate = false: vbar was written by the solver (multi-shift CG)
+void launch_finish(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st, bool accumulate = true);
 void launch_count_neighbours(const GridDev& g, const int64_t* obs, int64_t d, int64_t n,
                              int64_t* out2, cudaStream_t st);
 void launch_philox(uint64_t seed, int64_t count, double* out, cudaStream_t st);
@@ -150,6 +169,11 @@ bool band1d_eligible(const ProblemDev& p);
 int band1d_cluster_size(const ProblemDev& p, int requested);
 int launch_pcg_band1d(const ProblemDev& p, const ProblemDev* dp, int CS, int32_t* queue, int32_t* fallback,
                       int num_sms, cudaStream_t st);
+
+// Multi-shift CG (one Krylov run per member for all shifts): plan and launch.
+// mscg_plan returns -1 when one chain's full p does not fit a CTA.
+int mscg_plan(const ProblemTable& tab, int num_sms, int requested_cs, MsPlan* out);
+int launch_mscg(const ProblemTable& tab, const ProblemDev* dtab, const MsPlan& pl, int num_sms, cudaStream_t st);
 
 // Work counters of the PCG stage: [0] group queue of the general kernel,
 // [1 + i] system queue of the band kernel for problem i, [1 + kMaxProblems + i]

@@ -1,0 +1,804 @@
+// a5-a7 and a9 by multi-shift CG (Sec. 3.3, the first alternative to one PCG
+// run per system).  In normalized form every system of member i,
+//
+//     ((s_q + 1) I + C) u_q = b = R^-1/2 w^(i),    q = 1..Q,
+//
+// is the same C shifted by sigma_q = s_q + 1, and Krylov subspaces are
+// invariant under shifts.  So one CG run on the base system
+// (C + sigma_0 I) u = b, sigma_0 = min_q sigma_q, gives every shifted iterate:
+// the shifted residuals stay collinear with the base residual,
+// r_k^(q) = zeta_k^(q) r_k, and with delta_q = sigma_q - sigma_0
+//
+//   zeta_{k+1} = zeta_k zeta_{k-1} alpha_{k-1} /
+//                (alpha_k beta_{k-1} (zeta_{k-1} - zeta_k) + zeta_{k-1} alpha_{k-1} (1 + delta_q alpha_k)),
+//   alpha_k^(q) = alpha_k zeta_{k+1} / zeta_k,   beta_k^(q) = beta_k (zeta_{k+1} / zeta_k)^2,
+//   u_q += alpha_k^(q) p_q,   p_q <- zeta_{k+1} r_{k+1} + beta_k^(q) p_q
+//
+// (Frommer & Glassner 1998; Jegerlehner 1996).  No preconditioner (the LMP
+// of App. E is not shift-invariant).  Only sum_q p_q u_q is needed (Sec. 3.2),
+// so it is accumulated in place of the Q solutions.  Shift q stops once
+// |zeta^(q)| ||r|| <= tol ||b|| (1e-30 ||b|| in fixed-iteration mode, so that
+// zeta never underflows); the mean system is a chain with the single shift 1.
+//
+// GB300 mapping: one thread-block cluster of CS CTAs per group of LC chains
+// (members) of one problem.  CTA c of the cluster owns rows [c Rc, (c+1) Rc) of
+// the observation space: their residuals, shifted directions, quadrature sums
+// and the matvec rows of C (read from the L2-resident band).  Every CTA keeps a
+// full copy of each chain's base direction p in shared memory; after each
+// update the owner pushes its rows to all CTAs of the cluster as 16-byte
+// distributed-shared-memory stores.  An iteration has three cluster barriers:
+// the partial sums of p^T (C + sigma_0) p, those of r^T r, and the p exchange.
+// Every CTA then computes the same FP64 scalars from the same partials in the
+// same order, so the cluster stays in lockstep without a leader.
+#include <cooperative_groups.h>
+#include <math.h>
+#include <string.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace infoesrf {
+
+constexpr int kMsThreads = 256;
+constexpr int kMsWarps = kMsThreads / 32;
+constexpr int kMsMaxCS = 8;
+constexpr int kMsMaxLC = 4;
+// Dynamic shared memory the plan may use per CTA (the rest of the 227 KB
+// opt-in limit is left for the static arrays).
+constexpr size_t kMsSmemBudget = 224 * 1024;
+
+// Bytes of dynamic shared memory for LC chains (layout in k_mscg).
+static size_t ms_dyn_bytes(int LC, int Rc, int dall, int Qs, int cap, size_t esz, bool c_smem, bool ps_smem) {
+  size_t b = esz * ((size_t)LC * dall + 4 * (size_t)LC * Rc + 3 * (size_t)LC * Qs);
+  b += 8 * 6 * (size_t)LC * Qs + 4 * 4 * (size_t)LC * Qs + 4 * (size_t)Rc;
+  if (c_smem) b += (esz + 4) * (size_t)cap * Rc;
+  if (ps_smem) b += esz * (size_t)LC * Qs * Rc;
+  return b;
+}
+
+__host__ __device__ __forceinline__ int chains_of(const ProblemDev& p) {
+  return p.do_mean + (p.do_pert ? (int)p.N : 0);
+}
+
+// Float-float quotient a / b (b != 0), about 48 bits: the FP32 quotient of the
+// leading parts, corrected once by the residual a - q b formed in float-float.
+__device__ __forceinline__ FF ff_div(FF a, FF b) {
+  const float q1 = a.h / b.h;
+  const FF r = ff_sub(a, ff_mul(FF{q1, 0.f}, b));
+  return ff_norm(q1, r.h / b.h);
+}
+
+// Cluster-wide sums of LC per-thread partials: warp shuffles, one partial per
+// warp in shared memory, then thread (j, dst) combines the warps of chain j and
+// stores the CTA's sum into slot [crank][j] of CTA dst (a float-float pair for
+// FP32 vectors, a double for FP64).  Ends with the cluster barrier, after which
+// red[c * LC + j] holds CTA c's partial on every CTA.
+template <typename T, int LC>
+__device__ __forceinline__ void ms_push_partials(DotAcc<T> (&acc)[LC], double* red, float (*wff)[kMsMaxLC][2],
+                                                 double (*wdd)[kMsMaxLC], cg::cluster_group& cluster, int CS,
+                                                 int crank) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < LC; ++j) {
+    if constexpr (sizeof(T) == 4) {
+      float hi = acc[j].hi, lo = acc[j].lo;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        ff_merge(hi, lo, h2, l2);
+      }
+      if (lane == 0) {
+        wff[warp][j][0] = hi;
+        wff[warp][j][1] = lo;
+      }
+    } else {
+      const double s = warp_sum(acc[j].value());
+      if (lane == 0) wdd[warp][j] = s;
+    }
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < LC * CS) {
+    const int j = threadIdx.x % LC, dst = threadIdx.x / LC;
+    double* slot = cluster.map_shared_rank(red, dst) + crank * LC + j;
+    if constexpr (sizeof(T) == 4) {
+      float hi = 0.f, lo = 0.f;
+      for (int w = 0; w < kMsWarps; ++w) ff_merge(hi, lo, wff[w][j][0], wff[w][j][1]);
+      *reinterpret_cast<float2*>(slot) = make_float2(hi, lo);
+    } else {
+      double v = 0.0;
+      for (int w = 0; w < kMsWarps; ++w) v += wdd[w][j];
+      *slot = v;
+    }
+  }
+  cluster.sync();
+}
+
+// Sum over the cluster's CTAs of chain j's partials, in rank order.
+__device__ __forceinline__ FF ms_sum_ff(const double* red, int CS, int LC, int j) {
+  float hi = 0.f, lo = 0.f;
+  for (int c = 0; c < CS; ++c) {
+    const float2 v = reinterpret_cast<const float2*>(red)[c * LC + j];
+    ff_merge(hi, lo, v.x, v.y);
+  }
+  return ff_norm(hi, lo);
+}
+__device__ __forceinline__ double ms_sum_d(const double* red, int CS, int LC, int j) {
+  double s = 0.0;
+  for (int c = 0; c < CS; ++c) s += red[c * LC + j];
+  return s;
+}
+__device__ __forceinline__ double ff_to_d(FF a) { return (double)a.h + (double)a.l; }
+
+// Four consecutive rows of p (held by lanes 4m .. 4m+3) to every CTA: lane 4m
+// gathers them by shuffles and issues 16-byte distributed shared-memory stores.
+template <typename T>
+__device__ __forceinline__ void ms_push_p4(T pn, bool push, T* dst_local, cg::cluster_group& cluster, int CS) {
+  const T v1 = __shfl_down_sync(0xffffffffu, pn, 1);
+  const T v2 = __shfl_down_sync(0xffffffffu, pn, 2);
+  const T v3 = __shfl_down_sync(0xffffffffu, pn, 3);
+  if (!push || (threadIdx.x & 3) != 0) return;
+  for (int c = 0; c < CS; ++c) {
+    T* dst = cluster.map_shared_rank(dst_local, c);
+    if constexpr (sizeof(T) == 4) {
+      *reinterpret_cast<float4*>(dst) = make_float4(pn, v1, v2, v3);
+    } else {
+      reinterpret_cast<double2*>(dst)[0] = make_double2(pn, v1);
+      reinterpret_cast<double2*>(dst)[1] = make_double2(v2, v3);
+    }
+  }
+}
+
+// Shift t of the flattened active lists of the chains in `step`: chain j and
+// position in its list.
+template <int LC>
+__device__ __forceinline__ int ms_locate(int t, unsigned step, const int* nact, int& off) {
+  int j = 0;
+  for (; j < LC - 1; ++j) {
+    const int nj = (step >> j & 1u) ? nact[j] : 0;
+    if (t < nj) break;
+    t -= nj;
+  }
+  off = t;
+  return j;
+}
+
+constexpr int kMsZetaWarps = 4;   // warps that run the shifted recurrences while the others update r
+
+// Dynamic shared memory (T arrays first, all sizes multiples of 16 bytes):
+//   pfull [LC][dall]   full copy of each chain's base direction p
+//   rv, apv [LC][Rc]   own rows of r and (C + sigma_0 I) p
+//   ahi, alo [LC][Rc]  own rows of sum_q p_q u_q (float-float for FP32)
+//   cw, cz, cb [LC][Qs] this step's p_q alpha^(q), zeta_{k+1}, beta^(q)
+//   zeta, zprev, delta, wq, res, rat [LC][Qs] (FP64; res = |zeta| ||r||, rat = zeta_{k+1} / zeta_k)
+//   act, itq [LC][Qs], lst [2][LC][Qs] (int): active flags, iteration counts,
+//                      and the active shifts of this step and the next
+//   snnz [Rc] (int)
+//   sval [cap][Rc], scol [cap][Rc]  the CTA's rows of the band of C (if c_smem;
+//                      staged once per problem, read every iteration)
+//   ps [LC][Qs][Rc]    shifted directions (here, or in the CTA's scratch slice)
+template <typename T, int LC>
+__global__ void __launch_bounds__(kMsThreads, 1)
+    k_mscg(const ProblemDev* __restrict__ tab, int count, int Rc, int dall, int Qs, int cap, int c_smem,
+           int ps_smem, T* __restrict__ ps_scratch) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int CS = (int)cluster.num_blocks();
+  const int crank = (int)cluster.block_rank();
+  const int cl = blockIdx.x / CS, ncl = gridDim.x / CS;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  extern __shared__ __align__(16) unsigned char ms_dyn[];
+  T* pfull = reinterpret_cast<T*>(ms_dyn);
+  T* rv = pfull + (size_t)LC * dall;
+  T* apv = rv + LC * Rc;
+  T* ahi = apv + LC * Rc;
+  T* alo = ahi + LC * Rc;
+  T* cw = alo + LC * Rc;
+  T* cz = cw + LC * Qs;
+  T* cb = cz + LC * Qs;
+  double* zeta = reinterpret_cast<double*>(cb + LC * Qs);
+  double* zprev = zeta + LC * Qs;
+  double* delta = zprev + LC * Qs;
+  double* wq = delta + LC * Qs;
+  double* res = wq + LC * Qs;
+  double* rat = res + LC * Qs;
+  int* act = reinterpret_cast<int*>(rat + LC * Qs);
+  int* itq = act + LC * Qs;
+  int* lst = itq + LC * Qs;
+  int* snnz = lst + 2 * LC * Qs;
+  T* sval = reinterpret_cast<T*>(snnz + Rc);
+  int32_t* scol = reinterpret_cast<int32_t*>(sval + (c_smem ? (size_t)cap * Rc : 0));
+  T* ps_s = reinterpret_cast<T*>(scol + (c_smem ? (size_t)cap * Rc : 0));
+  T* ps_g = ps_scratch ? ps_scratch + (size_t)blockIdx.x * LC * Qs * Rc : nullptr;
+
+  __shared__ double s_red_pap[kMsMaxCS * kMsMaxLC];
+  __shared__ double s_red_rr[kMsMaxCS * kMsMaxLC];
+  __shared__ float s_wff[kMsWarps][kMsMaxLC][2];
+  __shared__ double s_wdd[kMsWarps][kMsMaxLC];
+  __shared__ double s_rr[LC], s_alpha[LC], s_aprev[LC], s_bprev[LC], s_beta[LC], s_srr[LC];
+  __shared__ double s_bn[LC], s_sig0[LC], s_stop[LC];
+  __shared__ float s_rrh[LC], s_rrl[LC];
+  __shared__ T s_alpha_t[LC], s_beta_t[LC];
+  __shared__ int s_live[LC], s_done[LC], s_qc[LC], s_mem[LC], s_k[LC];
+  __shared__ int s_nact[2][LC];
+  __shared__ int s_cprob;   // problem whose rows of C are staged
+  if (tid == 0) s_cprob = -1;
+
+  // threads per matvec row: a power of two <= 8 that keeps the CTA busy
+  int sub = 1;
+  while (sub < 8 && Rc * sub * 2 <= kMsThreads) sub <<= 1;
+
+  int G = 0;
+  for (int p = 0; p < count; ++p) G += (chains_of(tab[p]) + LC - 1) / LC;
+
+  for (int g = cl; g < G; g += ncl) {
+    int p = 0, gb = 0, nch = 0;
+    for (; p < count; ++p) {
+      nch = chains_of(tab[p]);
+      const int ng = (nch + LC - 1) / LC;
+      if (g < gb + ng) break;
+      gb += ng;
+    }
+    const ProblemDev& pr = tab[p];
+    const int c0 = (g - gb) * LC;
+    const int d = (int)pr.d;
+    const int64_t N = pr.N, N1 = pr.N + 1;
+    const int r0 = crank * Rc;
+    const int nrows = max(0, min(d - r0, Rc));
+    const bool fixed = pr.fixed_iters > 0;
+    const int limit = fixed ? pr.fixed_iters : pr.max_iter;
+
+    if (tid < LC) {
+      const int c = c0 + tid;
+      const bool live = c < nch;
+      const bool mean = live && pr.do_mean && c == 0;
+      s_live[tid] = live;
+      s_mem[tid] = live ? (mean ? -1 : c - pr.do_mean) : -2;
+      s_qc[tid] = live ? (mean ? 1 : pr.Q) : 0;
+      double sg0 = 1.0;
+      if (live && !mean) {
+        sg0 = pr.s[0] + 1.0;
+        for (int q = 1; q < pr.Q; ++q) sg0 = fmin(sg0, pr.s[q] + 1.0);
+      }
+      s_sig0[tid] = sg0;
+      s_aprev[tid] = 1.0;
+      s_bprev[tid] = 0.0;
+      s_k[tid] = 0;
+    }
+    __syncthreads();
+
+    // the CTA's rows of the band of C, once per problem
+    if (s_cprob != p) {
+      const T* __restrict__ gv = reinterpret_cast<const T*>(pr.oo_val);
+      const int cp = (int)pr.max_oo;
+      for (int row = tid; row < Rc; row += kMsThreads) snnz[row] = row < nrows ? pr.oo_nnz[r0 + row] : 0;
+      if (c_smem) {
+        for (int idx = tid; idx < cp * Rc; idx += kMsThreads) {
+          const int e = idx / Rc, row = idx % Rc;
+          if (row < nrows) {
+            sval[idx] = gv[(int64_t)e * d + r0 + row];
+            scol[idx] = pr.oo_col[(int64_t)e * d + r0 + row];
+          }
+        }
+      }
+    }
+    // p_0 = b for every chain, in full: b = R^-1/2 w^(i), or R^-1/2 (y - H mu)
+    const T* W = reinterpret_cast<const T*>(pr.W);
+    for (int idx = tid; idx < LC * dall; idx += kMsThreads) {
+      const int j = idx / dall, a = idx % dall;
+      const int m = s_mem[j];
+      T v = T(0);
+      if (a < d && m >= -1) v = m == -1 ? to_t<T>(pr.bmean[a]) : to_t<T>(pr.rinv[a]) * W[(int64_t)a * N + m];
+      pfull[idx] = v;
+    }
+    __syncthreads();
+    {
+      DotAcc<T> bb[LC];
+      T* psb = ps_smem ? ps_s : ps_g;
+      for (int idx = tid; idx < LC * Rc; idx += kMsThreads) {
+        const int j = idx / Rc, row = idx % Rc;
+        const T v = row < nrows ? pfull[(size_t)j * dall + r0 + row] : T(0);
+        rv[idx] = v;
+        apv[idx] = T(0);
+        ahi[idx] = T(0);
+        alo[idx] = T(0);
+        T* psj = psb + (size_t)j * Qs * Rc + row;
+        for (int q = 0; q < s_qc[j]; ++q) psj[(size_t)q * Rc] = v;
+#pragma unroll
+        for (int jj = 0; jj < LC; ++jj)
+          if (jj == j) bb[jj].add_prod(v, v);
+      }
+      ms_push_partials<T, LC>(bb, s_red_rr, s_wff, s_wdd, cluster, CS, crank);
+    }
+    if (tid < LC) {
+      double rr;
+      if constexpr (sizeof(T) == 4) {
+        const FF f = ms_sum_ff(s_red_rr, CS, LC, tid);
+        s_rrh[tid] = f.h;
+        s_rrl[tid] = f.l;
+        rr = ff_to_d(f);
+      } else {
+        rr = ms_sum_d(s_red_rr, CS, LC, tid);
+      }
+      const double bn = sqrt(rr);
+      s_rr[tid] = rr;
+      s_bn[tid] = bn;
+      s_stop[tid] = (fixed ? 1e-30 : pr.tol) * bn;
+      const bool on = s_live[tid] && bn > 0.0;
+      s_done[tid] = !on;
+      s_nact[0][tid] = on ? s_qc[tid] : 0;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < LC * Qs; idx += kMsThreads) {
+      const int j = idx / Qs, q = idx % Qs;
+      const bool has = q < s_qc[j];
+      double sg = 1.0, w = 1.0;
+      if (has && s_mem[j] >= 0) {
+        sg = pr.s[q] + 1.0;
+        w = pr.p[q];
+      }
+      zeta[idx] = 1.0;
+      zprev[idx] = 1.0;
+      delta[idx] = sg - s_sig0[j];
+      wq[idx] = w;
+      res[idx] = (has && s_bn[j] > 0.0) ? s_bn[j] : 0.0;
+      act[idx] = has && !s_done[j];
+      itq[idx] = 0;
+      lst[idx] = q;   // buffer 0: every shift of a live chain, in order
+    }
+    __syncthreads();
+
+    T sg0[LC];
+#pragma unroll
+    for (int j = 0; j < LC; ++j) sg0[j] = to_t<T>(s_sig0[j]);
+    const T* __restrict__ cval = reinterpret_cast<const T*>(pr.oo_val);
+    const int32_t* __restrict__ ccol = pr.oo_col;
+    int buf = 0;
+
+    for (;;) {
+      // identical on every CTA: the flags come from identical scalars
+      unsigned step = 0;
+#pragma unroll
+      for (int j = 0; j < LC; ++j) step |= (s_done[j] == 0 ? 1u : 0u) << j;
+      if (step == 0) break;
+      const int* nact = s_nact[buf];
+      const int* lcur = lst + buf * LC * Qs;
+
+      // q = (C + sigma_0 I) p over the own rows, and the partials of p^T q
+      DotAcc<T> pap[LC];
+      const int rows_per_pass = kMsThreads / sub;
+      for (int base = 0; base < nrows; base += rows_per_pass) {
+        const int rl = base + tid / sub, part = tid % sub;
+        const bool valid = rl < nrows;
+        const int a = r0 + rl;
+        T y[LC];
+#pragma unroll
+        for (int j = 0; j < LC; ++j) y[j] = T(0);
+        const int nnz = valid ? snnz[rl] : 0;
+        if (c_smem) {
+#pragma unroll 4
+          for (int e = part; e < nnz; e += sub) {
+            const T v = sval[e * Rc + rl];
+            const int c = scol[e * Rc + rl];
+#pragma unroll
+            for (int j = 0; j < LC; ++j) y[j] = fma(v, pfull[(size_t)j * dall + c], y[j]);
+          }
+        } else {
+#pragma unroll 8
+          for (int e = part; e < nnz; e += sub) {
+            const T v = __ldg(cval + (int64_t)e * d + a);
+            const int c = __ldg(ccol + (int64_t)e * d + a);
+#pragma unroll
+            for (int j = 0; j < LC; ++j) y[j] = fma(v, pfull[(size_t)j * dall + c], y[j]);
+          }
+        }
+        for (int o = sub >> 1; o > 0; o >>= 1) {
+#pragma unroll
+          for (int j = 0; j < LC; ++j) y[j] += __shfl_xor_sync(0xffffffffu, y[j], o);
+        }
+        if (valid && part == 0) {
+#pragma unroll
+          for (int j = 0; j < LC; ++j) {
+            const T pa = pfull[(size_t)j * dall + a];
+            const T yy = fma(sg0[j], pa, y[j]);
+            apv[j * Rc + rl] = yy;
+            if (step >> j & 1u) pap[j].add_prod(pa, yy);
+          }
+        }
+      }
+      ms_push_partials<T, LC>(pap, s_red_pap, s_wff, s_wdd, cluster, CS, crank);   // (1)
+
+      // alpha = r^T r / p^T q
+      if (tid < LC && (step >> tid & 1u)) {
+        bool bad;
+        double al = 0.0;
+        if constexpr (sizeof(T) == 4) {
+          const FF pq = ms_sum_ff(s_red_pap, CS, LC, tid);
+          bad = !(pq.h > 0.f) || !isfinite(pq.h);
+          if (!bad) {
+            const FF a = ff_div(FF{s_rrh[tid], s_rrl[tid]}, pq);
+            al = ff_to_d(a);
+            s_alpha_t[tid] = a.h + a.l;
+          }
+        } else {
+          const double pq = ms_sum_d(s_red_pap, CS, LC, tid);
+          bad = !(pq > 0.0) || !isfinite(pq);
+          if (!bad) {
+            al = s_rr[tid] / pq;
+            s_alpha_t[tid] = to_t<T>(al);
+          }
+        }
+        if (bad) {
+          s_done[tid] = 2;   // breakdown
+          s_alpha_t[tid] = T(0);
+        }
+        s_alpha[tid] = al;
+      }
+      __syncthreads();
+      step = 0;
+#pragma unroll
+      for (int j = 0; j < LC; ++j) step |= (s_done[j] == 0 ? 1u : 0u) << j;
+
+      DotAcc<T> rra[LC];
+      if (warp < kMsZetaWarps) {
+        // zeta_{k+1} / zeta_k and p_q alpha^(q) of every active shift (FP64)
+        int tot = 0;
+#pragma unroll
+        for (int j = 0; j < LC; ++j) tot += (step >> j & 1u) ? nact[j] : 0;
+        for (int t = tid; t < tot; t += kMsZetaWarps * 32) {
+          int off;
+          const int j = ms_locate<LC>(t, step, nact, off);
+          const int idx = j * Qs + lcur[j * Qs + off];
+          const double z0 = zeta[idx], zm = zprev[idx];
+          const double al = s_alpha[j], ap = s_aprev[j], bp = s_bprev[j];
+          const double ratio = zm * ap / (al * bp * (zm - z0) + zm * ap * (1.0 + delta[idx] * al));
+          const double z1 = z0 * ratio;
+          rat[idx] = ratio;
+          cw[idx] = to_t<T>(wq[idx] * al * ratio);
+          cz[idx] = to_t<T>(z1);
+          zprev[idx] = z0;
+          zeta[idx] = z1;
+        }
+      } else {
+        // r <- r - alpha q and the partials of r^T r
+        T alpha_t[LC];
+#pragma unroll
+        for (int j = 0; j < LC; ++j) alpha_t[j] = s_alpha_t[j];
+        for (int idx = tid - kMsZetaWarps * 32; idx < LC * Rc; idx += kMsThreads - kMsZetaWarps * 32) {
+          const int j = idx / Rc;
+          if (!(step >> j & 1u)) continue;
+          T al = T(0);
+#pragma unroll
+          for (int jj = 0; jj < LC; ++jj)
+            if (jj == j) al = alpha_t[jj];
+          const T rn = fma(-al, apv[idx], rv[idx]);
+          rv[idx] = rn;
+#pragma unroll
+          for (int jj = 0; jj < LC; ++jj)
+            if (jj == j) rra[jj].add_prod(rn, rn);
+        }
+      }
+      ms_push_partials<T, LC>(rra, s_red_rr, s_wff, s_wdd, cluster, CS, crank);   // (2)
+
+      // beta = r'^T r' / r^T r and ||r'||
+      if (tid < LC && (step >> tid & 1u)) {
+        if constexpr (sizeof(T) == 4) {
+          const FF rn = ms_sum_ff(s_red_rr, CS, LC, tid);
+          const FF b = ff_div(rn, FF{s_rrh[tid], s_rrl[tid]});
+          const FF sr = rn.h > 0.f ? ff_mul(rn, ff_rsqrt(rn)) : FF{0.f, 0.f};
+          s_beta[tid] = ff_to_d(b);
+          s_beta_t[tid] = b.h + b.l;
+          s_srr[tid] = ff_to_d(sr);
+          s_rrh[tid] = rn.h;
+          s_rrl[tid] = rn.l;
+          s_rr[tid] = ff_to_d(rn);
+        } else {
+          const double rrn = ms_sum_d(s_red_rr, CS, LC, tid);
+          const double b = rrn / s_rr[tid];
+          s_beta[tid] = b;
+          s_beta_t[tid] = to_t<T>(b);
+          s_srr[tid] = sqrt(rrn);
+          s_rr[tid] = rrn;
+        }
+      }
+      __syncthreads();
+
+      // beta^(q), the stopping test and the iteration count of every active shift
+      {
+        int tot = 0;
+#pragma unroll
+        for (int j = 0; j < LC; ++j) tot += (step >> j & 1u) ? nact[j] : 0;
+        for (int t = tid; t < tot; t += kMsThreads) {
+          int off;
+          const int j = ms_locate<LC>(t, step, nact, off);
+          const int idx = j * Qs + lcur[j * Qs + off];
+          const double ratio = rat[idx];
+          cb[idx] = to_t<T>(s_beta[j] * ratio * ratio);
+          itq[idx] = s_k[j] + 1;
+          const double rq = fabs(zeta[idx]) * s_srr[j];
+          res[idx] = rq;
+          if (!(rq > s_stop[j])) act[idx] = 0;
+        }
+      }
+      __syncthreads();
+
+      // warp 0: next step's active lists and the chain bookkeeping (read again
+      // only after barrier (3)); everyone else goes straight to the update
+      if (warp == 0) {
+        const int nb = buf ^ 1;
+        for (int j = 0; j < LC; ++j) {
+          if (!(step >> j & 1u)) continue;
+          int n = 0;
+          for (int q0 = 0; q0 < s_qc[j]; q0 += 32) {
+            const int q = q0 + lane;
+            const bool a = q < s_qc[j] && act[j * Qs + q];
+            const unsigned m = __ballot_sync(0xffffffffu, a);
+            if (a) lst[(nb * LC + j) * Qs + n + __popc(m & ((1u << lane) - 1u))] = q;
+            n += __popc(m);
+          }
+          if (lane == 0) {
+            s_nact[nb][j] = n;
+            s_aprev[j] = s_alpha[j];
+            s_bprev[j] = s_beta[j];
+            s_k[j] += 1;
+            if (n == 0 || s_k[j] >= limit) s_done[j] = 1;
+          }
+        }
+      }
+
+      // shifted directions, quadrature sum, base direction, and its exchange
+      T beta_t[LC];
+#pragma unroll
+      for (int j = 0; j < LC; ++j) beta_t[j] = s_beta_t[j];
+      auto update = [&](T* psb) {
+        for (int base = 0; base < LC * Rc; base += kMsThreads) {
+          const int idx = base + tid;
+          const bool in = idx < LC * Rc;
+          const int j = in ? idx / Rc : 0, row = in ? idx % Rc : 0;
+          const bool st = in && (step >> j & 1u);
+          T pn = T(0);
+          if (st) {
+            const T rn = rv[idx];
+            T sum = T(0);
+            T* pc = psb + (size_t)j * Qs * Rc + row;
+            const int* lj = lcur + j * Qs;
+            const int n = nact[j];
+            int i = 0;
+            for (; i + 4 <= n; i += 4) {
+              const int q0 = lj[i], q1 = lj[i + 1], q2 = lj[i + 2], q3 = lj[i + 3];
+              const T p0 = pc[(size_t)q0 * Rc], p1 = pc[(size_t)q1 * Rc];
+              const T p2 = pc[(size_t)q2 * Rc], p3 = pc[(size_t)q3 * Rc];
+              const int i0 = j * Qs + q0, i1 = j * Qs + q1, i2 = j * Qs + q2, i3 = j * Qs + q3;
+              sum = fma(cw[i0], p0, sum);
+              sum = fma(cw[i1], p1, sum);
+              sum = fma(cw[i2], p2, sum);
+              sum = fma(cw[i3], p3, sum);
+              pc[(size_t)q0 * Rc] = fma(cz[i0], rn, cb[i0] * p0);
+              pc[(size_t)q1 * Rc] = fma(cz[i1], rn, cb[i1] * p1);
+              pc[(size_t)q2 * Rc] = fma(cz[i2], rn, cb[i2] * p2);
+              pc[(size_t)q3 * Rc] = fma(cz[i3], rn, cb[i3] * p3);
+            }
+            for (; i < n; ++i) {
+              const int q = lj[i], ci = j * Qs + q;
+              const T po = pc[(size_t)q * Rc];
+              sum = fma(cw[ci], po, sum);
+              pc[(size_t)q * Rc] = fma(cz[ci], rn, cb[ci] * po);
+            }
+            if constexpr (sizeof(T) == 4) {
+              float s, e;
+              two_sum(ahi[idx], sum, s, e);
+              ahi[idx] = s;
+              alo[idx] += e;
+            } else {
+              ahi[idx] += sum;
+            }
+            T bt = T(0);
+#pragma unroll
+            for (int jj = 0; jj < LC; ++jj)
+              if (jj == j) bt = beta_t[jj];
+            pn = fma(bt, pfull[(size_t)j * dall + r0 + row], rn);
+          }
+          ms_push_p4<T>(pn, st, pfull + (size_t)j * dall + r0 + row, cluster, CS);
+        }
+      };
+      if (ps_smem) update(ps_s);
+      else update(ps_g);
+      cluster.sync();   // (3)
+      buf ^= 1;
+    }
+
+    // vbar = R^-1/2 sum_q p_q u_q (FP64) for the state update
+    for (int idx = tid; idx < LC * Rc; idx += kMsThreads) {
+      const int j = idx / Rc, row = idx % Rc;
+      if (!s_live[j] || row >= nrows) continue;
+      const int a = r0 + row;
+      const int64_t m = s_mem[j] == -1 ? N : (int64_t)s_mem[j];
+      const double u = (double)ahi[idx] + (double)alo[idx];
+      const double v = pr.rinv[a] * u;
+      pr.Vbar[(int64_t)a * N1 + m] = v;
+      reinterpret_cast<T*>(pr.VbarT)[(int64_t)a * N1 + m] = to_t<T>(v);
+    }
+    if (crank == 0) {
+      for (int idx = tid; idx < LC * Qs; idx += kMsThreads) {
+        const int j = idx / Qs, q = idx % Qs;
+        if (!s_live[j] || q >= s_qc[j]) continue;
+        const int64_t sid = s_mem[j] == -1 ? 0 : pr.mean_sys + (int64_t)q * N + s_mem[j];
+        pr.iters[sid] = itq[idx];
+        pr.relres[sid] = s_bn[j] > 0.0 ? res[idx] / s_bn[j] : 0.0;
+        if (act[idx] && !fixed) atomicOr(&pr.status[0], kStatNotConverged);
+      }
+      if (tid < LC && s_done[tid] == 2) atomicOr(&pr.status[0], kStatBreakdown);
+      if (tid == 0) atomicOr(&pr.status[1], 2);
+    }
+    if (tid == 0) s_cprob = p;
+    __syncthreads();
+  }
+  cluster.sync();   // no CTA leaves while another may still write to its shared memory
+}
+
+int mscg_plan(const ProblemTable& tab, int num_sms, int requested_cs, MsPlan* out) {
+  int64_t dmax = 1, cap = 1;
+  int qmax = 1;
+  for (int i = 0; i < tab.count; ++i) {
+    const ProblemDev& p = tab.p[i];
+    dmax = p.d > dmax ? p.d : dmax;
+    cap = p.max_oo > cap ? p.max_oo : cap;
+    if (p.do_pert) qmax = p.Q > qmax ? p.Q : qmax;
+  }
+  int CS = requested_cs > 0 ? requested_cs : kMsMaxCS;
+  if (requested_cs <= 0)
+    while (CS > 1 && (dmax + CS - 1) / CS < 64) CS >>= 1;
+  if (CS > num_sms) CS = 1;
+  MsPlan pl;
+  memset(&pl, 0, sizeof(pl));
+  pl.CS = CS;
+  pl.Rc = (int)((((dmax + CS - 1) / CS) + 3) / 4 * 4);
+  pl.dall = CS * pl.Rc;
+  pl.Qs = (qmax + 3) / 4 * 4;
+  pl.cap = (int)cap;
+  pl.esz = tab.p[0].precision == 0 ? 8 : 4;
+  // the slice of C (read every iteration by every thread) before the shifted
+  // directions (one read and one write per active shift)
+  const bool order[4][2] = {{true, true}, {true, false}, {false, true}, {false, false}};
+  for (int lc = 1; lc <= kMsMaxLC; ++lc) {
+    for (int o = 0; o < 4; ++o) {
+      const size_t b = ms_dyn_bytes(lc, pl.Rc, pl.dall, pl.Qs, pl.cap, pl.esz, order[o][0], order[o][1]);
+      if (b <= kMsSmemBudget) {
+        pl.c_smem[lc] = order[o][0];
+        pl.ps_smem[lc] = order[o][1];
+        pl.dyn[lc] = b;
+        pl.LCmax = lc;
+        if (!order[o][1]) {
+          const size_t sb = (size_t)num_sms * lc * pl.Qs * pl.Rc * pl.esz;
+          pl.scratch_bytes = sb > pl.scratch_bytes ? sb : pl.scratch_bytes;
+        }
+        break;
+      }
+    }
+  }
+  if (!pl.LCmax) return -1;
+  *out = pl;
+  return 0;
+}
+
+namespace {
+
+// Co-resident clusters per (device, instantiation, cluster size, dynamic
+// bytes), looked up once per host thread; the function attribute is raised to
+// the largest dynamic size the plan can ask for on first use.
+struct MsOcc {
+  int dev, esz, LC, CS;
+  size_t dyn;
+  int clusters;
+};
+
+template <typename T, int LC>
+int ms_max_clusters(int CS, size_t dyn) {
+  static thread_local MsOcc cache[32];
+  static thread_local int ncache = 0;
+  static thread_local int attr_dev_mask = 0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  for (int i = 0; i < ncache; ++i) {
+    const MsOcc& c = cache[i];
+    if (c.dev == dev && c.esz == (int)sizeof(T) && c.LC == LC && c.CS == CS && c.dyn == dyn) return c.clusters;
+  }
+  if (dev < 31 && !(attr_dev_mask & (1 << dev))) {
+    if (cudaFuncSetAttribute(k_mscg<T, LC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMsSmemBudget) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return -1;
+    }
+    attr_dev_mask |= 1 << dev;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CS, 1, 1);
+  cfg.blockDim = dim3(kMsThreads, 1, 1);
+  cfg.dynamicSmemBytes = dyn;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int mc = 0;
+  if (cudaOccupancyMaxActiveClusters(&mc, k_mscg<T, LC>, &cfg) != cudaSuccess || mc < 1) {
+    cudaGetLastError();
+    mc = -1;
+  }
+  MsOcc& e = cache[ncache < 32 ? ncache++ : 31];
+  e = MsOcc{dev, (int)sizeof(T), LC, CS, dyn, mc};
+  return mc;
+}
+
+template <typename T, int LC>
+int ms_launch(const ProblemTable& tab, const ProblemDev* dtab, const MsPlan& pl, int clusters, size_t dyn,
+              cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(clusters * pl.CS, 1, 1);
+  cfg.blockDim = dim3(kMsThreads, 1, 1);
+  cfg.dynamicSmemBytes = dyn;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = pl.CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  T* scratch = reinterpret_cast<T*>(tab.ms_scratch);
+  if (!pl.ps_smem[LC] && !scratch) return -1;
+  if (cudaLaunchKernelEx(&cfg, k_mscg<T, LC>, dtab, (int)tab.count, pl.Rc, pl.dall, pl.Qs, pl.cap,
+                         pl.c_smem[LC], pl.ps_smem[LC], scratch) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  note_launches(1);
+  return 0;
+}
+
+template <typename T>
+int ms_dispatch(const ProblemTable& tab, const ProblemDev* dtab, const MsPlan& pl, int num_sms, cudaStream_t st) {
+  // the smallest chain group that still fits one wave of co-resident clusters
+  int pick = 0, clusters = 0;
+  size_t dyn = 0;
+  for (int lc = 1; lc <= pl.LCmax; ++lc) {
+    if (!pl.dyn[lc]) continue;
+    const size_t b = pl.dyn[lc];
+    int mc = lc == 1 ? ms_max_clusters<T, 1>(pl.CS, b)
+             : lc == 2 ? ms_max_clusters<T, 2>(pl.CS, b)
+             : lc == 3 ? ms_max_clusters<T, 3>(pl.CS, b)
+                       : ms_max_clusters<T, 4>(pl.CS, b);
+    if (mc < 1) continue;
+    if (mc > num_sms / pl.CS) mc = num_sms / pl.CS;
+    if (mc < 1) continue;
+    int groups = 0;
+    for (int i = 0; i < tab.count; ++i) groups += (chains_of(tab.p[i]) + lc - 1) / lc;
+    pick = lc;
+    dyn = b;
+    clusters = groups < mc ? groups : mc;
+    if (groups <= mc) break;
+  }
+  if (!pick || clusters < 1) return -1;
+  switch (pick) {
+    case 1: return ms_launch<T, 1>(tab, dtab, pl, clusters, dyn, st);
+    case 2: return ms_launch<T, 2>(tab, dtab, pl, clusters, dyn, st);
+    case 3: return ms_launch<T, 3>(tab, dtab, pl, clusters, dyn, st);
+    default: return ms_launch<T, 4>(tab, dtab, pl, clusters, dyn, st);
+  }
+}
+
+}  // namespace
+
+int launch_mscg(const ProblemTable& tab, const ProblemDev* dtab, const MsPlan& pl, int num_sms, cudaStream_t st) {
+  return tab.p[0].precision == 0 ? ms_dispatch<double>(tab, dtab, pl, num_sms, st)
+                                 : ms_dispatch<float>(tab, dtab, pl, num_sms, st);
+}
+
+}  // namespace infoesrf
