@@ -49,11 +49,25 @@ constexpr int kMsMaxLC = 4;
 // opt-in limit is left for the static arrays).
 constexpr size_t kMsSmemBudget = 224 * 1024;
 
+// Threads per matvec row (a power of two <= 8 that keeps a CTA of kMsThreads
+// busy) and the row stride of the staged slice of C: a multiple of 32 plus
+// 32 / sub, so that the sub threads of a row, which read neighbouring slots,
+// fall in different banks.
+__host__ __device__ __forceinline__ int ms_sub(int Rc) {
+  int sub = 1;
+  while (sub < 8 && Rc * sub * 2 <= kMsThreads) sub <<= 1;
+  return sub;
+}
+__host__ __device__ __forceinline__ int ms_cstride(int Rc) {
+  const int sub = ms_sub(Rc);
+  return (Rc + 31) / 32 * 32 + (sub > 1 ? 32 / sub : 0);
+}
+
 // Bytes of dynamic shared memory for LC chains (layout in k_mscg).
 static size_t ms_dyn_bytes(int LC, int Rc, int dall, int Qs, int cap, size_t esz, bool c_smem, bool ps_smem) {
-  size_t b = esz * ((size_t)LC * dall + 4 * (size_t)LC * Rc + 3 * (size_t)LC * Qs);
+  size_t b = esz * ((size_t)LC * dall + 4 * (size_t)LC * Rc + 7 * (size_t)LC * Qs);
   b += 8 * 6 * (size_t)LC * Qs + 4 * 4 * (size_t)LC * Qs + 4 * (size_t)Rc;
-  if (c_smem) b += (esz + 4) * (size_t)cap * Rc;
+  if (c_smem) b += (esz + 4) * (size_t)cap * ms_cstride(Rc);
   if (ps_smem) b += esz * (size_t)LC * Qs * Rc;
   return b;
 }
@@ -132,22 +146,74 @@ __device__ __forceinline__ double ms_sum_d(const double* red, int CS, int LC, in
 }
 __device__ __forceinline__ double ff_to_d(FF a) { return (double)a.h + (double)a.l; }
 
-// Four consecutive rows of p (held by lanes 4m .. 4m+3) to every CTA: lane 4m
-// gathers them by shuffles and issues 16-byte distributed shared-memory stores.
+// A shift index carried in the packed coefficient entry as the bits of a T.
 template <typename T>
-__device__ __forceinline__ void ms_push_p4(T pn, bool push, T* dst_local, cg::cluster_group& cluster, int CS) {
+__device__ __forceinline__ T ms_q_bits(int q) {
+  if constexpr (sizeof(T) == 4) return __int_as_float(q);
+  else return __longlong_as_double((long long)q);
+}
+__device__ __forceinline__ int ms_q_of(float v) { return __float_as_int(v); }
+__device__ __forceinline__ int ms_q_of(double v) { return (int)__double_as_longlong(v); }
+
+// beta = r'^T r' / r^T r (as double and as T) and ||r'|| of chain j from the
+// cluster's partials; also r'^T r' itself (float-float and double) for the
+// next step.
+template <typename T>
+__device__ __forceinline__ void ms_beta(const double* red, int CS, int LC, int j, float rrh, float rrl, double rr,
+                                        double& beta, T& beta_t, double& srr, float& rnh, float& rnl,
+                                        double& rnd) {
+  if constexpr (sizeof(T) == 4) {
+    const FF rn = ms_sum_ff(red, CS, LC, j);
+    const FF b = ff_div(rn, FF{rrh, rrl});
+    const FF sr = rn.h > 0.f ? ff_mul(rn, ff_rsqrt(rn)) : FF{0.f, 0.f};
+    beta = ff_to_d(b);
+    beta_t = b.h + b.l;
+    srr = ff_to_d(sr);
+    rnh = rn.h;
+    rnl = rn.l;
+    rnd = ff_to_d(rn);
+  } else {
+    const double rn = ms_sum_d(red, CS, LC, j);
+    beta = rn / rr;
+    beta_t = to_t<T>(beta);
+    srr = sqrt(rn);
+    rnh = rnl = 0.f;
+    rnd = rn;
+  }
+}
+
+// Four consecutive rows of p (held by lanes 4m .. 4m+3) to every CTA of the
+// cluster whose rows of C read them (bit c of mask; this CTA's own copy is a
+// local store): lane 4m gathers the rows by shuffles and issues 16-byte
+// distributed shared-memory stores.
+template <typename T>
+__device__ __forceinline__ void ms_push_p4(T pn, bool push, T* dst_local, cg::cluster_group& cluster, int CS,
+                                           unsigned mask, int crank) {
   const T v1 = __shfl_down_sync(0xffffffffu, pn, 1);
   const T v2 = __shfl_down_sync(0xffffffffu, pn, 2);
   const T v3 = __shfl_down_sync(0xffffffffu, pn, 3);
   if (!push || (threadIdx.x & 3) != 0) return;
   for (int c = 0; c < CS; ++c) {
-    T* dst = cluster.map_shared_rank(dst_local, c);
+    if (!(mask >> c & 1u)) continue;
+    T* dst = c == crank ? dst_local : cluster.map_shared_rank(dst_local, c);
     if constexpr (sizeof(T) == 4) {
       *reinterpret_cast<float4*>(dst) = make_float4(pn, v1, v2, v3);
     } else {
       reinterpret_cast<double2*>(dst)[0] = make_double2(pn, v1);
       reinterpret_cast<double2*>(dst)[1] = make_double2(v2, v3);
     }
+  }
+}
+
+// Four consecutive elements from 16-byte-aligned shared memory.
+template <typename T>
+__device__ __forceinline__ void ms_ld4(const T* src, T (&v)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 x = *reinterpret_cast<const float4*>(src);
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+  } else {
+    const double2 x = reinterpret_cast<const double2*>(src)[0], y = reinterpret_cast<const double2*>(src)[1];
+    v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
   }
 }
 
@@ -171,13 +237,17 @@ constexpr int kMsZetaWarps = 4;   // warps that run the shifted recurrences whil
 //   pfull [LC][dall]   full copy of each chain's base direction p
 //   rv, apv [LC][Rc]   own rows of r and (C + sigma_0 I) p
 //   ahi, alo [LC][Rc]  own rows of sum_q p_q u_q (float-float for FP32)
-//   cw, cz, cb [LC][Qs] this step's p_q alpha^(q), zeta_{k+1}, beta^(q)
+//   pk [LC][Qs][4]     this step's p_q alpha^(q), zeta_{k+1}, beta^(q) and q of the
+//                      i-th active shift of each chain (one 16- or 32-byte load)
+//   wqt, ratt, zt [LC][Qs]  p_q, zeta_{k+1} / zeta_k and zeta_{k+1} in T, for the
+//                      coefficients (which only scale T vectors)
 //   zeta, zprev, delta, wq, res, rat [LC][Qs] (FP64; res = |zeta| ||r||, rat = zeta_{k+1} / zeta_k)
 //   act, itq [LC][Qs], lst [2][LC][Qs] (int): active flags, iteration counts,
 //                      and the active shifts of this step and the next
 //   snnz [Rc] (int)
-//   sval [cap][Rc], scol [cap][Rc]  the CTA's rows of the band of C (if c_smem;
-//                      staged once per problem, read every iteration)
+//   sval [cap][Cs], scol [cap][Cs]  the CTA's rows of the band of C (if c_smem;
+//                      staged once per problem, read every iteration; row
+//                      stride Cs = ms_cstride(Rc))
 //   ps [LC][Qs][Rc]    shifted directions (here, or in the CTA's scratch slice)
 template <typename T, int LC>
 __global__ void __launch_bounds__(kMsThreads, 1)
@@ -195,10 +265,11 @@ __global__ void __launch_bounds__(kMsThreads, 1)
   T* apv = rv + LC * Rc;
   T* ahi = apv + LC * Rc;
   T* alo = ahi + LC * Rc;
-  T* cw = alo + LC * Rc;
-  T* cz = cw + LC * Qs;
-  T* cb = cz + LC * Qs;
-  double* zeta = reinterpret_cast<double*>(cb + LC * Qs);
+  T* pk = alo + LC * Rc;
+  T* wqt = pk + 4 * LC * Qs;
+  T* ratt = wqt + LC * Qs;
+  T* zt = ratt + LC * Qs;
+  double* zeta = reinterpret_cast<double*>(zt + LC * Qs);
   double* zprev = zeta + LC * Qs;
   double* delta = zprev + LC * Qs;
   double* wq = delta + LC * Qs;
@@ -209,26 +280,28 @@ __global__ void __launch_bounds__(kMsThreads, 1)
   int* lst = itq + LC * Qs;
   int* snnz = lst + 2 * LC * Qs;
   T* sval = reinterpret_cast<T*>(snnz + Rc);
-  int32_t* scol = reinterpret_cast<int32_t*>(sval + (c_smem ? (size_t)cap * Rc : 0));
-  T* ps_s = reinterpret_cast<T*>(scol + (c_smem ? (size_t)cap * Rc : 0));
+  const int Cs = ms_cstride(Rc);
+  int32_t* scol = reinterpret_cast<int32_t*>(sval + (c_smem ? (size_t)cap * Cs : 0));
+  T* ps_s = reinterpret_cast<T*>(scol + (c_smem ? (size_t)cap * Cs : 0));
   T* ps_g = ps_scratch ? ps_scratch + (size_t)blockIdx.x * LC * Qs * Rc : nullptr;
 
   __shared__ double s_red_pap[kMsMaxCS * kMsMaxLC];
   __shared__ double s_red_rr[kMsMaxCS * kMsMaxLC];
   __shared__ float s_wff[kMsWarps][kMsMaxLC][2];
   __shared__ double s_wdd[kMsWarps][kMsMaxLC];
-  __shared__ double s_rr[LC], s_alpha[LC], s_aprev[LC], s_bprev[LC], s_beta[LC], s_srr[LC];
+  __shared__ double s_rr[2][LC], s_alpha[LC], s_aprev[LC], s_bprev[LC], s_beta[LC];
   __shared__ double s_bn[LC], s_sig0[LC], s_stop[LC];
-  __shared__ float s_rrh[LC], s_rrl[LC];
+  __shared__ float s_stop_f[LC];
+  __shared__ float s_rrh[2][LC], s_rrl[2][LC];   // r^T r as float-float, this step's and the next
   __shared__ T s_alpha_t[LC], s_beta_t[LC];
   __shared__ int s_live[LC], s_done[LC], s_qc[LC], s_mem[LC], s_k[LC];
   __shared__ int s_nact[2][LC];
   __shared__ int s_cprob;   // problem whose rows of C are staged
+  __shared__ unsigned s_needs[kMsMaxCS];   // bit s of entry c: CTA c's rows read slice s of p
+  __shared__ unsigned s_need, s_pushmask;  // slices this CTA reads; CTAs that read its slice
   if (tid == 0) s_cprob = -1;
 
-  // threads per matvec row: a power of two <= 8 that keeps the CTA busy
-  int sub = 1;
-  while (sub < 8 && Rc * sub * 2 <= kMsThreads) sub <<= 1;
+  const int sub = ms_sub(Rc);
 
   int G = 0;
   for (int p = 0; p < count; ++p) G += (chains_of(tab[p]) + LC - 1) / LC;
@@ -278,10 +351,28 @@ __global__ void __launch_bounds__(kMsThreads, 1)
         for (int idx = tid; idx < cp * Rc; idx += kMsThreads) {
           const int e = idx / Rc, row = idx % Rc;
           if (row < nrows) {
-            sval[idx] = gv[(int64_t)e * d + r0 + row];
-            scol[idx] = pr.oo_col[(int64_t)e * d + r0 + row];
+            sval[e * Cs + row] = gv[(int64_t)e * d + r0 + row];
+            scol[e * Cs + row] = pr.oo_col[(int64_t)e * d + r0 + row];
           }
         }
+      }
+      // which slices of p the own rows of C read, and so which CTAs need this
+      // CTA's slice after each update (on a 1-D band: itself and its neighbours)
+      if (tid == 0) s_need = 1u << crank;
+      __syncthreads();
+      unsigned need = 0;
+      for (int idx = tid; idx < cp * Rc; idx += kMsThreads) {
+        const int e = idx / Rc, row = idx % Rc;
+        if (row < nrows && e < snnz[row]) need |= 1u << (pr.oo_col[(int64_t)e * d + r0 + row] / Rc);
+      }
+      if (need) atomicOr(&s_need, need);
+      __syncthreads();
+      if (tid < CS) cluster.map_shared_rank(s_needs, tid)[crank] = s_need;
+      cluster.sync();
+      if (tid == 0) {
+        unsigned m = 0;
+        for (int c = 0; c < CS; ++c) m |= (s_needs[c] >> crank & 1u) << c;
+        s_pushmask = m;
       }
     }
     // p_0 = b for every chain, in full: b = R^-1/2 w^(i), or R^-1/2 (y - H mu)
@@ -316,16 +407,17 @@ __global__ void __launch_bounds__(kMsThreads, 1)
       double rr;
       if constexpr (sizeof(T) == 4) {
         const FF f = ms_sum_ff(s_red_rr, CS, LC, tid);
-        s_rrh[tid] = f.h;
-        s_rrl[tid] = f.l;
+        s_rrh[0][tid] = f.h;
+        s_rrl[0][tid] = f.l;
         rr = ff_to_d(f);
       } else {
         rr = ms_sum_d(s_red_rr, CS, LC, tid);
       }
       const double bn = sqrt(rr);
-      s_rr[tid] = rr;
+      s_rr[0][tid] = rr;
       s_bn[tid] = bn;
       s_stop[tid] = (fixed ? 1e-30 : pr.tol) * bn;
+      s_stop_f[tid] = (float)s_stop[tid];
       const bool on = s_live[tid] && bn > 0.0;
       s_done[tid] = !on;
       s_nact[0][tid] = on ? s_qc[tid] : 0;
@@ -343,6 +435,7 @@ __global__ void __launch_bounds__(kMsThreads, 1)
       zprev[idx] = 1.0;
       delta[idx] = sg - s_sig0[j];
       wq[idx] = w;
+      wqt[idx] = to_t<T>(w);
       res[idx] = (has && s_bn[j] > 0.0) ? s_bn[j] : 0.0;
       act[idx] = has && !s_done[j];
       itq[idx] = 0;
@@ -355,6 +448,7 @@ __global__ void __launch_bounds__(kMsThreads, 1)
     for (int j = 0; j < LC; ++j) sg0[j] = to_t<T>(s_sig0[j]);
     const T* __restrict__ cval = reinterpret_cast<const T*>(pr.oo_val);
     const int32_t* __restrict__ ccol = pr.oo_col;
+    const unsigned pushmask = s_pushmask;
     int buf = 0;
 
     for (;;) {
@@ -378,10 +472,10 @@ __global__ void __launch_bounds__(kMsThreads, 1)
         for (int j = 0; j < LC; ++j) y[j] = T(0);
         const int nnz = valid ? snnz[rl] : 0;
         if (c_smem) {
-#pragma unroll 4
+#pragma unroll 8
           for (int e = part; e < nnz; e += sub) {
-            const T v = sval[e * Rc + rl];
-            const int c = scol[e * Rc + rl];
+            const T v = sval[e * Cs + rl];
+            const int c = scol[e * Cs + rl];
 #pragma unroll
             for (int j = 0; j < LC; ++j) y[j] = fma(v, pfull[(size_t)j * dall + c], y[j]);
           }
@@ -418,7 +512,7 @@ __global__ void __launch_bounds__(kMsThreads, 1)
           const FF pq = ms_sum_ff(s_red_pap, CS, LC, tid);
           bad = !(pq.h > 0.f) || !isfinite(pq.h);
           if (!bad) {
-            const FF a = ff_div(FF{s_rrh[tid], s_rrl[tid]}, pq);
+            const FF a = ff_div(FF{s_rrh[buf][tid], s_rrl[buf][tid]}, pq);
             al = ff_to_d(a);
             s_alpha_t[tid] = a.h + a.l;
           }
@@ -426,7 +520,7 @@ __global__ void __launch_bounds__(kMsThreads, 1)
           const double pq = ms_sum_d(s_red_pap, CS, LC, tid);
           bad = !(pq > 0.0) || !isfinite(pq);
           if (!bad) {
-            al = s_rr[tid] / pq;
+            al = s_rr[buf][tid] / pq;
             s_alpha_t[tid] = to_t<T>(al);
           }
         }
@@ -443,7 +537,7 @@ __global__ void __launch_bounds__(kMsThreads, 1)
 
       DotAcc<T> rra[LC];
       if (warp < kMsZetaWarps) {
-        // zeta_{k+1} / zeta_k and p_q alpha^(q) of every active shift (FP64)
+        // zeta_{k+1} / zeta_k of every active shift (FP64)
         int tot = 0;
 #pragma unroll
         for (int j = 0; j < LC; ++j) tot += (step >> j & 1u) ? nact[j] : 0;
@@ -456,8 +550,8 @@ __global__ void __launch_bounds__(kMsThreads, 1)
           const double ratio = zm * ap / (al * bp * (zm - z0) + zm * ap * (1.0 + delta[idx] * al));
           const double z1 = z0 * ratio;
           rat[idx] = ratio;
-          cw[idx] = to_t<T>(wq[idx] * al * ratio);
-          cz[idx] = to_t<T>(z1);
+          ratt[idx] = to_t<T>(ratio);
+          zt[idx] = to_t<T>(z1);
           zprev[idx] = z0;
           zeta[idx] = z1;
         }
@@ -482,54 +576,69 @@ __global__ void __launch_bounds__(kMsThreads, 1)
       }
       ms_push_partials<T, LC>(rra, s_red_rr, s_wff, s_wdd, cluster, CS, crank);   // (2)
 
-      // beta = r'^T r' / r^T r and ||r'||
-      if (tid < LC && (step >> tid & 1u)) {
-        if constexpr (sizeof(T) == 4) {
-          const FF rn = ms_sum_ff(s_red_rr, CS, LC, tid);
-          const FF b = ff_div(rn, FF{s_rrh[tid], s_rrl[tid]});
-          const FF sr = rn.h > 0.f ? ff_mul(rn, ff_rsqrt(rn)) : FF{0.f, 0.f};
-          s_beta[tid] = ff_to_d(b);
-          s_beta_t[tid] = b.h + b.l;
-          s_srr[tid] = ff_to_d(sr);
-          s_rrh[tid] = rn.h;
-          s_rrl[tid] = rn.l;
-          s_rr[tid] = ff_to_d(rn);
-        } else {
-          const double rrn = ms_sum_d(s_red_rr, CS, LC, tid);
-          const double b = rrn / s_rr[tid];
-          s_beta[tid] = b;
-          s_beta_t[tid] = to_t<T>(b);
-          s_srr[tid] = sqrt(rrn);
-          s_rr[tid] = rrn;
-        }
-      }
-      __syncthreads();
-
-      // beta^(q), the stopping test and the iteration count of every active shift
+      // beta = r'^T r' / r^T r and ||r'||, formed from the same partials by the
+      // chain's owner (lane 0 of warp kMsWarps - 1 - j, which has no shift to
+      // update while there are at most 32 (kMsWarps - LC) active shifts) and by
+      // every thread of an active shift; then the packed coefficients, the
+      // stopping test and the iteration count of every active shift
       {
+        const int nb = buf ^ 1;
+        const int jo = kMsWarps - 1 - warp;
+        if (lane == 0 && jo >= 0 && jo < LC && (step >> jo & 1u)) {
+          double bd, srr;
+          T bt;
+          ms_beta<T>(s_red_rr, CS, LC, jo, s_rrh[buf][jo], s_rrl[buf][jo], s_rr[buf][jo], bd, bt, srr,
+                     s_rrh[nb][jo], s_rrl[nb][jo], s_rr[nb][jo]);
+          s_beta[jo] = bd;
+          s_beta_t[jo] = bt;
+        }
         int tot = 0;
 #pragma unroll
         for (int j = 0; j < LC; ++j) tot += (step >> j & 1u) ? nact[j] : 0;
         for (int t = tid; t < tot; t += kMsThreads) {
           int off;
           const int j = ms_locate<LC>(t, step, nact, off);
-          const int idx = j * Qs + lcur[j * Qs + off];
-          const double ratio = rat[idx];
-          cb[idx] = to_t<T>(s_beta[j] * ratio * ratio);
+          const int q = lcur[j * Qs + off], idx = j * Qs + q;
+          T* e = pk + 4 * (j * Qs + off);
           itq[idx] = s_k[j] + 1;
-          const double rq = fabs(zeta[idx]) * s_srr[j];
-          res[idx] = rq;
-          if (!(rq > s_stop[j])) act[idx] = 0;
+          if constexpr (sizeof(T) == 4) {
+            // FP32 coefficients of FP32 vectors: no FP64 instruction here
+            const FF rn = ms_sum_ff(s_red_rr, CS, LC, j);
+            const FF b = ff_div(rn, FF{s_rrh[buf][j], s_rrl[buf][j]});
+            const FF sr = rn.h > 0.f ? ff_mul(rn, ff_rsqrt(rn)) : FF{0.f, 0.f};
+            const float bt = b.h + b.l, ra = ratt[idx];
+            e[0] = wqt[idx] * s_alpha_t[j] * ra;
+            e[1] = zt[idx];
+            e[2] = bt * ra * ra;
+            e[3] = ms_q_bits<T>(q);
+            const float rq = fabsf(zt[idx]) * (sr.h + sr.l);
+            res[idx] = (double)rq;
+            if (!(rq > s_stop_f[j])) act[idx] = 0;
+          } else {
+            double bd, srr, rd;
+            T bt;
+            float rh, rl;
+            ms_beta<T>(s_red_rr, CS, LC, j, s_rrh[buf][j], s_rrl[buf][j], s_rr[buf][j], bd, bt, srr, rh, rl, rd);
+            const double ratio = rat[idx];
+            e[0] = to_t<T>(wq[idx] * s_alpha[j] * ratio);
+            e[1] = to_t<T>(zeta[idx]);
+            e[2] = to_t<T>(bd * ratio * ratio);
+            e[3] = ms_q_bits<T>(q);
+            const double rq = fabs(zeta[idx]) * srr;
+            res[idx] = rq;
+            if (!(rq > s_stop[j])) act[idx] = 0;
+          }
         }
       }
       __syncthreads();
 
-      // warp 0: next step's active lists and the chain bookkeeping (read again
-      // only after barrier (3)); everyone else goes straight to the update
-      if (warp == 0) {
-        const int nb = buf ^ 1;
-        for (int j = 0; j < LC; ++j) {
-          if (!(step >> j & 1u)) continue;
+      // next step's active lists and the chain bookkeeping (read again only
+      // after barrier (3)): chain j by warp kMsWarps - 1 - j, the warps with the
+      // least update work; everyone else goes straight to the update
+      {
+        const int j = kMsWarps - 1 - warp;
+        if (j >= 0 && j < LC && (step >> j & 1u)) {
+          const int nb = buf ^ 1;
           int n = 0;
           for (int q0 = 0; q0 < s_qc[j]; q0 += 32) {
             const int q = q0 + lane;
@@ -563,28 +672,28 @@ __global__ void __launch_bounds__(kMsThreads, 1)
             const T rn = rv[idx];
             T sum = T(0);
             T* pc = psb + (size_t)j * Qs * Rc + row;
-            const int* lj = lcur + j * Qs;
+            const T* ej = pk + 4 * j * Qs;
             const int n = nact[j];
             int i = 0;
             for (; i + 4 <= n; i += 4) {
-              const int q0 = lj[i], q1 = lj[i + 1], q2 = lj[i + 2], q3 = lj[i + 3];
-              const T p0 = pc[(size_t)q0 * Rc], p1 = pc[(size_t)q1 * Rc];
-              const T p2 = pc[(size_t)q2 * Rc], p3 = pc[(size_t)q3 * Rc];
-              const int i0 = j * Qs + q0, i1 = j * Qs + q1, i2 = j * Qs + q2, i3 = j * Qs + q3;
-              sum = fma(cw[i0], p0, sum);
-              sum = fma(cw[i1], p1, sum);
-              sum = fma(cw[i2], p2, sum);
-              sum = fma(cw[i3], p3, sum);
-              pc[(size_t)q0 * Rc] = fma(cz[i0], rn, cb[i0] * p0);
-              pc[(size_t)q1 * Rc] = fma(cz[i1], rn, cb[i1] * p1);
-              pc[(size_t)q2 * Rc] = fma(cz[i2], rn, cb[i2] * p2);
-              pc[(size_t)q3 * Rc] = fma(cz[i3], rn, cb[i3] * p3);
+              T c[4][4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) ms_ld4(ej + 4 * (i + u), c[u]);
+              T po[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) po[u] = pc[(size_t)ms_q_of(c[u][3]) * Rc];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                sum = fma(c[u][0], po[u], sum);
+                pc[(size_t)ms_q_of(c[u][3]) * Rc] = fma(c[u][1], rn, c[u][2] * po[u]);
+              }
             }
             for (; i < n; ++i) {
-              const int q = lj[i], ci = j * Qs + q;
-              const T po = pc[(size_t)q * Rc];
-              sum = fma(cw[ci], po, sum);
-              pc[(size_t)q * Rc] = fma(cz[ci], rn, cb[ci] * po);
+              T c[4];
+              ms_ld4(ej + 4 * i, c);
+              const T po = pc[(size_t)ms_q_of(c[3]) * Rc];
+              sum = fma(c[0], po, sum);
+              pc[(size_t)ms_q_of(c[3]) * Rc] = fma(c[1], rn, c[2] * po);
             }
             if constexpr (sizeof(T) == 4) {
               float s, e;
@@ -600,7 +709,7 @@ __global__ void __launch_bounds__(kMsThreads, 1)
               if (jj == j) bt = beta_t[jj];
             pn = fma(bt, pfull[(size_t)j * dall + r0 + row], rn);
           }
-          ms_push_p4<T>(pn, st, pfull + (size_t)j * dall + r0 + row, cluster, CS);
+          ms_push_p4<T>(pn, st, pfull + (size_t)j * dall + r0 + row, cluster, CS, pushmask, crank);
         }
       };
       if (ps_smem) update(ps_s);
