@@ -146,6 +146,8 @@ __device__ __forceinline__ double ms_sum_d(const double* red, int CS, int LC, in
 }
 __device__ __forceinline__ double ff_to_d(FF a) { return (double)a.h + (double)a.l; }
 
+__device__ __forceinline__ FF ff_add(FF a, FF b) { return ff_sub(a, FF{-b.h, -b.l}); }
+
 // A shift index carried in the packed coefficient entry as the bits of a T.
 template <typename T>
 __device__ __forceinline__ T ms_q_bits(int q) {
@@ -182,29 +184,6 @@ __device__ __forceinline__ void ms_beta(const double* red, int CS, int LC, int j
   }
 }
 
-// Four consecutive rows of p (held by lanes 4m .. 4m+3) to every CTA of the
-// cluster whose rows of C read them (bit c of mask; this CTA's own copy is a
-// local store): lane 4m gathers the rows by shuffles and issues 16-byte
-// distributed shared-memory stores.
-template <typename T>
-__device__ __forceinline__ void ms_push_p4(T pn, bool push, T* dst_local, cg::cluster_group& cluster, int CS,
-                                           unsigned mask, int crank) {
-  const T v1 = __shfl_down_sync(0xffffffffu, pn, 1);
-  const T v2 = __shfl_down_sync(0xffffffffu, pn, 2);
-  const T v3 = __shfl_down_sync(0xffffffffu, pn, 3);
-  if (!push || (threadIdx.x & 3) != 0) return;
-  for (int c = 0; c < CS; ++c) {
-    if (!(mask >> c & 1u)) continue;
-    T* dst = c == crank ? dst_local : cluster.map_shared_rank(dst_local, c);
-    if constexpr (sizeof(T) == 4) {
-      *reinterpret_cast<float4*>(dst) = make_float4(pn, v1, v2, v3);
-    } else {
-      reinterpret_cast<double2*>(dst)[0] = make_double2(pn, v1);
-      reinterpret_cast<double2*>(dst)[1] = make_double2(v2, v3);
-    }
-  }
-}
-
 // Four consecutive elements from 16-byte-aligned shared memory.
 template <typename T>
 __device__ __forceinline__ void ms_ld4(const T* src, T (&v)[4]) {
@@ -214,6 +193,17 @@ __device__ __forceinline__ void ms_ld4(const T* src, T (&v)[4]) {
   } else {
     const double2 x = reinterpret_cast<const double2*>(src)[0], y = reinterpret_cast<const double2*>(src)[1];
     v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
+  }
+}
+
+// Four consecutive elements to 16-byte-aligned shared (or global) memory.
+template <typename T>
+__device__ __forceinline__ void ms_st4(T* dst, const T (&v)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+    reinterpret_cast<double2*>(dst)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(dst)[1] = make_double2(v[2], v[3]);
   }
 }
 
@@ -290,6 +280,9 @@ __global__ void __launch_bounds__(kMsThreads, 1)
   __shared__ float s_wff[kMsWarps][kMsMaxLC][2];
   __shared__ double s_wdd[kMsWarps][kMsMaxLC];
   __shared__ double s_rr[2][LC], s_alpha[LC], s_aprev[LC], s_bprev[LC], s_beta[LC];
+  // the FP32 path keeps the CG scalars of the shifted recurrences as
+  // float-float pairs (about 48 bits) and issues no FP64 instruction per step
+  __shared__ float2 s_alpha2[LC], s_aprev2[LC], s_bprev2[LC], s_beta2[LC];
   __shared__ double s_bn[LC], s_sig0[LC], s_stop[LC];
   __shared__ float s_stop_f[LC];
   __shared__ float s_rrh[2][LC], s_rrl[2][LC];   // r^T r as float-float, this step's and the next
@@ -338,6 +331,8 @@ __global__ void __launch_bounds__(kMsThreads, 1)
       s_sig0[tid] = sg0;
       s_aprev[tid] = 1.0;
       s_bprev[tid] = 0.0;
+      s_aprev2[tid] = make_float2(1.f, 0.f);
+      s_bprev2[tid] = make_float2(0.f, 0.f);
       s_k[tid] = 0;
     }
     __syncthreads();
@@ -431,9 +426,16 @@ __global__ void __launch_bounds__(kMsThreads, 1)
         sg = pr.s[q] + 1.0;
         w = pr.p[q];
       }
-      zeta[idx] = 1.0;
-      zprev[idx] = 1.0;
-      delta[idx] = sg - s_sig0[j];
+      if constexpr (sizeof(T) == 4) {
+        const FF dl = ff_from(sg - s_sig0[j]);
+        reinterpret_cast<float2*>(zeta)[idx] = make_float2(1.f, 0.f);
+        reinterpret_cast<float2*>(zprev)[idx] = make_float2(1.f, 0.f);
+        reinterpret_cast<float2*>(delta)[idx] = make_float2(dl.h, dl.l);
+      } else {
+        zeta[idx] = 1.0;
+        zprev[idx] = 1.0;
+        delta[idx] = sg - s_sig0[j];
+      }
       wq[idx] = w;
       wqt[idx] = to_t<T>(w);
       res[idx] = (has && s_bn[j] > 0.0) ? s_bn[j] : 0.0;
@@ -513,7 +515,7 @@ __global__ void __launch_bounds__(kMsThreads, 1)
           bad = !(pq.h > 0.f) || !isfinite(pq.h);
           if (!bad) {
             const FF a = ff_div(FF{s_rrh[buf][tid], s_rrl[buf][tid]}, pq);
-            al = ff_to_d(a);
+            s_alpha2[tid] = make_float2(a.h, a.l);
             s_alpha_t[tid] = a.h + a.l;
           }
         } else {
@@ -537,7 +539,8 @@ __global__ void __launch_bounds__(kMsThreads, 1)
 
       DotAcc<T> rra[LC];
       if (warp < kMsZetaWarps) {
-        // zeta_{k+1} / zeta_k of every active shift (FP64)
+        // zeta_{k+1} / zeta_k of every active shift (FP64, or float-float on
+        // the FP32 path)
         int tot = 0;
 #pragma unroll
         for (int j = 0; j < LC; ++j) tot += (step >> j & 1u) ? nact[j] : 0;
@@ -545,15 +548,33 @@ __global__ void __launch_bounds__(kMsThreads, 1)
           int off;
           const int j = ms_locate<LC>(t, step, nact, off);
           const int idx = j * Qs + lcur[j * Qs + off];
-          const double z0 = zeta[idx], zm = zprev[idx];
-          const double al = s_alpha[j], ap = s_aprev[j], bp = s_bprev[j];
-          const double ratio = zm * ap / (al * bp * (zm - z0) + zm * ap * (1.0 + delta[idx] * al));
-          const double z1 = z0 * ratio;
-          rat[idx] = ratio;
-          ratt[idx] = to_t<T>(ratio);
-          zt[idx] = to_t<T>(z1);
-          zprev[idx] = z0;
-          zeta[idx] = z1;
+          if constexpr (sizeof(T) == 4) {
+            const float2 z0v = reinterpret_cast<const float2*>(zeta)[idx];
+            const float2 zmv = reinterpret_cast<const float2*>(zprev)[idx];
+            const float2 dv = reinterpret_cast<const float2*>(delta)[idx];
+            const FF z0{z0v.x, z0v.y}, zm{zmv.x, zmv.y}, dl{dv.x, dv.y};
+            const FF al{s_alpha2[j].x, s_alpha2[j].y}, ap{s_aprev2[j].x, s_aprev2[j].y};
+            const FF bp{s_bprev2[j].x, s_bprev2[j].y};
+            const FF A = ff_mul(zm, ap);
+            const FF den = ff_add(ff_mul(ff_mul(al, bp), ff_sub(zm, z0)),
+                                  ff_mul(A, ff_add(FF{1.f, 0.f}, ff_mul(dl, al))));
+            const FF ratio = ff_div(A, den);
+            const FF z1 = ff_mul(z0, ratio);
+            ratt[idx] = ratio.h + ratio.l;
+            zt[idx] = z1.h + z1.l;
+            reinterpret_cast<float2*>(zprev)[idx] = z0v;
+            reinterpret_cast<float2*>(zeta)[idx] = make_float2(z1.h, z1.l);
+          } else {
+            const double z0 = zeta[idx], zm = zprev[idx];
+            const double al = s_alpha[j], ap = s_aprev[j], bp = s_bprev[j];
+            const double ratio = zm * ap / (al * bp * (zm - z0) + zm * ap * (1.0 + delta[idx] * al));
+            const double z1 = z0 * ratio;
+            rat[idx] = ratio;
+            ratt[idx] = to_t<T>(ratio);
+            zt[idx] = to_t<T>(z1);
+            zprev[idx] = z0;
+            zeta[idx] = z1;
+          }
         }
       } else {
         // r <- r - alpha q and the partials of r^T r
@@ -585,12 +606,21 @@ __global__ void __launch_bounds__(kMsThreads, 1)
         const int nb = buf ^ 1;
         const int jo = kMsWarps - 1 - warp;
         if (lane == 0 && jo >= 0 && jo < LC && (step >> jo & 1u)) {
-          double bd, srr;
-          T bt;
-          ms_beta<T>(s_red_rr, CS, LC, jo, s_rrh[buf][jo], s_rrl[buf][jo], s_rr[buf][jo], bd, bt, srr,
-                     s_rrh[nb][jo], s_rrl[nb][jo], s_rr[nb][jo]);
-          s_beta[jo] = bd;
-          s_beta_t[jo] = bt;
+          if constexpr (sizeof(T) == 4) {
+            const FF rn = ms_sum_ff(s_red_rr, CS, LC, jo);
+            const FF b = ff_div(rn, FF{s_rrh[buf][jo], s_rrl[buf][jo]});
+            s_beta2[jo] = make_float2(b.h, b.l);
+            s_beta_t[jo] = b.h + b.l;
+            s_rrh[nb][jo] = rn.h;
+            s_rrl[nb][jo] = rn.l;
+          } else {
+            double bd, srr;
+            T bt;
+            ms_beta<T>(s_red_rr, CS, LC, jo, s_rrh[buf][jo], s_rrl[buf][jo], s_rr[buf][jo], bd, bt, srr,
+                       s_rrh[nb][jo], s_rrl[nb][jo], s_rr[nb][jo]);
+            s_beta[jo] = bd;
+            s_beta_t[jo] = bt;
+          }
         }
         int tot = 0;
 #pragma unroll
@@ -651,6 +681,8 @@ __global__ void __launch_bounds__(kMsThreads, 1)
             s_nact[nb][j] = n;
             s_aprev[j] = s_alpha[j];
             s_bprev[j] = s_beta[j];
+            s_aprev2[j] = s_alpha2[j];
+            s_bprev2[j] = s_beta2[j];
             s_k[j] += 1;
             if (n == 0 || s_k[j] >= limit) s_done[j] = 1;
           }
@@ -661,55 +693,77 @@ __global__ void __launch_bounds__(kMsThreads, 1)
       T beta_t[LC];
 #pragma unroll
       for (int j = 0; j < LC; ++j) beta_t[j] = s_beta_t[j];
+      // four consecutive rows of one chain per thread: 16-byte (FP32) accesses
+      // to r, the shifted directions, the quadrature sums and p, four
+      // independent FMA chains, and p pushed without a gather
       auto update = [&](T* psb) {
-        for (int base = 0; base < LC * Rc; base += kMsThreads) {
-          const int idx = base + tid;
-          const bool in = idx < LC * Rc;
-          const int j = in ? idx / Rc : 0, row = in ? idx % Rc : 0;
-          const bool st = in && (step >> j & 1u);
-          T pn = T(0);
-          if (st) {
-            const T rn = rv[idx];
-            T sum = T(0);
-            T* pc = psb + (size_t)j * Qs * Rc + row;
-            const T* ej = pk + 4 * j * Qs;
-            const int n = nact[j];
-            int i = 0;
-            for (; i + 4 <= n; i += 4) {
-              T c[4][4];
+        const int R4 = Rc / 4;
+        for (int it = tid; it < LC * R4; it += kMsThreads) {
+          const int j = it / R4, row = (it % R4) * 4;
+          if (!(step >> j & 1u)) continue;
+          const int idx = j * Rc + row;
+          T rn[4], sum[4] = {T(0), T(0), T(0), T(0)};
+          ms_ld4(rv + idx, rn);
+          T* pc = psb + (size_t)j * Qs * Rc + row;
+          const T* ej = pk + 4 * j * Qs;
+          const int n = nact[j];
+          int i = 0;
+          for (; i + 2 <= n; i += 2) {
+            T c0[4], c1[4], p0[4], p1[4];
+            ms_ld4(ej + 4 * i, c0);
+            ms_ld4(ej + 4 * i + 4, c1);
+            T* a0 = pc + (size_t)ms_q_of(c0[3]) * Rc;
+            T* a1 = pc + (size_t)ms_q_of(c1[3]) * Rc;
+            ms_ld4(a0, p0);
+            ms_ld4(a1, p1);
 #pragma unroll
-              for (int u = 0; u < 4; ++u) ms_ld4(ej + 4 * (i + u), c[u]);
-              T po[4];
-#pragma unroll
-              for (int u = 0; u < 4; ++u) po[u] = pc[(size_t)ms_q_of(c[u][3]) * Rc];
-#pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                sum = fma(c[u][0], po[u], sum);
-                pc[(size_t)ms_q_of(c[u][3]) * Rc] = fma(c[u][1], rn, c[u][2] * po[u]);
-              }
+            for (int r = 0; r < 4; ++r) {
+              sum[r] = fma(c0[0], p0[r], sum[r]);
+              sum[r] = fma(c1[0], p1[r], sum[r]);
+              p0[r] = fma(c0[1], rn[r], c0[2] * p0[r]);
+              p1[r] = fma(c1[1], rn[r], c1[2] * p1[r]);
             }
-            for (; i < n; ++i) {
-              T c[4];
-              ms_ld4(ej + 4 * i, c);
-              const T po = pc[(size_t)ms_q_of(c[3]) * Rc];
-              sum = fma(c[0], po, sum);
-              pc[(size_t)ms_q_of(c[3]) * Rc] = fma(c[1], rn, c[2] * po);
-            }
-            if constexpr (sizeof(T) == 4) {
-              float s, e;
-              two_sum(ahi[idx], sum, s, e);
-              ahi[idx] = s;
-              alo[idx] += e;
-            } else {
-              ahi[idx] += sum;
-            }
-            T bt = T(0);
-#pragma unroll
-            for (int jj = 0; jj < LC; ++jj)
-              if (jj == j) bt = beta_t[jj];
-            pn = fma(bt, pfull[(size_t)j * dall + r0 + row], rn);
+            ms_st4(a0, p0);
+            ms_st4(a1, p1);
           }
-          ms_push_p4<T>(pn, st, pfull + (size_t)j * dall + r0 + row, cluster, CS, pushmask, crank);
+          if (i < n) {
+            T c0[4], p0[4];
+            ms_ld4(ej + 4 * i, c0);
+            T* a0 = pc + (size_t)ms_q_of(c0[3]) * Rc;
+            ms_ld4(a0, p0);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+              sum[r] = fma(c0[0], p0[r], sum[r]);
+              p0[r] = fma(c0[1], rn[r], c0[2] * p0[r]);
+            }
+            ms_st4(a0, p0);
+          }
+          T hi[4], lo[4], pn[4];
+          ms_ld4(ahi + idx, hi);
+          ms_ld4(alo + idx, lo);
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            if constexpr (sizeof(T) == 4) {
+              float sh, e;
+              two_sum(hi[r], sum[r], sh, e);
+              hi[r] = sh;
+              lo[r] += e;
+            } else {
+              hi[r] += sum[r];
+            }
+          }
+          ms_st4(ahi + idx, hi);
+          ms_st4(alo + idx, lo);
+          T bt = T(0);
+#pragma unroll
+          for (int jj = 0; jj < LC; ++jj)
+            if (jj == j) bt = beta_t[jj];
+          T* pf = pfull + (size_t)j * dall + r0 + row;
+          ms_ld4(pf, pn);
+#pragma unroll
+          for (int r = 0; r < 4; ++r) pn[r] = fma(bt, pn[r], rn[r]);
+          for (int c = 0; c < CS; ++c)
+            if (pushmask >> c & 1u) ms_st4(c == crank ? pf : cluster.map_shared_rank(pf, c), pn);
         }
       };
       if (ps_smem) update(ps_s);
