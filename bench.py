@@ -39,6 +39,9 @@ TRAIN_SEEDS = (11, 12, 13)
 # learned correction, from the ncu capture summarised in
 # profiles/k_pcg_band1d_gauss1d_n8192_N40_d1024_Q32_fp32_learned.md; set to None when the kernel changes.
 PCG_DRAM_BYTES = 1458176
+# The same for one k_mscg launch (multi-shift CG, --solver multishift); None
+# until an ncu capture of the current kernel is summarised in profiles/.
+MSCG_DRAM_BYTES = None
 
 
 def _dist():
@@ -137,7 +140,8 @@ def run_ours(args):
     cap = max(max_oo, max_xo)
     prec = B.PRECISION_FP32 if args.precision == "fp32" else B.PRECISION_FP64
     tol = TOL_MIXED if prec == B.PRECISION_FP32 else args.fp64_tol
-    use_learned = args.preconditioner == "learned" and prec == B.PRECISION_FP32
+    multishift = args.solver == "multishift"
+    use_learned = args.preconditioner == "learned" and prec == B.PRECISION_FP32 and not multishift
     theta, cutoff, learn_info = None, 0.0, None
     if use_learned:
         from paper_2503_00253_gb300 import learned
@@ -148,11 +152,12 @@ def run_ours(args):
         learn_info = {"train_seeds": list(TRAIN_SEEDS), "fit_s": time.perf_counter() - t0,
                       "loss_first": float(hist[0]), "loss_last": float(hist[-1]), "max_shift": cutoff}
     opts = B.make_options(precision=prec, ritz_rank=RITZ, max_neighbors=cap, learned_model=theta,
-                          learned_max_shift=cutoff)
+                          learned_max_shift=cutoff,
+                          solver=B.SOLVER_MULTISHIFT if multishift else B.SOLVER_PCG)
     # native autotuner (untimed): cluster size, power iterations and oversampling of the eigensolver,
     # the settings that do not change the converged answer
     tune_info = None
-    if args.autotune:
+    if args.autotune and not multishift:
         t0 = time.perf_counter()
         best = B.autotune([dict(grid=pr.grid, X=X, obs_idx=obs, y=y, R=R, Q=pr.Q, tol=tol, max_oo=max_oo,
                                 max_xo=max_xo)], opts)
@@ -194,7 +199,7 @@ def run_ours(args):
     it_sys = torch.zeros(1 + pr.Q * N, dtype=torch.int32, device=dev)
     o_it = B.make_options(precision=prec, ritz_rank=RITZ, max_neighbors=cap, learned_model=theta,
                           learned_max_shift=cutoff, system_iters=it_sys, oversample=int(opts.oversample),
-                          power_iters=int(opts.power_iters))
+                          power_iters=int(opts.power_iters), solver=int(opts.solver))
     o_it.cluster_size = opts.cluster_size
     B.info_esrf_analysis(pr.grid, X, obs, y, R, pr.Q, tol, o_it, ws=wsp, mu_a=mu_a, A_a=A_a, stats=False,
                          stream=stream)
@@ -310,10 +315,11 @@ def run_ours(args):
     comparators = {}
     if rank == 0 and prec == B.PRECISION_FP32 and args.fp64_steps > 0:
         cases = [("fp64_pcg", B.PRECISION_FP64, B.SOLVER_PCG)]
-        if use_learned:
+        if use_learned or multishift:
             cases.insert(0, ("lmp_fp32", B.PRECISION_FP32, B.SOLVER_PCG))
-        # one unpreconditioned CG run per member for all shifts (Sec. 3.3)
-        cases.insert(0, ("multishift_fp32", B.PRECISION_FP32, B.SOLVER_MULTISHIFT))
+        if not multishift:
+            # one unpreconditioned CG run per member for all shifts (Sec. 3.3)
+            cases.insert(0, ("multishift_fp32", B.PRECISION_FP32, B.SOLVER_MULTISHIFT))
         for key, pc, sv in cases:
             oc = B.make_options(precision=pc, ritz_rank=RITZ, max_neighbors=cap, solver=sv)
             needc = B.library().info_esrf_workspace_size(ctypes.byref(g), N, d, pr.Q, ctypes.byref(oc))
@@ -390,19 +396,30 @@ def run_ours(args):
     #   + 68 where the learned term is active (a z, 33-tap S^T S r, add)
     flops_row = 2 * nnz_C / d + 2 + 8 * RITZ + 10
     pcg_flops = d * float(np.sum(it_sys * (flops_row + 68.0 * learned_sys)))
+    kernel = "k_pcg_band1d (cluster-resident persistent batched shifted PCG)"
+    traffic = PCG_DRAM_BYTES if (prec == B.PRECISION_FP32 and use_learned) else None
+    if multishift:
+        # multi-shift CG: per iteration of a chain (one member, or the mean)
+        # 2 nnz(C) + 2 d (matvec and base shift) + 8 d (r and p updates, two dots),
+        # and per row of every active shift 5 (its direction and the weighted sum)
+        chain_it = np.concatenate([[it_sys[0]], it_sys[1:].reshape(pr.Q, N).max(axis=0)])
+        pcg_flops = float(np.sum(chain_it)) * (2.0 * nnz_C + 10.0 * d) + 5.0 * d * float(np.sum(it_sys))
+        kernel = "k_mscg (cluster-resident multi-shift CG, one Krylov run per member for all shifts)"
+        traffic = MSCG_DRAM_BYTES if prec == B.PRECISION_FP32 else None
     pcg_ms_mean = statistics.mean(pcg_ms)
     achieved = pcg_flops / (pcg_ms_mean * 1e-3) / 1e12
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     max_mhz = clocks.get("sm_max_mhz") or 2070.0
     peak = sms * 128 * 2 * max_mhz * 1e6 / 1e12
-    traffic = PCG_DRAM_BYTES if (prec == B.PRECISION_FP32 and use_learned) else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if prec == B.PRECISION_FP32 else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "N": N, "d": d, "Q": pr.Q, "systems": st["n_systems"],
                    "precision": "fp32 bulk, fp64 scalars and quadrature sum" if prec else "fp64",
-                   "preconditioner": "LMP + learned correction" if use_learned else "LMP",
+                   "preconditioner": ("none (multi-shift CG, Sec. 3.3)" if multishift else
+                                      "LMP + learned correction" if use_learned else "LMP"),
+                   "solver": args.solver,
                    "tol": tol, "ritz_rank": RITZ, "band_nnz": nnz_C, "l2": "flushed between steps (512 MB write)",
                    "replicas": ws, "launch": "cuda graph of the analysis call" if graph is not None else
                    "direct call", **({"graph_error": graph_err} if graph_err else {})},
@@ -410,7 +427,7 @@ def run_ours(args):
         "e2e": {"value": replicas.whole_job_rate(args.steps, ws, e2e_total), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
-        "roofline": {"bound": "alu", "kernel": "k_pcg_band1d (cluster-resident persistent batched shifted PCG)",
+        "roofline": {"bound": "alu", "kernel": kernel,
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
                      "fma_probe_tflops": probe32 / 1e12, "pcg_ms": pcg_ms_mean,
@@ -451,6 +468,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--preconditioner", default="learned", choices=["learned", "lmp"])
+    ap.add_argument("--solver", default="pcg", choices=["pcg", "multishift"],
+                    help="pcg: one PCG run per shifted system (the headline); multishift: one CG run per member "
+                         "for all shifts (Sec. 3.3)")
     ap.add_argument("--graph", type=int, default=1, help="replay the analysis as a CUDA graph (0: direct calls)")
     ap.add_argument("--autotune", type=int, default=1, help="run the native autotuner before the timed region")
     ap.add_argument("--fp64-tol", type=float, default=1e-12)

@@ -485,8 +485,8 @@ void launch_count_neighbours(const GridDev& g, const int64_t* obs, int64_t d, in
 // a2: quadrature (App. D).  Elliptic rule with modulus g = sqrt(ell/(1+ell)):
 //   s_q = sc(u_q | g)^2,  p_q = (2 K / (pi Q)) dn(u_q | g),  u_q = (q - 1/2) K / Q,
 // which is r_q / (s_q + 1) with r_q = (2K/(pi Q)) nc dc (d sc/du = dc nc and
-// sc^2 + 1 = nc^2).  Jacobi functions by the arithmetic-geometric mean
-// (descending Landen transformation, Abramowitz & Stegun 16.4); nodes past
+// sc^2 + 1 = nc^2).  K by the arithmetic-geometric mean, the Jacobi functions
+// by the descending Landen transformation (below); nodes past
 // K/2 use sn(K - v) = cd(v), cn(K - v) = g' sd(v), dn(K - v) = g' nd(v) so that
 // small cn values keep full relative precision.
 // ---------------------------------------------------------------------------
@@ -500,27 +500,36 @@ __device__ double ellip_k(double m) {
   return kPi / (2.0 * a);
 }
 
+// sn, cn, dn by the descending Landen (Gauss) transformation (Abramowitz &
+// Stegun 16.12): with k1 = (1 - k') / (1 + k') and v = u / (1 + k1),
+//   sn(u|k) = (1 + k1) sn(v|k1) / (1 + k1 sn^2(v|k1)),
+//   cn(u|k) = cn(v|k1) dn(v|k1) / (1 + k1 sn^2(v|k1)),
+//   dn(u|k) = (1 - k1 sn^2(v|k1)) / (1 + k1 sn^2(v|k1)),
+// applied until the modulus underflows (quadratic convergence, about 7 steps
+// for k' = 1e-2), where sn = sin, cn = cos, dn = 1.  One sin and one cos, the
+// rest rational: no inverse trigonometric function per level.
 __device__ void ellip_jacobi(double u, double m, double& sn, double& cn, double& dn) {
-  double a[40], c[40];
-  a[0] = 1.0;
-  c[0] = sqrt(m);
-  double b = sqrt(1.0 - m);
-  int nn = 0;
-  while (nn < 38 && fabs(c[nn]) > 1e-17) {
-    a[nn + 1] = 0.5 * (a[nn] + b);
-    c[nn + 1] = 0.5 * (a[nn] - b);
-    b = sqrt(a[nn] * b);
-    ++nn;
+  double ks[24];
+  int nk = 0;
+  double k = sqrt(m), kp = sqrt(1.0 - m);
+  while (k > 1e-17 && nk < 24) {
+    const double k1 = (1.0 - kp) / (1.0 + kp);
+    ks[nk++] = k1;
+    u /= 1.0 + k1;
+    k = k1;
+    kp = sqrt((1.0 - k1) * (1.0 + k1));
   }
-  double phi = ldexp(a[nn] * u, nn);
-  double phi_prev = phi;
-  for (int i = nn; i > 0; --i) {
-    phi_prev = phi;
-    phi = 0.5 * (phi + asin(c[i] * sin(phi) / a[i]));
+  double s = sin(u), c = cos(u), dd = 1.0;
+  for (int i = nk - 1; i >= 0; --i) {
+    const double k1 = ks[i], s2 = k1 * s * s, den = 1.0 / (1.0 + s2);
+    const double s_new = (1.0 + k1) * s * den, c_new = c * dd * den, d_new = (1.0 - s2) * den;
+    s = s_new;
+    c = c_new;
+    dd = d_new;
   }
-  sn = sin(phi);
-  cn = cos(phi);
-  dn = nn > 0 ? cn / cos(phi_prev - phi) : 1.0;
+  sn = s;
+  cn = c;
+  dn = dd;
 }
 
 __device__ void quadrature_node(int32_t Q, double ell, int32_t rule, int q, double& s, double& p) {
