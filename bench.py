@@ -39,9 +39,10 @@ TRAIN_SEEDS = (11, 12, 13)
 # learned correction, from the ncu capture summarised in
 # profiles/k_pcg_band1d_gauss1d_n8192_N40_d1024_Q32_fp32_learned.md; set to None when the kernel changes.
 PCG_DRAM_BYTES = 1458176
-# The same for one k_mscg launch (multi-shift CG, --solver multishift); None
-# until an ncu capture of the current kernel is summarised in profiles/.
-MSCG_DRAM_BYTES = None
+# The same for one k_mscg launch (multi-shift CG, --solver multishift), from the
+# capture summarised in profiles/k_mscg_gauss1d_n8192_N40_d1024_Q32_fp32.md;
+# set to None when the kernel changes.
+MSCG_DRAM_BYTES = 1351168
 
 
 def _dist():
