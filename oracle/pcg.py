@@ -22,6 +22,11 @@ from matching the three-term residual recurrences of CG for the two systems
 (Frommer & Glassner 1998; Jegerlehner 1996).  It runs without a
 preconditioner, as the paper notes.
 
+Block CG (Sec. 3.3, second alternative): for one node, the N members'
+systems share the block Krylov space span{B, C_q B, ...}; O'Leary's block CG
+gives each member the C_q-norm-optimal iterate in it, with dense s x s solves
+per iteration.
+
 Readings (the paper does not fix them): Gaussian test matrix with
 ``oversample`` = 10 extra columns and ``power_iters`` = 1 power iteration
 on the range finder; x0 = 0; stop when ||r||_2 <= tol ||b||_2 or after
@@ -204,4 +209,58 @@ def solve_normalized_multishift(C, s, p, W, R, tol=1e-12, max_iter=1000, fixed_i
         U, it, _ = multishift_cg(lambda v: C @ v, B[:, i], shifts, tol, max_iter, fixed_iters)
         ubar[:, i] = np.asarray(p) @ U
         iters[:, i] = it
+    return rih[:, None] * ubar, iters
+
+
+def block_cg(A_mv, B, tol=1e-12, max_iter=1000, fixed_iters=None):
+    """Block CG (O'Leary 1980) for A X = B with X, B in R^{d x s} (Sec. 3.3, the
+    second alternative: the s members' systems of one shift share a block
+    Krylov space, span{B, A B, ..., A^{k-1} B}, and each column's iterate is the
+    A-norm-optimal approximation within it).
+
+    X_0 = 0, R_0 = B, P_0 = R_0; with Q = A P,
+        alpha = (P^T Q)^-1 (R^T R),  X += P alpha,  R' = R - Q alpha,
+        beta = (R^T R)^-1 (R'^T R'),  P <- R' + P beta.
+    Stops when every column has ||r_i|| <= tol ||b_i||, at max_iter, or after
+    fixed_iters iterations.  The s x s solves are dense (no deflation: the
+    block must stay of full rank, which holds while no column has converged
+    exactly).  Returns (X, iterations)."""
+    B = np.asarray(B, dtype=np.float64)
+    X = np.zeros_like(B)
+    R = B.copy()
+    bn = np.linalg.norm(B, axis=0)
+    if not np.any(bn > 0):
+        return X, 0
+    P = R.copy()
+    RR = R.T @ R
+    limit = fixed_iters if fixed_iters is not None else max_iter
+    k = 0
+    while k < limit:
+        if fixed_iters is None and np.all(np.linalg.norm(R, axis=0) <= tol * bn):
+            break
+        Q = A_mv(P)
+        alpha = np.linalg.solve(P.T @ Q, RR)
+        X = X + P @ alpha
+        R = R - Q @ alpha
+        RR_new = R.T @ R
+        beta = np.linalg.solve(RR, RR_new)
+        P = R + P @ beta
+        RR = RR_new
+        k += 1
+    return X, k
+
+
+def solve_normalized_block(C, s, p, W, R, tol=1e-12, max_iter=1000, fixed_iters=None):
+    """vbar = R^-1/2 sum_q p_q U_q with, for every node q, all members' systems
+    ((s_q + 1) I + C) U_q = R^-1/2 W solved together by block CG.  Returns
+    (vbar [d][N], iterations [Q])."""
+    rih = 1.0 / np.sqrt(np.asarray(R, dtype=np.float64))
+    B = rih[:, None] * W
+    ubar = np.zeros_like(W)
+    iters = np.zeros(len(s), dtype=np.int64)
+    for qi, (sq, pq) in enumerate(zip(s, p)):
+        sigma = sq + 1.0
+        U, it = block_cg(lambda V, sigma=sigma: sigma * V + C @ V, B, tol, max_iter, fixed_iters)
+        ubar += pq * U
+        iters[qi] = it
     return rih[:, None] * ubar, iters

@@ -168,3 +168,68 @@ def test_multishift_quadrature_sum_matches_exact_perturbation_solves():
 def test_multishift_zero_rhs():
     X, it, rel = pcg.multishift_cg(lambda v: v, np.zeros(5), [1.0, 2.0], tol=1e-10)
     assert not X.any() and not it.any() and not rel.any()
+
+
+# ---------------------------------------------------------------------------
+# Block CG (Sec. 3.3, second alternative)
+# ---------------------------------------------------------------------------
+
+def _block_galerkin(A, B, k):
+    """Definition of the k-th block CG iterate: the A-orthogonal (Galerkin)
+    projection of every column onto span{B, A B, ..., A^(k-1) B}, from an
+    orthonormal basis built block by block."""
+    V = np.zeros((B.shape[0], 0))
+    blk = B.copy()
+    for _ in range(k):
+        for _ in range(2):
+            blk = blk - V @ (V.T @ blk)
+        Qb, _ = np.linalg.qr(blk)
+        V = np.hstack([V, Qb])
+        blk = A @ Qb
+    return V @ np.linalg.solve(V.T @ A @ V, V.T @ B)
+
+
+def test_block_cg_iterates_are_block_galerkin_projections():
+    rng = np.random.default_rng(7)
+    d, s = 24, 3
+    Qm, _ = np.linalg.qr(rng.standard_normal((d, d)))
+    A = (Qm * np.geomspace(0.05, 40.0, d)) @ Qm.T
+    B = rng.standard_normal((d, s))
+    for k in range(1, 6):
+        X, it = pcg.block_cg(lambda V: A @ V, B, fixed_iters=k)
+        ref = _block_galerkin(A, B, k)
+        assert it == k
+        assert np.linalg.norm(X - ref) <= 1e-9 * np.linalg.norm(ref), k
+
+
+def test_block_cg_single_column_is_plain_cg():
+    pr, W, C = _C(seed=8)
+    b = W[:, 0] / np.sqrt(pr.R)
+    A = 1.4 * np.eye(C.shape[0]) + C
+    for k in (1, 4, 9):
+        X, it = pcg.block_cg(lambda V: A @ V, b[:, None], fixed_iters=k)
+        x, kk = pcg.pcg(lambda v: A @ v, b, lambda r: r, fixed_iters=k)
+        assert np.linalg.norm(X[:, 0] - x) <= 1e-12 * np.linalg.norm(x)
+
+
+def test_block_cg_matches_dense_and_needs_fewer_iterations_than_cg():
+    """Every member meets the tolerance against a dense solve, and the block
+    run needs fewer iterations than the slowest single-member CG run."""
+    pr, W, C = _C(seed=9)
+    A = 1.2 * np.eye(C.shape[0]) + C
+    B = W / np.sqrt(pr.R)[:, None]
+    X, it = pcg.block_cg(lambda V: A @ V, B, tol=1e-10)
+    assert np.linalg.norm(X - np.linalg.solve(A, B)) <= 1e-8 * np.linalg.norm(X)
+    single = max(pcg.pcg(lambda v: A @ v, B[:, i], lambda r: r, tol=1e-10)[1] for i in range(B.shape[1]))
+    assert it < single, (it, single)
+
+
+def test_block_cg_quadrature_sum_matches_exact_perturbation_solves():
+    pr, W, C = _C(seed=10)
+    s, p = quadrature.elliptic_rule(8, quadrature.ell_rule(C))
+    mu, Z = F.anomalies(pr.X)
+    _, _, Shh = F.localized_covariances(Z, pr.obs_idx, pr.grid)
+    ref = F.perturbation_solves(Shh, W, pr.R, s, p)
+    vbar, iters = pcg.solve_normalized_block(C, s, p, W, pr.R, tol=1e-12)
+    assert np.linalg.norm(vbar - ref) <= 1e-9 * np.linalg.norm(ref)
+    assert iters.shape == (8,) and np.all(np.diff(iters) <= 0)
