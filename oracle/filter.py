@@ -21,6 +21,10 @@ along the leading axis, [N][n], so the analysis ensemble is mu_a + A_a.
 
 A dense localization matrix can replace Gaspari-Cohn through ``L`` (used by
 tests for the unlocalized case L = all-ones).
+
+Error measures of the experiments: the exact Kalman analysis covariance and
+E^2 of Eq. diagonal_error_metric (Sec. 4.3), the forecast MSE and the MSE over
+the forecast variance (Sec. 5.2).
 """
 from __future__ import annotations
 
@@ -169,3 +173,40 @@ def relative_increment_error(A_test, A_ref, A_forecast):
     num = np.linalg.norm(np.asarray(A_test) - np.asarray(A_ref))
     den = np.linalg.norm(np.asarray(A_ref) - np.asarray(A_forecast))
     return float(num / den) if den > 0 else float(num)
+
+
+# ---------------------------------------------------------------------------
+# Error measures of the experiments (Sec. 4.3, Sec. 5.2)
+# ---------------------------------------------------------------------------
+
+def kalman_analysis_covariance(Sxx, H, R):
+    """Exact analysis covariance of the Kalman filter, the reference of
+    Eq. diagonal_error_metric: Sxx - Sxx H^T (H Sxx H^T + R)^-1 H Sxx."""
+    Sxx = np.asarray(Sxx, dtype=np.float64)
+    H = np.asarray(H, dtype=np.float64)
+    SH = Sxx @ H.T
+    return Sxx - SH @ np.linalg.solve(H @ SH + np.diag(np.asarray(R, dtype=np.float64)), SH.T)
+
+
+def variance_error_e2(A_a, Sa_diag):
+    """E^2 of Eq. diagonal_error_metric: the mean over state components of the squared relative
+    error of the analysis ensemble's empirical variance (anomalies A_a [N][n], divisor N - 1)
+    against the exact analysis variance Sa_diag [n]."""
+    A_a = np.asarray(A_a, dtype=np.float64)
+    emp = (A_a ** 2).sum(axis=0) / (A_a.shape[0] - 1)
+    Sa = np.asarray(Sa_diag, dtype=np.float64)
+    return float(np.mean(((emp - Sa) / Sa) ** 2))
+
+
+def forecast_mse(mu_f, truth):
+    """Squared forecast error per component, ||mu_f - x||^2 / n (Sec. 5.2)."""
+    e = np.asarray(mu_f, dtype=np.float64) - np.asarray(truth, dtype=np.float64)
+    return float(e @ e) / e.size
+
+
+def mse_over_variance(mu_f, truth, X_f):
+    """Forecast MSE over the forecast ensemble variance averaged over components (Sec. 5.2;
+    near 1 for a calibrated filter).  The printed formula omits the 1/n of the MSE; this is the
+    ratio of the two per-component quantities."""
+    var = float(np.mean(np.var(np.asarray(X_f, dtype=np.float64), axis=0, ddof=1)))
+    return forecast_mse(mu_f, truth) / var

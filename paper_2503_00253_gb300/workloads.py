@@ -299,3 +299,38 @@ def general_obs_problem(name: str, grid: Grid, X: np.ndarray, truth: np.ndarray,
     R = np.full(d, float(r2))
     y = H @ truth + math.sqrt(r2) * rng.standard_normal(d)
     return dict(name=name, grid=grid, X=X, truth=truth, H=H, y=y, R=R, Q=Q, tol=tol)
+
+
+# ---------------------------------------------------------------------------
+# Single-cycle experiment (Sec. 4.1)
+# ---------------------------------------------------------------------------
+
+def single_cycle_covariance(n: int = 2000, nu: float = 10.0, eta: float = 1e-4) -> np.ndarray:
+    """Forecast covariance of Eq. single_cycle_covar: eta delta_ij + exp(-c(i,j)^2 / (2 nu^2)),
+    with c the chordal distance on the circle of circumference n (dense [n][n])."""
+    idx = np.arange(n)
+    c = _chordal(idx[:, None] - idx[None, :], n)
+    return np.exp(-(c ** 2) / (2.0 * nu ** 2)) + eta * np.eye(n)
+
+
+def single_cycle_trial(trial: int, N: int = 20, n: int = 2000, nu: float = 10.0, eta: float = 1e-4,
+                       d: int = 100, bandwidth: float = 10.0, loc_length: float = 12.0, Q: int = 8,
+                       tol: float = 1e-12, Sxx: np.ndarray = None, seed: int = 1000, r2: float = None):
+    """One trial of the single-cycle experiment (Sec. 4.1): N forecast members and a truth (draw N + 1)
+    from N(0, Sxx), d Gaussian-channel observations (Eq. single_cycle_obsop) with R = r^2 I, r^2 one
+    tenth of the mean observable variance diag(H Sxx H^T) (Eq. single_cycle_obserr_covar).  The
+    paper's localization is a Gaussian taper of length L; the library localizes with Gaspari-Cohn, so
+    the grid carries the half-width sqrt(10/3) L of the matching Gaspari-Cohn function."""
+    rng = np.random.default_rng(seed + trial)
+    draws = gaussian_ensemble_1d(n, N + 1, nu, 1.0, eta, rng)
+    X, truth = draws[:N].copy(), draws[N].copy()
+    H, csr = gaussian_channel_operator(n, d, bandwidth)
+    if r2 is None:   # the same in every trial: pass it in to skip the contraction
+        if Sxx is None:
+            Sxx = single_cycle_covariance(n, nu, eta)
+        r2 = 0.1 * float(np.mean(np.einsum("ij,jk,ik->i", H, Sxx, H)))
+    R = np.full(d, r2)
+    y = H @ truth + math.sqrt(r2) * rng.standard_normal(d)
+    grid = Grid((n, 1, 1), (True, False, False), (math.sqrt(10.0 / 3.0) * loc_length, 1.0, 1.0), True)
+    return dict(name=f"single_cycle_{trial}", grid=grid, X=X, truth=truth, H=H, csr=csr, y=y, R=R, Q=Q,
+                tol=tol, r2=r2)

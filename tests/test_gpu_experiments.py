@@ -1,0 +1,87 @@
+"""The single-cycle experiment of Sec. 4 through the C ABI: the paper-faithful
+fixed-iteration mode (2 PCG iterations) on the paper's weighted-sum observing
+system, scored with E^2 (Eq. diagonal_error_metric) against the exact Kalman
+analysis variances.  The library's analysis equals the oracle's pipeline
+iterate for iterate, so the two E^2 values agree; the device metrics equal the
+oracle's."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import filter as F
+from oracle import pcg, philox, quadrature
+from paper_2503_00253_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2503_00253_gb300 import binding
+    binding.library()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def Sxx():
+    return workloads.single_cycle_covariance()
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def test_device_metrics_match_oracle(Sxx):
+    from paper_2503_00253_gb300 import metrics
+    tr = workloads.single_cycle_trial(3, Sxx=Sxx)
+    Sa_ref = np.diag(F.kalman_analysis_covariance(Sxx, tr["H"], tr["R"]))
+    Sa = metrics.kalman_analysis_variance(dev(Sxx), dev(tr["H"]), dev(tr["R"])).cpu().numpy()
+    assert np.max(np.abs(Sa - Sa_ref) / Sa_ref) <= 1e-10
+    A = tr["X"] - tr["X"].mean(0)
+    assert abs(metrics.variance_error_e2(dev(A), dev(Sa_ref)) - F.variance_error_e2(A, Sa_ref)) <= 1e-12
+    mu = tr["X"].mean(0)
+    assert abs(metrics.forecast_mse(dev(mu), dev(tr["truth"])) - F.forecast_mse(mu, tr["truth"])) <= 1e-12
+    assert abs(metrics.mse_over_variance(dev(mu), dev(tr["truth"]), dev(tr["X"]))
+               - F.mse_over_variance(mu, tr["truth"], tr["X"])) <= 1e-12
+
+
+@pytest.mark.parametrize("ritz_rank", [0, 10])
+def test_two_iteration_analysis_and_e2_match_oracle(B, Sxx, ritz_rank):
+    """Sec. 4.2: 2 PCG iterations per system, p Ritz vectors, k = Q = 8 nodes, FP64."""
+    Q, iters, os_, seed = 8, 2, 10, 0x1234ABCD
+    tr = workloads.single_cycle_trial(1, Q=Q, Sxx=Sxx)
+    H, R = tr["H"], tr["R"]
+    rowptr, col, val = tr["csr"]
+    prob = dict(grid=tr["grid"], X=dev(tr["X"]), H=(dev(rowptr), dev(col), dev(val)), y=dev(tr["y"]), R=dev(R),
+                Q=Q, tol=1e-12)
+    opts = B.make_options(precision=B.PRECISION_FP64, ritz_rank=ritz_rank, oversample=os_, seed=seed,
+                          fixed_iters=iters)
+    outs, st = B.info_esrf_analysis_batched([prob], opts)
+    torch.cuda.synchronize()
+    assert st[0]["status"] == 0 and st[0]["iters_max"] == iters
+    A_gpu = outs[0][1].cpu().numpy()
+    # the oracle's pipeline with the same nodes, test matrix and iteration count
+    mu, Z = F.anomalies(tr["X"])
+    W, Sxh, Shh = F.localized_covariances_H(Z, H, tr["grid"])
+    C = F.normalized_obs_covariance(Shh, R)
+    s, p = quadrature.elliptic_rule(Q, F.choose_ell(Shh, R))
+    Om = philox.test_matrix(H.shape[0], ritz_rank + os_, seed) if ritz_rank else None
+    vbar, _ = pcg.solve_normalized(C, s, p, W, R, k=ritz_rank, Omega=Om, fixed_iters=iters)
+    A_ref = math.sqrt(tr["X"].shape[0] - 1) * (Z - Sxh @ vbar).T
+    err = F.relative_increment_error(A_gpu, A_ref, tr["X"] - mu)
+    assert err < 1e-9, err
+    Sa = np.diag(F.kalman_analysis_covariance(Sxx, H, R))
+    e2_gpu, e2_ref = F.variance_error_e2(A_gpu, Sa), F.variance_error_e2(A_ref, Sa)
+    assert abs(e2_gpu - e2_ref) <= 1e-8 * e2_ref, (e2_gpu, e2_ref)
+    # 2 iterations leave the analysis between the forecast and the converged update
+    A_conv = F.perturbation_update_H(tr["X"], H, R, tr["grid"], Q)
+    assert F.variance_error_e2(A_conv, Sa) < F.variance_error_e2(tr["X"] - mu, Sa)
+
+
+def test_single_cycle_runner(B):
+    from paper_2503_00253_gb300 import experiments
+    out = experiments.single_cycle_e2(trials=2, Q=4, ritz_rank=10, iters=2)
+    assert out["trials"] == 2 and np.isfinite(out["e2_mean"]) and 0.0 < out["e2_mean"] < 10.0
+    assert out["ms_median"] > 0.0

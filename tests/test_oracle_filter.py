@@ -239,3 +239,47 @@ def test_weighted_sum_operators_follow_the_paper_forms():
     H2, _ = workloads.column_sum_operator((8, 1, 12), [1, 5], 3, 4.0, 2.0)
     assert np.allclose((H2 ** 2).sum(1), 1.0)
     assert np.all(H2.reshape(6, 12, 8)[:, :, [0, 2, 3, 4, 6, 7]] == 0.0)
+
+
+# ---------------------------------------------------------------------------
+# Error measures of the experiments (Sec. 4.3, Sec. 5.2)
+# ---------------------------------------------------------------------------
+
+def test_kalman_analysis_covariance_equals_information_form():
+    rng = np.random.default_rng(21)
+    n, d = 30, 8
+    M = rng.standard_normal((n, n))
+    Sxx = M @ M.T / n + 0.1 * np.eye(n)
+    H = rng.standard_normal((d, n))
+    R = rng.uniform(0.2, 2.0, d)
+    Sa = F.kalman_analysis_covariance(Sxx, H, R)
+    info = np.linalg.inv(np.linalg.inv(Sxx) + H.T @ np.diag(1.0 / R) @ H)
+    assert np.max(np.abs(Sa - info)) <= 1e-10 * np.max(np.abs(info))
+
+
+def test_variance_error_e2_closed_forms():
+    """E^2 = 0 when the empirical variances are exact, and 1 when they are twice
+    the reference (each term ((2 s - s) / s)^2 = 1)."""
+    rng = np.random.default_rng(22)
+    A = rng.standard_normal((12, 50))
+    emp = (A ** 2).sum(0) / 11
+    assert F.variance_error_e2(A, emp) <= 1e-28
+    assert abs(F.variance_error_e2(A, emp / 2.0) - 1.0) <= 1e-12
+    assert abs(F.variance_error_e2(A, emp * 2.0) - 0.25) <= 1e-12
+
+
+def test_forecast_mse_and_ratio():
+    truth = np.array([1.0, 2.0, 3.0, 4.0])
+    mu = np.array([1.0, 0.0, 3.0, 6.0])
+    assert F.forecast_mse(mu, truth) == 2.0
+    Xf = np.array([[0.0, 0.0, 0.0, 0.0], [2.0, 2.0, 2.0, 2.0]])   # variance 2 per component
+    assert F.mse_over_variance(mu, truth, Xf) == 1.0
+
+
+def test_single_cycle_observation_error_matches_the_paper():
+    """Sec. 4.1 (Eq. single_cycle_obserr_covar) prints r^2 ~ 36.3 as one tenth of the observable
+    variance under Eq. single_cycle_covar and Eq. single_cycle_obsop: the generator's covariance
+    and channels reproduce it."""
+    tr = workloads.single_cycle_trial(0)
+    assert abs(tr["r2"] - 36.3) < 0.05, tr["r2"]
+    assert tr["H"].shape == (100, 2000) and tr["X"].shape == (20, 2000)
