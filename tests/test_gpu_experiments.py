@@ -85,3 +85,22 @@ def test_single_cycle_runner(B):
     out = experiments.single_cycle_e2(trials=2, Q=4, ritz_rank=10, iters=2)
     assert out["trials"] == 2 and np.isfinite(out["e2_mean"]) and 0.0 < out["e2_mean"] < 10.0
     assert out["ms_median"] > 0.0
+
+
+def test_rtps_relaxes_each_component():
+    from paper_2503_00253_gb300 import experiments
+    rng = np.random.default_rng(5)
+    Af = torch.tensor(rng.standard_normal((10, 6)) * 2.0, device="cuda")
+    Aa = torch.tensor(rng.standard_normal((10, 6)), device="cuda")
+    out = experiments.rtps(Af, Aa, 0.3)
+    sf, sa, so = Af.std(0), Aa.std(0), out.std(0)
+    assert torch.allclose(so, 0.3 * sf + 0.7 * sa, rtol=1e-12)
+
+
+def test_cycled_l96_runner_reduced(B):
+    """A short cycled run on a reduced layered Lorenz-96 (4 x 240, N = 20): the Sec. 5.2 measures
+    are finite, and the forecast error stays below the climatological variance."""
+    from paper_2503_00253_gb300 import experiments
+    out = experiments.cycled_l96(cycles=16, burn_in=6, Q=8, nx=240, nz=4, N=20, spinup=500, alpha=0.3)
+    assert np.isfinite(out["forecast_mse"]) and np.isfinite(out["mse_over_variance"])
+    assert 0.0 < out["forecast_mse"] < out["climatological_variance"], out
