@@ -23,13 +23,17 @@
 // GB300 mapping: one thread-block cluster of CS CTAs per group of LC chains
 // (members) of one problem.  CTA c of the cluster owns rows [c Rc, (c+1) Rc) of
 // the observation space: their residuals, shifted directions, quadrature sums
-// and the matvec rows of C (read from the L2-resident band).  Every CTA keeps a
-// full copy of each chain's base direction p in shared memory; after each
-// update the owner pushes its rows to all CTAs of the cluster as 16-byte
-// distributed-shared-memory stores.  An iteration has three cluster barriers:
-// the partial sums of p^T (C + sigma_0) p, those of r^T r, and the p exchange.
-// Every CTA then computes the same FP64 scalars from the same partials in the
-// same order, so the cluster stays in lockstep without a leader.
+// and their rows of C's band (staged in shared memory once per problem when
+// they fit, else read from L2).  Every CTA keeps a full copy of each chain's
+// base direction p in shared memory; after each update the owner pushes its
+// rows, as 16-byte distributed-shared-memory stores, to the CTAs whose rows of
+// C read them (on a 1-D band: itself and its two neighbours).  An iteration has
+// three cluster barriers: the partial sums of p^T (C + sigma_0) p, those of
+// r^T r, and the p exchange.  Every CTA then forms the same scalars from the
+// same partials in the same order, so the cluster stays in lockstep without a
+// leader.  The scalars are FP64 on the FP64 path and float-float (about 48
+// bits, FP32 instructions only) on the FP32 path, where FP64 throughput would
+// dominate an iteration; the coefficients that scale FP32 vectors are FP32.
 #include <cooperative_groups.h>
 #include <math.h>
 #include <string.h>
