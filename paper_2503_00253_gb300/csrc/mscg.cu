@@ -863,11 +863,12 @@ struct MsOcc {
 
 template <typename T, int LC>
 int ms_max_clusters(int CS, size_t dyn) {
+  constexpr int kMaxDev = 64;
   static thread_local MsOcc cache[32];
   static thread_local int ncache = 0;
-  static thread_local int attr_dev_mask = 0;
+  static thread_local bool attr_set[kMaxDev] = {};
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) {
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
     cudaGetLastError();
     return -1;
   }
@@ -875,13 +876,13 @@ int ms_max_clusters(int CS, size_t dyn) {
     const MsOcc& c = cache[i];
     if (c.dev == dev && c.esz == (int)sizeof(T) && c.LC == LC && c.CS == CS && c.dyn == dyn) return c.clusters;
   }
-  if (dev < 31 && !(attr_dev_mask & (1 << dev))) {
+  if (!attr_set[dev]) {
     if (cudaFuncSetAttribute(k_mscg<T, LC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMsSmemBudget) !=
         cudaSuccess) {
       cudaGetLastError();
       return -1;
     }
-    attr_dev_mask |= 1 << dev;
+    attr_set[dev] = true;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(CS, 1, 1);
