@@ -222,6 +222,14 @@ __device__ __forceinline__ FF ff_from(double x) {
   const float h = (float)x;
   return FF{h, (float)(x - (double)h)};
 }
+__device__ __forceinline__ FF ff_add(FF a, FF b) { return ff_sub(a, FF{-b.h, -b.l}); }
+// a / b (b != 0): the FP32 quotient of the leading parts, corrected once by the
+// residual a - q b formed in float-float.
+__device__ __forceinline__ FF ff_div(FF a, FF b) {
+  const float q1 = a.h / b.h;
+  const FF r = ff_sub(a, ff_mul(FF{q1, 0.f}, b));
+  return ff_norm(q1, r.h / b.h);
+}
 // 1 / sqrt(g) for g > 0: FP32 seed, one Newton step with the residual
 // 1 - g y0^2 formed exactly enough in float-float arithmetic.
 __device__ __forceinline__ FF ff_rsqrt(FF g) {
@@ -231,6 +239,7 @@ __device__ __forceinline__ FF ff_rsqrt(FF g) {
   const float r = (1.f - t) - (te + fmaf(g.h, pe, g.l * p));
   return ff_norm(y0, 0.5f * y0 * r);
 }
+__device__ __forceinline__ FF ff_sqrt(FF g) { return ff_mul(g, ff_rsqrt(g)); }
 
 // ---------------------------------------------------------------------------
 // Accumulators.  For FP64 vectors a plain double sum.  For FP32 vectors a

@@ -80,14 +80,6 @@ __host__ __device__ __forceinline__ int chains_of(const ProblemDev& p) {
   return p.do_mean + (p.do_pert ? (int)p.N : 0);
 }
 
-// Float-float quotient a / b (b != 0), about 48 bits: the FP32 quotient of the
-// leading parts, corrected once by the residual a - q b formed in float-float.
-__device__ __forceinline__ FF ff_div(FF a, FF b) {
-  const float q1 = a.h / b.h;
-  const FF r = ff_sub(a, ff_mul(FF{q1, 0.f}, b));
-  return ff_norm(q1, r.h / b.h);
-}
-
 // Cluster-wide sums of LC per-thread partials: warp shuffles, one partial per
 // warp in shared memory, then thread (j, dst) combines the warps of chain j and
 // stores the CTA's sum into slot [crank][j] of CTA dst (a float-float pair for
@@ -149,8 +141,6 @@ __device__ __forceinline__ double ms_sum_d(const double* red, int CS, int LC, in
   return s;
 }
 __device__ __forceinline__ double ff_to_d(FF a) { return (double)a.h + (double)a.l; }
-
-__device__ __forceinline__ FF ff_add(FF a, FF b) { return ff_sub(a, FF{-b.h, -b.l}); }
 
 // A shift index carried in the packed coefficient entry as the bits of a T.
 template <typename T>

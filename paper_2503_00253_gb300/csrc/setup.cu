@@ -485,51 +485,37 @@ void launch_count_neighbours(const GridDev& g, const int64_t* obs, int64_t d, in
 // a2: quadrature (App. D).  Elliptic rule with modulus g = sqrt(ell/(1+ell)):
 //   s_q = sc(u_q | g)^2,  p_q = (2 K / (pi Q)) dn(u_q | g),  u_q = (q - 1/2) K / Q,
 // which is r_q / (s_q + 1) with r_q = (2K/(pi Q)) nc dc (d sc/du = dc nc and
-// sc^2 + 1 = nc^2).  K by the arithmetic-geometric mean, the Jacobi functions
-// by the descending Landen transformation (below); nodes past
-// K/2 use sn(K - v) = cd(v), cn(K - v) = g' sd(v), dn(K - v) = g' nd(v) so that
-// small cn values keep full relative precision.
+// sc^2 + 1 = nc^2).  K and the Jacobi functions come from one descending
+// Landen ladder in float-float (quadrature_node); nodes past K/2 use
+// sn(K - v) = cd(v), cn(K - v) = g' sd(v), dn(K - v) = g' nd(v) so that small
+// cn values keep full relative precision.
 // ---------------------------------------------------------------------------
-__device__ double ellip_k(double m) {
-  double a = 1.0, b = sqrt(1.0 - m);
-  for (int i = 0; i < 64 && fabs(a - b) > 1e-16 * a; ++i) {
-    const double an = 0.5 * (a + b);
-    b = sqrt(a * b);
-    a = an;
-  }
-  return kPi / (2.0 * a);
-}
+// pi / 2 as a float-float pair, and the Taylor coefficients (-1)^j / (2j+1)! and
+// (-1)^j / (2j)!, j = 0..9, as exact float-float pairs (hexadecimal literals).
+constexpr float kPiHalfHi = 0x1.921fb6p+0f, kPiHalfLo = -0x1.777a5cp-25f;
+__constant__ float kSinH[10] = {0x1p+0f, -0x1.555556p-3f, 0x1.111112p-7f, -0x1.a01a02p-13f, 0x1.71de3ap-19f,
+                                -0x1.ae6456p-26f, 0x1.612462p-33f, -0x1.ae7f3ep-41f, 0x1.952c78p-49f,
+                                -0x1.2f49b4p-57f};
+__constant__ float kSinL[10] = {0.f, 0x1.555556p-28f, -0x1.dddddep-32f, 0x1.7f97fap-39f, 0x1.55b1ccp-45f,
+                                -0x1.fd5138p-52f, -0x1.8af25ep-58f, -0x1.ccee08p-67f, -0x1.f9ea56p-74f,
+                                -0x1.a05056p-83f};
+__constant__ float kCosH[10] = {0x1p+0f, -0x1p-1f, 0x1.555556p-5f, -0x1.6c16c2p-10f, 0x1.a01a02p-16f,
+                                -0x1.27e4fcp-22f, 0x1.1eed8ep-29f, -0x1.93974ap-37f, 0x1.ae7f3ep-45f,
+                                -0x1.682786p-53f};
+__constant__ float kCosL[10] = {0.f, 0.f, -0x1.555556p-30f, 0x1.27d27ep-35f, -0x1.7f97fap-42f, 0x1.10ec14p-47f,
+                                0x1.ff1b14p-54f, -0x1.180f94p-62f, 0x1.ccee08p-71f, -0x1.dcbeccp-80f};
 
-// sn, cn, dn by the descending Landen (Gauss) transformation (Abramowitz &
-// Stegun 16.12): with k1 = (1 - k') / (1 + k') and v = u / (1 + k1),
-//   sn(u|k) = (1 + k1) sn(v|k1) / (1 + k1 sn^2(v|k1)),
-//   cn(u|k) = cn(v|k1) dn(v|k1) / (1 + k1 sn^2(v|k1)),
-//   dn(u|k) = (1 - k1 sn^2(v|k1)) / (1 + k1 sn^2(v|k1)),
-// applied until the modulus underflows (quadratic convergence, about 7 steps
-// for k' = 1e-2), where sn = sin, cn = cos, dn = 1.  One sin and one cos, the
-// rest rational: no inverse trigonometric function per level.
-__device__ void ellip_jacobi(double u, double m, double& sn, double& cn, double& dn) {
-  double ks[24];
-  int nk = 0;
-  double k = sqrt(m), kp = sqrt(1.0 - m);
-  while (k > 1e-17 && nk < 24) {
-    const double k1 = (1.0 - kp) / (1.0 + kp);
-    ks[nk++] = k1;
-    u /= 1.0 + k1;
-    k = k1;
-    kp = sqrt((1.0 - k1) * (1.0 + k1));
+// sin x and cos x for |x| <= pi/4 in float-float: Taylor series by Horner's
+// rule in x^2, truncated after x^19 (sin) and x^18 (cos), below 1e-17 there.
+__device__ void ff_sincos_small(FF x, FF& sn, FF& cn) {
+  const FF x2 = ff_mul(x, x);
+  FF as{kSinH[9], kSinL[9]}, ac{kCosH[9], kCosL[9]};
+  for (int j = 8; j >= 0; --j) {
+    as = ff_add(FF{kSinH[j], kSinL[j]}, ff_mul(as, x2));
+    ac = ff_add(FF{kCosH[j], kCosL[j]}, ff_mul(ac, x2));
   }
-  double s = sin(u), c = cos(u), dd = 1.0;
-  for (int i = nk - 1; i >= 0; --i) {
-    const double k1 = ks[i], s2 = k1 * s * s, den = 1.0 / (1.0 + s2);
-    const double s_new = (1.0 + k1) * s * den, c_new = c * dd * den, d_new = (1.0 - s2) * den;
-    s = s_new;
-    c = c_new;
-    dd = d_new;
-  }
-  sn = s;
-  cn = c;
-  dn = dd;
+  sn = ff_mul(x, as);
+  cn = ac;
 }
 
 __device__ void quadrature_node(int32_t Q, double ell, int32_t rule, int q, double& s, double& p) {
@@ -569,23 +555,59 @@ __device__ void quadrature_node(int32_t Q, double ell, int32_t rule, int q, doub
     p = 0.5 * v;
     return;
   }
-  const double m = ell / (1.0 + ell);
-  const double kp = sqrt(1.0 / (1.0 + ell));   // complementary modulus g'
-  const double K = ellip_k(m);
-  const double scale = 2.0 * K / (kPi * Q);
-  const double t = (q + 0.5) / Q;
-  double sn, cn, dn;
-  if (t <= 0.5) {
-    ellip_jacobi(t * K, m, sn, cn, dn);
-    s = (sn / cn) * (sn / cn);
-    p = scale * dn;
-  } else {
-    const double v = ((Q - q) - 0.5) / Q * K;   // K - u_q, formed without cancellation
-    ellip_jacobi(v, m, sn, cn, dn);
-    const double sc = cn / (kp * sn);         // sc(K - v) = cd(v) / (g' sd(v))
-    s = sc * sc;
-    p = scale * kp / dn;                       // dn(K - v) = g' / dn(v)
+  // Elliptic rule in float-float (about 48 bits, FP32 instructions only; a
+  // chain of FP64 instructions is slow on this GPU).  Descending Landen
+  // ladder of the modulus g (g^2 = ell / (1 + ell), g' = (1 + ell)^-1/2):
+  //   k_{n+1} = k_n^2 / (1 + k'_n)^2 = (1 - k'_n) / (1 + k'_n),  k'_{n+1} = 2 sqrt(k'_n) / (1 + k'_n),
+  // free of cancellation for k near 1, with K = (pi/2) prod_n (1 + k_n).  The
+  // argument at the bottom of the ladder is u prod_n (1 + k_n)^-1 = t pi / 2
+  // for u = t K, so sin and cos are of a known angle <= pi/4 (Taylor series);
+  // sn, cn, dn then ascend the ladder by the descending Landen (Gauss)
+  // transformation (Abramowitz & Stegun 16.12): with s2 = k_{n+1} sn^2,
+  //   sn <- (1 + k_{n+1}) sn / (1 + s2),  cn <- cn dn / (1 + s2),  dn <- (1 - s2) / (1 + s2).
+  // Nodes past K/2 use the reflection below.
+  const FF one{1.f, 0.f};
+  const FF L = ff_from(ell);
+  const FF kp0 = ff_rsqrt(ff_add(one, L));
+  FF k = ff_mul(ff_sqrt(L), kp0), kp = kp0, prod = one;
+  FF ks[24];
+  int nk = 0;
+  while (k.h > 1e-17f && nk < 24) {
+    const FF opk = ff_add(one, kp);
+    const FF k1 = ff_div(ff_mul(k, k), ff_mul(opk, opk));
+    ks[nk++] = k1;
+    prod = ff_mul(prod, ff_add(one, k1));
+    kp = ff_div(ff_mul(FF{2.f, 0.f}, ff_sqrt(kp)), opk);
+    k = k1;
   }
+  const double t = (q + 0.5) / Q;
+  const bool refl = t > 0.5;
+  const double tt = refl ? ((Q - q) - 0.5) / Q : t;   // K - u_q, formed without cancellation
+  FF sn, cn;
+  ff_sincos_small(ff_mul(FF{kPiHalfHi, kPiHalfLo}, ff_from(tt)), sn, cn);
+  FF dn = one;
+  for (int i = nk - 1; i >= 0; --i) {
+    const FF s2 = ff_mul(ks[i], ff_mul(sn, sn));
+    const FF den = ff_div(one, ff_add(one, s2));
+    const FF s_new = ff_mul(ff_mul(ff_add(one, ks[i]), sn), den);
+    const FF c_new = ff_mul(ff_mul(cn, dn), den);
+    dn = ff_mul(ff_sub(one, s2), den);
+    sn = s_new;
+    cn = c_new;
+  }
+  const FF scale = ff_div(prod, ff_from((double)Q));   // 2 K / (pi Q)
+  FF sq, pq;
+  if (!refl) {
+    const FF r = ff_div(sn, cn);                       // sc(u_q)
+    sq = ff_mul(r, r);
+    pq = ff_mul(scale, dn);
+  } else {
+    const FF r = ff_div(cn, ff_mul(kp0, sn));          // sc(K - v) = cd(v) / (g' sd(v))
+    sq = ff_mul(r, r);
+    pq = ff_div(ff_mul(scale, kp0), dn);               // dn(K - v) = g' / dn(v)
+  }
+  s = (double)sq.h + (double)sq.l;
+  p = (double)pq.h + (double)pq.l;
 }
 
 __global__ void k_quadrature(ProblemDev* tab) {
