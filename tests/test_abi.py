@@ -97,3 +97,40 @@ def test_host_side_validation_without_gpu(lib):
     rc = L.info_esrf_analysis(ctypes.byref(g), 10, 8, 20, 8, 8, 8, 4, 1e-8, ctypes.byref(o), None, 0,
                               None, 8, 8, None)
     assert rc == binding.ERR_WORKSPACE
+
+
+def test_multishift_plan_limits_without_gpu(lib):
+    """Workspace sizing runs on the host: the solver option is validated, a d whose
+    full direction vector cannot fit a CTA's shared memory is unsupported (size 0),
+    and shifted directions that do not fit shared memory get a scratch area."""
+    from paper_2503_00253_gb300 import binding
+    L = binding.library()
+
+    def grid(n, hw):
+        g = binding.Grid()
+        for i in range(3):
+            g.shape[i] = 1
+            g.half_width[i] = 1.0
+        g.shape[0] = n
+        g.half_width[0] = hw
+        return g
+
+    g = grid(8192, 5.0)
+    ms = dict(solver=binding.SOLVER_MULTISHIFT)
+    for sv, ok in ((0, True), (1, True), (2, False), (-1, False)):
+        o = binding.make_options(solver=sv)
+        assert (L.info_esrf_workspace_size(ctypes.byref(g), 10, 1024, 8, ctypes.byref(o)) > 0) == ok, sv
+    # one chain's p in shared memory: about 35,000 FP32 observations at most
+    big = grid(80000, 5.0)
+    o32 = binding.make_options(precision=binding.PRECISION_FP32, **ms)
+    assert L.info_esrf_workspace_size(ctypes.byref(big), 10, 40000, 8, ctypes.byref(o32)) == 0
+    assert L.info_esrf_workspace_size(ctypes.byref(big), 10, 20000, 8, ctypes.byref(o32)) > 0
+    pcg = binding.make_options(precision=binding.PRECISION_FP32)
+    assert L.info_esrf_workspace_size(ctypes.byref(big), 10, 40000, 8, ctypes.byref(pcg)) > 0
+    # FP64, 48 shifts: at 2 CTAs per cluster (512 rows each) the directions need scratch,
+    # at 8 (128 rows) they fit in shared memory
+    o2 = binding.make_options(precision=binding.PRECISION_FP64, cluster_size=2, **ms)
+    o8 = binding.make_options(precision=binding.PRECISION_FP64, cluster_size=8, **ms)
+    s2 = L.info_esrf_workspace_size(ctypes.byref(g), 10, 1024, 48, ctypes.byref(o2))
+    s8 = L.info_esrf_workspace_size(ctypes.byref(g), 10, 1024, 48, ctypes.byref(o8))
+    assert s2 >= s8 + 160 * 48 * 512 * 8, (s2, s8)
