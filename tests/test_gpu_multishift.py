@@ -213,3 +213,25 @@ def test_multishift_replays_as_cuda_graph(B):
         graph.replay()
     torch.cuda.synchronize()
     assert torch.equal(mu1, ref_mu) and torch.equal(A1, ref_A)
+
+
+@pytest.mark.parametrize("N,Q,stride", [(2, 1, 5), (3, 2, 7), (9, 3, 1), (17, 5, 4)])
+def test_multishift_ragged_and_degenerate_sizes(B, N, Q, stride):
+    """Two members, one node, every point observed (d = n = 331, rows not a multiple of 4 per CTA)."""
+    pr = workloads.gaussian_problem_1d("g", n=331, N=N, length_scale=5.0, obs_stride=stride, r2=0.7,
+                                       half_width=6.0, Q=Q, tol=1e-12, seed=N * 10 + Q)
+    for precision, bound, tol in ((0, 1e-10, 1e-12), (1, 1e-4, 1e-6)):
+        mu_a, A_a, st = run(B, pr, precision, tol)
+        assert st["status"] == 0 and st["solver_path"] == 2, st
+        ea, em = errors(pr, mu_a, A_a)
+        assert ea <= bound and em <= bound, (precision, ea, em)
+
+
+def test_multishift_single_observation(B):
+    pr = workloads.gaussian_problem_1d("one", n=50, N=6, length_scale=4.0, obs_stride=50, r2=0.2,
+                                       half_width=5.0, Q=4, tol=1e-12, seed=9)
+    assert pr.d == 1
+    mu_a, A_a, st = run(B, pr, 0, 1e-12)
+    assert st["status"] == 0, st
+    ea, em = errors(pr, mu_a, A_a)
+    assert ea <= 1e-10 and em <= 1e-10, (ea, em)
