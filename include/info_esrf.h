@@ -103,7 +103,8 @@ typedef struct {
    * shift and the spectrum statistics of C.  Used by the cluster-resident
    * FP32 solver for 1-D networks; a system that breaks down or reaches
    * max_iter with it is solved again with P_q^-1 alone.  Convergence is
-   * always tested on the unpreconditioned residual ||b - C_q u||. */
+   * always tested on the unpreconditioned residual ||b - C_q u||.  Other
+   * solvers do not apply it and report so in info_esrf_stats.learned. */
   const float* learned_model;
   double learned_max_shift;  /* > 0: the learned term is used only for shifts sigma = s_q + 1 <= this */
   /* NULL, or a device int32 array receiving each system's PCG iteration
@@ -144,6 +145,12 @@ typedef struct {
   double max_rel_resid;   /* max recurrence ||r|| / ||b|| at exit */
   double ell_used;
   double gershgorin;      /* max_a sum_b |C(a, b)| */
+  /* Learned correction of options.learned_model: 0 no model was given; 1 the
+   * solver that ran applies it (systems with shift <= learned_max_shift);
+   * -1 a model was given but the solver that ran does not apply it (the
+   * analysis is still correct, preconditioned by P_q^-1 alone). */
+  int32_t learned;
+  int32_t pad_;
 } info_esrf_stats;
 
 /* One problem of a batched call: inputs and outputs are device pointers.
@@ -259,15 +266,21 @@ int info_esrf_autotune(const info_esrf_problem* probs, int32_t count, info_esrf_
  * options.max_neighbors, e.g. from info_esrf_neighbor_counts, to shrink the
  * bands).  The call allocates nothing and never calls cudaMalloc/cudaFree.
  *
- * The first call on a device looks up the array's device address with that
- * device current; make that first call before any stream capture.  All
- * calls share the one array, so calls whose GPU work overlaps (other streams,
- * other threads) race and corrupt each other: serialize them.  Every scratch
- * word a call reads is written earlier in the same call, so leftovers of the
- * previous call are harmless.  The call is asynchronous and returns no
- * statistics; device-detected input errors are not reported (use
- * info_esrf_analysis with stats to diagnose).  Arguments and outputs as for
- * info_esrf_analysis. */
+ * Each call looks up the array's device address in the calling thread's
+ * current CUDA context (the primary context of the current device, or a
+ * driver context the caller made current); every context holds its own copy
+ * of the array, and a context re-created after cudaDeviceReset gets a fresh
+ * address.  A call made during stream capture cannot query the runtime and
+ * reuses the address found by the last uncaptured call in the same context,
+ * so make one uncaptured call in each context before any capture (a captured
+ * first call returns INFO_ESRF_ERR_CUDA).  All calls in one context share the
+ * one array, so calls whose GPU work overlaps (other streams, other threads)
+ * race and corrupt each other: serialize them.  Every scratch word a call
+ * reads is written earlier in the same call, so leftovers of the previous
+ * call are harmless.  The call is asynchronous and returns no statistics;
+ * device-detected input errors are not reported (use info_esrf_analysis
+ * with stats to diagnose).  Arguments, outputs and the return codes of
+ * invalid or unsupported arguments are those of info_esrf_analysis. */
 int info_esrf_analysis_noalloc(const info_esrf_grid* grid, int64_t N, const double* X_dev, int64_t d,
                                const int64_t* obs_idx_dev, const double* y_dev, const double* R_diag_dev,
                                int32_t Q, double tol, const info_esrf_options* opt, void* stream,
