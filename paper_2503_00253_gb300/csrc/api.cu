@@ -413,6 +413,7 @@ int run_batch(const info_esrf_problem* probs, int32_t count, const info_esrf_opt
     s.max_rel_resid = rmax;
     s.ell_used = scal[2];
     s.gershgorin = scal[0];
+    s.learned = !pr.learned_model ? 0 : (s.solver_path == 1 ? 1 : -1);
     s.status = status_to_code(status[0]);
     if (s.status < 0 && (worst >= 0 || s.status < worst)) worst = s.status;
     else if (worst == INFO_ESRF_OK && s.status > 0) worst = s.status;

@@ -235,7 +235,7 @@ k_pcg(const ProblemDev* tab, int count, int total_groups, int32_t* counter, T* g
     const int maxit = pr.fixed_iters > 0 ? pr.fixed_iters : pr.max_iter;
     const int pk = pr.kR;   // row stride of Phi / CPhi
 
-    // rr, f = Phi^T r, g = A^T r (+ learned projections) -> preconditioner scalars
+    // rr, f = Phi^T r, g = A^T r -> preconditioner scalars
     auto reduce_residual = [&]() {
 #pragma unroll 1
       for (int j = 0; j < JT; ++j) {
@@ -325,7 +325,7 @@ k_pcg(const ProblemDev* tab, int count, int total_groups, int32_t* counter, T* g
       __syncthreads();
     };
 
-    // z = P^-1 r (+ learned), p = z + beta p
+    // z = P^-1 r, p = z + beta p
     auto update_direction = [&]() {
       for (int64_t a = tid; a < d; a += blockDim.x) {
         const Row<T, JT> r = ld_row<T, JT>(vr, a);
