@@ -57,6 +57,7 @@ extern "C" {
 #define INFO_ESRF_ERR_BAND_OVERFLOW (-7)   /* more neighbours than max_neighbors */
 #define INFO_ESRF_ERR_BREAKDOWN (-8)       /* PCG breakdown (p^T C_q p <= 0) */
 #define INFO_ESRF_ERR_UNSUPPORTED (-9)     /* size beyond a documented limit */
+#define INFO_ESRF_ERR_TIMEOUT (-10)        /* a bounded device wait expired (no hang) */
 
 #define INFO_ESRF_PRECISION_FP64 0         /* every vector and matrix in FP64 */
 #define INFO_ESRF_PRECISION_FP32 1         /* FP32 bulk, FP64 scalars and quadrature sum */

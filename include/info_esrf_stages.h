@@ -153,6 +153,26 @@ int info_esrf_krylov_capture(const info_esrf_grid* grid, int64_t N, const double
 int info_esrf_model_save(const char* path, const float* theta_host, double max_shift);
 int info_esrf_model_load(const char* path, float* theta_host, double* max_shift);
 
+/* Block-sparse BF16 matvec of the BF16 path (App. E: the localized-covariance
+ * product of every PCG iteration, y_j = sigma_j p_j + C p_j for J systems at
+ * once; C is shared by every system, Sec. 2.3), on the fifth-generation tensor
+ * cores.  C (d_pad = 128 n_row_tiles rows and columns) is given as n_tiles
+ * stored 128 x 64 blocks: row tile t owns blocks rowptr[t] .. rowptr[t+1]-1
+ * (rowptr [n_row_tiles + 1], int32, rowptr[0] = 0, rowptr[n_row_tiles] =
+ * n_tiles, every row tile at least one block), block b covering columns
+ * 64 colblk[b] .. 64 colblk[b] + 63 (colblk [n_tiles], < d_pad / 64).  Each
+ * block is two BF16 planes (uint16 bit patterns, row-major [n_tiles][128][64]):
+ * C = C_hi + C_lo.  P [J][d_pad] BF16 directions, sigma [J] FP32 shifts.
+ * Outputs: Y [J][d_pad] FP32 = sigma P + (C_hi + C_lo) P (products exact,
+ * FP32 accumulation) and, if pty_dev is not NULL, pty [n_row_tiles][J] FP32,
+ * the dot product of P_j and Y_j over each row tile's 128 rows.  status_dev
+ * (may be NULL) receives bit 7 if a bounded device wait expired.  Every
+ * pointer 16-byte aligned.  Asynchronous; allocates nothing. */
+int info_esrf_bf16_tile_matvec(int32_t n_row_tiles, const int32_t* rowptr_dev, const int32_t* colblk_dev,
+                               int64_t n_tiles, const uint16_t* C_hi_dev, const uint16_t* C_lo_dev, int32_t J,
+                               const uint16_t* P_dev, const float* sigma_dev, float* Y_dev, float* pty_dev,
+                               int32_t* status_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

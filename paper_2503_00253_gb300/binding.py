@@ -30,6 +30,7 @@ ERR_NONFINITE = -6
 ERR_BAND_OVERFLOW = -7
 ERR_BREAKDOWN = -8
 ERR_UNSUPPORTED = -9
+ERR_TIMEOUT = -10
 
 PRECISION_FP64 = 0
 PRECISION_FP32 = 1
@@ -146,6 +147,8 @@ def library() -> ctypes.CDLL:
         "info_esrf_fma_probe": (c_int32, [c_int32, c_int64, P(c_double), P(c_double), c_void_p]),
         "info_esrf_prepared_band_capacity": (c_int32, [P(Grid), c_int64, c_int64, c_int32, P(Options),
                                                        P(c_int64), P(c_int64)]),
+        "info_esrf_bf16_tile_matvec": (c_int32, [c_int32, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_int32,
+                                                 c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -418,6 +421,28 @@ def autotune(problems: Sequence[dict], options: Options, ws: Optional[torch.Tens
     _check(library().info_esrf_autotune(arr, len(problems), ctypes.byref(options), ws.data_ptr(), ws.numel(),
                                         _stream(stream), ctypes.byref(best)), "info_esrf_autotune")
     return best.value
+
+
+def info_esrf_bf16_tile_matvec(rowptr: torch.Tensor, colblk: torch.Tensor, C_hi: torch.Tensor, C_lo: torch.Tensor,
+                               P: torch.Tensor, sigma: torch.Tensor, want_pty: bool = True, stream=None):
+    """Y = sigma P + (C_hi + C_lo) P for the block-sparse BF16 C (tensor-core stage entry).
+    rowptr int32 [nrt + 1], colblk int32 [tiles], C_hi / C_lo bfloat16 [tiles][128][64],
+    P bfloat16 [J][128 nrt], sigma float32 [J].  Returns (Y float32 [J][d_pad], pty float32 [nrt][J], status)."""
+    _need(rowptr, torch.int32, "rowptr")
+    _need(colblk, torch.int32, "colblk")
+    for t, name in ((C_hi, "C_hi"), (C_lo, "C_lo"), (P, "P")):
+        _need(t, torch.bfloat16, name)
+    _need(sigma, torch.float32, "sigma")
+    nrt = rowptr.numel() - 1
+    J, d_pad = P.shape
+    Y = torch.empty((J, d_pad), dtype=torch.float32, device=P.device)
+    pty = torch.empty((nrt, J), dtype=torch.float32, device=P.device) if want_pty else None
+    status = torch.zeros(1, dtype=torch.int32, device=P.device)
+    _check(library().info_esrf_bf16_tile_matvec(nrt, rowptr.data_ptr(), colblk.data_ptr(), colblk.numel(),
+                                                C_hi.data_ptr(), C_lo.data_ptr(), J, P.data_ptr(), sigma.data_ptr(),
+                                                Y.data_ptr(), pty.data_ptr() if want_pty else None,
+                                                status.data_ptr(), _stream(stream)), "info_esrf_bf16_tile_matvec")
+    return Y, pty, status
 
 
 def info_esrf_philox_normals(seed: int, count: int, device="cuda", stream=None) -> torch.Tensor:

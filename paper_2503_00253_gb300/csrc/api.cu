@@ -251,6 +251,8 @@ int status_to_code(int32_t bits) {
   if (bits & kStatBadR) return INFO_ESRF_ERR_NONPOSITIVE_R;
   if (bits & kStatNonFinite) return INFO_ESRF_ERR_NONFINITE;
   if (bits & kStatBandOverflow) return INFO_ESRF_ERR_BAND_OVERFLOW;
+  if (bits & kStatTimeout) return INFO_ESRF_ERR_TIMEOUT;
+  if (bits & kStatTileOverflow) return INFO_ESRF_ERR_BAND_OVERFLOW;
   if (bits & kStatBreakdown) return INFO_ESRF_ERR_BREAKDOWN;
   if (bits & kStatNotConverged) return INFO_ESRF_NOT_CONVERGED;
   return INFO_ESRF_OK;
@@ -477,6 +479,7 @@ const char* info_esrf_error_string(int code) {
     case INFO_ESRF_ERR_BAND_OVERFLOW: return "more neighbours than the band capacity";
     case INFO_ESRF_ERR_BREAKDOWN: return "PCG breakdown";
     case INFO_ESRF_ERR_UNSUPPORTED: return "size beyond a documented limit";
+    case INFO_ESRF_ERR_TIMEOUT: return "a bounded device wait expired";
     default: return "unknown status";
   }
 }

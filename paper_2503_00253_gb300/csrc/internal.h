@@ -1,6 +1,7 @@
 // Internal layout shared by the host API and the kernels (not part of the ABI).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -26,7 +27,30 @@ enum : int32_t {
   kStatBreakdown = 1 << 4,     // PCG breakdown (p^T A p <= 0 or NaN)
   kStatNotConverged = 1 << 5,  // iteration cap reached
   kStatEigFail = 1 << 6,       // randomized eigensolver lost rank
+  kStatTimeout = 1 << 7,       // a bounded device wait expired
+  kStatTileOverflow = 1 << 8,  // more C blocks than the tile capacity
 };
+
+// BF16 block-tile path: C stored in 128 x 64 blocks (row tile x column block)
+// of tile-ordered observations.
+constexpr int kTileM = 128;
+constexpr int kTileK = 64;
+
+struct TileMmArgs {
+  const int32_t* rowptr;        // [nrt + 1] first block of each row tile
+  const int32_t* colblk;        // [tiles] column block of each stored block
+  const __nv_bfloat16* P;       // [J][d_pad] directions
+  const float* sigma;           // [J] shifts
+  const int32_t* active;        // [nchunks] nonzero: chunk has an unconverged system (or NULL: all)
+  float* Y;                     // [J][d_pad] sigma p + C p
+  float* pty;                   // [nrt][J] partial p^T y per row tile (or NULL)
+  int32_t* status;              // status bits (kStatTimeout), or NULL
+  int64_t d_pad;
+  int32_t J, nrt, nchunks;
+};
+// Systems per CTA of the tile matvec for J systems (128 or 256).
+int tile_chunk_width(int32_t J);
+int launch_tile_mm(TileMmArgs a, const void* chi, const void* clo, int64_t ntiles, cudaStream_t st);
 
 struct GridDev {
   int64_t ext[3];
@@ -104,6 +128,41 @@ struct ProblemDev {
   double* relres;       // [nsys] final ||r|| / ||b|| (recurrence)
   double* Vbar;         // [d][N + 1] FP64 R^-1/2 sum_q p_q u_q (last column: mean)
   void* VbarT;          // [d][N + 1] T copy for the state apply
+  // BF16 block-tile path (precision 2).  Observations are numbered in tile
+  // order: position a' of original observation a is the rank of the Morton
+  // code of its grid point.  C is stored in 128 x 64 blocks (kTileM x kTileK)
+  // of tile-ordered rows and columns; the state update runs over state tiles
+  // of 128 consecutive grid points against the same 64-column blocks.
+  int32_t nrt, nblk;            // row tiles (d_pad / 128), column blocks (d_pad / 64)
+  int32_t nst, nsort;           // state tiles (ceil(n / 128)); sort length (power of two >= d)
+  int64_t d_pad, tile_cap, st_cap;
+  uint64_t* skey;               // [nsort] Morton keys (sort scratch)
+  int32_t* sidx;                // [nsort] original observation of each key
+  int32_t* tpos_src;            // [d_pad] original observation at tile position (-1: padding)
+  int32_t* obs_tpos;            // [d] tile position of each original observation
+  int32_t* tbox;                // [nblk][6] bounding box of each column block (lo, hi per axis)
+  int32_t* tcount;              // [nrt + nst] blocks per row tile / state tile
+  int32_t* rowptr;              // [nrt + 1] first stored block of each row tile
+  int32_t* colblk;              // [tile_cap] column block of each stored block
+  int32_t* st_rowptr;           // [nst + 1]
+  int32_t* st_colblk;           // [st_cap]
+  __nv_bfloat16* Chi;           // [tile_cap][128][64] bf16(C)
+  __nv_bfloat16* Clo;           // [tile_cap][128][64] bf16(C - Chi)
+  float* Wp;                    // [d_pad][N] W in tile order (0 at padding)
+  float* rinvp;                 // [d_pad] R^-1/2 in tile order (0 at padding)
+  // BF16 PCG state: systems j = sid (mean first, then q * N + i), J = nsys
+  __nv_bfloat16* Pdir;          // [J][d_pad] search directions (bf16, as used)
+  float* Yv;                    // [J][d_pad] sigma p + C p
+  float* Xv;                    // [J][d_pad] iterates
+  float* Rv;                    // [J][d_pad] residuals
+  float* pty;                   // [nrt][J] p^T y per row tile
+  double* dots;                 // [nsub][J][2 kR + 1] partial r^T r, Phi^T r, (C Phi)^T r
+  double* sysd;                 // [J][8] per-system scalars (see tile_pcg.cu)
+  float* lcoef;                 // [J][2 kR] LMP coefficients of the current direction update
+  float* sigmaf;                // [J] shift per system (FP32)
+  int32_t* active;              // [J] 1 while the system runs
+  int32_t* chunk_active;        // [nchunks] 1 while a chunk of the tile matvec has a running system
+  int32_t* nactive;             // [2] running systems; iterations done
 };
 
 // Launch plan of the multi-shift CG kernel (host side): CTAs per cluster,
