@@ -61,6 +61,15 @@ extern "C" {
 
 #define INFO_ESRF_PRECISION_FP64 0         /* every vector and matrix in FP64 */
 #define INFO_ESRF_PRECISION_FP32 1         /* FP32 bulk, FP64 scalars and quadrature sum */
+/* BF16 tensor-core matvec (block-tile path): C formed in FP32 and kept as
+ * two BF16 planes hi + lo (about 16 significant bits), search directions in
+ * BF16, products on the tensor cores with FP32 accumulation; iterates,
+ * residuals and the preconditioner in FP32; CG scalars, partial-sum merges
+ * and the quadrature sum in FP64.  Any grid (1-D, 2-D, layered), subsampling
+ * observations only, N <= 128, solver PCG.  The call synchronizes its stream
+ * once per PCG iteration (convergence is tested on the host), so it cannot be
+ * captured in a CUDA graph. */
+#define INFO_ESRF_PRECISION_BF16 2
 
 #define INFO_ESRF_RULE_ELLIPTIC 0          /* App. D, Eq. elliptic_quadrature_rule */
 #define INFO_ESRF_RULE_GAUSS_LEGENDRE 1    /* App. D, Eq. gaussian_quadrature_rule */
@@ -132,6 +141,13 @@ typedef struct {
    * INFO_ESRF_ERR_UNSUPPORTED. */
   int32_t solver;
   int32_t reserved_;
+  /* BF16 path: stored 128 x 64 blocks of C (tile_capacity) and of the state
+   * update (state_tile_capacity) to reserve in the workspace; <= 0: an
+   * estimate from the geometry and the mean observation density (1.3 x the
+   * count for evenly spread observations).  More blocks than reserved make
+   * the call return INFO_ESRF_ERR_BAND_OVERFLOW. */
+  int64_t tile_capacity;
+  int64_t state_tile_capacity;
 } info_esrf_options;
 
 typedef struct {
@@ -142,7 +158,7 @@ typedef struct {
   double iters_mean;
   int32_t n_unconverged;
   int32_t solver_path;    /* 1: cluster-resident band kernel (1-D networks), 0: general kernel,
-                             2: multi-shift CG */
+                             2: multi-shift CG, 3: BF16 block-tile path (tensor cores) */
   double max_rel_resid;   /* max recurrence ||r|| / ||b|| at exit */
   double ell_used;
   double gershgorin;      /* max_a sum_b |C(a, b)| */

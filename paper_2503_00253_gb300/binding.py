@@ -34,6 +34,7 @@ ERR_TIMEOUT = -10
 
 PRECISION_FP64 = 0
 PRECISION_FP32 = 1
+PRECISION_BF16 = 2
 RULE_ELLIPTIC = 0
 RULE_GAUSS_LEGENDRE = 1
 SOLVER_PCG = 0
@@ -54,7 +55,8 @@ class Options(ctypes.Structure):
                 ("rule", c_int32), ("cluster_size", c_int32), ("ell", c_double), ("seed", c_uint64),
                 ("max_neighbors", c_int64), ("learned_model", c_void_p), ("learned_max_shift", c_double),
                 ("system_iters", c_void_p), ("phase_events", ctypes.POINTER(c_void_p)),
-                ("solver", c_int32), ("reserved_", c_int32)]
+                ("solver", c_int32), ("reserved_", c_int32), ("tile_capacity", c_int64),
+                ("state_tile_capacity", c_int64)]
 
 
 class Stats(ctypes.Structure):
@@ -194,7 +196,8 @@ def make_options(precision: int = PRECISION_FP64, ritz_rank: int = 10, oversampl
                  rule: int = RULE_ELLIPTIC, ell: float = 0.0, seed: int = 0x1234ABCD,
                  max_neighbors: int = 0, learned_model: Optional[torch.Tensor] = None,
                  learned_max_shift: float = 0.0, system_iters: Optional[torch.Tensor] = None,
-                 cluster_size: int = 0, solver: int = SOLVER_PCG) -> Options:
+                 cluster_size: int = 0, solver: int = SOLVER_PCG, tile_capacity: int = 0,
+                 state_tile_capacity: int = 0) -> Options:
     o = Options()
     library().info_esrf_default_options(ctypes.byref(o))
     o.precision, o.ritz_rank, o.oversample, o.power_iters = precision, ritz_rank, oversample, power_iters
@@ -202,6 +205,7 @@ def make_options(precision: int = PRECISION_FP64, ritz_rank: int = 10, oversampl
     o.max_neighbors = max_neighbors
     o.cluster_size = cluster_size
     o.solver = solver
+    o.tile_capacity, o.state_tile_capacity = tile_capacity, state_tile_capacity
     if system_iters is not None:
         _need(system_iters, torch.int32, "system_iters")
         o.system_iters = system_iters.data_ptr()

@@ -97,7 +97,8 @@ int64_t geometric_bound(const GridDev& g, int64_t d) {
 int check_options(const info_esrf_options* in, info_esrf_options* out) {
   info_esrf_default_options(out);
   if (in) *out = *in;
-  if (out->precision != 0 && out->precision != 1) return INFO_ESRF_ERR_INVALID_ARG;
+  if (out->precision != 0 && out->precision != 1 && out->precision != 2) return INFO_ESRF_ERR_INVALID_ARG;
+  if (out->precision == 2 && out->solver != INFO_ESRF_SOLVER_PCG) return INFO_ESRF_ERR_UNSUPPORTED;
   if (out->ritz_rank < 0 || out->ritz_rank > kMaxK) return INFO_ESRF_ERR_UNSUPPORTED;
   if (out->oversample < 0) return INFO_ESRF_ERR_INVALID_ARG;
   if (out->power_iters < 0 || out->power_iters > 8) return INFO_ESRF_ERR_INVALID_ARG;
@@ -112,6 +113,81 @@ int check_options(const info_esrf_options* in, info_esrf_options* out) {
 }
 
 // Fills pr (sizes, options) and carves its workspace slice.
+// Volume (cells) of a box of extents P dilated by the axis-aligned ellipsoid
+// of half-axes R (Steiner formula: sum over axis subsets S of the box's
+// extents outside S times the |S|-ball volume times prod R over S).
+double dilated_volume(const double* P, const double* R, int na) {
+  static const double omega[4] = {1.0, 2.0, M_PI, 4.0 * M_PI / 3.0};
+  double vol = 0.0;
+  for (int mask = 0; mask < (1 << na); ++mask) {
+    double v = 1.0;
+    int k = 0;
+    for (int a = 0; a < na; ++a) {
+      if (mask & (1 << a)) {
+        v *= R[a];
+        ++k;
+      } else {
+        v *= P[a];
+      }
+    }
+    vol += omega[k] * v;
+  }
+  return vol;
+}
+
+// Estimated stored blocks per row of the BF16 path: a row tile (state = false,
+// a Morton patch of kTileM observations) or a state tile (kTileM consecutive
+// grid points) against column blocks (Morton patches of kTileK observations),
+// for observations spread evenly at density d / n; 1.3 x plus 4 of margin.
+int64_t tile_blocks_estimate(const GridDev& g, int64_t n, int64_t d, bool state) {
+  const double rho = (double)d / (double)n;
+  auto patch = [&](double cnt, double* e) {
+    for (int ax = 0; ax < 3; ++ax) e[ax] = 1.0;
+    for (int guard = 0; guard < 200; ++guard) {
+      double cells = 1.0;
+      for (int ax = 0; ax < 3; ++ax) cells *= e[ax];
+      if (cells * rho >= cnt) break;
+      int best = -1;
+      for (int ax = 0; ax < 3; ++ax)
+        if (g.ext[ax] > 1 && e[ax] < (double)g.ext[ax] && (best < 0 || e[ax] < e[best])) best = ax;
+      if (best < 0) break;
+      e[best] = std::min(2.0 * e[best], (double)g.ext[best]);
+    }
+  };
+  double Pr[3], Pb[3];
+  patch((double)kTileK, Pb);
+  if (state) {
+    double left = (double)kTileM;
+    for (int ax = 0; ax < 3; ++ax) {
+      Pr[ax] = std::min(left, (double)g.ext[ax]);
+      left = std::ceil(left / (double)g.ext[ax]);
+    }
+  } else {
+    patch((double)kTileM, Pr);
+  }
+  double P[3], R[3], whole = 1.0;
+  int na = 0;
+  for (int ax = 0; ax < 3; ++ax) {
+    if (g.ext[ax] <= 1) continue;
+    const double span = Pr[ax] + Pb[ax] + 2.0 * (double)g.reach[ax];
+    if (g.whole[ax] || span >= (double)g.ext[ax]) {
+      whole *= (double)g.ext[ax];   // the support wraps this axis: all of it
+      continue;
+    }
+    P[na] = Pr[ax] + Pb[ax];
+    R[na] = (double)g.reach[ax];
+    ++na;
+  }
+  const double cells = whole * (na ? dilated_volume(P, R, na) : 1.0);
+  return (int64_t)std::ceil(1.3 * cells * rho / (double)kTileK) + 4;
+}
+
+int64_t next_pow2(int64_t v) {
+  int64_t p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
 void carve_problem(Carver& cv, ProblemDev& pr, const info_esrf_options& o) {
   const size_t esz = o.precision == 0 ? 8 : 4;
   const int64_t n = pr.n, N = pr.N, d = pr.d;
@@ -141,13 +217,44 @@ void carve_problem(Carver& cv, ProblemDev& pr, const info_esrf_options& o) {
   pr.CPhi = cv.take<void>((size_t)d * k * esz);
   pr.theta = cv.take<double>((size_t)k * 8);
   pr.gram = cv.take<double>((size_t)3 * k * k * 8);
-  pr.U = cv.take<void>((size_t)pr.nsys * d * esz);
+  pr.U = cv.take<void>(o.precision == 2 ? 0 : (size_t)pr.nsys * d * esz);
   pr.iters = cv.take<int32_t>((size_t)pr.nsys * 4);
   pr.relres = cv.take<double>((size_t)pr.nsys * 8);
   pr.Vbar = cv.take<double>((size_t)d * (N + 1) * 8);
   pr.VbarT = cv.take<void>((size_t)d * (N + 1) * esz);
   pr.learn_coef = cv.take<float>((size_t)(pr.Q + 1) * kLearnOut * 4);
   pr.learn_T = cv.take<float>((size_t)(pr.Q + 1) * kLearnT * 4);
+  if (o.precision == 2) {
+    const int64_t J = pr.nsys, dp = pr.d_pad, kk = pr.kR;
+    const int bn = tile_chunk_width((int32_t)std::max<int64_t>(J, 1));
+    const int64_t nsub = (dp + kTileDotRows - 1) / kTileDotRows;
+    pr.skey = cv.take<uint64_t>((size_t)pr.nsort * 8);
+    pr.sidx = cv.take<int32_t>((size_t)pr.nsort * 4);
+    pr.tpos_src = cv.take<int32_t>((size_t)dp * 4);
+    pr.obs_tpos = cv.take<int32_t>((size_t)pr.d * 4);
+    pr.tbox = cv.take<int32_t>((size_t)pr.nblk * 6 * 4);
+    pr.tcount = cv.take<int32_t>((size_t)(pr.nrt + pr.nst) * 4);
+    pr.rowptr = cv.take<int32_t>((size_t)(pr.nrt + 1) * 4);
+    pr.colblk = cv.take<int32_t>((size_t)pr.tile_cap * 4);
+    pr.st_rowptr = cv.take<int32_t>((size_t)(pr.nst + 1) * 4);
+    pr.st_colblk = cv.take<int32_t>((size_t)pr.st_cap * 4);
+    pr.Chi = cv.take<__nv_bfloat16>((size_t)pr.tile_cap * kTileM * kTileK * 2);
+    pr.Clo = cv.take<__nv_bfloat16>((size_t)pr.tile_cap * kTileM * kTileK * 2);
+    pr.Wp = cv.take<float>((size_t)dp * N * 4);
+    pr.rinvp = cv.take<float>((size_t)dp * 4);
+    pr.Pdir = cv.take<__nv_bfloat16>((size_t)J * dp * 2);
+    pr.Yv = cv.take<float>((size_t)J * dp * 4);
+    pr.Xv = cv.take<float>((size_t)J * dp * 4);
+    pr.Rv = cv.take<float>((size_t)J * dp * 4);
+    pr.pty = cv.take<float>((size_t)pr.nrt * J * 4);
+    pr.dots = cv.take<double>((size_t)nsub * J * (2 * kk + 1) * 8);
+    pr.sysd = cv.take<double>((size_t)J * 8 * 8);
+    pr.lcoef = cv.take<float>((size_t)J * 2 * kMaxK * 4);
+    pr.sigmaf = cv.take<float>((size_t)J * 4);
+    pr.active = cv.take<int32_t>((size_t)J * 4);
+    pr.chunk_active = cv.take<int32_t>((size_t)((J + bn - 1) / bn) * 4);
+    pr.nactive = cv.take<int32_t>(2 * 4);
+  }
 }
 
 // Builds the host table for a batch; with ws == nullptr only sizes it.
@@ -196,7 +303,24 @@ int build_table(const info_esrf_problem* probs, int32_t count, const info_esrf_o
     pr.ell_fixed = o.ell;
     pr.seed = o.seed;
     pr.sqrt_nm1 = sqrt((double)(pr.N - 1));
-    if (general_h) {
+    if (o.precision == 2) {
+      // BF16 block-tile path: no bands; tile counts and capacities
+      if (general_h || pr.N > tile_max_members()) return INFO_ESRF_ERR_UNSUPPORTED;
+      pr.max_oo = 0;
+      pr.max_xo = 0;
+      pr.d_pad = (pr.d + kTileM - 1) / kTileM * kTileM;
+      pr.nrt = (int32_t)(pr.d_pad / kTileM);
+      pr.nblk = (int32_t)(pr.d_pad / kTileK);
+      pr.nst = (int32_t)((pr.n + kTileM - 1) / kTileM);
+      pr.nsort = std::max<int64_t>(1024, next_pow2(pr.d));
+      const int64_t est_c = std::min<int64_t>(pr.nblk, tile_blocks_estimate(pr.grid, pr.n, pr.d, false));
+      const int64_t est_s = std::min<int64_t>(pr.nblk, tile_blocks_estimate(pr.grid, pr.n, pr.d, true));
+      pr.tile_cap = o.tile_capacity > 0 ? o.tile_capacity : (int64_t)pr.nrt * est_c;
+      pr.st_cap = o.state_tile_capacity > 0 ? o.state_tile_capacity : (int64_t)pr.nst * est_s;
+      pr.tile_cap = std::max<int64_t>(pr.tile_cap, pr.nrt);
+      pr.st_cap = std::max<int64_t>(pr.st_cap, 1);
+      if (pr.tile_cap * kTileM >= (int64_t(1) << 31) || pr.st_cap >= INT32_MAX) return INFO_ESRF_ERR_UNSUPPORTED;
+    } else if (general_h) {
       // dense covariances: every row of C and of Sxh holds all d columns
       if (pr.n * pr.d > (int64_t(1) << 28)) return INFO_ESRF_ERR_UNSUPPORTED;
       pr.max_oo = pr.d;
@@ -320,8 +444,22 @@ int run_batch(const info_esrf_problem* probs, int32_t count, const info_esrf_opt
   mark(0);
   launch_prepare(tab, dtab, st);
   launch_anomalies(tab, dtab, st);
-  launch_band_obs(tab, dtab, st);
-  if (o.solver == INFO_ESRF_SOLVER_MULTISHIFT) {
+  if (o.precision == INFO_ESRF_PRECISION_BF16) {
+    // block-tile path: tile order and C blocks, quadrature, Ritz pairs over
+    // the blocks, then each problem's PCG loop (host-driven) and the finish
+    launch_tile_setup(tab, dtab, st);
+    launch_quadrature(tab, dtab, st);
+    mark(1);
+    launch_ritz(tab, dtab, st);
+    mark(2);
+    for (int i = 0; i < count; ++i) {
+      const int r = run_tile_pcg(tab.p[i], dtab + i, st);
+      if (r != 0) return r;
+    }
+    mark(3);
+    launch_tile_finish(tab, dtab, st);
+  } else if (o.solver == INFO_ESRF_SOLVER_MULTISHIFT) {
+    launch_band_obs(tab, dtab, st);
     // no Ritz stage and no learned coefficients: the quadrature and the
     // state-obs band run on the side stream while nothing else waits
     AuxStream* aux = aux_stream();
@@ -344,6 +482,7 @@ int run_batch(const info_esrf_problem* probs, int32_t count, const info_esrf_opt
     if (aux) cudaStreamWaitEvent(st, aux->jb, 0);
     launch_finish(tab, dtab, st, false);
   } else {
+    launch_band_obs(tab, dtab, st);
     // the quadrature and the state-obs band overlap the Ritz stage on a side
     // stream, which rejoins before the first use of each
     AuxStream* aux = aux_stream();
@@ -407,7 +546,7 @@ int run_batch(const info_esrf_problem* probs, int32_t count, const info_esrf_opt
       if (o.fixed_iters <= 0 && !(rr[sidx] <= pr.tol)) ++unconv;
     }
     s.device_flags = status[0];
-    s.solver_path = (status[1] & 2) ? 2 : (status[1] & 1);
+    s.solver_path = o.precision == INFO_ESRF_PRECISION_BF16 ? 3 : (status[1] & 2) ? 2 : (status[1] & 1);
     s.iters_max = it_max;
     s.n_systems = (int32_t)live;
     s.iters_mean = live ? (double)sum_it / (double)live : 0.0;

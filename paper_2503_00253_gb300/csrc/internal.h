@@ -51,6 +51,17 @@ struct TileMmArgs {
 // Systems per CTA of the tile matvec for J systems (128 or 256).
 int tile_chunk_width(int32_t J);
 int launch_tile_mm(TileMmArgs a, const void* chi, const void* clo, int64_t ntiles, cudaStream_t st);
+constexpr int kTileDotRows = 512;   // rows per partial dot product of the BF16 PCG
+struct ProblemDev;
+struct ProblemTable;
+int64_t tile_max_members();
+// Set-up (tile order, block patterns, C blocks), the Ritz-stage matvec, the
+// per-problem PCG loop (synchronizes the stream once per iteration) and the
+// finish (quadrature sum and state update) of the BF16 path.
+void launch_tile_setup(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st);
+void launch_tile_ritz_matvec(const ProblemTable& tab, const ProblemDev* dtab, int src, cudaStream_t st);
+int run_tile_pcg(const ProblemDev& p, const ProblemDev* dp, cudaStream_t st);
+void launch_tile_finish(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st);
 
 struct GridDev {
   int64_t ext[3];

@@ -1139,8 +1139,10 @@ __global__ void k_ritz_grams(const ProblemDev* tab) {
   if (threadIdx.x == 0) pr.gram[e] = out[0];
 }
 
+// tile = true: the BF16 block-tile path, whose C exists only as stored blocks;
+// the matvec of the range finder then runs over those blocks (FP32 basis).
 template <typename T>
-static void launch_ritz_t(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st) {
+static void launch_ritz_t(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st, bool tile = false) {
   int64_t dl = 0, dmax = 0;
   int lmax = 0, kmax = 0;
   for (int i = 0; i < tab.count; ++i) {
@@ -1157,6 +1159,10 @@ static void launch_ritz_t(const ProblemTable& tab, const ProblemDev* dtab, cudaS
   const dim3 gll((unsigned)(lmax * lmax), tab.count);
   int cur = 0;   // buffer holding the current basis candidate
   auto matvec = [&]() {   // buf[1 - cur] = C buf[cur]
+    if (tile) {
+      launch_tile_ritz_matvec(tab, dtab, cur, st);
+      return;
+    }
     k_ritz_matvec<T><<<gdw, 256, 0, st>>>(dtab, cur);
     note_launches(1);
   };
@@ -1189,6 +1195,10 @@ static void launch_ritz_t(const ProblemTable& tab, const ProblemDev* dtab, cudaS
 void launch_ritz(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st) {
   if (tab.p[0].precision == 0) {
     launch_ritz_t<double>(tab, dtab, st);
+    return;
+  }
+  if (tab.p[0].precision == 2) {
+    launch_ritz_t<float>(tab, dtab, st, true);
     return;
   }
   // FP32: one cluster launch for the whole stage when every problem fits it
