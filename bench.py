@@ -485,6 +485,184 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def config5_record(B, dev, steps, warmup, no_parity=False, ritz=RITZ):
+    """The 2-D workload at full size: periodic 1024 x 1024 grid (n = 1,048,576), N = 80 from a
+    Gaussian covariance with length scale 32 cells, observations every 2nd cell in each direction
+    (d = 262,144), R = 0.5, Gaspari-Cohn half-width 96 cells, Q = 32 (2560 + 1 systems), on the BF16
+    block-tile path (tensor-core matvec), tol 1e-6.  Direct calls timed with CUDA events (the path
+    synchronizes once per PCG iteration, so it is not captured in a graph); inputs and workspace
+    (about 70 GB) are far larger than L2.  The roofline is that of the tensor-core matvec: algorithmic
+    FLOPs 2 nnz(C) + 2 d per system-iteration over the summed device time of its launches, against
+    the measured sustained BF16 tensor peak."""
+    import numpy as np
+    import torch
+
+    from paper_2503_00253_gb300 import workloads
+    t0 = time.perf_counter()
+    pr = workloads.config5(tol=TOL_MIXED)
+    gen_s = time.perf_counter() - t0
+    X = torch.tensor(pr.X, device=dev)
+    obs = torch.tensor(pr.obs_idx, device=dev)
+    y = torch.tensor(pr.y, device=dev)
+    R = torch.tensor(pr.R, device=dev)
+    N, n = pr.X.shape
+    it_sys = torch.zeros(1 + pr.Q * N, dtype=torch.int32, device=dev)
+    opts = B.make_options(precision=B.PRECISION_BF16, ritz_rank=ritz, oversample=min(10, 32 - ritz),
+                          system_iters=it_sys)
+    import ctypes
+    g = B.make_grid(pr.grid)
+    need = B.library().info_esrf_workspace_size(ctypes.byref(g), N, pr.d, pr.Q, ctypes.byref(opts))
+    wsp = B.workspace(need, dev)
+    mu_a = torch.empty(n, dtype=torch.float64, device=dev)
+    A_a = torch.empty((N, n), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    events = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    for e in events:
+        e.record(stream)           # torch creates the CUDA event at its first record
+    B.set_phase_events(opts, events)
+    times, stats, phases = [], [], []
+    for s_ in range(warmup + steps):
+        e0.record(stream)
+        st = B.info_esrf_analysis(pr.grid, X, obs, y, R, pr.Q, TOL_MIXED, opts, ws=wsp, mu_a=mu_a, A_a=A_a,
+                                  stats=True, stream=stream)[2]
+        e1.record(stream)
+        e1.synchronize()
+        if s_ >= warmup:
+            times.append(e0.elapsed_time(e1))
+            stats.append(st)
+            phases.append([events[i].elapsed_time(events[i + 1]) for i in range(4)])
+    B.set_phase_events(opts, None)
+    its = it_sys.cpu().numpy().astype(np.float64)
+    st = stats[-1]
+    flops = float(np.sum(its)) * (2.0 * st["c_nnz"] + 2.0 * pr.d)
+    mm_ms = statistics.mean(x["matvec_ms"] for x in stats)
+    peaks = _measured_peaks()
+    peak = peaks.get("bf16_tflops_sustained")
+    achieved = flops / (mm_ms * 1e-3) / 1e12
+    issued_per_alg = (st["tile_blocks"] * 128 * 64 * 2.0) / st["c_nnz"]
+    rec = {"workload": "gauss2d_1024x1024_N80_d262144_Q32_R0.5_gc96 (2560 shifted systems + mean)",
+           "precision": "bf16 tensor-core matvec (C as hi + lo BF16 planes, BF16 directions), fp32 vectors, "
+                        "fp64 scalars and quadrature sum",
+           "value": 1e3 / statistics.mean(times), "unit": UNIT, "ms_per_step": statistics.mean(times),
+           "steps": steps, "warmup": warmup, "launch": "direct calls (one stream sync per PCG iteration)",
+           "tol": TOL_MIXED, "ritz_rank": ritz, "iters_mean": st["iters_mean"], "iters_max": st["iters_max"],
+           "n_unconverged": st["n_unconverged"], "status": st["status"], "solver_path": st["solver_path"],
+           "c_nnz": st["c_nnz"], "taps_per_row": st["c_nnz"] / pr.d, "tile_blocks": st["tile_blocks"],
+           "workspace_gb": need / 1e9, "input_gen_s": gen_s, "ell": st["ell_used"], "gershgorin": st["gershgorin"],
+           "phases_ms": {k: statistics.mean(p[i] for p in phases)
+                         for i, k in enumerate(["setup_a1_a3", "ritz_a4", "pcg_a5_a8", "finish_a9_a11"])},
+           "iters_hist": np.histogram(its, bins=[0, 10, 20, 40, 80, 160, 320, 640, 2000])[0].tolist(),
+           "roofline": {"bound": "tensor", "kernel": "k_tile_mm (tcgen05.mma kind::f16, TMA-staged)",
+                        "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                        "frac": (achieved / peak) if peak else None,
+                        "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (measured)",
+                        "traffic": None, "matvec_ms_per_analysis": mm_ms,
+                        "matvec_launches": stats[-1]["matvec_launches"], "flops_per_analysis": flops,
+                        "issued_tensor_flops_per_algorithmic": issued_per_alg,
+                        "issued_tensor_tflops": achieved * issued_per_alg}}
+    if not no_parity:
+        # at this size the oracle cannot form the update; a property that holds at any size:
+        # the analysis perturbations keep zero ensemble mean (Thm. 3, linearity of the solves)
+        A = A_a.cpu().numpy()
+        Af = pr.X - pr.X.mean(0)
+        rec["zero_mean_rel"] = float(np.max(np.abs(A.sum(0))) / np.max(np.abs(A - Af)))
+    del wsp
+    torch.cuda.empty_cache()
+    return rec
+
+
+def run_config5(args):
+    import torch
+
+    from paper_2503_00253_gb300 import binding as B
+    _, rank, local = _dist()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.library()
+    rec = config5_record(B, dev, args.steps, args.warmup, args.no_parity, args.ritz)
+    line = {"metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": rec["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": rec["workload"], "precision": rec["precision"], "launch": rec["launch"],
+                       "l2": "inputs and workspace far larger than L2"},
+            "roofline": rec["roofline"], "config5": rec}
+    print(json.dumps(line), flush=True)
+
+
+def run_tilemm(args):
+    """The tensor-core block-tile matvec alone (stage entry info_esrf_bf16_tile_matvec), on a seeded
+    synthetic block structure with the 2-D workload's shape per row tile: 256 row tiles of 128
+    observations (d_pad = 32,768), 300 stored 128 x 64 blocks per row tile (hi + lo BF16 planes),
+    J = 2561 systems (11 chunks of 256).  About 3 GB on the device, more than L2.  Timed with CUDA
+    events per launch after warm-up; FLOPs counted as issued by the tensor cores (two planes,
+    2 x 128 x 64 x 256 per block and chunk)."""
+    import numpy as np
+    import torch
+
+    from paper_2503_00253_gb300 import binding as B
+    _, rank, local = _dist()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.library()
+    nrt, per_row, J = 256, 300, 2561
+    nblk = 2 * nrt
+    rng = np.random.default_rng(17)
+    cols = np.stack([np.sort(rng.choice(nblk, size=per_row, replace=False)) for _ in range(nrt)])
+    rowptr = torch.tensor(np.arange(nrt + 1) * per_row, dtype=torch.int32, device=dev)
+    colblk = torch.tensor(cols.reshape(-1), dtype=torch.int32, device=dev)
+    ntiles = nrt * per_row
+    gen = torch.Generator(device=dev).manual_seed(5)
+    C = torch.randn((ntiles, 128, 64), device=dev, generator=gen)
+    C_hi = C.to(torch.bfloat16)
+    C_lo = (C - C_hi.float()).to(torch.bfloat16)
+    del C
+    torch.cuda.empty_cache()
+    P = torch.randn((J, 128 * nrt), device=dev, generator=gen).to(torch.bfloat16)
+    sigma = torch.rand(J, device=dev, generator=gen) + 1.0
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        B.info_esrf_bf16_tile_matvec(rowptr, colblk, C_hi, C_lo, P, sigma, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ts = []
+    for _ in range(args.steps):
+        e0.record(stream)
+        _, _, status = B.info_esrf_bf16_tile_matvec(rowptr, colblk, C_hi, C_lo, P, sigma, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    assert int(status.item()) == 0
+    nchunks = (J + 255) // 256
+    flops = ntiles * nchunks * 2 * 2.0 * 128 * 64 * 256
+    nbytes = ntiles * 2 * 16384 + 2.0 * J * 128 * nrt + 4.0 * J * 128 * nrt
+    ms = statistics.mean(ts)
+    peaks = _measured_peaks()
+    peak = peaks.get("bf16_tflops")
+    line = {"metric": "tensor-core block-tile matvec TFLOP/s (issued)", "value": flops / (ms * 1e-3) / 1e12,
+            "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": f"tilemm: {nrt} row tiles x {per_row} blocks, J={J}", "ntiles": ntiles},
+            "roofline": {"bound": "tensor", "achieved": flops / (ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": (flops / (ms * 1e-3) / 1e12 / peak) if peak else None,
+                         "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, measured)",
+                         "min_bytes": nbytes, "min_bytes_gbs": nbytes / (ms * 1e-3) / 1e9}}
+    print(json.dumps(line), flush=True)
+
+
 def run_batched(args):
     """Config-4 workload: 64 independent uneven 1-D problems (n log-uniform in [1024, 65536], N in
     {20, 40, 80}, observation stride 4..16, Q 16..48, seed 4) as one batched call (one launch per
@@ -622,16 +800,22 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="config2", choices=["config2", "batched64"],
+    ap.add_argument("--ritz", type=int, default=RITZ, help="Ritz rank of the preconditioner (config5)")
+    ap.add_argument("--workload", default="config2", choices=["config2", "batched64", "config5", "tilemm"],
                     help="config2: the headline single analysis; batched64: 64 uneven problems in one batched "
                          "call against 64 single calls")
     args = ap.parse_args()
-    if args.warmup < 3:
-        args.warmup = 3
+    if args.warmup < 3 and args.workload != "config5":
+        args.warmup = 3   # config5: one analysis takes seconds; --warmup as given (at least 1)
+    args.warmup = max(args.warmup, 1)
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched64":
         run_batched(args)
+    elif args.workload == "config5":
+        run_config5(args)
+    elif args.workload == "tilemm":
+        run_tilemm(args)
     else:
         run_ours(args)
 

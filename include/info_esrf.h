@@ -168,6 +168,16 @@ typedef struct {
    * analysis is still correct, preconditioned by P_q^-1 alone). */
   int32_t learned;
   int32_t pad_;
+  /* BF16 path (solver_path 3), zero otherwise: device time of the
+   * tensor-core matvec launches, summed from CUDA events recorded on the
+   * call's stream around each launch; their count; the stored 128 x 64 blocks
+   * of C; and the nonzeros of C (entries inside the Gaspari-Cohn support,
+   * counted while forming the blocks). */
+  double matvec_ms;
+  int64_t tile_blocks;
+  double c_nnz;
+  int32_t matvec_launches;
+  int32_t pad2_;
 } info_esrf_stats;
 
 /* One problem of a batched call: inputs and outputs are device pointers.

@@ -63,10 +63,11 @@ class Stats(ctypes.Structure):
     _fields_ = [("status", c_int32), ("device_flags", c_int32), ("iters_max", c_int32),
                 ("n_systems", c_int32), ("iters_mean", c_double), ("n_unconverged", c_int32),
                 ("solver_path", c_int32), ("max_rel_resid", c_double), ("ell_used", c_double),
-                ("gershgorin", c_double), ("learned", c_int32), ("pad_", c_int32)]
+                ("gershgorin", c_double), ("learned", c_int32), ("pad_", c_int32), ("matvec_ms", c_double),
+                ("tile_blocks", c_int64), ("c_nnz", c_double), ("matvec_launches", c_int32), ("pad2_", c_int32)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("pad")}
 
 
 class ProblemC(ctypes.Structure):

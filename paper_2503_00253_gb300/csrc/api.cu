@@ -254,6 +254,7 @@ void carve_problem(Carver& cv, ProblemDev& pr, const info_esrf_options& o) {
     pr.active = cv.take<int32_t>((size_t)J * 4);
     pr.chunk_active = cv.take<int32_t>((size_t)((J + bn - 1) / bn) * 4);
     pr.nactive = cv.take<int32_t>(2 * 4);
+    pr.alist = cv.take<int32_t>((size_t)J * 4);
   }
 }
 
@@ -441,6 +442,12 @@ int run_batch(const info_esrf_problem* probs, int32_t count, const info_esrf_opt
   auto mark = [&](int i) {
     if (o.phase_events && o.phase_events[i]) cudaEventRecord(reinterpret_cast<cudaEvent_t>(o.phase_events[i]), st);
   };
+  static thread_local double tile_mm_ms[kMaxProblems];
+  static thread_local int tile_mm_n[kMaxProblems];
+  for (int i = 0; i < count; ++i) {
+    tile_mm_ms[i] = 0.0;
+    tile_mm_n[i] = 0;
+  }
   mark(0);
   launch_prepare(tab, dtab, st);
   launch_anomalies(tab, dtab, st);
@@ -453,7 +460,8 @@ int run_batch(const info_esrf_problem* probs, int32_t count, const info_esrf_opt
     launch_ritz(tab, dtab, st);
     mark(2);
     for (int i = 0; i < count; ++i) {
-      const int r = run_tile_pcg(tab.p[i], dtab + i, st);
+      const int r = run_tile_pcg(tab.p[i], dtab + i, st, stats ? &tile_mm_ms[i] : nullptr,
+                                 stats ? &tile_mm_n[i] : nullptr);
       if (r != 0) return r;
     }
     mark(3);
@@ -555,6 +563,15 @@ int run_batch(const info_esrf_problem* probs, int32_t count, const info_esrf_opt
     s.ell_used = scal[2];
     s.gershgorin = scal[0];
     s.learned = !pr.learned_model ? 0 : (s.solver_path == 1 ? 1 : -1);
+    if (o.precision == INFO_ESRF_PRECISION_BF16) {
+      int32_t nblocks = 0;
+      if (cudaMemcpy(&nblocks, pr.rowptr + pr.nrt, sizeof(nblocks), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return INFO_ESRF_ERR_CUDA;
+      s.matvec_ms = tile_mm_ms[i];
+      s.matvec_launches = tile_mm_n[i];
+      s.tile_blocks = nblocks;
+      s.c_nnz = scal[3];
+    }
     s.status = status_to_code(status[0]);
     if (s.status < 0 && (worst >= 0 || s.status < worst)) worst = s.status;
     else if (worst == INFO_ESRF_OK && s.status > 0) worst = s.status;

@@ -60,7 +60,9 @@ int64_t tile_max_members();
 // finish (quadrature sum and state update) of the BF16 path.
 void launch_tile_setup(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st);
 void launch_tile_ritz_matvec(const ProblemTable& tab, const ProblemDev* dtab, int src, cudaStream_t st);
-int run_tile_pcg(const ProblemDev& p, const ProblemDev* dp, cudaStream_t st);
+// mm_ms / mm_count (host, may be NULL): summed device time and count of the
+// tensor-core matvec launches, from CUDA events on st around each launch.
+int run_tile_pcg(const ProblemDev& p, const ProblemDev* dp, cudaStream_t st, double* mm_ms, int* mm_count);
 void launch_tile_finish(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st);
 
 struct GridDev {
@@ -102,7 +104,7 @@ struct ProblemDev {
   void* W;              // [d][N] T observed anomalies W = H Z
   double* rinv;         // [d] R^-1/2
   double* bmean;        // [d] R^-1/2 (y - H mu)
-  double* scal;         // [8] 0 gershgorin bound, 1 min diag C, 2 ell, 3 unused, 4 sum of diag C
+  double* scal;         // [8] 0 gershgorin bound, 1 min diag C, 2 ell, 3 nonzeros of C (BF16 path), 4 sum of diag C
   int32_t* status;      // [4]
   double* s;            // [Q] quadrature nodes
   double* p;            // [Q] quadrature weights
@@ -173,7 +175,8 @@ struct ProblemDev {
   float* sigmaf;                // [J] shift per system (FP32)
   int32_t* active;              // [J] 1 while the system runs
   int32_t* chunk_active;        // [nchunks] 1 while a chunk of the tile matvec has a running system
-  int32_t* nactive;             // [2] running systems; iterations done
+  int32_t* nactive;             // [2] running systems; copy of status[0] for the host
+  int32_t* alist;               // [J] the running systems (unordered), rebuilt every iteration
 };
 
 // Launch plan of the multi-shift CG kernel (host side): CTAs per cluster,

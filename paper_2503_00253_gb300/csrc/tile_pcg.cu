@@ -104,16 +104,27 @@ __global__ void k_tpcg_alpha(const ProblemDev* dpr, int it, int nchunks, int res
 // Step 3 (update = 1) or the dot products of r alone (update = 0): CTA =
 // (block of kDotRows rows, group of kSys systems); Phi and C Phi of the rows
 // are staged in shared memory once and reused by every system of the group.
-__global__ void __launch_bounds__(kVecThreads) k_tpcg_update(const ProblemDev* dpr, int update) {
+// Systems: list[blockIdx.y * kSys + s] for positions below count (list = NULL:
+// systems blockIdx.y * kSys + s).
+__device__ __forceinline__ int64_t listed_system(const int32_t* list, int64_t count, int64_t pos, int64_t J) {
+  if (pos >= count) return J;   // past the end: no system
+  return list ? list[pos] : pos;
+}
+
+__global__ void __launch_bounds__(kVecThreads) k_tpcg_update(const ProblemDev* dpr, int update,
+                                                             const int32_t* list, int64_t count) {
   const ProblemDev& pr = *dpr;
   const int64_t sb = blockIdx.x;
-  const int64_t j0 = (int64_t)blockIdx.y * kSys;
+  const int64_t g0 = (int64_t)blockIdx.y * kSys;
   const int k = pr.kR, NV = 2 * k + 1;
   const int64_t J = pr.nsys, dp = pr.d_pad;
   extern __shared__ float phs_dyn[];   // [kDotRows][2 k + 1]
   __shared__ float wred[kVecThreads / 32][2 * kMaxK + 1];
   bool any = false;
-  for (int s = 0; s < kSys; ++s) any |= (j0 + s < J) && pr.active[j0 + s];
+  for (int s = 0; s < kSys; ++s) {
+    const int64_t j = listed_system(list, count, g0 + s, J);
+    any |= j < J && pr.active[j];
+  }
   if (!any) return;
   const float* Phi = reinterpret_cast<const float*>(pr.Phi);
   const float* CPhi = reinterpret_cast<const float*>(pr.CPhi);
@@ -128,7 +139,7 @@ __global__ void __launch_bounds__(kVecThreads) k_tpcg_update(const ProblemDev* d
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int s = 0; s < kSys; ++s) {
-    const int64_t j = j0 + s;
+    const int64_t j = listed_system(list, count, g0 + s, J);
     if (j >= J || !pr.active[j]) continue;   // uniform across the CTA
     const float al = (float)pr.sysd[j * 8 + kAlpha];
     float acc[2 * kMaxK + 1];
@@ -172,6 +183,7 @@ __global__ void __launch_bounds__(kVecThreads) k_tpcg_update(const ProblemDev* d
 __global__ void k_tpcg_scalars(const ProblemDev* dpr, int nsub, int bn, int last) {
   const ProblemDev& pr = *dpr;
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j == 0) pr.nactive[1] = pr.status[0];   // timeouts and overflow are set by earlier kernels
   if (j >= pr.nsys || !pr.active[j]) return;
   const int k = pr.kR, NV = 2 * k + 1;
   double v[2 * kMaxK + 1];
@@ -228,7 +240,7 @@ __global__ void k_tpcg_scalars(const ProblemDev* dpr, int nsub, int bn, int last
   sd[kRho] = rho;
   sd[kFirst] = 0.0;
   pr.chunk_active[j / bn] = 1;
-  atomicAdd(&pr.nactive[0], 1);
+  pr.alist[atomicAdd(&pr.nactive[0], 1)] = (int32_t)j;
 }
 
 // Step 5: p = bf16(r - (C Phi) t + Phi c + beta p) for the running systems;
@@ -236,13 +248,17 @@ __global__ void k_tpcg_scalars(const ProblemDev* dpr, int nsub, int bn, int last
 __global__ void __launch_bounds__(kVecThreads) k_tpcg_direction(const ProblemDev* dpr) {
   const ProblemDev& pr = *dpr;
   const int64_t sb = blockIdx.x;
-  const int64_t j0 = (int64_t)blockIdx.y * kSys;
+  const int64_t g0 = (int64_t)blockIdx.y * kSys;
   const int k = pr.kR;
   const int64_t J = pr.nsys, dp = pr.d_pad;
+  const int64_t count = pr.nactive[0];   // the list the scalars kernel just built
   extern __shared__ float phs_dyn[];   // [kDotRows][2 k + 1]
   __shared__ float tc[2 * kMaxK];
   bool any = false;
-  for (int s = 0; s < kSys; ++s) any |= (j0 + s < J) && pr.active[j0 + s];
+  for (int s = 0; s < kSys; ++s) {
+    const int64_t j = listed_system(pr.alist, count, g0 + s, J);
+    any |= j < J && pr.active[j];
+  }
   if (!any) return;
   const float* Phi = reinterpret_cast<const float*>(pr.Phi);
   const float* CPhi = reinterpret_cast<const float*>(pr.CPhi);
@@ -255,7 +271,7 @@ __global__ void __launch_bounds__(kVecThreads) k_tpcg_direction(const ProblemDev
     phs_dyn[row * (2 * k + 1) + m] = v;
   }
   for (int s = 0; s < kSys; ++s) {
-    const int64_t j = j0 + s;
+    const int64_t j = listed_system(pr.alist, count, g0 + s, J);
     if (j >= J || !pr.active[j]) continue;   // uniform across the CTA
     __syncthreads();
     for (int m = threadIdx.x; m < 2 * k; m += blockDim.x)
@@ -281,9 +297,32 @@ __global__ void __launch_bounds__(kVecThreads) k_tpcg_direction(const ProblemDev
 // Runs the PCG of one BF16 problem (host copy p, device copy dp) to
 // convergence or the iteration cap.  Synchronizes the stream once per
 // iteration to read the number of running systems.
-int run_tile_pcg(const ProblemDev& p, const ProblemDev* dp, cudaStream_t st) {
+int run_tile_pcg(const ProblemDev& p, const ProblemDev* dp, cudaStream_t st, double* mm_ms, int* mm_count) {
   const int64_t J = p.nsys;
   if (J < 1) return 0;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  if (mm_ms && (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess)) {
+    cudaGetLastError();
+    if (ev[0]) cudaEventDestroy(ev[0]);
+    return INFO_ESRF_ERR_CUDA;
+  }
+  bool timed = false;   // an event pair of the previous iteration awaits reading
+  auto read_time = [&]() {
+    if (!timed) return;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess) {
+      *mm_ms += ms;
+      ++*mm_count;
+    }
+    timed = false;
+  };
+  struct Destroy {
+    cudaEvent_t* e;
+    ~Destroy() {
+      if (e[0]) cudaEventDestroy(e[0]);
+      if (e[1]) cudaEventDestroy(e[1]);
+    }
+  } destroy{ev};
   const int bn = tile_chunk_width((int32_t)J);
   const int nchunks = (int)((J + bn - 1) / bn);
   const int nsub = (int)((p.d_pad + kDotRows - 1) / kDotRows);
@@ -316,26 +355,37 @@ int run_tile_pcg(const ProblemDev& p, const ProblemDev* dp, cudaStream_t st) {
   }
   int32_t host[2] = {0, 0};
   k_tpcg_init<<<gall, 256, 0, st>>>(dp);
-  k_tpcg_update<<<gvec, kVecThreads, vsm, st>>>(dp, 0);
+  k_tpcg_update<<<gvec, kVecThreads, vsm, st>>>(dp, 0, nullptr, J);
   const dim3 galpha((unsigned)(((J > nchunks ? J : nchunks) + 127) / 128));
   k_tpcg_alpha<<<galpha, 128, 0, st>>>(dp, 0, nchunks, 1);   // resets the chunk flags and the count
   k_tpcg_scalars<<<gsys, 128, 0, st>>>(dp, nsub, bn, maxit <= 0 ? 1 : 0);
   k_tpcg_direction<<<gvec, kVecThreads, vsm, st>>>(dp);
   note_launches(5);
   for (int it = 1; it <= maxit; ++it) {
+    // running systems (and the status word) after the previous iteration
     if (cudaMemcpyAsync(host, p.nactive, sizeof(host), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
       return INFO_ESRF_ERR_CUDA;
+    read_time();   // the previous launch has completed (stream synchronized)
     if (host[0] == 0) break;
-    int32_t stat = 0;
-    if (cudaMemcpy(&stat, p.status, sizeof(stat), cudaMemcpyDeviceToHost) != cudaSuccess) return INFO_ESRF_ERR_CUDA;
-    if (stat & (kStatTimeout | kStatTileOverflow)) break;
-    if (launch_tile_mm(ta, p.Chi, p.Clo, p.rowptr ? p.tile_cap : 0, st) != 0) return INFO_ESRF_ERR_CUDA;
+    if (host[1] & (kStatTimeout | kStatTileOverflow)) break;
+    const int64_t nrun = host[0];
+    const dim3 glist((unsigned)nsub, (unsigned)((nrun + kSys - 1) / kSys));
+    if (mm_ms) cudaEventRecord(ev[0], st);
+    if (launch_tile_mm(ta, p.Chi, p.Clo, p.tile_cap, st) != 0) return INFO_ESRF_ERR_CUDA;
+    if (mm_ms) {
+      cudaEventRecord(ev[1], st);
+      timed = true;
+    }
     k_tpcg_alpha<<<galpha, 128, 0, st>>>(dp, it, nchunks, 0);
-    k_tpcg_update<<<gvec, kVecThreads, vsm, st>>>(dp, 1);
+    k_tpcg_update<<<glist, kVecThreads, vsm, st>>>(dp, 1, p.alist, nrun);
     k_tpcg_scalars<<<gsys, 128, 0, st>>>(dp, nsub, bn, it == maxit ? 1 : 0);
-    k_tpcg_direction<<<gvec, kVecThreads, vsm, st>>>(dp);
+    k_tpcg_direction<<<glist, kVecThreads, vsm, st>>>(dp);
     note_launches(4);
+  }
+  if (timed) {
+    if (cudaEventSynchronize(ev[1]) != cudaSuccess) return INFO_ESRF_ERR_CUDA;
+    read_time();
   }
   return cudaGetLastError() == cudaSuccess ? 0 : INFO_ESRF_ERR_CUDA;
 }

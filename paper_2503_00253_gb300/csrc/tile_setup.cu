@@ -368,6 +368,7 @@ __global__ void __launch_bounds__(kTileM) k_tile_form(const ProblemDev* tab) {
   const Coord3 ca = flat_to_coord(pr.grid, srca >= 0 ? pr.obs[srca] : 0);
   const float ra = pr.rinvp[a];
   double rowsum = 0.0;
+  int64_t nnz = 0;
   const int t0 = pr.rowptr[row], t1 = pr.rowptr[row + 1];
   for (int t = t0; t < t1; ++t) {
     const int64_t blk = pr.colblk[t];
@@ -405,6 +406,7 @@ __global__ void __launch_bounds__(kTileM) k_tile_form(const ProblemDev* tab) {
         const double r2 = scaled_r2_tab(pr.grid, pr.d2tab, ca, cbc);
         float v = 0.f;
         if (r2 < 4.0) v = gaspari_cohn_f(sqrtf((float)r2)) * acc[cc] * ra * rb[c];
+        nnz += (r2 < 4.0 && srca >= 0 && pr.tpos_src[blk * kTileK + c] >= 0) ? 1 : 0;
         const __nv_bfloat16 h = __float2bfloat16_rn(v);
         h16[cc] = h;
         l16[cc] = __float2bfloat16_rn(v - __bfloat162float(h));
@@ -425,6 +427,7 @@ __global__ void __launch_bounds__(kTileM) k_tile_form(const ProblemDev* tab) {
     }
   }
   if (srca >= 0) atomic_max_nonneg(&pr.scal[0], rowsum);
+  if (nnz) atomicAdd(&pr.scal[3], (double)nnz);   // nonzeros of C (an exact integer count in FP64)
 }
 
 // Y = C X for the Ritz basis: X, Y [d][l] FP32 in tile order (Om / Yb), one
@@ -466,8 +469,11 @@ __global__ void __launch_bounds__(kTileM) k_tile_ritz_matvec(const ProblemDev* t
       }
     }
   }
-  if (a < pr.d)
-    for (int m = 0; m < l; ++m) Y[a * l + m] = acc[m];
+  if (a < pr.d) {
+#pragma unroll
+    for (int m = 0; m < kMaxRitz; ++m)   // unrolled: acc stays in registers
+      if (m < l) Y[a * l + m] = acc[m];
+  }
 }
 
 // vbar (natural order, FP64 and the FP32 copy) from the tile-ordered iterates.
@@ -494,94 +500,150 @@ __global__ void k_tile_accumulate(const ProblemDev* tab) {
   reinterpret_cast<float*>(pr.VbarT)[a * N1 + m] = (float)v;
 }
 
-// State update over state tiles: 256 threads, S(x, c) = GC (z_x . w_c) for the
-// tile's 128 points and a block's 64 observations, then acc(x, m) += S(x, :) vbar(:, m),
-// threads 0-127 taking columns m < M0 and 128-255 the rest.
-__global__ void __launch_bounds__(256) k_tile_state_apply(const ProblemDev* tab) {
+// State update over state tiles (256 threads).  For each stored column block:
+//   S = GC o (Z_tile W_blk^T)   (128 x 64; thread: 4 points x 8 observations)
+//   acc += S Vbar_blk           (128 x (N + 1); thread: 4 points x up to 17 columns)
+// Operands sit k-major in shared memory so a thread's 4 points or 8
+// observations are one or two 16-byte loads; the per-axis distance table is
+// staged in FP32.  Register-blocked so each shared-memory load feeds 3-4 FMAs.
+constexpr int kStCols = 17;     // columns per thread in the S Vbar product: 8 groups cover N + 1 <= 136
+constexpr int kD2Max = 4096;    // distance-table entries staged in shared memory (sum of the extents)
+__global__ void __launch_bounds__(256, 1) k_tile_state_apply(const ProblemDev* tab) {
   const ProblemDev& pr = tab[blockIdx.y];
   if (pr.precision != 2 || blockIdx.x >= pr.nst) return;
   if (pr.status[0] & kStatTileOverflow) return;
   extern __shared__ __align__(16) float fsm[];
-  const int N = (int)pr.N, NS = N + 1, N1 = N + 1, VS = N1 + 1;
-  float* Zs = fsm;                         // [128][N + 1]
-  float* Wb = Zs + kTileM * NS;            // [64][N + 1]
-  float* Vb = Wb + kTileK * NS;            // [64][N + 2]
-  float* S = Vb + kTileK * VS;             // [128][65]
-  int32_t* cb = reinterpret_cast<int32_t*>(S + kTileM * (kTileK + 1));   // [64][3]
+  const int N = (int)pr.N, N1 = N + 1;
+  const int cpg = (N1 + 7) / 8;           // columns per column group (<= kStCols)
+  const int N1p = 8 * cpg;
+  float* Zs = fsm;                        // [N][128]
+  float* Wb = Zs + N * kTileM;            // [N][64]
+  float* S = Wb + N * kTileK;             // [64][128]
+  float* Vb = S + kTileK * kTileM;        // [64][N1p]
+  float* d2 = Vb + kTileK * N1p;          // [ext0 + ext1 + ext2] (when <= kD2Max)
+  int32_t* cb = reinterpret_cast<int32_t*>(d2 + kD2Max);   // [64][3]
+  const GridDev& g = pr.grid;
+  const int64_t next = g.ext[0] + g.ext[1] + g.ext[2];
+  const bool d2s = next <= kD2Max;
   const int64_t st = blockIdx.x, x0 = st * kTileM;
   const float* Zt = reinterpret_cast<const float*>(pr.Zt);
   const float* VbT = reinterpret_cast<const float*>(pr.VbarT);
   for (int e = threadIdx.x; e < kTileM * N; e += blockDim.x) {
     const int i = e / N, k = e % N;
     const int64_t x = x0 + i;
-    Zs[i * NS + k] = x < pr.n ? Zt[x * N + k] : 0.f;
+    Zs[k * kTileM + i] = x < pr.n ? Zt[x * N + k] : 0.f;
   }
-  const int xi = threadIdx.x & (kTileM - 1), half = threadIdx.x >> 7;
-  const int M0 = (N1 + 1) / 2;
-  const int mlo = half ? M0 : 0, mhi = half ? N1 : M0;
-  constexpr int kAcc = 65;   // columns per thread: N + 1 <= 129
-  float acc[kAcc];
+  if (d2s)
+    for (int e = threadIdx.x; e < next; e += blockDim.x) d2[e] = (float)pr.d2tab[e];
+  const int tid = threadIdx.x;
+  const int rg = tid >> 3, cg = tid & 7;  // 32 row groups of 4 points x 8 column groups
+  Coord3 cx[4];
 #pragma unroll
-  for (int m = 0; m < kAcc; ++m) acc[m] = 0.f;
+  for (int i = 0; i < 4; ++i) {
+    const int64_t x = x0 + 4 * rg + i;
+    cx[i] = flat_to_coord(g, x < pr.n ? x : 0);
+  }
+  float acc[4][kStCols];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < kStCols; ++j) acc[i][j] = 0.f;
   for (int t = pr.st_rowptr[st]; t < pr.st_rowptr[st + 1]; ++t) {
     const int64_t blk = pr.st_colblk[t];
     __syncthreads();
-    for (int e = threadIdx.x; e < kTileK * N; e += blockDim.x) {
+    for (int e = tid; e < kTileK * N; e += blockDim.x) {
       const int c = e / N, k = e % N;
-      Wb[c * NS + k] = pr.Wp[(blk * kTileK + c) * N + k];
+      Wb[k * kTileK + c] = pr.Wp[(blk * kTileK + c) * N + k];
     }
-    for (int e = threadIdx.x; e < kTileK * N1; e += blockDim.x) {
-      const int c = e / N1, m = e % N1;
+    for (int e = tid; e < kTileK * N1p; e += blockDim.x) {
+      const int c = e / N1p, m = e % N1p;
       const int32_t src = pr.tpos_src[blk * kTileK + c];
-      Vb[c * VS + m] = src >= 0 ? VbT[(int64_t)src * N1 + m] : 0.f;
+      Vb[c * N1p + m] = (src >= 0 && m < N1) ? VbT[(int64_t)src * N1 + m] : 0.f;
     }
-    if (threadIdx.x < kTileK) {
-      const int32_t src = pr.tpos_src[blk * kTileK + threadIdx.x];
-      const Coord3 c = flat_to_coord(pr.grid, src >= 0 ? pr.obs[src] : 0);
-      cb[3 * threadIdx.x] = (int32_t)c.x;
-      cb[3 * threadIdx.x + 1] = (int32_t)c.y;
-      cb[3 * threadIdx.x + 2] = (int32_t)c.z;
+    if (tid < kTileK) {
+      const int32_t src = pr.tpos_src[blk * kTileK + tid];
+      const Coord3 c = flat_to_coord(g, src >= 0 ? pr.obs[src] : 0);
+      cb[3 * tid] = src >= 0 ? (int32_t)c.x : -1;   // -1: padding column
+      cb[3 * tid + 1] = (int32_t)c.y;
+      cb[3 * tid + 2] = (int32_t)c.z;
     }
     __syncthreads();
-    // S: 128 x 64 entries, 32 per thread (point xi, columns half*32 .. half*32 + 31)
+    // S for points 4 rg .. 4 rg + 3 and observations 8 cg .. 8 cg + 7
     {
-      const Coord3 cx = flat_to_coord(pr.grid, x0 + xi < pr.n ? x0 + xi : 0);
-      float sacc[32];
+      float sa[4][8];
 #pragma unroll
-      for (int cc = 0; cc < 32; ++cc) sacc[cc] = 0.f;
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) sa[i][j] = 0.f;
       for (int k = 0; k < N; ++k) {
-        const float z = Zs[xi * NS + k];
+        const float4 z = *reinterpret_cast<const float4*>(Zs + k * kTileM + 4 * rg);
+        const float4 w0 = *reinterpret_cast<const float4*>(Wb + k * kTileK + 8 * cg);
+        const float4 w1 = *reinterpret_cast<const float4*>(Wb + k * kTileK + 8 * cg + 4);
+        const float zz[4] = {z.x, z.y, z.z, z.w};
+        const float ww[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
-        for (int cc = 0; cc < 32; ++cc) sacc[cc] = fmaf(z, Wb[(half * 32 + cc) * NS + k], sacc[cc]);
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) sa[i][j] = fmaf(zz[i], ww[j], sa[i][j]);
       }
 #pragma unroll
-      for (int cc = 0; cc < 32; ++cc) {
-        const int c = half * 32 + cc;
-        const Coord3 cbc{cb[3 * c], cb[3 * c + 1], cb[3 * c + 2]};
-        const double r2 = scaled_r2_tab(pr.grid, pr.d2tab, cx, cbc);
-        const bool real = pr.tpos_src[blk * kTileK + c] >= 0;
-        S[xi * (kTileK + 1) + c] = (real && r2 < 4.0) ? gaspari_cohn_f(sqrtf((float)r2)) * sacc[cc] : 0.f;
+      for (int j = 0; j < 8; ++j) {
+        const int c = 8 * cg + j;
+        const int32_t bc[3] = {cb[3 * c], cb[3 * c + 1], cb[3 * c + 2]};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          float v = 0.f;
+          if (bc[0] >= 0) {
+            const int64_t ca[3] = {cx[i].x, cx[i].y, cx[i].z};
+            float r2 = 0.f;
+            int64_t off = 0;
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) {
+              if (g.ext[ax] > 1) {
+                const int64_t dl = ca[ax] > bc[ax] ? ca[ax] - bc[ax] : bc[ax] - ca[ax];
+                r2 += d2s ? d2[off + dl] : (float)pr.d2tab[off + dl];
+              }
+              off += g.ext[ax];
+            }
+            if (r2 < 4.f) v = gaspari_cohn_f(sqrtf(r2)) * sa[i][j];
+          }
+          S[c * kTileM + 4 * rg + i] = v;
+        }
       }
     }
     __syncthreads();
+    // acc += S Vbar for columns cg * cpg .. cg * cpg + cpg - 1
     for (int c = 0; c < kTileK; ++c) {
-      const float sv = S[xi * (kTileK + 1) + c];
+      const float4 sv = *reinterpret_cast<const float4*>(S + c * kTileM + 4 * rg);
+      const float ss[4] = {sv.x, sv.y, sv.z, sv.w};
+      const float* vr = Vb + c * N1p + cg * cpg;
 #pragma unroll
-      for (int m = 0; m < kAcc; ++m)
-        if (mlo + m < mhi) acc[m] = fmaf(sv, Vb[c * VS + mlo + m], acc[m]);
+      for (int j = 0; j < kStCols; ++j) {
+        if (j < cpg) {
+          const float v = vr[j];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) acc[i][j] = fmaf(ss[i], v, acc[i][j]);
+        }
+      }
     }
   }
-  const int64_t x = x0 + xi;
-  if (x >= pr.n) return;
-  const double mu = pr.mu[x];
-  for (int m = 0; m < kAcc; ++m) {
-    const int col = mlo + m;
-    if (col >= mhi) break;
-    const double inc = (double)acc[m];
-    if (col < N) {
-      if (pr.do_pert) pr.A_a[(int64_t)col * pr.n + x] = (pr.X[(int64_t)col * pr.n + x] - mu) - pr.sqrt_nm1 * inc;
-    } else if (pr.do_mean) {
-      pr.mu_a[x] = mu + inc;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t x = x0 + 4 * rg + i;
+    if (x >= pr.n) continue;
+    const double mu = pr.mu[x];
+#pragma unroll
+    for (int j = 0; j < kStCols; ++j) {   // unrolled: acc stays in registers
+      const int col = cg * cpg + j;
+      if (j < cpg && col < N1) {
+        const double inc = (double)acc[i][j];
+        if (col < N) {
+          if (pr.do_pert)
+            pr.A_a[(int64_t)col * pr.n + x] = (pr.X[(int64_t)col * pr.n + x] - mu) - pr.sqrt_nm1 * inc;
+        } else if (pr.do_mean) {
+          pr.mu_a[x] = mu + inc;
+        }
+      }
     }
   }
 }
@@ -590,7 +652,8 @@ size_t form_smem(int64_t N) {
   return (size_t)(kTileM + kTileK) * (N + 1) * 4 + 3 * kTileK * 4 + kTileK * 4;
 }
 size_t state_smem(int64_t N) {
-  return (size_t)(kTileM + kTileK) * (N + 1) * 4 + (size_t)kTileK * (N + 2) * 4 + kTileM * (kTileK + 1) * 4 +
+  const int64_t n1p = 8 * ((N + 1 + 7) / 8);
+  return (size_t)(kTileM + kTileK) * N * 4 + (size_t)kTileK * kTileM * 4 + (size_t)kTileK * n1p * 4 + kD2Max * 4 +
          3 * kTileK * 4;
 }
 

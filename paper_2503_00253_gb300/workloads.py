@@ -225,6 +225,13 @@ def gaussian_problem_2d(nx: int = 1024, ny: int = 1024, N: int = 80, length_scal
     return Problem(f"gauss2d_{nx}x{ny}_N{N}_Q{Q}", grid, X, truth, obs_idx, y, R, Q, tol)
 
 
+def config5(tol: float = 1e-6, seed: int = 5) -> Problem:
+    """2-D periodic 1024 x 1024 (n = 1,048,576), N = 80, length scale 32 cells, observations every
+    2nd cell per axis (d = 262,144), R = 0.5, GC half-width 96 cells, Q = 32 (2560 shifted systems)."""
+    return gaussian_problem_2d(nx=1024, ny=1024, N=80, length_scale=32.0, obs_stride=2, r2=0.5,
+                               half_width=96.0, Q=32, tol=tol, seed=seed)
+
+
 def random_obs_problem(grid: Grid, N: int, d: int, r2: float, Q: int, tol: float,
                        seed: int, length_scale: float = 4.0) -> Problem:
     """Small problem with random observation positions and random R (for edge cases)."""

@@ -496,13 +496,14 @@ def _l96(nx, nz, N, spinup, seed, c_x, c_z):
 
 def test_layered_l96_full_size_parity(B):
     """Layered Lorenz-96 analysis at full size: 8 layers x 960 longitudes, N=40, 25% random
-    observations (d=1920), anisotropic Gaspari-Cohn (60 horizontally, 2 layers vertically), Q=24."""
+    observations (d=1920), anisotropic Gaspari-Cohn (60 horizontally, 2 layers vertically), Q=24,
+    in FP32, in BF16 (tensor-core block-tile path: BF16 matvec with FP32 accumulation) and in FP64."""
     pr = workloads.layered_l96_problem()
     A_ref = F.perturbation_update(pr.X, pr.obs_idx, pr.R, pr.grid, pr.Q)
     mu_ref = F.mean_update(pr.X, pr.obs_idx, pr.y, pr.R, pr.grid)
     Af = pr.X - pr.X.mean(0)
     mu0 = pr.X.mean(0)
-    for prec, tol, bound in ((1, 1e-6, 1e-4), (0, 1e-12, 1e-10)):
+    for prec, tol, bound in ((1, 1e-6, 1e-4), (2, 1e-6, 1e-4), (0, 1e-12, 1e-10)):
         mu_a, A_a, st = B.info_esrf_analysis(pr.grid, dev(pr.X), dev(pr.obs_idx), dev(pr.y), dev(pr.R), pr.Q, tol,
                                              B.make_options(precision=prec))
         torch.cuda.synchronize()
@@ -512,7 +513,8 @@ def test_layered_l96_full_size_parity(B):
         assert ea <= bound and em <= bound, (prec, ea, em)
 
 
-def test_layered_l96_cycling_tracks_truth(B):
+@pytest.mark.parametrize("precision", [1, 2])
+def test_layered_l96_cycling_tracks_truth(B, precision):
     """Cycled assimilation on a reduced layered Lorenz-96 (4 layers x 240, N=20, 25% observed,
     localization 12 horizontally and 1 layer vertically, relaxation to prior spread 0.5), starting
     from a climatological ensemble: every cycle converges, the first matches the oracle, and the
@@ -525,7 +527,7 @@ def test_layered_l96_cycling_tracks_truth(B):
     truth = pr.truth.reshape(nz, nx).copy()
     obs = pr.obs_idx
     rmse_f, rmse_a = [], []
-    opts = B.make_options(precision=1)
+    opts = B.make_options(precision=precision)
     for c in range(cycles):
         if c > 0:
             X = workloads.ll96_rk4(X, dt, steps)
