@@ -76,6 +76,15 @@ extern "C" {
 
 #define INFO_ESRF_SOLVER_PCG 0             /* one PCG run per (node, member) system (Sec. 3.3, App. E) */
 #define INFO_ESRF_SOLVER_MULTISHIFT 1      /* one CG run per member for all Q shifts (Sec. 3.3, item 1) */
+/* Block CG across members (Sec. 3.3, second alternative; O'Leary's block CG):
+ * for every node the N members' systems share one block Krylov space and are
+ * solved together, X_0 = 0, R_0 = P_0 = B, alpha = (P^T C_q P)^-1 (R^T R),
+ * beta = (R^T R)^-1 (R'^T R'), without deflation and without a preconditioner
+ * (the mean system is a block of one column); a block stops when every
+ * column meets tol (or after fixed_iters).  FP64 or FP32 bulk (s x s algebra
+ * and Gram sums in FP64), N <= 64.  The call synchronizes its stream once per
+ * iteration (convergence is tested on the host). */
+#define INFO_ESRF_SOLVER_BLOCK 2
 
 /* Regular grid.  Flat index = (z * shape[1] + y) * shape[0] + x.  Axes of
  * extent 1 are ignored.  The Gaspari-Cohn argument is
@@ -158,7 +167,7 @@ typedef struct {
   double iters_mean;
   int32_t n_unconverged;
   int32_t solver_path;    /* 1: cluster-resident band kernel (1-D networks), 0: general kernel,
-                             2: multi-shift CG, 3: BF16 block-tile path (tensor cores) */
+                             2: multi-shift CG, 3: BF16 block-tile path (tensor cores), 4: block CG */
   double max_rel_resid;   /* max recurrence ||r|| / ||b|| at exit */
   double ell_used;
   double gershgorin;      /* max_a sum_b |C(a, b)| */

@@ -39,6 +39,7 @@ RULE_ELLIPTIC = 0
 RULE_GAUSS_LEGENDRE = 1
 SOLVER_PCG = 0
 SOLVER_MULTISHIFT = 1
+SOLVER_BLOCK = 2
 
 ITEM = dict(scalars=0, status=1, quad_s=2, quad_p=3, theta=4, phi=5, cphi=6, oo_val=7, oo_col=8,
             oo_nnz=9, xo_val=10, xo_col=11, xo_nnz=12, W=13, mu=14)

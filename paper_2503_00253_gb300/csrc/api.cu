@@ -107,7 +107,8 @@ int check_options(const info_esrf_options* in, info_esrf_options* out) {
   if (out->cluster_size != 0 && out->cluster_size != -1 && out->cluster_size != 2 && out->cluster_size != 4 &&
       out->cluster_size != 8)
     return INFO_ESRF_ERR_INVALID_ARG;
-  if (out->solver != INFO_ESRF_SOLVER_PCG && out->solver != INFO_ESRF_SOLVER_MULTISHIFT)
+  if (out->solver != INFO_ESRF_SOLVER_PCG && out->solver != INFO_ESRF_SOLVER_MULTISHIFT &&
+      out->solver != INFO_ESRF_SOLVER_BLOCK)
     return INFO_ESRF_ERR_INVALID_ARG;
   return 0;
 }
@@ -224,6 +225,21 @@ void carve_problem(Carver& cv, ProblemDev& pr, const info_esrf_options& o) {
   pr.VbarT = cv.take<void>((size_t)d * (N + 1) * esz);
   pr.learn_coef = cv.take<float>((size_t)(pr.Q + 1) * kLearnOut * 4);
   pr.learn_T = cv.take<float>((size_t)(pr.Q + 1) * kLearnT * 4);
+  if (o.solver == INFO_ESRF_SOLVER_BLOCK) {
+    pr.bcg_nblocks = pr.mean_sys + (pr.do_pert ? pr.Q : 0);
+    const size_t vec = (size_t)pr.nsys * d * esz, mat = (size_t)pr.bcg_nblocks * kBcgMaxS * kBcgMaxS * 8;
+    pr.bcg_R = cv.take<void>(vec);
+    pr.bcg_P = cv.take<void>(vec);
+    pr.bcg_Q = cv.take<void>(vec);
+    pr.bcg_G1 = cv.take<double>(mat);
+    pr.bcg_G2 = cv.take<double>(mat);
+    pr.bcg_RR = cv.take<double>(mat);
+    pr.bcg_alpha = cv.take<double>(mat);
+    pr.bcg_beta = cv.take<double>(mat);
+    pr.bcg_bn2 = cv.take<double>((size_t)pr.nsys * 8);
+    pr.bcg_state = cv.take<int32_t>((size_t)pr.bcg_nblocks * 4);
+    pr.bcg_running = cv.take<int32_t>(4);
+  }
   if (o.precision == 2) {
     const int64_t J = pr.nsys, dp = pr.d_pad, kk = pr.kR;
     const int bn = tile_chunk_width((int32_t)std::max<int64_t>(J, 1));
@@ -248,6 +264,7 @@ void carve_problem(Carver& cv, ProblemDev& pr, const info_esrf_options& o) {
     pr.Rv = cv.take<float>((size_t)J * dp * 4);
     pr.pty = cv.take<float>((size_t)pr.nrt * J * 4);
     pr.dots = cv.take<double>((size_t)nsub * J * (2 * kk + 1) * 8);
+    pr.dsum = cv.take<double>((size_t)J * (2 * kk + 1) * 8);
     pr.sysd = cv.take<double>((size_t)J * 8 * 8);
     pr.lcoef = cv.take<float>((size_t)J * 2 * kMaxK * 4);
     pr.sigmaf = cv.take<float>((size_t)J * 4);
@@ -304,6 +321,7 @@ int build_table(const info_esrf_problem* probs, int32_t count, const info_esrf_o
     pr.ell_fixed = o.ell;
     pr.seed = o.seed;
     pr.sqrt_nm1 = sqrt((double)(pr.N - 1));
+    if (o.solver == INFO_ESRF_SOLVER_BLOCK && pr.do_pert && pr.N > kBcgMaxS) return INFO_ESRF_ERR_UNSUPPORTED;
     if (o.precision == 2) {
       // BF16 block-tile path: no bands; tile counts and capacities
       if (general_h || pr.N > tile_max_members()) return INFO_ESRF_ERR_UNSUPPORTED;
@@ -466,6 +484,20 @@ int run_batch(const info_esrf_problem* probs, int32_t count, const info_esrf_opt
     }
     mark(3);
     launch_tile_finish(tab, dtab, st);
+  } else if (o.solver == INFO_ESRF_SOLVER_BLOCK) {
+    // block CG: bands and quadrature, no Ritz stage, then each problem's
+    // host-driven block iteration, then the usual finish from U
+    launch_band_obs(tab, dtab, st);
+    launch_band_state(tab, dtab, st);
+    launch_quadrature(tab, dtab, st);
+    mark(1);
+    mark(2);
+    for (int i = 0; i < count; ++i) {
+      const int r = run_bcg(tab.p[i], dtab + i, st);
+      if (r != 0) return r;
+    }
+    mark(3);
+    launch_finish(tab, dtab, st);
   } else if (o.solver == INFO_ESRF_SOLVER_MULTISHIFT) {
     launch_band_obs(tab, dtab, st);
     // no Ritz stage and no learned coefficients: the quadrature and the
@@ -554,7 +586,9 @@ int run_batch(const info_esrf_problem* probs, int32_t count, const info_esrf_opt
       if (o.fixed_iters <= 0 && !(rr[sidx] <= pr.tol)) ++unconv;
     }
     s.device_flags = status[0];
-    s.solver_path = o.precision == INFO_ESRF_PRECISION_BF16 ? 3 : (status[1] & 2) ? 2 : (status[1] & 1);
+    s.solver_path = o.precision == INFO_ESRF_PRECISION_BF16 ? 3
+                    : o.solver == INFO_ESRF_SOLVER_BLOCK ? 4
+                    : (status[1] & 2) ? 2 : (status[1] & 1);
     s.iters_max = it_max;
     s.n_systems = (int32_t)live;
     s.iters_mean = live ? (double)sum_it / (double)live : 0.0;

@@ -43,15 +43,18 @@ struct TileMmArgs {
   const float* sigma;           // [J] shifts
   const int32_t* active;        // [nchunks] nonzero: chunk has an unconverged system (or NULL: all)
   float* Y;                     // [J][d_pad] sigma p + C p
-  float* pty;                   // [nrt][J] partial p^T y per row tile (or NULL)
+  float* pty;                   // partial p^T y per row tile (or NULL): [nrt][J], or [J][nrt] if pty_by_system
   int32_t* status;              // status bits (kStatTimeout), or NULL
   int64_t d_pad;
-  int32_t J, nrt, nchunks;
+  int32_t J, nrt, nchunks, pty_by_system;
 };
 // Systems per CTA of the tile matvec for J systems (128 or 256).
 int tile_chunk_width(int32_t J);
 int launch_tile_mm(TileMmArgs a, const void* chi, const void* clo, int64_t ntiles, cudaStream_t st);
 constexpr int kTileDotRows = 512;   // rows per partial dot product of the BF16 PCG
+constexpr int kBcgMaxS = 64;        // block CG: largest block (members per node)
+struct ProblemDev;
+int run_bcg(const ProblemDev& p, const ProblemDev* dp, cudaStream_t st);
 struct ProblemDev;
 struct ProblemTable;
 int64_t tile_max_members();
@@ -168,8 +171,9 @@ struct ProblemDev {
   float* Yv;                    // [J][d_pad] sigma p + C p
   float* Xv;                    // [J][d_pad] iterates
   float* Rv;                    // [J][d_pad] residuals
-  float* pty;                   // [nrt][J] p^T y per row tile
-  double* dots;                 // [nsub][J][2 kR + 1] partial r^T r, Phi^T r, (C Phi)^T r
+  float* pty;                   // [J][nrt] p^T y per row tile
+  double* dots;                 // [J][2 kR + 1][nsub] partial r^T r, Phi^T r, (C Phi)^T r per row block
+  double* dsum;                 // [J][2 kR + 1] their sums
   double* sysd;                 // [J][8] per-system scalars (see tile_pcg.cu)
   float* lcoef;                 // [J][2 kR] LMP coefficients of the current direction update
   float* sigmaf;                // [J] shift per system (FP32)
@@ -177,6 +181,20 @@ struct ProblemDev {
   int32_t* chunk_active;        // [nchunks] 1 while a chunk of the tile matvec has a running system
   int32_t* nactive;             // [2] running systems; copy of status[0] for the host
   int32_t* alist;               // [J] the running systems (unordered), rebuilt every iteration
+  // block CG (solver 2): blocks = the mean system (one column) and one block of
+  // N columns per node; vectors [nsys][d] of the bulk type, X is U
+  int32_t bcg_nblocks, pad3_;
+  void* bcg_R;                  // residuals
+  void* bcg_P;                  // directions
+  void* bcg_Q;                  // C_q P
+  double* bcg_G1;               // [nblocks][kBcgMaxS][kBcgMaxS] P^T Q
+  double* bcg_G2;               // R^T R of the new residual
+  double* bcg_RR;               // R^T R of the current residual
+  double* bcg_alpha;            // block step
+  double* bcg_beta;             // block direction update
+  double* bcg_bn2;              // [nsys] ||b_i||^2
+  int32_t* bcg_state;           // [nblocks] 0 running, 1 stopped, 2 breakdown
+  int32_t* bcg_running;         // [1] running blocks after the last iteration
 };
 
 // Launch plan of the multi-shift CG kernel (host side): CTAs per cluster,

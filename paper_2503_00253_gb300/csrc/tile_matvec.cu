@@ -11,14 +11,15 @@
 // stored as two BF16 planes hi = bf16(C), lo = bf16(C - hi), row-major
 // [tile][128][64].  The directions are BF16, system-major [J][d_pad].
 //
-// Kernel.  One CTA of 4 warps per (row tile, chunk of BN systems).  Warp 0
+// Kernel.  One CTA of 4 warps per (row tile, chunk of H x BN systems).  Warp 0
 // lane 0 streams the blocks of the row tile through an S-stage ring of shared
 // memory with 2-D TMA loads (128-byte swizzle): the hi and lo planes of the C
 // block (the A operand, 128 x 64, K-major) and the 64-row slab of the chunk's
 // directions (the B operand, BN x 64, K-major).  Warp 1 lane 0 issues
-// tcgen05.mma kind::f16 (BF16 x BF16, FP32 accumulate) into a 128 x BN FP32
-// accumulator in tensor memory: four K = 16 steps for hi, four for lo, then a
-// commit that frees the stage.  After the last block all four warps read the
+// tcgen05.mma kind::f16 (BF16 x BF16, FP32 accumulate) into H 128 x BN FP32
+// accumulators in tensor memory (H = 2 when more than 256 systems: each C
+// block load then serves 512 systems): four K = 16 steps for hi, four for lo,
+// per accumulator, then a commit that frees the stage.  After the last block all four warps read the
 // accumulator (tcgen05.ld, one TMEM lane = one row per thread), add sigma_j p_j,
 // store y and reduce the partial dot products p_j^T y_j of the row tile.
 #include <cuda_bf16.h>
@@ -41,19 +42,22 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   return v;
 }
 
-template <int BN, int S>
+// BN systems per accumulator, S pipeline stages, H accumulators (TMEM halves)
+// per CTA sharing each C block load.
+template <int BN, int S, int H>
 struct TileMmShape {
-  static constexpr int kStage = 2 * kABytes + BN * kTileK * 2;
+  static constexpr int kStage = 2 * kABytes + H * BN * kTileK * 2;
   static constexpr int kCtrl = 256;   // mbarriers, TMEM slot, flags
-  static constexpr size_t kSmem = 1024 + (size_t)S * kStage + kCtrl + 4 * BN * sizeof(float);
+  static constexpr size_t kSmem = 1024 + (size_t)S * kStage + kCtrl + 4 * H * BN * sizeof(float);
 };
 
-template <int BN, int S>
+template <int BN, int S, int H>
 __global__ void __launch_bounds__(128, 1)
     k_tile_mm(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
               const __grid_constant__ CUtensorMap map_p, const TileMmArgs args) {
-  using Shape = TileMmShape<BN, S>;
+  using Shape = TileMmShape<BN, S, H>;
   constexpr int kStage = Shape::kStage;
+  constexpr int kCols = H * BN;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                          ~static_cast<uintptr_t>(1023));
@@ -68,7 +72,18 @@ __global__ void __launch_bounds__(128, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int chunk = (int)(blockIdx.x % (unsigned)args.nchunks);
   const int rt = (int)(blockIdx.x / (unsigned)args.nchunks);
-  if (args.active && !args.active[chunk]) return;   // every system of the chunk has converged
+  // accumulator h serves systems (chunk H + h) BN ..; skipped when it has none
+  // or all of them have converged (args.active has one flag per BN systems)
+  bool hact[H];
+  int nh = 0;
+#pragma unroll
+  for (int h = 0; h < H; ++h) {
+    const int unit = chunk * H + h;
+    hact[h] = unit * BN < args.J && (!args.active || args.active[unit]);
+    nh += hact[h];
+  }
+  if (nh == 0) return;
+  const uint32_t stage_bytes = 2 * kABytes + nh * BN * kTileK * 2;
   const int t0 = args.rowptr[rt];
   const int nk = args.rowptr[rt + 1] - t0;
 
@@ -86,7 +101,7 @@ __global__ void __launch_bounds__(128, 1)
     tma_prefetch_map(&map_lo);
     tma_prefetch_map(&map_p);
   }
-  if (warp == 2) tmem_alloc(tslot, BN);
+  if (warp == 2) tmem_alloc(tslot, kCols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -104,10 +119,14 @@ __global__ void __launch_bounds__(128, 1)
       if (*reinterpret_cast<volatile int*>(&flags[0])) break;
       unsigned char* st = smem + s * kStage;
       const int tile = t0 + kb;
-      mbar_arrive_expect_tx(&full[s], kStage);
+      mbar_arrive_expect_tx(&full[s], stage_bytes);
       tma_load_2d(st, &map_hi, &full[s], 0, tile * kTileM);
       tma_load_2d(st + kABytes, &map_lo, &full[s], 0, tile * kTileM);
-      tma_load_2d(st + 2 * kABytes, &map_p, &full[s], args.colblk[tile] * kTileK, chunk * BN);
+#pragma unroll
+      for (int h = 0; h < H; ++h)
+        if (hact[h])
+          tma_load_2d(st + 2 * kABytes + h * BN * kTileK * 2, &map_p, &full[s], args.colblk[tile] * kTileK,
+                      (chunk * H + h) * BN);
     }
     flags[1] = kb;
   } else if (warp == 1 && lane == 0) {
@@ -123,12 +142,17 @@ __global__ void __launch_bounds__(128, 1)
       tc_fence_after();
       const uint32_t base = smem_u32(smem + s * kStage);
       const uint64_t dhi = sw128_desc(base), dlo = sw128_desc(base + kABytes);
-      const uint64_t db = sw128_desc(base + 2 * kABytes);
 #pragma unroll
-      for (int k = 0; k < kTileK / 16; ++k)   // K = 16 per MMA: 32 bytes along the swizzled row
-        mma_bf16(tmem, dhi + 2 * k, db + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
+      for (int h = 0; h < H; ++h) {
+        if (!hact[h]) continue;
+        const uint64_t db = sw128_desc(base + 2 * kABytes + h * BN * kTileK * 2);
+        const uint32_t td = tmem + (uint32_t)(h * BN);
 #pragma unroll
-      for (int k = 0; k < kTileK / 16; ++k) mma_bf16(tmem, dlo + 2 * k, db + 2 * k, idesc, 1u);
+        for (int k = 0; k < kTileK / 16; ++k)   // K = 16 per MMA: 32 bytes along the swizzled row
+          mma_bf16(td, dhi + 2 * k, db + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
+#pragma unroll
+        for (int k = 0; k < kTileK / 16; ++k) mma_bf16(td, dlo + 2 * k, db + 2 * k, idesc, 1u);
+      }
       mma_commit(&empty[s]);
     }
     flags[2] = kb;
@@ -143,28 +167,36 @@ __global__ void __launch_bounds__(128, 1)
     const int row = warp * 32 + lane;
     const int64_t a = (int64_t)rt * kTileM + row;
     const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-      float v[16];
-      tmem_ld16(tbase + (uint32_t)c0, v);
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        const int j = chunk * BN + c0 + c;
-        float dot = 0.f;
-        if (j < args.J) {
-          const float p = __bfloat162float(args.P[(int64_t)j * args.d_pad + a]);
-          const float y = fmaf(args.sigma[j], p, v[c]);
-          args.Y[(int64_t)j * args.d_pad + a] = y;
-          dot = p * y;
+    for (int h = 0; h < H; ++h) {
+      if (!hact[h]) continue;   // uniform across the CTA
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        float v[16];
+        tmem_ld16(tbase + (uint32_t)(h * BN + c0), v);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const int j = (chunk * H + h) * BN + c0 + c;
+          float dot = 0.f;
+          if (j < args.J) {
+            const float p = __bfloat162float(args.P[(int64_t)j * args.d_pad + a]);
+            const float y = fmaf(args.sigma[j], p, v[c]);
+            args.Y[(int64_t)j * args.d_pad + a] = y;
+            dot = p * y;
+          }
+          dot = warp_sum_f(dot);
+          if (lane == 0) red[warp * kCols + h * BN + c0 + c] = dot;
         }
-        dot = warp_sum_f(dot);
-        if (lane == 0) red[warp * BN + c0 + c] = dot;
       }
     }
     __syncthreads();
     if (args.pty)
-      for (int t = threadIdx.x; t < BN; t += blockDim.x) {
-        const int j = chunk * BN + t;
-        if (j < args.J) args.pty[(int64_t)rt * args.J + j] = (red[t] + red[BN + t]) + (red[2 * BN + t] + red[3 * BN + t]);
+      for (int t = threadIdx.x; t < kCols; t += blockDim.x) {
+        const int j = chunk * kCols + t;
+        if (j < args.J && hact[t / BN]) {
+          const float v = (red[t] + red[kCols + t]) + (red[2 * kCols + t] + red[3 * kCols + t]);
+          if (args.pty_by_system) args.pty[(int64_t)j * args.nrt + rt] = v;
+          else args.pty[(int64_t)rt * args.J + j] = v;
+        }
       }
   } else if (threadIdx.x == 0) {
     // wait (bounded) for the loads still in flight before the CTA's shared memory goes away
@@ -173,7 +205,7 @@ __global__ void __launch_bounds__(128, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 2) tmem_dealloc(tmem, BN);
+  if (warp == 2) tmem_dealloc(tmem, kCols);
 }
 
 using EncodeFn = PFN_cuTensorMapEncodeTiled_v12000;
@@ -207,9 +239,10 @@ bool encode_bf16(CUtensorMap* m, const void* base, uint64_t cols, uint64_t rows,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN, int S>
-int launch_tile_mm_t(const TileMmArgs& a, const void* chi, const void* clo, int64_t ntiles, cudaStream_t st) {
-  using Shape = TileMmShape<BN, S>;
+template <int BN, int S, int H>
+int launch_tile_mm_t(TileMmArgs a, const void* chi, const void* clo, int64_t ntiles, cudaStream_t st) {
+  using Shape = TileMmShape<BN, S, H>;
+  a.nchunks = (a.J + H * BN - 1) / (H * BN);
   CUtensorMap mh, ml, mp;
   if (!encode_bf16(&mh, chi, kTileK, (uint64_t)ntiles * kTileM, kTileK, kTileM) ||
       !encode_bf16(&ml, clo, kTileK, (uint64_t)ntiles * kTileM, kTileK, kTileM) ||
@@ -219,13 +252,13 @@ int launch_tile_mm_t(const TileMmArgs& a, const void* chi, const void* clo, int6
   int dev = 0;
   cudaGetDevice(&dev);
   if (raised_dev != dev) {
-    if (cudaFuncSetAttribute(k_tile_mm<BN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Shape::kSmem) !=
+    if (cudaFuncSetAttribute(k_tile_mm<BN, S, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Shape::kSmem) !=
         cudaSuccess)
       return INFO_ESRF_ERR_CUDA;
     raised_dev = dev;
   }
   const int64_t grid = (int64_t)a.nrt * a.nchunks;
-  k_tile_mm<BN, S><<<(unsigned)grid, 128, Shape::kSmem, st>>>(mh, ml, mp, a);
+  k_tile_mm<BN, S, H><<<(unsigned)grid, 128, Shape::kSmem, st>>>(mh, ml, mp, a);
   note_launches(1);
   return cudaGetLastError() == cudaSuccess ? INFO_ESRF_OK : INFO_ESRF_ERR_CUDA;
 }
@@ -238,10 +271,12 @@ int launch_tile_mm(TileMmArgs a, const void* chi, const void* clo, int64_t ntile
   if (a.nrt < 1 || a.J < 1 || a.d_pad % kTileM || (int64_t)a.nrt * kTileM != a.d_pad ||
       ntiles * kTileM >= (int64_t(1) << 31))
     return INFO_ESRF_ERR_INVALID_ARG;
-  const int BN = tile_chunk_width(a.J);
-  a.nchunks = (a.J + BN - 1) / BN;
-  if (BN == 128) return launch_tile_mm_t<128, 4>(a, chi, clo, ntiles, st);
-  return launch_tile_mm_t<256, 3>(a, chi, clo, ntiles, st);
+  // up to 128 systems per CTA: one 128-column accumulator, 4 stages; else
+  // 256-column accumulators, 3 stages.  (Two accumulators per CTA, so that a
+  // C block load serves 512 systems, leave room for two stages only and
+  // measured slower: 1225 against 1273 TFLOP/s on the tilemm workload.)
+  if (a.J <= 128) return launch_tile_mm_t<128, 4, 1>(a, chi, clo, ntiles, st);
+  return launch_tile_mm_t<256, 3, 1>(a, chi, clo, ntiles, st);
 }
 
 }  // namespace infoesrf

@@ -36,7 +36,7 @@ namespace {
 
 constexpr int kSys = 8;            // systems per CTA in the vector kernels
 constexpr int kDotRows = kTileDotRows;   // rows per CTA (and per partial dot product)
-constexpr int kVecThreads = 256;   // two rows per thread
+constexpr int kVecThreads = 128;   // four rows per thread
 // per-system FP64 scalars in sysd[j][8]
 enum { kRho = 0, kAlpha = 1, kBeta = 2, kBn2 = 3, kRr = 4, kFirst = 5 };
 
@@ -77,20 +77,27 @@ __global__ void k_tpcg_init(const ProblemDev* dpr) {
   pr.Pdir[i] = __float2bfloat16_rn(0.f);
 }
 
-// alpha_j = rho_j / p_j^T y_j; resets the chunk flags and the running count.
+// alpha_j = rho_j / p_j^T y_j (one warp per system: lanes over the row-tile
+// partials, a fixed shuffle tree); resets the chunk flags and the running count.
 __global__ void k_tpcg_alpha(const ProblemDev* dpr, int it, int nchunks, int reset_only) {
   const ProblemDev& pr = *dpr;
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < nchunks) pr.chunk_active[j] = 0;
-  if (j == 0) pr.nactive[0] = 0;
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gt < nchunks) pr.chunk_active[gt] = 0;
+  if (gt == 0) pr.nactive[0] = 0;
+  const int lane = threadIdx.x & 31;
+  const int64_t j = gt >> 5;
   if (j >= pr.nsys || reset_only) return;
   double* sd = pr.sysd + j * 8;
   if (!pr.active[j]) {
-    sd[kAlpha] = 0.0;
+    if (lane == 0) sd[kAlpha] = 0.0;
     return;
   }
   double pap = 0.0;
-  for (int64_t t = 0; t < pr.nrt; ++t) pap += (double)pr.pty[t * pr.nsys + j];
+  const float* src = pr.pty + j * pr.nrt;
+  for (int64_t t = lane; t < pr.nrt; t += 32) pap += (double)src[t];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) pap += __shfl_xor_sync(0xffffffffu, pap, o);
+  if (lane != 0) return;
   if (pap > 0.0 && isfinite(pap)) {
     sd[kAlpha] = sd[kRho] / pap;
     pr.iters[j] = it;
@@ -111,71 +118,178 @@ __device__ __forceinline__ int64_t listed_system(const int32_t* list, int64_t co
   return list ? list[pos] : pos;
 }
 
+// Row stride (floats) of the staged [Phi | C Phi] rows: 2 k rounded up to a
+// multiple of 4 so that a row is read with 16-byte loads (zero padding).
+__host__ __device__ __forceinline__ int phi_stride(int k) { return (2 * k + 3) & ~3; }
+
+// Stages rows abase .. abase + kDotRows - 1 of [Phi | C Phi] into the padded
+// shared layout phs[row * S2 + m] (m < k: Phi, k <= m < 2k: C Phi, zero
+// padding).  Phi and C Phi are contiguous [d][k] blocks, so each is read with
+// 16-byte loads that are all independent (a block of rows starts at a
+// multiple of 4 floats); rows at or past d are zero.
+__device__ __forceinline__ void stage_phi(const ProblemDev& pr, int64_t abase, int k, int S2, float* phs) {
+  const int64_t a1 = abase + kDotRows < pr.d ? abase + kDotRows : pr.d;
+  const int nrows = a1 > abase ? (int)(a1 - abase) : 0;
+  const int tot = nrows * k;
+  for (int e = threadIdx.x; e < kDotRows * S2; e += blockDim.x) {
+    const int row = e / S2, m = e - row * S2;
+    if (row >= nrows || m >= 2 * k) phs[e] = 0.f;
+  }
+#pragma unroll
+  for (int which = 0; which < 2; ++which) {
+    const float* src = reinterpret_cast<const float*>(which == 0 ? pr.Phi : pr.CPhi) + abase * k;
+    const float4* src4 = reinterpret_cast<const float4*>(src);
+    const int off = which * k;
+#pragma unroll 4
+    for (int q = threadIdx.x; q < tot / 4; q += blockDim.x) {
+      const float4 v = src4[q];
+      const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int e = 4 * q + i, row = e / k, m = e - row * k;
+        phs[row * S2 + off + m] = vv[i];
+      }
+    }
+    for (int e = (tot & ~3) + threadIdx.x; e < tot; e += blockDim.x) {
+      const int row = e / k, m = e - row * k;
+      phs[row * S2 + off + m] = src[e];
+    }
+  }
+}
+
+// CTA layout of steps 3 and 5: thread t serves system t / kRowLanes of the
+// group and rows t % kRowLanes, t % kRowLanes + kRowLanes, ... of the block,
+// so the kSys systems advance side by side and each thread runs a long loop
+// of independent rows.
+constexpr int kRowLanes = kVecThreads / kSys;   // 16
+
+// Step 3 (update = 1) or the dot products of r alone (update = 0).
+// NV32: 32-value chunks of the dot vector (r^T r, f, g): 1 for k <= 14 (the
+// float4 loop then covers 28 columns of [Phi | C Phi]), else 2 (k <= 24).
+template <int NV32>
 __global__ void __launch_bounds__(kVecThreads) k_tpcg_update(const ProblemDev* dpr, int update,
                                                              const int32_t* list, int64_t count) {
   const ProblemDev& pr = *dpr;
   const int64_t sb = blockIdx.x;
   const int64_t g0 = (int64_t)blockIdx.y * kSys;
-  const int k = pr.kR, NV = 2 * k + 1;
+  const int k = pr.kR, NV = 2 * k + 1, S2 = phi_stride(k);
   const int64_t J = pr.nsys, dp = pr.d_pad;
-  extern __shared__ float phs_dyn[];   // [kDotRows][2 k + 1]
-  __shared__ float wred[kVecThreads / 32][2 * kMaxK + 1];
-  bool any = false;
-  for (int s = 0; s < kSys; ++s) {
-    const int64_t j = listed_system(list, count, g0 + s, J);
-    any |= j < J && pr.active[j];
-  }
-  if (!any) return;
-  const float* Phi = reinterpret_cast<const float*>(pr.Phi);
-  const float* CPhi = reinterpret_cast<const float*>(pr.CPhi);
-  const int64_t abase = sb * kDotRows;
-  for (int e = threadIdx.x; e < kDotRows * 2 * k; e += blockDim.x) {
-    const int row = e / (2 * k), m = e % (2 * k);
-    const int64_t a = abase + row;
-    float v = 0.f;
-    if (a < pr.d) v = m < k ? Phi[a * k + m] : CPhi[a * k + (m - k)];
-    phs_dyn[row * (2 * k + 1) + m] = v;
+  extern __shared__ float4 phs_dyn4[];   // [kDotRows][S2 / 4]
+  float* phs = reinterpret_cast<float*>(phs_dyn4);
+  __shared__ float part[kSys][2][32 * NV32];   // per system: the two half-lanes' reduce-scatter results
+  __shared__ int64_t sys[kSys];
+  __shared__ float als[kSys];
+  if (threadIdx.x < kSys) {
+    const int64_t j = listed_system(list, count, g0 + threadIdx.x, J);
+    const bool run = j < J && pr.active[j];
+    sys[threadIdx.x] = run ? j : -1;
+    als[threadIdx.x] = run ? (float)pr.sysd[j * 8 + kAlpha] : 0.f;
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int s = 0; s < kSys; ++s) {
-    const int64_t j = listed_system(list, count, g0 + s, J);
-    if (j >= J || !pr.active[j]) continue;   // uniform across the CTA
-    const float al = (float)pr.sysd[j * 8 + kAlpha];
-    float acc[2 * kMaxK + 1];
+  bool any = false;
+  for (int s = 0; s < kSys; ++s) any |= sys[s] >= 0;
+  if (!any) return;
+  const int64_t abase = sb * kDotRows;
+  stage_phi(pr, abase, k, S2, phs);
+  __syncthreads();
+  const int s = threadIdx.x / kRowLanes, r0 = threadIdx.x % kRowLanes;
+  const int64_t j = sys[s];
+  float acc[32 * NV32];
 #pragma unroll
-    for (int v = 0; v < 2 * kMaxK + 1; ++v) acc[v] = 0.f;
-    for (int rr = threadIdx.x; rr < kDotRows; rr += blockDim.x) {
-      const int64_t a = abase + rr;
+  for (int v = 0; v < 32 * NV32; ++v) acc[v] = 0.f;
+  if (j >= 0) {
+    const float al = als[s];
+    // four consecutive rows per step: 16-byte loads of r, y, x and 8 bytes of p
+    // (d_pad and the row block are multiples of 4, so a group never straddles dp)
+    for (int r4 = 4 * r0; r4 < kDotRows; r4 += 4 * kRowLanes) {
+      const int64_t a = abase + r4;
       if (a >= dp) break;
       const int64_t e = j * dp + a;
-      float r = pr.Rv[e];
+      float4 rv = *reinterpret_cast<const float4*>(pr.Rv + e);
       if (update) {
-        const float p = __bfloat162float(pr.Pdir[e]);
-        pr.Xv[e] = fmaf(al, p, pr.Xv[e]);
-        r = fmaf(-al, pr.Yv[e], r);
-        pr.Rv[e] = r;
+        const uint2 pw = *reinterpret_cast<const uint2*>(pr.Pdir + e);
+        const __nv_bfloat162* pp = reinterpret_cast<const __nv_bfloat162*>(&pw);
+        const float2 p01 = __bfloat1622float2(pp[0]), p23 = __bfloat1622float2(pp[1]);
+        float4 xv = *reinterpret_cast<const float4*>(pr.Xv + e);
+        const float4 yv = *reinterpret_cast<const float4*>(pr.Yv + e);
+        xv.x = fmaf(al, p01.x, xv.x);
+        xv.y = fmaf(al, p01.y, xv.y);
+        xv.z = fmaf(al, p23.x, xv.z);
+        xv.w = fmaf(al, p23.y, xv.w);
+        rv.x = fmaf(-al, yv.x, rv.x);
+        rv.y = fmaf(-al, yv.y, rv.y);
+        rv.z = fmaf(-al, yv.z, rv.z);
+        rv.w = fmaf(-al, yv.w, rv.w);
+        *reinterpret_cast<float4*>(pr.Xv + e) = xv;
+        *reinterpret_cast<float4*>(pr.Rv + e) = rv;
       }
-      acc[0] = fmaf(r, r, acc[0]);
+      const float rr4[4] = {rv.x, rv.y, rv.z, rv.w};
 #pragma unroll
-      for (int m = 0; m < 2 * kMaxK; ++m)
-        if (m < 2 * k) acc[1 + m] = fmaf(phs_dyn[rr * (2 * k + 1) + m], r, acc[1 + m]);
-    }
+      for (int i = 0; i < 4; ++i) {
+        const float r = rr4[i];
+        acc[0] = fmaf(r, r, acc[0]);
+        const float4* row4 = phs_dyn4 + (r4 + i) * (S2 / 4);
 #pragma unroll
-    for (int v = 0; v < 2 * kMaxK + 1; ++v) {
-      if (v >= NV) break;
-      float x = acc[v];
+        for (int q = 0; q < (32 * NV32 - 1) / 4; ++q) {
+          if (4 * q < 2 * k) {
+            const float4 f = row4[q];
+            acc[1 + 4 * q] = fmaf(f.x, r, acc[1 + 4 * q]);
+            acc[2 + 4 * q] = fmaf(f.y, r, acc[2 + 4 * q]);
+            acc[3 + 4 * q] = fmaf(f.z, r, acc[3 + 4 * q]);
+            acc[4 + 4 * q] = fmaf(f.w, r, acc[4 + 4 * q]);
+          }
+        }
+      }
+    }
+  }
+  // reduce over the 16 row lanes of each system (a half-warp): a reduce-scatter
+  // with offsets 8, 4, 2, 1 leaves lane l of the half with values 2 l and 2 l + 1
+  // of each 32-value chunk (fixed order of additions)
+  const int hl = r0;   // lane within the half-warp
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      if (lane == 0) wred[warp][v] = x;
+  for (int c = 0; c < NV32; ++c) {
+    float* v = acc + 32 * c;
+#pragma unroll
+    for (int off = 8, width = 16; off >= 1; off >>= 1, width >>= 1) {
+      const bool up = (hl & off) != 0;
+#pragma unroll
+      for (int i = 0; i < width; ++i) {
+        const float send = up ? v[i] : v[i + width];
+        const float keep = up ? v[i + width] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+      }
     }
-    __syncthreads();
-    for (int v = threadIdx.x; v < NV; v += blockDim.x) {
-      double t = 0.0;
-      for (int w = 0; w < kVecThreads / 32; ++w) t += (double)wred[w][v];
-      pr.dots[(sb * J + j) * NV + v] = t;
-    }
-    __syncthreads();
+    // after the rounds lane hl holds the sums of values 2 hl', 2 hl' + 1 with hl' the
+    // bit-reversal-free index: value index = 16 b3 + 8 b2 + 4 b1 + 2 b0 + i, i in {0, 1}
+    const int vbase = 32 * c + 16 * ((hl >> 3) & 1) + 8 * ((hl >> 2) & 1) + 4 * ((hl >> 1) & 1) + 2 * (hl & 1);
+    part[s][0][vbase] = v[0];
+    part[s][0][vbase + 1] = v[1];
+  }
+  __syncthreads();
+  const int64_t nsub = gridDim.x;
+  for (int e = threadIdx.x; e < kSys * NV; e += blockDim.x) {
+    const int ss = e / NV, v = e % NV;
+    if (sys[ss] >= 0) pr.dots[(sys[ss] * NV + v) * nsub + sb] = (double)part[ss][0][v];
+  }
+}
+
+// Sums of the row-block partials: one CTA per listed system, one warp per
+// value (r^T r, f, g), lanes over the row blocks (contiguous), then a fixed
+// shuffle tree: the same order every call.
+__global__ void __launch_bounds__(256) k_tpcg_reduce(const ProblemDev* dpr, int nsub, const int32_t* list,
+                                                     int64_t count) {
+  const ProblemDev& pr = *dpr;
+  const int64_t j = listed_system(list, count, blockIdx.x, pr.nsys);
+  if (j >= pr.nsys || !pr.active[j]) return;
+  const int NV = 2 * pr.kR + 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int v = warp; v < NV; v += blockDim.x >> 5) {
+    const double* src = pr.dots + (j * NV + v) * (int64_t)nsub;
+    double t = 0.0;
+    for (int sb = lane; sb < nsub; sb += 32) t += src[sb];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) pr.dsum[j * NV + v] = t;
   }
 }
 
@@ -186,10 +300,8 @@ __global__ void k_tpcg_scalars(const ProblemDev* dpr, int nsub, int bn, int last
   if (j == 0) pr.nactive[1] = pr.status[0];   // timeouts and overflow are set by earlier kernels
   if (j >= pr.nsys || !pr.active[j]) return;
   const int k = pr.kR, NV = 2 * k + 1;
-  double v[2 * kMaxK + 1];
-  for (int e = 0; e < NV; ++e) v[e] = 0.0;
-  for (int s = 0; s < nsub; ++s)
-    for (int e = 0; e < NV; ++e) v[e] += pr.dots[((int64_t)s * pr.nsys + j) * NV + e];
+  const double* v = pr.dsum + j * NV;   // r^T r, f = Phi^T r, g = (C Phi)^T r
+  (void)nsub;
   double* sd = pr.sysd + j * 8;
   const double rr = v[0];
   const bool first = sd[kFirst] != 0.0;
@@ -244,51 +356,74 @@ __global__ void k_tpcg_scalars(const ProblemDev* dpr, int nsub, int bn, int last
 }
 
 // Step 5: p = bf16(r - (C Phi) t + Phi c + beta p) for the running systems;
-// same CTA shape as step 3.
+// same CTA layout as step 3, the coefficients of all its systems staged once.
 __global__ void __launch_bounds__(kVecThreads) k_tpcg_direction(const ProblemDev* dpr) {
   const ProblemDev& pr = *dpr;
   const int64_t sb = blockIdx.x;
   const int64_t g0 = (int64_t)blockIdx.y * kSys;
-  const int k = pr.kR;
+  const int k = pr.kR, S2 = phi_stride(k);
   const int64_t J = pr.nsys, dp = pr.d_pad;
   const int64_t count = pr.nactive[0];   // the list the scalars kernel just built
-  extern __shared__ float phs_dyn[];   // [kDotRows][2 k + 1]
-  __shared__ float tc[2 * kMaxK];
+  extern __shared__ float4 phs_dyn4[];   // [kDotRows][S2 / 4]
+  float* phs = reinterpret_cast<float*>(phs_dyn4);
+  __shared__ float4 tc4[kSys][2 * kMaxK / 4];   // per system: c (Phi coefficients), then -t (C Phi)
+  __shared__ int64_t sys[kSys];
+  __shared__ float bes[kSys];
+  if (threadIdx.x < kSys) {
+    const int64_t j = listed_system(pr.alist, count, g0 + threadIdx.x, J);
+    const bool run = j < J && pr.active[j];
+    sys[threadIdx.x] = run ? j : -1;
+    bes[threadIdx.x] = run ? (float)pr.sysd[j * 8 + kBeta] : 0.f;
+  }
+  __syncthreads();
   bool any = false;
-  for (int s = 0; s < kSys; ++s) {
-    const int64_t j = listed_system(pr.alist, count, g0 + s, J);
-    any |= j < J && pr.active[j];
-  }
+  for (int s = 0; s < kSys; ++s) any |= sys[s] >= 0;
   if (!any) return;
-  const float* Phi = reinterpret_cast<const float*>(pr.Phi);
-  const float* CPhi = reinterpret_cast<const float*>(pr.CPhi);
   const int64_t abase = sb * kDotRows;
-  for (int e = threadIdx.x; e < kDotRows * 2 * k; e += blockDim.x) {
-    const int row = e / (2 * k), m = e % (2 * k);
-    const int64_t a = abase + row;
+  stage_phi(pr, abase, k, S2, phs);
+  float* tcf = reinterpret_cast<float*>(tc4);
+  for (int e = threadIdx.x; e < kSys * 2 * kMaxK; e += blockDim.x) {
+    const int s = e / (2 * kMaxK), m = e % (2 * kMaxK);
     float v = 0.f;
-    if (a < pr.d) v = m < k ? Phi[a * k + m] : CPhi[a * k + (m - k)];
-    phs_dyn[row * (2 * k + 1) + m] = v;
-  }
-  for (int s = 0; s < kSys; ++s) {
-    const int64_t j = listed_system(pr.alist, count, g0 + s, J);
-    if (j >= J || !pr.active[j]) continue;   // uniform across the CTA
-    __syncthreads();
-    for (int m = threadIdx.x; m < 2 * k; m += blockDim.x)
-      tc[m] = pr.lcoef[j * 2 * kMaxK + (m < k ? m : kMaxK + (m - k))];   // t then c
-    __syncthreads();
-    const float be = (float)pr.sysd[j * 8 + kBeta];
-    for (int rr = threadIdx.x; rr < kDotRows; rr += blockDim.x) {
-      const int64_t a = abase + rr;
-      if (a >= dp) break;
-      const int64_t e = j * dp + a;
-      float z = pr.Rv[e];
-#pragma unroll
-      for (int m = 0; m < kMaxK; ++m)
-        if (m < k) z += phs_dyn[rr * (2 * k + 1) + m] * tc[k + m] - phs_dyn[rr * (2 * k + 1) + k + m] * tc[m];
-      const float p = __bfloat162float(pr.Pdir[e]);
-      pr.Pdir[e] = __float2bfloat16_rn(a < pr.d ? fmaf(be, p, z) : 0.f);
+    if (sys[s] >= 0 && m < S2) {
+      // aligned with the staged row: Phi columns take c, C Phi columns take -t
+      if (m < k) v = pr.lcoef[sys[s] * 2 * kMaxK + kMaxK + m];
+      else if (m < 2 * k) v = -pr.lcoef[sys[s] * 2 * kMaxK + (m - k)];
     }
+    tcf[e] = v;
+  }
+  __syncthreads();
+  const int s = threadIdx.x / kRowLanes, r0 = threadIdx.x % kRowLanes;
+  const int64_t j = sys[s];
+  if (j < 0) return;
+  const float be = bes[s];
+  for (int r4 = 4 * r0; r4 < kDotRows; r4 += 4 * kRowLanes) {   // four rows per step
+    const int64_t a = abase + r4;
+    if (a >= dp) break;
+    const int64_t e = j * dp + a;
+    const float4 rv = *reinterpret_cast<const float4*>(pr.Rv + e);
+    const uint2 pw = *reinterpret_cast<const uint2*>(pr.Pdir + e);
+    const __nv_bfloat162* pp = reinterpret_cast<const __nv_bfloat162*>(&pw);
+    const float2 p01 = __bfloat1622float2(pp[0]), p23 = __bfloat1622float2(pp[1]);
+    float z[4] = {rv.x, rv.y, rv.z, rv.w};
+    const float pv[4] = {p01.x, p01.y, p23.x, p23.y};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float4* row4 = phs_dyn4 + (r4 + i) * (S2 / 4);
+#pragma unroll
+      for (int q = 0; q < 2 * kMaxK / 4; ++q) {
+        if (4 * q < 2 * k) {
+          const float4 f = row4[q], c = tc4[s][q];
+          z[i] = fmaf(f.x, c.x, z[i]);
+          z[i] = fmaf(f.y, c.y, z[i]);
+          z[i] = fmaf(f.z, c.z, z[i]);
+          z[i] = fmaf(f.w, c.w, z[i]);
+        }
+      }
+      z[i] = (a + i < pr.d) ? fmaf(be, pv[i], z[i]) : 0.f;
+    }
+    __nv_bfloat162 out[2] = {__floats2bfloat162_rn(z[0], z[1]), __floats2bfloat162_rn(z[2], z[3])};
+    *reinterpret_cast<uint2*>(pr.Pdir + e) = *reinterpret_cast<const uint2*>(out);
   }
 }
 
@@ -341,26 +476,34 @@ int run_tile_pcg(const ProblemDev& p, const ProblemDev* dp, cudaStream_t st, dou
   ta.d_pad = p.d_pad;
   ta.J = (int32_t)J;
   ta.nrt = p.nrt;
+  ta.pty_by_system = 1;
   const int maxit = p.fixed_iters > 0 ? p.fixed_iters : p.max_iter;
-  const size_t vsm = (size_t)kDotRows * (2 * p.kR + 1) * sizeof(float);
+  const size_t vsm = (size_t)kDotRows * phi_stride(p.kR) * sizeof(float);
+  const bool wide = 2 * p.kR > 28;   // k > 14: 64-value dot vectors (the 32-value loop covers 28 columns)
   static thread_local int raised = -1;
   int dev = 0;
   cudaGetDevice(&dev);
   if (raised != dev) {
-    const int mx = (int)((size_t)kDotRows * (2 * kMaxK + 1) * sizeof(float));
-    if (cudaFuncSetAttribute(k_tpcg_update, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess ||
+    const int mx = (int)((size_t)kDotRows * phi_stride(kMaxK) * sizeof(float));
+    if (cudaFuncSetAttribute(k_tpcg_update<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess ||
+        cudaFuncSetAttribute(k_tpcg_update<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess ||
         cudaFuncSetAttribute(k_tpcg_direction, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess)
       return INFO_ESRF_ERR_CUDA;
     raised = dev;
   }
   int32_t host[2] = {0, 0};
   k_tpcg_init<<<gall, 256, 0, st>>>(dp);
-  k_tpcg_update<<<gvec, kVecThreads, vsm, st>>>(dp, 0, nullptr, J);
-  const dim3 galpha((unsigned)(((J > nchunks ? J : nchunks) + 127) / 128));
-  k_tpcg_alpha<<<galpha, 128, 0, st>>>(dp, 0, nchunks, 1);   // resets the chunk flags and the count
+  auto update = [&](dim3 grid, int upd, const int32_t* list, int64_t count) {
+    if (wide) k_tpcg_update<2><<<grid, kVecThreads, vsm, st>>>(dp, upd, list, count);
+    else k_tpcg_update<1><<<grid, kVecThreads, vsm, st>>>(dp, upd, list, count);
+  };
+  update(gvec, 0, nullptr, J);
+  k_tpcg_reduce<<<(unsigned)J, 256, 0, st>>>(dp, nsub, nullptr, J);
+  const dim3 galpha((unsigned)(((32 * J > nchunks ? 32 * J : nchunks) + 255) / 256));
+  k_tpcg_alpha<<<galpha, 256, 0, st>>>(dp, 0, nchunks, 1);   // resets the chunk flags and the count
   k_tpcg_scalars<<<gsys, 128, 0, st>>>(dp, nsub, bn, maxit <= 0 ? 1 : 0);
   k_tpcg_direction<<<gvec, kVecThreads, vsm, st>>>(dp);
-  note_launches(5);
+  note_launches(6);
   for (int it = 1; it <= maxit; ++it) {
     // running systems (and the status word) after the previous iteration
     if (cudaMemcpyAsync(host, p.nactive, sizeof(host), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -377,11 +520,12 @@ int run_tile_pcg(const ProblemDev& p, const ProblemDev* dp, cudaStream_t st, dou
       cudaEventRecord(ev[1], st);
       timed = true;
     }
-    k_tpcg_alpha<<<galpha, 128, 0, st>>>(dp, it, nchunks, 0);
-    k_tpcg_update<<<glist, kVecThreads, vsm, st>>>(dp, 1, p.alist, nrun);
+    k_tpcg_alpha<<<galpha, 256, 0, st>>>(dp, it, nchunks, 0);
+    update(glist, 1, p.alist, nrun);
+    k_tpcg_reduce<<<(unsigned)nrun, 256, 0, st>>>(dp, nsub, p.alist, nrun);
     k_tpcg_scalars<<<gsys, 128, 0, st>>>(dp, nsub, bn, it == maxit ? 1 : 0);
     k_tpcg_direction<<<glist, kVecThreads, vsm, st>>>(dp);
-    note_launches(4);
+    note_launches(5);
   }
   if (timed) {
     if (cudaEventSynchronize(ev[1]) != cudaSuccess) return INFO_ESRF_ERR_CUDA;

@@ -117,7 +117,7 @@ def test_multishift_plan_limits_without_gpu(lib):
 
     g = grid(8192, 5.0)
     ms = dict(solver=binding.SOLVER_MULTISHIFT)
-    for sv, ok in ((0, True), (1, True), (2, False), (-1, False)):
+    for sv, ok in ((0, True), (1, True), (2, True), (3, False), (-1, False)):
         o = binding.make_options(solver=sv)
         assert (L.info_esrf_workspace_size(ctypes.byref(g), 10, 1024, 8, ctypes.byref(o)) > 0) == ok, sv
     # one chain's p in shared memory: about 35,000 FP32 observations at most

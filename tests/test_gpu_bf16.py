@@ -76,7 +76,7 @@ def test_bf16_layered_l96(B):
     check(pr, mu_a, A_a)
 
 
-@pytest.mark.parametrize("case", ["ragged", "one_obs", "two_members", "all_observed", "no_ritz"])
+@pytest.mark.parametrize("case", ["ragged", "one_obs", "two_members", "all_observed", "no_ritz", "ritz20"])
 def test_bf16_ragged_and_degenerate_sizes(B, case):
     kw = {}
     if case == "ragged":
@@ -91,10 +91,14 @@ def test_bf16_ragged_and_degenerate_sizes(B, case):
     elif case == "all_observed":
         pr = workloads.gaussian_problem_1d("all", n=200, N=10, length_scale=5.0, obs_stride=1, r2=1.0,
                                            half_width=5.0, Q=6, tol=1e-6, seed=7)
-    else:
+    elif case == "no_ritz":
         pr = workloads.gaussian_problem_1d("nor", n=500, N=10, length_scale=5.0, obs_stride=2, r2=0.5,
                                            half_width=7.0, Q=6, tol=1e-6, seed=8)
         kw = dict(ritz_rank=0)
+    else:   # more than 14 Ritz vectors: the 64-value dot-product path of the vector kernels
+        pr = workloads.gaussian_problem_2d(nx=64, ny=64, N=12, length_scale=5.0, obs_stride=2, r2=0.5,
+                                           half_width=6.0, Q=6, tol=1e-6, seed=9)
+        kw = dict(ritz_rank=20, oversample=8)
     mu_a, A_a, st = run(B, pr, **kw)
     assert st["status"] == 0 and st["n_unconverged"] == 0, (case, st)
     check(pr, mu_a, A_a)

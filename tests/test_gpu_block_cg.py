@@ -1,0 +1,109 @@
+"""Block CG across members (Sec. 3.3, second alternative) on the GPU, through the C ABI.
+
+- Converged analyses against the oracle's same-node result (exact solves per
+  node, Sec. 3.2): FP64 at tol 1e-12 within 1e-10, FP32 at tol 1e-6 within
+  1e-4, element-wise per member; on a 1-D problem (config-1 shape), a layered
+  grid and a 2-D grid.
+- Fixed iteration counts (2, 5): the analysis built from the oracle's own
+  block CG iterates (oracle/pcg.py::solve_normalized_block with fixed_iters)
+  is reproduced at FP64 (1e-9), iteration for iteration.
+- The mean update and the perturbation update alone; more than 64 members is
+  unsupported; the iteration cap reports NOT_CONVERGED.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import filter as F
+from oracle import pcg, quadrature
+from paper_2503_00253_gb300 import workloads
+from parity_checks import increment_error, mean_error
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2503_00253_gb300 import binding
+    binding.library()
+    return binding
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def run(B, pr, precision, tol, **kw):
+    opts = B.make_options(precision=precision, solver=B.SOLVER_BLOCK, **kw)
+    mu_a, A_a, st = B.info_esrf_analysis(pr.grid, dev(pr.X), dev(pr.obs_idx), dev(pr.y), dev(pr.R), pr.Q, tol, opts)
+    torch.cuda.synchronize()
+    return mu_a.cpu().numpy(), A_a.cpu().numpy(), st
+
+
+PROBLEMS = {
+    "config1": lambda: workloads.config1(),
+    "layered": lambda: workloads.layered_l96_problem(nx=120, nz=4, N=12, spinup=200, c_x=10.0, c_z=1.0, Q=8),
+    "grid2d": lambda: workloads.gaussian_problem_2d(nx=48, ny=40, N=10, length_scale=4.0, obs_stride=2, r2=0.5,
+                                                    half_width=5.0, Q=6, tol=1e-12, seed=3),
+}
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+@pytest.mark.parametrize("precision,tol,bound", [(0, 1e-12, 1e-10), (1, 1e-6, 1e-4)])
+def test_block_cg_matches_oracle(B, name, precision, tol, bound):
+    pr = PROBLEMS[name]()
+    mu_a, A_a, st = run(B, pr, precision, tol)
+    assert st["status"] == 0 and st["solver_path"] == 4 and st["n_unconverged"] == 0, st
+    A_ref = F.perturbation_update(pr.X, pr.obs_idx, pr.R, pr.grid, pr.Q)
+    mu_ref = F.mean_update(pr.X, pr.obs_idx, pr.y, pr.R, pr.grid)
+    ea = increment_error(A_a, A_ref, pr.X - pr.X.mean(0))
+    em = mean_error(mu_a, mu_ref, pr.X.mean(0))
+    print(f"{name} block CG prec {precision}: {ea:.2e} {em:.2e}, iters {st['iters_mean']:.1f}/{st['iters_max']}")
+    assert ea <= bound and em <= bound, (ea, em)
+
+
+@pytest.mark.parametrize("iters", [2, 5])
+def test_block_cg_fixed_iterations_match_oracle_iterates(B, iters):
+    pr = workloads.gaussian_problem_1d("bfix", n=600, N=8, length_scale=6.0, obs_stride=2, r2=0.4,
+                                       half_width=10.0, Q=5, tol=1e-12, seed=11)
+    mu, Z = F.anomalies(pr.X)
+    W, Sxh, Shh = F.localized_covariances(Z, pr.obs_idx, pr.grid)
+    C = F.normalized_obs_covariance(Shh, pr.R)
+    s, p = quadrature.elliptic_rule(pr.Q, F.choose_ell(Shh, pr.R))
+    vbar, it = pcg.solve_normalized_block(C, s, p, W, pr.R, fixed_iters=iters)
+    assert np.all(it == iters)
+    A_ref = math.sqrt(pr.N - 1) * (Z - Sxh @ vbar).T
+    opts = B.make_options(precision=0, solver=B.SOLVER_BLOCK, fixed_iters=iters)
+    A_a, st = B.info_esrf_perturbation_update(pr.grid, dev(pr.X), dev(pr.obs_idx), dev(pr.R), pr.Q, 1e-12, opts)
+    torch.cuda.synchronize()
+    assert st["iters_max"] == iters
+    err = increment_error(A_a, A_ref, pr.X - pr.X.mean(0))
+    assert err < 1e-9, (iters, err)
+
+
+def test_block_cg_mean_and_perturbation_alone_and_limits(B):
+    pr = workloads.gaussian_problem_1d("balone", n=500, N=12, length_scale=5.0, obs_stride=4, r2=0.5,
+                                       half_width=8.0, Q=6, tol=1e-12, seed=10)
+    X, obs, y, R = dev(pr.X), dev(pr.obs_idx), dev(pr.y), dev(pr.R)
+    opts = B.make_options(precision=0, solver=B.SOLVER_BLOCK)
+    mu_a, st_m = B.info_esrf_mean_update(pr.grid, X, obs, y, R, 1e-12, opts)
+    A_a, st_p = B.info_esrf_perturbation_update(pr.grid, X, obs, R, pr.Q, 1e-12, opts)
+    torch.cuda.synchronize()
+    assert st_m["n_systems"] == 1 and st_p["n_systems"] == pr.Q * pr.N
+    A_ref = F.perturbation_update(pr.X, pr.obs_idx, pr.R, pr.grid, pr.Q)
+    mu_ref = F.mean_update(pr.X, pr.obs_idx, pr.y, pr.R, pr.grid)
+    assert increment_error(A_a, A_ref, pr.X - pr.X.mean(0)) <= 1e-10
+    assert mean_error(mu_a, mu_ref, pr.X.mean(0)) <= 1e-10
+    # iteration cap: NOT_CONVERGED with outputs written
+    capped = B.make_options(precision=0, solver=B.SOLVER_BLOCK, max_iter=2)
+    _, _, st = B.info_esrf_analysis(pr.grid, X, obs, y, R, pr.Q, 1e-12, capped)
+    torch.cuda.synchronize()
+    assert st["status"] == B.NOT_CONVERGED and st["n_unconverged"] > 0
+    # more than 64 members per block
+    big = workloads.gaussian_problem_1d("bbig", n=300, N=70, length_scale=5.0, obs_stride=3, r2=0.5,
+                                        half_width=6.0, Q=3, tol=1e-12, seed=12)
+    with pytest.raises(B.InfoEsrfError) as e:
+        B.info_esrf_analysis(big.grid, dev(big.X), dev(big.obs_idx), dev(big.y), dev(big.R), big.Q, 1e-12, opts)
+    assert e.value.code == B.ERR_UNSUPPORTED
