@@ -79,9 +79,11 @@ extern "C" {
 /* Block CG across members (Sec. 3.3, second alternative; O'Leary's block CG):
  * for every node the N members' systems share one block Krylov space and are
  * solved together, X_0 = 0, R_0 = P_0 = B, alpha = (P^T C_q P)^-1 (R^T R),
- * beta = (R^T R)^-1 (R'^T R'), without deflation and without a preconditioner
- * (the mean system is a block of one column); a block stops when every
- * column meets tol (or after fixed_iters).  FP64 or FP32 bulk (s x s algebra
+ * beta = (R^T R)^-1 (R'^T R'), without a preconditioner (the mean system is
+ * a block of one column); a block stops when every column meets tol (or
+ * after fixed_iters).  The members' right-hand sides sum to zero, so the
+ * block runs on N - 1 columns and the last member's solution is minus the sum
+ * of the others; Gram pivots at rounding level count as zero.  FP64 or FP32 bulk (s x s algebra
  * and Gram sums in FP64), N <= 64.  The call synchronizes its stream once per
  * iteration (convergence is tested on the host). */
 #define INFO_ESRF_SOLVER_BLOCK 2

@@ -9,8 +9,11 @@
 //     beta = (R^T R)^-1 (R'^T R'),  P = R' + P beta.
 //
 // A block stops when every column has ||r_i|| <= tol ||b_i|| (or after
-// fixed_iters iterations), and is iterated at full rank until then (no
-// deflation).  Kernels per iteration, over all running blocks at once:
+// fixed_iters iterations).  The members' right-hand sides sum to zero, so a
+// node's block runs on N - 1 columns and the last member's solution is minus
+// the sum of the others (the same block Krylov space, so the same iterates in
+// exact arithmetic); pivots of the s x s Gram matrices at rounding level are
+// taken as zero (semidefinite Cholesky), which deflates converged columns.  Kernels per iteration, over all running blocks at once:
 // the banded product Q = sigma P + C P (the ELL band of C from set-up), the
 // Gram matrices P^T Q and R^T R (FP64 sums in a fixed order), one CTA per
 // block for the s x s Cholesky solves (FP64), and the block updates of X, R
@@ -40,12 +43,40 @@ __device__ __forceinline__ BlockInfo block_info(const ProblemDev& pr, int b) {
     bi.s = 1;
     bi.sigma = 1.0;
   } else {
+    // the members' right-hand sides sum to zero (anomalies of the ensemble
+    // mean), so the last member's system is minus the sum of the others and
+    // shares their block Krylov space: the block iterates over N - 1 columns
+    // and k_bcg_complete fills in the last
     const int q = b - pr.mean_sys;
     bi.sid0 = pr.mean_sys + (int64_t)q * pr.N;
-    bi.s = (int)pr.N;
+    bi.s = (int)pr.N - 1;
     bi.sigma = pr.s[q] + 1.0;
   }
   return bi;
+}
+
+// The last member of every perturbation block: x_N = -(x_1 + ... + x_(N-1)),
+// with the block's iteration count and the largest relative residual.
+template <typename T>
+__global__ void k_bcg_complete(const ProblemDev* dp) {
+  const ProblemDev& pr = *dp;
+  const int b = pr.mean_sys + blockIdx.y;
+  if (b >= pr.bcg_nblocks) return;
+  const BlockInfo bi = block_info(pr, b);
+  const int64_t d = pr.d, last = bi.sid0 + bi.s;
+  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  T* X = reinterpret_cast<T*>(pr.U);
+  if (a < d) {
+    double acc = 0.0;
+    for (int i = 0; i < bi.s; ++i) acc += (double)X[(bi.sid0 + i) * d + a];
+    X[last * d + a] = to_t<T>(-acc);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double rmax = 0.0;
+    for (int i = 0; i < bi.s; ++i) rmax = fmax(rmax, pr.relres[bi.sid0 + i]);
+    pr.relres[last] = rmax;
+    pr.iters[last] = bi.s > 0 ? pr.iters[bi.sid0] : 0;
+  }
 }
 
 // X = 0, R = P = b for every system.
@@ -70,6 +101,7 @@ __global__ void k_bcg_matvec(const ProblemDev* dp) {
   const int64_t sid = blockIdx.y;
   const int b = sid < pr.mean_sys ? 0 : pr.mean_sys + (int)((sid - pr.mean_sys) / pr.N);
   if (pr.bcg_state[b] != 0) return;
+  if (sid >= pr.mean_sys && (sid - pr.mean_sys) % pr.N == pr.N - 1) return;   // completed at the end
   const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= pr.d) return;
   const int64_t d = pr.d;
@@ -359,6 +391,10 @@ int run_bcg_t(const ProblemDev& p, const ProblemDev* dp, cudaStream_t st) {
     k_bcg_solve<<<nb, 128, ssm, st>>>(dp, 1, it, it == maxit);  // convergence, beta
     k_bcg_update<T><<<gupd, 128, 0, st>>>(dp, 1);               // P
     note_launches(8);
+  }
+  if (p.do_pert) {
+    k_bcg_complete<T><<<dim3((unsigned)((p.d + 255) / 256), (unsigned)p.Q), 256, 0, st>>>(dp);
+    note_launches(1);
   }
   return cudaGetLastError() == cudaSuccess ? 0 : INFO_ESRF_ERR_CUDA;
 }

@@ -4,9 +4,10 @@
   node, Sec. 3.2): FP64 at tol 1e-12 within 1e-10, FP32 at tol 1e-6 within
   1e-4, element-wise per member; on a 1-D problem (config-1 shape), a layered
   grid and a 2-D grid.
-- Fixed iteration counts (2, 5): the analysis built from the oracle's own
+- Fixed iteration counts (2, 3, 5): the analysis built from the oracle's own
   block CG iterates (oracle/pcg.py::solve_normalized_block with fixed_iters)
-  is reproduced at FP64 (1e-9), iteration for iteration.
+  is reproduced at FP64, iteration for iteration (1e-9 while every column is
+  above rounding level, 1e-7 after columns have converged).
 - The mean update and the perturbation update alone; more than 64 members is
   unsupported; the iteration cap reports NOT_CONVERGED.
 """
@@ -64,8 +65,12 @@ def test_block_cg_matches_oracle(B, name, precision, tol, bound):
     assert ea <= bound and em <= bound, (ea, em)
 
 
-@pytest.mark.parametrize("iters", [2, 5])
-def test_block_cg_fixed_iterations_match_oracle_iterates(B, iters):
+@pytest.mark.parametrize("iters,bound", [(2, 1e-9), (3, 1e-9), (5, 1e-7)])
+def test_block_cg_fixed_iterations_match_oracle_iterates(B, iters, bound):
+    """Once columns of a block have converged to rounding level (here after about 4 iterations), the
+    block's Gram matrices are singular to rounding and the k-th block iterate is fixed only up to those
+    directions: the oracle's dense LU solve and the library's semidefinite Cholesky then differ at that
+    level, hence the looser bound at 5 iterations."""
     pr = workloads.gaussian_problem_1d("bfix", n=600, N=8, length_scale=6.0, obs_stride=2, r2=0.4,
                                        half_width=10.0, Q=5, tol=1e-12, seed=11)
     mu, Z = F.anomalies(pr.X)
@@ -80,7 +85,7 @@ def test_block_cg_fixed_iterations_match_oracle_iterates(B, iters):
     torch.cuda.synchronize()
     assert st["iters_max"] == iters
     err = increment_error(A_a, A_ref, pr.X - pr.X.mean(0))
-    assert err < 1e-9, (iters, err)
+    assert err < bound, (iters, err)
 
 
 def test_block_cg_mean_and_perturbation_alone_and_limits(B):
