@@ -36,15 +36,16 @@ TOL_MIXED = 1e-6
 RITZ = 10
 TRAIN_SEEDS = (11, 12, 13)
 SOLVER_KERNELS = {0: "k_pcg (general persistent batched PCG)", 1: "k_pcg_band1d (cluster-resident band PCG)",
-                  2: "k_mscg (multi-shift CG)"}
+                  2: "k_mscg (multi-shift CG)", 3: "k_tile_mm + k_tpcg_* (BF16 tensor-core block-tile PCG)",
+                  4: "k_bcg_* (block CG across members)"}
 # DRAM bytes (read + write) of one launch of a kernel on the headline workload,
 # measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum) on this
 # bench, keyed by the SHA-256 prefix of the kernel's source file when the
 # counters were taken.  The figure is reported only while that file is
 # unchanged; otherwise the line's "traffic" is null.
 TRAFFIC = {
-    "k_pcg_band1d": ("pcg_cluster.cu", None, None),
-    "k_mscg": ("mscg.cu", None, None),
+    "k_pcg_band1d": ("pcg_cluster.cu", "7a2311a839860dfe", 1459712),
+    "k_mscg": ("mscg.cu", "1fdc47a794982019", 1351680),
 }
 
 
@@ -338,6 +339,8 @@ def run_ours(args):
         if not multishift:
             # one unpreconditioned CG run per member for all shifts (Sec. 3.3)
             cases.insert(0, ("multishift_fp32", B.PRECISION_FP32, B.SOLVER_MULTISHIFT))
+            # block CG across members, one block per node (Sec. 3.3, second alternative)
+            cases.insert(1, ("block_fp32", B.PRECISION_FP32, B.SOLVER_BLOCK))
         for key, pc, sv in cases:
             # the headline's autotuned eigensolver settings, so that only the
             # preconditioner (or the solver, or the precision) differs
@@ -363,7 +366,8 @@ def run_ours(args):
             # timed like the headline: CUDA-graph replays of the analysis call
             # (direct calls where capture is refused), L2 flushed between steps
             gc, how = None, "direct call"
-            if args.graph:
+            # the block solver tests convergence on the host every iteration: not capturable
+            if args.graph and sv != B.SOLVER_BLOCK:
                 try:
                     cs_ = torch.cuda.Stream(dev)
                     cs_.wait_stream(stream)
@@ -465,6 +469,9 @@ def run_ours(args):
     }
     line.update(result)
     line.update(comparators)
+    if not args.no_config5:
+        # the 2-D workload on the BF16 tensor-core path, its own record (one warm-up, two timed analyses)
+        line["config5"] = config5_record(B, dev, steps=2, warmup=1, no_parity=args.no_parity)
     if learn_info:
         line["learned"] = learn_info
     if tune_info:
@@ -800,6 +807,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-config5", action="store_true", help="skip the 2-D BF16 record of the default line")
     ap.add_argument("--ritz", type=int, default=RITZ, help="Ritz rank of the preconditioner (config5)")
     ap.add_argument("--workload", default="config2", choices=["config2", "batched64", "config5", "tilemm"],
                     help="config2: the headline single analysis; batched64: 64 uneven problems in one batched "
