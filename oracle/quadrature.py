@@ -42,10 +42,37 @@ import numpy as np
 from scipy.special import ellipj, ellipk
 
 
+def _elliptic_rule_mp(Q: int, ell: float, digits: int = 40):
+    """The same rule with the elliptic functions evaluated by mpmath at `digits`
+    significant digits and the parameter m = ell / (1 + ell) formed exactly.
+    For large ell, m is within 1/ell of 1 and SciPy's double-precision
+    ellipk / ellipj lose digits (K off by about 3e-12 at ell = 1e6, 2e-10 at
+    1e8)."""
+    import mpmath
+    with mpmath.workdps(digits):
+        L = mpmath.mpf(ell)
+        m = L / (1 + L)
+        K = mpmath.ellipk(m)
+        s = np.empty(Q)
+        p = np.empty(Q)
+        for q in range(1, Q + 1):
+            u = (q - mpmath.mpf(1) / 2) / Q * K
+            sn, cn, dn = (mpmath.ellipfun(f, u, m=m) for f in ("sn", "cn", "dn"))
+            sq = (sn / cn) ** 2
+            rq = 2 / (mpmath.pi * Q) * K / cn * (dn / cn)
+            s[q - 1] = float(sq)
+            p[q - 1] = float(rq / (sq + 1))
+    return s, p
+
+
 def elliptic_rule(Q: int, ell: float):
-    """(s_q, p_q), q = 1..Q, of the elliptic rule (App. D) for spectrum bound ell."""
+    """(s_q, p_q), q = 1..Q, of the elliptic rule (App. D) for spectrum bound ell.
+    Above ell = 1e4 the elliptic functions are evaluated in extended precision
+    (_elliptic_rule_mp); below, SciPy's are accurate to rounding."""
     if Q < 1 or not ell > 0:
         raise ValueError("need Q >= 1 and ell > 0")
+    if ell > 1e4:
+        return _elliptic_rule_mp(Q, ell)
     g2 = 1.0 - 1.0 / (1.0 + ell)           # parameter m = g^2, g as printed in App. D
     K = ellipk(g2)
     t = (np.arange(1, Q + 1) - 0.5) / Q

@@ -104,3 +104,24 @@ def test_ell_rule_powers_of_ten():
     assert quadrature.ell_rule(np.zeros((3, 3))) == 10.0
     lam_max = np.linalg.eigvalsh(C)[-1]
     assert quadrature.ell_rule(C) > lam_max
+
+
+@pytest.mark.parametrize("Q,ell,bound", [(24, 1e6, 1e-11), (32, 1e8, 1e-11), (48, 1e10, 1e-12)])
+def test_elliptic_rule_at_large_ell_meets_the_identity(Q, ell, bound):
+    """Above ell = 1e4 the oracle evaluates the elliptic functions in extended precision; the rule must still
+    satisfy sum_q r_q / (s_q + c + 1) = (c + 1)^-1/2 over c in [0, ell] (Eq. generic_invsqrt_integral)."""
+    pytest.importorskip("mpmath")
+    s, p = quadrature.elliptic_rule(Q, ell)
+    r = p * (s + 1.0)
+    c = np.concatenate([[0.0], np.logspace(-4, math.log10(ell), 300)])
+    err = np.max(np.abs((r[None, :] / (s[None, :] + c[:, None] + 1.0)).sum(1) * np.sqrt(c + 1.0) - 1.0))
+    assert err < bound
+    assert np.all(np.diff(s) > 0) and np.all(p > 0)
+
+
+def test_extended_precision_rule_agrees_with_scipy_where_both_are_accurate():
+    pytest.importorskip("mpmath")
+    for Q, ell in ((16, 100.0), (32, 1e4)):
+        s1, p1 = quadrature._elliptic_rule_mp(Q, ell)
+        s2, p2 = quadrature.elliptic_rule(Q, ell)
+        assert np.max(np.abs(s1 / s2 - 1)) < 1e-12 and np.max(np.abs(p1 / p2 - 1)) < 1e-12
