@@ -134,6 +134,48 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_band_phases(args):
+    """Per-round phase cycles of the 1-D band PCG kernel on the headline workload (learned model trained as
+    in the default line, autotuned), from the instrumented build of the library (INFO_ESRF_PHASE_CLOCKS=1,
+    set before the library loads). The timed bench line never uses this build."""
+    os.environ["INFO_ESRF_PHASE_CLOCKS"] = "1"
+    import torch
+
+    from paper_2503_00253_gb300 import binding as B
+    from paper_2503_00253_gb300 import learned, workloads
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    B.library()
+    pr = workloads.config2()
+    X, obs, y, R = (torch.tensor(a, device=dev) for a in (pr.X, pr.obs_idx, pr.y, pr.R))
+    max_oo, max_xo = B.neighbor_counts(pr.grid, obs)
+    theta, cutoff = None, 0.0
+    if args.preconditioner == "learned":
+        train_set = [workloads.config2(tol=TOL_MIXED, seed=s) for s in TRAIN_SEEDS]
+        theta, cutoff, _ = learned.fit(train_set, K=12, members_per_q=3, steps=300)
+    opts = B.make_options(precision=B.PRECISION_FP32, ritz_rank=RITZ, max_neighbors=max(max_oo, max_xo),
+                          learned_model=theta, learned_max_shift=cutoff)
+    if args.autotune:
+        B.autotune([dict(grid=pr.grid, X=X, obs_idx=obs, y=y, R=R, Q=pr.Q, tol=TOL_MIXED, max_oo=max_oo,
+                         max_xo=max_xo)], opts)
+    st = None
+    for _ in range(args.warmup):
+        st = B.info_esrf_analysis(pr.grid, X, obs, y, R, pr.Q, TOL_MIXED, opts)[2]
+    torch.cuda.synchronize()
+    B.band_phase_clocks(reset=True)
+    for _ in range(args.steps):
+        B.info_esrf_analysis(pr.grid, X, obs, y, R, pr.Q, TOL_MIXED, opts)
+    torch.cuda.synchronize()
+    ph = B.band_phase_clocks(reset=True)
+    ph["launches"] = args.steps
+    ph["ctas"] //= args.steps
+    rec = {"workload": WORKLOAD, "kind": "band_phase_clocks", "preconditioner": args.preconditioner,
+           "cluster_size": int(opts.cluster_size), "solver_path": st["solver_path"] if st else None,
+           "iters_mean": st["iters_mean"] if st else None, **ph}
+    print(json.dumps(rec))
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -809,9 +851,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-config5", action="store_true", help="skip the 2-D BF16 record of the default line")
     ap.add_argument("--ritz", type=int, default=RITZ, help="Ritz rank of the preconditioner (config5)")
-    ap.add_argument("--workload", default="config2", choices=["config2", "batched64", "config5", "tilemm"],
+    ap.add_argument("--workload", default="config2",
+                    choices=["config2", "batched64", "config5", "tilemm", "band_phases"],
                     help="config2: the headline single analysis; batched64: 64 uneven problems in one batched "
-                         "call against 64 single calls")
+                         "call against 64 single calls; band_phases: per-round phase cycles of the band PCG "
+                         "kernel (instrumented build)")
     args = ap.parse_args()
     if args.warmup < 3 and args.workload != "config5":
         args.warmup = 3   # config5: one analysis takes seconds; --warmup as given (at least 1)
@@ -824,6 +868,8 @@ def main():
         run_config5(args)
     elif args.workload == "tilemm":
         run_tilemm(args)
+    elif args.workload == "band_phases":
+        run_band_phases(args)
     else:
         run_ours(args)
 

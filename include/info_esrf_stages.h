@@ -85,6 +85,21 @@ int64_t info_esrf_launch_count(void);
  * Writes the achieved FLOP/s (2 per FMA) and the kernel time in ms; synchronizes. */
 int info_esrf_fma_probe(int32_t precision, int64_t iters, double* flops_per_s, double* ms, void* stream);
 
+/* Per-phase clock counts of the cluster-resident 1-D band PCG kernel (the
+ * kernel of solver_path 1; App. E, one PCG iteration per round), for a
+ * separate build of the library compiled with -DINFO_ESRF_PHASE_CLOCKS (the
+ * default build returns INFO_ESRF_ERR_UNSUPPORTED).  Thread 0 of every CTA
+ * sums clock64() deltas per phase over the launches since the last reset:
+ * out[0..9] the cycles of the ten phases of a round (0 band matvec, 1 p^T y
+ * push and cluster barrier 1, 2 alpha and right-hand-side prefetch wait,
+ * 3 residual update and its dot products, 4 learned term, 5 reductions push
+ * and cluster barrier 2, 6 CG and preconditioner scalars, 7 direction update,
+ * 8 queue, halo push and cluster barrier 3, 9 refills), out[10] rounds,
+ * out[11] set-up cycles, out[12] CTAs, each summed over CTAs; n values are
+ * written (at most 13).  reset != 0 zeroes the counters afterwards.
+ * Synchronizes the device. */
+int info_esrf_band_phase_clocks(int64_t* out, int32_t n, int32_t reset);
+
 /* Band capacities the workspace layout uses for these arguments. */
 int info_esrf_prepared_band_capacity(const info_esrf_grid* grid, int64_t N, int64_t d, int32_t Q,
                                      const info_esrf_options* opt, int64_t* max_oo, int64_t* max_xo);

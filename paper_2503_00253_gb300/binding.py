@@ -83,13 +83,16 @@ _LIB = None
 
 
 def library() -> ctypes.CDLL:
-    """Loads libinfo_esrf.so (building it first if sources are newer)."""
+    """Loads libinfo_esrf.so (building it first if sources are newer); with
+    INFO_ESRF_PHASE_CLOCKS=1 in the environment, the instrumented build
+    libinfo_esrf_phase.so instead."""
     global _LIB
     if _LIB is not None:
         return _LIB
-    path = _build.library_path()
-    if not _build.up_to_date():
-        path = _build.build()
+    phase = os.environ.get("INFO_ESRF_PHASE_CLOCKS") == "1"
+    path = _build.library_path(phase)
+    if not _build.up_to_date(phase):
+        path = _build.build(phase_clocks=phase)
     if not os.path.exists(path):
         raise RuntimeError(f"CUDA library {path} is missing; run build() first")
     lib = ctypes.CDLL(path)
@@ -151,6 +154,7 @@ def library() -> ctypes.CDLL:
         "info_esrf_fma_probe": (c_int32, [c_int32, c_int64, P(c_double), P(c_double), c_void_p]),
         "info_esrf_prepared_band_capacity": (c_int32, [P(Grid), c_int64, c_int64, c_int32, P(Options),
                                                        P(c_int64), P(c_int64)]),
+        "info_esrf_band_phase_clocks": (c_int32, [P(c_int64), c_int32, c_int32]),
         "info_esrf_bf16_tile_matvec": (c_int32, [c_int32, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_int32,
                                                  c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     }
@@ -243,6 +247,24 @@ def set_phase_events(options: Options, events) -> None:
 
 def launch_count() -> int:
     return int(library().info_esrf_launch_count())
+
+
+BAND_PHASES = ("band matvec", "p^T y push + cluster barrier 1", "alpha, RHS prefetch wait",
+               "residual update, Phi^T r, A^T r", "learned term (r halo push, barrier 2a, T r)",
+               "reductions push + cluster barrier 2", "decisions (CG scalars, LMP algebra)",
+               "direction update z, p", "queue, halo push, cluster barrier 3", "refills, RHS prefetch issue")
+
+
+def band_phase_clocks(reset: bool = True) -> dict:
+    """Per-round phase cycles of the 1-D band PCG kernel since the last reset
+    (instrumented build only: INFO_ESRF_PHASE_CLOCKS=1), averaged over CTAs."""
+    out = (c_int64 * 13)()
+    _check(library().info_esrf_band_phase_clocks(out, 13, 1 if reset else 0), "info_esrf_band_phase_clocks")
+    v = list(out)
+    rounds, ctas = v[10], max(v[12], 1)
+    per_round = {name: v[i] / max(rounds, 1) for i, name in enumerate(BAND_PHASES)}
+    return {"cycles_per_round": per_round, "rounds_per_cta": rounds / ctas, "setup_cycles_per_cta": v[11] / ctas,
+            "ctas": v[12], "total_per_round": sum(v[:10]) / max(rounds, 1)}
 
 
 def fma_probe(precision: int, iters: int, stream=None):

@@ -4,6 +4,13 @@ Compiles every ``csrc/*.cu`` translation unit in parallel with nvcc and links
 them into ``paper_2503_00253_gb300/lib/libinfo_esrf.so``.  No PyTorch is
 involved; the library's C ABI is declared in ``include/info_esrf.h`` and
 ``include/info_esrf_stages.h``.
+
+``build(phase_clocks=True)`` makes a second, instrumented library,
+``libinfo_esrf_phase.so`` (objects in ``lib/obj_phase``), compiled with
+``-DINFO_ESRF_PHASE_CLOCKS``: the 1-D band PCG kernel then records clock
+counts per phase of each round (``info_esrf_band_phase_clocks``).  The
+binding loads it instead of the default library when the environment has
+``INFO_ESRF_PHASE_CLOCKS=1``.
 """
 from __future__ import annotations
 
@@ -19,11 +26,12 @@ INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(PKG, "lib")
 OBJDIR = os.path.join(LIBDIR, "obj")
 LIBNAME = "libinfo_esrf.so"
+PHASE_LIBNAME = "libinfo_esrf_phase.so"
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
-def library_path() -> str:
-    return os.path.join(LIBDIR, LIBNAME)
+def library_path(phase_clocks: bool = False) -> str:
+    return os.path.join(LIBDIR, PHASE_LIBNAME if phase_clocks else LIBNAME)
 
 
 def _nvcc() -> str:
@@ -44,26 +52,29 @@ def _deps():
     return files
 
 
-def up_to_date() -> bool:
-    lib = library_path()
+def up_to_date(phase_clocks: bool = False) -> bool:
+    lib = library_path(phase_clocks)
     if not os.path.exists(lib):
         return False
     t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, phase_clocks: bool = False) -> str:
     """Compiles and links the library if any source is newer; returns its path."""
-    if not force and up_to_date():
-        return library_path()
-    os.makedirs(OBJDIR, exist_ok=True)
+    if not force and up_to_date(phase_clocks):
+        return library_path(phase_clocks)
+    objdir = os.path.join(LIBDIR, "obj_phase") if phase_clocks else OBJDIR
+    os.makedirs(objdir, exist_ok=True)
     nvcc = _nvcc()
     flags = [ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
              "-I" + INCLUDE, "-I" + CSRC, "--expt-relaxed-constexpr"]
+    if phase_clocks:
+        flags.append("-DINFO_ESRF_PHASE_CLOCKS")
     procs = []
     objs = []
     for src in _sources():
-        obj = os.path.join(OBJDIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         cmd = [nvcc] + flags + ["-c", src, "-o", obj]
         if verbose:
@@ -79,12 +90,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if failed:
         msg = "\n".join(f"{s}:\n{o}" for s, o in failed)
         raise RuntimeError(f"nvcc failed:\n{msg}")
-    tmp = library_path() + ".tmp"
+    tmp = library_path(phase_clocks) + ".tmp"
     cmd = [nvcc, "-shared", ARCH, "-o", tmp] + objs
     subprocess.run(cmd, check=True, capture_output=not verbose)
-    os.replace(tmp, library_path())
-    return library_path()
+    os.replace(tmp, library_path(phase_clocks))
+    return library_path(phase_clocks)
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, phase_clocks="--phase-clocks" in sys.argv))

@@ -41,6 +41,8 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "info_esrf.h"
+#include "info_esrf_stages.h"
 #include "internal.h"
 
 namespace cg = cooperative_groups;
@@ -58,15 +60,33 @@ constexpr int kNR = 4 + 2 * kK; // residual reduction values per lane: rr (hi, l
 constexpr int kRetry = 1 << 30; // queue id flag: solve this system again without the learned term
 constexpr int kTH = 2 * kLearnH;          // half-width of T = S^T S (autocorrelation of the taps)
 constexpr int kTT = 2 * kTH + 1;          // taps of T
-constexpr int kTrRows = 4;                // rows per thread for which T r is kept in registers
+constexpr int kStRows = 16;               // own rows per warp in the learned stencil (kNW kStRows >= R_s)
 constexpr int kMaxTiles = 128;  // rows per CTA <= 2048
 constexpr int kMaxCS = 8;       // CTAs per cluster
+constexpr int kQTab = 65;       // shift slots (Q + 1) whose lane scalars are staged in shared memory
 
 enum : int { kEmpty = 0, kStart = 1, kActive = 2 };
 
+// Phase clocks (built only with -DINFO_ESRF_PHASE_CLOCKS, a separate build of
+// the library): thread 0 of every CTA sums clock64() deltas per phase of a
+// round in shared memory and adds them, with the round count and its set-up
+// cycles, into g_band_phase at exit; info_esrf_band_phase_clocks reads them.
+constexpr int kPhases = 10;
+[[maybe_unused]] constexpr int kPhaseSlots = kPhases + 3;   // phases, rounds, set-up cycles, CTAs
+#ifdef INFO_ESRF_PHASE_CLOCKS
+#define BAND_PHASE(i)                 \
+  if (tid == 0) {                     \
+    const long long now_ = clock64(); \
+    s_ph[i] += now_ - ph_t;           \
+    ph_t = now_;                      \
+  }
+#else
+#define BAND_PHASE(i)
+#endif
+
 struct LaneState {
   int sid[kJ], state[kJ], it[kJ], newsid[kJ], fin[kJ];
-  double sigma[kJ];
+  int qs[kJ];                         // coefficient slot of the learned term (q, Q: mean), -1: none
   float rho[kJ];                      // r^T M r of the current iterate
   float rrh[kJ], rrl[kJ];             // r^T r as a float-float pair (FP64-accurate)
   float bn2[kJ];                      // b^T b
@@ -143,6 +163,10 @@ __device__ __forceinline__ void pow2_scale(float m, float& scale, float& inv) {
   }
 }
 
+#ifdef INFO_ESRF_PHASE_CLOCKS
+__device__ unsigned long long g_band_phase[kPhaseSlots];
+#endif
+
 }  // namespace
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -166,6 +190,11 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
   const int crank = (int)cluster.block_rank();
   const int cl_id = blockIdx.x / CS;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#ifdef INFO_ESRF_PHASE_CLOCKS
+  __shared__ long long s_ph[kPhaseSlots];
+  long long ph_t = clock64();
+  if (tid < kPhaseSlots) s_ph[tid] = 0;
+#endif
   const ProblemDev& pr = tab[0];
   const int64_t d = pr.d, N = pr.N;
   const int k = pr.kR < kK ? pr.kR : kK;
@@ -274,7 +303,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
   };
   auto for_each_push = [&](auto&& f) { for_each_push_w(hl, hr, f); };
   // learned term: T r needs r on a window of +-kTH rows around the own rows
-  const bool learn_ok = pr.learned_model != nullptr && R_s <= 32 * kTrRows;
+  const bool learn_ok = pr.learned_model != nullptr && R_s <= kNW * kStRows;
   if (tid == 0) { S.npush = 0; S.nrpush = 0; }
   __syncthreads();
   {
@@ -311,12 +340,12 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
   }
   if (cl_id == 0 && crank == 0 && tid == 0) atomicOr(&pr.status[1], 1);
   float* Ct = dyn;
-  float* pw = dyn + o_pw;
-  float* vr = dyn + o_r;
-  float* vx = dyn + o_x;
-  float* vy = dyn + o_y;
-  float* phT = dyn + o_ph;
-  float* aT = dyn + o_at;
+  float* __restrict__ pw = dyn + o_pw;   // the six vector regions are disjoint
+  float* __restrict__ vr = dyn + o_r;
+  float* __restrict__ vx = dyn + o_x;
+  float* __restrict__ vy = dyn + o_y;
+  float* __restrict__ phT = dyn + o_ph;
+  float* __restrict__ aT = dyn + o_at;
   int2* push = reinterpret_cast<int2*>(dyn + o_push);
   int2* rpush = reinterpret_cast<int2*>(dyn + o_rpush);
   float* s_rinv = dyn + o_rinv;
@@ -390,7 +419,22 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
   const int maxit = pr.fixed_iters > 0 ? pr.fixed_iters : pr.max_iter;
   const float tol2f = (float)(pr.tol * pr.tol);
 
-  // Starts system sid in lane j on the own rows (r = b, x = 0; p own rows are 0).
+  // Per-shift lane scalars, staged once: sigma = s_q + 1 as FP32, the
+  // preconditioner's beta - sigma (App. E) and the learned scale a_q (> 0 when
+  // the term applies to shift q); slot Q is the mean system (sigma = 1).
+  __shared__ float s_qsigf[kQTab], s_qbmf[kQTab], s_qla[kQTab];
+  const bool qtab = pr.Q + 1 <= kQTab;
+  auto shift_scalars = [&](int qs, float& sgf, float& bmf, float& la0) {
+    const double sg = qs >= pr.Q ? 1.0 : pr.s[qs] + 1.0;
+    sgf = (float)sg;
+    bmf = (float)(sg + cmin) - sgf;
+    la0 = pr.learn_coef[(int64_t)qs * kLearnOut];
+  };
+  if (qtab)
+    for (int qs = tid; qs <= pr.Q; qs += blockDim.x) shift_scalars(qs, s_qsigf[qs], s_qbmf[qs], s_qla[qs]);
+  __syncthreads();
+  // Starts system sid in lane j (scalars; the taps of the learned term follow
+  // with the lane's right-hand side in lane_vectors_all).
   auto lane_scalars = [&](int j, int code) {
     const bool retry = code >= kRetry;
     const int sid = retry ? code - kRetry : code;
@@ -398,26 +442,32 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
     L.fin[j] = 0;
     L.learn[j] = 0;
     L.la[j] = 1.f;
-    for (int u = 0; u < kTT; ++u) L.ltT[u][j] = 0.f;
+    L.qs[j] = -1;
     L.mem[j] = -1;
+    float sgf = 1.f, bmf = (float)(1.0 + cmin) - 1.f;
     if (sid < 0) {
       L.state[j] = kEmpty;
-      L.sigma[j] = 1.0;
     } else {
       L.state[j] = kStart;
-      const int q = sid < pr.mean_sys ? -1 : (int)((sid - pr.mean_sys) / N);
-      if (q >= 0) L.mem[j] = (int)((sid - pr.mean_sys) % N);
-      L.sigma[j] = q < 0 ? 1.0 : pr.s[q] + 1.0;
-      const float* cf = pr.learn_coef + (int64_t)(q < 0 ? pr.Q : q) * kLearnOut;
-      if (learn_ok && !retry && cf[0] > 0.f) {
+      const int q = sid < pr.mean_sys ? -1 : (sid - pr.mean_sys) / (int)N;
+      if (q >= 0) L.mem[j] = sid - pr.mean_sys - q * (int)N;
+      const int qs = q < 0 ? pr.Q : q;
+      float la0;
+      if (qtab) {
+        sgf = s_qsigf[qs];
+        bmf = s_qbmf[qs];
+        la0 = s_qla[qs];
+      } else {
+        shift_scalars(qs, sgf, bmf, la0);
+      }
+      if (learn_ok && !retry && la0 > 0.f) {
         L.learn[j] = 1;
-        L.la[j] = cf[0];
-        const float* tT = pr.learn_T + (int64_t)(q < 0 ? pr.Q : q) * kLearnT;   // taps of S^T S
-        for (int u = 0; u < kTT; ++u) L.ltT[u][j] = tT[u];
+        L.la[j] = la0;
+        L.qs[j] = qs;
       }
     }
-    L.sigf[j] = (float)L.sigma[j];
-    L.bmf[j] = (float)(L.sigma[j] + cmin) - L.sigf[j];
+    L.sigf[j] = sgf;
+    L.bmf[j] = bmf;
     L.it[j] = 0;
     L.alpha[j] = 0.f;
     L.beta[j] = 0.f;
@@ -427,17 +477,24 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
   // member's observed anomalies by asynchronous copies that complete during the
   // matvec; the residual step scales them by R^-1/2 (the mean system's
   // right-hand side, already scaled, is stored directly).
-  __shared__ int s_start[kJ], s_nstart, s_live;
-  auto lane_masks = [&]() {           // warp 0: which lanes are live / just started
+  __shared__ int s_start[kJ], s_nstart, s_live, s_anyl;
+  auto lane_masks = [&]() {           // warp 0: which lanes are live / just started / use the learned term
     if (tid < kJ) {
       const unsigned lm = __ballot_sync(0xffffffffu, L.state[tid] != kEmpty);
       const unsigned sm = __ballot_sync(0xffffffffu, L.state[tid] == kStart);
+      const unsigned ll = __ballot_sync(0xffffffffu, L.learn[tid] != 0);
       if (sm & (1u << tid)) s_start[__popc(sm & ((1u << tid) - 1u))] = tid;
-      if (tid == 0) { s_live = lm != 0u; s_nstart = __popc(sm); }
+      if (tid == 0) { s_live = lm != 0u; s_nstart = __popc(sm); s_anyl = ll != 0u; }
     }
   };
   auto lane_vectors_all = [&]() {
     const int ns = s_nstart;
+    // taps of T = S^T S of the started lanes (zero without the learned term)
+    for (int e = tid; e < ns * kTT; e += blockDim.x) {
+      const int j = s_start[e / kTT], u = e % kTT, qs = L.qs[j];
+      if (qs >= 0) cp_async4(&L.ltT[u][j], pr.learn_T + (int64_t)qs * kLearnT + u);
+      else L.ltT[u][j] = 0.f;
+    }
     for (int e = tid; e < R_s * ns; e += blockDim.x) {
       const int row = e / ns, j = s_start[e % ns];
       float* dst = vr + row * kLD + j;
@@ -465,6 +522,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
   __syncthreads();
   lane_vectors_all();
   cluster.sync();   // all CTAs initialized before anyone pushes into their windows
+  BAND_PHASE(kPhases + 1);
 
   for (;;) {
     // ---------------- A: y = sigma p + C p on the own rows, partial p^T y ----------------
@@ -554,6 +612,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       s_wpap[warp][8 * q + g][0] = vh[0];
       s_wpap[warp][8 * q + g][1] = vl[0];
     }
+    BAND_PHASE(0);
     __syncthreads();
     if (tid < (kJ / 2) * CS) {   // two lanes per thread: one 16-byte store per destination
       const int j = 2 * (tid % (kJ / 2)), dst = tid / (kJ / 2);
@@ -565,6 +624,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       st4(cluster.map_shared_rank(&s_pap_in[crank][j][0], dst), make_float4(h0, l0, h1, l1));
     }
     cluster.sync();   // (1)
+    BAND_PHASE(1);
     // ---------------- alpha ----------------
     if (tid < kJ) {
       const int j = tid;
@@ -584,8 +644,8 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
     }
     cp_async_wait_all();   // right-hand sides of lanes started in the previous step
     __syncthreads();
+    BAND_PHASE(2);
     // ---------------- x += alpha p, r -= alpha y; partial rr, Phi^T r, A^T r ----------------
-    float4 trr[kTrRows];   // (T r) of this thread's rows and its warp's four lanes (learned term)
     {
       const int j0 = 4 * warp;   // this warp's four lanes
       const float a0 = L.alpha[j0], a1 = L.alpha[j0 + 1], a2 = L.alpha[j0 + 2], a3 = L.alpha[j0 + 3];
@@ -601,85 +661,67 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
 #pragma unroll
       for (int jj = 0; jj < 4; ++jj) sc[jj] = L.state[j0 + jj] == kStart && L.mem[j0 + jj] >= 0;
       const bool any_sc = sc[0] | sc[1] | sc[2] | sc[3];
-      for (int row = lane; row < nrows; row += 32) {
-        const float4 p4 = ld4(pw + (row + hl) * kLD + j0);
-        const float4 y4 = ld4(vy + (row + kTH) * kLD + j0);
-        float4 x4 = ld4(vx + row * kLD + j0);
-        float4 r4 = ld4(vr + row * kLD + j0);
+      // two rows (row, row + 32) per iteration, every shared-memory load of
+      // both issued before their arithmetic; sums run in row order
+      const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int row = lane; row < nrows; row += 64) {
+        const int rb = row + 32;
+        const bool hb = rb < nrows;
+        const float4 p4a = ld4(pw + (row + hl) * kLD + j0), y4a = ld4(vy + (row + kTH) * kLD + j0);
+        const float4 x4a = ld4(vx + row * kLD + j0), r4a0 = ld4(vr + row * kLD + j0);
+        const float4 p4b = hb ? ld4(pw + (rb + hl) * kLD + j0) : zero4;
+        const float4 y4b = hb ? ld4(vy + (rb + kTH) * kLD + j0) : zero4;
+        const float4 x4b = hb ? ld4(vx + rb * kLD + j0) : zero4, r4b0 = hb ? ld4(vr + rb * kLD + j0) : zero4;
+        float ra[4] = {r4a0.x, r4a0.y, r4a0.z, r4a0.w}, rb4[4] = {r4b0.x, r4b0.y, r4b0.z, r4b0.w};
         if (any_sc) {                                   // b = R^-1/2 w of a lane started last step
-          const float ri = s_rinv[row];
-          if (sc[0]) r4.x *= ri;
-          if (sc[1]) r4.y *= ri;
-          if (sc[2]) r4.z *= ri;
-          if (sc[3]) r4.w *= ri;
+          const float ria = s_rinv[row], rib = hb ? s_rinv[rb] : 0.f;
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj)
+            if (sc[jj]) { ra[jj] *= ria; rb4[jj] *= rib; }
         }
-        x4.x = fmaf(a0, p4.x, x4.x); x4.y = fmaf(a1, p4.y, x4.y);
-        x4.z = fmaf(a2, p4.z, x4.z); x4.w = fmaf(a3, p4.w, x4.w);
-        r4.x = fmaf(-a0, y4.x, r4.x); r4.y = fmaf(-a1, y4.y, r4.y);
-        r4.z = fmaf(-a2, y4.z, r4.z); r4.w = fmaf(-a3, y4.w, r4.w);
-        st4(vx + row * kLD + j0, x4);
-        st4(vr + row * kLD + j0, r4);
-        st4(vy + (row + kTH) * kLD + j0, r4);     // r window (y is no longer needed)
-        rr[0].add_prod(r4.x, r4.x); rr[1].add_prod(r4.y, r4.y);
-        rr[2].add_prod(r4.z, r4.z); rr[3].add_prod(r4.w, r4.w);
-        const float rv[4] = {r4.x, r4.y, r4.z, r4.w};
+        const float al[4] = {a0, a1, a2, a3};
+        const float pa[4] = {p4a.x, p4a.y, p4a.z, p4a.w}, pb[4] = {p4b.x, p4b.y, p4b.z, p4b.w};
+        const float ya[4] = {y4a.x, y4a.y, y4a.z, y4a.w}, yb[4] = {y4b.x, y4b.y, y4b.z, y4b.w};
+        float xa[4] = {x4a.x, x4a.y, x4a.z, x4a.w}, xb[4] = {x4b.x, x4b.y, x4b.z, x4b.w};
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          xa[jj] = fmaf(al[jj], pa[jj], xa[jj]);
+          xb[jj] = fmaf(al[jj], pb[jj], xb[jj]);
+          ra[jj] = fmaf(-al[jj], ya[jj], ra[jj]);
+          rb4[jj] = fmaf(-al[jj], yb[jj], rb4[jj]);
+        }
+        const float4 r4a = make_float4(ra[0], ra[1], ra[2], ra[3]), r4b = make_float4(rb4[0], rb4[1], rb4[2], rb4[3]);
+        st4(vx + row * kLD + j0, make_float4(xa[0], xa[1], xa[2], xa[3]));
+        st4(vr + row * kLD + j0, r4a);
+        st4(vy + (row + kTH) * kLD + j0, r4a);     // r window (y is no longer needed)
+        if (hb) {
+          st4(vx + rb * kLD + j0, make_float4(xb[0], xb[1], xb[2], xb[3]));
+          st4(vr + rb * kLD + j0, r4b);
+          st4(vy + (rb + kTH) * kLD + j0, r4b);
+        }
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          rr[jj].add_prod(ra[jj], ra[jj]);
+          rr[jj].add_prod(rb4[jj], rb4[jj]);   // zero for a missing second row
+        }
 #pragma unroll
         for (int m = 0; m < kK; ++m) {
           if (m < k) {
-            const float ph = phT[m * R_s + row], at = aT[m * R_s + row];
+            const float pha = phT[m * R_s + row], ata = aT[m * R_s + row];
+            const float phb = hb ? phT[m * R_s + rb] : 0.f, atb = hb ? aT[m * R_s + rb] : 0.f;
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj) {
               const int idx = jj * 2 * kK + m, idg = idx + kK;
               float& vf = idx < 32 ? v0[idx] : idx < 64 ? v1[idx - 32] : v2[idx - 64];
-              vf = fmaf(ph, rv[jj], vf);
+              vf = fmaf(phb, rb4[jj], fmaf(pha, ra[jj], vf));
               float& vg = idg < 32 ? v0[idg] : idg < 64 ? v1[idg - 32] : v2[idg - 64];
-              vg = fmaf(at, rv[jj], vg);
+              vg = fmaf(atb, rb4[jj], fmaf(ata, ra[jj], vg));
             }
           }
         }
       }
-      // learned term, applied periodically across the slices: the halo rows
-      // of the r window come from their owners, then T r = S^T S r on the own
-      // rows stays in registers until the direction update
-      DotAcc<float> uu[4];
-      bool any_learn = false;
-      if (learn_ok) {
-        __syncthreads();
-        const int nrp = s_nrpush;
-        for (int e = tid; e < nrp * (kJ / 4); e += blockDim.x) {
-          const int2 t = rpush[e / (kJ / 4)];
-          const int q4 = e % (kJ / 4);
-          const int row = t.x & 0xffff, c2 = t.x >> 16;
-          st4(cluster.map_shared_rank(vy, c2) + t.y * kLD + 4 * q4, ld4(vy + (row + kTH) * kLD + 4 * q4));
-        }
-        cluster.sync();   // (2a) r windows complete
-        any_learn = L.learn[j0] | L.learn[j0 + 1] | L.learn[j0 + 2] | L.learn[j0 + 3];
-        if (any_learn) {
-          // rows lane + 32 ii (all inside the r window, which spans R_s + 2 kTH rows)
-#pragma unroll
-          for (int ii = 0; ii < kTrRows; ++ii) trr[ii] = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 3
-          for (int tp = 0; tp < kTT; ++tp) {
-            const float4 w4 = ld4(&L.ltT[tp][j0]);
-#pragma unroll
-            for (int ii = 0; ii < kTrRows; ++ii) {
-              const float4 r4 = ld4(vy + (lane + 32 * ii + tp) * kLD + j0);   // r[row + tp - kTH]
-              trr[ii].x = fmaf(w4.x, r4.x, trr[ii].x);
-              trr[ii].y = fmaf(w4.y, r4.y, trr[ii].y);
-              trr[ii].z = fmaf(w4.z, r4.z, trr[ii].z);
-              trr[ii].w = fmaf(w4.w, r4.w, trr[ii].w);
-            }
-          }
-#pragma unroll
-          for (int ii = 0; ii < kTrRows; ++ii) {
-            if (lane + 32 * ii < nrows) {
-              const float4 r4 = ld4(vy + (lane + 32 * ii + kTH) * kLD + j0);
-              uu[0].add_prod(r4.x, trr[ii].x); uu[1].add_prod(r4.y, trr[ii].y);
-              uu[2].add_prod(r4.z, trr[ii].z); uu[3].add_prod(r4.w, trr[ii].w);
-            }
-          }
-        }
-      }
+      // the warp's partial Phi^T r and A^T r are reduced first, which frees
+      // their 80 registers before the learned term's stencil
       const float s0v = warp_reduce_scatter32<float>(v0, lane);
       const float s1v = warp_reduce_scatter32<float>(v1, lane);
       // 16-value block: fold the warp halves, then reduce-scatter over 16 lanes
@@ -696,19 +738,16 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
         }
       }
       const float sv[3] = {s0v, s1v, v2[0]};
-      // r^T r and r^T T r of the four lanes: eight float-float values,
-      // reduce-scattered over the lane bits 4, 3, 2 and summed over bits 1, 0;
-      // lane L ends with value v = 4 b4 + 2 b3 + b2 (v < 4: r^T r of lane j0 + v,
-      // v >= 4: r^T T r of lane j0 + v - 4)
-      float vh[8], vl[8];
+      // r^T r of the four lanes: four float-float values reduce-scattered over
+      // the lane bits 4, 3 and summed over bits 2, 1, 0; lane L ends with r^T r
+      // of lane j0 + qj, qj = 2 b4 + b3.  Lanes with bit 2 set carry r^T T r
+      // of the same lane instead (learned term, below).
+      float vh[4], vl[4];
 #pragma unroll
-      for (int jj = 0; jj < 4; ++jj) {
-        vh[jj] = rr[jj].hi; vl[jj] = rr[jj].lo;
-        vh[4 + jj] = uu[jj].hi; vl[4 + jj] = uu[jj].lo;
-      }
+      for (int jj = 0; jj < 4; ++jj) { vh[jj] = rr[jj].hi; vl[jj] = rr[jj].lo; }
 #pragma unroll
-      for (int lev = 0; lev < 3; ++lev) {
-        const int off = 16 >> lev, half = 4 >> lev;
+      for (int lev = 0; lev < 2; ++lev) {
+        const int off = 16 >> lev, half = 2 >> lev;
         const bool up = (lane & off) != 0;
 #pragma unroll
         for (int i = 0; i < half; ++i) {
@@ -721,13 +760,68 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       }
       float qh = vh[0], ql = vl[0];
 #pragma unroll
-      for (int o = 2; o > 0; o >>= 1) {
+      for (int o = 4; o > 0; o >>= 1) {
         const float h2 = __shfl_xor_sync(0xffffffffu, qh, o);
         const float l2 = __shfl_xor_sync(0xffffffffu, ql, o);
         ff_merge(qh, ql, h2, l2);
       }
-      const int qv = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-      const int qdst = (j0 + (qv & 3)) * kNR + (qv < 4 ? 0 : 2);
+      const int qj = ((lane >> 4) & 1) * 2 + ((lane >> 3) & 1);
+      const bool q_uu = (lane & 4) != 0;
+      if (q_uu) { qh = 0.f; ql = 0.f; }
+      // learned term, applied periodically across the slices: the halo rows of
+      // the r window come from their owners, then T r = S^T S r replaces r on
+      // the own rows of the window, where the direction update reads it
+      BAND_PHASE(3);
+      if (s_anyl) {
+        __syncthreads();
+        const int nrp = s_nrpush;
+        for (int e = tid; e < nrp * (kJ / 4); e += blockDim.x) {
+          const int2 t = rpush[e / (kJ / 4)];
+          const int q4 = e % (kJ / 4);
+          const int row = t.x & 0xffff, c2 = t.x >> 16;
+          st4(cluster.map_shared_rank(vy, c2) + t.y * kLD + 4 * q4, ld4(vy + (row + kTH) * kLD + 4 * q4));
+        }
+        cluster.sync();   // (2a) r windows complete
+        // thread = (system lane `lane`, own rows kStRows warp ..): the
+        // kStRows + 2 kTH rows of its window are read once into registers,
+        // one conflict-free wavefront per row for the warp (lanes without the
+        // term have zero taps and produce zeros)
+        const int jl = lane, r0 = kStRows * warp;
+        DotAcc<float> ua;
+        float tr[kStRows];
+        if (r0 < R_s) {
+          float tap[kTT], win[kStRows + 2 * kTH];
+#pragma unroll
+          for (int tp = 0; tp < kTT; ++tp) tap[tp] = L.ltT[tp][jl];
+#pragma unroll
+          for (int i = 0; i < kStRows + 2 * kTH; ++i)
+            win[i] = r0 + i < R_s + 2 * kTH ? vy[(r0 + i) * kLD + jl] : 0.f;
+#pragma unroll
+          for (int o = 0; o < kStRows; ++o) {
+            float acc = 0.f;
+#pragma unroll
+            for (int tp = 0; tp < kTT; ++tp) acc = fmaf(tap[tp], win[o + tp], acc);   // r[row + tp - kTH]
+            tr[o] = acc;
+            if (r0 + o < nrows) ua.add_prod(win[o + kTH], acc);
+          }
+        }
+        s_wpap[warp][jl][0] = ua.hi;   // p^T y partials were consumed by alpha
+        s_wpap[warp][jl][1] = ua.lo;
+        __syncthreads();   // every window read
+        if (r0 < R_s) {
+#pragma unroll
+          for (int o = 0; o < kStRows; ++o)
+            if (r0 + o < R_s) vy[(r0 + o + kTH) * kLD + jl] = tr[o];
+        }
+        if (q_uu) {
+          float uh = 0.f, ul = 0.f;
+          for (int w = 0; w < kNW; ++w) ff_merge(uh, ul, s_wpap[w][j0 + qj][0], s_wpap[w][j0 + qj][1]);
+          qh = uh;
+          ql = ul;
+        }
+      }
+      BAND_PHASE(4);
+      const int qdst = (j0 + qj) * kNR + (q_uu ? 2 : 0);
       // push this warp's four lanes to every CTA of the cluster.  Distributed
       // shared-memory stores are separate transactions, so lanes 4 k gather
       // values 4 k .. 4 k + 3 of each block and store them as one 16-byte word
@@ -753,6 +847,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       }
     }
     cluster.sync();   // (2)
+    BAND_PHASE(5);
     // ---------------- decisions, then z = P^-1 r and p = z + beta p ----------------
     // Each warp handles its four lanes (the lanes of the residual step), so no
     // block barrier is needed until the queue.  Sums over the cluster are taken
@@ -761,44 +856,60 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
     // c = (beta - sigma) t - T^-1 t2, with G_q = (C_q Phi)^T (C_q Phi).
     {
       const int j0 = 4 * warp;
-      const int m = lane & 15;
-      const bool mv = m < k;
-#pragma unroll
-      for (int pass = 0; pass < 2; ++pass) {
-        const int j = j0 + 2 * pass + (lane >> 4);
+      static_assert(kK <= 16, "two Ritz indices per thread");
+      {
+        // eight threads per lane: thread m0 = lane % 8 of lane j holds Ritz
+        // indices m0 and m0 + 8
+        const int j = j0 + (lane >> 3);
+        const int mA = lane & 7, mB = mA + 8;
+        const bool vA = mA < k, vB = mB < k;
         // pairwise (tree) sums over the cluster's partials, the same order in every CTA
-        float fc[kMaxCS], gc[kMaxCS];
+        float fa[kMaxCS], ga[kMaxCS], fb[kMaxCS], gb[kMaxCS];
 #pragma unroll
         for (int c = 0; c < kMaxCS; ++c) {
-          fc[c] = (mv && c < CS) ? s_res_in[c][j][4 + m] : 0.f;
-          gc[c] = (mv && c < CS) ? s_res_in[c][j][4 + kK + m] : 0.f;
+          fa[c] = (vA && c < CS) ? s_res_in[c][j][4 + mA] : 0.f;
+          ga[c] = (vA && c < CS) ? s_res_in[c][j][4 + kK + mA] : 0.f;
+          fb[c] = (vB && c < CS) ? s_res_in[c][j][4 + mB] : 0.f;
+          gb[c] = (vB && c < CS) ? s_res_in[c][j][4 + kK + mB] : 0.f;
         }
 #pragma unroll
         for (int w2 = 1; w2 < kMaxCS; w2 <<= 1)
 #pragma unroll
-          for (int c = 0; c + w2 < kMaxCS; c += 2 * w2) { fc[c] += fc[c + w2]; gc[c] += gc[c + w2]; }
-        const float f = fc[0], g = gc[0];
+          for (int c = 0; c + w2 < kMaxCS; c += 2 * w2) {
+            fa[c] += fa[c + w2];
+            ga[c] += ga[c + w2];
+            fb[c] += fb[c + w2];
+            gb[c] += gb[c + w2];
+          }
         const float sg = L.sigf[j];
-        const float rth = mv ? __frcp_rn(s_theta[m] + sg) : 0.f;   // (T_q)^-1 entry
-        const float t = f * rth;
-        float t2 = g + sg * f;
+        const float rthA = vA ? __frcp_rn(s_theta[mA] + sg) : 0.f;   // (T_q)^-1 entries
+        const float rthB = vB ? __frcp_rn(s_theta[mB] + sg) : 0.f;
+        const float tA = fa[0] * rthA, tB = fb[0] * rthB;
+        float t2A = ga[0] + sg * fa[0], t2B = gb[0] + sg * fb[0];
+        auto gq = [&](int mm, int i) {   // (G_q)_{mm i}
+          return s_gram[2][mm * k + i] + sg * (s_gram[1][mm * k + i] + s_gram[1][i * k + mm]) +
+                 sg * sg * s_gram[0][mm * k + i];
+        };
 #pragma unroll
         for (int i = 0; i < kK; ++i) {
-          const float ti = __shfl_sync(0xffffffffu, t, (lane & 16) + i);
-          if (mv && i < k) {
-            const float G = s_gram[2][m * k + i] + sg * (s_gram[1][m * k + i] + s_gram[1][i * k + m]) +
-                            sg * sg * s_gram[0][m * k + i];
-            t2 = fmaf(-G, ti, t2);
+          const float ti = __shfl_sync(0xffffffffu, i < 8 ? tA : tB, (lane & 24) + (i & 7));
+          if (i < k) {
+            if (vA) t2A = fmaf(-gq(mA, i), ti, t2A);
+            if (vB) t2B = fmaf(-gq(mB, i), ti, t2B);
           }
         }
-        const float cc = mv ? fmaf(L.bmf[j], t, -t2 * rth) : 0.f;
-        if (mv) { L.t[j][m] = t; L.c[j][m] = cc; }
+        const float bm = L.bmf[j];
+        const float ccA = vA ? fmaf(bm, tA, -t2A * rthA) : 0.f;
+        const float ccB = vB ? fmaf(bm, tB, -t2B * rthB) : 0.f;
+        if (vA) { L.t[j][mA] = tA; L.c[j][mA] = ccA; }
+        if (vB) { L.t[j][mB] = tB; L.c[j][mB] = ccB; }
         // rho = r^T M r = a r^T P^-1 r + r^T S^T S r.  The dot products are
         // float-float (FP64-accurate); rho, alpha and beta multiply FP32
         // vectors and are formed in FP32, and so is the k-term LMP correction.
-        float corr = mv ? fmaf(f, cc, -g * t) : 0.f;
+        float corr = (vA ? fmaf(fa[0], ccA, -ga[0] * tA) : 0.f) + (vB ? fmaf(fb[0], ccB, -gb[0] * tB) : 0.f);
 #pragma unroll
-        for (int o = 8; o > 0; o >>= 1) corr += __shfl_xor_sync(0xffffffffu, corr, o);
+        for (int o = 4; o > 0; o >>= 1) corr += __shfl_xor_sync(0xffffffffu, corr, o);
+        const int m = mA;
         if (m == 0) {
           float rh[kMaxCS], rl[kMaxCS], uh[kMaxCS], ul[kMaxCS];
 #pragma unroll
@@ -846,6 +957,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
         }
       }
       __syncwarp();
+      BAND_PHASE(6);
       float tj[4][kK], cj[4][kK];
 #pragma unroll
       for (int jj = 0; jj < 4; ++jj)
@@ -864,44 +976,58 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
         aj[jj] = L.la[j0 + jj];
       }
       const bool any_learn2 = L.learn[j0] | L.learn[j0 + 1] | L.learn[j0 + 2] | L.learn[j0 + 3];
-      int ir = 0;
       float pmx[4] = {0.f, 0.f, 0.f, 0.f};   // max |p| of the four lanes over this thread's rows
       float* U = reinterpret_cast<float*>(pr.U);
-      for (int row = lane; row < nrows; row += 32) {
-        float* prow = pw + (row + hl) * kLD + j0;
-        const float4 r4 = ld4(vr + row * kLD + j0);
-        const float4 p4 = ld4(prow);
-        float z[4] = {r4.x, r4.y, r4.z, r4.w};
+      // two rows (row, row + 32) per iteration, every shared-memory load of
+      // both issued before their arithmetic
+      const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int row = lane; row < nrows; row += 64) {
+        const int rb = row + 32;
+        const bool hb = rb < nrows;
+        const float4 r4a = ld4(vr + row * kLD + j0), p4a = ld4(pw + (row + hl) * kLD + j0);
+        const float4 r4b = hb ? ld4(vr + rb * kLD + j0) : zero4, p4b = hb ? ld4(pw + (rb + hl) * kLD + j0) : zero4;
+        float4 w4a = zero4, w4b = zero4;   // (T r)_row from the learned step
+        if (any_learn2) {
+          w4a = ld4(vy + (row + kTH) * kLD + j0);
+          if (hb) w4b = ld4(vy + (rb + kTH) * kLD + j0);
+        }
+        float za[4] = {r4a.x, r4a.y, r4a.z, r4a.w}, zb[4] = {r4b.x, r4b.y, r4b.z, r4b.w};
 #pragma unroll
         for (int mm = 0; mm < kK; ++mm) {
           if (mm < k) {
-            const float ph = phT[mm * R_s + row], at = aT[mm * R_s + row];
+            const float pha = phT[mm * R_s + row], ata = aT[mm * R_s + row];
+            const float phb = hb ? phT[mm * R_s + rb] : 0.f, atb = hb ? aT[mm * R_s + rb] : 0.f;
 #pragma unroll
-            for (int jj = 0; jj < 4; ++jj) z[jj] = fmaf(ph, cj[jj][mm], fmaf(-at, tj[jj][mm], z[jj]));
+            for (int jj = 0; jj < 4; ++jj) {
+              za[jj] = fmaf(pha, cj[jj][mm], fmaf(-ata, tj[jj][mm], za[jj]));
+              zb[jj] = fmaf(phb, cj[jj][mm], fmaf(-atb, tj[jj][mm], zb[jj]));
+            }
           }
         }
         if (any_learn2) {
-          float4 w4 = make_float4(0.f, 0.f, 0.f, 0.f);     // (T r)_row from the residual step
+          const float wa[4] = {w4a.x, w4a.y, w4a.z, w4a.w}, wb[4] = {w4b.x, w4b.y, w4b.z, w4b.w};
 #pragma unroll
-          for (int ii = 0; ii < kTrRows; ++ii)
-            if (ii == ir) w4 = trr[ii];
-          z[0] = fmaf(aj[0], z[0], w4.x);
-          z[1] = fmaf(aj[1], z[1], w4.y);
-          z[2] = fmaf(aj[2], z[2], w4.z);
-          z[3] = fmaf(aj[3], z[3], w4.w);
+          for (int jj = 0; jj < 4; ++jj) {
+            za[jj] = fmaf(aj[jj], za[jj], wa[jj]);
+            zb[jj] = fmaf(aj[jj], zb[jj], wb[jj]);
+          }
         }
-        ++ir;
-        const float pv[4] = {p4.x, p4.y, p4.z, p4.w};
-        float pn[4];
+        const float pva[4] = {p4a.x, p4a.y, p4a.z, p4a.w}, pvb[4] = {p4b.x, p4b.y, p4b.z, p4b.w};
+        float pna[4], pnb[4];
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) {
-          pn[jj] = act[jj] ? fmaf(bj[jj], pv[jj], z[jj]) : 0.f;
-          pmx[jj] = fmaxf(pmx[jj], fabsf(pn[jj]));
+          pna[jj] = act[jj] ? fmaf(bj[jj], pva[jj], za[jj]) : 0.f;
+          pnb[jj] = (act[jj] && hb) ? fmaf(bj[jj], pvb[jj], zb[jj]) : 0.f;
+          pmx[jj] = fmaxf(pmx[jj], fmaxf(fabsf(pna[jj]), fabsf(pnb[jj])));
         }
-        st4(prow, make_float4(pn[0], pn[1], pn[2], pn[3]));
+        st4(pw + (row + hl) * kLD + j0, make_float4(pna[0], pna[1], pna[2], pna[3]));
+        if (hb) st4(pw + (rb + hl) * kLD + j0, make_float4(pnb[0], pnb[1], pnb[2], pnb[3]));
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj)
-          if (fin[jj]) U[(int64_t)L.sid[j0 + jj] * d + s0 + row] = vx[row * kLD + j0 + jj];
+          if (fin[jj]) {
+            U[(int64_t)L.sid[j0 + jj] * d + s0 + row] = vx[row * kLD + j0 + jj];
+            if (hb) U[(int64_t)L.sid[j0 + jj] * d + s0 + rb] = vx[rb * kLD + j0 + jj];
+          }
       }
       // the lanes' max |p| over the own rows, to every CTA (the scale of p in the next matvec)
 #pragma unroll
@@ -909,6 +1035,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) pmx[jj] = fmaxf(pmx[jj], __shfl_xor_sync(0xffffffffu, pmx[jj], o));
       if (lane < CS) st4(cluster.map_shared_rank(&s_pmax_in[crank][j0], lane), make_float4(pmx[0], pmx[1], pmx[2], pmx[3]));
+      BAND_PHASE(7);
     }
     __syncthreads();
     // finished lanes: stats, and rank 0 takes the next systems off the queue
@@ -931,7 +1058,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
           v = sid + kRetry;
         } else {
           pr.iters[sid] = L.it[j];
-          pr.relres[sid] = bn > 0.f ? sqrt(((double)L.rrh[j] + (double)L.rrl[j]) / (double)bn) : 0.0;
+          pr.relres[sid] = bn > 0.f ? (double)sqrtf(rrj / bn) : 0.0;
           if (L.fin[j] == 2) atomicOr(&pr.status[0], kStatBreakdown);
           else if (failed) atomicOr(&pr.status[0], kStatNotConverged);
           const int nid = base + __popc(fm & ((1u << j) - 1u));
@@ -951,6 +1078,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       }
     }
     cluster.sync();   // (3)
+    BAND_PHASE(8);
     // ---------------- refills, exit test, halo ----------------
     if (tid < kJ && L.fin[tid]) lane_scalars(tid, L.newsid[tid]);
     if (tid < kJ) {
@@ -963,8 +1091,16 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
     if (!s_live) break;
     lane_vectors_all();   // lanes started in this step: own rows of r and x
     __syncthreads();
+    BAND_PHASE(9);
+#ifdef INFO_ESRF_PHASE_CLOCKS
+    if (tid == 0) s_ph[kPhases] += 1;
+#endif
   }
   cluster.sync();   // no CTA leaves while another may still read its shared memory
+#ifdef INFO_ESRF_PHASE_CLOCKS
+  if (tid < kPhaseSlots - 1) atomicAdd(&g_band_phase[tid], (unsigned long long)s_ph[tid]);
+  if (tid == 0) atomicAdd(&g_band_phase[kPhaseSlots - 1], 1ull);
+#endif
 }
 
 // Whether the band kernel above can take problem p (FP32, at most kK Ritz
@@ -1064,3 +1200,29 @@ int launch_pcg_band1d(const ProblemDev& p, const ProblemDev* dp, int CS, int32_t
 }
 
 }  // namespace infoesrf
+
+extern "C" int info_esrf_band_phase_clocks(int64_t* out, int32_t n, int32_t reset) {
+#ifdef INFO_ESRF_PHASE_CLOCKS
+  using namespace infoesrf;
+  if (!out || n < 1) return INFO_ESRF_ERR_INVALID_ARG;
+  unsigned long long h[kPhaseSlots] = {};
+  if (cudaMemcpyFromSymbol(h, g_band_phase, sizeof(h)) != cudaSuccess) {
+    cudaGetLastError();
+    return INFO_ESRF_ERR_CUDA;
+  }
+  for (int i = 0; i < n && i < kPhaseSlots; ++i) out[i] = (int64_t)h[i];
+  if (reset) {
+    const unsigned long long z[kPhaseSlots] = {};
+    if (cudaMemcpyToSymbol(g_band_phase, z, sizeof(z)) != cudaSuccess) {
+      cudaGetLastError();
+      return INFO_ESRF_ERR_CUDA;
+    }
+  }
+  return 0;
+#else
+  (void)out;
+  (void)n;
+  (void)reset;
+  return INFO_ESRF_ERR_UNSUPPORTED;
+#endif
+}
