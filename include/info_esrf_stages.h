@@ -92,7 +92,7 @@ int info_esrf_fma_probe(int32_t precision, int64_t iters, double* flops_per_s, d
  * sums clock64() deltas per phase over the launches since the last reset:
  * out[0..9] the cycles of the ten phases of a round (0 band matvec, 1 p^T y
  * push and cluster barrier 1, 2 alpha and right-hand-side prefetch wait,
- * 3 residual update and its dot products, 4 learned term, 5 reductions push
+ * 3 residual update and its dot products, 4 warp reductions and learned term, 5 reductions push
  * and cluster barrier 2, 6 CG and preconditioner scalars, 7 direction update,
  * 8 queue, halo push and cluster barrier 3, 9 refills), out[10] rounds,
  * out[11] set-up cycles, out[12] CTAs, each summed over CTAs; n values are

@@ -250,7 +250,7 @@ def launch_count() -> int:
 
 
 BAND_PHASES = ("band matvec", "p^T y push + cluster barrier 1", "alpha, RHS prefetch wait",
-               "residual update, Phi^T r, A^T r", "learned term (r halo push, barrier 2a, T r)",
+               "residual update, Phi^T r, A^T r", "warp reductions, learned term (r halo push, barrier 2a, T r)",
                "reductions push + cluster barrier 2", "decisions (CG scalars, LMP algebra)",
                "direction update z, p", "queue, halo push, cluster barrier 3", "refills, RHS prefetch issue")
 

@@ -39,6 +39,7 @@
 #include <cooperative_groups.h>
 #include <cuda_fp16.h>
 #include <math.h>
+#include <stddef.h>
 
 #include "common.cuh"
 #include "info_esrf.h"
@@ -57,6 +58,7 @@ constexpr int kTile = 16;       // rows per matvec tile
 constexpr int kNW = kThreads / 32;
 constexpr int kK = 10;          // Ritz vectors handled by this kernel
 constexpr int kNR = 4 + 2 * kK; // residual reduction values per lane: rr (hi, lo), uu (hi, lo), f[k], g[k]
+constexpr int kKP = (kK + 3) & ~3;   // kK rounded up to a multiple of 4
 constexpr int kRetry = 1 << 30; // queue id flag: solve this system again without the learned term
 constexpr int kTH = 2 * kLearnH;          // half-width of T = S^T S (autocorrelation of the taps)
 constexpr int kTT = 2 * kTH + 1;          // taps of T
@@ -91,11 +93,27 @@ struct LaneState {
   float rrh[kJ], rrl[kJ];             // r^T r as a float-float pair (FP64-accurate)
   float bn2[kJ];                      // b^T b
   float sigf[kJ], alpha[kJ], beta[kJ];
-  float t[kJ][kK], c[kJ][kK];
+  float t[kJ][kKP], c[kJ][kKP];       // LMP coefficients, rows padded for 16-byte loads
   float la[kJ], ltT[kTT][kJ];         // learned correction: a and the taps of T = S^T S (tap-major)
   float bmf[kJ];                      // beta_q - sigma_q of the preconditioner (App. E)
   int learn[kJ];
   int mem[kJ];                        // ensemble member of the lane's system, -1 for the mean system
+};
+
+static_assert(offsetof(LaneState, t) % 16 == 0 && offsetof(LaneState, c) % 16 == 0, "16-byte rows of t and c");
+
+// Problem fields read inside the iteration loop, copied to shared memory once:
+// global loads after a cluster barrier (acquire at cluster scope) cannot be
+// served from a stale L1 line, so every ProblemDev access there would be an
+// L2 round trip on the critical path.
+struct LoopArgs {
+  const float* learn_T;
+  const double* bmean;
+  float* U;
+  int32_t* iters;
+  double* relres;
+  int32_t* status;
+  int mean_sys, Q, nsys, fixed_iters;
 };
 
 struct Setup {
@@ -116,6 +134,11 @@ __device__ __forceinline__ void cp_async4(float* dst_smem, const float* src_glob
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+// Split cluster barrier: arrive (releasing this thread's earlier shared and
+// distributed shared-memory writes), independent work, then wait (acquiring
+// every CTA's).  All threads of the cluster execute both, in the same order.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory"); }
 
 // Two FP32 values (already scaled into FP16 range) as hi + lo pairs of
 // packed FP16: hi = the values rounded to FP16, lo = the remainders rounded to
@@ -224,8 +247,8 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       if (row < nrows) {
         const int64_t a = s0 + row;
         nnz = pr.oo_nnz[a];
-#pragma unroll 4
-        for (int e = part; e < nnz; e += 2) {
+#pragma unroll 8
+        for (int e = part; e < nnz; e += 2) {   // eight entries' loads in flight
           const int dl = wrap_delta(pr.oo_col[(int64_t)e * d + a], (int)a, (int)d);
           dmin = dl < dmin ? dl : dmin;
           dmax = dl > dmax ? dl : dmax;
@@ -378,7 +401,8 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       const int nnz = pr.oo_nnz[a];
       const int t = row / kTile, r = row % kTile;
       const float sc = rsc[row];
-      for (int e = part; e < nnz; e += 2) {
+#pragma unroll 8
+      for (int e = part; e < nnz; e += 2) {   // eight entries' loads in flight
         const int rel = row + wrap_delta(pr.oo_col[(int64_t)e * d + a], (int)a, (int)d);
         const int kk = rel - s_klo[t], kc = kk & 15;
         const int ln = (r & 7) * 4 + ((kc & 7) >> 1);         // lane holding this element
@@ -432,6 +456,19 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
   };
   if (qtab)
     for (int qs = tid; qs <= pr.Q; qs += blockDim.x) shift_scalars(qs, s_qsigf[qs], s_qbmf[qs], s_qla[qs]);
+  __shared__ LoopArgs LA;
+  if (tid == 0) {
+    LA.learn_T = pr.learn_T;
+    LA.bmean = pr.bmean;
+    LA.U = reinterpret_cast<float*>(pr.U);
+    LA.iters = pr.iters;
+    LA.relres = pr.relres;
+    LA.status = pr.status;
+    LA.mean_sys = (int)pr.mean_sys;
+    LA.Q = pr.Q;
+    LA.nsys = (int)pr.nsys;
+    LA.fixed_iters = pr.fixed_iters;
+  }
   __syncthreads();
   // Starts system sid in lane j (scalars; the taps of the learned term follow
   // with the lane's right-hand side in lane_vectors_all).
@@ -449,9 +486,9 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       L.state[j] = kEmpty;
     } else {
       L.state[j] = kStart;
-      const int q = sid < pr.mean_sys ? -1 : (sid - pr.mean_sys) / (int)N;
-      if (q >= 0) L.mem[j] = sid - pr.mean_sys - q * (int)N;
-      const int qs = q < 0 ? pr.Q : q;
+      const int q = sid < LA.mean_sys ? -1 : (sid - LA.mean_sys) / (int)N;
+      if (q >= 0) L.mem[j] = sid - LA.mean_sys - q * (int)N;
+      const int qs = q < 0 ? LA.Q : q;
       float la0;
       if (qtab) {
         sgf = s_qsigf[qs];
@@ -492,18 +529,19 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
     // taps of T = S^T S of the started lanes (zero without the learned term)
     for (int e = tid; e < ns * kTT; e += blockDim.x) {
       const int j = s_start[e / kTT], u = e % kTT, qs = L.qs[j];
-      if (qs >= 0) cp_async4(&L.ltT[u][j], pr.learn_T + (int64_t)qs * kLearnT + u);
+      if (qs >= 0) cp_async4(&L.ltT[u][j], LA.learn_T + (int64_t)qs * kLearnT + u);
       else L.ltT[u][j] = 0.f;
     }
-    for (int e = tid; e < R_s * ns; e += blockDim.x) {
-      const int row = e / ns, j = s_start[e % ns];
-      float* dst = vr + row * kLD + j;
-      vx[row * kLD + j] = 0.f;
-      if (row >= nrows) { *dst = 0.f; continue; }
-      const int64_t a = s0 + row;
-      const int i = L.mem[j];
-      if (i < 0) *dst = (float)pr.bmean[a];
-      else cp_async4(dst, W + a * N + i);
+    for (int is = 0; is < ns; ++is) {
+      const int j = s_start[is], i = L.mem[j];
+      for (int row = tid; row < R_s; row += blockDim.x) {
+        float* dst = vr + row * kLD + j;
+        vx[row * kLD + j] = 0.f;
+        if (row >= nrows) { *dst = 0.f; continue; }
+        const int64_t a = s0 + row;
+        if (i < 0) *dst = (float)LA.bmean[a];
+        else cp_async4(dst, W + a * N + i);
+      }
     }
     cp_async_commit();
   };
@@ -623,7 +661,9 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       }
       st4(cluster.map_shared_rank(&s_pap_in[crank][j][0], dst), make_float4(h0, l0, h1, l1));
     }
-    cluster.sync();   // (1)
+    cluster_arrive();
+    cp_async_wait_all();   // right-hand sides of lanes started in the previous step
+    cluster_wait();   // (1)
     BAND_PHASE(1);
     // ---------------- alpha ----------------
     if (tid < kJ) {
@@ -642,7 +682,6 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       }
       L.alpha[j] = alpha;
     }
-    cp_async_wait_all();   // right-hand sides of lanes started in the previous step
     __syncthreads();
     BAND_PHASE(2);
     // ---------------- x += alpha p, r -= alpha y; partial rr, Phi^T r, A^T r ----------------
@@ -720,6 +759,21 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
           }
         }
       }
+      BAND_PHASE(3);
+      // learned term, applied periodically across the slices: the halo rows of
+      // the r window go to the CTAs that hold them (split barrier 2a: the
+      // warp reductions below run while the rows are in flight)
+      if (s_anyl) {
+        __syncthreads();
+        const int nrp = s_nrpush;
+        for (int e = tid; e < nrp * (kJ / 4); e += blockDim.x) {
+          const int2 t = rpush[e / (kJ / 4)];
+          const int q4 = e % (kJ / 4);
+          const int row = t.x & 0xffff, c2 = t.x >> 16;
+          st4(cluster.map_shared_rank(vy, c2) + t.y * kLD + 4 * q4, ld4(vy + (row + kTH) * kLD + 4 * q4));
+        }
+        cluster_arrive();   // (2a)
+      }
       // the warp's partial Phi^T r and A^T r are reduced first, which frees
       // their 80 registers before the learned term's stencil
       const float s0v = warp_reduce_scatter32<float>(v0, lane);
@@ -768,20 +822,10 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       const int qj = ((lane >> 4) & 1) * 2 + ((lane >> 3) & 1);
       const bool q_uu = (lane & 4) != 0;
       if (q_uu) { qh = 0.f; ql = 0.f; }
-      // learned term, applied periodically across the slices: the halo rows of
-      // the r window come from their owners, then T r = S^T S r replaces r on
-      // the own rows of the window, where the direction update reads it
-      BAND_PHASE(3);
+      // T r = S^T S r then replaces r on the own rows of the window, where the
+      // direction update reads it
       if (s_anyl) {
-        __syncthreads();
-        const int nrp = s_nrpush;
-        for (int e = tid; e < nrp * (kJ / 4); e += blockDim.x) {
-          const int2 t = rpush[e / (kJ / 4)];
-          const int q4 = e % (kJ / 4);
-          const int row = t.x & 0xffff, c2 = t.x >> 16;
-          st4(cluster.map_shared_rank(vy, c2) + t.y * kLD + 4 * q4, ld4(vy + (row + kTH) * kLD + 4 * q4));
-        }
-        cluster.sync();   // (2a) r windows complete
+        cluster_wait();   // (2a) r windows complete
         // thread = (system lane `lane`, own rows kStRows warp ..): the
         // kStRows + 2 kTH rows of its window are read once into registers,
         // one conflict-free wavefront per row for the warp (lanes without the
@@ -823,27 +867,28 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       BAND_PHASE(4);
       const int qdst = (j0 + qj) * kNR + (q_uu ? 2 : 0);
       // push this warp's four lanes to every CTA of the cluster.  Distributed
-      // shared-memory stores are separate transactions, so lanes 4 k gather
-      // values 4 k .. 4 k + 3 of each block and store them as one 16-byte word
-      // (2 kK is a multiple of 4, so a group never straddles two lanes' rows).
+      // shared-memory stores are separate transactions, so the four lanes of
+      // a group 4 k .. 4 k + 3 gather values 4 k .. 4 k + 3 of each block into
+      // one 16-byte word (2 kK is a multiple of 4, so a group never straddles
+      // two lanes' rows) and share the destinations: lane 4 k + c stores to
+      // ranks c, c + 4, ...
       float4 sv4[3];
+      const int gbase = lane & ~3;
 #pragma unroll
       for (int b = 0; b < 3; ++b)
-        sv4[b] = make_float4(sv[b], __shfl_down_sync(0xffffffffu, sv[b], 1),
-                             __shfl_down_sync(0xffffffffu, sv[b], 2), __shfl_down_sync(0xffffffffu, sv[b], 3));
+        sv4[b] = make_float4(__shfl_sync(0xffffffffu, sv[b], gbase), __shfl_sync(0xffffffffu, sv[b], gbase + 1),
+                             __shfl_sync(0xffffffffu, sv[b], gbase + 2), __shfl_sync(0xffffffffu, sv[b], gbase + 3));
       static_assert((2 * kK) % 4 == 0 && kNR % 4 == 0, "16-byte groups of the residual partials");
-      if ((lane & 3) == 0) {
-        for (int dst = 0; dst < CS; ++dst) {
-          float* base = cluster.map_shared_rank(&s_res_in[crank][0][0], dst);
+      for (int dst = lane & 3; dst < CS; dst += 4) {
+        float* base = cluster.map_shared_rank(&s_res_in[crank][0][0], dst);
 #pragma unroll
-          for (int b = 0; b < 3; ++b) {
-            const int idx = 32 * b + lane;          // = jj * 2kK + (m or kK + m)
-            if (idx >= 4 * 2 * kK) continue;
-            const int jj = idx / (2 * kK), w = idx % (2 * kK);
-            st4(base + (j0 + jj) * kNR + 4 + w, sv4[b]);
-          }
-          *reinterpret_cast<float2*>(base + qdst) = make_float2(qh, ql);
+        for (int b = 0; b < 3; ++b) {
+          const int idx = 32 * b + gbase;          // = jj * 2kK + (m or kK + m)
+          if (idx >= 4 * 2 * kK) continue;
+          const int jj = idx / (2 * kK), w = idx % (2 * kK);
+          st4(base + (j0 + jj) * kNR + 4 + w, sv4[b]);
         }
+        *reinterpret_cast<float2*>(base + qdst) = make_float2(qh, ql);
       }
     }
     cluster.sync();   // (2)
@@ -945,7 +990,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
           } else if (st == kActive && L.fin[j] == 0) {
             bool done = false;
             if (!isfinite(rr)) { done = true; L.fin[j] = 2; }
-            else if (pr.fixed_iters > 0) done = L.it[j] >= pr.fixed_iters || !(rr > 0.f);
+            else if (LA.fixed_iters > 0) done = L.it[j] >= LA.fixed_iters || !(rr > 0.f);
             else done = !(rr > tol2f * L.bn2[j]) || L.it[j] >= maxit;
             if (done) {
               if (L.fin[j] == 0) L.fin[j] = 1;
@@ -962,9 +1007,17 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
 #pragma unroll
       for (int jj = 0; jj < 4; ++jj)
 #pragma unroll
-        for (int mm = 0; mm < kK; ++mm) {
-          tj[jj][mm] = mm < k ? L.t[j0 + jj][mm] : 0.f;
-          cj[jj][mm] = mm < k ? L.c[j0 + jj][mm] : 0.f;
+        for (int q4 = 0; q4 < kKP / 4; ++q4) {
+          const float4 t4 = ld4(&L.t[j0 + jj][4 * q4]), c4 = ld4(&L.c[j0 + jj][4 * q4]);
+          const float tv[4] = {t4.x, t4.y, t4.z, t4.w}, cv[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int mm = 4 * q4 + e;
+            if (mm < kK) {
+              tj[jj][mm] = mm < k ? tv[e] : 0.f;
+              cj[jj][mm] = mm < k ? cv[e] : 0.f;
+            }
+          }
         }
       bool act[4], fin[4];
       float bj[4], aj[4];
@@ -977,7 +1030,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       }
       const bool any_learn2 = L.learn[j0] | L.learn[j0 + 1] | L.learn[j0 + 2] | L.learn[j0 + 3];
       float pmx[4] = {0.f, 0.f, 0.f, 0.f};   // max |p| of the four lanes over this thread's rows
-      float* U = reinterpret_cast<float*>(pr.U);
+      float* U = LA.U;
       // two rows (row, row + 32) per iteration, every shared-memory load of
       // both issued before their arithmetic
       const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1044,7 +1097,7 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
       const bool f = L.fin[j] != 0;
       const float bn = L.bn2[j];
       const float rrj = L.rrh[j] + L.rrl[j];
-      const bool failed = f && (L.fin[j] == 2 || (pr.fixed_iters <= 0 && !(rrj <= tol2f * bn)));
+      const bool failed = f && (L.fin[j] == 2 || (LA.fixed_iters <= 0 && !(rrj <= tol2f * bn)));
       const bool retry = failed && L.learn[j];          // plain PCG solves it again
       const bool take = f && !retry;
       const unsigned fm = __ballot_sync(0xffffffffu, take);
@@ -1057,12 +1110,12 @@ k_pcg_band1d(const ProblemDev* tab, int32_t* queue, int32_t* fallback, int dyn_f
         if (retry) {
           v = sid + kRetry;
         } else {
-          pr.iters[sid] = L.it[j];
-          pr.relres[sid] = bn > 0.f ? (double)sqrtf(rrj / bn) : 0.0;
-          if (L.fin[j] == 2) atomicOr(&pr.status[0], kStatBreakdown);
-          else if (failed) atomicOr(&pr.status[0], kStatNotConverged);
+          LA.iters[sid] = L.it[j];
+          LA.relres[sid] = bn > 0.f ? (double)sqrtf(rrj / bn) : 0.0;
+          if (L.fin[j] == 2) atomicOr(&LA.status[0], kStatBreakdown);
+          else if (failed) atomicOr(&LA.status[0], kStatNotConverged);
           const int nid = base + __popc(fm & ((1u << j) - 1u));
-          v = nid < pr.nsys ? nid : -1;
+          v = nid < LA.nsys ? nid : -1;
         }
         for (int dst = 0; dst < CS; ++dst) cluster.map_shared_rank(&L.newsid[0], dst)[j] = v;
       }
