@@ -23,6 +23,20 @@ b2 [32], W3 [18][32], b3 [18] (row-major), 1810 values; h = 8.
 Training minimizes, over Krylov vectors v with images y = C_q v and
 z = P_q^-1 y taken from the method's own runs,
     L = (1/S) sum_s ||a_s z_s + S_s^T S_s y_s - v_s||^2 / ||v_s||^2.
+
+Two-dimensional lattice form (observations on every point of a periodic
+Lx x Ly lattice, vectors indexed a = i + Lx j in lattice order): S is the
+stencil over the lattice offsets (dx, dy) with dx^2 + dy^2 <= 8 (the 5 x 5
+square), with one tap per squared length (LAT_BINS = 0, 1, 2, 4, 5, 8), so S
+is symmetric and S^T S = S S.  The network is the same; w_q holds the bin taps
+in its first len(LAT_BINS) entries, the rest unused.  Same loss with S S.
+
+Parity pins: the 1-D stencil against the explicit circulant matrix; the lattice
+stencil against a brute-force double loop and against its Fourier symbol
+(eigenvalues sum_offsets w cos(2 pi (k dx / Lx + l dy / Ly))); M SPD by
+construction; the loss against the base preconditioner at a zero network; the
+finite-difference gradients against autograd of an independent PyTorch
+restatement (tests/test_oracle_learned.py).
 """
 from __future__ import annotations
 
@@ -119,3 +133,63 @@ def init_params(seed=0, scale=0.1):
     p = {name: scale * rng.standard_normal(shape) for name, shape in SHAPES}
     p["b3"] = np.zeros(NOUT)
     return np.concatenate([p[name].reshape(-1) for name, _ in SHAPES])
+
+
+# ---- two-dimensional lattice form ----
+H2_LAT = 8
+LAT_BINS = (0, 1, 2, 4, 5, 8)
+NBIN = len(LAT_BINS)
+
+
+def lattice_offsets():
+    """(dx, dy, bin) for every offset of the stencil, bin = LAT_BINS.index(dx^2 + dy^2)."""
+    out = []
+    for dy in range(-2, 3):
+        for dx in range(-2, 3):
+            r2 = dx * dx + dy * dy
+            if r2 <= H2_LAT:
+                out.append((dx, dy, LAT_BINS.index(r2)))
+    return out
+
+
+def stencil_lattice(wb, r, Lx, Ly):
+    """(S r)_(i, j) = sum_offsets wb[bin] r_((i + dx) mod Lx, (j + dy) mod Ly), r in lattice order."""
+    R = np.asarray(r, dtype=np.float64).reshape(Ly, Lx)
+    out = np.zeros_like(R)
+    for dx, dy, b in lattice_offsets():
+        out += wb[b] * np.roll(np.roll(R, -dy, axis=0), -dx, axis=1)
+    return out.reshape(-1)
+
+
+def apply_correction_lattice(log_a, wb, z, r, Lx, Ly):
+    """a z + S S r (S symmetric; z = P^-1 r computed by the caller)."""
+    return np.exp(log_a) * z + stencil_lattice(wb, stencil_lattice(wb, r, Lx, Ly), Lx, Ly)
+
+
+def sample_losses_lattice(theta, phi, V, Y, Z, Lx, Ly):
+    la, w = coefficients(theta, phi)
+    out = np.empty(V.shape[0])
+    for s in range(V.shape[0]):
+        e = apply_correction_lattice(la[s], w[s, :NBIN], Z[s], Y[s], Lx, Ly) - V[s]
+        out[s] = float(e @ e) / float(V[s] @ V[s])
+    return out
+
+
+def loss_lattice(theta, phi, V, Y, Z, Lx, Ly):
+    return float(np.mean(sample_losses_lattice(theta, phi, V, Y, Z, Lx, Ly)))
+
+
+def fd_gradient_lattice(theta, phi, V, Y, Z, Lx, Ly, eps=1e-6):
+    """Central finite differences of the lattice-form loss in float64."""
+    g = np.zeros(NPARAM)
+    th = np.asarray(theta, dtype=np.float64).copy()
+    for i in range(NPARAM):
+        old = th[i]
+        th[i] = old + eps
+        lp = loss_lattice(th, phi, V, Y, Z, Lx, Ly)
+        th[i] = old - eps
+        lm = loss_lattice(th, phi, V, Y, Z, Lx, Ly)
+        th[i] = old
+        g[i] = (lp - lm) / (2 * eps)
+    return g
+
