@@ -122,10 +122,14 @@ typedef struct {
    * preconditioned by M_q = a_q P_q^-1 + S_q^T S_q (symmetric positive
    * definite), a_q and the stencil S_q produced by the network from the
    * shift and the spectrum statistics of C.  Used by the cluster-resident
-   * FP32 solver for 1-D networks; a system that breaks down or reaches
-   * max_iter with it is solved again with P_q^-1 alone.  Convergence is
-   * always tested on the unpreconditioned residual ||b - C_q u||.  Other
-   * solvers do not apply it and report so in info_esrf_stats.learned. */
+   * FP32 solver for 1-D networks (S_q a circulant over the observation
+   * index), and by the BF16 path where the observations fill a periodic 2-D
+   * lattice (S_q a symmetric 5 x 5 lattice stencil, M_q = a_q P_q^-1 + S_q S_q;
+   * the workspace then holds one more vector per system).  A system that
+   * breaks down or reaches max_iter with it is solved again with P_q^-1
+   * alone.  Convergence is always tested on the unpreconditioned residual
+   * ||b - C_q u||.  Other solvers and geometries do not apply it and report
+   * so in info_esrf_stats.learned. */
   const float* learned_model;
   double learned_max_shift;  /* > 0: the learned term is used only for shifts sigma = s_q + 1 <= this */
   /* NULL, or a device int32 array receiving each system's PCG iteration

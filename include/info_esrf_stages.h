@@ -162,6 +162,50 @@ int info_esrf_krylov_capture(const info_esrf_grid* grid, int64_t N, const double
                              const int32_t* sel_dev, int32_t K, float* V_dev, float* Y_dev, float* Z_dev,
                              float* feat_dev, void* stream);
 
+/* Two-dimensional lattice form (BF16 path, precision INFO_ESRF_PRECISION_BF16):
+ * where the observations are exactly the points (x0 + i sx, y0 + j sy),
+ * i < Lx, j < Ly, of the two axes of extent > 1 of the grid, both periodic
+ * (Lx sx and Ly sy the extents), the correction is M_q = a_q P_q^-1 + S_q S_q
+ * with S_q the symmetric stencil over the lattice offsets (dx, dy),
+ * dx^2 + dy^2 <= 8 (the 5 x 5 square), whose tap for squared length
+ * 0, 1, 2, 4, 5, 8 is w_q[0..5] (the first six stencil outputs of the same
+ * network).  Vectors of the lattice form are in lattice order, index i + Lx j.
+ * The loss is the same with S S in place of S^T S. */
+
+/* Scratch bytes for info_esrf_learn_loss_grad_lattice / _train_lattice with
+ * nsamp samples of d = Lx Ly values. */
+size_t info_esrf_learn_lattice_scratch_size(int32_t nsamp, int64_t d);
+
+/* grad = dL/dtheta and *loss_dev = L of the lattice form (device, hand-written
+ * forward and backward kernels); samples [nsamp][Lx Ly] float in lattice
+ * order, feat [nsamp][4]; samples with v = 0 contribute nothing. */
+int info_esrf_learn_loss_grad_lattice(const float* theta_dev, int32_t nsamp, int32_t Lx, int32_t Ly,
+                                      const float* feat_dev, const float* V_dev, const float* Y_dev,
+                                      const float* Z_dev, float* grad_dev, double* loss_dev, void* scratch_dev,
+                                      size_t scratch_bytes, void* stream);
+
+/* `steps` Adam steps on the lattice-form loss (as info_esrf_learn_train). */
+int info_esrf_learn_train_lattice(float* theta_dev, float* m_dev, float* v_dev, int32_t first_step, int32_t steps,
+                                  float lr, int32_t nsamp, int32_t Lx, int32_t Ly, const float* feat_dev,
+                                  const float* V_dev, const float* Y_dev, const float* Z_dev, float* grad_dev,
+                                  double* loss_hist_dev, void* scratch_dev, size_t scratch_bytes, void* stream);
+
+/* Krylov samples of the BF16 path for the lattice form (options.precision
+ * must be INFO_ESRF_PRECISION_BF16; the model in the options is ignored:
+ * the paper's preconditioner runs): prepares one analysis into the
+ * workspace and runs K iterations of the BF16 PCG from the systems' own
+ * right-hand sides, recording for each of the nsel systems sel_dev[]
+ * (number q * N + i) and iteration v = p / ||p||, y = (sigma p + C p) / ||p||
+ * (p the BF16 direction the matvec used), z = P_q^-1 y and phi; all zero for
+ * a system that stopped before that iteration.  Outputs [nsel * K][d] and
+ * [nsel * K][4] float in lattice order, *Lx and *Ly the lattice shape.
+ * INFO_ESRF_ERR_UNSUPPORTED when the observations are not a 2-D lattice. */
+int info_esrf_krylov_capture_lattice(const info_esrf_grid* grid, int64_t N, const double* X_dev, int64_t d,
+                                     const int64_t* obs_idx_dev, const double* R_diag_dev, int32_t Q,
+                                     const info_esrf_options* opt, void* workspace, size_t ws_bytes, int32_t nsel,
+                                     const int32_t* sel_dev, int32_t K, float* V_dev, float* Y_dev, float* Z_dev,
+                                     float* feat_dev, int32_t* Lx, int32_t* Ly, void* stream);
+
 /* Versioned binary model file: 8-byte tag "IESRFNN1", int32 parameter count,
  * parameters (float), then the shift cut-off (double, see
  * options.learned_max_shift); little-endian.  Host arrays. */

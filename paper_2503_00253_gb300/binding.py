@@ -155,6 +155,18 @@ def library() -> ctypes.CDLL:
         "info_esrf_prepared_band_capacity": (c_int32, [P(Grid), c_int64, c_int64, c_int32, P(Options),
                                                        P(c_int64), P(c_int64)]),
         "info_esrf_band_phase_clocks": (c_int32, [P(c_int64), c_int32, c_int32]),
+        "info_esrf_learn_lattice_scratch_size": (ctypes.c_size_t, [c_int32, c_int64]),
+        "info_esrf_learn_loss_grad_lattice": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p,
+                                                        c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                                        ctypes.c_size_t, c_void_p]),
+        "info_esrf_learn_train_lattice": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, ctypes.c_float,
+                                                    c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
+                                                    c_void_p, c_void_p, c_void_p, c_void_p, ctypes.c_size_t,
+                                                    c_void_p]),
+        "info_esrf_krylov_capture_lattice": (c_int32, [P(Grid), c_int64, c_void_p, c_int64, c_void_p, c_void_p,
+                                                       c_int32, P(Options), c_void_p, ctypes.c_size_t, c_int32,
+                                                       c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
+                                                       P(c_int32), P(c_int32), c_void_p]),
         "info_esrf_bf16_tile_matvec": (c_int32, [c_int32, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_int32,
                                                  c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     }
@@ -515,6 +527,57 @@ def krylov_capture(grid, X, obs_idx, R, Q, sel, K, options: Optional[Options] = 
                                               sel_t.data_ptr(), K, V.data_ptr(), Y.data_ptr(), Z.data_ptr(),
                                               feat.data_ptr(), _stream(stream)), "info_esrf_krylov_capture")
     return V, Y, Z, feat
+
+
+def krylov_capture_lattice(grid, X, obs_idx, R, Q, sel, K, options: Optional[Options] = None, stream=None):
+    """Krylov samples (V, Y, Z, feat) of the BF16 path in lattice order, and the lattice shape (Lx, Ly)."""
+    o = options if options is not None else make_options(precision=PRECISION_BF16)
+    g = make_grid(grid)
+    N, n = X.shape
+    d = obs_idx.numel()
+    need = library().info_esrf_workspace_size(ctypes.byref(g), N, d, Q, ctypes.byref(o))
+    ws = workspace(need, X.device)
+    sel_t = torch.as_tensor(sel, dtype=torch.int32, device=X.device)
+    S = sel_t.numel() * K
+    V = torch.empty((S, d), dtype=torch.float32, device=X.device)
+    Y = torch.empty_like(V)
+    Z = torch.empty_like(V)
+    feat = torch.empty((S, 4), dtype=torch.float32, device=X.device)
+    lx, ly = c_int32(), c_int32()
+    _check(library().info_esrf_krylov_capture_lattice(
+        ctypes.byref(g), N, X.data_ptr(), d, obs_idx.data_ptr(), R.data_ptr(), Q, ctypes.byref(o), ws.data_ptr(),
+        ws.numel(), sel_t.numel(), sel_t.data_ptr(), K, V.data_ptr(), Y.data_ptr(), Z.data_ptr(), feat.data_ptr(),
+        ctypes.byref(lx), ctypes.byref(ly), _stream(stream)), "info_esrf_krylov_capture_lattice")
+    return V, Y, Z, feat, int(lx.value), int(ly.value)
+
+
+def learn_loss_grad_lattice(theta, feat, V, Y, Z, Lx, Ly, stream=None):
+    S, d = V.shape
+    scratch = workspace(library().info_esrf_learn_lattice_scratch_size(S, d), V.device)
+    grad = torch.empty_like(theta)
+    loss = torch.zeros(1, dtype=torch.float64, device=V.device)
+    _check(library().info_esrf_learn_loss_grad_lattice(theta.data_ptr(), S, Lx, Ly, feat.data_ptr(), V.data_ptr(),
+                                                       Y.data_ptr(), Z.data_ptr(), grad.data_ptr(), loss.data_ptr(),
+                                                       scratch.data_ptr(), scratch.numel(), _stream(stream)),
+           "info_esrf_learn_loss_grad_lattice")
+    return float(loss.item()), grad
+
+
+def learn_train_lattice(theta, feat, V, Y, Z, Lx, Ly, steps, lr=1e-2, state=None, stream=None):
+    """Adam training of the lattice form in place on theta.  Returns (loss history, state)."""
+    S, d = V.shape
+    if state is None:
+        state = dict(m=torch.zeros_like(theta), v=torch.zeros_like(theta), step=1)
+    scratch = workspace(library().info_esrf_learn_lattice_scratch_size(S, d), V.device)
+    grad = torch.empty_like(theta)
+    hist = torch.zeros(steps, dtype=torch.float64, device=V.device)
+    _check(library().info_esrf_learn_train_lattice(theta.data_ptr(), state["m"].data_ptr(), state["v"].data_ptr(),
+                                                   state["step"], steps, lr, S, Lx, Ly, feat.data_ptr(),
+                                                   V.data_ptr(), Y.data_ptr(), Z.data_ptr(), grad.data_ptr(),
+                                                   hist.data_ptr(), scratch.data_ptr(), scratch.numel(),
+                                                   _stream(stream)), "info_esrf_learn_train_lattice")
+    state["step"] += steps
+    return hist, state
 
 
 def learn_loss_grad(theta, feat, V, Y, Z, stream=None):

@@ -263,8 +263,8 @@ void carve_problem(Carver& cv, ProblemDev& pr, const info_esrf_options& o) {
     pr.Xv = cv.take<float>((size_t)J * dp * 4);
     pr.Rv = cv.take<float>((size_t)J * dp * 4);
     pr.pty = cv.take<float>((size_t)pr.nrt * J * 4);
-    pr.dots = cv.take<double>((size_t)nsub * J * (2 * kk + 1) * 8);
-    pr.dsum = cv.take<double>((size_t)J * (2 * kk + 1) * 8);
+    pr.dots = cv.take<double>((size_t)nsub * J * tile_dot_values((int)kk) * 8);
+    pr.dsum = cv.take<double>((size_t)J * tile_dot_values((int)kk) * 8);
     pr.sysd = cv.take<double>((size_t)J * 8 * 8);
     pr.lcoef = cv.take<float>((size_t)J * 2 * kMaxK * 4);
     pr.sigmaf = cv.take<float>((size_t)J * 4);
@@ -272,6 +272,14 @@ void carve_problem(Carver& cv, ProblemDev& pr, const info_esrf_options& o) {
     pr.chunk_active = cv.take<int32_t>((size_t)((J + bn - 1) / bn) * 4);
     pr.nactive = cv.take<int32_t>(2 * 4);
     pr.alist = cv.take<int32_t>((size_t)J * 4);
+    // observation lattice and the learned term's vectors (tile_learn.cu)
+    pr.lat_info = cv.take<int32_t>(8 * 4);
+    pr.lat_tpos = cv.take<int32_t>((size_t)pr.d * 4);
+    pr.lat_nbr = cv.take<int32_t>((size_t)dp * kLatPts * 4);
+    if (o.learned_model) {
+      pr.learn_u = cv.take<float>((size_t)J * dp * 4);
+      pr.learn_on = cv.take<int32_t>((size_t)J * 4);
+    }
   }
 }
 
@@ -474,6 +482,12 @@ int run_batch(const info_esrf_problem* probs, int32_t count, const info_esrf_opt
     // the blocks, then each problem's PCG loop (host-driven) and the finish
     launch_tile_setup(tab, dtab, st);
     launch_quadrature(tab, dtab, st);
+    if (o.learned_model) {
+      // learned term on 2-D observation lattices: per-shift coefficients and
+      // the lattice's stencil tables
+      launch_learn_coef(tab, dtab, st);
+      launch_tile_lattice(tab, dtab, st);
+    }
     mark(1);
     launch_ritz(tab, dtab, st);
     mark(2);
@@ -597,6 +611,12 @@ int run_batch(const info_esrf_problem* probs, int32_t count, const info_esrf_opt
     s.ell_used = scal[2];
     s.gershgorin = scal[0];
     s.learned = !pr.learned_model ? 0 : (s.solver_path == 1 ? 1 : -1);
+    if (pr.learned_model && s.solver_path == 3) {   // applied where the observations form a 2-D lattice
+      int32_t lat_ok = 0;
+      if (cudaMemcpy(&lat_ok, pr.lat_info, sizeof(lat_ok), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return INFO_ESRF_ERR_CUDA;
+      s.learned = lat_ok == 1 ? 1 : -1;
+    }
     if (o.precision == INFO_ESRF_PRECISION_BF16) {
       int32_t nblocks = 0;
       if (cudaMemcpy(&nblocks, pr.rowptr + pr.nrt, sizeof(nblocks), cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -967,6 +987,53 @@ int info_esrf_krylov_capture(const info_esrf_grid* grid, int64_t N, const double
   cudaGetLastError();
   rc = launch_krylov_capture(tab, dpr, nsel, sel_dev, K, V_dev, Y_dev, Z_dev, feat_dev,
                              reinterpret_cast<cudaStream_t>(stream));
+  if (rc) return rc;
+  return cudaGetLastError() == cudaSuccess ? 0 : INFO_ESRF_ERR_CUDA;
+}
+
+int info_esrf_krylov_capture_lattice(const info_esrf_grid* grid, int64_t N, const double* X_dev, int64_t d,
+                                     const int64_t* obs_idx_dev, const double* R_diag_dev, int32_t Q,
+                                     const info_esrf_options* opt, void* workspace, size_t ws_bytes, int32_t nsel,
+                                     const int32_t* sel_dev, int32_t K, float* V_dev, float* Y_dev, float* Z_dev,
+                                     float* feat_dev, int32_t* Lx, int32_t* Ly, void* stream) {
+  if (nsel < 1 || K < 1 || !sel_dev || !V_dev || !Y_dev || !Z_dev || !feat_dev || !Lx || !Ly)
+    return INFO_ESRF_ERR_INVALID_ARG;
+  info_esrf_options o;
+  int rc = check_options(opt, &o);
+  if (rc) return rc;
+  if (o.precision != INFO_ESRF_PRECISION_BF16) return INFO_ESRF_ERR_UNSUPPORTED;
+  info_esrf_options o2 = o;
+  o2.learned_model = nullptr;   // the paper's preconditioner
+  ProblemDev* dpr;
+  ProblemDev hpr;
+  rc = prepare_one(grid, N, X_dev, d, obs_idx_dev, R_diag_dev, Q, &o2, workspace, ws_bytes, stream, false, &dpr,
+                   &hpr);
+  if (rc) return rc;
+  static thread_local ProblemTable tab;
+  tab.count = 1;
+  tab.p[0] = hpr;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaGetLastError();
+  launch_prepare(tab, dpr, st);
+  launch_anomalies(tab, dpr, st);
+  launch_tile_setup(tab, dpr, st);
+  launch_quadrature(tab, dpr, st);
+  launch_tile_lattice(tab, dpr, st);
+  launch_ritz(tab, dpr, st);
+  int32_t info[8] = {};
+  if (cudaMemcpyAsync(info, hpr.lat_info, sizeof(info), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return INFO_ESRF_ERR_CUDA;
+  if (info[0] != 1) return INFO_ESRF_ERR_UNSUPPORTED;   // the observations are not a 2-D lattice
+  *Lx = info[1];
+  *Ly = info[2];
+  TileCapture cap;
+  cap.nsel = nsel;
+  cap.K = K;
+  cap.sel = sel_dev;
+  cap.V = V_dev;
+  cap.Y = Y_dev;
+  rc = run_tile_pcg_capture(hpr, dpr, cap, Z_dev, feat_dev, st);
   if (rc) return rc;
   return cudaGetLastError() == cudaSuccess ? 0 : INFO_ESRF_ERR_CUDA;
 }

@@ -247,6 +247,17 @@ __device__ __forceinline__ FF ff_sqrt(FF g) { return ff_mul(g, ff_rsqrt(g)); }
 // summed with Knuth's TwoSum, so the dot product carries about 48 bits,
 // without issuing FP64 instructions in the inner loop.
 // ---------------------------------------------------------------------------
+// Features of the learned correction's network for shift sigma (learn.cu):
+// (log(sigma)/5, (log(sigma)/5)^2, log(mean diag C)/5, log(Gershgorin(C))/10),
+// single-precision logarithms (features of a small network; FP64 is slow here).
+__device__ __forceinline__ void learn_features(double sigma, double mean_diag, double gersh, float* phi) {
+  const float ls = logf((float)sigma) * 0.2f;
+  phi[0] = ls;
+  phi[1] = ls * ls;
+  phi[2] = logf(fmaxf((float)mean_diag, 1e-30f)) * 0.2f;
+  phi[3] = logf(fmaxf((float)gersh, 1e-30f)) * 0.1f;
+}
+
 template <typename T> struct DotAcc;
 
 template <> struct DotAcc<double> {

@@ -16,6 +16,16 @@ constexpr int kLearnTaps = 2 * kLearnH + 1;
 constexpr int kLearnOut = 1 + kLearnTaps;  // log a and the taps
 constexpr int kLearnT = 4 * kLearnH + 1;   // taps of S^T S
 constexpr int kLearnParams = 1810;    // network parameters (see learn.cu)
+constexpr int kLatPts = 25;           // points of the 2-D lattice stencil (dx^2 + dy^2 <= 8, the 5 x 5 square)
+constexpr int kLatBins = 6;           // its taps: one per squared length 0, 1, 2, 4, 5, 8
+// Point n of the lattice stencil: dx = n % 5 - 2, dy = n / 5 - 2; its tap is
+// the rank of dx^2 + dy^2 among 0, 1, 2, 4, 5, 8.
+__host__ __device__ inline int lat_dx(int n) { return n % 5 - 2; }
+__host__ __device__ inline int lat_dy(int n) { return n / 5 - 2; }
+__host__ __device__ inline int lat_bin(int n) {
+  const int dx = lat_dx(n), dy = lat_dy(n), r2 = dx * dx + dy * dy;
+  return r2 < 3 ? r2 : (r2 == 4 ? 3 : (r2 == 5 ? 4 : 5));
+}
 constexpr int kThreads = 256;         // CTA size of the persistent PCG kernel
 
 // Status bits written by kernels (ws status word 0).
@@ -52,6 +62,9 @@ struct TileMmArgs {
 int tile_chunk_width(int32_t J);
 int launch_tile_mm(TileMmArgs a, const void* chi, const void* clo, int64_t ntiles, cudaStream_t st);
 constexpr int kTileDotRows = 512;   // rows per partial dot product of the BF16 PCG
+// Dot values per system of the BF16 PCG: r^T r, f = Phi^T r, g = (C Phi)^T r,
+// then u^T u of the learned term.
+__host__ __device__ inline int tile_dot_values(int k) { return 2 * k + 2; }
 constexpr int kBcgMaxS = 64;        // block CG: largest block (members per node)
 struct ProblemDev;
 int run_bcg(const ProblemDev& p, const ProblemDev* dp, cudaStream_t st);
@@ -67,6 +80,27 @@ void launch_tile_ritz_matvec(const ProblemTable& tab, const ProblemDev* dtab, in
 // tensor-core matvec launches, from CUDA events on st around each launch.
 int run_tile_pcg(const ProblemDev& p, const ProblemDev* dp, cudaStream_t st, double* mm_ms, int* mm_count);
 void launch_tile_finish(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st);
+// Lattice of the observations of each BF16 problem with a learned model (or
+// for a capture): detection and the stencil tables (tile_learn.cu).
+void launch_tile_lattice(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st);
+// Krylov samples of the BF16 path (paper preconditioner): directions and
+// their images of the selected systems at iterations 1..K, in lattice order.
+struct TileCapture {
+  int32_t nsel, K;
+  const int32_t* sel;   // [nsel] systems q * N + i
+  float* V;             // [nsel * K][d]
+  float* Y;
+};
+int run_tile_pcg_capture(const ProblemDev& p, const ProblemDev* dp, const TileCapture& cap, float* Z, float* feat,
+                         cudaStream_t st);
+// u = S r for the listed learned systems, with partial sums of u^T u
+// (tile_learn.cu); stages of the BF16 PCG loop.
+void launch_tile_learn_u(const ProblemDev& p, const ProblemDev* dp, const int32_t* list, int64_t count, int nsub,
+                         cudaStream_t st);
+void launch_tile_capture_record(const ProblemDev& p, const ProblemDev* dp, const TileCapture& cap, int it,
+                                cudaStream_t st);
+void launch_tile_capture_finish(const ProblemDev& p, const ProblemDev* dp, const TileCapture& cap, float* Z,
+                                float* feat, cudaStream_t st);
 
 struct GridDev {
   int64_t ext[3];
@@ -181,6 +215,13 @@ struct ProblemDev {
   int32_t* chunk_active;        // [nchunks] 1 while a chunk of the tile matvec has a running system
   int32_t* nactive;             // [2] running systems; copy of status[0] for the host
   int32_t* alist;               // [J] the running systems (unordered), rebuilt every iteration
+  // learned correction on the BF16 path, for observations on every point of a
+  // periodic 2-D lattice (the stencil S over lattice offsets, see tile_learn.cu)
+  int32_t* lat_info;            // [8] device: ok, Lx, Ly, x0, y0, sx, sy, retries
+  int32_t* lat_tpos;            // [d] tile position of lattice point i + Lx j
+  int32_t* lat_nbr;             // [d_pad][kLatPts] tile positions of the stencil points of each row
+  float* learn_u;               // [J][d_pad] u = S r of the current residual (learned systems)
+  int32_t* learn_on;            // [J] 1: the system applies the learned term; 2: retry without it
   // block CG (solver 2): blocks = the mean system (one column) and one block of
   // N columns per node; vectors [nsys][d] of the bulk type, X is U
   int32_t bcg_nblocks, pad3_;

@@ -35,14 +35,6 @@ constexpr int kOW1 = 0, kOB1 = kOW1 + kHid * kIn, kOW2 = kOB1 + kHid, kOB2 = kOW
 static_assert(kOB3 + kLearnOut == kLearnParams, "parameter layout");
 }  // namespace
 
-__device__ __forceinline__ void learn_features(double sigma, double mean_diag, double gersh, float* phi) {
-  // single-precision logarithms (features of a small network; FP64 is slow here)
-  const float ls = logf((float)sigma) * 0.2f;
-  phi[0] = ls;
-  phi[1] = ls * ls;
-  phi[2] = logf(fmaxf((float)mean_diag, 1e-30f)) * 0.2f;
-  phi[3] = logf(fmaxf((float)gersh, 1e-30f)) * 0.1f;
-}
 
 // Forward pass by one thread (inference: a handful of shifts).
 __device__ void learn_forward_thread(const float* th, const float* phi, float* out) {
@@ -259,6 +251,163 @@ k_learn_loss_grad(const float* theta, int nsamp, int64_t d, const float* feat, c
     gout[0] = (float)(scale * (double)sa * sums[2]);
   }
   if (tid < kLearnTaps) gout[1 + tid] = (float)(scale * (sums[3 + tid] + sums[3 + kLearnTaps + tid])) * rs;
+  __syncthreads();
+  // backward through the network
+  float* g = G + (int64_t)s * kLearnParams;
+  for (int e2 = tid; e2 < kLearnOut * kHid; e2 += blockDim.x) {
+    const int o = e2 / kHid, j = e2 % kHid;
+    g[kOW3 + e2] = gout[o] * h2[j];
+  }
+  if (tid < kLearnOut) g[kOB3 + tid] = gout[tid];
+  if (tid < kHid) {
+    float gh = 0.f;
+    for (int o = 0; o < kLearnOut; ++o) gh = fmaf(th[kOW3 + o * kHid + tid], gout[o], gh);
+    ga2[tid] = gh * (1.f - h2[tid] * h2[tid]);
+  }
+  __syncthreads();
+  for (int e2 = tid; e2 < kHid * kHid; e2 += blockDim.x) {
+    const int i = e2 / kHid, j = e2 % kHid;
+    g[kOW2 + e2] = ga2[i] * h1[j];
+  }
+  if (tid < kHid) {
+    g[kOB2 + tid] = ga2[tid];
+    float gh = 0.f;
+    for (int i = 0; i < kHid; ++i) gh = fmaf(th[kOW2 + i * kHid + tid], ga2[i], gh);
+    ga1[tid] = gh * (1.f - h1[tid] * h1[tid]);
+  }
+  __syncthreads();
+  for (int e2 = tid; e2 < kHid * kIn; e2 += blockDim.x) {
+    const int i = e2 / kIn, c = e2 % kIn;
+    g[kOW1 + e2] = ga1[i] * phi[c];
+  }
+  if (tid < kHid) g[kOB1 + tid] = ga1[tid];
+}
+
+// ---------------------------------------------------------------------------
+// Loss and gradient of the 2-D lattice form (tile_learn.cu): S symmetric over
+// the 5 x 5 lattice offsets with one tap per squared length, so
+// e = a z + S S y - v and dL/dw_b = 2 (e^T B_b u + (S e)^T B_b y) / ||v||^2
+// with u = S y and B_b the 0/1 stencil of bin b.  One block per sample;
+// vectors (lattice order, i + Lx j) in global memory, u, e and S e in the
+// sample's slice of tmp.
+// ---------------------------------------------------------------------------
+// The 25 stencil points of lattice point a = i + Lx j (periodic), nb[n]:
+// a + dx + Lx dy away from the lattice edges, wrapped near them.
+__device__ __forceinline__ void lat_points(int a, int Lx, int Ly, const int (&off)[kLatPts], int (&nb)[kLatPts]) {
+  const int i = a % Lx, j = a / Lx;
+  if (i >= 2 && i < Lx - 2 && j >= 2 && j < Ly - 2) {
+#pragma unroll
+    for (int n = 0; n < kLatPts; ++n) nb[n] = a + off[n];
+  } else {
+#pragma unroll
+    for (int n = 0; n < kLatPts; ++n) {
+      int ii = (i + lat_dx(n)) % Lx, jj = (j + lat_dy(n)) % Ly;
+      ii = ii < 0 ? ii + Lx : ii;
+      jj = jj < 0 ? jj + Ly : jj;
+      nb[n] = ii + Lx * jj;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_learn_loss_grad_lat(const float* theta, int nsamp, int Lx, int Ly, const float* feat, const float* V,
+                      const float* Y, const float* Z, float* G, double* sample_loss, float* tmp) {
+  __shared__ float h1[kHid], h2[kHid], out[kLearnOut], gout[kLearnOut], ga2[kHid], ga1[kHid];
+  __shared__ float phi[kIn];
+  __shared__ float wsc[kLatBins];
+  constexpr int NV = 3 + kLatBins;
+  __shared__ double red_scratch[NV * (kThreads / 32)];
+  const int s = blockIdx.x;
+  const int tid = threadIdx.x;
+  if (s >= nsamp) return;
+  const int d = Lx * Ly;   // < 2^31 (checked by the host)
+  const float* th = theta;
+  if (tid < kIn) phi[tid] = feat[(int64_t)s * kIn + tid];
+  __syncthreads();
+  if (tid < kHid) {
+    float a = th[kOB1 + tid];
+    for (int c = 0; c < kIn; ++c) a = fmaf(th[kOW1 + tid * kIn + c], phi[c], a);
+    h1[tid] = tanhf(a);
+  }
+  __syncthreads();
+  if (tid < kHid) {
+    float a = th[kOB2 + tid];
+    for (int j = 0; j < kHid; ++j) a = fmaf(th[kOW2 + tid * kHid + j], h1[j], a);
+    h2[tid] = tanhf(a);
+  }
+  __syncthreads();
+  if (tid < kLearnOut) {
+    float a = th[kOB3 + tid];
+    for (int j = 0; j < kHid; ++j) a = fmaf(th[kOW3 + tid * kHid + j], h2[j], a);
+    out[tid] = a;
+  }
+  __syncthreads();
+  const float rs = expf(-2.5f * phi[0]);       // sigma^-1/2
+  if (tid < kLatBins) wsc[tid] = out[1 + tid] * rs;
+  __syncthreads();
+  const float sa = expf(out[0]) * rs * rs;
+  float w[kLatPts];
+  int off[kLatPts], nb[kLatPts];
+#pragma unroll
+  for (int n = 0; n < kLatPts; ++n) {
+    w[n] = wsc[lat_bin(n)];
+    off[n] = lat_dx(n) + Lx * lat_dy(n);
+  }
+  const float* y = Y + (int64_t)s * d;
+  const float* z = Z + (int64_t)s * d;
+  const float* v = V + (int64_t)s * d;
+  float* u = tmp + (int64_t)s * 3 * d;
+  float* e = u + d;
+  float* se = e + d;
+  for (int a = tid; a < d; a += blockDim.x) {   // u = S y
+    lat_points(a, Lx, Ly, off, nb);
+    float acc = 0.f;
+#pragma unroll
+    for (int n = 0; n < kLatPts; ++n) acc = fmaf(w[n], y[nb[n]], acc);
+    u[a] = acc;
+  }
+  __syncthreads();
+  for (int a = tid; a < d; a += blockDim.x) {   // e = a z + S u - v
+    lat_points(a, Lx, Ly, off, nb);
+    float acc = 0.f;
+#pragma unroll
+    for (int n = 0; n < kLatPts; ++n) acc = fmaf(w[n], u[nb[n]], acc);
+    e[a] = sa * z[a] + acc - v[a];
+  }
+  __syncthreads();
+  for (int a = tid; a < d; a += blockDim.x) {   // S e
+    lat_points(a, Lx, Ly, off, nb);
+    float acc = 0.f;
+#pragma unroll
+    for (int n = 0; n < kLatPts; ++n) acc = fmaf(w[n], e[nb[n]], acc);
+    se[a] = acc;
+  }
+  __syncthreads();
+  // ||v||^2, ||e||^2, e.z and per bin sum_{delta in bin} sum_a e_a u_{a+delta} + (S e)_a y_{a+delta}
+  DotAcc<float> acc[NV];
+  for (int a = tid; a < d; a += blockDim.x) {
+    acc[0].add_prod(v[a], v[a]);
+    acc[1].add_prod(e[a], e[a]);
+    acc[2].add_prod(e[a], z[a]);
+    lat_points(a, Lx, Ly, off, nb);
+    float bsum[kLatBins];
+#pragma unroll
+    for (int b = 0; b < kLatBins; ++b) bsum[b] = 0.f;
+#pragma unroll
+    for (int n = 0; n < kLatPts; ++n)
+      bsum[lat_bin(n)] = fmaf(e[a], u[nb[n]], fmaf(se[a], y[nb[n]], bsum[lat_bin(n)]));
+#pragma unroll
+    for (int b = 0; b < kLatBins; ++b) acc[3 + b].add(bsum[b]);
+  }
+  double sums[NV];
+  block_sum<NV>(acc, sums, red_scratch);
+  const double vv = sums[0] > 0 ? sums[0] : 1.0;
+  const double scale = 2.0 / ((double)nsamp * vv);
+  if (tid == 0) {
+    sample_loss[s] = sums[0] > 0 ? sums[1] / vv / (double)nsamp : 0.0;
+    gout[0] = sums[0] > 0 ? (float)(scale * (double)sa * sums[2]) : 0.f;
+  }
+  if (tid < kLearnTaps) gout[1 + tid] = (tid < kLatBins && sums[0] > 0) ? (float)(scale * sums[3 + tid]) * rs : 0.f;
   __syncthreads();
   // backward through the network
   float* g = G + (int64_t)s * kLearnParams;
@@ -532,6 +681,53 @@ int info_esrf_learn_loss_grad(const float* theta_dev, int32_t nsamp, int64_t d, 
   k_learn_reduce<<<(kLearnParams + 255) / 256, 256, 0, st>>>(nsamp, G, sl, grad_dev, loss_dev);
   note_launches(2);
   return cudaGetLastError() == cudaSuccess ? 0 : INFO_ESRF_ERR_CUDA;
+}
+
+size_t info_esrf_learn_lattice_scratch_size(int32_t nsamp, int64_t d) {
+  if (nsamp < 1 || d < 1) return 0;
+  return (size_t)nsamp * kLearnParams * sizeof(float) + (size_t)nsamp * sizeof(double) +
+         (size_t)nsamp * 3 * (size_t)d * sizeof(float) + 512;
+}
+
+int info_esrf_learn_loss_grad_lattice(const float* theta_dev, int32_t nsamp, int32_t Lx, int32_t Ly,
+                                      const float* feat_dev, const float* V_dev, const float* Y_dev,
+                                      const float* Z_dev, float* grad_dev, double* loss_dev, void* scratch_dev,
+                                      size_t scratch_bytes, void* stream) {
+  if (!theta_dev || nsamp < 1 || Lx < 1 || Ly < 1 || !feat_dev || !V_dev || !Y_dev || !Z_dev || !grad_dev)
+    return INFO_ESRF_ERR_INVALID_ARG;
+  const int64_t d = (int64_t)Lx * Ly;
+  if (d >= ((int64_t)1 << 31)) return INFO_ESRF_ERR_UNSUPPORTED;
+  if (!scratch_dev || scratch_bytes < info_esrf_learn_lattice_scratch_size(nsamp, d) ||
+      (reinterpret_cast<uintptr_t>(scratch_dev) % 16) != 0)
+    return INFO_ESRF_ERR_WORKSPACE;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  float* G = reinterpret_cast<float*>(scratch_dev);
+  double* sl = reinterpret_cast<double*>(G + (size_t)nsamp * kLearnParams);
+  uintptr_t t = reinterpret_cast<uintptr_t>(sl + nsamp);
+  t = (t + 255) & ~(uintptr_t)255;
+  float* tmp = reinterpret_cast<float*>(t);
+  cudaGetLastError();
+  k_learn_loss_grad_lat<<<nsamp, kThreads, 0, st>>>(theta_dev, nsamp, Lx, Ly, feat_dev, V_dev, Y_dev, Z_dev, G, sl,
+                                                     tmp);
+  k_learn_reduce<<<(kLearnParams + 255) / 256, 256, 0, st>>>(nsamp, G, sl, grad_dev, loss_dev);
+  note_launches(2);
+  return cudaGetLastError() == cudaSuccess ? 0 : INFO_ESRF_ERR_CUDA;
+}
+
+int info_esrf_learn_train_lattice(float* theta_dev, float* m_dev, float* v_dev, int32_t first_step, int32_t steps,
+                                  float lr, int32_t nsamp, int32_t Lx, int32_t Ly, const float* feat_dev,
+                                  const float* V_dev, const float* Y_dev, const float* Z_dev, float* grad_dev,
+                                  double* loss_hist_dev, void* scratch_dev, size_t scratch_bytes, void* stream) {
+  if (steps < 1 || first_step < 1) return INFO_ESRF_ERR_INVALID_ARG;
+  for (int t = 0; t < steps; ++t) {
+    int rc = info_esrf_learn_loss_grad_lattice(theta_dev, nsamp, Lx, Ly, feat_dev, V_dev, Y_dev, Z_dev, grad_dev,
+                                               loss_hist_dev ? loss_hist_dev + t : nullptr, scratch_dev,
+                                               scratch_bytes, stream);
+    if (rc) return rc;
+    rc = info_esrf_learn_adam_step(theta_dev, m_dev, v_dev, grad_dev, first_step + t, lr, stream);
+    if (rc) return rc;
+  }
+  return 0;
 }
 
 size_t info_esrf_learn_scratch_size(int32_t nsamp) {

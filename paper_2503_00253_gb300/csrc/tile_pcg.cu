@@ -14,6 +14,12 @@
 //      beta = rho' / rho (FP64);
 //   5. p_j = bf16(z_j + beta_j p_j), z = r - (C Phi) t + Phi c.
 //
+// Learned correction (2-D observation lattices with a model; tile_learn.cu):
+// after step 3, u = S r and u^T u; step 4 takes rho = a (r^T P^-1 r) + u^T u,
+// step 5 z = a P^-1 r + S u.  A learned system that breaks down or reaches
+// the iteration cap is solved again from the start without the term (plain
+// PCG as the fallback), after the other systems.
+//
 // The directions are stored in BF16 and the same BF16 vector enters the
 // matvec and the update of x (step 3), so x and r stay consistent:
 // r = b - C_q x up to the accuracy of the product (C kept as hi + lo BF16
@@ -46,12 +52,14 @@ __device__ __forceinline__ double sys_sigma(const ProblemDev& pr, int64_t j) {
   return pr.s[q] + 1.0;
 }
 
-// x = 0, r = b, p = 0 and the per-system state.
-__global__ void k_tpcg_init(const ProblemDev* dpr) {
+// x = 0, r = b, p = 0 and the per-system state (mode 0), or (mode 1) the
+// per-system state of the systems marked for a retry without the learned
+// term, whose vectors k_tpcg_retry_vectors has reset.
+__global__ void k_tpcg_init(const ProblemDev* dpr, int mode, int allow_learn) {
   const ProblemDev& pr = *dpr;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t J = pr.nsys;
-  if (i < J) {
+  if (i < J && (mode == 0 || pr.learn_on[i] == 2)) {
     double* sd = pr.sysd + i * 8;
     sd[kRho] = 0.0;
     sd[kAlpha] = 0.0;
@@ -63,8 +71,16 @@ __global__ void k_tpcg_init(const ProblemDev* dpr) {
     pr.active[i] = 1;
     pr.iters[i] = 0;
     pr.relres[i] = 0.0;
+    if (pr.learn_on) {
+      int on = 0;
+      if (mode == 0 && allow_learn && pr.learned_model && pr.lat_info[0] == 1) {
+        const int64_t q = i < pr.mean_sys ? pr.Q : (i - pr.mean_sys) / pr.N;
+        on = pr.learn_coef[q * kLearnOut] > 0.f ? 1 : 0;
+      }
+      pr.learn_on[i] = on;
+    }
   }
-  if (i >= J * pr.d_pad) return;
+  if (mode != 0 || i >= J * pr.d_pad) return;
   const int64_t j = i / pr.d_pad, a = i % pr.d_pad;
   float b = 0.f;
   const int32_t src = a < pr.d ? pr.tpos_src[a] : -1;
@@ -75,6 +91,31 @@ __global__ void k_tpcg_init(const ProblemDev* dpr) {
   pr.Xv[i] = 0.f;
   pr.Rv[i] = b;
   pr.Pdir[i] = __float2bfloat16_rn(0.f);
+}
+
+// x = 0, r = b, p = 0 for the systems marked for a retry (learn_on == 2).
+__global__ void k_tpcg_retry_vectors(const ProblemDev* dpr) {
+  const ProblemDev& pr = *dpr;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= pr.nsys * pr.d_pad) return;
+  const int64_t j = i / pr.d_pad, a = i % pr.d_pad;
+  if (pr.learn_on[j] != 2) return;
+  float b = 0.f;
+  const int32_t src = a < pr.d ? pr.tpos_src[a] : -1;
+  if (src >= 0) {
+    if (j < pr.mean_sys) b = (float)pr.bmean[src];
+    else b = pr.Wp[a * pr.N + (j - pr.mean_sys) % pr.N] * pr.rinvp[a];
+  }
+  pr.Xv[i] = 0.f;
+  pr.Rv[i] = b;
+  pr.Pdir[i] = __float2bfloat16_rn(0.f);
+}
+
+// A learned system that failed: stop it and mark it for the retry.
+__device__ __forceinline__ void mark_retry(const ProblemDev& pr, int64_t j) {
+  pr.active[j] = 0;
+  pr.learn_on[j] = 2;
+  atomicAdd(&pr.lat_info[7], 1);
 }
 
 // alpha_j = rho_j / p_j^T y_j (one warp per system: lanes over the row-tile
@@ -103,8 +144,12 @@ __global__ void k_tpcg_alpha(const ProblemDev* dpr, int it, int nchunks, int res
     pr.iters[j] = it;
   } else {
     sd[kAlpha] = 0.0;
-    pr.active[j] = 0;
-    atomicOr(&pr.status[0], kStatBreakdown);
+    if (pr.learn_on && pr.learn_on[j] == 1) {
+      mark_retry(pr, j);
+    } else {
+      pr.active[j] = 0;
+      atomicOr(&pr.status[0], kStatBreakdown);
+    }
   }
 }
 
@@ -172,7 +217,7 @@ __global__ void __launch_bounds__(kVecThreads) k_tpcg_update(const ProblemDev* d
   const ProblemDev& pr = *dpr;
   const int64_t sb = blockIdx.x;
   const int64_t g0 = (int64_t)blockIdx.y * kSys;
-  const int k = pr.kR, NV = 2 * k + 1, S2 = phi_stride(k);
+  const int k = pr.kR, NV = 2 * k + 1, NVD = tile_dot_values(k), S2 = phi_stride(k);
   const int64_t J = pr.nsys, dp = pr.d_pad;
   extern __shared__ float4 phs_dyn4[];   // [kDotRows][S2 / 4]
   float* phs = reinterpret_cast<float*>(phs_dyn4);
@@ -269,7 +314,7 @@ __global__ void __launch_bounds__(kVecThreads) k_tpcg_update(const ProblemDev* d
   const int64_t nsub = gridDim.x;
   for (int e = threadIdx.x; e < kSys * NV; e += blockDim.x) {
     const int ss = e / NV, v = e % NV;
-    if (sys[ss] >= 0) pr.dots[(sys[ss] * NV + v) * nsub + sb] = (double)part[ss][0][v];
+    if (sys[ss] >= 0) pr.dots[(sys[ss] * NVD + v) * nsub + sb] = (double)part[ss][0][v];
   }
 }
 
@@ -281,7 +326,7 @@ __global__ void __launch_bounds__(256) k_tpcg_reduce(const ProblemDev* dpr, int 
   const ProblemDev& pr = *dpr;
   const int64_t j = listed_system(list, count, blockIdx.x, pr.nsys);
   if (j >= pr.nsys || !pr.active[j]) return;
-  const int NV = 2 * pr.kR + 1;
+  const int NV = tile_dot_values(pr.kR);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int v = warp; v < NV; v += blockDim.x >> 5) {
     const double* src = pr.dots + (j * NV + v) * (int64_t)nsub;
@@ -299,8 +344,8 @@ __global__ void k_tpcg_scalars(const ProblemDev* dpr, int nsub, int bn, int last
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j == 0) pr.nactive[1] = pr.status[0];   // timeouts and overflow are set by earlier kernels
   if (j >= pr.nsys || !pr.active[j]) return;
-  const int k = pr.kR, NV = 2 * k + 1;
-  const double* v = pr.dsum + j * NV;   // r^T r, f = Phi^T r, g = (C Phi)^T r
+  const int k = pr.kR, NVD = tile_dot_values(k);
+  const double* v = pr.dsum + j * NVD;   // r^T r, f = Phi^T r, g = (C Phi)^T r, u^T u
   (void)nsub;
   double* sd = pr.sysd + j * 8;
   const double rr = v[0];
@@ -309,11 +354,20 @@ __global__ void k_tpcg_scalars(const ProblemDev* dpr, int nsub, int bn, int last
   sd[kRr] = rr;
   const double bn2 = sd[kBn2];
   pr.relres[j] = bn2 > 0.0 ? sqrt(rr / bn2) : 0.0;
+  const bool lrn = pr.learn_on && pr.learn_on[j] == 1;
   bool act = true;
   if (pr.fixed_iters <= 0 && !(rr > pr.tol * pr.tol * bn2)) act = false;
+  if (!isfinite(rr) && lrn) {
+    mark_retry(pr, j);
+    return;
+  }
   if (!(rr > 0.0) || !isfinite(rr)) act = false;
   if (last && act) {
     // iteration cap reached with the system still running
+    if (lrn && pr.fixed_iters <= 0) {
+      mark_retry(pr, j);
+      return;
+    }
     if (pr.fixed_iters <= 0) atomicOr(&pr.status[0], kStatNotConverged);
     act = false;
   }
@@ -348,6 +402,10 @@ __global__ void k_tpcg_scalars(const ProblemDev* dpr, int nsub, int bn, int last
     }
     rho = rr - gt + fc;
   }
+  if (lrn) {   // rho = r^T (a P^-1 + S S) r = a r^T P^-1 r + u^T u
+    const int64_t q = j < pr.mean_sys ? pr.Q : (j - pr.mean_sys) / pr.N;
+    rho = (double)pr.learn_coef[q * kLearnOut] * rho + v[2 * k + 1];
+  }
   sd[kBeta] = first ? 0.0 : rho / sd[kRho];
   sd[kRho] = rho;
   sd[kFirst] = 0.0;
@@ -357,7 +415,9 @@ __global__ void k_tpcg_scalars(const ProblemDev* dpr, int nsub, int bn, int last
 
 // Step 5: p = bf16(r - (C Phi) t + Phi c + beta p) for the running systems;
 // same CTA layout as step 3, the coefficients of all its systems staged once.
-__global__ void __launch_bounds__(kVecThreads) k_tpcg_direction(const ProblemDev* dpr) {
+// learned != 0: the dynamic buffer also holds the block's stencil table, and
+// a learned system takes z = a (r - (C Phi) t + Phi c) + S u.
+__global__ void __launch_bounds__(kVecThreads) k_tpcg_direction(const ProblemDev* dpr, int learned) {
   const ProblemDev& pr = *dpr;
   const int64_t sb = blockIdx.x;
   const int64_t g0 = (int64_t)blockIdx.y * kSys;
@@ -369,18 +429,36 @@ __global__ void __launch_bounds__(kVecThreads) k_tpcg_direction(const ProblemDev
   __shared__ float4 tc4[kSys][2 * kMaxK / 4];   // per system: c (Phi coefficients), then -t (C Phi)
   __shared__ int64_t sys[kSys];
   __shared__ float bes[kSys];
+  __shared__ int lon[kSys];
+  __shared__ float las[kSys], ltap[kSys][kLatBins];
   if (threadIdx.x < kSys) {
     const int64_t j = listed_system(pr.alist, count, g0 + threadIdx.x, J);
     const bool run = j < J && pr.active[j];
     sys[threadIdx.x] = run ? j : -1;
     bes[threadIdx.x] = run ? (float)pr.sysd[j * 8 + kBeta] : 0.f;
+    const bool on = learned && run && pr.learn_on[j] == 1;
+    lon[threadIdx.x] = on ? 1 : 0;
+    las[threadIdx.x] = 1.f;
+    if (on) {
+      const int64_t q = j < pr.mean_sys ? pr.Q : (j - pr.mean_sys) / pr.N;
+      las[threadIdx.x] = pr.learn_coef[q * kLearnOut];
+      for (int b = 0; b < kLatBins; ++b) ltap[threadIdx.x][b] = pr.learn_coef[q * kLearnOut + 1 + b];
+    }
   }
   __syncthreads();
-  bool any = false;
-  for (int s = 0; s < kSys; ++s) any |= sys[s] >= 0;
+  bool any = false, anyl = false;
+  for (int s = 0; s < kSys; ++s) {
+    any |= sys[s] >= 0;
+    anyl |= lon[s] != 0;
+  }
   if (!any) return;
   const int64_t abase = sb * kDotRows;
   stage_phi(pr, abase, k, S2, phs);
+  int32_t* nbr_s = reinterpret_cast<int32_t*>(phs + kDotRows * S2);   // [kDotRows][kLatPts]
+  if (anyl) {
+    const int64_t nrow = dp - abase < kDotRows ? dp - abase : kDotRows;
+    for (int64_t e = threadIdx.x; e < nrow * kLatPts; e += blockDim.x) nbr_s[e] = pr.lat_nbr[abase * kLatPts + e];
+  }
   float* tcf = reinterpret_cast<float*>(tc4);
   for (int e = threadIdx.x; e < kSys * 2 * kMaxK; e += blockDim.x) {
     const int s = e / (2 * kMaxK), m = e % (2 * kMaxK);
@@ -397,6 +475,12 @@ __global__ void __launch_bounds__(kVecThreads) k_tpcg_direction(const ProblemDev
   const int64_t j = sys[s];
   if (j < 0) return;
   const float be = bes[s];
+  const bool sl = lon[s] != 0;
+  const float la = las[s];
+  float w[kLatPts];
+#pragma unroll
+  for (int n = 0; n < kLatPts; ++n) w[n] = sl ? ltap[s][lat_bin(n)] : 0.f;
+  const float* u = pr.learn_u + j * dp;
   for (int r4 = 4 * r0; r4 < kDotRows; r4 += 4 * kRowLanes) {   // four rows per step
     const int64_t a = abase + r4;
     if (a >= dp) break;
@@ -420,6 +504,13 @@ __global__ void __launch_bounds__(kVecThreads) k_tpcg_direction(const ProblemDev
           z[i] = fmaf(f.w, c.w, z[i]);
         }
       }
+      if (sl) {   // z = a P^-1 r + S u
+        const int32_t* nb = nbr_s + (r4 + i) * kLatPts;
+        float su = 0.f;
+#pragma unroll
+        for (int n = 0; n < kLatPts; ++n) su = fmaf(w[n], __ldg(u + nb[n]), su);
+        z[i] = fmaf(la, z[i], su);
+      }
       z[i] = (a + i < pr.d) ? fmaf(be, pv[i], z[i]) : 0.f;
     }
     __nv_bfloat162 out[2] = {__floats2bfloat162_rn(z[0], z[1]), __floats2bfloat162_rn(z[2], z[3])};
@@ -431,8 +522,11 @@ __global__ void __launch_bounds__(kVecThreads) k_tpcg_direction(const ProblemDev
 
 // Runs the PCG of one BF16 problem (host copy p, device copy dp) to
 // convergence or the iteration cap.  Synchronizes the stream once per
-// iteration to read the number of running systems.
-int run_tile_pcg(const ProblemDev& p, const ProblemDev* dp, cudaStream_t st, double* mm_ms, int* mm_count) {
+// iteration to read the number of running systems.  cap != NULL: records the
+// Krylov samples of its systems at iterations 1..cap->K and stops after K
+// iterations, without the learned term.
+static int tile_pcg_loop(const ProblemDev& p, const ProblemDev* dp, cudaStream_t st, double* mm_ms, int* mm_count,
+                         const TileCapture* cap) {
   const int64_t J = p.nsys;
   if (J < 1) return 0;
   cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -477,60 +571,106 @@ int run_tile_pcg(const ProblemDev& p, const ProblemDev* dp, cudaStream_t st, dou
   ta.J = (int32_t)J;
   ta.nrt = p.nrt;
   ta.pty_by_system = 1;
-  const int maxit = p.fixed_iters > 0 ? p.fixed_iters : p.max_iter;
+  int maxit = p.fixed_iters > 0 ? p.fixed_iters : p.max_iter;
+  if (cap) maxit = cap->K;
+  // the learned term is possible when the problem has a model and its tables
+  const bool learned = !cap && p.learned_model && p.learn_on && p.lat_info;
   const size_t vsm = (size_t)kDotRows * phi_stride(p.kR) * sizeof(float);
+  const size_t dsm = vsm + (learned ? (size_t)kDotRows * kLatPts * sizeof(int32_t) : 0);
   const bool wide = 2 * p.kR > 28;   // k > 14: 64-value dot vectors (the 32-value loop covers 28 columns)
   static thread_local int raised = -1;
   int dev = 0;
   cudaGetDevice(&dev);
   if (raised != dev) {
     const int mx = (int)((size_t)kDotRows * phi_stride(kMaxK) * sizeof(float));
+    const int mxd = mx + kDotRows * kLatPts * (int)sizeof(int32_t);
     if (cudaFuncSetAttribute(k_tpcg_update<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess ||
         cudaFuncSetAttribute(k_tpcg_update<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess ||
-        cudaFuncSetAttribute(k_tpcg_direction, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess)
+        cudaFuncSetAttribute(k_tpcg_direction, cudaFuncAttributeMaxDynamicSharedMemorySize, mxd) != cudaSuccess)
       return INFO_ESRF_ERR_CUDA;
     raised = dev;
   }
   int32_t host[2] = {0, 0};
-  k_tpcg_init<<<gall, 256, 0, st>>>(dp);
   auto update = [&](dim3 grid, int upd, const int32_t* list, int64_t count) {
     if (wide) k_tpcg_update<2><<<grid, kVecThreads, vsm, st>>>(dp, upd, list, count);
     else k_tpcg_update<1><<<grid, kVecThreads, vsm, st>>>(dp, upd, list, count);
   };
-  update(gvec, 0, nullptr, J);
-  k_tpcg_reduce<<<(unsigned)J, 256, 0, st>>>(dp, nsub, nullptr, J);
   const dim3 galpha((unsigned)(((32 * J > nchunks ? 32 * J : nchunks) + 255) / 256));
-  k_tpcg_alpha<<<galpha, 256, 0, st>>>(dp, 0, nchunks, 1);   // resets the chunk flags and the count
-  k_tpcg_scalars<<<gsys, 128, 0, st>>>(dp, nsub, bn, maxit <= 0 ? 1 : 0);
-  k_tpcg_direction<<<gvec, kVecThreads, vsm, st>>>(dp);
-  note_launches(6);
-  for (int it = 1; it <= maxit; ++it) {
-    // running systems (and the status word) after the previous iteration
-    if (cudaMemcpyAsync(host, p.nactive, sizeof(host), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+  // the first direction of every running system: r = b, z = M r, p = z
+  auto start = [&]() {
+    update(gvec, 0, nullptr, J);
+    if (learned) launch_tile_learn_u(p, dp, nullptr, J, nsub, st);
+    k_tpcg_reduce<<<(unsigned)J, 256, 0, st>>>(dp, nsub, nullptr, J);
+    k_tpcg_alpha<<<galpha, 256, 0, st>>>(dp, 0, nchunks, 1);   // resets the chunk flags and the count
+    k_tpcg_scalars<<<gsys, 128, 0, st>>>(dp, nsub, bn, maxit <= 0 ? 1 : 0);
+    k_tpcg_direction<<<gvec, kVecThreads, dsm, st>>>(dp, learned ? 1 : 0);
+    note_launches(5);
+  };
+  auto iterate = [&]() -> int {
+    for (int it = 1; it <= maxit; ++it) {
+      // running systems (and the status word) after the previous iteration
+      if (cudaMemcpyAsync(host, p.nactive, sizeof(host), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess)
+        return INFO_ESRF_ERR_CUDA;
+      read_time();   // the previous launch has completed (stream synchronized)
+      if (host[0] == 0) break;
+      if (host[1] & (kStatTimeout | kStatTileOverflow)) break;
+      const int64_t nrun = host[0];
+      const dim3 glist((unsigned)nsub, (unsigned)((nrun + kSys - 1) / kSys));
+      if (mm_ms) cudaEventRecord(ev[0], st);
+      if (launch_tile_mm(ta, p.Chi, p.Clo, p.tile_cap, st) != 0) return INFO_ESRF_ERR_CUDA;
+      if (mm_ms) {
+        cudaEventRecord(ev[1], st);
+        timed = true;
+      }
+      if (cap) launch_tile_capture_record(p, dp, *cap, it, st);
+      k_tpcg_alpha<<<galpha, 256, 0, st>>>(dp, it, nchunks, 0);
+      update(glist, 1, p.alist, nrun);
+      if (learned) launch_tile_learn_u(p, dp, p.alist, nrun, nsub, st);
+      k_tpcg_reduce<<<(unsigned)nrun, 256, 0, st>>>(dp, nsub, p.alist, nrun);
+      k_tpcg_scalars<<<gsys, 128, 0, st>>>(dp, nsub, bn, it == maxit ? 1 : 0);
+      k_tpcg_direction<<<glist, kVecThreads, dsm, st>>>(dp, learned ? 1 : 0);
+      note_launches(5);
+    }
+    return 0;
+  };
+  k_tpcg_init<<<gall, 256, 0, st>>>(dp, 0, learned ? 1 : 0);
+  note_launches(1);
+  start();
+  int rc = iterate();
+  if (rc) return rc;
+  if (learned) {
+    // plain PCG for the learned systems that broke down or hit the cap
+    int32_t retries = 0;
+    if (cudaMemcpyAsync(&retries, p.lat_info + 7, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
       return INFO_ESRF_ERR_CUDA;
-    read_time();   // the previous launch has completed (stream synchronized)
-    if (host[0] == 0) break;
-    if (host[1] & (kStatTimeout | kStatTileOverflow)) break;
-    const int64_t nrun = host[0];
-    const dim3 glist((unsigned)nsub, (unsigned)((nrun + kSys - 1) / kSys));
-    if (mm_ms) cudaEventRecord(ev[0], st);
-    if (launch_tile_mm(ta, p.Chi, p.Clo, p.tile_cap, st) != 0) return INFO_ESRF_ERR_CUDA;
-    if (mm_ms) {
-      cudaEventRecord(ev[1], st);
-      timed = true;
+    read_time();
+    if (retries > 0) {
+      k_tpcg_retry_vectors<<<gall, 256, 0, st>>>(dp);
+      k_tpcg_init<<<gsys, 128, 0, st>>>(dp, 1, 0);
+      note_launches(2);
+      start();
+      rc = iterate();
+      if (rc) return rc;
     }
-    k_tpcg_alpha<<<galpha, 256, 0, st>>>(dp, it, nchunks, 0);
-    update(glist, 1, p.alist, nrun);
-    k_tpcg_reduce<<<(unsigned)nrun, 256, 0, st>>>(dp, nsub, p.alist, nrun);
-    k_tpcg_scalars<<<gsys, 128, 0, st>>>(dp, nsub, bn, it == maxit ? 1 : 0);
-    k_tpcg_direction<<<glist, kVecThreads, vsm, st>>>(dp);
-    note_launches(5);
   }
   if (timed) {
     if (cudaEventSynchronize(ev[1]) != cudaSuccess) return INFO_ESRF_ERR_CUDA;
     read_time();
   }
+  return cudaGetLastError() == cudaSuccess ? 0 : INFO_ESRF_ERR_CUDA;
+}
+
+int run_tile_pcg(const ProblemDev& p, const ProblemDev* dp, cudaStream_t st, double* mm_ms, int* mm_count) {
+  return tile_pcg_loop(p, dp, st, mm_ms, mm_count, nullptr);
+}
+
+int run_tile_pcg_capture(const ProblemDev& p, const ProblemDev* dp, const TileCapture& cap, float* Z, float* feat,
+                         cudaStream_t st) {
+  const int rc = tile_pcg_loop(p, dp, st, nullptr, nullptr, &cap);
+  if (rc) return rc;
+  launch_tile_capture_finish(p, dp, cap, Z, feat, st);
   return cudaGetLastError() == cudaSuccess ? 0 : INFO_ESRF_ERR_CUDA;
 }
 

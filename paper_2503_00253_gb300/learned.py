@@ -4,7 +4,9 @@ The correction M_q = a_q P_q^-1 + S_q^T S_q and its network are described in
 include/info_esrf_stages.h.  This module only orchestrates library calls:
 Krylov samples are captured from the method's own PCG runs on training
 problems (info_esrf_krylov_capture), and the network is trained by the
-library's forward, backward and Adam kernels (info_esrf_learn_train).
+library's forward, backward and Adam kernels (info_esrf_learn_train).  The
+2-D lattice form (BF16 path) uses info_esrf_krylov_capture_lattice and
+info_esrf_learn_train_lattice the same way (fit_lattice).
 """
 from __future__ import annotations
 
@@ -105,3 +107,58 @@ def fit(train_problems, K: int = 12, members_per_q: int = 3, steps: int = 300, l
     V, Y, Z, feat = capture(train_problems, K=K, members_per_q=members_per_q)
     theta, hist = train(V, Y, Z, feat, steps=steps, lr=lr, seed=seed)
     return theta, choose_max_shift(theta, train_problems), hist
+
+
+def capture_lattice(problems, K: int = 12, members_per_q: int = 3, ritz_rank: int = 10, device="cuda"):
+    """Krylov samples (V, Y, Z, feat) of the BF16 path from each 2-D problem, and the common lattice shape."""
+    parts, shape = [], None
+    for idx, pr in enumerate(problems):
+        opts = B.make_options(precision=B.PRECISION_BF16, ritz_rank=ritz_rank)
+        X = torch.tensor(pr.X, device=device)
+        obs = torch.tensor(pr.obs_idx, device=device)
+        R = torch.tensor(pr.R, device=device)
+        sel = select_systems(pr.N, pr.Q, members_per_q, seed=idx)
+        V, Y, Z, feat, lx, ly = B.krylov_capture_lattice(pr.grid, X, obs, R, pr.Q, sel, K, opts)
+        if shape is not None and shape != (lx, ly):
+            raise ValueError("training problems on different lattices")
+        shape = (lx, ly)
+        parts.append((V, Y, Z, feat))
+    return tuple(torch.cat([p[i] for p in parts], 0) for i in range(4)) + shape
+
+
+def system_iterations_bf16(pr, theta=None, max_shift: float = 0.0, ritz_rank: int = 10, device="cuda"):
+    """Per-system iterations of one BF16 analysis, with the lattice-form model or without."""
+    o = B.make_options(precision=B.PRECISION_BF16, ritz_rank=ritz_rank, learned_model=theta,
+                       learned_max_shift=max_shift)
+    return system_iterations(pr, o, device=device)
+
+
+def choose_max_shift_bf16(theta, problems, ritz_rank: int = 10):
+    """As choose_max_shift, on the BF16 path (the lattice form)."""
+    shifts, gain = None, None
+    for pr in problems:
+        it0, st = system_iterations_bf16(pr, None, 0.0, ritz_rank)
+        it1, _ = system_iterations_bf16(pr, theta, 0.0, ritz_rank)
+        s, _ = B.info_esrf_quadrature_nodes(pr.Q, st["ell_used"])
+        sig = s.cpu().numpy() + 1.0
+        g = np.array([it1[1 + q * pr.N:1 + (q + 1) * pr.N].sum() - it0[1 + q * pr.N:1 + (q + 1) * pr.N].sum()
+                      for q in range(pr.Q)], dtype=np.float64)
+        g[0] += it1[0] - it0[0]
+        shifts = sig if shifts is None else shifts
+        gain = g if gain is None else gain + g
+    best_c, best, acc = -1, 0.0, 0.0
+    for c in range(len(gain)):
+        acc += gain[c]
+        if acc < best:
+            best, best_c = acc, c
+    return 0.5 if best_c < 0 else float(shifts[best_c]) * (1.0 + 1e-9)
+
+
+def fit_lattice(train_problems, K: int = 12, members_per_q: int = 3, steps: int = 300, lr: float = 3e-3,
+                seed: int = 0):
+    """Capture, train and judge the 2-D lattice form on BF16 problems: returns (theta, max_shift, loss history)."""
+    V, Y, Z, feat, lx, ly = capture_lattice(train_problems, K=K, members_per_q=members_per_q)
+    theta = init_params(seed, device=V.device)
+    hist, _ = B.learn_train_lattice(theta, feat, V, Y, Z, lx, ly, steps, lr)
+    return theta, choose_max_shift_bf16(theta, train_problems), hist.cpu().numpy()
+
