@@ -273,7 +273,7 @@ void carve_problem(Carver& cv, ProblemDev& pr, const info_esrf_options& o) {
     pr.nactive = cv.take<int32_t>(2 * 4);
     pr.alist = cv.take<int32_t>((size_t)J * 4);
     // observation lattice and the learned term's vectors (tile_learn.cu)
-    pr.lat_info = cv.take<int32_t>(8 * 4);
+    pr.lat_info = cv.take<int32_t>(16 * 4);
     pr.lat_tpos = cv.take<int32_t>((size_t)pr.d * 4);
     pr.lat_nbr = cv.take<int32_t>((size_t)dp * kLatPts * 4);
     if (o.learned_model) {

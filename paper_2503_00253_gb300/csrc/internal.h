@@ -217,7 +217,7 @@ struct ProblemDev {
   int32_t* alist;               // [J] the running systems (unordered), rebuilt every iteration
   // learned correction on the BF16 path, for observations on every point of a
   // periodic 2-D lattice (the stencil S over lattice offsets, see tile_learn.cu)
-  int32_t* lat_info;            // [8] device: ok, Lx, Ly, x0, y0, sx, sy, retries
+  int32_t* lat_info;            // [16] device: ok, Lx, Ly, x0, y0, sx, sy, retries, learned systems
   int32_t* lat_tpos;            // [d] tile position of lattice point i + Lx j
   int32_t* lat_nbr;             // [d_pad][kLatPts] tile positions of the stencil points of each row
   float* learn_u;               // [J][d_pad] u = S r of the current residual (learned systems)

@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(1024) k_lat_scan(const ProblemDev* tab) {
   }
   __syncthreads();
   if (!ok) {
-    if (threadIdx.x < 8) pr.lat_info[threadIdx.x] = 0;
+    if (threadIdx.x < 16) pr.lat_info[threadIdx.x] = 0;
     return;
   }
   int64_t org[2], gap[2];
@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(1024) k_lat_scan(const ProblemDev* tab) {
     pr.lat_info[5] = (int32_t)sx;
     pr.lat_info[6] = (int32_t)sy;
     pr.lat_info[7] = 0;
+    pr.lat_info[8] = 0;
   }
 }
 

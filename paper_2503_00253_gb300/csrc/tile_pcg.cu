@@ -76,6 +76,7 @@ __global__ void k_tpcg_init(const ProblemDev* dpr, int mode, int allow_learn) {
       if (mode == 0 && allow_learn && pr.learned_model && pr.lat_info[0] == 1) {
         const int64_t q = i < pr.mean_sys ? pr.Q : (i - pr.mean_sys) / pr.N;
         on = pr.learn_coef[q * kLearnOut] > 0.f ? 1 : 0;
+        if (on) atomicAdd(&pr.lat_info[8], 1);
       }
       pr.learn_on[i] = on;
     }
@@ -574,9 +575,9 @@ static int tile_pcg_loop(const ProblemDev& p, const ProblemDev* dp, cudaStream_t
   int maxit = p.fixed_iters > 0 ? p.fixed_iters : p.max_iter;
   if (cap) maxit = cap->K;
   // the learned term is possible when the problem has a model and its tables
-  const bool learned = !cap && p.learned_model && p.learn_on && p.lat_info;
+  bool learned = !cap && p.learned_model && p.learn_on && p.lat_info;
   const size_t vsm = (size_t)kDotRows * phi_stride(p.kR) * sizeof(float);
-  const size_t dsm = vsm + (learned ? (size_t)kDotRows * kLatPts * sizeof(int32_t) : 0);
+  size_t dsm = vsm;   // + the stencil table while learned systems run (set below)
   const bool wide = 2 * p.kR > 28;   // k > 14: 64-value dot vectors (the 32-value loop covers 28 columns)
   static thread_local int raised = -1;
   int dev = 0;
@@ -636,6 +637,14 @@ static int tile_pcg_loop(const ProblemDev& p, const ProblemDev* dp, cudaStream_t
   };
   k_tpcg_init<<<gall, 256, 0, st>>>(dp, 0, learned ? 1 : 0);
   note_launches(1);
+  if (learned) {   // systems that use the term (none: the plain loop)
+    int32_t nl = 0;
+    if (cudaMemcpyAsync(&nl, p.lat_info + 8, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return INFO_ESRF_ERR_CUDA;
+    learned = nl > 0;
+  }
+  if (learned) dsm = vsm + (size_t)kDotRows * kLatPts * sizeof(int32_t);
   start();
   int rc = iterate();
   if (rc) return rc;
