@@ -197,7 +197,8 @@ int info_esrf_learn_train_lattice(float* theta_dev, float* m_dev, float* v_dev, 
  * right-hand sides, recording for each of the nsel systems sel_dev[]
  * (number q * N + i) and iteration v = p / ||p||, y = (sigma p + C p) / ||p||
  * (p the BF16 direction the matvec used), z = P_q^-1 y and phi; all zero for
- * a system that stopped before that iteration.  Outputs [nsel * K][d] and
+ * a system that stopped (residual at 1e-6 of its right-hand side) before that
+ * iteration.  Outputs [nsel * K][d] and
  * [nsel * K][4] float in lattice order, *Lx and *Ly the lattice shape.
  * INFO_ESRF_ERR_UNSUPPORTED when the observations are not a 2-D lattice. */
 int info_esrf_krylov_capture_lattice(const info_esrf_grid* grid, int64_t N, const double* X_dev, int64_t d,

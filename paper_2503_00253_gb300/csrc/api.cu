@@ -272,6 +272,12 @@ void carve_problem(Carver& cv, ProblemDev& pr, const info_esrf_options& o) {
     pr.chunk_active = cv.take<int32_t>((size_t)((J + bn - 1) / bn) * 4);
     pr.nactive = cv.take<int32_t>(2 * 4);
     pr.alist = cv.take<int32_t>((size_t)J * 4);
+    // operand planes of the tensor-core state update (tile_state.cu)
+    pr.st_NV = (int32_t)((N + 15) / 16 * 16);
+    pr.st_W = cv.take<__nv_bfloat16>((size_t)3 * dp * kStK * 2);
+    pr.st_V = cv.take<__nv_bfloat16>((size_t)2 * pr.st_NV * dp * 2);
+    pr.st_vm = cv.take<float>((size_t)dp * 4);
+    pr.st_xyz = cv.take<int4>((size_t)dp * 16);
     // observation lattice and the learned term's vectors (tile_learn.cu)
     pr.lat_info = cv.take<int32_t>(16 * 4);
     pr.lat_tpos = cv.take<int32_t>((size_t)pr.d * 4);
@@ -863,13 +869,13 @@ int info_esrf_quadrature_nodes(int32_t Q, double ell, int32_t rule, double* s_de
 static int prepare_one(const info_esrf_grid* grid, int64_t N, const double* X_dev, int64_t d,
                        const int64_t* obs_idx_dev, const double* R_diag_dev, int32_t Q,
                        const info_esrf_options* opt_in, void* ws, size_t ws_bytes, void* stream, bool run,
-                       ProblemDev** dpr, ProblemDev* hpr) {
+                       ProblemDev** dpr, ProblemDev* hpr, double tol = 1.0) {
   info_esrf_options o;
   int rc = check_options(opt_in, &o);
   if (rc) return rc;
   if (!ws || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0) return INFO_ESRF_ERR_WORKSPACE;
   static double dummy;
-  info_esrf_problem P = one_problem(grid, N, X_dev, d, obs_idx_dev, nullptr, R_diag_dev, Q, 1.0, nullptr, &dummy);
+  info_esrf_problem P = one_problem(grid, N, X_dev, d, obs_idx_dev, nullptr, R_diag_dev, Q, tol, nullptr, &dummy);
   static thread_local ProblemTable tab;
   size_t need = 0;
   ProblemDev* dtab = nullptr;
@@ -1006,8 +1012,9 @@ int info_esrf_krylov_capture_lattice(const info_esrf_grid* grid, int64_t N, cons
   o2.learned_model = nullptr;   // the paper's preconditioner
   ProblemDev* dpr;
   ProblemDev hpr;
+  // a system stops recording once its residual is at 1e-6 of the right-hand side
   rc = prepare_one(grid, N, X_dev, d, obs_idx_dev, R_diag_dev, Q, &o2, workspace, ws_bytes, stream, false, &dpr,
-                   &hpr);
+                   &hpr, 1e-6);
   if (rc) return rc;
   static thread_local ProblemTable tab;
   tab.count = 1;

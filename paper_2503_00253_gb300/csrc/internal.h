@@ -61,6 +61,7 @@ struct TileMmArgs {
 // Systems per CTA of the tile matvec for J systems (128 or 256).
 int tile_chunk_width(int32_t J);
 int launch_tile_mm(TileMmArgs a, const void* chi, const void* clo, int64_t ntiles, cudaStream_t st);
+constexpr int kStK = 128;           // member slots of the tensor-core state update (N <= 128)
 constexpr int kTileDotRows = 512;   // rows per partial dot product of the BF16 PCG
 // Dot values per system of the BF16 PCG: r^T r, f = Phi^T r, g = (C Phi)^T r,
 // then u^T u of the learned term.
@@ -80,6 +81,9 @@ void launch_tile_ritz_matvec(const ProblemTable& tab, const ProblemDev* dtab, in
 // tensor-core matvec launches, from CUDA events on st around each launch.
 int run_tile_pcg(const ProblemDev& p, const ProblemDev* dp, cudaStream_t st, double* mm_ms, int* mm_count);
 void launch_tile_finish(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st);
+// The state update on the tensor cores (tile_state.cu): 0 when launched for
+// every BF16 problem; otherwise the caller runs the CUDA-core kernel.
+int launch_tile_state_mma(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st);
 // Lattice of the observations of each BF16 problem with a learned model (or
 // for a capture): detection and the stencil tables (tile_learn.cu).
 void launch_tile_lattice(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st);
@@ -222,6 +226,13 @@ struct ProblemDev {
   int32_t* lat_nbr;             // [d_pad][kLatPts] tile positions of the stencil points of each row
   float* learn_u;               // [J][d_pad] u = S r of the current residual (learned systems)
   int32_t* learn_on;            // [J] 1: the system applies the learned term; 2: retry without it
+  // state update on the tensor cores (tile_state.cu): BF16 hi and lo planes
+  // of the operands in tile order, made by the finish
+  __nv_bfloat16* st_W;          // [3][d_pad][kStK] W in three planes, members padded to kStK
+  __nv_bfloat16* st_V;          // [2][st_NV][d_pad] Vbar^T of the members, padded to st_NV columns
+  float* st_vm;                 // [d_pad] the mean column of Vbar
+  int4* st_xyz;                 // [d_pad] grid coordinates of each tile position (w = -1: padding)
+  int32_t st_NV, pad4_;
   // block CG (solver 2): blocks = the mean system (one column) and one block of
   // N columns per node; vectors [nsys][d] of the bulk type, X is U
   int32_t bcg_nblocks, pad3_;

@@ -208,37 +208,6 @@ __global__ void __launch_bounds__(128, 1)
   if (warp == 2) tmem_dealloc(tmem, kCols);
 }
 
-using EncodeFn = PFN_cuTensorMapEncodeTiled_v12000;
-
-EncodeFn encoder() {
-  static EncodeFn fn = [] {
-    void* f = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
-            cudaSuccess ||
-        q != cudaDriverEntryPointSuccess) {
-      cudaGetLastError();
-      f = nullptr;
-    }
-    return reinterpret_cast<EncodeFn>(f);
-  }();
-  return fn;
-}
-
-// Row-major BF16 matrix [rows][cols] (row stride in elements), boxes of
-// box_rows x 64 columns with the 128-byte swizzle.
-bool encode_bf16(CUtensorMap* m, const void* base, uint64_t cols, uint64_t rows, uint64_t stride, uint32_t box_rows) {
-  EncodeFn enc = encoder();
-  if (!enc || !base || (reinterpret_cast<uintptr_t>(base) & 15) || (stride * 2) % 16) return false;
-  const cuuint64_t dims[2] = {cols, rows};
-  const cuuint64_t strides[1] = {stride * 2};
-  const cuuint32_t box[2] = {(cuuint32_t)kTileK, box_rows};
-  const cuuint32_t estr[2] = {1, 1};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 template <int BN, int S, int H>
 int launch_tile_mm_t(TileMmArgs a, const void* chi, const void* clo, int64_t ntiles, cudaStream_t st) {
   using Shape = TileMmShape<BN, S, H>;

@@ -723,8 +723,13 @@ void launch_tile_finish(const ProblemTable& tab, const ProblemDev* dtab, cudaStr
     Nmax = p.N > Nmax ? p.N : Nmax;
   }
   k_tile_accumulate<<<dim3((unsigned)((dn1 + 255) / 256), tab.count), 256, 0, st>>>(dtab);
-  k_tile_state_apply<<<dim3((unsigned)nst, tab.count), 256, state_smem(Nmax), st>>>(dtab);
-  note_launches(2);
+  note_launches(1);
+  // the state update on the tensor cores (tile_state.cu) where every problem
+  // qualifies, else on the CUDA cores
+  if (launch_tile_state_mma(tab, dtab, st) == -1) {
+    k_tile_state_apply<<<dim3((unsigned)nst, tab.count), 256, state_smem(Nmax), st>>>(dtab);
+    note_launches(1);
+  }
 }
 
 }  // namespace infoesrf

@@ -1,0 +1,491 @@
+// a10, BF16 path, on the fifth-generation tensor cores: the state update
+//     z_a(x) = z(x) - sum_b Sxh(x, b) vbar_b,  Sxh(x, b) = GC(r_xb) (z_x . w_b)
+// (Sec. 2.3 model-space localization with Eq. localized_state_covar; vbar
+// from the quadrature accumulation).  Per state tile (128 consecutive grid
+// points) and stored column block (64 tile-ordered observations within the
+// Gaspari-Cohn support), two dense products:
+//     S   = Z_tile W_blk^T        128 x 64, K = members (padded to kStK)
+//     acc += (GC o S) Vbar_blk    128 x NV, K = 64 observations (the members' columns)
+// as tcgen05.mma kind::f16 with FP32 accumulation in tensor memory.
+// Precision: z . w sums members' products of both signs, so S is formed from
+// three BF16 planes of each operand (h = bf16(a), m = bf16(a - h),
+// l = bf16(a - h - m)) in the six terms hh, hm, mh, hl, lh, mm (about 2^-26
+// relative per product); the second product takes two planes (hi, lo) in three
+// terms.  The mean column, whose sum cancels far more (the innovation
+// weights), is accumulated per thread in FP32 from the weighted S in registers
+// and across blocks in FP64.
+//
+// CTA of 10 warps per state tile: warp 8 lane 0 loads W_blk and Vbar_blk^T with
+// 2-D TMA (128-byte swizzle) and the block's coordinates and mean-column values
+// with bulk copies; warp 9 lane 0 issues the MMAs; warps 0-7 (two per TMEM lane
+// quadrant, one state point and half of the block's observations per thread)
+// read S from tensor memory, apply the Gaspari-Cohn weights, add the mean
+// column's terms, split S and write it to shared memory as the A operand of the
+// second product, and finally write A_a and mu_a.  Z_tile is split and placed in shared memory once
+// per CTA.  All waits are bounded (kStatTimeout).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "info_esrf.h"
+#include "internal.h"
+#include "tile_mma.cuh"
+
+namespace infoesrf {
+
+namespace {
+
+constexpr int kStThreads = 320;   // warps 0-7 epilogue (two per TMEM lane quadrant), 8 loads, 9 MMAs
+constexpr int kSideBytes = kTileK * 16 + kTileK * 4;   // a block's grid coordinates and mean-column values
+constexpr int kHalf = kTileM * 64 * 2;         // one 64-member half of a 128-row BF16 operand: 16 KB
+constexpr int kWHalf = kTileK * 64 * 2;        // one 64-member half of the W block: 8 KB
+constexpr int kStages = 1;                     // shared memory holds one block's operands
+
+struct StLayout {
+  int NV;
+  uint32_t z, s, stage, stage_bytes, w_bytes, v_bytes, ctrl, d2, total;
+};
+
+__host__ __device__ inline StLayout st_layout(int NV, int nd2) {
+  StLayout L;
+  L.NV = NV;
+  L.z = 0;                                         // Z planes h, m, l (two halves each)
+  L.s = 6 * kHalf;                                 // S planes hi, lo
+  L.w_bytes = 6 * kWHalf;                          // W planes h, m, l (two halves each)
+  L.v_bytes = 2 * (uint32_t)NV * 128;              // Vbar^T hi, lo: NV rows of 64 observations
+  L.stage_bytes = L.w_bytes + L.v_bytes + kSideBytes;
+  L.stage = L.s + 2 * kHalf;
+  L.ctrl = L.stage + kStages * L.stage_bytes;
+  L.d2 = L.ctrl + 256;
+  L.total = L.d2 + 4 * (uint32_t)nd2;
+  return L;
+}
+
+// Byte offset of 16-byte chunk `chunk` (elements 8 chunk .. 8 chunk + 7) of
+// row `row` in a 128-byte-swizzled K-major region of 128-byte rows: 8-row
+// atoms of 1024 B, the chunk index XORed with row % 8 (the layout TMA writes
+// in SWIZZLE_128B mode).
+__device__ __forceinline__ uint32_t sw128_off(int row, int chunk) {
+  return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+__device__ __forceinline__ uint4 pack8(const float* v) {
+  return make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
+                    pack_bf16x2(v[6], v[7]));
+}
+
+__device__ __forceinline__ float bf16_round(float a) { return __bfloat162float(__float2bfloat16_rn(a)); }
+
+// Eight FP32 values as NP BF16 planes (16 bytes each): plane i holds the
+// rounding of what the planes before it leave.
+template <int NP>
+__device__ __forceinline__ void split8(const float* v, uint4 (&out)[NP]) {
+  float rem[8], pl[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) rem[i] = v[i];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      pl[i] = bf16_round(rem[i]);
+      rem[i] -= pl[i];
+    }
+    out[p] = pack8(pl);
+  }
+}
+
+// Operand planes of the finish in tile order: W in three planes (members
+// padded to kStK), the members' columns of Vbar^T in two (padded to NV), the
+// mean column of Vbar in FP32, and the grid coordinates of each tile position.
+__global__ void k_tile_state_prep(const ProblemDev* tab) {
+  const ProblemDev& pr = tab[blockIdx.y];
+  if (pr.precision != 2 || !pr.st_W) return;
+  const int64_t N = pr.N, N1 = N + 1, dp = pr.d_pad, NV = pr.st_NV;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nw = dp * kStK, nv = NV * dp;
+  const float* Vt = reinterpret_cast<const float*>(pr.VbarT);
+  if (i < nw) {
+    const int64_t a = i / kStK, k = i % kStK;
+    float r = k < N ? pr.Wp[a * N + k] : 0.f;
+#pragma unroll
+    for (int pl = 0; pl < 3; ++pl) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(r);
+      pr.st_W[pl * nw + i] = h;
+      r -= __bfloat162float(h);
+    }
+  }
+  if (i < nv) {
+    const int64_t m = i / dp, a = i % dp;
+    const int32_t src = a < pr.d ? pr.tpos_src[a] : -1;
+    const float v = (src >= 0 && m < N) ? Vt[(int64_t)src * N1 + m] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    pr.st_V[i] = h;
+    pr.st_V[nv + i] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+  if (i < dp) {
+    const int32_t src = i < pr.d ? pr.tpos_src[i] : -1;
+    int4 c = make_int4(0, 0, 0, -1);
+    if (src >= 0) {
+      const Coord3 cc = flat_to_coord(pr.grid, pr.obs[src]);
+      c = make_int4((int)cc.x, (int)cc.y, (int)cc.z, 1);
+    }
+    pr.st_xyz[i] = c;
+    pr.st_vm[i] = src >= 0 ? Vt[(int64_t)src * N1 + N] : 0.f;
+  }
+}
+
+constexpr int kD2St = 4096;   // distance-table entries staged in shared memory (sum of the extents)
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// 1-D bulk copy global -> shared of `bytes` (multiple of 16, both addresses
+// 16-byte aligned), completing that many bytes of transaction count on `bar`.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic-proxy smem writes -> tensor core
+}
+
+__global__ void __launch_bounds__(kStThreads, 1)
+    k_tile_state_mma(const __grid_constant__ CUtensorMap map_w0, const __grid_constant__ CUtensorMap map_w1,
+                     const __grid_constant__ CUtensorMap map_w2, const __grid_constant__ CUtensorMap map_vh,
+                     const __grid_constant__ CUtensorMap map_vl, const ProblemDev* dpr) {
+  const ProblemDev& pr = *dpr;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                         ~static_cast<uintptr_t>(1023));
+  const GridDev& g = pr.grid;
+  const int64_t next = g.ext[0] + g.ext[1] + g.ext[2];
+  const bool d2s = next <= kD2St;
+  const int NV = pr.st_NV;
+  const StLayout Lo = st_layout(NV, d2s ? (int)next : 0);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + Lo.ctrl);
+  uint64_t* empty = full + kStages;
+  uint64_t* sfull = empty + kStages;
+  uint64_t* sready = sfull + 1;
+  uint64_t* sfree = sready + 1;
+  uint64_t* accf = sfree + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(accf + 1);
+  int* flags = reinterpret_cast<int*>(tslot + 1);   // [0] abort, [1] blocks loaded, [2] blocks consumed, [3] skip
+  float* d2 = reinterpret_cast<float*>(smem + Lo.d2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t st = blockIdx.x;
+  if (st >= pr.nst) return;
+  // a timeout anywhere in the grid stops the CTAs that have not started (uniform per CTA)
+  if (tid == 0) flags[3] = (pr.status[0] & (kStatTimeout | kStatTileOverflow)) ? 1 : 0;
+  __syncthreads();
+  if (flags[3]) return;
+  const int t0 = pr.st_rowptr[st], nk = pr.st_rowptr[st + 1] - t0;
+  const int64_t x0 = st * kTileM;
+  const int N = (int)pr.N;
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(sfull, 1);
+    mbar_init(sready, 256);
+    mbar_init(sfree, 1);
+    mbar_init(accf, 1);
+    flags[0] = 0;
+    flags[1] = 0;
+    flags[2] = 0;
+    fence_mbar_init();
+    tma_prefetch_map(&map_w0);
+    tma_prefetch_map(&map_w1);
+    tma_prefetch_map(&map_w2);
+    tma_prefetch_map(&map_vh);
+    tma_prefetch_map(&map_vl);
+  }
+  if (warp == 8) tmem_alloc(tslot, 256);
+  // Z_tile as the A operand of the first product: one state point per thread,
+  // members split into three BF16 planes, 128-byte-swizzled 64-member halves
+  if (tid < kTileM) {   // warps 0-3
+    const int64_t x = x0 + tid;
+    const float* Zt = reinterpret_cast<const float*>(pr.Zt);
+#pragma unroll 1
+    for (int chunk = 0; chunk < kStK / 8; ++chunk) {
+      float v[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int k = 8 * chunk + i;
+        v[i] = (x < pr.n && k < N) ? Zt[x * N + k] : 0.f;
+      }
+      uint4 pl[3];
+      split8<3>(v, pl);
+      const int half = chunk >> 3;
+      const uint32_t off = sw128_off(tid, chunk & 7);
+#pragma unroll
+      for (int p = 0; p < 3; ++p) *reinterpret_cast<uint4*>(smem + Lo.z + (2 * p + half) * kHalf + off) = pl[p];
+    }
+  }
+  if (d2s)
+    for (int64_t e = tid; e < next; e += blockDim.x) d2[e] = (float)pr.d2tab[e];
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t t_s = tmem, t_acc = tmem + 64;
+
+  if (warp == 8) {
+    if (lane == 0) {
+      // producer: W_blk (three planes, two 64-member halves each) and Vbar_blk^T (hi, lo)
+      int kb = 0;
+      for (; kb < nk; ++kb) {
+        const int s = kb % kStages;
+        if (kb >= kStages && !mbar_wait(&empty[s], ((kb / kStages) & 1) ^ 1)) {
+          atomicExch(&flags[0], 1);
+          break;
+        }
+        if (*reinterpret_cast<volatile int*>(&flags[0])) break;
+        unsigned char* sp = smem + Lo.stage + s * Lo.stage_bytes;
+        const int row = pr.st_colblk[t0 + kb] * kTileK;
+        mbar_arrive_expect_tx(&full[s], Lo.stage_bytes);
+        tma_load_2d(sp, &map_w0, &full[s], 0, row);
+        tma_load_2d(sp + kWHalf, &map_w0, &full[s], 64, row);
+        tma_load_2d(sp + 2 * kWHalf, &map_w1, &full[s], 0, row);
+        tma_load_2d(sp + 3 * kWHalf, &map_w1, &full[s], 64, row);
+        tma_load_2d(sp + 4 * kWHalf, &map_w2, &full[s], 0, row);
+        tma_load_2d(sp + 5 * kWHalf, &map_w2, &full[s], 64, row);
+        tma_load_2d(sp + Lo.w_bytes, &map_vh, &full[s], row, 0);
+        tma_load_2d(sp + Lo.w_bytes + NV * 128, &map_vl, &full[s], row, 0);
+        bulk_load(sp + Lo.w_bytes + Lo.v_bytes, pr.st_xyz + row, kTileK * 16, &full[s]);
+        bulk_load(sp + Lo.w_bytes + Lo.v_bytes + kTileK * 16, pr.st_vm + row, kTileK * 4, &full[s]);
+      }
+      flags[1] = kb;
+    }
+  } else if (warp == 9) {
+    if (lane == 0) {
+      // MMA issuer: S = Z W^T (six terms, two halves), then acc += S Vbar (three terms)
+      const uint32_t id1 = idesc_bf16_f32(kTileM, kTileK), id2 = idesc_bf16_f32(kTileM, NV);
+      const uint32_t zb = smem_u32(smem + Lo.z), sb = smem_u32(smem + Lo.s);
+      int kb = 0;
+      for (; kb < nk; ++kb) {
+        const int s = kb % kStages;
+        if (!mbar_wait(&full[s], (kb / kStages) & 1)) {
+          atomicExch(&flags[0], 1);
+          break;
+        }
+        if (*reinterpret_cast<volatile int*>(&flags[0])) break;
+        tc_fence_after();
+        const uint32_t wb = smem_u32(smem + Lo.stage + s * Lo.stage_bytes);
+        const uint32_t vb = wb + Lo.w_bytes;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const uint64_t z0 = sw128_desc(zb + h * kHalf), z1 = sw128_desc(zb + (2 + h) * kHalf),
+                         z2 = sw128_desc(zb + (4 + h) * kHalf);
+          const uint64_t w0 = sw128_desc(wb + h * kWHalf), w1 = sw128_desc(wb + (2 + h) * kWHalf),
+                         w2 = sw128_desc(wb + (4 + h) * kWHalf);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {   // K = 16 per MMA: 32 bytes along the swizzled row
+            mma_bf16(t_s, z0 + 2 * k, w0 + 2 * k, id1, (h | k) != 0 ? 1u : 0u);
+            mma_bf16(t_s, z0 + 2 * k, w1 + 2 * k, id1, 1u);
+            mma_bf16(t_s, z1 + 2 * k, w0 + 2 * k, id1, 1u);
+            mma_bf16(t_s, z0 + 2 * k, w2 + 2 * k, id1, 1u);
+            mma_bf16(t_s, z2 + 2 * k, w0 + 2 * k, id1, 1u);
+            mma_bf16(t_s, z1 + 2 * k, w1 + 2 * k, id1, 1u);
+          }
+        }
+        mma_commit(sfull);
+        if (!mbar_wait(sready, kb & 1)) {
+          atomicExch(&flags[0], 1);
+          break;
+        }
+        tc_fence_after();
+        const uint64_t sh = sw128_desc(sb), sl = sw128_desc(sb + kHalf);
+        const uint64_t vh = sw128_desc(vb), vl = sw128_desc(vb + NV * 128);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          mma_bf16(t_acc, sh + 2 * k, vh + 2 * k, id2, (kb | k) != 0 ? 1u : 0u);
+          mma_bf16(t_acc, sh + 2 * k, vl + 2 * k, id2, 1u);
+          mma_bf16(t_acc, sl + 2 * k, vh + 2 * k, id2, 1u);
+        }
+        mma_commit(&empty[s]);
+        mma_commit(sfree);
+      }
+      flags[2] = kb;
+      mma_commit(accf);
+    }
+  } else {
+    // warps 0-7: state point `row` (TMEM lane) and observations half * 32 .. half * 32 + 31
+    const int quad = warp & 3, half = warp >> 2;
+    const int row = quad * 32 + lane;
+    const int64_t x = x0 + row;
+    const bool xin = x < pr.n;
+    const Coord3 cx = flat_to_coord(g, xin ? x : 0);
+    const int64_t ca[3] = {cx.x, cx.y, cx.z};
+    const uint32_t trow = (uint32_t)(quad * 32) << 16;
+    unsigned char* s_hi = smem + Lo.s;
+    const unsigned char* side = smem + Lo.stage + Lo.w_bytes + Lo.v_bytes;   // stage 0 (one stage)
+    const int4* cs = reinterpret_cast<const int4*>(side);
+    const float* vm = reinterpret_cast<const float*>(side + kTileK * 16);
+    double macc = 0.0;   // this half's part of the mean column, FP64 across blocks
+    // exits are warp-uniform: the TMEM loads below are warp-collective
+    for (int kb = 0; kb < nk; ++kb) {
+      if (!__all_sync(0xffffffffu, mbar_wait(sfull, kb & 1) && mbar_wait(&full[0], kb & 1))) {
+        atomicExch(&flags[0], 1);
+        break;
+      }
+      tc_fence_after();
+      float sv[32];
+#pragma unroll
+      for (int c0 = 0; c0 < 32; c0 += 16) {
+        float v[16];
+        tmem_ld16(t_s + trow + (uint32_t)(half * 32 + c0), v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) sv[c0 + i] = v[i];
+      }
+      // Gaspari-Cohn weights of the pairs (state point, observation), and the mean column
+      float mb = 0.f;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        const int4 ob = cs[half * 32 + c];
+        const int64_t cbv[3] = {ob.x, ob.y, ob.z};
+        float r2 = 0.f;
+        int64_t off = 0;
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+          if (g.ext[ax] > 1) {
+            const int64_t dl = ca[ax] > cbv[ax] ? ca[ax] - cbv[ax] : cbv[ax] - ca[ax];
+            r2 += d2s ? d2[off + dl] : (float)pr.d2tab[off + dl];
+          }
+          off += g.ext[ax];
+        }
+        sv[c] = (ob.w >= 0 && r2 < 4.f) ? gaspari_cohn_f(sqrtf(r2)) * sv[c] : 0.f;
+        mb = fmaf(sv[c], vm[half * 32 + c], mb);
+      }
+      macc += (double)mb;
+      // the second product of the previous block has read the S planes
+      if (kb > 0 && !__all_sync(0xffffffffu, mbar_wait(sfree, (kb - 1) & 1))) {
+        atomicExch(&flags[0], 1);
+        break;
+      }
+#pragma unroll
+      for (int chunk = 0; chunk < 4; ++chunk) {
+        uint4 pl[2];
+        split8<2>(sv + 8 * chunk, pl);
+        const uint32_t off = sw128_off(row, half * 4 + chunk);
+        *reinterpret_cast<uint4*>(s_hi + off) = pl[0];
+        *reinterpret_cast<uint4*>(s_hi + kHalf + off) = pl[1];
+      }
+      fence_proxy_async();
+      tc_fence_before();
+      mbar_arrive(sready);
+    }
+    const bool got = mbar_wait(accf, 0);
+    if (!got) atomicExch(&flags[0], 1);
+    tc_fence_after();
+    const bool ok = __all_sync(0xffffffffu, got && *reinterpret_cast<volatile int*>(&flags[0]) == 0);
+    const double mu = xin ? pr.mu[x] : 0.0;
+    for (int c0 = half * 16; c0 < NV; c0 += 32) {   // the halves take alternate 16-column chunks
+      float v[16];
+      if (nk > 0 && ok) {
+        tmem_ld16(t_acc + trow + (uint32_t)c0, v);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = 0.f;
+      }
+      if (!xin || !ok) continue;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int col = c0 + i;
+        const double inc = (double)v[i];
+        if (col < N && pr.do_pert)
+          pr.A_a[(int64_t)col * pr.n + x] = (pr.X[(int64_t)col * pr.n + x] - mu) - pr.sqrt_nm1 * inc;
+      }
+    }
+    // the mean column: half 1 hands its part to half 0 (the S planes are free now)
+    double* red = reinterpret_cast<double*>(s_hi);
+    if (half == 1) red[row] = macc;
+    asm volatile("bar.sync 1, 256;" ::: "memory");   // the eight epilogue warps
+    if (half == 0 && xin && ok && pr.do_mean) pr.mu_a[x] = mu + (macc + red[row]);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (tid == 0 && flags[0]) {
+    // wait (bounded) for the loads still in flight before the CTA's shared memory goes away
+    for (int kb = flags[2]; kb < flags[1]; ++kb) mbar_wait(&full[kb % kStages], (kb / kStages) & 1);
+    atomicOr(&pr.status[0], kStatTimeout);
+  }
+  __syncthreads();
+  if (warp == 8) tmem_dealloc(tmem, 256);
+}
+
+}  // namespace
+
+}  // namespace infoesrf
+
+namespace infoesrf {
+
+// Launches the tensor-core state update for every problem of the table (all
+// BF16 with N <= kStK, and shared memory for one block's operands); returns -1
+// without launching anything when one of them does not qualify or the device
+// cannot be configured, and the caller runs the CUDA-core kernel instead.
+int launch_tile_state_mma(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  size_t smax = 0;
+  int64_t nmax = 0;
+  for (int i = 0; i < tab.count; ++i) {
+    const ProblemDev& p = tab.p[i];
+    if (p.precision != 2 || !p.st_W || p.N > kStK || p.st_NV > kStK || p.st_NV < 16) return -1;
+    const int64_t next = p.grid.ext[0] + p.grid.ext[1] + p.grid.ext[2];
+    const size_t need = 1024 + st_layout(p.st_NV, next <= kD2St ? (int)next : 0).total;
+    smax = need > smax ? need : smax;
+    const int64_t np = std::max<int64_t>(p.d_pad * kStK, (int64_t)p.st_NV * p.d_pad);
+    nmax = np > nmax ? np : nmax;
+  }
+  if (smax > (size_t)optin) return -1;
+  CUtensorMap maps[kMaxProblems][5];
+  for (int i = 0; i < tab.count; ++i) {
+    const ProblemDev& p = tab.p[i];
+    const uint64_t dp = (uint64_t)p.d_pad, NV = (uint64_t)p.st_NV;
+    if (!encode_bf16(&maps[i][0], p.st_W, kStK, dp, kStK, kTileK) ||
+        !encode_bf16(&maps[i][1], p.st_W + dp * kStK, kStK, dp, kStK, kTileK) ||
+        !encode_bf16(&maps[i][2], p.st_W + 2 * dp * kStK, kStK, dp, kStK, kTileK) ||
+        !encode_bf16(&maps[i][3], p.st_V, dp, NV, dp, (uint32_t)NV) ||
+        !encode_bf16(&maps[i][4], p.st_V + NV * dp, dp, NV, dp, (uint32_t)NV))
+      return -1;
+  }
+  static thread_local int raised_dev = -1;
+  static thread_local size_t raised_bytes = 0;
+  if (raised_dev != dev || raised_bytes < smax) {
+    if (cudaFuncSetAttribute(k_tile_state_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return -1;
+    }
+    raised_dev = dev;
+    raised_bytes = smax;
+  }
+  k_tile_state_prep<<<dim3((unsigned)((nmax + 255) / 256), tab.count), 256, 0, st>>>(dtab);
+  note_launches(1);
+  for (int i = 0; i < tab.count; ++i) {
+    const ProblemDev& p = tab.p[i];
+    if (p.nst < 1) continue;
+    k_tile_state_mma<<<(unsigned)p.nst, kStThreads, smax, st>>>(maps[i][0], maps[i][1], maps[i][2], maps[i][3],
+                                                                maps[i][4], dtab + i);
+    note_launches(1);
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : INFO_ESRF_ERR_CUDA;
+}
+
+}  // namespace infoesrf
