@@ -748,9 +748,9 @@ def run_tilemm(args):
     """The tensor-core block-tile matvec alone (stage entry info_esrf_bf16_tile_matvec), on a seeded
     synthetic block structure with the 2-D workload's shape per row tile: 256 row tiles of 128
     observations (d_pad = 32,768), 300 stored 128 x 64 blocks per row tile (hi + lo BF16 planes),
-    J = 2561 systems (11 chunks of 256).  About 3 GB on the device, more than L2.  Timed with CUDA
-    events per launch after warm-up; FLOPs counted as issued by the tensor cores (two planes,
-    2 x 128 x 64 x 256 per block and chunk)."""
+    J = 2561 systems (161 units of 16, 11 chunks of at most 16 units).  About 3 GB on the device,
+    more than L2.  Timed with CUDA events per launch after warm-up; FLOPs counted as issued by the
+    tensor cores (two planes, 2 x 128 x 64 x 16 per block and unit)."""
     import numpy as np
     import torch
 
@@ -789,8 +789,8 @@ def run_tilemm(args):
         e1.synchronize()
         ts.append(e0.elapsed_time(e1))
     assert int(status.item()) == 0
-    nchunks = (J + 255) // 256
-    flops = ntiles * nchunks * 2 * 2.0 * 128 * 64 * 256
+    units = (J + 15) // 16
+    flops = ntiles * units * 2 * 2.0 * 128 * 64 * 16
     nbytes = ntiles * 2 * 16384 + 2.0 * J * 128 * nrt + 4.0 * J * 128 * nrt
     ms = statistics.mean(ts)
     peaks = _measured_peaks()

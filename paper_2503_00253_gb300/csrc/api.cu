@@ -242,7 +242,6 @@ void carve_problem(Carver& cv, ProblemDev& pr, const info_esrf_options& o) {
   }
   if (o.precision == 2) {
     const int64_t J = pr.nsys, dp = pr.d_pad, kk = pr.kR;
-    const int bn = tile_chunk_width((int32_t)std::max<int64_t>(J, 1));
     const int64_t nsub = (dp + kTileDotRows - 1) / kTileDotRows;
     pr.skey = cv.take<uint64_t>((size_t)pr.nsort * 8);
     pr.sidx = cv.take<int32_t>((size_t)pr.nsort * 4);
@@ -269,8 +268,9 @@ void carve_problem(Carver& cv, ProblemDev& pr, const info_esrf_options& o) {
     pr.lcoef = cv.take<float>((size_t)J * 2 * kMaxK * 4);
     pr.sigmaf = cv.take<float>((size_t)J * 4);
     pr.active = cv.take<int32_t>((size_t)J * 4);
-    pr.chunk_active = cv.take<int32_t>((size_t)((J + bn - 1) / bn) * 4);
-    pr.nactive = cv.take<int32_t>(2 * 4);
+    pr.unit_active = cv.take<int32_t>((size_t)((J + kTileUnit - 1) / kTileUnit) * 4);
+    pr.unit_list = cv.take<int32_t>((size_t)((J + kTileUnit - 1) / kTileUnit) * 4);
+    pr.nactive = cv.take<int32_t>(4 * 4);
     pr.alist = cv.take<int32_t>((size_t)J * 4);
     // operand planes of the tensor-core state update (tile_state.cu)
     pr.st_NV = (int32_t)((N + 15) / 16 * 16);

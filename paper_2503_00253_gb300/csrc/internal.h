@@ -51,15 +51,16 @@ struct TileMmArgs {
   const int32_t* colblk;        // [tiles] column block of each stored block
   const __nv_bfloat16* P;       // [J][d_pad] directions
   const float* sigma;           // [J] shifts
-  const int32_t* active;        // [nchunks] nonzero: chunk has an unconverged system (or NULL: all)
+  const int32_t* active;        // [ceil(J / 16)] nonzero: the unit of 16 systems has an unconverged one (or NULL: all)
   float* Y;                     // [J][d_pad] sigma p + C p
   float* pty;                   // partial p^T y per row tile (or NULL): [nrt][J], or [J][nrt] if pty_by_system
   int32_t* status;              // status bits (kStatTimeout), or NULL
   int64_t d_pad;
   int32_t J, nrt, nchunks, pty_by_system;
+  int32_t units;                // number of nonzero flags in `active` (ignored when it is NULL)
+  int32_t* ulist;               // [ceil(J / 16)] scratch: the ordered list of those units
 };
-// Systems per CTA of the tile matvec for J systems (128 or 256).
-int tile_chunk_width(int32_t J);
+constexpr int kTileUnit = 16;   // systems per unit of the tile matvec (one 16-row TMA box of P)
 int launch_tile_mm(TileMmArgs a, const void* chi, const void* clo, int64_t ntiles, cudaStream_t st);
 constexpr int kStK = 128;           // member slots of the tensor-core state update (N <= 128)
 constexpr int kTileDotRows = 512;   // rows per partial dot product of the BF16 PCG
@@ -216,7 +217,8 @@ struct ProblemDev {
   float* lcoef;                 // [J][2 kR] LMP coefficients of the current direction update
   float* sigmaf;                // [J] shift per system (FP32)
   int32_t* active;              // [J] 1 while the system runs
-  int32_t* chunk_active;        // [nchunks] 1 while a chunk of the tile matvec has a running system
+  int32_t* unit_active;         // [ceil(J / 16)] 1 while a unit of 16 systems has a running system
+  int32_t* unit_list;           // [ceil(J / 16)] the tile matvec's ordered list of those units
   int32_t* nactive;             // [2] running systems; copy of status[0] for the host
   int32_t* alist;               // [J] the running systems (unordered), rebuilt every iteration
   // learned correction on the BF16 path, for observations on every point of a

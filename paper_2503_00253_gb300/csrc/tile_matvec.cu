@@ -11,17 +11,21 @@
 // stored as two BF16 planes hi = bf16(C), lo = bf16(C - hi), row-major
 // [tile][128][64].  The directions are BF16, system-major [J][d_pad].
 //
-// Kernel.  One CTA of 4 warps per (row tile, chunk of H x BN systems).  Warp 0
-// lane 0 streams the blocks of the row tile through an S-stage ring of shared
-// memory with 2-D TMA loads (128-byte swizzle): the hi and lo planes of the C
-// block (the A operand, 128 x 64, K-major) and the 64-row slab of the chunk's
-// directions (the B operand, BN x 64, K-major).  Warp 1 lane 0 issues
-// tcgen05.mma kind::f16 (BF16 x BF16, FP32 accumulate) into H 128 x BN FP32
-// accumulators in tensor memory (H = 2 when more than 256 systems: each C
-// block load then serves 512 systems): four K = 16 steps for hi, four for lo,
-// per accumulator, then a commit that frees the stage.  After the last block all four warps read the
-// accumulator (tcgen05.ld, one TMEM lane = one row per thread), add sigma_j p_j,
-// store y and reduce the partial dot products p_j^T y_j of the row tile.
+// Kernel.  Systems are grouped in units of 16 (one 16-row TMA box of P); a
+// launch covers the units that hold an unconverged system, split evenly over
+// `nchunks` CTAs per row tile (at most BN / 16 units each), so that converged
+// systems cost no tensor-core work.  One CTA of 4 warps per (row tile, chunk):
+// warp 0 lane 0 streams the blocks of the row tile through an S-stage ring of
+// shared memory with 2-D TMA loads (128-byte swizzle): the hi and lo planes of
+// the C block (the A operand, 128 x 64, K-major) and, per run of consecutive
+// units, one slab of their directions (together the B operand, 16 u x 64,
+// K-major; one tensor map per box height 16 .. 256 rows).  Warp 1
+// lane 0 issues tcgen05.mma kind::f16 (BF16 x BF16, FP32 accumulate, N = 16 u)
+// into a 128 x 16 u FP32 accumulator in tensor memory: four K = 16 steps for
+// hi, four for lo, then a commit that frees the stage.  After the last block
+// all four warps read the accumulator (tcgen05.ld, one TMEM lane = one row per
+// thread), add sigma_j p_j, store y and reduce the partial dot products
+// p_j^T y_j of the row tile.
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
@@ -34,7 +38,8 @@ namespace infoesrf {
 
 namespace {
 
-constexpr int kABytes = kTileM * kTileK * 2;   // one BF16 plane of a C block: 16 KB
+constexpr int kABytes = kTileM * kTileK * 2;     // one BF16 plane of a C block: 16 KB
+constexpr int kUnitBytes = kTileUnit * kTileK * 2;   // one unit's slab of P: 2 KB
 
 __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
@@ -42,22 +47,53 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   return v;
 }
 
-// BN systems per accumulator, S pipeline stages, H accumulators (TMEM halves)
-// per CTA sharing each C block load.
-template <int BN, int S, int H>
+constexpr int kMaxUnits = 16;                        // units per CTA at most (256 systems)
+
+// At most BN systems (BN / 16 units) per CTA, S pipeline stages.
+template <int BN, int S>
 struct TileMmShape {
-  static constexpr int kStage = 2 * kABytes + H * BN * kTileK * 2;
-  static constexpr int kCtrl = 256;   // mbarriers, TMEM slot, flags
-  static constexpr size_t kSmem = 1024 + (size_t)S * kStage + kCtrl + 4 * H * BN * sizeof(float);
+  static constexpr int kUnits = BN / kTileUnit;
+  static constexpr int kStage = 2 * kABytes + BN * kTileK * 2;
+  static constexpr int kCtrl = 256;   // mbarriers, TMEM slot, flags, the CTA's units and loads
+  static_assert(kUnits <= kMaxUnits, "units per CTA");
+  static_assert(8 * (2 * S + 1) + 4 + 16 + 8 * kUnits <= kCtrl, "control block");
+  static constexpr size_t kSmem = 1024 + (size_t)S * kStage + kCtrl + 4 * BN * sizeof(float);
 };
 
-template <int BN, int S, int H>
+// Tensor maps of P with boxes of 64 columns and 16 (i + 1) rows, i = 0 .. 15.
+struct PMaps {
+  CUtensorMap m[kMaxUnits];
+};
+
+// Ordered list of the units whose flag is set (one CTA of 1024 threads).
+__global__ void __launch_bounds__(1024) k_tile_units(const int32_t* flags, int nunits, int32_t* ulist) {
+  __shared__ int wsum[32];
+  __shared__ int base;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  for (int u0 = 0; u0 < nunits; u0 += 1024) {
+    const int u = u0 + (int)threadIdx.x;
+    const bool act = u < nunits && flags[u] != 0;
+    const unsigned m = __ballot_sync(0xffffffffu, act);
+    if (lane == 0) wsum[warp] = __popc(m);
+    __syncthreads();
+    int off = base;
+    for (int w = 0; w < warp; ++w) off += wsum[w];
+    if (act) ulist[off + __popc(m & ((1u << lane) - 1u))] = u;
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int w = 0; w < 32; ++w) base += wsum[w];
+    __syncthreads();
+  }
+}
+
+template <int BN, int S>
 __global__ void __launch_bounds__(128, 1)
     k_tile_mm(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
-              const __grid_constant__ CUtensorMap map_p, const TileMmArgs args) {
-  using Shape = TileMmShape<BN, S, H>;
+              const __grid_constant__ PMaps maps_p, const TileMmArgs args) {
+  using Shape = TileMmShape<BN, S>;
   constexpr int kStage = Shape::kStage;
-  constexpr int kCols = H * BN;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                          ~static_cast<uintptr_t>(1023));
@@ -66,24 +102,34 @@ __global__ void __launch_bounds__(128, 1)
   uint64_t* empty = full + S;
   uint64_t* accf = empty + S;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(accf + 1);
-  int* flags = reinterpret_cast<int*>(tslot + 1);   // [0] abort, [1] loads issued, [2] stages consumed
+  int* flags = reinterpret_cast<int*>(tslot + 1);   // [0] abort, [1] loads issued, [2] stages consumed, [3] runs
+  int* units = flags + 4;                            // the CTA's units, in order
+  int* runs = units + Shape::kUnits;                 // runs of consecutive units: first rank | length << 8
   float* red = reinterpret_cast<float*>(ctrl + Shape::kCtrl);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int chunk = (int)(blockIdx.x % (unsigned)args.nchunks);
   const int rt = (int)(blockIdx.x / (unsigned)args.nchunks);
-  // accumulator h serves systems (chunk H + h) BN ..; skipped when it has none
-  // or all of them have converged (args.active has one flag per BN systems)
-  bool hact[H];
-  int nh = 0;
-#pragma unroll
-  for (int h = 0; h < H; ++h) {
-    const int unit = chunk * H + h;
-    hact[h] = unit * BN < args.J && (!args.active || args.active[unit]);
-    nh += hact[h];
+  // this CTA's units: ranks [chunk T / nchunks, (chunk + 1) T / nchunks) of the T listed units
+  // (at most kUnits: nchunks >= T / kUnits)
+  const int T = args.units;
+  const int lo = (int)((int64_t)chunk * T / args.nchunks);
+  const int nu = min((int)((int64_t)(chunk + 1) * T / args.nchunks) - lo, Shape::kUnits);
+  if (nu <= 0) return;   // uniform across the CTA, before any barrier or TMEM use
+  if (threadIdx.x < nu) units[threadIdx.x] = args.ulist ? args.ulist[lo + threadIdx.x] : lo + (int)threadIdx.x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int nr = 0;
+    for (int i = 0; i < nu;) {
+      int len = 1;
+      while (i + len < nu && units[i + len] == units[i] + len) ++len;
+      runs[nr++] = i | (len << 8);
+      i += len;
+    }
+    flags[3] = nr;
   }
-  if (nh == 0) return;
-  const uint32_t stage_bytes = 2 * kABytes + nh * BN * kTileK * 2;
+  const int ncol = nu * kTileUnit;
+  const uint32_t stage_bytes = 2 * kABytes + nu * kUnitBytes;
   const int t0 = args.rowptr[rt];
   const int nk = args.rowptr[rt + 1] - t0;
 
@@ -99,16 +145,16 @@ __global__ void __launch_bounds__(128, 1)
     fence_mbar_init();
     tma_prefetch_map(&map_hi);
     tma_prefetch_map(&map_lo);
-    tma_prefetch_map(&map_p);
   }
-  if (warp == 2) tmem_alloc(tslot, kCols);
+  if (warp == 2) tmem_alloc(tslot, BN);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
+  const int nruns = flags[3];
 
   if (warp == 0 && lane == 0) {
-    // producer: C block planes and the directions' slab of each column block
+    // producer: C block planes and each unit's slab of the directions for the block's columns
     int kb = 0;
     for (; kb < nk; ++kb) {
       const int s = kb % S;
@@ -119,19 +165,19 @@ __global__ void __launch_bounds__(128, 1)
       if (*reinterpret_cast<volatile int*>(&flags[0])) break;
       unsigned char* st = smem + s * kStage;
       const int tile = t0 + kb;
+      const int xcol = args.colblk[tile] * kTileK;
       mbar_arrive_expect_tx(&full[s], stage_bytes);
       tma_load_2d(st, &map_hi, &full[s], 0, tile * kTileM);
       tma_load_2d(st + kABytes, &map_lo, &full[s], 0, tile * kTileM);
-#pragma unroll
-      for (int h = 0; h < H; ++h)
-        if (hact[h])
-          tma_load_2d(st + 2 * kABytes + h * BN * kTileK * 2, &map_p, &full[s], args.colblk[tile] * kTileK,
-                      (chunk * H + h) * BN);
+      for (int r = 0; r < nruns; ++r) {
+        const int i = runs[r] & 255, len = runs[r] >> 8;
+        tma_load_2d(st + 2 * kABytes + i * kUnitBytes, &maps_p.m[len - 1], &full[s], xcol, units[i] * kTileUnit);
+      }
     }
     flags[1] = kb;
   } else if (warp == 1 && lane == 0) {
     // MMA issuer: acc = sum over blocks of (C_hi + C_lo) P, FP32 in TMEM
-    constexpr uint32_t idesc = idesc_bf16_f32(kTileM, BN);
+    const uint32_t idesc = idesc_bf16_f32(kTileM, ncol);
     int kb = 0;
     for (; kb < nk; ++kb) {
       const int s = kb % S;
@@ -142,17 +188,12 @@ __global__ void __launch_bounds__(128, 1)
       tc_fence_after();
       const uint32_t base = smem_u32(smem + s * kStage);
       const uint64_t dhi = sw128_desc(base), dlo = sw128_desc(base + kABytes);
+      const uint64_t db = sw128_desc(base + 2 * kABytes);
 #pragma unroll
-      for (int h = 0; h < H; ++h) {
-        if (!hact[h]) continue;
-        const uint64_t db = sw128_desc(base + 2 * kABytes + h * BN * kTileK * 2);
-        const uint32_t td = tmem + (uint32_t)(h * BN);
+      for (int k = 0; k < kTileK / 16; ++k)   // K = 16 per MMA: 32 bytes along the swizzled row
+        mma_bf16(tmem, dhi + 2 * k, db + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
 #pragma unroll
-        for (int k = 0; k < kTileK / 16; ++k)   // K = 16 per MMA: 32 bytes along the swizzled row
-          mma_bf16(td, dhi + 2 * k, db + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
-#pragma unroll
-        for (int k = 0; k < kTileK / 16; ++k) mma_bf16(td, dlo + 2 * k, db + 2 * k, idesc, 1u);
-      }
+      for (int k = 0; k < kTileK / 16; ++k) mma_bf16(tmem, dlo + 2 * k, db + 2 * k, idesc, 1u);
       mma_commit(&empty[s]);
     }
     flags[2] = kb;
@@ -167,33 +208,30 @@ __global__ void __launch_bounds__(128, 1)
     const int row = warp * 32 + lane;
     const int64_t a = (int64_t)rt * kTileM + row;
     const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int i = 0; i < nu; ++i) {   // one unit = 16 accumulator columns
+      float v[16];
+      tmem_ld16(tbase + (uint32_t)(i * kTileUnit), v);
+      const int jb = units[i] * kTileUnit;
 #pragma unroll
-    for (int h = 0; h < H; ++h) {
-      if (!hact[h]) continue;   // uniform across the CTA
-      for (int c0 = 0; c0 < BN; c0 += 16) {
-        float v[16];
-        tmem_ld16(tbase + (uint32_t)(h * BN + c0), v);
-#pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const int j = (chunk * H + h) * BN + c0 + c;
-          float dot = 0.f;
-          if (j < args.J) {
-            const float p = __bfloat162float(args.P[(int64_t)j * args.d_pad + a]);
-            const float y = fmaf(args.sigma[j], p, v[c]);
-            args.Y[(int64_t)j * args.d_pad + a] = y;
-            dot = p * y;
-          }
-          dot = warp_sum_f(dot);
-          if (lane == 0) red[warp * kCols + h * BN + c0 + c] = dot;
+      for (int c = 0; c < kTileUnit; ++c) {
+        const int j = jb + c;
+        float dot = 0.f;
+        if (j < args.J) {
+          const float p = __bfloat162float(args.P[(int64_t)j * args.d_pad + a]);
+          const float y = fmaf(args.sigma[j], p, v[c]);
+          args.Y[(int64_t)j * args.d_pad + a] = y;
+          dot = p * y;
         }
+        dot = warp_sum_f(dot);
+        if (lane == 0) red[warp * BN + i * kTileUnit + c] = dot;
       }
     }
     __syncthreads();
     if (args.pty)
-      for (int t = threadIdx.x; t < kCols; t += blockDim.x) {
-        const int j = chunk * kCols + t;
-        if (j < args.J && hact[t / BN]) {
-          const float v = (red[t] + red[kCols + t]) + (red[2 * kCols + t] + red[3 * kCols + t]);
+      for (int t = threadIdx.x; t < ncol; t += blockDim.x) {
+        const int j = units[t / kTileUnit] * kTileUnit + t % kTileUnit;
+        if (j < args.J) {
+          const float v = (red[t] + red[BN + t]) + (red[2 * BN + t] + red[3 * BN + t]);
           if (args.pty_by_system) args.pty[(int64_t)j * args.nrt + rt] = v;
           else args.pty[(int64_t)rt * args.J + j] = v;
         }
@@ -205,47 +243,57 @@ __global__ void __launch_bounds__(128, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 2) tmem_dealloc(tmem, kCols);
+  if (warp == 2) tmem_dealloc(tmem, BN);
 }
 
-template <int BN, int S, int H>
+template <int BN, int S>
 int launch_tile_mm_t(TileMmArgs a, const void* chi, const void* clo, int64_t ntiles, cudaStream_t st) {
-  using Shape = TileMmShape<BN, S, H>;
-  a.nchunks = (a.J + H * BN - 1) / (H * BN);
-  CUtensorMap mh, ml, mp;
+  using Shape = TileMmShape<BN, S>;
+  a.nchunks = (a.units + Shape::kUnits - 1) / Shape::kUnits;
+  CUtensorMap mh, ml;
+  PMaps mp;
   if (!encode_bf16(&mh, chi, kTileK, (uint64_t)ntiles * kTileM, kTileK, kTileM) ||
-      !encode_bf16(&ml, clo, kTileK, (uint64_t)ntiles * kTileM, kTileK, kTileM) ||
-      !encode_bf16(&mp, a.P, (uint64_t)a.d_pad, (uint64_t)a.J, (uint64_t)a.d_pad, BN))
+      !encode_bf16(&ml, clo, kTileK, (uint64_t)ntiles * kTileM, kTileK, kTileM))
     return INFO_ESRF_ERR_CUDA;
+  for (int i = 0; i < Shape::kUnits; ++i)
+    if (!encode_bf16(&mp.m[i], a.P, (uint64_t)a.d_pad, (uint64_t)a.J, (uint64_t)a.d_pad, (uint32_t)(kTileUnit * (i + 1))))
+      return INFO_ESRF_ERR_CUDA;
   static thread_local int raised_dev = -1;
   int dev = 0;
   cudaGetDevice(&dev);
   if (raised_dev != dev) {
-    if (cudaFuncSetAttribute(k_tile_mm<BN, S, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Shape::kSmem) !=
+    if (cudaFuncSetAttribute(k_tile_mm<BN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Shape::kSmem) !=
         cudaSuccess)
       return INFO_ESRF_ERR_CUDA;
     raised_dev = dev;
   }
   const int64_t grid = (int64_t)a.nrt * a.nchunks;
-  k_tile_mm<BN, S, H><<<(unsigned)grid, 128, Shape::kSmem, st>>>(mh, ml, mp, a);
+  k_tile_mm<BN, S><<<(unsigned)grid, 128, Shape::kSmem, st>>>(mh, ml, mp, a);
   note_launches(1);
   return cudaGetLastError() == cudaSuccess ? INFO_ESRF_OK : INFO_ESRF_ERR_CUDA;
 }
 
 }  // namespace
 
-int tile_chunk_width(int32_t J) { return J <= 128 ? 128 : 256; }
-
 int launch_tile_mm(TileMmArgs a, const void* chi, const void* clo, int64_t ntiles, cudaStream_t st) {
+  const int32_t nunits = (a.J + kTileUnit - 1) / kTileUnit;
   if (a.nrt < 1 || a.J < 1 || a.d_pad % kTileM || (int64_t)a.nrt * kTileM != a.d_pad ||
-      ntiles * kTileM >= (int64_t(1) << 31))
+      ntiles * kTileM >= (int64_t(1) << 31) || (a.active && (!a.ulist || a.units < 0 || a.units > nunits)))
     return INFO_ESRF_ERR_INVALID_ARG;
-  // up to 128 systems per CTA: one 128-column accumulator, 4 stages; else
-  // 256-column accumulators, 3 stages.  (Two accumulators per CTA, so that a
-  // C block load serves 512 systems, leave room for two stages only and
-  // measured slower: 1225 against 1273 TFLOP/s on the tilemm workload.)
-  if (a.J <= 128) return launch_tile_mm_t<128, 4, 1>(a, chi, clo, ntiles, st);
-  return launch_tile_mm_t<256, 3, 1>(a, chi, clo, ntiles, st);
+  if (a.active) {
+    if (a.units == 0) return INFO_ESRF_OK;
+    k_tile_units<<<1, 1024, 0, st>>>(a.active, nunits, a.ulist);
+    note_launches(1);
+  } else {
+    a.units = nunits;
+    a.ulist = nullptr;
+  }
+  // up to 8 units (128 systems): a 128-column accumulator and 4 stages; else
+  // up to 16 units per CTA, 3 stages.  (Two 256-column accumulators per CTA,
+  // so that a C block load serves 512 systems, leave room for two stages only
+  // and measured slower: 1225 against 1273 TFLOP/s on the tilemm workload.)
+  if (a.units <= 8) return launch_tile_mm_t<128, 4>(a, chi, clo, ntiles, st);
+  return launch_tile_mm_t<256, 3>(a, chi, clo, ntiles, st);
 }
 
 }  // namespace infoesrf

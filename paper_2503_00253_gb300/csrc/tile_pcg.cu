@@ -120,12 +120,15 @@ __device__ __forceinline__ void mark_retry(const ProblemDev& pr, int64_t j) {
 }
 
 // alpha_j = rho_j / p_j^T y_j (one warp per system: lanes over the row-tile
-// partials, a fixed shuffle tree); resets the chunk flags and the running count.
-__global__ void k_tpcg_alpha(const ProblemDev* dpr, int it, int nchunks, int reset_only) {
+// partials, a fixed shuffle tree); resets the unit flags and the running counts.
+__global__ void k_tpcg_alpha(const ProblemDev* dpr, int it, int nunits, int reset_only) {
   const ProblemDev& pr = *dpr;
   const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gt < nchunks) pr.chunk_active[gt] = 0;
-  if (gt == 0) pr.nactive[0] = 0;
+  if (gt < nunits) pr.unit_active[gt] = 0;
+  if (gt == 0) {
+    pr.nactive[0] = 0;
+    pr.nactive[2] = 0;
+  }
   const int lane = threadIdx.x & 31;
   const int64_t j = gt >> 5;
   if (j >= pr.nsys || reset_only) return;
@@ -340,7 +343,7 @@ __global__ void __launch_bounds__(256) k_tpcg_reduce(const ProblemDev* dpr, int 
 }
 
 // Step 4: one thread per system.
-__global__ void k_tpcg_scalars(const ProblemDev* dpr, int nsub, int bn, int last) {
+__global__ void k_tpcg_scalars(const ProblemDev* dpr, int nsub, int last) {
   const ProblemDev& pr = *dpr;
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j == 0) pr.nactive[1] = pr.status[0];   // timeouts and overflow are set by earlier kernels
@@ -410,7 +413,7 @@ __global__ void k_tpcg_scalars(const ProblemDev* dpr, int nsub, int bn, int last
   sd[kBeta] = first ? 0.0 : rho / sd[kRho];
   sd[kRho] = rho;
   sd[kFirst] = 0.0;
-  pr.chunk_active[j / bn] = 1;
+  if (atomicExch(&pr.unit_active[j / kTileUnit], 1) == 0) atomicAdd(&pr.nactive[2], 1);
   pr.alist[atomicAdd(&pr.nactive[0], 1)] = (int32_t)j;
 }
 
@@ -553,8 +556,7 @@ static int tile_pcg_loop(const ProblemDev& p, const ProblemDev* dp, cudaStream_t
       if (e[1]) cudaEventDestroy(e[1]);
     }
   } destroy{ev};
-  const int bn = tile_chunk_width((int32_t)J);
-  const int nchunks = (int)((J + bn - 1) / bn);
+  const int nunits = (int)((J + kTileUnit - 1) / kTileUnit);
   const int nsub = (int)((p.d_pad + kDotRows - 1) / kDotRows);
   const dim3 gsys((unsigned)((J + 127) / 128));
   const dim3 gall((unsigned)((J * p.d_pad + 255) / 256));
@@ -564,7 +566,8 @@ static int tile_pcg_loop(const ProblemDev& p, const ProblemDev* dp, cudaStream_t
   ta.colblk = p.colblk;
   ta.P = p.Pdir;
   ta.sigma = p.sigmaf;
-  ta.active = p.chunk_active;
+  ta.active = p.unit_active;
+  ta.ulist = p.unit_list;
   ta.Y = p.Yv;
   ta.pty = p.pty;
   ta.status = p.status;
@@ -591,19 +594,19 @@ static int tile_pcg_loop(const ProblemDev& p, const ProblemDev* dp, cudaStream_t
       return INFO_ESRF_ERR_CUDA;
     raised = dev;
   }
-  int32_t host[2] = {0, 0};
+  int32_t host[3] = {0, 0, 0};   // running systems, status bits, active units
   auto update = [&](dim3 grid, int upd, const int32_t* list, int64_t count) {
     if (wide) k_tpcg_update<2><<<grid, kVecThreads, vsm, st>>>(dp, upd, list, count);
     else k_tpcg_update<1><<<grid, kVecThreads, vsm, st>>>(dp, upd, list, count);
   };
-  const dim3 galpha((unsigned)(((32 * J > nchunks ? 32 * J : nchunks) + 255) / 256));
+  const dim3 galpha((unsigned)(((32 * J > nunits ? 32 * J : nunits) + 255) / 256));
   // the first direction of every running system: r = b, z = M r, p = z
   auto start = [&]() {
     update(gvec, 0, nullptr, J);
     if (learned) launch_tile_learn_u(p, dp, nullptr, J, nsub, st);
     k_tpcg_reduce<<<(unsigned)J, 256, 0, st>>>(dp, nsub, nullptr, J);
-    k_tpcg_alpha<<<galpha, 256, 0, st>>>(dp, 0, nchunks, 1);   // resets the chunk flags and the count
-    k_tpcg_scalars<<<gsys, 128, 0, st>>>(dp, nsub, bn, maxit <= 0 ? 1 : 0);
+    k_tpcg_alpha<<<galpha, 256, 0, st>>>(dp, 0, nunits, 1);   // resets the unit flags and the counts
+    k_tpcg_scalars<<<gsys, 128, 0, st>>>(dp, nsub, maxit <= 0 ? 1 : 0);
     k_tpcg_direction<<<gvec, kVecThreads, dsm, st>>>(dp, learned ? 1 : 0);
     note_launches(5);
   };
@@ -617,6 +620,7 @@ static int tile_pcg_loop(const ProblemDev& p, const ProblemDev* dp, cudaStream_t
       if (host[0] == 0) break;
       if (host[1] & (kStatTimeout | kStatTileOverflow)) break;
       const int64_t nrun = host[0];
+      ta.units = host[2];
       const dim3 glist((unsigned)nsub, (unsigned)((nrun + kSys - 1) / kSys));
       if (mm_ms) cudaEventRecord(ev[0], st);
       if (launch_tile_mm(ta, p.Chi, p.Clo, p.tile_cap, st) != 0) return INFO_ESRF_ERR_CUDA;
@@ -625,11 +629,11 @@ static int tile_pcg_loop(const ProblemDev& p, const ProblemDev* dp, cudaStream_t
         timed = true;
       }
       if (cap) launch_tile_capture_record(p, dp, *cap, it, st);
-      k_tpcg_alpha<<<galpha, 256, 0, st>>>(dp, it, nchunks, 0);
+      k_tpcg_alpha<<<galpha, 256, 0, st>>>(dp, it, nunits, 0);
       update(glist, 1, p.alist, nrun);
       if (learned) launch_tile_learn_u(p, dp, p.alist, nrun, nsub, st);
       k_tpcg_reduce<<<(unsigned)nrun, 256, 0, st>>>(dp, nsub, p.alist, nrun);
-      k_tpcg_scalars<<<gsys, 128, 0, st>>>(dp, nsub, bn, it == maxit ? 1 : 0);
+      k_tpcg_scalars<<<gsys, 128, 0, st>>>(dp, nsub, it == maxit ? 1 : 0);
       k_tpcg_direction<<<glist, kVecThreads, dsm, st>>>(dp, learned ? 1 : 0);
       note_launches(5);
     }
