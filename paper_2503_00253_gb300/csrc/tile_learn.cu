@@ -25,7 +25,7 @@ namespace infoesrf {
 
 namespace {
 
-constexpr int kVecThreads = 128;      // as the vector kernels of tile_pcg.cu
+constexpr int kVecThreads = 128;      // 8 systems per CTA, 16 row lanes each
 constexpr int kSys = 8;
 constexpr int kRowLanes = kVecThreads / kSys;
 constexpr int kRows = kTileDotRows;   // rows per CTA (and per partial sum)

@@ -40,9 +40,9 @@ namespace infoesrf {
 
 namespace {
 
-constexpr int kSys = 8;            // systems per CTA in the vector kernels
+constexpr int kSys = 16;           // systems per CTA in the vector kernels
 constexpr int kDotRows = kTileDotRows;   // rows per CTA (and per partial dot product)
-constexpr int kVecThreads = 128;   // four rows per thread
+constexpr int kVecThreads = 256;   // 16 row lanes per system, four rows per lane and step
 // per-system FP64 scalars in sysd[j][8]
 enum { kRho = 0, kAlpha = 1, kBeta = 2, kBn2 = 3, kRr = 4, kFirst = 5 };
 
@@ -167,28 +167,32 @@ __device__ __forceinline__ int64_t listed_system(const int32_t* list, int64_t co
   return list ? list[pos] : pos;
 }
 
-// Row stride (floats) of the staged [Phi | C Phi] rows: 2 k rounded up to a
-// multiple of 4 so that a row is read with 16-byte loads (zero padding).
-__host__ __device__ __forceinline__ int phi_stride(int k) { return (2 * k + 3) & ~3; }
+// Column stride (floats) of the staged [Phi | C Phi]: the block's rows plus
+// 4, so that a column is read along the rows with 16-byte loads (four
+// consecutive rows per thread, consecutive threads on consecutive rows: no
+// bank conflict) and the transposing writes of the staging spread over the
+// banks.
+constexpr int kPhCol = kDotRows + 4;
+__host__ __device__ __forceinline__ size_t phi_stage_bytes(int k) { return (size_t)2 * k * kPhCol * sizeof(float); }
 
-// Stages rows abase .. abase + kDotRows - 1 of [Phi | C Phi] into the padded
-// shared layout phs[row * S2 + m] (m < k: Phi, k <= m < 2k: C Phi, zero
-// padding).  Phi and C Phi are contiguous [d][k] blocks, so each is read with
-// 16-byte loads that are all independent (a block of rows starts at a
-// multiple of 4 floats); rows at or past d are zero.
-__device__ __forceinline__ void stage_phi(const ProblemDev& pr, int64_t abase, int k, int S2, float* phs) {
+// Stages rows abase .. abase + kDotRows - 1 of [Phi | C Phi] transposed into
+// shared memory: pht[m * kPhCol + row] (m < k: Phi, k <= m < 2k: C Phi).
+// Phi and C Phi are contiguous [d][k] blocks, so each is read with 16-byte
+// loads that are all independent (a block of rows starts at a multiple of 4
+// floats); rows at or past d are zero.
+__device__ __forceinline__ void stage_phi(const ProblemDev& pr, int64_t abase, int k, float* pht) {
   const int64_t a1 = abase + kDotRows < pr.d ? abase + kDotRows : pr.d;
   const int nrows = a1 > abase ? (int)(a1 - abase) : 0;
-  const int tot = nrows * k;
-  for (int e = threadIdx.x; e < kDotRows * S2; e += blockDim.x) {
-    const int row = e / S2, m = e - row * S2;
-    if (row >= nrows || m >= 2 * k) phs[e] = 0.f;
+  const int tot = nrows * k, ntail = kDotRows - nrows;
+  for (int e = threadIdx.x; e < 2 * k * ntail; e += blockDim.x) {
+    const int m = e / ntail, row = nrows + e % ntail;
+    pht[m * kPhCol + row] = 0.f;
   }
 #pragma unroll
   for (int which = 0; which < 2; ++which) {
     const float* src = reinterpret_cast<const float*>(which == 0 ? pr.Phi : pr.CPhi) + abase * k;
     const float4* src4 = reinterpret_cast<const float4*>(src);
-    const int off = which * k;
+    float* dst = pht + which * k * kPhCol;
 #pragma unroll 4
     for (int q = threadIdx.x; q < tot / 4; q += blockDim.x) {
       const float4 v = src4[q];
@@ -196,12 +200,12 @@ __device__ __forceinline__ void stage_phi(const ProblemDev& pr, int64_t abase, i
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int e = 4 * q + i, row = e / k, m = e - row * k;
-        phs[row * S2 + off + m] = vv[i];
+        dst[m * kPhCol + row] = vv[i];
       }
     }
     for (int e = (tot & ~3) + threadIdx.x; e < tot; e += blockDim.x) {
       const int row = e / k, m = e - row * k;
-      phs[row * S2 + off + m] = src[e];
+      dst[m * kPhCol + row] = src[e];
     }
   }
 }
@@ -221,9 +225,9 @@ __global__ void __launch_bounds__(kVecThreads) k_tpcg_update(const ProblemDev* d
   const ProblemDev& pr = *dpr;
   const int64_t sb = blockIdx.x;
   const int64_t g0 = (int64_t)blockIdx.y * kSys;
-  const int k = pr.kR, NV = 2 * k + 1, NVD = tile_dot_values(k), S2 = phi_stride(k);
+  const int k = pr.kR, NV = 2 * k + 1, NVD = tile_dot_values(k);
   const int64_t J = pr.nsys, dp = pr.d_pad;
-  extern __shared__ float4 phs_dyn4[];   // [kDotRows][S2 / 4]
+  extern __shared__ float4 phs_dyn4[];   // [2 k][kPhCol / 4]
   float* phs = reinterpret_cast<float*>(phs_dyn4);
   __shared__ float part[kSys][2][32 * NV32];   // per system: the two half-lanes' reduce-scatter results
   __shared__ int64_t sys[kSys];
@@ -239,7 +243,7 @@ __global__ void __launch_bounds__(kVecThreads) k_tpcg_update(const ProblemDev* d
   for (int s = 0; s < kSys; ++s) any |= sys[s] >= 0;
   if (!any) return;
   const int64_t abase = sb * kDotRows;
-  stage_phi(pr, abase, k, S2, phs);
+  stage_phi(pr, abase, k, phs);
   __syncthreads();
   const int s = threadIdx.x / kRowLanes, r0 = threadIdx.x % kRowLanes;
   const int64_t j = sys[s];
@@ -272,21 +276,21 @@ __global__ void __launch_bounds__(kVecThreads) k_tpcg_update(const ProblemDev* d
         *reinterpret_cast<float4*>(pr.Xv + e) = xv;
         *reinterpret_cast<float4*>(pr.Rv + e) = rv;
       }
-      const float rr4[4] = {rv.x, rv.y, rv.z, rv.w};
+      acc[0] = fmaf(rv.x, rv.x, acc[0]);
+      acc[0] = fmaf(rv.y, rv.y, acc[0]);
+      acc[0] = fmaf(rv.z, rv.z, acc[0]);
+      acc[0] = fmaf(rv.w, rv.w, acc[0]);
+      // column m of [Phi | C Phi] at the four rows: one 16-byte load
+      const float4* col4 = phs_dyn4 + r4 / 4;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const float r = rr4[i];
-        acc[0] = fmaf(r, r, acc[0]);
-        const float4* row4 = phs_dyn4 + (r4 + i) * (S2 / 4);
-#pragma unroll
-        for (int q = 0; q < (32 * NV32 - 1) / 4; ++q) {
-          if (4 * q < 2 * k) {
-            const float4 f = row4[q];
-            acc[1 + 4 * q] = fmaf(f.x, r, acc[1 + 4 * q]);
-            acc[2 + 4 * q] = fmaf(f.y, r, acc[2 + 4 * q]);
-            acc[3 + 4 * q] = fmaf(f.z, r, acc[3 + 4 * q]);
-            acc[4 + 4 * q] = fmaf(f.w, r, acc[4 + 4 * q]);
-          }
+      for (int m = 0; m < 32 * NV32 - 1; ++m) {
+        if (m < 2 * k) {
+          const float4 f = col4[m * (kPhCol / 4)];
+          float t = acc[1 + m];
+          t = fmaf(f.x, rv.x, t);
+          t = fmaf(f.y, rv.y, t);
+          t = fmaf(f.z, rv.z, t);
+          acc[1 + m] = fmaf(f.w, rv.w, t);
         }
       }
     }
@@ -425,10 +429,10 @@ __global__ void __launch_bounds__(kVecThreads) k_tpcg_direction(const ProblemDev
   const ProblemDev& pr = *dpr;
   const int64_t sb = blockIdx.x;
   const int64_t g0 = (int64_t)blockIdx.y * kSys;
-  const int k = pr.kR, S2 = phi_stride(k);
+  const int k = pr.kR;
   const int64_t J = pr.nsys, dp = pr.d_pad;
   const int64_t count = pr.nactive[0];   // the list the scalars kernel just built
-  extern __shared__ float4 phs_dyn4[];   // [kDotRows][S2 / 4]
+  extern __shared__ float4 phs_dyn4[];   // [2 k][kPhCol / 4]
   float* phs = reinterpret_cast<float*>(phs_dyn4);
   __shared__ float4 tc4[kSys][2 * kMaxK / 4];   // per system: c (Phi coefficients), then -t (C Phi)
   __shared__ int64_t sys[kSys];
@@ -457,8 +461,8 @@ __global__ void __launch_bounds__(kVecThreads) k_tpcg_direction(const ProblemDev
   }
   if (!any) return;
   const int64_t abase = sb * kDotRows;
-  stage_phi(pr, abase, k, S2, phs);
-  int32_t* nbr_s = reinterpret_cast<int32_t*>(phs + kDotRows * S2);   // [kDotRows][kLatPts]
+  stage_phi(pr, abase, k, phs);
+  int32_t* nbr_s = reinterpret_cast<int32_t*>(phs + 2 * k * kPhCol);   // [kDotRows][kLatPts]
   if (anyl) {
     const int64_t nrow = dp - abase < kDotRows ? dp - abase : kDotRows;
     for (int64_t e = threadIdx.x; e < nrow * kLatPts; e += blockDim.x) nbr_s[e] = pr.lat_nbr[abase * kLatPts + e];
@@ -467,8 +471,8 @@ __global__ void __launch_bounds__(kVecThreads) k_tpcg_direction(const ProblemDev
   for (int e = threadIdx.x; e < kSys * 2 * kMaxK; e += blockDim.x) {
     const int s = e / (2 * kMaxK), m = e % (2 * kMaxK);
     float v = 0.f;
-    if (sys[s] >= 0 && m < S2) {
-      // aligned with the staged row: Phi columns take c, C Phi columns take -t
+    if (sys[s] >= 0) {
+      // aligned with the staged columns: Phi columns take c, C Phi columns take -t
       if (m < k) v = pr.lcoef[sys[s] * 2 * kMaxK + kMaxK + m];
       else if (m < 2 * k) v = -pr.lcoef[sys[s] * 2 * kMaxK + (m - k)];
     }
@@ -495,19 +499,22 @@ __global__ void __launch_bounds__(kVecThreads) k_tpcg_direction(const ProblemDev
     const float2 p01 = __bfloat1622float2(pp[0]), p23 = __bfloat1622float2(pp[1]);
     float z[4] = {rv.x, rv.y, rv.z, rv.w};
     const float pv[4] = {p01.x, p01.y, p23.x, p23.y};
+    // column m of [Phi | C Phi] at the four rows: one 16-byte load
+    const float4* col4 = phs_dyn4 + r4 / 4;
+    const float* cs = tcf + s * 2 * kMaxK;
+#pragma unroll
+    for (int m = 0; m < 2 * kMaxK; ++m) {
+      if (m < 2 * k) {
+        const float4 f = col4[m * (kPhCol / 4)];
+        const float c = cs[m];
+        z[0] = fmaf(f.x, c, z[0]);
+        z[1] = fmaf(f.y, c, z[1]);
+        z[2] = fmaf(f.z, c, z[2]);
+        z[3] = fmaf(f.w, c, z[3]);
+      }
+    }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const float4* row4 = phs_dyn4 + (r4 + i) * (S2 / 4);
-#pragma unroll
-      for (int q = 0; q < 2 * kMaxK / 4; ++q) {
-        if (4 * q < 2 * k) {
-          const float4 f = row4[q], c = tc4[s][q];
-          z[i] = fmaf(f.x, c.x, z[i]);
-          z[i] = fmaf(f.y, c.y, z[i]);
-          z[i] = fmaf(f.z, c.z, z[i]);
-          z[i] = fmaf(f.w, c.w, z[i]);
-        }
-      }
       if (sl) {   // z = a P^-1 r + S u
         const int32_t* nb = nbr_s + (r4 + i) * kLatPts;
         float su = 0.f;
@@ -579,14 +586,14 @@ static int tile_pcg_loop(const ProblemDev& p, const ProblemDev* dp, cudaStream_t
   if (cap) maxit = cap->K;
   // the learned term is possible when the problem has a model and its tables
   bool learned = !cap && p.learned_model && p.learn_on && p.lat_info;
-  const size_t vsm = (size_t)kDotRows * phi_stride(p.kR) * sizeof(float);
+  const size_t vsm = phi_stage_bytes(p.kR);
   size_t dsm = vsm;   // + the stencil table while learned systems run (set below)
   const bool wide = 2 * p.kR > 28;   // k > 14: 64-value dot vectors (the 32-value loop covers 28 columns)
   static thread_local int raised = -1;
   int dev = 0;
   cudaGetDevice(&dev);
   if (raised != dev) {
-    const int mx = (int)((size_t)kDotRows * phi_stride(kMaxK) * sizeof(float));
+    const int mx = (int)phi_stage_bytes(kMaxK);
     const int mxd = mx + kDotRows * kLatPts * (int)sizeof(int32_t);
     if (cudaFuncSetAttribute(k_tpcg_update<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess ||
         cudaFuncSetAttribute(k_tpcg_update<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess ||
