@@ -618,7 +618,10 @@ def _measured_peaks():
         return {}
 
 
-def config5_record(B, dev, steps, warmup, no_parity=False, ritz=RITZ, learned_term=True):
+SMALL_2D = {"nx": 512, "half_width": 48.0, "Q": 8}   # profiling case of the 2-D family: a few GB on the device
+
+
+def config5_record(B, dev, steps, warmup, no_parity=False, ritz=RITZ, learned_term=True, small=False):
     """The 2-D workload at full size: periodic 1024 x 1024 grid (n = 1,048,576), N = 80 from a
     Gaussian covariance with length scale 32 cells, observations every 2nd cell in each direction
     (d = 262,144), R = 0.5, Gaspari-Cohn half-width 96 cells, Q = 32 (2560 + 1 systems), on the BF16
@@ -632,7 +635,10 @@ def config5_record(B, dev, steps, warmup, no_parity=False, ritz=RITZ, learned_te
     Krylov samples of the BF16 path from two problems of the same geometry on a 512 x 512 grid
     (seeds 51, 52; 12 directions of 3 members per node, 300 Adam steps), with the shift cut-off
     chosen by the plain-PCG judge on those problems; the timed analyses use it where the judge
-    keeps it."""
+    keeps it.
+
+    small: the same family on a 512 x 512 grid with GC half-width 48 cells and Q = 8 (d = 65,536,
+    641 systems, about 3 GB of C blocks), the case that ncu captures of the path's kernels use."""
     import numpy as np
     import torch
 
@@ -649,7 +655,15 @@ def config5_record(B, dev, steps, warmup, no_parity=False, ritz=RITZ, learned_te
                       "loss_first": float(hist[0]), "loss_last": float(hist[-1]), "max_shift": cutoff}
         del train
     t0 = time.perf_counter()
-    pr = workloads.config5(tol=TOL_MIXED)
+    if small:
+        pr = workloads.gaussian_problem_2d(nx=SMALL_2D["nx"], ny=SMALL_2D["nx"], N=80, length_scale=32.0,
+                                           obs_stride=2, r2=0.5, half_width=SMALL_2D["half_width"],
+                                           Q=SMALL_2D["Q"], tol=TOL_MIXED, seed=5)
+        label = "gauss2d_{0}x{0}_N80_d{1}_Q{2}_R0.5_gc{3:g} ({4} shifted systems + mean)".format(
+            SMALL_2D["nx"], pr.d, SMALL_2D["Q"], SMALL_2D["half_width"], SMALL_2D["Q"] * 80)
+    else:
+        pr = workloads.config5(tol=TOL_MIXED)
+        label = "gauss2d_1024x1024_N80_d262144_Q32_R0.5_gc96 (2560 shifted systems + mean)"
     gen_s = time.perf_counter() - t0
     X = torch.tensor(pr.X, device=dev)
     obs = torch.tensor(pr.obs_idx, device=dev)
@@ -691,7 +705,7 @@ def config5_record(B, dev, steps, warmup, no_parity=False, ritz=RITZ, learned_te
     peak = peaks.get("bf16_tflops_sustained")
     achieved = flops / (mm_ms * 1e-3) / 1e12
     issued_per_alg = (st["tile_blocks"] * 128 * 64 * 2.0) / st["c_nnz"]
-    rec = {"workload": "gauss2d_1024x1024_N80_d262144_Q32_R0.5_gc96 (2560 shifted systems + mean)",
+    rec = {"workload": label,
            "precision": "bf16 tensor-core matvec (C as hi + lo BF16 planes, BF16 directions), fp32 vectors, "
                         "fp64 scalars and quadrature sum",
            "value": 1e3 / statistics.mean(times), "unit": UNIT, "ms_per_step": statistics.mean(times),
@@ -733,8 +747,9 @@ def run_config5(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     B.library()
+    small = args.workload == "gauss2d_512"
     rec = config5_record(B, dev, args.steps, args.warmup, args.no_parity, args.ritz,
-                         learned_term=not args.no_config5_learned)
+                         learned_term=not args.no_config5_learned and not small, small=small)
     line = {"metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": rec["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
@@ -948,19 +963,21 @@ def main():
                     help="2-D record without training the lattice form of the learned correction")
     ap.add_argument("--ritz", type=int, default=RITZ, help="Ritz rank of the preconditioner (config5)")
     ap.add_argument("--workload", default="config2",
-                    choices=["config2", "batched64", "config5", "tilemm", "band_phases", "general_h"],
+                    choices=["config2", "batched64", "config5", "gauss2d_512", "tilemm", "band_phases",
+                             "general_h"],
                     help="config2: the headline single analysis; batched64: 64 uneven problems in one batched "
-                         "call against 64 single calls; band_phases: per-round phase cycles of the band PCG "
+                         "call against 64 single calls; gauss2d_512: the 2-D BF16 path on a 512 x 512 grid "
+                         "(profiling case); band_phases: per-round phase cycles of the band PCG "
                          "kernel (instrumented build)")
     args = ap.parse_args()
-    if args.warmup < 3 and args.workload != "config5":
+    if args.warmup < 3 and args.workload not in ("config5", "gauss2d_512"):
         args.warmup = 3   # config5: one analysis takes seconds; --warmup as given (at least 1)
     args.warmup = max(args.warmup, 1)
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched64":
         run_batched(args)
-    elif args.workload == "config5":
+    elif args.workload in ("config5", "gauss2d_512"):
         run_config5(args)
     elif args.workload == "tilemm":
         run_tilemm(args)

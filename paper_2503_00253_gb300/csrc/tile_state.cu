@@ -82,6 +82,43 @@ __device__ __forceinline__ uint4 pack8(const float* v) {
 
 __device__ __forceinline__ float bf16_round(float a) { return __bfloat162float(__float2bfloat16_rn(a)); }
 
+// The FP32 values of the packed BF16 pairs of w (.x = the first value, in the low half).
+__device__ __forceinline__ void unpack8(const uint4& w, float* v) {
+  const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    v[2 * i] = __uint_as_float(u[i] << 16);
+    v[2 * i + 1] = __uint_as_float(u[i] & 0xffff0000u);
+  }
+}
+
+// Eight FP32 values as two BF16 planes: hi = bf16(v), lo = bf16(v - hi).
+__device__ __forceinline__ void split8x2(const float* v, uint4& hi, uint4& lo) {
+  hi = pack8(v);
+  float h[8], r[8];
+  unpack8(hi, h);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) r[i] = v[i] - h[i];
+  lo = pack8(r);
+}
+
+// Gaspari-Cohn correlation at z = r / c >= 0 (Gaspari & Cohn 1999, Eq. 4.10),
+// branch-free: one degree-5 Horner form whose coefficients are selected by the
+// piece (z <= 1, 1 < z < 2), the rational term -2 / (3 z) of the outer piece,
+// zero from z = 2.  Lanes of a warp take different points, so a branch on the
+// piece would run both polynomials.
+__device__ __forceinline__ float gc_select(float z) {
+  const bool outer = z > 1.f;
+  const float a = outer ? (1.f / 12.f) : -0.25f;
+  const float b = outer ? -0.5f : 0.5f;
+  const float d = outer ? (5.f / 3.f) : (-5.f / 3.f);
+  const float e = outer ? -5.f : 0.f;
+  const float f = outer ? 4.f : 1.f;
+  float p = fmaf(fmaf(fmaf(fmaf(fmaf(a, z, b), z, 0.625f), z, d), z, e), z, f);
+  p = outer ? fmaf(-2.f / 3.f, __frcp_rn(z), p) : p;
+  return z < 2.f ? p : 0.f;
+}
+
 // Eight FP32 values as NP BF16 planes (16 bytes each): plane i holds the
 // rounding of what the planes before it leave.
 template <int NP>
@@ -168,9 +205,9 @@ __global__ void __launch_bounds__(kStThreads, 1)
                                                          ~static_cast<uintptr_t>(1023));
   const GridDev& g = pr.grid;
   const int64_t next = g.ext[0] + g.ext[1] + g.ext[2];
-  const bool d2s = next <= kD2St;
+  // the distance table in shared memory (the launcher checks next <= kD2St)
   const int NV = pr.st_NV;
-  const StLayout Lo = st_layout(NV, d2s ? (int)next : 0);
+  const StLayout Lo = st_layout(NV, (int)next);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + Lo.ctrl);
   uint64_t* empty = full + kStages;
   uint64_t* sfull = empty + kStages;
@@ -231,8 +268,7 @@ __global__ void __launch_bounds__(kStThreads, 1)
       for (int p = 0; p < 3; ++p) *reinterpret_cast<uint4*>(smem + Lo.z + (2 * p + half) * kHalf + off) = pl[p];
     }
   }
-  if (d2s)
-    for (int64_t e = tid; e < next; e += blockDim.x) d2[e] = (float)pr.d2tab[e];
+  for (int64_t e = tid; e < next; e += blockDim.x) d2[e] = (float)pr.d2tab[e];
   fence_proxy_async();
   tc_fence_before();
   __syncthreads();
@@ -326,7 +362,10 @@ __global__ void __launch_bounds__(kStThreads, 1)
     const int64_t x = x0 + row;
     const bool xin = x < pr.n;
     const Coord3 cx = flat_to_coord(g, xin ? x : 0);
-    const int64_t ca[3] = {cx.x, cx.y, cx.z};
+    const int cxi = (int)cx.x, cyi = (int)cx.y, czi = (int)cx.z;
+    // offsets of the y and z axes in the distance table; distance 0 has entry 0, so an axis of
+    // extent 1 adds nothing
+    const int offy = (int)g.ext[0], offz = (int)(g.ext[0] + g.ext[1]);
     const uint32_t trow = (uint32_t)(quad * 32) << 16;
     unsigned char* s_hi = smem + Lo.s;
     const unsigned char* side = smem + Lo.stage + Lo.w_bytes + Lo.v_bytes;   // stage 0 (one stage)
@@ -353,18 +392,9 @@ __global__ void __launch_bounds__(kStThreads, 1)
 #pragma unroll
       for (int c = 0; c < 32; ++c) {
         const int4 ob = cs[half * 32 + c];
-        const int64_t cbv[3] = {ob.x, ob.y, ob.z};
-        float r2 = 0.f;
-        int64_t off = 0;
-#pragma unroll
-        for (int ax = 0; ax < 3; ++ax) {
-          if (g.ext[ax] > 1) {
-            const int64_t dl = ca[ax] > cbv[ax] ? ca[ax] - cbv[ax] : cbv[ax] - ca[ax];
-            r2 += d2s ? d2[off + dl] : (float)pr.d2tab[off + dl];
-          }
-          off += g.ext[ax];
-        }
-        sv[c] = (ob.w >= 0 && r2 < 4.f) ? gaspari_cohn_f(sqrtf(r2)) * sv[c] : 0.f;
+        const float r2 = (d2[abs(cxi - ob.x)] + d2[offy + abs(cyi - ob.y)]) + d2[offz + abs(czi - ob.z)];
+        const float z = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
+        sv[c] = (ob.w >= 0 && r2 < 4.f) ? gc_select(z) * sv[c] : 0.f;
         mb = fmaf(sv[c], vm[half * 32 + c], mb);
       }
       macc += (double)mb;
@@ -375,11 +405,11 @@ __global__ void __launch_bounds__(kStThreads, 1)
       }
 #pragma unroll
       for (int chunk = 0; chunk < 4; ++chunk) {
-        uint4 pl[2];
-        split8<2>(sv + 8 * chunk, pl);
+        uint4 hi, lo;
+        split8x2(sv + 8 * chunk, hi, lo);
         const uint32_t off = sw128_off(row, half * 4 + chunk);
-        *reinterpret_cast<uint4*>(s_hi + off) = pl[0];
-        *reinterpret_cast<uint4*>(s_hi + kHalf + off) = pl[1];
+        *reinterpret_cast<uint4*>(s_hi + off) = hi;
+        *reinterpret_cast<uint4*>(s_hi + kHalf + off) = lo;
       }
       fence_proxy_async();
       tc_fence_before();
@@ -431,7 +461,8 @@ __global__ void __launch_bounds__(kStThreads, 1)
 namespace infoesrf {
 
 // Launches the tensor-core state update for every problem of the table (all
-// BF16 with N <= kStK, and shared memory for one block's operands); returns -1
+// BF16 with N <= kStK, grid extents summing to at most kD2St, and shared
+// memory for one block's operands); returns -1
 // without launching anything when one of them does not qualify or the device
 // cannot be configured, and the caller runs the CUDA-core kernel instead.
 int launch_tile_state_mma(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st) {
@@ -446,9 +477,9 @@ int launch_tile_state_mma(const ProblemTable& tab, const ProblemDev* dtab, cudaS
   int64_t nmax = 0;
   for (int i = 0; i < tab.count; ++i) {
     const ProblemDev& p = tab.p[i];
-    if (p.precision != 2 || !p.st_W || p.N > kStK || p.st_NV > kStK || p.st_NV < 16) return -1;
     const int64_t next = p.grid.ext[0] + p.grid.ext[1] + p.grid.ext[2];
-    const size_t need = 1024 + st_layout(p.st_NV, next <= kD2St ? (int)next : 0).total;
+    if (p.precision != 2 || !p.st_W || p.N > kStK || p.st_NV > kStK || p.st_NV < 16 || next > kD2St) return -1;
+    const size_t need = 1024 + st_layout(p.st_NV, (int)next).total;
     smax = need > smax ? need : smax;
     const int64_t np = std::max<int64_t>(p.d_pad * kStK, (int64_t)p.st_NV * p.d_pad);
     nmax = np > nmax ? np : nmax;
