@@ -21,7 +21,10 @@
 // quadrant, one state point and half of the block's observations per thread)
 // read S from tensor memory, apply the Gaspari-Cohn weights, add the mean
 // column's terms, split S and write it to shared memory as the A operand of the
-// second product, and finally write A_a and mu_a.  Z_tile is split and placed in shared memory once
+// second product, and finally write A_a and mu_a.  Pipelined: S has two TMEM
+// buffers and W is free once the first product of its block is done, so the
+// loads and the first product of block b + 1 run during the weighting of
+// block b; the coordinates have two buffers, Vbar^T and the S planes one.  Z_tile is split and placed in shared memory once
 // per CTA.  All waits are bounded (kStatTimeout).
 #include <cuda_bf16.h>
 
@@ -40,11 +43,10 @@ constexpr int kStThreads = 320;   // warps 0-7 epilogue (two per TMEM lane quadr
 constexpr int kSideBytes = kTileK * 16 + kTileK * 4;   // a block's grid coordinates and mean-column values
 constexpr int kHalf = kTileM * 64 * 2;         // one 64-member half of a 128-row BF16 operand: 16 KB
 constexpr int kWHalf = kTileK * 64 * 2;        // one 64-member half of the W block: 8 KB
-constexpr int kStages = 1;                     // shared memory holds one block's operands
 
 struct StLayout {
   int NV;
-  uint32_t z, s, stage, stage_bytes, w_bytes, v_bytes, ctrl, d2, total;
+  uint32_t z, s, stage, w_bytes, v_bytes, side, ctrl, d2, total;
 };
 
 __host__ __device__ inline StLayout st_layout(int NV, int nd2) {
@@ -54,9 +56,9 @@ __host__ __device__ inline StLayout st_layout(int NV, int nd2) {
   L.s = 6 * kHalf;                                 // S planes hi, lo
   L.w_bytes = 6 * kWHalf;                          // W planes h, m, l (two halves each)
   L.v_bytes = 2 * (uint32_t)NV * 128;              // Vbar^T hi, lo: NV rows of 64 observations
-  L.stage_bytes = L.w_bytes + L.v_bytes + kSideBytes;
-  L.stage = L.s + 2 * kHalf;
-  L.ctrl = L.stage + kStages * L.stage_bytes;
+  L.stage = L.s + 2 * kHalf;                       // W, then Vbar^T, then two side buffers
+  L.side = L.stage + L.w_bytes + L.v_bytes;
+  L.ctrl = L.side + 2 * kSideBytes;
   L.d2 = L.ctrl + 256;
   L.total = L.d2 + 4 * (uint32_t)nd2;
   return L;
@@ -208,14 +210,18 @@ __global__ void __launch_bounds__(kStThreads, 1)
   // the distance table in shared memory (the launcher checks next <= kD2St)
   const int NV = pr.st_NV;
   const StLayout Lo = st_layout(NV, (int)next);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + Lo.ctrl);
-  uint64_t* empty = full + kStages;
-  uint64_t* sfull = empty + kStages;
-  uint64_t* sready = sfull + 1;
-  uint64_t* sfree = sready + 1;
-  uint64_t* accf = sfree + 1;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(accf + 1);
-  int* flags = reinterpret_cast<int*>(tslot + 1);   // [0] abort, [1] blocks loaded, [2] blocks consumed, [3] skip
+  // Barriers, one phase per block b unless noted.  A waiter never falls two
+  // phases behind: each next completion depends on the waiter having passed.
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + Lo.ctrl);
+  uint64_t* wfull = bar + 0;     // W(b) landed                                  (MMA)
+  uint64_t* vfull = bar + 1;     // Vbar^T(b) landed                             (MMA)
+  uint64_t* xfull = bar + 2;     // [2] side buffer b % 2 landed, phase b / 2    (epilogue)
+  uint64_t* g1done = bar + 4;    // [2] S(b) in TMEM buffer b % 2, phase b / 2   (epilogue, loads)
+  uint64_t* g2done = bar + 6;    // second product of b done: Vbar^T and the S planes free (loads, epilogue)
+  uint64_t* sready = bar + 7;    // S planes of b written, TMEM buffer b % 2 read (MMA; 256 arrivals)
+  uint64_t* accf = bar + 8;      // every MMA done
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 9);
+  int* flags = reinterpret_cast<int*>(tslot + 1);   // [0] abort, [1] W/side loads issued, [2] Vbar loads, [3] skip
   float* d2 = reinterpret_cast<float*>(smem + Lo.d2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t st = blockIdx.x;
@@ -228,14 +234,7 @@ __global__ void __launch_bounds__(kStThreads, 1)
   const int64_t x0 = st * kTileM;
   const int N = (int)pr.N;
   if (tid == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
-    }
-    mbar_init(sfull, 1);
-    mbar_init(sready, 256);
-    mbar_init(sfree, 1);
-    mbar_init(accf, 1);
+    for (int i = 0; i < 9; ++i) mbar_init(bar + i, i == 7 ? 256 : 1);
     flags[0] = 0;
     flags[1] = 0;
     flags[2] = 0;
@@ -274,85 +273,102 @@ __global__ void __launch_bounds__(kStThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  const uint32_t t_s = tmem, t_acc = tmem + 64;
+  const uint32_t t_s = tmem, t_acc = tmem + 2 * kTileK;   // S buffers at columns 0 and 64, acc at 128
 
   if (warp == 8) {
     if (lane == 0) {
-      // producer: W_blk (three planes, two 64-member halves each) and Vbar_blk^T (hi, lo)
-      int kb = 0;
+      // loads: W_blk (three planes, two 64-member halves each) with the block's
+      // coordinates and mean-column values, then Vbar_blk^T (hi, lo)
+      int kb = 0, kv = 0;
       for (; kb < nk; ++kb) {
-        const int s = kb % kStages;
-        if (kb >= kStages && !mbar_wait(&empty[s], ((kb / kStages) & 1) ^ 1)) {
+        // W is free once the first product of kb - 1 is done; side buffer kb % 2 once the
+        // weighting of kb - 2 is, which the wait for Vbar below covered in the previous step
+        if (kb >= 1 && !mbar_wait(&g1done[(kb - 1) & 1], ((kb - 1) >> 1) & 1)) {
           atomicExch(&flags[0], 1);
           break;
         }
         if (*reinterpret_cast<volatile int*>(&flags[0])) break;
-        unsigned char* sp = smem + Lo.stage + s * Lo.stage_bytes;
         const int row = pr.st_colblk[t0 + kb] * kTileK;
-        mbar_arrive_expect_tx(&full[s], Lo.stage_bytes);
-        tma_load_2d(sp, &map_w0, &full[s], 0, row);
-        tma_load_2d(sp + kWHalf, &map_w0, &full[s], 64, row);
-        tma_load_2d(sp + 2 * kWHalf, &map_w1, &full[s], 0, row);
-        tma_load_2d(sp + 3 * kWHalf, &map_w1, &full[s], 64, row);
-        tma_load_2d(sp + 4 * kWHalf, &map_w2, &full[s], 0, row);
-        tma_load_2d(sp + 5 * kWHalf, &map_w2, &full[s], 64, row);
-        tma_load_2d(sp + Lo.w_bytes, &map_vh, &full[s], row, 0);
-        tma_load_2d(sp + Lo.w_bytes + NV * 128, &map_vl, &full[s], row, 0);
-        bulk_load(sp + Lo.w_bytes + Lo.v_bytes, pr.st_xyz + row, kTileK * 16, &full[s]);
-        bulk_load(sp + Lo.w_bytes + Lo.v_bytes + kTileK * 16, pr.st_vm + row, kTileK * 4, &full[s]);
+        unsigned char* wp = smem + Lo.stage;
+        mbar_arrive_expect_tx(wfull, Lo.w_bytes);
+        tma_load_2d(wp, &map_w0, wfull, 0, row);
+        tma_load_2d(wp + kWHalf, &map_w0, wfull, 64, row);
+        tma_load_2d(wp + 2 * kWHalf, &map_w1, wfull, 0, row);
+        tma_load_2d(wp + 3 * kWHalf, &map_w1, wfull, 64, row);
+        tma_load_2d(wp + 4 * kWHalf, &map_w2, wfull, 0, row);
+        tma_load_2d(wp + 5 * kWHalf, &map_w2, wfull, 64, row);
+        unsigned char* xp = smem + Lo.side + (kb & 1) * kSideBytes;
+        mbar_arrive_expect_tx(&xfull[kb & 1], kSideBytes);
+        bulk_load(xp, pr.st_xyz + row, kTileK * 16, &xfull[kb & 1]);
+        bulk_load(xp + kTileK * 16, pr.st_vm + row, kTileK * 4, &xfull[kb & 1]);
+        flags[1] = kb + 1;
+        // Vbar^T is free once the second product of kb - 1 is done
+        if (kb >= 1 && !mbar_wait(g2done, (kb - 1) & 1)) {
+          atomicExch(&flags[0], 1);
+          break;
+        }
+        unsigned char* vp = smem + Lo.stage + Lo.w_bytes;
+        mbar_arrive_expect_tx(vfull, Lo.v_bytes);
+        tma_load_2d(vp, &map_vh, vfull, row, 0);
+        tma_load_2d(vp + NV * 128, &map_vl, vfull, row, 0);
+        kv = kb + 1;
+        flags[2] = kv;
       }
-      flags[1] = kb;
     }
   } else if (warp == 9) {
     if (lane == 0) {
-      // MMA issuer: S = Z W^T (six terms, two halves), then acc += S Vbar (three terms)
+      // MMAs, software-pipelined: the first product of it, then the second of it - 1
+      //   S(it) = Z W(it)^T (six terms, two halves) into TMEM buffer it % 2
+      //   acc += (GC o S(it - 1)) Vbar(it - 1) (three terms)
       const uint32_t id1 = idesc_bf16_f32(kTileM, kTileK), id2 = idesc_bf16_f32(kTileM, NV);
       const uint32_t zb = smem_u32(smem + Lo.z), sb = smem_u32(smem + Lo.s);
-      int kb = 0;
-      for (; kb < nk; ++kb) {
-        const int s = kb % kStages;
-        if (!mbar_wait(&full[s], (kb / kStages) & 1)) {
-          atomicExch(&flags[0], 1);
-          break;
-        }
-        if (*reinterpret_cast<volatile int*>(&flags[0])) break;
-        tc_fence_after();
-        const uint32_t wb = smem_u32(smem + Lo.stage + s * Lo.stage_bytes);
-        const uint32_t vb = wb + Lo.w_bytes;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const uint64_t z0 = sw128_desc(zb + h * kHalf), z1 = sw128_desc(zb + (2 + h) * kHalf),
-                         z2 = sw128_desc(zb + (4 + h) * kHalf);
-          const uint64_t w0 = sw128_desc(wb + h * kWHalf), w1 = sw128_desc(wb + (2 + h) * kWHalf),
-                         w2 = sw128_desc(wb + (4 + h) * kWHalf);
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {   // K = 16 per MMA: 32 bytes along the swizzled row
-            mma_bf16(t_s, z0 + 2 * k, w0 + 2 * k, id1, (h | k) != 0 ? 1u : 0u);
-            mma_bf16(t_s, z0 + 2 * k, w1 + 2 * k, id1, 1u);
-            mma_bf16(t_s, z1 + 2 * k, w0 + 2 * k, id1, 1u);
-            mma_bf16(t_s, z0 + 2 * k, w2 + 2 * k, id1, 1u);
-            mma_bf16(t_s, z2 + 2 * k, w0 + 2 * k, id1, 1u);
-            mma_bf16(t_s, z1 + 2 * k, w1 + 2 * k, id1, 1u);
+      const uint32_t wb = smem_u32(smem + Lo.stage), vb = wb + Lo.w_bytes;
+      for (int it = 0; it <= nk; ++it) {
+        if (it < nk) {
+          if (!mbar_wait(wfull, it & 1)) {
+            atomicExch(&flags[0], 1);
+            break;
           }
-        }
-        mma_commit(sfull);
-        if (!mbar_wait(sready, kb & 1)) {
-          atomicExch(&flags[0], 1);
-          break;
-        }
-        tc_fence_after();
-        const uint64_t sh = sw128_desc(sb), sl = sw128_desc(sb + kHalf);
-        const uint64_t vh = sw128_desc(vb), vl = sw128_desc(vb + NV * 128);
+          if (*reinterpret_cast<volatile int*>(&flags[0])) break;
+          tc_fence_after();
+          const uint32_t ts = t_s + (uint32_t)((it & 1) * kTileK);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          mma_bf16(t_acc, sh + 2 * k, vh + 2 * k, id2, (kb | k) != 0 ? 1u : 0u);
-          mma_bf16(t_acc, sh + 2 * k, vl + 2 * k, id2, 1u);
-          mma_bf16(t_acc, sl + 2 * k, vh + 2 * k, id2, 1u);
+          for (int h = 0; h < 2; ++h) {
+            const uint64_t z0 = sw128_desc(zb + h * kHalf), z1 = sw128_desc(zb + (2 + h) * kHalf),
+                           z2 = sw128_desc(zb + (4 + h) * kHalf);
+            const uint64_t w0 = sw128_desc(wb + h * kWHalf), w1 = sw128_desc(wb + (2 + h) * kWHalf),
+                           w2 = sw128_desc(wb + (4 + h) * kWHalf);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {   // K = 16 per MMA: 32 bytes along the swizzled row
+              if (16 * (4 * h + k) >= N) break;   // members past N are zero in both operands
+              mma_bf16(ts, z0 + 2 * k, w0 + 2 * k, id1, (h | k) != 0 ? 1u : 0u);
+              mma_bf16(ts, z0 + 2 * k, w1 + 2 * k, id1, 1u);
+              mma_bf16(ts, z1 + 2 * k, w0 + 2 * k, id1, 1u);
+              mma_bf16(ts, z0 + 2 * k, w2 + 2 * k, id1, 1u);
+              mma_bf16(ts, z2 + 2 * k, w0 + 2 * k, id1, 1u);
+              mma_bf16(ts, z1 + 2 * k, w1 + 2 * k, id1, 1u);
+            }
+          }
+          mma_commit(&g1done[it & 1]);
         }
-        mma_commit(&empty[s]);
-        mma_commit(sfree);
+        if (it >= 1) {
+          const int kb = it - 1;
+          if (!mbar_wait(sready, kb & 1) || !mbar_wait(vfull, kb & 1)) {
+            atomicExch(&flags[0], 1);
+            break;
+          }
+          tc_fence_after();
+          const uint64_t sh = sw128_desc(sb), sl = sw128_desc(sb + kHalf);
+          const uint64_t vh = sw128_desc(vb), vl = sw128_desc(vb + NV * 128);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            mma_bf16(t_acc, sh + 2 * k, vh + 2 * k, id2, (kb | k) != 0 ? 1u : 0u);
+            mma_bf16(t_acc, sh + 2 * k, vl + 2 * k, id2, 1u);
+            mma_bf16(t_acc, sl + 2 * k, vh + 2 * k, id2, 1u);
+          }
+          mma_commit(g2done);
+        }
       }
-      flags[2] = kb;
       mma_commit(accf);
     }
   } else {
@@ -368,22 +384,23 @@ __global__ void __launch_bounds__(kStThreads, 1)
     const int offy = (int)g.ext[0], offz = (int)(g.ext[0] + g.ext[1]);
     const uint32_t trow = (uint32_t)(quad * 32) << 16;
     unsigned char* s_hi = smem + Lo.s;
-    const unsigned char* side = smem + Lo.stage + Lo.w_bytes + Lo.v_bytes;   // stage 0 (one stage)
-    const int4* cs = reinterpret_cast<const int4*>(side);
-    const float* vm = reinterpret_cast<const float*>(side + kTileK * 16);
     double macc = 0.0;   // this half's part of the mean column, FP64 across blocks
     // exits are warp-uniform: the TMEM loads below are warp-collective
     for (int kb = 0; kb < nk; ++kb) {
-      if (!__all_sync(0xffffffffu, mbar_wait(sfull, kb & 1) && mbar_wait(&full[0], kb & 1))) {
+      const int bf = kb & 1, ph = (kb >> 1) & 1;
+      if (!__all_sync(0xffffffffu, mbar_wait(&g1done[bf], ph) && mbar_wait(&xfull[bf], ph))) {
         atomicExch(&flags[0], 1);
         break;
       }
       tc_fence_after();
+      const unsigned char* side = smem + Lo.side + bf * kSideBytes;
+      const int4* cs = reinterpret_cast<const int4*>(side);
+      const float* vm = reinterpret_cast<const float*>(side + kTileK * 16);
       float sv[32];
 #pragma unroll
       for (int c0 = 0; c0 < 32; c0 += 16) {
         float v[16];
-        tmem_ld16(t_s + trow + (uint32_t)(half * 32 + c0), v);
+        tmem_ld16(t_s + (uint32_t)(bf * kTileK) + trow + (uint32_t)(half * 32 + c0), v);
 #pragma unroll
         for (int i = 0; i < 16; ++i) sv[c0 + i] = v[i];
       }
@@ -399,7 +416,7 @@ __global__ void __launch_bounds__(kStThreads, 1)
       }
       macc += (double)mb;
       // the second product of the previous block has read the S planes
-      if (kb > 0 && !__all_sync(0xffffffffu, mbar_wait(sfree, (kb - 1) & 1))) {
+      if (kb > 0 && !__all_sync(0xffffffffu, mbar_wait(g2done, (kb - 1) & 1))) {
         atomicExch(&flags[0], 1);
         break;
       }
@@ -446,8 +463,15 @@ __global__ void __launch_bounds__(kStThreads, 1)
   tc_fence_before();
   __syncthreads();
   if (tid == 0 && flags[0]) {
-    // wait (bounded) for the loads still in flight before the CTA's shared memory goes away
-    for (int kb = flags[2]; kb < flags[1]; ++kb) mbar_wait(&full[kb % kStages], (kb / kStages) & 1);
+    // wait (bounded) for the loads still in flight before the CTA's shared memory goes away:
+    // each barrier has at most its last issued phase outstanding
+    const int nw = flags[1], nv = flags[2];
+    if (nw > 0) mbar_wait(wfull, (nw - 1) & 1);
+    if (nv > 0) mbar_wait(vfull, (nv - 1) & 1);
+    for (int b = 0; b < 2; ++b) {
+      const int cnt = nw > b ? (nw - b + 1) / 2 : 0;   // side loads into buffer b
+      if (cnt > 0) mbar_wait(&xfull[b], (cnt - 1) & 1);
+    }
     atomicOr(&pr.status[0], kStatTimeout);
   }
   __syncthreads();
