@@ -50,7 +50,7 @@ struct TileMmArgs {
   const int32_t* rowptr;        // [nrt + 1] first block of each row tile
   const int32_t* colblk;        // [tiles] column block of each stored block
   const __nv_bfloat16* P;       // [J][d_pad] directions
-  const float* sigma;           // [J] shifts
+  const float* sigma;           // [J] shifts (NULL: zero)
   const int32_t* active;        // [ceil(J / 16)] nonzero: the unit of 16 systems has an unconverged one (or NULL: all)
   float* Y;                     // [J][d_pad] sigma p + C p
   float* pty;                   // partial p^T y per row tile (or NULL): [nrt][J], or [J][nrt] if pty_by_system

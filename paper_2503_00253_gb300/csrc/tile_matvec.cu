@@ -108,6 +108,8 @@ __global__ void __launch_bounds__(128, 1)
   float* red = reinterpret_cast<float*>(ctrl + Shape::kCtrl);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // an overflowed block pattern is not read (uniform across the grid)
+  if (args.status && (*reinterpret_cast<volatile int32_t*>(args.status) & kStatTileOverflow)) return;
   const int chunk = (int)(blockIdx.x % (unsigned)args.nchunks);
   const int rt = (int)(blockIdx.x / (unsigned)args.nchunks);
   // this CTA's units: ranks [chunk T / nchunks, (chunk + 1) T / nchunks) of the T listed units
@@ -218,7 +220,7 @@ __global__ void __launch_bounds__(128, 1)
         float dot = 0.f;
         if (j < args.J) {
           const float p = __bfloat162float(args.P[(int64_t)j * args.d_pad + a]);
-          const float y = fmaf(args.sigma[j], p, v[c]);
+          const float y = args.sigma ? fmaf(args.sigma[j], p, v[c]) : v[c];
           args.Y[(int64_t)j * args.d_pad + a] = y;
           dot = p * y;
         }

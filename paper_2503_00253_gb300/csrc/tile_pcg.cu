@@ -501,16 +501,20 @@ __global__ void __launch_bounds__(kVecThreads) k_tpcg_direction(const ProblemDev
     const float pv[4] = {p01.x, p01.y, p23.x, p23.y};
     // column m of [Phi | C Phi] at the four rows: one 16-byte load
     const float4* col4 = phs_dyn4 + r4 / 4;
-    const float* cs = tcf + s * 2 * kMaxK;
 #pragma unroll
-    for (int m = 0; m < 2 * kMaxK; ++m) {
-      if (m < 2 * k) {
-        const float4 f = col4[m * (kPhCol / 4)];
-        const float c = cs[m];
-        z[0] = fmaf(f.x, c, z[0]);
-        z[1] = fmaf(f.y, c, z[1]);
-        z[2] = fmaf(f.z, c, z[2]);
-        z[3] = fmaf(f.w, c, z[3]);
+    for (int q = 0; q < 2 * kMaxK / 4; ++q) {
+      if (4 * q < 2 * k) {
+        const float4 c4 = tc4[s][q];   // four coefficients (a broadcast load)
+        const float cq[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          if (4 * q + i >= 2 * k) break;   // only 2 k columns are staged
+          const float4 f = col4[(4 * q + i) * (kPhCol / 4)];
+          z[0] = fmaf(f.x, cq[i], z[0]);
+          z[1] = fmaf(f.y, cq[i], z[1]);
+          z[2] = fmaf(f.z, cq[i], z[2]);
+          z[3] = fmaf(f.w, cq[i], z[3]);
+        }
       }
     }
 #pragma unroll

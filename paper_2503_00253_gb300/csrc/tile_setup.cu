@@ -707,7 +707,67 @@ void launch_tile_setup(const ProblemTable& tab, const ProblemDev* dtab, cudaStre
   note_launches(launches + 8);
 }
 
+// Y = C X of the Ritz basis on the tensor cores: X [d][l] (tile order) split
+// exactly into BF16 planes Xh = bf16(X), Xl = bf16(X - Xh), stored as the 2 l
+// "systems" [Xh; Xl] of the tile matvec in the PCG's direction buffer (free
+// during the set-up); then Y = C Xh + C Xl.
+__global__ void k_ritz_split(const ProblemDev* dp, int src) {
+  const ProblemDev& pr = *dp;
+  const int l = pr.l;
+  const int64_t dpad = pr.d_pad;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)l * dpad) return;
+  const int64_t m = i / dpad, a = i % dpad;
+  const float* X = reinterpret_cast<const float*>(src == 0 ? pr.Om : pr.Yb);
+  const float x = a < pr.d ? X[a * l + m] : 0.f;
+  const __nv_bfloat16 h = __float2bfloat16_rn(x);
+  pr.Pdir[i] = h;
+  pr.Pdir[(int64_t)l * dpad + i] = __float2bfloat16_rn(x - __bfloat162float(h));
+}
+
+__global__ void k_ritz_sum(const ProblemDev* dp, int src) {
+  const ProblemDev& pr = *dp;
+  const int l = pr.l;
+  const int64_t dpad = pr.d_pad;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= pr.d * l) return;
+  const int64_t a = i / l, m = i % l;
+  float* Y = reinterpret_cast<float*>(src == 0 ? pr.Yb : pr.Om);
+  Y[i] = pr.Yv[m * dpad + a] + pr.Yv[(l + m) * dpad + a];
+}
+
 void launch_tile_ritz_matvec(const ProblemTable& tab, const ProblemDev* dtab, int src, cudaStream_t st) {
+  // the tensor-core form needs room for 2 l systems in the direction buffer
+  bool tc = true;
+  for (int i = 0; i < tab.count; ++i) {
+    const ProblemDev& p = tab.p[i];
+    if (p.precision == 2 && p.l > 0 && p.nsys < 2 * (int64_t)p.l) tc = false;
+  }
+  for (int i = 0; tc && i < tab.count; ++i) {
+    const ProblemDev& p = tab.p[i];
+    if (p.precision != 2 || p.l <= 0) continue;
+    k_ritz_split<<<(unsigned)(((int64_t)p.l * p.d_pad + 255) / 256), 256, 0, st>>>(dtab + i, src);
+    TileMmArgs a{};
+    a.rowptr = p.rowptr;
+    a.colblk = p.colblk;
+    a.P = p.Pdir;
+    a.sigma = nullptr;
+    a.active = nullptr;
+    a.Y = p.Yv;
+    a.pty = nullptr;
+    a.status = p.status;
+    a.d_pad = p.d_pad;
+    a.J = 2 * p.l;
+    a.nrt = (int32_t)p.nrt;
+    if (launch_tile_mm(a, p.Chi, p.Clo, p.tile_cap, st) != 0) {
+      cudaGetLastError();
+      tc = false;   // the CUDA-core kernel below recomputes every problem
+      break;
+    }
+    k_ritz_sum<<<(unsigned)((p.d * p.l + 255) / 256), 256, 0, st>>>(dtab + i, src);
+    note_launches(2);
+  }
+  if (tc) return;
   int64_t nrt = 0;
   for (int i = 0; i < tab.count; ++i) nrt = tab.p[i].nrt > nrt ? tab.p[i].nrt : nrt;
   k_tile_ritz_matvec<<<dim3((unsigned)nrt, tab.count), kTileM, 0, st>>>(dtab, src);
