@@ -85,6 +85,8 @@ void launch_tile_finish(const ProblemTable& tab, const ProblemDev* dtab, cudaStr
 // The state update on the tensor cores (tile_state.cu): 0 when launched for
 // every BF16 problem; otherwise the caller runs the CUDA-core kernel.
 int launch_tile_state_mma(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st);
+// The C blocks of the set-up on the tensor cores (tile_form.cu), same contract.
+int launch_tile_form_mma(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st);
 // Lattice of the observations of each BF16 problem with a learned model (or
 // for a capture): detection and the stencil tables (tile_learn.cu).
 void launch_tile_lattice(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st);

@@ -5,6 +5,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -146,6 +147,99 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// --- operand staging shared by the tcgen05 kernels -------------------------
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// 1-D bulk copy global -> shared of `bytes` (multiple of 16, both addresses
+// 16-byte aligned), completing that many bytes of transaction count on `bar`.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic-proxy smem writes -> tensor core
+}
+
+// Byte offset of 16-byte chunk `chunk` (elements 8 chunk .. 8 chunk + 7) of
+// row `row` in a 128-byte-swizzled K-major region of 128-byte rows: 8-row
+// atoms of 1024 B, the chunk index XORed with row % 8 (the layout TMA writes
+// in SWIZZLE_128B mode).
+__device__ __forceinline__ uint32_t sw128_off(int row, int chunk) {
+  return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+__device__ __forceinline__ uint4 pack8(const float* v) {
+  return make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
+                    pack_bf16x2(v[6], v[7]));
+}
+
+__device__ __forceinline__ float bf16_round(float a) { return __bfloat162float(__float2bfloat16_rn(a)); }
+
+// The FP32 values of the packed BF16 pairs of w (.x = the first value, in the low half).
+__device__ __forceinline__ void unpack8(const uint4& w, float* v) {
+  const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    v[2 * i] = __uint_as_float(u[i] << 16);
+    v[2 * i + 1] = __uint_as_float(u[i] & 0xffff0000u);
+  }
+}
+
+// Eight FP32 values as two BF16 planes: hi = bf16(v), lo = bf16(v - hi).
+__device__ __forceinline__ void split8x2(const float* v, uint4& hi, uint4& lo) {
+  hi = pack8(v);
+  float h[8], r[8];
+  unpack8(hi, h);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) r[i] = v[i] - h[i];
+  lo = pack8(r);
+}
+
+// Gaspari-Cohn correlation at z = r / c >= 0 (Gaspari & Cohn 1999, Eq. 4.10),
+// branch-free: one degree-5 Horner form whose coefficients are selected by the
+// piece (z <= 1, 1 < z < 2), the rational term -2 / (3 z) of the outer piece,
+// zero from z = 2.  Lanes of a warp take different points, so a branch on the
+// piece would run both polynomials.
+__device__ __forceinline__ float gc_select(float z) {
+  const bool outer = z > 1.f;
+  const float a = outer ? (1.f / 12.f) : -0.25f;
+  const float b = outer ? -0.5f : 0.5f;
+  const float d = outer ? (5.f / 3.f) : (-5.f / 3.f);
+  const float e = outer ? -5.f : 0.f;
+  const float f = outer ? 4.f : 1.f;
+  float p = fmaf(fmaf(fmaf(fmaf(fmaf(a, z, b), z, 0.625f), z, d), z, e), z, f);
+  p = outer ? fmaf(-2.f / 3.f, __frcp_rn(z), p) : p;
+  return z < 2.f ? p : 0.f;
+}
+
+// Eight FP32 values as NP BF16 planes (16 bytes each): plane i holds the
+// rounding of what the planes before it leave.
+template <int NP>
+__device__ __forceinline__ void split8(const float* v, uint4 (&out)[NP]) {
+  float rem[8], pl[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) rem[i] = v[i];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      pl[i] = bf16_round(rem[i]);
+      rem[i] -= pl[i];
+    }
+    out[p] = pack8(pl);
+  }
 }
 
 // --- host: tensor maps ------------------------------------------------------

@@ -703,8 +703,13 @@ void launch_tile_setup(const ProblemTable& tab, const ProblemDev* dtab, cudaStre
                          (int)state_smem(kTileMaxN));
     raised = dev;
   }
-  k_tile_form<<<dim3((unsigned)nrt, P), kTileM, fs, st>>>(dtab);
-  note_launches(launches + 8);
+  note_launches(launches + 7);
+  // the C blocks on the tensor cores where every problem qualifies, else on the CUDA cores
+  if (launch_tile_form_mma(tab, dtab, st) != 0) {
+    cudaGetLastError();
+    k_tile_form<<<dim3((unsigned)nrt, P), kTileM, fs, st>>>(dtab);
+    note_launches(1);
+  }
 }
 
 // Y = C X of the Ritz basis on the tensor cores: X [d][l] (tile order) split
