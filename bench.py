@@ -209,7 +209,8 @@ def run_general_h(args):
 
 
 def run_band_phases(args):
-    """Per-round phase cycles of the 1-D band PCG kernel on the headline workload (learned model trained as
+    """Per-round phase cycles of the 1-D band PCG kernel, and per-stage cycles of the fused eigensolver
+    kernel, on the headline workload (learned model trained as
     in the default line, autotuned), from the instrumented build of the library (INFO_ESRF_PHASE_CLOCKS=1,
     set before the library loads). The timed bench line never uses this build."""
     os.environ["INFO_ESRF_PHASE_CLOCKS"] = "1"
@@ -238,10 +239,12 @@ def run_band_phases(args):
         st = B.info_esrf_analysis(pr.grid, X, obs, y, R, pr.Q, TOL_MIXED, opts)[2]
     torch.cuda.synchronize()
     B.band_phase_clocks(reset=True)
+    B.ritz_phase_clocks(reset=True)
     for _ in range(args.steps):
         B.info_esrf_analysis(pr.grid, X, obs, y, R, pr.Q, TOL_MIXED, opts)
     torch.cuda.synchronize()
     ph = B.band_phase_clocks(reset=True)
+    ph["ritz"] = B.ritz_phase_clocks(reset=True)
     ph["launches"] = args.steps
     ph["ctas"] //= args.steps
     rec = {"workload": WORKLOAD, "kind": "band_phase_clocks", "preconditioner": args.preconditioner,

@@ -100,6 +100,17 @@ int info_esrf_fma_probe(int32_t precision, int64_t iters, double* flops_per_s, d
  * Synchronizes the device. */
 int info_esrf_band_phase_clocks(int64_t* out, int32_t n, int32_t reset);
 
+/* Per-stage clock counts of the fused randomized eigensolver kernel (a4 of
+ * the FP32 path, App. E and Halko, Martinsson & Tropp Alg. 5.3), same build
+ * and contract as info_esrf_band_phase_clocks: thread 0 of cluster rank 0
+ * sums clock64() deltas over the launches since the last reset: out[0] test
+ * matrix, out[1] band products of the range finder, out[2] first and out[3]
+ * second CholeskyQR pass, out[4] C Q, out[5] Q^T C Q partials, out[6]
+ * Rayleigh-Ritz (merge, one-sided Jacobi, ordering), out[7] broadcast of the
+ * Ritz coefficients, out[8] Ritz vectors, out[9] Gram matrices; out[10]
+ * launches.  n values are written (at most 11). */
+int info_esrf_ritz_phase_clocks(int64_t* out, int32_t n, int32_t reset);
+
 /* Band capacities the workspace layout uses for these arguments. */
 int info_esrf_prepared_band_capacity(const info_esrf_grid* grid, int64_t N, int64_t d, int32_t Q,
                                      const info_esrf_options* opt, int64_t* max_oo, int64_t* max_xo);

@@ -155,6 +155,7 @@ def library() -> ctypes.CDLL:
         "info_esrf_prepared_band_capacity": (c_int32, [P(Grid), c_int64, c_int64, c_int32, P(Options),
                                                        P(c_int64), P(c_int64)]),
         "info_esrf_band_phase_clocks": (c_int32, [P(c_int64), c_int32, c_int32]),
+        "info_esrf_ritz_phase_clocks": (c_int32, [P(c_int64), c_int32, c_int32]),
         "info_esrf_learn_lattice_scratch_size": (ctypes.c_size_t, [c_int32, c_int64]),
         "info_esrf_learn_loss_grad_lattice": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p,
                                                         c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
@@ -277,6 +278,22 @@ def band_phase_clocks(reset: bool = True) -> dict:
     per_round = {name: v[i] / max(rounds, 1) for i, name in enumerate(BAND_PHASES)}
     return {"cycles_per_round": per_round, "rounds_per_cta": rounds / ctas, "setup_cycles_per_cta": v[11] / ctas,
             "ctas": v[12], "total_per_round": sum(v[:10]) / max(rounds, 1)}
+
+
+RITZ_PHASES = ("test matrix", "range-finder band products", "CholeskyQR pass 1", "CholeskyQR pass 2", "C Q",
+               "Q^T C Q partials", "Rayleigh-Ritz (merge, Jacobi, ordering)", "Ritz coefficient broadcast",
+               "Ritz vectors", "Gram matrices")
+
+
+def ritz_phase_clocks(reset: bool = True) -> dict:
+    """Per-stage cycles of the fused eigensolver kernel since the last reset
+    (instrumented build only: INFO_ESRF_PHASE_CLOCKS=1), averaged over launches."""
+    out = (c_int64 * 11)()
+    _check(library().info_esrf_ritz_phase_clocks(out, 11, 1 if reset else 0), "info_esrf_ritz_phase_clocks")
+    v = list(out)
+    n = max(v[10], 1)
+    return {"cycles_per_launch": {name: v[i] / n for i, name in enumerate(RITZ_PHASES)}, "launches": v[10],
+            "total_per_launch": sum(v[:10]) / n}
 
 
 def fma_probe(precision: int, iters: int, stream=None):

@@ -20,6 +20,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "info_esrf.h"
 #include "internal.h"
 
 namespace cg = cooperative_groups;
@@ -35,7 +36,23 @@ constexpr int kRTmp = 1024;                         // (entry, chunk) partials
 constexpr int kRParts = 4;                          // threads per row in the band product
 constexpr int kRMaxRows = kRT / kRParts;            // own rows per CTA (128)
 constexpr size_t kRStageBytes = 144 * 1024;         // shared staging of a full d x l block
+// Phase clocks (built only with -DINFO_ESRF_PHASE_CLOCKS, a separate build of
+// the library): thread 0 of cluster rank 0 sums clock64() deltas per stage
+// and adds them, with a launch count, into g_ritz_phase at exit;
+// info_esrf_ritz_phase_clocks reads them.
+constexpr int kRitzPhases = 10;
 }  // namespace
+#ifdef INFO_ESRF_PHASE_CLOCKS
+__device__ unsigned long long g_ritz_phase[kRitzPhases + 1];
+#define RITZ_PHASE(i)                 \
+  if (tid == 0 && crank == 0) {       \
+    const long long now_ = clock64(); \
+    ph_c[i] += now_ - ph_t;           \
+    ph_t = now_;                      \
+  }
+#else
+#define RITZ_PHASE(i)
+#endif
 
 // Whether the fused kernel takes a problem: the whole d x l block must fit the
 // shared staging area and the own rows of a CTA one pass of the band product.
@@ -70,6 +87,10 @@ __global__ void __launch_bounds__(kRT, 1) k_ritz_cluster(const ProblemDev* tab) 
   __shared__ float Vk[kRL][kMaxK];
   __shared__ float s_scale, s_tiny, s_trw[kRW];
   if (l <= 0 || k <= 0) return;                     // uniform over the cluster
+#ifdef INFO_ESRF_PHASE_CLOCKS
+  long long ph_c[kRitzPhases] = {};
+  long long ph_t = clock64();
+#endif
 
   // ---- partial Gram of the own rows from shared memory: entries (i, j) of A^T B ----
   auto gram_partial = [&](const float (*A)[kRL + 1], const float (*Bm)[kRL + 1], int nc, bool sym) {
@@ -240,22 +261,31 @@ __global__ void __launch_bounds__(kRT, 1) k_ritz_cluster(const ProblemDev* tab) 
     buf[0][a * l + j] = philox_normal_f(pr.seed, (uint64_t)j * (uint64_t)d + (uint64_t)a);
   }
   cluster.sync();
+  RITZ_PHASE(0);
   matvec(buf[0], buf[1], ys);                        // Y = C Omega (own rows in ys)
+  RITZ_PHASE(1);
   for (int it = 0; it < pr.power_iters; ++it) {
     cholqr_pass(buf[0]);
+    RITZ_PHASE(2);
     cholqr_pass(buf[1]);                             // Q in ys and buf[1]
+    RITZ_PHASE(3);
     matvec(buf[1], buf[0], ys);                      // C Q
     cluster.sync();
+    RITZ_PHASE(1);
     // the next block lives in buf[0]; keep buf[1] as the spare
     float* t = buf[0]; buf[0] = buf[1]; buf[1] = t;
   }
   cholqr_pass(buf[0]);
+  RITZ_PHASE(2);
   cholqr_pass(buf[1]);                               // basis Q: ys, buf[1]
+  RITZ_PHASE(3);
   matvec(buf[1], buf[0], zs);                        // C Q: zs, buf[0]
   cluster.sync();
+  RITZ_PHASE(4);
   // ---- Rayleigh-Ritz: B = Q^T (C Q), eigenpairs by one-sided Jacobi in CTA 0 ----
   gram_partial(ys, zs, l, false);
   cluster.sync();
+  RITZ_PHASE(5);
   if (crank == 0) {
     gram_merge(l * l, Tp_h, Tp_l);
     __syncthreads();
@@ -350,12 +380,14 @@ __global__ void __launch_bounds__(kRT, 1) k_ritz_cluster(const ProblemDev* tab) 
       }
     }
   }
+  RITZ_PHASE(6);
   cluster.sync();                                    // Vk of CTA 0 complete
   {
     const float* Vk0 = cluster.map_shared_rank(&Vk[0][0], 0);
     for (int e = tid; e < l * kMaxK; e += kRT) (&Vk[0][0])[e] = Vk0[e];
   }
   cluster.sync();                                    // copies done before CTA 0 moves on
+  RITZ_PHASE(7);
   // ---- Ritz vectors on the own rows: Phi = Q V_k, C Phi = (C Q) V_k ----
   float* Phi = reinterpret_cast<float*>(pr.Phi);
   float* CPhi = reinterpret_cast<float*>(pr.CPhi);
@@ -374,6 +406,7 @@ __global__ void __launch_bounds__(kRT, 1) k_ritz_cluster(const ProblemDev* tab) 
     CPhi[(r0 + a) * k + j] = cp;
   }
   __syncthreads();
+  RITZ_PHASE(8);
   // ---- Gram matrices of Phi and A = C Phi: gram[0] = Phi^T Phi, [1] = A^T Phi, [2] = A^T A ----
   for (int w3 = 0; w3 < 3; ++w3) {
     gram_partial(w3 == 0 ? ph_s : cp_s, w3 == 2 ? cp_s : ph_s, k, false);
@@ -385,6 +418,13 @@ __global__ void __launch_bounds__(kRT, 1) k_ritz_cluster(const ProblemDev* tab) 
     }
     cluster.sync();                                  // partial reads done before the next overwrite
   }
+  RITZ_PHASE(9);
+#ifdef INFO_ESRF_PHASE_CLOCKS
+  if (tid == 0 && crank == 0) {
+    for (int i = 0; i < kRitzPhases; ++i) atomicAdd(&g_ritz_phase[i], (unsigned long long)ph_c[i]);
+    atomicAdd(&g_ritz_phase[kRitzPhases], 1ull);
+  }
+#endif
 }
 
 int launch_ritz_cluster(const ProblemTable& tab, const ProblemDev* dtab, cudaStream_t st) {
@@ -437,3 +477,29 @@ int launch_ritz_cluster(const ProblemTable& tab, const ProblemDev* dtab, cudaStr
 }
 
 }  // namespace infoesrf
+
+extern "C" int info_esrf_ritz_phase_clocks(int64_t* out, int32_t n, int32_t reset) {
+#ifdef INFO_ESRF_PHASE_CLOCKS
+  using namespace infoesrf;
+  if (!out || n < 1) return INFO_ESRF_ERR_INVALID_ARG;
+  unsigned long long h[kRitzPhases + 1] = {};
+  if (cudaMemcpyFromSymbol(h, g_ritz_phase, sizeof(h)) != cudaSuccess) {
+    cudaGetLastError();
+    return INFO_ESRF_ERR_CUDA;
+  }
+  for (int i = 0; i < n && i < kRitzPhases + 1; ++i) out[i] = (int64_t)h[i];
+  if (reset) {
+    const unsigned long long z[kRitzPhases + 1] = {};
+    if (cudaMemcpyToSymbol(g_ritz_phase, z, sizeof(z)) != cudaSuccess) {
+      cudaGetLastError();
+      return INFO_ESRF_ERR_CUDA;
+    }
+  }
+  return 0;
+#else
+  (void)out;
+  (void)n;
+  (void)reset;
+  return INFO_ESRF_ERR_UNSUPPORTED;
+#endif
+}
