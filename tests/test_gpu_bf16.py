@@ -104,6 +104,18 @@ def test_bf16_ragged_and_degenerate_sizes(B, case):
     check(pr, mu_a, A_a)
 
 
+@pytest.mark.parametrize("N", [3, 17, 100, 128])
+def test_bf16_member_counts(B, N):
+    """Member counts around the 16-member steps of the tensor-core C formation and state update (the
+    steps past N are skipped) and their largest case, N = 128, on a 2-D periodic grid."""
+    pr = workloads.gaussian_problem_2d(nx=48, ny=48, N=N, length_scale=6.0, obs_stride=2, r2=0.5,
+                                       half_width=5.0, Q=4, tol=1e-6, seed=40 + N)
+    mu_a, A_a, st = run(B, pr)
+    assert st["status"] == 0 and st["solver_path"] == 3 and st["n_unconverged"] == 0, (N, st)
+    ea, em = check(pr, mu_a, A_a)
+    print(f"N = {N}: {ea:.2e} {em:.2e}")
+
+
 def test_bf16_matches_fp32_path_and_reports_unsupported(B):
     pr = workloads.gaussian_problem_1d("cmp", n=4096, N=24, length_scale=32.0, obs_stride=4, r2=0.25,
                                        half_width=128.0, Q=12, tol=1e-6, seed=9)
