@@ -15,10 +15,10 @@
 // weights), is accumulated per thread in FP32 from the weighted S in registers
 // and across blocks in FP64.
 //
-// CTA of 10 warps per state tile: warp 8 lane 0 loads W_blk and Vbar_blk^T with
+// CTA of 18 warps per state tile: warp 16 lane 0 loads W_blk and Vbar_blk^T with
 // 2-D TMA (128-byte swizzle) and the block's coordinates and mean-column values
-// with bulk copies; warp 9 lane 0 issues the MMAs; warps 0-7 (two per TMEM lane
-// quadrant, one state point and half of the block's observations per thread)
+// with bulk copies; warp 17 lane 0 issues the MMAs; warps 0-15 (four per TMEM
+// lane quadrant, one state point and 16 of the block's observations per thread)
 // read S from tensor memory, apply the Gaspari-Cohn weights, add the mean
 // column's terms, split S and write it to shared memory as the A operand of the
 // second product, and finally write A_a and mu_a.  Pipelined: S has two TMEM
@@ -39,7 +39,10 @@ namespace infoesrf {
 
 namespace {
 
-constexpr int kStThreads = 320;   // warps 0-7 epilogue (two per TMEM lane quadrant), 8 loads, 9 MMAs
+constexpr int kEpiWarps = 16;                  // epilogue warps: four per TMEM lane quadrant
+constexpr int kEpiCols = kTileK * 4 / kEpiWarps;   // columns of S per epilogue thread (16)
+constexpr int kLoadWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1;
+constexpr int kStThreads = (kEpiWarps + 2) * 32;
 constexpr int kSideBytes = kTileK * 16 + kTileK * 4;   // a block's grid coordinates and mean-column values
 constexpr int kHalf = kTileM * 64 * 2;         // one 64-member half of a 128-row BF16 operand: 16 KB
 constexpr int kWHalf = kTileK * 64 * 2;        // one 64-member half of the W block: 8 KB
@@ -127,7 +130,7 @@ __global__ void __launch_bounds__(kStThreads, 1)
   uint64_t* xfull = bar + 2;     // [2] side buffer b % 2 landed, phase b / 2    (epilogue)
   uint64_t* g1done = bar + 4;    // [2] S(b) in TMEM buffer b % 2, phase b / 2   (epilogue, loads)
   uint64_t* g2done = bar + 6;    // second product of b done: Vbar^T and the S planes free (loads, epilogue)
-  uint64_t* sready = bar + 7;    // S planes of b written, TMEM buffer b % 2 read (MMA; 256 arrivals)
+  uint64_t* sready = bar + 7;    // S planes of b written, TMEM buffer b % 2 read (MMA; every epilogue thread)
   uint64_t* accf = bar + 8;      // every MMA done
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 9);
   int* flags = reinterpret_cast<int*>(tslot + 1);   // [0] abort, [1] W/side loads issued, [2] Vbar loads, [3] skip
@@ -143,7 +146,7 @@ __global__ void __launch_bounds__(kStThreads, 1)
   const int64_t x0 = st * kTileM;
   const int N = (int)pr.N;
   if (tid == 0) {
-    for (int i = 0; i < 9; ++i) mbar_init(bar + i, i == 7 ? 256 : 1);
+    for (int i = 0; i < 9; ++i) mbar_init(bar + i, i == 7 ? kEpiWarps * 32 : 1);
     flags[0] = 0;
     flags[1] = 0;
     flags[2] = 0;
@@ -154,7 +157,7 @@ __global__ void __launch_bounds__(kStThreads, 1)
     tma_prefetch_map(&map_vh);
     tma_prefetch_map(&map_vl);
   }
-  if (warp == 8) tmem_alloc(tslot, 256);
+  if (warp == kLoadWarp) tmem_alloc(tslot, 256);
   // Z_tile as the A operand of the first product: one state point per thread,
   // members split into three BF16 planes, 128-byte-swizzled 64-member halves
   if (tid < kTileM) {   // warps 0-3
@@ -184,7 +187,7 @@ __global__ void __launch_bounds__(kStThreads, 1)
   const uint32_t tmem = *tslot;
   const uint32_t t_s = tmem, t_acc = tmem + 2 * kTileK;   // S buffers at columns 0 and 64, acc at 128
 
-  if (warp == 8) {
+  if (warp == kLoadWarp) {
     if (lane == 0) {
       // loads: W_blk (three planes, two 64-member halves each) with the block's
       // coordinates and mean-column values, then Vbar_blk^T (hi, lo)
@@ -224,7 +227,7 @@ __global__ void __launch_bounds__(kStThreads, 1)
         flags[2] = kv;
       }
     }
-  } else if (warp == 9) {
+  } else if (warp == kMmaWarp) {
     if (lane == 0) {
       // MMAs, software-pipelined: the first product of it, then the second of it - 1
       //   S(it) = Z W(it)^T (six terms, two halves) into TMEM buffer it % 2
@@ -281,8 +284,8 @@ __global__ void __launch_bounds__(kStThreads, 1)
       mma_commit(accf);
     }
   } else {
-    // warps 0-7: state point `row` (TMEM lane) and observations half * 32 .. half * 32 + 31
-    const int quad = warp & 3, half = warp >> 2;
+    // warps 0-15: state point `row` (TMEM lane) and observations grp * 16 .. grp * 16 + 15
+    const int quad = warp & 3, grp = warp >> 2;
     const int row = quad * 32 + lane;
     const int64_t x = x0 + row;
     const bool xin = x < pr.n;
@@ -293,7 +296,7 @@ __global__ void __launch_bounds__(kStThreads, 1)
     const int offy = (int)g.ext[0], offz = (int)(g.ext[0] + g.ext[1]);
     const uint32_t trow = (uint32_t)(quad * 32) << 16;
     unsigned char* s_hi = smem + Lo.s;
-    double macc = 0.0;   // this half's part of the mean column, FP64 across blocks
+    double macc = 0.0;   // this group's part of the mean column, FP64 across blocks
     // exits are warp-uniform: the TMEM loads below are warp-collective
     for (int kb = 0; kb < nk; ++kb) {
       const int bf = kb & 1, ph = (kb >> 1) & 1;
@@ -303,25 +306,19 @@ __global__ void __launch_bounds__(kStThreads, 1)
       }
       tc_fence_after();
       const unsigned char* side = smem + Lo.side + bf * kSideBytes;
-      const int4* cs = reinterpret_cast<const int4*>(side);
-      const float* vm = reinterpret_cast<const float*>(side + kTileK * 16);
-      float sv[32];
-#pragma unroll
-      for (int c0 = 0; c0 < 32; c0 += 16) {
-        float v[16];
-        tmem_ld16(t_s + (uint32_t)(bf * kTileK) + trow + (uint32_t)(half * 32 + c0), v);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) sv[c0 + i] = v[i];
-      }
+      const int4* cs = reinterpret_cast<const int4*>(side) + grp * kEpiCols;
+      const float* vm = reinterpret_cast<const float*>(side + kTileK * 16) + grp * kEpiCols;
+      float sv[kEpiCols];
+      tmem_ld16(t_s + (uint32_t)(bf * kTileK) + trow + (uint32_t)(grp * kEpiCols), sv);
       // Gaspari-Cohn weights of the pairs (state point, observation), and the mean column
       float mb = 0.f;
 #pragma unroll
-      for (int c = 0; c < 32; ++c) {
-        const int4 ob = cs[half * 32 + c];
+      for (int c = 0; c < kEpiCols; ++c) {
+        const int4 ob = cs[c];
         const float r2 = (d2[abs(cxi - ob.x)] + d2[offy + abs(cyi - ob.y)]) + d2[offz + abs(czi - ob.z)];
         const float z = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
         sv[c] = (ob.w >= 0 && r2 < 4.f) ? gc_select(z) * sv[c] : 0.f;
-        mb = fmaf(sv[c], vm[half * 32 + c], mb);
+        mb = fmaf(sv[c], vm[c], mb);
       }
       macc += (double)mb;
       // the second product of the previous block has read the S planes
@@ -330,10 +327,10 @@ __global__ void __launch_bounds__(kStThreads, 1)
         break;
       }
 #pragma unroll
-      for (int chunk = 0; chunk < 4; ++chunk) {
+      for (int chunk = 0; chunk < kEpiCols / 8; ++chunk) {
         uint4 hi, lo;
         split8x2(sv + 8 * chunk, hi, lo);
-        const uint32_t off = sw128_off(row, half * 4 + chunk);
+        const uint32_t off = sw128_off(row, grp * (kEpiCols / 8) + chunk);
         *reinterpret_cast<uint4*>(s_hi + off) = hi;
         *reinterpret_cast<uint4*>(s_hi + kHalf + off) = lo;
       }
@@ -346,7 +343,7 @@ __global__ void __launch_bounds__(kStThreads, 1)
     tc_fence_after();
     const bool ok = __all_sync(0xffffffffu, got && *reinterpret_cast<volatile int*>(&flags[0]) == 0);
     const double mu = xin ? pr.mu[x] : 0.0;
-    for (int c0 = half * 16; c0 < NV; c0 += 32) {   // the halves take alternate 16-column chunks
+    for (int c0 = grp * 16; c0 < NV; c0 += 16 * (kEpiWarps / 4)) {   // the groups take alternate 16-column chunks
       float v[16];
       if (nk > 0 && ok) {
         tmem_ld16(t_acc + trow + (uint32_t)c0, v);
@@ -363,11 +360,15 @@ __global__ void __launch_bounds__(kStThreads, 1)
           pr.A_a[(int64_t)col * pr.n + x] = (pr.X[(int64_t)col * pr.n + x] - mu) - pr.sqrt_nm1 * inc;
       }
     }
-    // the mean column: half 1 hands its part to half 0 (the S planes are free now)
-    double* red = reinterpret_cast<double*>(s_hi);
-    if (half == 1) red[row] = macc;
-    asm volatile("bar.sync 1, 256;" ::: "memory");   // the eight epilogue warps
-    if (half == 0 && xin && ok && pr.do_mean) pr.mu_a[x] = mu + (macc + red[row]);
+    // the mean column: groups 1.. hand their parts to group 0 (the S planes are free now)
+    double* red = reinterpret_cast<double*>(s_hi);   // [groups - 1][128]
+    if (grp > 0) red[(grp - 1) * kTileM + row] = macc;
+    asm volatile("bar.sync 1, %0;" ::"r"(kEpiWarps * 32) : "memory");   // the epilogue warps
+    if (grp == 0 && xin && ok && pr.do_mean) {
+      double t = macc;
+      for (int q = 1; q < kEpiWarps / 4; ++q) t += red[(q - 1) * kTileM + row];
+      pr.mu_a[x] = mu + t;
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -384,7 +385,7 @@ __global__ void __launch_bounds__(kStThreads, 1)
     atomicOr(&pr.status[0], kStatTimeout);
   }
   __syncthreads();
-  if (warp == 8) tmem_dealloc(tmem, 256);
+  if (warp == kLoadWarp) tmem_dealloc(tmem, 256);
 }
 
 }  // namespace
