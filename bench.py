@@ -637,7 +637,7 @@ def config5_record(B, dev, steps, warmup, no_parity=False, ritz=RITZ, learned_te
     Learned correction (learned_term): the 2-D lattice form, trained before the timed region on
     Krylov samples of the BF16 path from two problems of the same geometry on a 512 x 512 grid
     (seeds 51, 52; 12 directions of 3 members per node, 300 Adam steps), with the shift cut-off
-    chosen by the plain-PCG judge on those problems; the timed analyses use it where the judge
+    chosen by the plain-PCG comparison on those problems; the timed analyses use it where that comparison
     keeps it.
 
     small: the same family on a 512 x 512 grid with GC half-width 48 cells and Q = 8 (d = 65,536,

@@ -74,7 +74,7 @@ def system_iterations(pr, options, device="cuda"):
 
 
 def choose_max_shift(theta, problems, ritz_rank: int = 10):
-    """Plain PCG as the judge: the shift cut-off that minimizes the total number
+    """Plain PCG as the reference: the shift cut-off that minimizes the total number
     of iterations over the problems, comparing every quadrature node's systems
     with and without the learned term.  Returns sigma*; when the term never
     helps, 0.5 (below every shift sigma = s_q + 1 >= 1, so the term is off)."""
@@ -103,7 +103,7 @@ def choose_max_shift(theta, problems, ritz_rank: int = 10):
 
 
 def fit(train_problems, K: int = 12, members_per_q: int = 3, steps: int = 300, lr: float = 3e-3, seed: int = 0):
-    """Capture, train and judge: returns (theta, max_shift, loss history)."""
+    """Capture, train and choose the shift cut-off: returns (theta, max_shift, loss history)."""
     V, Y, Z, feat = capture(train_problems, K=K, members_per_q=members_per_q)
     theta, hist = train(V, Y, Z, feat, steps=steps, lr=lr, seed=seed)
     return theta, choose_max_shift(theta, train_problems), hist
@@ -156,7 +156,8 @@ def choose_max_shift_bf16(theta, problems, ritz_rank: int = 10):
 
 def fit_lattice(train_problems, K: int = 12, members_per_q: int = 3, steps: int = 300, lr: float = 3e-3,
                 seed: int = 0):
-    """Capture, train and judge the 2-D lattice form on BF16 problems: returns (theta, max_shift, loss history)."""
+    """Capture, train and choose the shift cut-off of the 2-D lattice form on BF16 problems: returns (theta,
+    max_shift, loss history)."""
     V, Y, Z, feat, lx, ly = capture_lattice(train_problems, K=K, members_per_q=members_per_q)
     theta = init_params(seed, device=V.device)
     hist, _ = B.learn_train_lattice(theta, feat, V, Y, Z, lx, ly, steps, lr)
