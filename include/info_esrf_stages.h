@@ -111,6 +111,19 @@ int info_esrf_band_phase_clocks(int64_t* out, int32_t n, int32_t reset);
  * launches.  n values are written (at most 11). */
 int info_esrf_ritz_phase_clocks(int64_t* out, int32_t n, int32_t reset);
 
+/* One bounded wait on a shared-memory mbarrier, the wait every tensor-core
+ * kernel of the BF16 path uses for its copies and MMAs (those give up after
+ * about 2^32 cycles and report INFO_ESRF_ERR_TIMEOUT).  Thread 0 of one block
+ * initializes a barrier expecting one arrival, arrives on it first when
+ * `arrive` != 0, then waits for it at most `limit_cycles` SM cycles
+ * (1 .. 2^32); *status_dev (device, one int32) becomes 0 when the wait
+ * succeeded and the timeout status bit (128) when it ran out.  With arrive = 0
+ * nothing ever arrives, so the call shows the bounded wait ending and the
+ * context staying usable, without a fault or a hang.  Asynchronous on
+ * `stream`; INFO_ESRF_ERR_INVALID_ARG for a null status or a limit out of
+ * range. */
+int info_esrf_wait_probe(int64_t limit_cycles, int32_t arrive, int32_t* status_dev, void* stream);
+
 /* Band capacities the workspace layout uses for these arguments. */
 int info_esrf_prepared_band_capacity(const info_esrf_grid* grid, int64_t N, int64_t d, int32_t Q,
                                      const info_esrf_options* opt, int64_t* max_oo, int64_t* max_xo);

@@ -156,6 +156,7 @@ def library() -> ctypes.CDLL:
                                                        P(c_int64), P(c_int64)]),
         "info_esrf_band_phase_clocks": (c_int32, [P(c_int64), c_int32, c_int32]),
         "info_esrf_ritz_phase_clocks": (c_int32, [P(c_int64), c_int32, c_int32]),
+        "info_esrf_wait_probe": (c_int32, [c_int64, c_int32, c_void_p, c_void_p]),
         "info_esrf_learn_lattice_scratch_size": (ctypes.c_size_t, [c_int32, c_int64]),
         "info_esrf_learn_loss_grad_lattice": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p,
                                                         c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
@@ -294,6 +295,13 @@ def ritz_phase_clocks(reset: bool = True) -> dict:
     n = max(v[10], 1)
     return {"cycles_per_launch": {name: v[i] / n for i, name in enumerate(RITZ_PHASES)}, "launches": v[10],
             "total_per_launch": sum(v[:10]) / n}
+
+
+def wait_probe(limit_cycles: int, arrive: bool, status: torch.Tensor, stream=None) -> None:
+    """One bounded mbarrier wait on the device (status: int32 CUDA tensor, one element)."""
+    _need(status, torch.int32, "status")
+    _check(library().info_esrf_wait_probe(int(limit_cycles), 1 if arrive else 0, status.data_ptr(), _stream(stream)),
+           "info_esrf_wait_probe")
 
 
 def fma_probe(precision: int, iters: int, stream=None):

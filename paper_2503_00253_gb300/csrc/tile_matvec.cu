@@ -324,3 +324,32 @@ extern "C" int info_esrf_bf16_tile_matvec(int32_t n_row_tiles, const int32_t* ro
   cudaGetLastError();
   return launch_tile_mm(a, C_hi_dev, C_lo_dev, n_tiles, reinterpret_cast<cudaStream_t>(stream));
 }
+
+namespace infoesrf {
+namespace {
+
+// One bounded mbarrier wait, as the tensor-core kernels wait for their copies
+// and MMAs: thread 0 initializes a barrier of one arrival, arrives on it first
+// when `arrive` is set, then waits for its phase 0 at most `limit` cycles and
+// records kStatTimeout in *status when the wait ran out.  Nothing faults or
+// hangs: with no arrival the wait ends after the limit.
+__global__ void k_wait_probe(long long limit, int arrive, int32_t* status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  fence_mbar_init();
+  if (arrive) mbar_arrive(&bar);
+  status[0] = mbar_wait(&bar, 0, limit) ? 0 : kStatTimeout;
+}
+
+}  // namespace
+}  // namespace infoesrf
+
+extern "C" int info_esrf_wait_probe(int64_t limit_cycles, int32_t arrive, int32_t* status_dev, void* stream) {
+  if (!status_dev || limit_cycles < 1 || limit_cycles > infoesrf::kWaitCycles) return INFO_ESRF_ERR_INVALID_ARG;
+  cudaGetLastError();
+  infoesrf::k_wait_probe<<<1, 32, 0, reinterpret_cast<cudaStream_t>(stream)>>>((long long)limit_cycles,
+                                                                                arrive ? 1 : 0, status_dev);
+  infoesrf::note_launches(1);
+  return cudaGetLastError() == cudaSuccess ? INFO_ESRF_OK : INFO_ESRF_ERR_CUDA;
+}
