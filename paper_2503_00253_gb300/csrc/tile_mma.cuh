@@ -209,8 +209,8 @@ __device__ __forceinline__ void split8x2(const float* v, uint4& hi, uint4& lo) {
 
 // Gaspari-Cohn correlation at z = r / c >= 0 (Gaspari & Cohn 1999, Eq. 4.10),
 // branch-free: one degree-5 Horner form whose coefficients are selected by the
-// piece (z <= 1, 1 < z < 2), the rational term -2 / (3 z) of the outer piece,
-// zero from z = 2.  Lanes of a warp take different points, so a branch on the
+// piece (z <= 1, 1 < z < 2), the rational term -2 / (3 z) of the outer piece
+// through the fast reciprocal, zero from z = 2.  Lanes of a warp take different points, so a branch on the
 // piece would run both polynomials.
 __device__ __forceinline__ float gc_select(float z) {
   const bool outer = z > 1.f;
@@ -220,7 +220,7 @@ __device__ __forceinline__ float gc_select(float z) {
   const float e = outer ? -5.f : 0.f;
   const float f = outer ? 4.f : 1.f;
   float p = fmaf(fmaf(fmaf(fmaf(fmaf(a, z, b), z, 0.625f), z, d), z, e), z, f);
-  p = outer ? fmaf(-2.f / 3.f, __frcp_rn(z), p) : p;
+  p = outer ? fmaf(-2.f / 3.f, __fdividef(1.f, z), p) : p;   // z in (1, 2): within 2 ulp
   return z < 2.f ? p : 0.f;
 }
 
