@@ -212,7 +212,7 @@ def run_band_phases(args):
     """Per-round phase cycles of the 1-D band PCG kernel, and per-stage cycles of the fused eigensolver
     kernel, on the headline workload (learned model trained as
     in the default line, autotuned), from the instrumented build of the library (INFO_ESRF_PHASE_CLOCKS=1,
-    set before the library loads). The timed bench line never uses this build."""
+    set before the library loads). The timed bench line never uses the instrumented library."""
     os.environ["INFO_ESRF_PHASE_CLOCKS"] = "1"
     import torch
 
